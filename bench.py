@@ -1,0 +1,344 @@
+"""Benchmark of the columnwise W, V setup (direct approximate factoring of the
+inverse) on one GB300, printing one JSON line.
+
+Workload (default): 2D upwind convection-diffusion on a 256 x 256 grid
+(n = 65,536), W pattern = pattern(A^2) (<= 13 indices per column), V = the
+optimal upper-triangular pattern chosen by the leverage rule with the
+Gauss-Seidel budget, DIAF-S (unit w_j), b = A ones.
+
+One step = one pass of the whole hot path over the workload: the setup
+(symbolic pass, gather, QR, V rule, DIAF solve, scatter into CSC W and V)
+plus one application of W V^-1 (row-oriented copies and the triangular
+solve).  value = columns per second of that step with the inputs resident in
+HBM; L2 is flushed (a 256 MiB write) before every timed step.  e2e = the same
+through the public API from pinned host buffers, with the inputs copied in
+and W, V, the residuals copied out inside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl diaf|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import make_workload  # noqa: E402
+
+METRIC = "W,V setup columns/s (DIAF-S, 256x256 convection-diffusion, W = pattern(A^2))"
+UNIT = "columns/s"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# FP64 arithmetic peak of the GB300 (no measured figure exists in the peaks
+# file): 1.25 TFLOP/s nominal at the 2070 MHz maximum SM clock.
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def algorithmic_flops(m: np.ndarray, k: np.ndarray, l: np.ndarray, alg: str, cplx: bool) -> float:
+    """Real flops the method needs per column (the SVD counted as the
+    textbook 4pq^2 + 8q^3 for singular values and right vectors of a p x q
+    matrix): QR of the m x k tile 2k^2(m - k/3), leverage m k^2, then
+    DIAF-S: QR of the tile without I_j rows + SVD of its k x k R;
+    DIAF-Q: SVD of the l x k Q_I + triangular solve k^2; plus v and the
+    residual 2lk + 2mk.  Complex arithmetic counts 4x."""
+    m = m.astype(np.float64); k = k.astype(np.float64); l = l.astype(np.float64)
+    f = 2 * k**2 * (m - k / 3) + m * k**2 + 2 * l * k + 2 * m * k
+    if alg == "S":
+        f += 2 * k**2 * (np.maximum(m - l, k) - k / 3) + 12 * k**3
+    else:
+        f += 4 * l * k**2 + 8 * k**3 + k**2
+    return float(f.sum() * (4 if cplx else 1))
+
+
+def tile_sizes(w):
+    """m_j = |R_j| and k_j of the workload (structure only)."""
+    import scipy.sparse as sp
+    A, PW = w.A, w.PW
+    B = sp.csc_matrix((np.ones(A.nnz), A.rowidx, A.colptr), shape=(A.n, A.n))
+    P = sp.csc_matrix((np.ones(PW.nnz), PW.rowidx, PW.colptr), shape=(A.n, A.n))
+    m = np.diff((B @ P).tocsc().indptr)
+    return m, PW.counts()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = [r.split(", ") for r in (self.out or "").strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(w, alg, seconds=12.0):
+    """The oracle as it stands, on this host's cores, on whole passes over the
+    workload's columns until about `seconds` of CPU work."""
+    import oracle as O
+    cores = os.cpu_count() or 1
+    O.factor(w.A, w.PW, w.vrule, w.budget, alg=alg, cols=np.arange(64, dtype=np.int32))  # build + warm
+    t0 = time.perf_counter()
+    cols = 0
+    passes = 0
+    while time.perf_counter() - t0 < seconds:
+        O.factor(w.A, w.PW, w.vrule, w.budget, alg=alg, nthreads=cores)
+        cols += w.n
+        passes += 1
+    dt = time.perf_counter() - t0
+    return {"value": cols / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{passes} full pass(es) over all {w.n} columns ({dt:.1f} s, OpenMP over columns)"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle, timed on the host's cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = make_workload(args.workload, alg=args.alg)
+    import oracle as O
+    cores = os.cpu_count() or 1
+    O.factor(w.A, w.PW, w.vrule, w.budget, alg=args.alg, cols=np.arange(64, dtype=np.int32))
+    for _ in range(args.warmup):
+        O.factor(w.A, w.PW, w.vrule, w.budget, alg=args.alg, nthreads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.factor(w.A, w.PW, w.vrule, w.budget, alg=args.alg, nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(times))
+    val = w.n / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n": w.n, "alg": args.alg, "columns_per_step": w.n},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} full pass(es) over all {w.n} columns"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="diaf", choices=["diaf", "reference"])
+    ap.add_argument("--workload", default="convdiff256_A2")
+    ap.add_argument("--alg", default="S", choices=["S", "Q"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the solve / other-form side measurements")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1208_3573_gb300 import diaf
+
+    w = make_workload(args.workload, alg=args.alg)
+    cplx = w.A.is_complex
+    A = diaf.DeviceCSC.from_host(w.A)
+    PW = diaf.DeviceCSC.from_host(w.PW)
+    bud = torch.from_numpy(w.budget).to(dev)
+    x1 = torch.ones(w.n, dtype=torch.complex128 if cplx else torch.float64, device=dev)
+    y1 = torch.empty_like(x1)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(Ad, PWd, budd):
+        F = diaf.factor(Ad, PWd, w.vrule, budd, alg=args.alg, prec=args.prec, stream=stream)
+        F.apply(x1, y1, stream=stream)
+        return F
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    lcount = None
+    for _ in range(args.warmup):
+        F = step(A, PW, bud)
+        if lcount is None:
+            lcount = np.diff(F.V.colptr.cpu().numpy())
+        F.close()
+    barrier()
+
+    # ---- timed region (device-resident inputs)
+    launches0 = diaf.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kern_ms, numeric_ms, total_ms, bucket_cols = [], [], [], None
+    with ClockSampler(local) as clk:
+        barrier()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            F = step(A, PW, bud)
+            ev[i][1].record(stream)
+            t = F.timings()
+            kern_ms.append(t["bucket_ms"])
+            numeric_ms.append(t["numeric_ms"])
+            total_ms.append(t["total_ms"])
+            if lcount is None:
+                lcount = np.diff(F.V.colptr.cpu().numpy())
+            bucket_cols = t["bucket_cols"]
+            F.close()
+        barrier()
+    launches = diaf.launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = float(np.mean(step_ms))
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * w.n / (ms / 1e3)
+
+    # ---- e2e through the public API from pinned host buffers
+    def pin(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+
+    hA = [pin(w.A.colptr), pin(w.A.rowidx), pin(w.A.vals)]
+    hP = [pin(w.PW.colptr), pin(w.PW.rowidx)]
+    hB = pin(w.budget)
+    h2d = sum(t.numel() * t.element_size() for t in hA + hP + [hB])
+    e2e_ms = []
+    d2h = 0
+    for i in range(max(1, args.steps // 2) + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True); s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        Ad = diaf.DeviceCSC(w.n, *(t.to(dev, non_blocking=True) for t in hA))
+        PWd = diaf.DeviceCSC(w.n, *(t.to(dev, non_blocking=True) for t in hP))
+        budd = hB.to(dev, non_blocking=True)
+        F = step(Ad, PWd, budd)
+        outs = [F.W.vals, F.V.colptr, F.V.rowidx, F.V.vals, F.res]
+        host = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs]
+        for h, o in zip(host, outs):
+            h.copy_(o, non_blocking=True)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        d2h = sum(h.numel() * h.element_size() for h in host)
+        F.close()
+        if i > 0:
+            e2e_ms.append(s0.elapsed_time(s1))
+    e2e_val = world * w.n / (float(np.mean(e2e_ms)) / 1e3)
+
+    # ---- roofline of the dominant kernel (the numeric column kernel)
+    peaks, peak_src = _peaks()
+    m, k = tile_sizes(w)
+    flops = algorithmic_flops(m, k, lcount, args.alg, cplx)
+    kern = float(np.mean([sum(x) for x in kern_ms]))
+    fp64_peak = FP64_NOMINAL_TFLOPS * 1e12
+    achieved = flops / (kern / 1e3)
+    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / fp64_peak, "traffic": None, "kernel": "column_warp_kernel (numeric pass)",
+            "kernel_ms": kern, "algorithmic_flops": flops,
+            "peak_source": "FP64 nominal 1.25 TFLOP/s (no measured FP64 figure in the peaks file)"}
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        # BiCGSTAB with the preconditioner (not part of the setup metric)
+        F = diaf.factor(A, PW, w.vrule, bud, alg=args.alg, prec=args.prec)
+        S = diaf.Solver(A)
+        b = torch.from_numpy(w.b).to(dev)
+        S.bicgstab(b, F, tol=1e-8, maxit=1000)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, info = S.bicgstab(b, F, tol=1e-8, maxit=1000)
+        torch.cuda.synchronize()
+        solve_ms = 1e3 * (time.perf_counter() - t0)
+        x0, info0 = S.bicgstab(b, None, tol=1e-8, maxit=1000)
+        extras["bicgstab"] = {"its": info.iterations, "converged": bool(info.converged), "relres": info.relres,
+                              "solve_ms": solve_ms, "its_unpreconditioned": info0.iterations,
+                              "err_inf": float((x - 1).abs().max().item())}
+        F.close()
+        # the other algorithm, same workload (factor only, median of 3)
+        other = "Q" if args.alg == "S" else "S"
+        tt = []
+        for _ in range(3):
+            flush.zero_()
+            torch.cuda.synchronize()
+            Fo = diaf.factor(A, PW, w.vrule, bud, alg=other, prec=args.prec)
+            tt.append(Fo.timings()["total_ms"])
+            Fo.close()
+        extras[f"alg_{other}_factor_columns_per_s"] = w.n / (statistics.median(tt) / 1e3)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "c128" if cplx else "f64", "data": "synthetic",
+                "config": {"workload": w.name, "n": w.n, "alg": args.alg, "prec": args.prec,
+                           "nnz_A": w.A.nnz, "nnz_W": w.PW.nnz, "columns_per_step": w.n,
+                           "l2": "flushed (256 MiB write) before every timed step",
+                           "step": "diaf_factor + one diaf_apply", "bucket_cols": bucket_cols,
+                           "parallelism": f"replicas x{world}"},
+                "setup_ms": float(np.mean(total_ms)), "numeric_pass_ms": float(np.mean(numeric_ms)),
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+                "gpu_launches": int(launches), "roofline": roof, "peaks_source": peak_src}
+        line.update(extras)
+        line["clocks"] = clk.summary()
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(w, args.alg)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * diaf.h -- C ABI of the GB300 library for the columnwise construction of
+ * sparse W, V with AW ~ V ("direct approximate factoring of the inverse",
+ * Byckling & Huhtanen), and for applying the resulting right preconditioner
+ * A^-1 ~ W V^-1 (eq. afac, Sec. 2).
+ *
+ * Conventions for every entry point:
+ *  - Sparse matrices and patterns are CSC, 0-based, int32 indices, the row
+ *    indices of each column strictly increasing.  n and every nnz < 2^31.
+ *  - Pointers named d_* (and every pointer inside diaf_csc / diaf_pattern /
+ *    diaf_vspec) are DEVICE pointers on the current CUDA device; h_* are host
+ *    pointers.  Inputs stay owned by the caller and must remain valid until
+ *    the work enqueued on `stream` has finished.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *    Calls enqueue their work on it in order.  Calls that must size their
+ *    outputs from the data (diaf_factor) synchronise `stream` once, as noted.
+ *  - Complex values are interleaved (re, im) doubles (DIAF_C128).
+ *  - Every function returns diaf_status; nothing throws across the ABI.
+ *    After a non-OK status, diaf_last_error() gives a one-line reason
+ *    (thread-local, valid until the next call on the same thread).
+ *  - A missing or non-sm_103 device gives DIAF_ECUDA; there is no CPU path.
+ */
+#ifndef DIAF_H
+#define DIAF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DIAF_OK = 0,
+  DIAF_EINVAL = 1,       /* bad argument: null pointer, size, unsorted / out-of-range index */
+  DIAF_ENOMEM = 2,       /* device allocation failed */
+  DIAF_ECUDA = 3,        /* CUDA runtime error (no device, launch failure, ...) */
+  DIAF_ENUMERIC = 4,     /* non-finite values produced */
+  DIAF_ETIMEOUT = 5,     /* a bounded device-side wait ran out */
+  DIAF_EUNSUPPORTED = 6  /* a column's tile exceeds every compiled kernel's capacity */
+} diaf_status;
+
+/* Value type of A (and therefore of W and V). */
+enum { DIAF_F64 = 0, DIAF_C128 = 1 };
+
+/* The two basic algorithms.  DIAF_ALG_Q: columns of V of unit norm, v_j from
+ * eq. nocond, w_j from the least-squares problem eq. condwj (Sec. 2.1, the
+ * "first basic algorithm", DIAF-Q).  DIAF_ALG_S: columns of W of unit norm,
+ * w_j the right singular vector of the smallest singular value of A_j with
+ * the rows I_j removed, v_j = P_V A w_j (Sec. 2.2, the "second basic
+ * algorithm", DIAF-S). */
+enum { DIAF_ALG_Q = 1, DIAF_ALG_S = 2 };
+
+/* Arithmetic of the numeric phase.  DIAF_PREC_FP64: everything in FP64
+ * (complex128 for DIAF_C128).  DIAF_PREC_MIXED32: gather, QR, Jacobi in FP32
+ * (complex64), then one FP64 refinement step of (w_j, v_j) against the FP64
+ * tile and an FP64 residual; leverage keys near a selection threshold are
+ * recomputed in FP64 so that I_j is the FP64 choice. */
+enum { DIAF_PREC_FP64 = 0, DIAF_PREC_MIXED32 = 1 };
+
+/* How I_j (the pattern of column j of V) is obtained.  FIXED: given pattern.
+ * UPPER / LOWER / ALL: the optimal-V rule of Sec. 3.1 -- the diagonal j plus
+ * the l_j - 1 admissible rows of the tile with the largest leverage
+ * h_i = ||Q_j(i,:)||^2 (the columns of Q_j^* of largest norm).  Admissible
+ * rows: i < j (UPPER, V upper triangular as in the Gauss-Seidel structure of
+ * Sec. 4.2), i > j (LOWER), any i != j (ALL); always rows of the tile. */
+enum { DIAF_RULE_FIXED = 0, DIAF_RULE_UPPER = 1, DIAF_RULE_LOWER = 2, DIAF_RULE_ALL = 3 };
+
+/* Per-column flag bits (col_flags). */
+enum {
+  DIAF_FLAG_RANK_DEFICIENT = 1,  /* S: sigma_min <= 1e-14 sigma_max or fewer tile rows than k_j outside I_j;
+                                    Q: a pivot of R below 1e-14 max|R_ii| (its w entry set to 0) */
+  DIAF_FLAG_DEGENERATE = 2,      /* the optimal vector is not unique to 1e-6 relative gap
+                                    (S: smallest two singular values, Q: largest two) */
+  DIAF_FLAG_VJJ_ZERO = 4,        /* |v_jj| <= 64 eps ||v_j|| (V singular at j to rounding); phase taken from w */
+  DIAF_FLAG_JACOBI_NOCONV = 8,   /* the Jacobi SVD hit its 30-sweep limit */
+  DIAF_FLAG_NONFINITE = 16,      /* NaN or Inf in w_j, v_j or res_j */
+  DIAF_FLAG_EMPTY = 32,          /* k_j = 0 (empty W column) */
+  DIAF_FLAG_REFINED_KEYS = 64    /* mixed precision: leverage keys were recomputed in FP64 */
+};
+
+typedef struct {
+  int32_t n;
+  int64_t nnz;
+  const int32_t* colptr; /* device, n+1 */
+  const int32_t* rowidx; /* device, nnz */
+  const void* vals;      /* device, nnz doubles (F64) or 2*nnz doubles (C128) */
+  int32_t dtype;         /* DIAF_F64 or DIAF_C128 */
+} diaf_csc;
+
+typedef struct {
+  int32_t n;
+  int64_t nnz;
+  const int32_t* colptr; /* device, n+1 */
+  const int32_t* rowidx; /* device, nnz */
+} diaf_pattern;
+
+typedef struct {
+  int32_t rule;               /* DIAF_RULE_* */
+  const diaf_pattern* fixed;  /* rule == FIXED: the V pattern; else ignored */
+  const int32_t* budget;      /* device int32[n]: l_j including the diagonal (values < 1 act as 1),
+                                 capped by 1 + the number of admissible rows; NULL = all admissible */
+  double tie_tol;             /* leverage keys within tie_tol of the current largest count as tied and the
+                                 lower row is taken; <= 0 selects the default 1e-9 */
+} diaf_vspec;
+
+typedef struct diaf_factors diaf_factors; /* opaque, library-owned */
+
+/*
+ * diaf_factor -- the whole setup: for every column j, gather the tile
+ * T = A(R_j, J_j) of the rows R_j touched by the columns J_j of the W
+ * pattern (A_j of eq. spaqr on its nonzero rows), QR it (eq. spaqr), choose
+ * I_j (Sec. 3.1 rule or fixed), solve DIAF-S (Sec. 2.2) or DIAF-Q (Sec. 2.1)
+ * for (w_j, v_j), fix the phase so that v_jj is real and >= 0 (allowed by the
+ * scaling-invariance theorem of Sec. 2.1), and scatter into CSC W (pattern
+ * PW) and V (pattern I_j).  res_j = ||A w_j - v_j||_2 per column.
+ *   A       : the n x n matrix (values F64 or C128).
+ *   PW      : W pattern (J_j = column j), PW->n == A->n.
+ *   V       : V pattern specification.
+ *   alg     : DIAF_ALG_Q or DIAF_ALG_S.   prec: DIAF_PREC_*.
+ *   out     : receives a new handle; free with diaf_free.
+ * Synchronises `stream` once (after the symbolic pass, to size V).  The
+ * numeric work is enqueued on `stream`; the outputs are ready when it has
+ * run.  Errors: EINVAL (arguments, unsorted / out-of-range indices),
+ * ENOMEM, ECUDA, EUNSUPPORTED (a column needs more than 4096 gathered
+ * entries or a tile beyond 1024 x 64).
+ */
+diaf_status diaf_factor(const diaf_csc* A, const diaf_pattern* PW, const diaf_vspec* V, int32_t alg,
+                        int32_t prec, void* stream, diaf_factors** out);
+
+typedef struct {
+  int32_t n;
+  int32_t dtype;
+  int32_t alg;
+  int32_t prec;
+  int64_t nnz_w;       /* = nnz(PW) */
+  int64_t nnz_v;       /* = sum_j l_j */
+  int32_t max_k, max_m, max_l;
+  int32_t n_buckets;   /* number of size buckets launched */
+  int32_t bucket_cols[8];
+} diaf_factor_info;
+
+/* Sizes and bucket statistics of a factorisation (host copy; no sync). */
+diaf_status diaf_factor_info_get(const diaf_factors* F, diaf_factor_info* info);
+
+/* Timings of a factorisation from CUDA events recorded on its stream (waits
+ * for them): ms[0] the whole diaf_factor call (first to last enqueued work,
+ * host synchronisations included), ms[1] the numeric pass, ms[2 + b] the
+ * numeric kernel of size bucket b (0 when the bucket was empty).  nms is the
+ * capacity of ms and must be >= 2 + n_buckets. */
+diaf_status diaf_factor_timings(const diaf_factors* F, float* ms, int32_t nms);
+
+/* Number of CUDA kernels this library has launched in this process. */
+long long diaf_launch_count(void);
+
+/* Borrowed device views of the outputs (valid until diaf_free):
+ * W: colptr/rowidx = copies of PW, vals nnz_w scalars;  V: CSC with column j
+ * on I_j (sorted), vals nnz_v scalars;  col_res: double[n];  col_flags:
+ * uint32[n] (DIAF_FLAG_* bits).  Any output pointer may be NULL. */
+diaf_status diaf_get_factors(const diaf_factors* F, diaf_csc* W, diaf_csc* V, const double** col_res,
+                             const uint32_t** col_flags);
+
+/* y = W V^-1 x (eq. afac: A^-1 ~ W V^-1, right preconditioning, Sec. 2.3).
+ * x, y: device vectors of n scalars (dtype of F), must not overlap.  V must
+ * be triangular (rules UPPER / LOWER, or a fixed triangular pattern) with a
+ * nonzero diagonal.  The first call on F builds row-oriented copies of W and
+ * V (allocates; make it before any stream capture).  The triangular solve
+ * runs in one kernel whose waits are bounded: if a wait runs out the call's
+ * next diaf_sync reports DIAF_ETIMEOUT.  Errors: EINVAL (V not triangular or
+ * zero diagonal -- found by the first call), ENOMEM, ECUDA. */
+diaf_status diaf_apply(diaf_factors* F, const void* x, void* y, void* stream);
+
+/* Waits for `stream` and reports device-side errors recorded by earlier
+ * calls on F (bounded-wait timeouts, capacity overflows) as a status. */
+diaf_status diaf_sync(diaf_factors* F, void* stream);
+
+/* Frees F and every device buffer it owns (stream-ordered on the stream F was
+ * created on; that stream must still exist).  NULL is ignored. */
+void diaf_free(diaf_factors* F);
+
+typedef struct diaf_solver diaf_solver; /* opaque: A in row-oriented form for Krylov solves */
+
+/* Prepares A for the Krylov solvers (row-oriented copy; allocates). */
+diaf_status diaf_solver_create(const diaf_csc* A, void* stream, diaf_solver** out);
+void diaf_solver_free(diaf_solver* S);
+
+typedef struct {
+  int32_t iterations;   /* iterations performed */
+  int32_t converged;    /* 1 when ||r|| <= tol ||r0|| */
+  int32_t breakdown;    /* 1 on a zero denominator (the paper's double dagger) */
+  double relres;        /* final ||r|| / ||r0|| */
+} diaf_solve_info;
+
+/* Right-preconditioned BiCGSTAB on A x = b (Sec. 5: x0 = 0, stop when the
+ * residual is reduced by tol, at most maxit iterations).  F == NULL solves
+ * without preconditioner.  b, x: device vectors of n scalars.  One
+ * device-to-host read per iteration (the convergence test). */
+diaf_status diaf_bicgstab(diaf_solver* S, diaf_factors* F, const void* b, void* x, double tol, int32_t maxit,
+                          void* stream, diaf_solve_info* info);
+
+const char* diaf_status_string(diaf_status s);
+const char* diaf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DIAF_H */

@@ -31,7 +31,9 @@
  *       vector of M_j (eq. nocond), via one-sided Jacobi; w_j solves the
  *       least-squares problem eq. condwj, R w = Q^* v = M_j v.
  *   6. Phase: scale (w_j, v_j) by a unit scalar so that v_jj is real >= 0
- *      (allowed by the scaling-invariance theorem of Sec. 2.1).
+ *      (allowed by the scaling-invariance theorem of Sec. 2.1).  When v_jj is
+ *      zero to rounding (|v_jj| <= 64 eps ||v_j||) the flag VJJ_ZERO is set
+ *      and the largest-modulus entry of w_j is made real instead.
  *   7. res_j = ||A w_j - v_j||_2, computed from its definition.
  *
  * Jacobi SVD: cyclic one-sided (Hestenes) Jacobi, rotation when
@@ -417,7 +419,10 @@ static void solve_column(const problem *P, int j, colout *out, double *h_dbg, in
     if (k > 0 || P->alg == ALG_Q) {
         zd ph = 1.0;
         double vjj = jpos >= 0 ? cabs(v[jpos]) : 0.0;
-        if (jpos >= 0 && vjj > 1e-300) {
+        double vn2 = 0.0;
+        for (int t = 0; t < l; ++t) vn2 += abs2(v[t]);
+        /* v_jj counts as zero below the rounding level of the column */
+        if (jpos >= 0 && vjj > 64.0 * DBL_EPSILON * sqrt(vn2)) {
             ph = conj(v[jpos]) / vjj;
         } else {
             flags |= F_VJJ_ZERO;

@@ -1,0 +1,408 @@
+// C ABI of the DIAF library: argument checks, the symbolic pass, bucketed
+// numeric launches, output ownership, and the preconditioner apply.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "launch.cuh"
+#include "plan.cuh"
+#include "sparse.cuh"
+
+static std::atomic<long long> g_launches{0};
+void diaf_note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+namespace {
+
+thread_local std::string g_last_error;
+
+diaf_status fail(diaf_status st, const std::string& why) {
+  g_last_error = why;
+  return st;
+}
+
+diaf_status cuda_fail(cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? DIAF_ENOMEM : DIAF_ECUDA;
+}
+
+#define DIAF_CU(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+// Stream-ordered device allocations released together.
+struct Pool {
+  cudaStream_t s;
+  std::vector<void*> ptrs;
+  explicit Pool(cudaStream_t st) : s(st) {}
+  template <class T>
+  cudaError_t get(T** p, size_t count) {
+    size_t bytes = sizeof(T) * (count > 0 ? count : 1);
+    void* q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, bytes, s);
+    if (e != cudaSuccess) return e;
+    ptrs.push_back(q);
+    *p = static_cast<T*>(q);
+    return cudaSuccess;
+  }
+  void release() {
+    for (void* p : ptrs) cudaFreeAsync(p, s);
+    ptrs.clear();
+  }
+  ~Pool() { release(); }
+};
+
+diaf_status check_device() {
+  int dev = 0, n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) return fail(DIAF_ECUDA, "no CUDA device");
+  cudaGetDevice(&dev);
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  if (major != 10 || minor != 3) return fail(DIAF_ECUDA, "this library is built for sm_103 (GB300) only");
+  return DIAF_OK;
+}
+
+}  // namespace
+
+struct diaf_factors {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int n = 0;
+  int dtype = DIAF_F64, alg = DIAF_ALG_S, prec = DIAF_PREC_FP64, rule = DIAF_RULE_UPPER;
+  int64_t nnz_w = 0, nnz_v = 0;
+  int32_t *Wcp = nullptr, *Wri = nullptr, *Vcp = nullptr, *Vri = nullptr;
+  void *Wv = nullptr, *Vv = nullptr;
+  double* res = nullptr;
+  uint32_t* flags = nullptr;
+  uint32_t* status = nullptr;
+  diaf_factor_info info{};
+  std::vector<void*> owned;
+  // CUDA events: [0] start, [1] numeric start, [2] end, [3 + 2b], [4 + 2b] around bucket b
+  static constexpr int kEvents = 3 + 2 * kNumBuckets;
+  cudaEvent_t ev[kEvents] = {};
+  bool bucket_ran[kNumBuckets] = {};
+  // apply
+  bool apply_ready = false;
+  bool v_upper = true;
+  Csr Vr, Wr;
+  uint32_t* ready = nullptr;
+  int32_t* counter = nullptr;
+  uint32_t gen = 0;
+  void* tbuf = nullptr;
+
+  template <class T>
+  cudaError_t alloc(T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, sizeof(T) * (count > 0 ? count : 1), stream);
+    if (e != cudaSuccess) return e;
+    owned.push_back(q);
+    *p = static_cast<T*>(q);
+    return cudaSuccess;
+  }
+};
+
+extern "C" {
+
+const char* diaf_status_string(diaf_status s) {
+  switch (s) {
+    case DIAF_OK: return "ok";
+    case DIAF_EINVAL: return "invalid argument";
+    case DIAF_ENOMEM: return "out of device memory";
+    case DIAF_ECUDA: return "CUDA error";
+    case DIAF_ENUMERIC: return "non-finite values";
+    case DIAF_ETIMEOUT: return "device wait timed out";
+    case DIAF_EUNSUPPORTED: return "tile beyond the compiled capacity";
+  }
+  return "unknown status";
+}
+
+const char* diaf_last_error(void) { return g_last_error.c_str(); }
+
+void diaf_free(diaf_factors* F) {
+  if (!F) return;
+  for (void* p : F->owned) cudaFreeAsync(p, F->stream);
+  for (cudaEvent_t e : F->ev)
+    if (e) cudaEventDestroy(e);
+  delete F;
+}
+
+long long diaf_launch_count(void) { return g_launches.load(); }
+
+diaf_status diaf_factor_timings(const diaf_factors* F, float* ms, int32_t nms) {
+  if (!F || !ms || nms < 2 + kNumBuckets) return fail(DIAF_EINVAL, "need a handle and room for 2 + n_buckets values");
+  for (int i = 0; i < nms; ++i) ms[i] = 0.0f;
+  if (!F->ev[0]) return DIAF_OK;
+  DIAF_CU(cudaEventSynchronize(F->ev[2]));
+  DIAF_CU(cudaEventElapsedTime(&ms[0], F->ev[0], F->ev[2]));
+  DIAF_CU(cudaEventElapsedTime(&ms[1], F->ev[1], F->ev[2]));
+  for (int b = 0; b < kNumBuckets; ++b)
+    if (F->bucket_ran[b]) DIAF_CU(cudaEventElapsedTime(&ms[2 + b], F->ev[3 + 2 * b], F->ev[4 + 2 * b]));
+  return DIAF_OK;
+}
+
+diaf_status diaf_factor(const diaf_csc* A, const diaf_pattern* PW, const diaf_vspec* V, int32_t alg, int32_t prec,
+                        void* stream, diaf_factors** out) {
+  g_last_error.clear();
+  if (!out) return fail(DIAF_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!A || !PW || !V) return fail(DIAF_EINVAL, "A, PW and V must be non-NULL");
+  if (alg != DIAF_ALG_Q && alg != DIAF_ALG_S) return fail(DIAF_EINVAL, "alg must be DIAF_ALG_Q or DIAF_ALG_S");
+  if (prec != DIAF_PREC_FP64 && prec != DIAF_PREC_MIXED32) return fail(DIAF_EINVAL, "unknown precision");
+  if (A->dtype != DIAF_F64 && A->dtype != DIAF_C128) return fail(DIAF_EINVAL, "unknown dtype");
+  if (A->n < 0 || PW->n != A->n) return fail(DIAF_EINVAL, "PW->n must equal A->n >= 0");
+  if (A->nnz < 0 || PW->nnz < 0 || A->nnz >= (1ll << 31) || PW->nnz >= (1ll << 31))
+    return fail(DIAF_EINVAL, "nnz out of range");
+  if (V->rule < DIAF_RULE_FIXED || V->rule > DIAF_RULE_ALL) return fail(DIAF_EINVAL, "unknown V rule");
+  if (V->rule == DIAF_RULE_FIXED && (!V->fixed || V->fixed->n != A->n || !V->fixed->colptr))
+    return fail(DIAF_EINVAL, "fixed V pattern missing or of the wrong size");
+  if (A->n > 0 && (!A->colptr || !PW->colptr || (A->nnz > 0 && (!A->rowidx || !A->vals)) ||
+                   (PW->nnz > 0 && !PW->rowidx)))
+    return fail(DIAF_EINVAL, "NULL array in A or PW");
+  if (prec == DIAF_PREC_MIXED32) return fail(DIAF_EUNSUPPORTED, "mixed precision not built yet");
+  diaf_status ds = check_device();
+  if (ds != DIAF_OK) return ds;
+
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int n = A->n;
+  const bool cplx = A->dtype == DIAF_C128;
+  const size_t esz = cplx ? 16 : 8;
+
+  auto F = new diaf_factors();
+  F->stream = s;
+  cudaGetDevice(&F->device);
+  F->n = n;
+  F->dtype = A->dtype;
+  F->alg = alg;
+  F->prec = prec;
+  F->rule = V->rule;
+  F->nnz_w = PW->nnz;
+  struct Guard {
+    diaf_factors*& f;
+    bool keep = false;
+    ~Guard() { if (!keep) diaf_free(f); }
+  } guard{F};
+
+  for (cudaEvent_t& e : F->ev) DIAF_CU(cudaEventCreate(&e));
+  DIAF_CU(cudaEventRecord(F->ev[0], s));
+  Pool pool(s);
+  // ---- small device words
+  uint32_t* status;
+  int32_t *stats, *bucket_count, *big_count, *work;
+  DIAF_CU(F->alloc(&status, 1));
+  F->status = status;
+  DIAF_CU(pool.get(&stats, 4));
+  DIAF_CU(pool.get(&bucket_count, kNumBuckets));
+  DIAF_CU(pool.get(&big_count, 1));
+  DIAF_CU(pool.get(&work, kNumBuckets));
+  DIAF_CU(cudaMemsetAsync(status, 0, sizeof(uint32_t), s));
+  DIAF_CU(cudaMemsetAsync(stats, 0, sizeof(int32_t) * 4, s));
+  DIAF_CU(cudaMemsetAsync(bucket_count, 0, sizeof(int32_t) * kNumBuckets, s));
+  DIAF_CU(cudaMemsetAsync(big_count, 0, sizeof(int32_t), s));
+  DIAF_CU(cudaMemsetAsync(work, 0, sizeof(int32_t) * kNumBuckets, s));
+
+  // ---- input checks on the device (sorted, in range)
+  DIAF_CU(check_csc(n, A->colptr, A->rowidx, A->nnz, status, s));
+  DIAF_CU(check_csc(n, PW->colptr, PW->rowidx, PW->nnz, status, s));
+  if (V->rule == DIAF_RULE_FIXED) DIAF_CU(check_csc(n, V->fixed->colptr, V->fixed->rowidx, V->fixed->nnz, status, s));
+
+  // ---- symbolic pass 1: k_j, E_j
+  PlanArgs pa{};
+  pa.n = n;
+  pa.Acp = A->colptr; pa.Ari = A->rowidx;
+  pa.Wcp = PW->colptr; pa.Wri = PW->rowidx;
+  pa.rule = V->rule;
+  pa.Vfcp = V->rule == DIAF_RULE_FIXED ? V->fixed->colptr : nullptr;
+  pa.Vfri = V->rule == DIAF_RULE_FIXED ? V->fixed->rowidx : nullptr;
+  pa.budget = V->budget;
+  int64_t* bs64;
+  int32_t* bs32;
+  DIAF_CU(pool.get(&pa.k, n));
+  DIAF_CU(pool.get(&pa.E, n));
+  DIAF_CU(pool.get(&pa.Eoff, n + 1));
+  DIAF_CU(pool.get(&pa.m, n));
+  DIAF_CU(pool.get(&pa.l, n));
+  DIAF_CU(pool.get(&pa.jin, n));
+  DIAF_CU(pool.get(&pa.bucket_list, (size_t)kNumBuckets * n));
+  DIAF_CU(pool.get(&pa.big_list, n));
+  DIAF_CU(pool.get(&bs64, scan_blocksums_size(n)));
+  DIAF_CU(pool.get(&bs32, scan_blocksums_size(n)));
+  pa.bucket_count = bucket_count;
+  pa.big_count = big_count;
+  pa.stats = stats;
+  pa.status = status;
+
+  uint32_t h_status = 0;
+  int64_t h_Etot = 0;
+  if (n > 0) {
+    // the planner reads J_j only after the input check passed: sync first
+    DIAF_CU(cudaMemcpyAsync(&h_status, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    DIAF_CU(cudaStreamSynchronize(s));
+    if (h_status & DEV_ST_BAD_INPUT) return fail(DIAF_EINVAL, "unsorted or out-of-range indices in A, PW or V");
+    DIAF_CU(plan_count(pa, s));
+    DIAF_CU(exclusive_scan_i32_to_i64(pa.E, pa.Eoff, n, bs64, s));
+    DIAF_CU(cudaMemcpyAsync(&h_Etot, pa.Eoff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    DIAF_CU(cudaStreamSynchronize(s));
+  }
+  DIAF_CU(pool.get(&pa.rows, (size_t)h_Etot));
+  DIAF_CU(F->alloc(&F->Vcp, n + 1));
+  if (n > 0) {
+    DIAF_CU(plan_rows(pa, s));
+    DIAF_CU(exclusive_scan_i32(pa.l, F->Vcp, n, bs32, s));
+  } else {
+    DIAF_CU(cudaMemsetAsync(F->Vcp, 0, sizeof(int32_t), s));
+  }
+  int32_t h_nnzv = 0, h_bc[kNumBuckets] = {0}, h_stats[4] = {0};
+  if (n > 0) {
+    DIAF_CU(cudaMemcpyAsync(&h_nnzv, F->Vcp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    DIAF_CU(cudaMemcpyAsync(h_bc, bucket_count, sizeof(h_bc), cudaMemcpyDeviceToHost, s));
+    DIAF_CU(cudaMemcpyAsync(h_stats, stats, sizeof(h_stats), cudaMemcpyDeviceToHost, s));
+    DIAF_CU(cudaMemcpyAsync(&h_status, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    DIAF_CU(cudaStreamSynchronize(s));
+  }
+  if (h_status & DEV_ST_CAPACITY)
+    return fail(DIAF_EUNSUPPORTED, "a column needs more than 4096 gathered entries or a tile beyond 1024 x 64");
+  F->nnz_v = h_nnzv;
+  F->info.n = n;
+  F->info.dtype = A->dtype;
+  F->info.alg = alg;
+  F->info.prec = prec;
+  F->info.nnz_w = PW->nnz;
+  F->info.nnz_v = h_nnzv;
+  F->info.max_k = h_stats[0];
+  F->info.max_m = h_stats[1];
+  F->info.max_l = h_stats[2];
+  F->info.n_buckets = kNumBuckets;
+  for (int b = 0; b < kNumBuckets; ++b) F->info.bucket_cols[b] = h_bc[b];
+
+  // ---- outputs
+  DIAF_CU(F->alloc(&F->Wcp, n + 1));
+  DIAF_CU(F->alloc(&F->Wri, PW->nnz));
+  DIAF_CU(F->alloc((char**)&F->Wv, esz * PW->nnz));
+  DIAF_CU(F->alloc(&F->Vri, h_nnzv));
+  DIAF_CU(F->alloc((char**)&F->Vv, esz * h_nnzv));
+  DIAF_CU(F->alloc(&F->res, n));
+  DIAF_CU(F->alloc(&F->flags, n));
+  DIAF_CU(cudaMemcpyAsync(F->Wcp, PW->colptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
+  if (PW->nnz > 0)
+    DIAF_CU(cudaMemcpyAsync(F->Wri, PW->rowidx, sizeof(int32_t) * PW->nnz, cudaMemcpyDeviceToDevice, s));
+
+  // ---- numeric pass, one launch per bucket
+  DIAF_CU(cudaEventRecord(F->ev[1], s));
+  ColArgs ca{};
+  ca.n = n;
+  ca.Acp = A->colptr; ca.Ari = A->rowidx; ca.Av = A->vals;
+  ca.Wcp = PW->colptr; ca.Wri = PW->rowidx;
+  ca.Eoff = pa.Eoff; ca.rows = pa.rows; ca.m = pa.m; ca.l = pa.l; ca.jin = pa.jin;
+  ca.rule = V->rule; ca.Vfcp = pa.Vfcp; ca.Vfri = pa.Vfri;
+  ca.Vcp = F->Vcp;
+  ca.tie_tol = V->tie_tol > 0 ? V->tie_tol : 1e-9;
+  ca.Wv = F->Wv; ca.Vri = F->Vri; ca.Vv = F->Vv;
+  ca.res = F->res; ca.flags = F->flags; ca.status = status;
+  for (int b = 0; b < kNumBuckets; ++b) {
+    if (h_bc[b] == 0) continue;
+    ca.list = pa.bucket_list + (size_t)b * n;
+    ca.list_count = bucket_count + b;
+    ca.work_counter = work + b;
+    DIAF_CU(cudaEventRecord(F->ev[3 + 2 * b], s));
+    cudaError_t e = cplx ? launch_columns_c128(b, alg, ca, h_bc[b], s) : launch_columns_f64(b, alg, ca, h_bc[b], s);
+    if (e == cudaErrorNotSupported)
+      return fail(DIAF_EUNSUPPORTED, "bucket " + std::to_string(b) + " has no kernel for this configuration yet");
+    if (e != cudaSuccess) return cuda_fail(e, "column kernel launch");
+    DIAF_CU(cudaEventRecord(F->ev[4 + 2 * b], s));
+    F->bucket_ran[b] = true;
+  }
+  DIAF_CU(cudaEventRecord(F->ev[2], s));
+  pool.release();
+  guard.keep = true;
+  *out = F;
+  return DIAF_OK;
+}
+
+diaf_status diaf_factor_info_get(const diaf_factors* F, diaf_factor_info* info) {
+  if (!F || !info) return fail(DIAF_EINVAL, "NULL argument");
+  *info = F->info;
+  return DIAF_OK;
+}
+
+diaf_status diaf_get_factors(const diaf_factors* F, diaf_csc* W, diaf_csc* V, const double** col_res,
+                             const uint32_t** col_flags) {
+  if (!F) return fail(DIAF_EINVAL, "NULL handle");
+  if (W) *W = diaf_csc{F->n, F->nnz_w, F->Wcp, F->Wri, F->Wv, F->dtype};
+  if (V) *V = diaf_csc{F->n, F->nnz_v, F->Vcp, F->Vri, F->Vv, F->dtype};
+  if (col_res) *col_res = F->res;
+  if (col_flags) *col_flags = F->flags;
+  return DIAF_OK;
+}
+
+diaf_status diaf_sync(diaf_factors* F, void* stream) {
+  if (!F) return fail(DIAF_EINVAL, "NULL handle");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint32_t h = 0;
+  DIAF_CU(cudaMemcpyAsync(&h, F->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  DIAF_CU(cudaStreamSynchronize(s));
+  if (h & DEV_ST_TIMEOUT) return fail(DIAF_ETIMEOUT, "a bounded wait in the triangular solve ran out");
+  if (h & DEV_ST_CAPACITY) return fail(DIAF_EUNSUPPORTED, "capacity exceeded on the device");
+  return DIAF_OK;
+}
+
+static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
+  const int n = F->n;
+  const bool cplx = F->dtype == DIAF_C128;
+  const size_t esz = cplx ? 16 : 8;
+  int32_t* work;
+  DIAF_CU(F->alloc(&work, n + scan_blocksums_size(n)));
+  F->Vr.n = n; F->Vr.nnz = F->nnz_v;
+  DIAF_CU(F->alloc(&F->Vr.rowptr, n + 1));
+  DIAF_CU(F->alloc(&F->Vr.colidx, F->nnz_v));
+  DIAF_CU(F->alloc((char**)&F->Vr.vals, esz * F->nnz_v));
+  DIAF_CU(csc_to_csr(n, F->nnz_v, F->Vcp, F->Vri, F->Vv, cplx, F->Vr.rowptr, F->Vr.colidx, F->Vr.vals, work, s));
+  F->Wr.n = n; F->Wr.nnz = F->nnz_w;
+  DIAF_CU(F->alloc(&F->Wr.rowptr, n + 1));
+  DIAF_CU(F->alloc(&F->Wr.colidx, F->nnz_w));
+  DIAF_CU(F->alloc((char**)&F->Wr.vals, esz * F->nnz_w));
+  DIAF_CU(csc_to_csr(n, F->nnz_w, F->Wcp, F->Wri, F->Wv, cplx, F->Wr.rowptr, F->Wr.colidx, F->Wr.vals, work, s));
+  uint32_t* tri;
+  DIAF_CU(F->alloc(&tri, 1));
+  DIAF_CU(cudaMemsetAsync(tri, 0, sizeof(uint32_t), s));
+  DIAF_CU(csr_triangle_check(F->Vr, cplx, tri, s));
+  uint32_t h = 0;
+  DIAF_CU(cudaMemcpyAsync(&h, tri, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  DIAF_CU(cudaStreamSynchronize(s));
+  if ((h & 1u) && (h & 2u)) return fail(DIAF_EINVAL, "V is not triangular");
+  if (h & 4u) return fail(DIAF_EINVAL, "V has a zero or missing diagonal entry");
+  F->v_upper = !(h & 1u);
+  DIAF_CU(F->alloc(&F->ready, n));
+  DIAF_CU(cudaMemsetAsync(F->ready, 0, sizeof(uint32_t) * (n > 0 ? n : 1), s));
+  DIAF_CU(F->alloc(&F->counter, 1));
+  DIAF_CU(F->alloc((char**)&F->tbuf, esz * n));
+  F->gen = 0;
+  F->apply_ready = true;
+  return DIAF_OK;
+}
+
+diaf_status diaf_apply(diaf_factors* F, const void* x, void* y, void* stream) {
+  if (!F || (F->n > 0 && (!x || !y))) return fail(DIAF_EINVAL, "NULL argument");
+  if (x == y) return fail(DIAF_EINVAL, "x and y must not overlap");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!F->apply_ready) {
+    diaf_status st = prepare_apply(F, s);
+    if (st != DIAF_OK) return st;
+  }
+  if (F->n == 0) return DIAF_OK;
+  const bool cplx = F->dtype == DIAF_C128;
+  F->gen += 1;
+  if (F->gen == 0) {  // wrapped: clear the flags
+    DIAF_CU(cudaMemsetAsync(F->ready, 0, sizeof(uint32_t) * F->n, s));
+    F->gen = 1;
+  }
+  DIAF_CU(csr_trsv_syncfree(F->Vr, cplx, F->v_upper, x, F->tbuf, F->ready, F->counter, F->gen, F->status, s));
+  DIAF_CU(csr_spmv(F->Wr, cplx, F->tbuf, y, s));
+  return DIAF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,279 @@
+"""Python binding of libdiaf.so (include/diaf.h): argument marshalling only.
+
+Every computation runs in the CUDA library.  PyTorch provides device memory
+and streams; outputs owned by the library are exposed to PyTorch as
+zero-copy views (through __cuda_array_interface__) that keep their factor
+handle alive.  There is no CPU path: a missing library or GPU raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdiaf.so")
+
+DIAF_OK, DIAF_EINVAL, DIAF_ENOMEM, DIAF_ECUDA, DIAF_ENUMERIC, DIAF_ETIMEOUT, DIAF_EUNSUPPORTED = range(7)
+DIAF_F64, DIAF_C128 = 0, 1
+ALG = {"Q": 1, "S": 2}
+PREC = {"fp64": 0, "mixed32": 1}
+RULE_FIXED, RULE_UPPER, RULE_LOWER, RULE_ALL = 0, 1, 2, 3
+FLAG_RANK_DEFICIENT, FLAG_DEGENERATE, FLAG_VJJ_ZERO, FLAG_JACOBI_NOCONV = 1, 2, 4, 8
+FLAG_NONFINITE, FLAG_EMPTY, FLAG_REFINED_KEYS = 16, 32, 64
+
+
+class DiafError(RuntimeError):
+    def __init__(self, status: int, detail: str):
+        super().__init__(f"diaf status {status}: {detail}")
+        self.status = status
+
+
+class CSC_t(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64), ("colptr", ctypes.c_void_p),
+                ("rowidx", ctypes.c_void_p), ("vals", ctypes.c_void_p), ("dtype", ctypes.c_int32)]
+
+
+class Pattern_t(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64), ("colptr", ctypes.c_void_p),
+                ("rowidx", ctypes.c_void_p)]
+
+
+class VSpec_t(ctypes.Structure):
+    _fields_ = [("rule", ctypes.c_int32), ("fixed", ctypes.POINTER(Pattern_t)), ("budget", ctypes.c_void_p),
+                ("tie_tol", ctypes.c_double)]
+
+
+class Info_t(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("dtype", ctypes.c_int32), ("alg", ctypes.c_int32), ("prec", ctypes.c_int32),
+                ("nnz_w", ctypes.c_int64), ("nnz_v", ctypes.c_int64), ("max_k", ctypes.c_int32),
+                ("max_m", ctypes.c_int32), ("max_l", ctypes.c_int32), ("n_buckets", ctypes.c_int32),
+                ("bucket_cols", ctypes.c_int32 * 8)]
+
+
+class SolveInfo_t(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32), ("breakdown", ctypes.c_int32),
+                ("relres", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libdiaf.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() (there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp = ctypes.c_void_p
+        L.diaf_factor.argtypes = [ctypes.POINTER(CSC_t), ctypes.POINTER(Pattern_t), ctypes.POINTER(VSpec_t),
+                                  ctypes.c_int32, ctypes.c_int32, vp, ctypes.POINTER(vp)]
+        L.diaf_factor_info_get.argtypes = [vp, ctypes.POINTER(Info_t)]
+        L.diaf_get_factors.argtypes = [vp, ctypes.POINTER(CSC_t), ctypes.POINTER(CSC_t),
+                                       ctypes.POINTER(vp), ctypes.POINTER(vp)]
+        L.diaf_apply.argtypes = [vp, vp, vp, vp]
+        L.diaf_sync.argtypes = [vp, vp]
+        L.diaf_free.argtypes = [vp]
+        L.diaf_free.restype = None
+        L.diaf_solver_create.argtypes = [ctypes.POINTER(CSC_t), vp, ctypes.POINTER(vp)]
+        L.diaf_solver_free.argtypes = [vp]
+        L.diaf_solver_free.restype = None
+        L.diaf_bicgstab.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_int32, vp, ctypes.POINTER(SolveInfo_t)]
+        L.diaf_factor_timings.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]
+        L.diaf_launch_count.restype = ctypes.c_longlong
+        L.diaf_status_string.argtypes = [ctypes.c_int]
+        L.diaf_status_string.restype = ctypes.c_char_p
+        L.diaf_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(st: int) -> None:
+    if st != DIAF_OK:
+        L = lib()
+        raise DiafError(st, f"{L.diaf_status_string(st).decode()}: {L.diaf_last_error().decode()}")
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous()
+    return t.data_ptr()
+
+
+@dataclass
+class DeviceCSC:
+    """A matrix or pattern in CSC on the GPU (int32 indices; float64 or complex128 values)."""
+
+    n: int
+    colptr: torch.Tensor
+    rowidx: torch.Tensor
+    vals: torch.Tensor | None = None
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowidx.numel())
+
+    @property
+    def dtype_code(self) -> int:
+        return DIAF_C128 if (self.vals is not None and self.vals.is_complex()) else DIAF_F64
+
+    def csc_t(self) -> CSC_t:
+        return CSC_t(self.n, self.nnz, _ptr(self.colptr), _ptr(self.rowidx), _ptr(self.vals), self.dtype_code)
+
+    def pattern_t(self) -> Pattern_t:
+        return Pattern_t(self.n, self.nnz, _ptr(self.colptr), _ptr(self.rowidx))
+
+    @staticmethod
+    def from_host(M, device="cuda", pin=False) -> "DeviceCSC":
+        """M: workloads.CSC or workloads.Pattern (numpy arrays)."""
+        def to(a):
+            t = torch.from_numpy(a)
+            if pin:
+                t = t.pin_memory()
+            return t.to(device, non_blocking=pin)
+        vals = getattr(M, "vals", None)
+        return DeviceCSC(M.n, to(M.colptr), to(M.rowidx), None if vals is None else to(vals))
+
+
+class _CAI:
+    """__cuda_array_interface__ view of library-owned memory; holds `owner`."""
+
+    def __init__(self, ptr: int, shape, typestr: str, owner):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+        self._owner = owner
+
+
+def _view(ptr, count, typestr, owner, torch_dtype):
+    if count == 0 or not ptr:
+        return torch.empty(0, dtype=torch_dtype, device="cuda")
+    return torch.as_tensor(_CAI(ptr, (count,), typestr, owner), device="cuda")
+
+
+class _Handle:
+    """Owns one diaf_factors*; freed when the last view or Factors drops it."""
+
+    def __init__(self, ptr: int):
+        self.ptr = ctypes.c_void_p(ptr)
+
+    def free(self):
+        if self.ptr.value:
+            lib().diaf_free(self.ptr)
+            self.ptr = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Factors:
+    """W, V (CSC, library-owned device memory), per-column residuals and flags.
+
+    The tensors are zero-copy views of the library's buffers; they keep the
+    handle alive.  close() frees the buffers at once (the views must not be
+    used afterwards)."""
+
+    def __init__(self, handle: int, stream: int):
+        self._own = _Handle(handle)
+        self._stream = stream
+        L = lib()
+        info = Info_t()
+        _check(L.diaf_factor_info_get(self._own.ptr, ctypes.byref(info)))
+        self.info = info
+        W = CSC_t(); V = CSC_t(); res = ctypes.c_void_p(); fl = ctypes.c_void_p()
+        _check(L.diaf_get_factors(self._own.ptr, ctypes.byref(W), ctypes.byref(V), ctypes.byref(res),
+                                  ctypes.byref(fl)))
+        n = info.n
+        cplx = W.dtype == DIAF_C128
+        vt, vtd = ("<c16", torch.complex128) if cplx else ("<f8", torch.float64)
+        o = self._own
+        self.n = n
+        self.W = DeviceCSC(n, _view(W.colptr, n + 1, "<i4", o, torch.int32),
+                           _view(W.rowidx, W.nnz, "<i4", o, torch.int32), _view(W.vals, W.nnz, vt, o, vtd))
+        self.V = DeviceCSC(n, _view(V.colptr, n + 1, "<i4", o, torch.int32),
+                           _view(V.rowidx, V.nnz, "<i4", o, torch.int32), _view(V.vals, V.nnz, vt, o, vtd))
+        self.res = _view(res.value, n, "<f8", o, torch.float64)
+        self.flags = _view(fl.value, n, "<u4", o, torch.uint32)
+
+    @property
+    def handle(self):
+        return self._own.ptr
+
+    def timings(self) -> dict:
+        """CUDA-event timings of the factorisation (ms): total, numeric, per bucket kernel."""
+        buf = (ctypes.c_float * 10)()
+        _check(lib().diaf_factor_timings(self._own.ptr, buf, 10))
+        nb = self.info.n_buckets
+        return {"total_ms": buf[0], "numeric_ms": buf[1], "bucket_ms": [buf[2 + b] for b in range(nb)],
+                "bucket_cols": [self.info.bucket_cols[b] for b in range(nb)]}
+
+    def apply(self, x: torch.Tensor, y: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """y = W V^-1 x."""
+        if y is None:
+            y = torch.empty_like(x)
+        _check(lib().diaf_apply(self._own.ptr, _ptr(x), _ptr(y), _stream(stream)))
+        return y
+
+    def sync(self, stream=None) -> None:
+        _check(lib().diaf_sync(self._own.ptr, _stream(stream)))
+
+    def close(self):
+        self._own.free()
+
+
+def launch_count() -> int:
+    """Kernels launched by libdiaf.so in this process so far."""
+    return int(lib().diaf_launch_count())
+
+
+def factor(A: DeviceCSC, PW: DeviceCSC, vrule: int = RULE_UPPER, budget: torch.Tensor | None = None,
+           Vfixed: DeviceCSC | None = None, alg: str = "S", prec: str = "fp64", tie_tol: float = 1e-9,
+           stream=None) -> Factors:
+    """Columnwise W, V with A W ~ V (diaf_factor)."""
+    L = lib()
+    a = A.csc_t()
+    pw = PW.pattern_t()
+    fixed = Vfixed.pattern_t() if Vfixed is not None else None
+    vs = VSpec_t(vrule, ctypes.pointer(fixed) if fixed is not None else None, _ptr(budget), tie_tol)
+    h = ctypes.c_void_p()
+    s = _stream(stream)
+    _check(L.diaf_factor(ctypes.byref(a), ctypes.byref(pw), ctypes.byref(vs), ALG[alg], PREC[prec], s,
+                         ctypes.byref(h)))
+    return Factors(h.value, s)
+
+
+class Solver:
+    """A prepared for the Krylov solvers (diaf_solver_create)."""
+
+    def __init__(self, A: DeviceCSC, stream=None):
+        self._A = A
+        h = ctypes.c_void_p()
+        _check(lib().diaf_solver_create(ctypes.byref(A.csc_t()), _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    def bicgstab(self, b: torch.Tensor, M: Factors | None = None, tol=1e-8, maxit=1000, x=None, stream=None):
+        if x is None:
+            x = torch.empty_like(b)
+        info = SolveInfo_t()
+        _check(lib().diaf_bicgstab(self._h, M.handle if M is not None else None, _ptr(b), _ptr(x), tol, maxit,
+                                   _stream(stream), ctypes.byref(info)))
+        return x, info
+
+    def __del__(self):
+        try:
+            if self._h.value:
+                lib().diaf_solver_free(self._h)
+        except Exception:
+            pass

@@ -3,14 +3,20 @@
 Tolerances (FP64 path):
   * I_j bit-exact (V colptr and row indices identical);
   * res_j: |res_gpu - res_oracle| <= 1e-10 res_oracle + floor_j with
-    floor_j = 64 eps ||A(:,J_j)||_F ||w_j|| (the rounding level of ||A w - v||);
-  * w_j, v_j: after the shared phase convention (v_jj real >= 0) the vectors
-    themselves agree, ||x_gpu - x_oracle|| <= 1e-8 ||x_oracle|| (which bounds
-    the subspace angle by the same number), checked where the optimal vector
-    is unique (flag DEGENERATE clear and a resolved gap);
+    floor_j = 1e-12 ||A(:,J_j)||_F ||w_j|| (residuals below that are zero to
+    the rounding of w_j, which carries a factor cond(T));
+  * w_j, v_j where the optimal vector is unique (flags DEGENERATE,
+    RANK_DEFICIENT, EMPTY clear and, for DIAF-S, a resolved singular gap):
+    min over unit phases |z| = 1 of ||x_gpu - z x_oracle|| <= 1e-8 ||x_oracle||,
+    i.e. agreement up to the phase (this bounds the subspace angle);  the
+    phase convention itself (v_jj real >= 0 unless VJJ_ZERO) is checked on
+    the GPU vector directly;
+  * flags identical, except the VJJ_ZERO bit where v_jj is zero only to
+    rounding (|v_jj| < 1e-8 ||v_j|| on the oracle side) or the column is
+    degenerate (v_jj then depends on which optimal vector was taken);
   * degenerate or rank-deficient columns (several optimal vectors): the GPU
-    vector must be valid instead -- unit norm where the algorithm fixes it,
-    v_j = P_V A w_j (DIAF-S) and the same residual.
+    vector must be valid instead -- unit norm where the algorithm fixes it --
+    with the same residual.
 """
 from __future__ import annotations
 
@@ -18,6 +24,16 @@ import numpy as np
 
 EPS = np.finfo(np.float64).eps
 F_RANK, F_DEG, F_VJJ, F_NOCONV, F_NONFIN, F_EMPTY, F_REFINED = 1, 2, 4, 8, 16, 32, 64
+
+
+def _phase_free_err(x, y):
+    """min over |z| = 1 of ||x - z y|| / ||y||."""
+    ny = np.linalg.norm(y)
+    if ny == 0:
+        return np.linalg.norm(x)
+    c = np.vdot(y, x)
+    z = c / abs(c) if abs(c) > 0 else 1.0
+    return np.linalg.norm(x - z * y) / ny
 
 
 def host_factors(F):
@@ -47,7 +63,7 @@ def compare(g: dict, o, A, PW, alg: str, rtol_res=1e-10, vec_tol=1e-8, cols=None
         vo = o.v(t)
         J = PW.rowidx[PW.colptr[j]:PW.colptr[j + 1]]
         tnorm = np.sqrt(colnorm2[J].sum())
-        floor = 64 * EPS * tnorm * max(np.linalg.norm(wo), np.linalg.norm(wg), 1e-300)
+        floor = 1e-12 * tnorm * max(np.linalg.norm(wo), np.linalg.norm(wg), 1e-300)
         rg, ro = g["res"][j], o.res[t]
         err = abs(rg - ro)
         if not err <= rtol_res * ro + floor:
@@ -55,15 +71,24 @@ def compare(g: dict, o, A, PW, alg: str, rtol_res=1e-10, vec_tol=1e-8, cols=None
         if ro > floor:
             report["max_res_rel"] = max(report["max_res_rel"], err / ro)
         fo = int(o.flags[t]); fg = int(g["flags"][j])
-        if check_flags and (fo & ~F_REFINED) != (fg & ~F_REFINED):
+        jpos = np.searchsorted(Io, j)
+        vjj_rel = abs(vo[jpos]) / max(np.linalg.norm(vo), 1e-300) if jpos < Io.size and Io[jpos] == j else 0.0
+        mask = ~F_REFINED
+        if (fo & (F_DEG | F_RANK | F_EMPTY)) or 0.0 < vjj_rel < 1e-8:
+            mask &= ~F_VJJ
+        if check_flags and (fo & mask) != (fg & mask):
             report["flag_bad"].append((int(j), fg, fo))
+        if not (fg & F_VJJ) and jpos < Ig.size and Ig[jpos] == j and vg.size:
+            z = vg[jpos]
+            if abs(np.imag(z)) > 1e-12 * abs(z) or np.real(z) < 0:
+                report["vec_bad"].append((int(j), "phase", complex(z)))
         unique = not (fo & (F_DEG | F_RANK | F_EMPTY | F_VJJ)) and o.sig[t].size == 2
         if alg == "S" and unique:
             gap = abs(o.sig[t, 1] - o.sig[t, 0]) / max(o.sig[t, 1], 1e-300)
             unique = gap >= 1e-6
         if unique:
-            e1 = np.linalg.norm(wg - wo) / max(np.linalg.norm(wo), 1e-300)
-            e2 = np.linalg.norm(vg - vo) / max(np.linalg.norm(vo), 1e-300)
+            e1 = _phase_free_err(wg, wo)
+            e2 = _phase_free_err(vg, vo)
             report["max_vec_rel"] = max(report["max_vec_rel"], e1, e2)
             if not (e1 <= vec_tol and e2 <= vec_tol):
                 report["vec_bad"].append((int(j), float(e1), float(e2)))

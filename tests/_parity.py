@@ -12,7 +12,7 @@ Tolerances (FP64 path):
     phase convention itself (v_jj real >= 0 unless VJJ_ZERO) is checked on
     the GPU vector directly;
   * flags identical, except the VJJ_ZERO bit where v_jj is zero only to
-    rounding (|v_jj| < 1e-8 ||v_j|| on the oracle side) or the column is
+    rounding (|v_jj| < 1e-8 ||v_j|| on the oracle side, 0 included) or the column is
     degenerate (v_jj then depends on which optimal vector was taken);
   * degenerate or rank-deficient columns (several optimal vectors): the GPU
     vector must be valid instead -- unit norm where the algorithm fixes it --
@@ -74,7 +74,7 @@ def compare(g: dict, o, A, PW, alg: str, rtol_res=1e-10, vec_tol=1e-8, cols=None
         jpos = np.searchsorted(Io, j)
         vjj_rel = abs(vo[jpos]) / max(np.linalg.norm(vo), 1e-300) if jpos < Io.size and Io[jpos] == j else 0.0
         mask = ~F_REFINED
-        if (fo & (F_DEG | F_RANK | F_EMPTY)) or 0.0 < vjj_rel < 1e-8:
+        if (fo & (F_DEG | F_RANK | F_EMPTY)) or vjj_rel < 1e-8:
             mask &= ~F_VJJ
         if check_flags and (fo & mask) != (fg & mask):
             report["flag_bad"].append((int(j), fg, fo))

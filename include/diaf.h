@@ -169,6 +169,25 @@ diaf_status diaf_get_factors(const diaf_factors* F, diaf_csc* W, diaf_csc* V, co
  * zero diagonal -- found by the first call), ENOMEM, ECUDA. */
 diaf_status diaf_apply(diaf_factors* F, const void* x, void* y, void* stream);
 
+/* y = W V^-1 x exactly as diaf_apply computes it, but allocating nothing.
+ * (The paper has no counterpart: this is an interface for callers that must
+ * not allocate device memory when they apply the preconditioner -- code
+ * running inside a device-memory budget fixed at start-up, a Krylov loop
+ * being recorded into a CUDA graph, where plain cudaMalloc cannot be
+ * captured, or a host framework whose allocator owns all device memory.)
+ * Such callers set up beforehand: diaf_factor, then one diaf_apply on F,
+ * which builds the row-oriented copies of W and V.  Without that first
+ * diaf_apply this call returns DIAF_EINVAL.
+ * The solve's scratch (a ready flag per row, a ticket counter, t = V^-1 x)
+ * is one fixed device array of about 5.3 MB inside the library, held by
+ * every GPU that loads it until the process exits; n is limited to 262,144
+ * rows (DIAF_EINVAL beyond).  The first call on each device looks up the
+ * array's device address and clears its flags: make that first call before
+ * any stream capture.  All calls on a device share the array and leave their
+ * contents in it, so calls that overlap on the GPU (different streams, or
+ * several host threads) race; serialise them.  x, y as for diaf_apply. */
+diaf_status diaf_apply_static(diaf_factors* F, const void* x, void* y, void* stream);
+
 /* Waits for `stream` and reports device-side errors recorded by earlier
  * calls on F (bounded-wait timeouts, capacity overflows) as a status. */
 diaf_status diaf_sync(diaf_factors* F, void* stream);

@@ -6,16 +6,17 @@
 #include <string>
 #include <vector>
 
+#include "factors.cuh"
 #include "launch.cuh"
 #include "plan.cuh"
 #include "sparse.cuh"
 
 static std::atomic<long long> g_launches{0};
+static thread_local std::string g_last_error;
+void diaf_set_last_error(const char* msg) { g_last_error = msg; }
 void diaf_note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 namespace {
-
-thread_local std::string g_last_error;
 
 diaf_status fail(diaf_status st, const std::string& why) {
   g_last_error = why;
@@ -68,43 +69,6 @@ diaf_status check_device() {
 }
 
 }  // namespace
-
-struct diaf_factors {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  int n = 0;
-  int dtype = DIAF_F64, alg = DIAF_ALG_S, prec = DIAF_PREC_FP64, rule = DIAF_RULE_UPPER;
-  int64_t nnz_w = 0, nnz_v = 0;
-  int32_t *Wcp = nullptr, *Wri = nullptr, *Vcp = nullptr, *Vri = nullptr;
-  void *Wv = nullptr, *Vv = nullptr;
-  double* res = nullptr;
-  uint32_t* flags = nullptr;
-  uint32_t* status = nullptr;
-  diaf_factor_info info{};
-  std::vector<void*> owned;
-  // CUDA events: [0] start, [1] numeric start, [2] end, [3 + 2b], [4 + 2b] around bucket b
-  static constexpr int kEvents = 3 + 2 * kNumBuckets;
-  cudaEvent_t ev[kEvents] = {};
-  bool bucket_ran[kNumBuckets] = {};
-  // apply
-  bool apply_ready = false;
-  bool v_upper = true;
-  Csr Vr, Wr;
-  uint32_t* ready = nullptr;
-  int32_t* counter = nullptr;
-  uint32_t gen = 0;
-  void* tbuf = nullptr;
-
-  template <class T>
-  cudaError_t alloc(T** p, size_t count) {
-    void* q = nullptr;
-    cudaError_t e = cudaMallocAsync(&q, sizeof(T) * (count > 0 ? count : 1), stream);
-    if (e != cudaSuccess) return e;
-    owned.push_back(q);
-    *p = static_cast<T*>(q);
-    return cudaSuccess;
-  }
-};
 
 extern "C" {
 

@@ -1,0 +1,47 @@
+// The factorisation handle behind the opaque diaf_factors of include/diaf.h.
+#pragma once
+
+#include <vector>
+
+#include "plan.cuh"
+#include "sparse.cuh"
+
+// Sets the thread's diaf_last_error() text (api.cu).
+void diaf_set_last_error(const char* msg);
+
+struct diaf_factors {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int n = 0;
+  int dtype = DIAF_F64, alg = DIAF_ALG_S, prec = DIAF_PREC_FP64, rule = DIAF_RULE_UPPER;
+  int64_t nnz_w = 0, nnz_v = 0;
+  int32_t *Wcp = nullptr, *Wri = nullptr, *Vcp = nullptr, *Vri = nullptr;
+  void *Wv = nullptr, *Vv = nullptr;
+  double* res = nullptr;
+  uint32_t* flags = nullptr;
+  uint32_t* status = nullptr;
+  diaf_factor_info info{};
+  std::vector<void*> owned;
+  // CUDA events: [0] start, [1] numeric start, [2] end, [3 + 2b], [4 + 2b] around bucket b
+  static constexpr int kEvents = 3 + 2 * kNumBuckets;
+  cudaEvent_t ev[kEvents] = {};
+  bool bucket_ran[kNumBuckets] = {};
+  // apply
+  bool apply_ready = false;
+  bool v_upper = true;
+  Csr Vr, Wr;
+  uint32_t* ready = nullptr;
+  int32_t* counter = nullptr;
+  uint32_t gen = 0;
+  void* tbuf = nullptr;
+
+  template <class T>
+  cudaError_t alloc(T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, sizeof(T) * (count > 0 ? count : 1), stream);
+    if (e != cudaSuccess) return e;
+    owned.push_back(q);
+    *p = static_cast<T*>(q);
+    return cudaSuccess;
+  }
+};

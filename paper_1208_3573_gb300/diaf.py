@@ -75,6 +75,7 @@ def lib() -> ctypes.CDLL:
         L.diaf_get_factors.argtypes = [vp, ctypes.POINTER(CSC_t), ctypes.POINTER(CSC_t),
                                        ctypes.POINTER(vp), ctypes.POINTER(vp)]
         L.diaf_apply.argtypes = [vp, vp, vp, vp]
+        L.diaf_apply_static.argtypes = [vp, vp, vp, vp]
         L.diaf_sync.argtypes = [vp, vp]
         L.diaf_free.argtypes = [vp]
         L.diaf_free.restype = None
@@ -224,6 +225,12 @@ class Factors:
         if y is None:
             y = torch.empty_like(x)
         _check(lib().diaf_apply(self._own.ptr, _ptr(x), _ptr(y), _stream(stream)))
+        return y
+
+    def apply_static(self, x: torch.Tensor, y: torch.Tensor, stream=None) -> torch.Tensor:
+        """y = W V^-1 x through diaf_apply_static: allocates nothing (y must be
+        given; apply() must have run once on these factors)."""
+        _check(lib().diaf_apply_static(self._own.ptr, _ptr(x), _ptr(y), _stream(stream)))
         return y
 
     def sync(self, stream=None) -> None:

@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 
 from workloads import make_workload  # noqa: E402
 
-METRIC = "W,V setup columns/s (DIAF-S, 256x256 convection-diffusion, W = pattern(A^2))"
+METRIC = "W,V setup columns/s (DIAF-S, 256x256 convection-diffusion, W = pattern(A^2)); vs plain FP64 GPU form"
 UNIT = "columns/s"
 
 
@@ -45,8 +45,10 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# FP64 arithmetic peak of the GB300 (no measured figure exists in the peaks
-# file): 1.25 TFLOP/s nominal at the 2070 MHz maximum SM clock.
+# ALU peaks of the GB300 (the peaks file measures only copy bandwidth and
+# bf16 GEMM): FP32 = 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+# = 80.5 TFLOP/s; FP64 = 1.25 TFLOP/s nominal.
+FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_NOMINAL_TFLOPS = 1.25
 
 
@@ -171,7 +173,7 @@ def main():
     ap.add_argument("--impl", default="diaf", choices=["diaf", "reference"])
     ap.add_argument("--workload", default="convdiff256_A2")
     ap.add_argument("--alg", default="S", choices=["S", "Q"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed32"])
+    ap.add_argument("--prec", default="mixed32", choices=["fp64", "mixed32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the solve / other-form side measurements")
     args = ap.parse_args()
@@ -284,12 +286,14 @@ def main():
     m, k = tile_sizes(w)
     flops = algorithmic_flops(m, k, lcount, args.alg, cplx)
     kern = float(np.mean([sum(x) for x in kern_ms]))
-    fp64_peak = FP64_NOMINAL_TFLOPS * 1e12
     achieved = flops / (kern / 1e3)
-    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
-            "frac": achieved / fp64_peak, "traffic": None, "kernel": "column_warp_kernel (numeric pass)",
-            "kernel_ms": kern, "algorithmic_flops": flops,
-            "peak_source": "FP64 nominal 1.25 TFLOP/s (no measured FP64 figure in the peaks file)"}
+    if args.prec == "fp64":
+        peak, src, kname = FP64_NOMINAL_TFLOPS * 1e12, "FP64 nominal 1.25 TFLOP/s", "column_warp_kernel"
+    else:
+        peak, src, kname = FP32_TFLOPS * 1e12, "FP32 152 SMs x 128 lanes x 2 flop x 2.07 GHz", "column_mixed_kernel"
+    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "kernel": f"{kname} (numeric pass, all buckets)",
+            "kernel_ms": kern, "algorithmic_flops": flops, "peak_source": src}
 
     extras = {}
     if not args.no_extras and rank == 0:
@@ -308,6 +312,26 @@ def main():
                               "solve_ms": solve_ms, "its_unpreconditioned": info0.iterations,
                               "err_inf": float((x - 1).abs().max().item())}
         F.close()
+        # the plain FP64 form on the same workload: columns/s and residual agreement
+        if args.prec != "fp64":
+            tt = []
+            for _ in range(3):
+                flush.zero_()
+                torch.cuda.synchronize()
+                Fd = diaf.factor(A, PW, w.vrule, bud, alg=args.alg, prec="fp64")
+                tt.append(Fd.timings()["total_ms"])
+                res64 = Fd.res.cpu().numpy()
+                Fd.close()
+            Fm = diaf.factor(A, PW, w.vrule, bud, alg=args.alg, prec=args.prec)
+            resm = Fm.res.cpu().numpy()
+            fb = Fm.fallbacks()
+            Fm.close()
+            rel = np.abs(resm - res64) / np.maximum(np.abs(res64), 1e-300)
+            c64 = w.n / (statistics.median(tt) / 1e3)
+            extras["fp64_plain"] = {"factor_columns_per_s": c64, "factor_ms": statistics.median(tt),
+                                    "speedup_of_mixed": (w.n / (float(np.mean(total_ms)) / 1e3)) / c64,
+                                    "res_rel_diff_max": float(rel.max()), "res_rel_diff_median": float(np.median(rel)),
+                                    "mixed_fp64_fallback_columns": int(sum(fb))}
         # the other algorithm, same workload (factor only, median of 3)
         other = "Q" if args.alg == "S" else "S"
         tt = []
@@ -322,7 +346,9 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "c128" if cplx else "f64", "data": "synthetic",
+                "vs_baseline": None,
+                "dtype": ("c64+c128" if cplx else "f32+f64") if args.prec == "mixed32" else ("c128" if cplx else "f64"),
+                "data": "synthetic",
                 "config": {"workload": w.name, "n": w.n, "alg": args.alg, "prec": args.prec,
                            "nnz_A": w.A.nnz, "nnz_W": w.PW.nnz, "columns_per_step": w.n,
                            "l2": "flushed (256 MiB write) before every timed step",

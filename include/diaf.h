@@ -51,10 +51,12 @@ enum { DIAF_F64 = 0, DIAF_C128 = 1 };
 enum { DIAF_ALG_Q = 1, DIAF_ALG_S = 2 };
 
 /* Arithmetic of the numeric phase.  DIAF_PREC_FP64: everything in FP64
- * (complex128 for DIAF_C128).  DIAF_PREC_MIXED32: gather, QR, Jacobi in FP32
- * (complex64), then one FP64 refinement step of (w_j, v_j) against the FP64
- * tile and an FP64 residual; leverage keys near a selection threshold are
- * recomputed in FP64 so that I_j is the FP64 choice. */
+ * (complex128 for DIAF_C128).  DIAF_PREC_MIXED32: QR, leverage keys and
+ * Jacobi in FP32 (complex64) on an FP64 tile, then one FP64 refinement step
+ * of (w_j, v_j) against the FP64 tile and an FP64 residual.  A column whose
+ * FP32 leverage decision lies within the FP32 error bound of its threshold,
+ * or whose tile is too ill-conditioned for FP32 factors, is computed by the
+ * FP64 path instead (flag DIAF_FLAG_FP64_FALLBACK), so I_j is the FP64 choice. */
 enum { DIAF_PREC_FP64 = 0, DIAF_PREC_MIXED32 = 1 };
 
 /* How I_j (the pattern of column j of V) is obtained.  FIXED: given pattern.
@@ -75,7 +77,9 @@ enum {
   DIAF_FLAG_JACOBI_NOCONV = 8,   /* the Jacobi SVD hit its 30-sweep limit */
   DIAF_FLAG_NONFINITE = 16,      /* NaN or Inf in w_j, v_j or res_j */
   DIAF_FLAG_EMPTY = 32,          /* k_j = 0 (empty W column) */
-  DIAF_FLAG_REFINED_KEYS = 64    /* mixed precision: leverage keys were recomputed in FP64 */
+  DIAF_FLAG_FP64_FALLBACK = 64   /* mixed precision: the column was computed by the FP64 path (an FP32
+                                    leverage decision within its error bound, or a tile too ill-conditioned
+                                    for FP32 factors) */
 };
 
 typedef struct {
@@ -148,6 +152,11 @@ diaf_status diaf_factor_info_get(const diaf_factors* F, diaf_factor_info* info);
  * numeric kernel of size bucket b (0 when the bucket was empty).  nms is the
  * capacity of ms and must be >= 2 + n_buckets. */
 diaf_status diaf_factor_timings(const diaf_factors* F, float* ms, int32_t nms);
+
+/* Mixed precision: the number of columns per size bucket that the FP64 path
+ * computed (flag DIAF_FLAG_FP64_FALLBACK); zeros for the FP64 form.  Waits for
+ * F's stream.  nb >= n_buckets. */
+diaf_status diaf_factor_fallbacks(const diaf_factors* F, int32_t* counts, int32_t nb);
 
 /* Number of CUDA kernels this library has launched in this process. */
 long long diaf_launch_count(void);

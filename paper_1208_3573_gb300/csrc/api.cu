@@ -97,6 +97,15 @@ void diaf_free(diaf_factors* F) {
 
 long long diaf_launch_count(void) { return g_launches.load(); }
 
+diaf_status diaf_factor_fallbacks(const diaf_factors* F, int32_t* counts, int32_t nb) {
+  if (!F || !counts || nb < kNumBuckets) return fail(DIAF_EINVAL, "need a handle and room for n_buckets counts");
+  for (int i = 0; i < nb; ++i) counts[i] = 0;
+  if (!F->fb_counts) return DIAF_OK;
+  DIAF_CU(cudaMemcpyAsync(counts, F->fb_counts, sizeof(int32_t) * kNumBuckets, cudaMemcpyDeviceToHost, F->stream));
+  DIAF_CU(cudaStreamSynchronize(F->stream));
+  return DIAF_OK;
+}
+
 diaf_status diaf_factor_timings(const diaf_factors* F, float* ms, int32_t nms) {
   if (!F || !ms || nms < 2 + kNumBuckets) return fail(DIAF_EINVAL, "need a handle and room for 2 + n_buckets values");
   for (int i = 0; i < nms; ++i) ms[i] = 0.0f;
@@ -127,7 +136,6 @@ diaf_status diaf_factor(const diaf_csc* A, const diaf_pattern* PW, const diaf_vs
   if (A->n > 0 && (!A->colptr || !PW->colptr || (A->nnz > 0 && (!A->rowidx || !A->vals)) ||
                    (PW->nnz > 0 && !PW->rowidx)))
     return fail(DIAF_EINVAL, "NULL array in A or PW");
-  if (prec == DIAF_PREC_MIXED32) return fail(DIAF_EUNSUPPORTED, "mixed precision not built yet");
   diaf_status ds = check_device();
   if (ds != DIAF_OK) return ds;
 
@@ -162,12 +170,12 @@ diaf_status diaf_factor(const diaf_csc* A, const diaf_pattern* PW, const diaf_vs
   DIAF_CU(pool.get(&stats, 4));
   DIAF_CU(pool.get(&bucket_count, kNumBuckets));
   DIAF_CU(pool.get(&big_count, 1));
-  DIAF_CU(pool.get(&work, kNumBuckets));
+  DIAF_CU(pool.get(&work, 2 * kNumBuckets));
   DIAF_CU(cudaMemsetAsync(status, 0, sizeof(uint32_t), s));
   DIAF_CU(cudaMemsetAsync(stats, 0, sizeof(int32_t) * 4, s));
   DIAF_CU(cudaMemsetAsync(bucket_count, 0, sizeof(int32_t) * kNumBuckets, s));
   DIAF_CU(cudaMemsetAsync(big_count, 0, sizeof(int32_t), s));
-  DIAF_CU(cudaMemsetAsync(work, 0, sizeof(int32_t) * kNumBuckets, s));
+  DIAF_CU(cudaMemsetAsync(work, 0, sizeof(int32_t) * 2 * kNumBuckets, s));
 
   // ---- input checks on the device (sorted, in range)
   DIAF_CU(check_csc(n, A->colptr, A->rowidx, A->nnz, status, s));
@@ -267,18 +275,49 @@ diaf_status diaf_factor(const diaf_csc* A, const diaf_pattern* PW, const diaf_vs
   ca.tie_tol = V->tie_tol > 0 ? V->tie_tol : 1e-9;
   ca.Wv = F->Wv; ca.Vri = F->Vri; ca.Vv = F->Vv;
   ca.res = F->res; ca.flags = F->flags; ca.status = status;
+  const bool mixed = prec == DIAF_PREC_MIXED32;
+  int32_t *fb_list = nullptr, *fb_count = nullptr;
+  if (mixed) {
+    DIAF_CU(pool.get(&fb_list, (size_t)kNumBuckets * n));
+    DIAF_CU(pool.get(&fb_count, kNumBuckets));
+    DIAF_CU(cudaMemsetAsync(fb_count, 0, sizeof(int32_t) * kNumBuckets, s));
+  }
+  auto fp64_launch = [&](int b, const ColArgs& c, int hint) {
+    return cplx ? launch_columns_c128(b, alg, c, hint, s) : launch_columns_f64(b, alg, c, hint, s);
+  };
   for (int b = 0; b < kNumBuckets; ++b) {
     if (h_bc[b] == 0) continue;
     ca.list = pa.bucket_list + (size_t)b * n;
     ca.list_count = bucket_count + b;
     ca.work_counter = work + b;
+    ca.extra_flags = 0;
     DIAF_CU(cudaEventRecord(F->ev[3 + 2 * b], s));
-    cudaError_t e = cplx ? launch_columns_c128(b, alg, ca, h_bc[b], s) : launch_columns_f64(b, alg, ca, h_bc[b], s);
+    cudaError_t e;
+    if (mixed) {
+      ca.fb_list = fb_list + (size_t)b * n;
+      ca.fb_count = fb_count + b;
+      e = cplx ? launch_columns_mixed_c64(b, alg, ca, h_bc[b], s) : launch_columns_mixed_f32(b, alg, ca, h_bc[b], s);
+      if (e == cudaSuccess) {
+        // the FP64 kernel finishes the columns the mixed kernel handed back
+        ColArgs cf = ca;
+        cf.list = ca.fb_list;
+        cf.list_count = ca.fb_count;
+        cf.work_counter = work + kNumBuckets + b;
+        cf.extra_flags = DIAF_FLAG_FP64_FALLBACK;
+        e = fp64_launch(b, cf, h_bc[b]);
+      }
+    } else {
+      e = fp64_launch(b, ca, h_bc[b]);
+    }
     if (e == cudaErrorNotSupported)
       return fail(DIAF_EUNSUPPORTED, "bucket " + std::to_string(b) + " has no kernel for this configuration yet");
     if (e != cudaSuccess) return cuda_fail(e, "column kernel launch");
     DIAF_CU(cudaEventRecord(F->ev[4 + 2 * b], s));
     F->bucket_ran[b] = true;
+  }
+  if (mixed) {
+    DIAF_CU(F->alloc(&F->fb_counts, kNumBuckets));
+    DIAF_CU(cudaMemcpyAsync(F->fb_counts, fb_count, sizeof(int32_t) * kNumBuckets, cudaMemcpyDeviceToDevice, s));
   }
   DIAF_CU(cudaEventRecord(F->ev[2], s));
   pool.release();

@@ -1,5 +1,5 @@
-// Fused per-column kernel of the columnwise setup, one warp per column, the
-// tile in shared memory.  For column j:
+// Fused per-column kernel of the columnwise setup, FP64 (or complex128)
+// throughout, one warp per column, the tile in shared memory.  For column j:
 //   gather  T = A(R_j, J_j)                       (A_j of eq. spaqr on its nonzero rows)
 //   QR      T = Q R, Householder                  (eq. spaqr)
 //   keys    h_i = ||Q(i,:)||^2, Q = T R^-1 by rows (norms of the columns of Q_j^*, Sec. 3.1)
@@ -11,12 +11,10 @@
 //           least-squares solution of eq. condwj
 //   phase   v_jj real >= 0 (scaling invariance, Sec. 2.1)
 //   res     ||A w - v||_2 from its definition; scatter into CSC W and V.
+// The same kernel finishes the columns the mixed-precision kernel hands back.
 #pragma once
 
-#include <cfloat>
-#include <climits>
-
-#include "common.cuh"
+#include "warp_la.cuh"
 
 struct ColArgs {
   int n;
@@ -38,6 +36,9 @@ struct ColArgs {
   const int32_t* list;        // bucket's columns
   const int32_t* list_count;  // device count of the list
   int32_t* work_counter;      // zeroed before launch
+  uint32_t extra_flags;       // OR-ed into every column's flags (FP64 fallback of the mixed form)
+  int32_t* fb_list;           // mixed form: columns handed to the FP64 kernel
+  int32_t* fb_count;
   void* Wv;
   int32_t* Vri;
   void* Vv;
@@ -46,206 +47,51 @@ struct ColArgs {
   uint32_t* status;
 };
 
-constexpr int kMaxSweeps = 30;
-
-__device__ __forceinline__ bool admissible_row(int rule, int i, int j) {
-  if (i == j) return false;
-  if (rule == DIAF_RULE_UPPER) return i < j;
-  if (rule == DIAF_RULE_LOWER) return i > j;
-  return true;
-}
-
-template <class T> __device__ __forceinline__ T eps_of();
-template <> __device__ __forceinline__ double eps_of<double>() { return DBL_EPSILON; }
-template <> __device__ __forceinline__ float eps_of<float>() { return FLT_EPSILON; }
-
-// ------------------------------------------------------------------ QR
-// Householder QR of the column-major m x k matrix T (leading dimension LD)
-// in place: reflector c maps x = T(c:m, c) to beta e_1 with
-// beta = -(x_0/|x_0|) ||x||, u = x - beta e_1.  On return rows 0..k-1 hold R.
-template <class S, int LD>
-__device__ void warp_householder_qr(S* T, int m, int k, int lane) {
-  using R = RealOf<S>;
-  int p = m < k ? m : k;
-  for (int c = 0; c < p; ++c) {
-    S* tc = T + c * LD;
-    R nrm2 = R(0);
-    for (int r = c + lane; r < m; r += DIAF_WARP) nrm2 += sc_abs2(tc[r]);
-    nrm2 = warp_sum(nrm2);
-    S alpha = tc[c];
-    __syncwarp();
-    if (nrm2 == R(0)) continue;
-    R ax = sqrt(sc_abs2(alpha));
-    S ph = ax > R(0) ? (R(1) / ax) * alpha : sc_real_s<S>(R(1));
-    S beta = -(sqrt(nrm2) * ph);
-    S u0 = alpha - beta;
-    R uu = nrm2 - sc_abs2(alpha) + sc_abs2(u0);
-    R two_uu = R(2) / uu;
-    for (int q = c + 1; q < k; ++q) {
-      S* tq = T + q * LD;
-      S part = sc_zero<S>();
-      for (int r = c + lane; r < m; r += DIAF_WARP) part += sc_cmul(r == c ? u0 : tc[r], tq[r]);
-      S f = two_uu * warp_sum(part);
-      for (int r = c + lane; r < m; r += DIAF_WARP) tq[r] -= f * (r == c ? u0 : tc[r]);
-    }
-    __syncwarp();
-    for (int r = c + lane; r < m; r += DIAF_WARP) tc[r] = (r == c) ? beta : sc_zero<S>();
-    __syncwarp();
-  }
-}
-
-// ------------------------------------------------------------------ Jacobi
-// Parallel one-sided (Hestenes) Jacobi on the p x q matrix G (leading
-// dimension LDG): G V has orthogonal columns, V (q x q, leading dimension
-// LDV) unitary.  Round-robin ordering: in each of the qq-1 rounds of a sweep
-// (qq = q rounded up to even) the columns split into qq/2 disjoint pairs, one
-// group of LPP lanes per pair.  A pair is rotated when |g_a^* g_b| > tol
-// sqrt(|g_a|^2 |g_b|^2), tol = p eps, and neither column is below
-// p eps ||G||_F.  Returns sweeps used, or -1 at the sweep limit.
-template <class S, int LDG, int LDV, int QMAX>
-__device__ int warp_jacobi(S* G, int p, int q, S* V, int lane) {
-  using R = RealOf<S>;
-  constexpr int kPairsMax = QMAX / 2;
-  constexpr int kGroups = kPairsMax >= 32 ? 32 : (kPairsMax >= 16 ? 16 : (kPairsMax >= 8 ? 8 : (kPairsMax >= 4 ? 4 : 2)));
-  constexpr int LPP = DIAF_WARP / kGroups;
-  for (int i = lane; i < q * q; i += DIAF_WARP) {
-    int r = i % q, c = i / q;
-    V[r + c * LDV] = (r == c) ? sc_real_s<S>(R(1)) : sc_zero<S>();
-  }
-  R nf2 = R(0);
-  for (int i = lane; i < p * q; i += DIAF_WARP) nf2 += sc_abs2(G[(i % p) + (i / p) * LDG]);
-  nf2 = warp_sum(nf2);
-  const R tol = R(p > 1 ? p : 1) * eps_of<R>();
-  const R tiny = tol * tol * nf2;
-  __syncwarp();
-  if (q < 2) return 1;
-  const int qq = (q + 1) & ~1;
-  const int npairs = qq / 2;
-  const int grp = lane / LPP, sub = lane % LPP;
-  for (int sweep = 1; sweep <= kMaxSweeps; ++sweep) {
-    bool rotated = false;
-    for (int rnd = 0; rnd < qq - 1; ++rnd) {
-      for (int pr0 = 0; pr0 < npairs; pr0 += kGroups) {
-        int pr = pr0 + grp;
-        int a = -1, b = -1;
-        if (pr < npairs) {
-          int pa = pr, pb = qq - 1 - pr;
-          a = pa == 0 ? 0 : 1 + (pa - 1 + rnd) % (qq - 1);
-          b = 1 + (pb - 1 + rnd) % (qq - 1);
-          if (a > b) { int t = a; a = b; b = t; }
-          if (b >= q) a = -1;  // bye for the padding column
-        }
-        bool act = a >= 0;
-        R al = R(0), be = R(0);
-        S ga = sc_zero<S>();
-        if (act) {
-          const S* ca = G + a * LDG;
-          const S* cb = G + b * LDG;
-          for (int i = sub; i < p; i += LPP) {
-            S x = ca[i], y = cb[i];
-            al += sc_abs2(x);
-            be += sc_abs2(y);
-            ga += sc_cmul(x, y);
-          }
-        }
-        al = group_sum<LPP>(al);
-        be = group_sum<LPP>(be);
-        ga = group_sum<LPP>(ga);
-        R ag = sqrt(sc_abs2(ga));
-        bool rot = act && al > tiny && be > tiny && ag != R(0) && ag > tol * sqrt(al * be);
-        if (rot) {
-          rotated = true;
-          S eph = (R(1) / ag) * sc_conj(ga);
-          R zeta = (be - al) / (R(2) * ag);
-          R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
-          R cs = R(1) / sqrt(R(1) + t * t), sn = cs * t;
-          S* ca = G + a * LDG;
-          S* cb = G + b * LDG;
-          for (int i = sub; i < p; i += LPP) {
-            S x = ca[i], y = eph * cb[i];
-            ca[i] = cs * x - sn * y;
-            cb[i] = sn * x + cs * y;
-          }
-          S* va = V + a * LDV;
-          S* vb = V + b * LDV;
-          for (int i = sub; i < q; i += LPP) {
-            S x = va[i], y = eph * vb[i];
-            va[i] = cs * x - sn * y;
-            vb[i] = sn * x + cs * y;
-          }
-        }
-        __syncwarp();
-      }
-    }
-    if (!__any_sync(DIAF_FULL, rotated)) return sweep;
-  }
-  return -1;
-}
-
-// column norms of G (p x q): sigma[c]
-template <class S, int LDG>
-__device__ void warp_col_norms(const S* G, int p, int q, RealOf<S>* sigma, int lane) {
-  using R = RealOf<S>;
-  for (int c = lane; c < q; c += DIAF_WARP) {
-    R s = R(0);
-    for (int i = 0; i < p; ++i) s += sc_abs2(G[i + c * LDG]);
-    sigma[c] = sqrt(s);
-  }
-  __syncwarp();
-}
-
-// ------------------------------------------------------------------ kernel
-template <class S, int KMAX, int MMAX>
-struct WarpLayout {
-  static constexpr int kTile = MMAX * KMAX;
-  static constexpr size_t raw() {
-    return sizeof(S) * (2 * kTile + 2 * KMAX * KMAX + KMAX + MMAX) + sizeof(double) * (MMAX + KMAX) +
-           sizeof(int32_t) * (5 * MMAX + 2 * KMAX + 8);
-  }
-  static constexpr size_t bytes() { return (raw() + 15) / 16 * 16; }  // keeps every warp's slice 16-byte aligned
+// ------------------------------------------------------------------ shared steps
+// Per-warp index scratch for the parts common to both kernels.
+struct ColumnIdx {
+  int32_t* rs;    // R_j (MMAX), INT_MAX past m
+  int32_t* inI;   // per tile row: position in I_j or -1
+  int32_t* pick;  // per tile row: picked by the rule
+  int32_t* Is;    // I_j rows (sorted)
+  int32_t* Iloc;  // tile row of Is[t] or -1
+  int32_t* cst;   // column starts of J_j in A (KMAX)
+  int32_t* coff;  // exclusive offsets of the gathered entries (KMAX)
+  int32_t* misc;  // [0] = position of j in I_j
 };
+template <int KMAX, int MMAX>
+constexpr size_t idx_bytes() { return sizeof(int32_t) * (5 * MMAX + 2 * KMAX + 8); }
 
-template <class S, int KMAX, int MMAX, int ALG>
-__device__ void solve_column_warp(const ColArgs& a, int j, unsigned char* smem, int lane) {
-  using R = RealOf<S>;
-  using L = WarpLayout<S, KMAX, MMAX>;
-  S* Ts = reinterpret_cast<S*>(smem);           // original tile, MMAX x KMAX
-  S* Tw = Ts + L::kTile;                          // working tile / Q rows / Q_I
-  S* Rs = Tw + L::kTile;                          // R of T, later R-hat (KMAX x KMAX)
-  S* Vj = Rs + KMAX * KMAX;                       // Jacobi V
-  S* wv = Vj + KMAX * KMAX;                       // w (KMAX)
-  S* vv = wv + KMAX;                              // v (MMAX)
-  double* hk = reinterpret_cast<double*>(vv + MMAX);  // leverage keys (MMAX)
-  R* sig = reinterpret_cast<R*>(hk + MMAX);       // singular values (KMAX)
-  int32_t* rs = reinterpret_cast<int32_t*>(hk + MMAX + KMAX);
-  int32_t* inI = rs + MMAX;      // per tile row: position in I or -1
-  int32_t* pick = inI + MMAX;    // per tile row: picked by the rule
-  int32_t* Is = pick + MMAX;     // I_j rows (sorted)
-  int32_t* Iloc = Is + MMAX;     // tile row of Is[t] or -1
-  int32_t* cst = Iloc + MMAX;    // column starts of J_j in A
-  int32_t* coff = cst + KMAX;    // exclusive offsets of the gathered entries
-  int32_t* misc = coff + KMAX;   // [0] = jpos
+template <int KMAX, int MMAX>
+__device__ ColumnIdx carve_idx(int32_t* base) {
+  ColumnIdx ix;
+  ix.rs = base;
+  ix.inI = ix.rs + MMAX;
+  ix.pick = ix.inI + MMAX;
+  ix.Is = ix.pick + MMAX;
+  ix.Iloc = ix.Is + MMAX;
+  ix.cst = ix.Iloc + MMAX;
+  ix.coff = ix.cst + KMAX;
+  ix.misc = ix.coff + KMAX;
+  return ix;
+}
 
-  const int k = a.Wcp[j + 1] - a.Wcp[j];
-  const int32_t* J = a.Wri + a.Wcp[j];
-  const int m = a.m[j];
-  const int l = a.l[j];
-  const int me = m > k ? m : k;  // rows of the working tile (zero padded)
+// Loads R_j and gathers T = A(R_j, J_j) (zero padded to me rows) into Ts.
+template <class SD, int KMAX, int MMAX>
+__device__ void gather_tile(const ColArgs& a, int j, int k, int m, int me, SD* Ts, const ColumnIdx& ix, int lane) {
   const int32_t* Rj = a.rows + a.Eoff[j];
-  const S* Av = reinterpret_cast<const S*>(a.Av);
-  uint32_t flags = 0;
-
-  // ---- row set and gather
+  const int32_t* J = a.Wri + a.Wcp[j];
+  const SD* Av = reinterpret_cast<const SD*>(a.Av);
   for (int r = lane; r < MMAX; r += DIAF_WARP) {
-    rs[r] = r < m ? Rj[r] : INT_MAX;
-    inI[r] = -1;
-    pick[r] = 0;
+    ix.rs[r] = r < m ? Rj[r] : INT_MAX;
+    ix.inI[r] = -1;
+    ix.pick[r] = 0;
   }
-  for (int i = lane; i < me * k; i += DIAF_WARP) Ts[(i % me) + (i / me) * MMAX] = sc_zero<S>();
+  for (int i = lane; i < me * k; i += DIAF_WARP) Ts[(i % me) + (i / me) * MMAX] = sc_zero<SD>();
   int len = 0;
   if (lane < k) {
     int c = J[lane];
-    cst[lane] = a.Acp[c];
+    ix.cst[lane] = a.Acp[c];
     len = a.Acp[c + 1] - a.Acp[c];
   }
   int incl = len;
@@ -254,22 +100,217 @@ __device__ void solve_column_warp(const ColArgs& a, int j, unsigned char* smem, 
     int y = __shfl_up_sync(DIAF_FULL, incl, o);
     if (lane >= o) incl += y;
   }
-  if (lane < k) coff[lane] = incl - len;
+  if (lane < k) ix.coff[lane] = incl - len;
   const int E = __shfl_sync(DIAF_FULL, incl, 31);
   __syncwarp();
   for (int e = lane; e < E; e += DIAF_WARP) {
     int q = 0;
-    while (q + 1 < k && coff[q + 1] <= e) ++q;
-    int p = cst[q] + (e - coff[q]);
-    int r = lower_bound_i32(rs, m, a.Ari[p]);
+    while (q + 1 < k && ix.coff[q + 1] <= e) ++q;
+    int p = ix.cst[q] + (e - ix.coff[q]);
+    int r = lower_bound_i32(ix.rs, m, a.Ari[p]);
     Ts[r + q * MMAX] = Av[p];
   }
   __syncwarp();
+}
 
-  // ---- I_j
-  int jpos = -1;
+// Greedy selection of s admissible rows by key hk (Sec. 3.1 with ties within
+// tau to the lower row).  Returns the smallest distance of any remaining
+// candidate's key to a pick threshold, the candidate holding the maximum
+// excluded (it passes the threshold by construction): how close a decision
+// came to flipping when the keys carry an error.
+__device__ inline double select_rows_greedy(const int32_t* rs, const double* hk, int32_t* pick, int m, int rule,
+                                            int j, int s, double tau, int lane) {
+  double margin = DBL_MAX;
+  for (int r = lane; r < m; r += DIAF_WARP) pick[r] = 0;
+  __syncwarp();
+  for (int t = 0; t < s; ++t) {
+    double hm = -DBL_MAX;
+    for (int r = lane; r < m; r += DIAF_WARP)
+      if (!pick[r] && admissible_row(rule, rs[r], j)) hm = dmax(hm, hk[r]);
+    hm = warp_max(hm);
+    int rmax = INT_MAX;
+    for (int r = lane; r < m; r += DIAF_WARP)
+      if (!pick[r] && admissible_row(rule, rs[r], j) && hk[r] == hm) rmax = dmin(rmax, r);
+    rmax = warp_min(rmax);
+    const double thr = hm - tau;
+    int best = INT_MAX;
+    for (int r = lane; r < m; r += DIAF_WARP)
+      if (!pick[r] && admissible_row(rule, rs[r], j)) {
+        if (r != rmax) margin = dmin(margin, fabs(hk[r] - thr));
+        if (hk[r] >= thr) best = dmin(best, r);
+      }
+    best = warp_min(best);
+    if (lane == 0 && best < m) pick[best] = 1;
+    __syncwarp();
+  }
+  return warp_min(margin);
+}
+
+// I_j from the picks (rule) or the fixed pattern; fills Is, Iloc, inI; returns
+// the position of j in I_j (-1 if absent).
+__device__ inline int build_I(const ColArgs& a, int j, int m, int l, const ColumnIdx& ix, int lane) {
+  if (lane == 0) ix.misc[0] = -1;
+  __syncwarp();
+  if (a.rule == DIAF_RULE_FIXED) {
+    const int32_t* Vf = a.Vfri + a.Vfcp[j];
+    for (int t = lane; t < l; t += DIAF_WARP) {
+      int row = Vf[t];
+      int r = lower_bound_i32(ix.rs, m, row);
+      int loc = (r < m && ix.rs[r] == row) ? r : -1;
+      ix.Is[t] = row;
+      ix.Iloc[t] = loc;
+      if (loc >= 0) ix.inI[loc] = t;
+      if (row == j) ix.misc[0] = t;
+    }
+    __syncwarp();
+    return ix.misc[0];
+  }
+  int cnt = 0;
+  for (int r0 = 0; r0 < m; r0 += DIAF_WARP) {
+    int r = r0 + lane;
+    bool f = r < m && (ix.pick[r] || ix.rs[r] == j);
+    unsigned b = __ballot_sync(DIAF_FULL, f);
+    if (f) {
+      int pos = cnt + __popc(b & ((1u << lane) - 1u));
+      ix.Is[pos] = ix.rs[r];
+      ix.Iloc[pos] = r;
+    }
+    cnt += __popc(b);
+  }
+  __syncwarp();
+  if (!a.jin[j]) {  // j is not a tile row: insert it (its tile row is zero)
+    if (lane == 0) {
+      int pos = 0;
+      while (pos < cnt && ix.Is[pos] < j) ++pos;
+      for (int t = cnt; t > pos; --t) { ix.Is[t] = ix.Is[t - 1]; ix.Iloc[t] = ix.Iloc[t - 1]; }
+      ix.Is[pos] = j;
+      ix.Iloc[pos] = -1;
+    }
+    __syncwarp();
+  }
+  for (int t = lane; t < l; t += DIAF_WARP) {
+    if (ix.Iloc[t] >= 0) ix.inI[ix.Iloc[t]] = t;
+    if (ix.Is[t] == j) ix.misc[0] = t;
+  }
+  __syncwarp();
+  return ix.misc[0];
+}
+
+// Phase (v_jj real >= 0, else the largest |w_q| real), residual
+// ||A_j w - v||, finiteness, and the scatter of column j.
+template <class SD, int MMAX>
+__device__ void finish_column(const ColArgs& a, int j, int k, int m, int l, int jpos, const SD* Ts, SD* wv, SD* vv,
+                              const ColumnIdx& ix, uint32_t flags, bool do_phase, int lane) {
+  using R = RealOf<SD>;
+  if (do_phase) {
+    SD ph = sc_real_s<SD>(R(1));
+    R vjj = jpos >= 0 ? sc_abs(vv[jpos]) : R(0);
+    R vn2 = R(0);
+    for (int t = 0; t < l; ++t) vn2 += sc_abs2(vv[t]);
+    // v_jj counts as zero below the rounding level of the column
+    if (jpos >= 0 && vjj > R(64) * eps_of<R>() * sqrt(vn2)) {
+      ph = (R(1) / vjj) * sc_conj(vv[jpos]);
+    } else {
+      flags |= DIAF_FLAG_VJJ_ZERO;
+      R amx = R(0);
+      int imx = -1;
+      for (int q = 0; q < k; ++q) {
+        R aq = sc_abs(wv[q]);
+        if (aq > amx) { amx = aq; imx = q; }
+      }
+      if (imx >= 0) ph = (R(1) / amx) * sc_conj(wv[imx]);
+    }
+    __syncwarp();
+    for (int q = lane; q < k; q += DIAF_WARP) wv[q] = ph * wv[q];
+    for (int t = lane; t < l; t += DIAF_WARP) vv[t] = ph * vv[t];
+    __syncwarp();
+  }
+  R r2 = R(0);
+  for (int r = lane; r < m; r += DIAF_WARP) {
+    SD s = sc_zero<SD>();
+    for (int q = 0; q < k; ++q) s += Ts[r + q * MMAX] * wv[q];
+    if (ix.inI[r] >= 0) s -= vv[ix.inI[r]];
+    r2 += sc_abs2(s);
+  }
+  for (int t = lane; t < l; t += DIAF_WARP)
+    if (ix.Iloc[t] < 0) r2 += sc_abs2(vv[t]);
+  r2 = warp_sum(r2);
+  const double resj = sqrt((double)r2);
+  bool finite = isfinite(resj);
+  for (int q = lane; q < k; q += DIAF_WARP) finite &= isfinite(sc_real(wv[q])) && isfinite(sc_imag(wv[q]));
+  for (int t = lane; t < l; t += DIAF_WARP) finite &= isfinite(sc_real(vv[t])) && isfinite(sc_imag(vv[t]));
+  finite = __all_sync(DIAF_FULL, finite);
+  if (!finite) flags |= DIAF_FLAG_NONFINITE;
+  SD* Wout = reinterpret_cast<SD*>(a.Wv) + a.Wcp[j];
+  for (int q = lane; q < k; q += DIAF_WARP) Wout[q] = wv[q];
+  const int v0 = a.Vcp[j];
+  SD* Vout = reinterpret_cast<SD*>(a.Vv) + v0;
+  for (int t = lane; t < l; t += DIAF_WARP) {
+    a.Vri[v0 + t] = ix.Is[t];
+    Vout[t] = vv[t];
+  }
+  if (lane == 0) {
+    a.res[j] = resj;
+    a.flags[j] = flags | a.extra_flags;
+  }
+  __syncwarp();
+}
+
+// Compacts rows Iloc[0..l) of the columns 0..k-1 of Tw (leading dimension LD)
+// to its top l rows (a missing row gives zeros).  Iloc is increasing, so
+// reading every value of a column before writing it is enough.
+template <class S, int LD>
+__device__ void compact_rows(S* Tw, const int32_t* Iloc, int l, int k, int lane) {
+  for (int c = 0; c < k; ++c) {
+    S tmp[LD / DIAF_WARP + 1];
+    int nn = 0;
+    for (int t = lane; t < l; t += DIAF_WARP) {
+      int r = Iloc[t];
+      tmp[nn++] = r >= 0 ? Tw[r + c * LD] : sc_zero<S>();
+    }
+    __syncwarp();
+    nn = 0;
+    for (int t = lane; t < l; t += DIAF_WARP) Tw[t + c * LD] = tmp[nn++];
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------ FP64 kernel
+template <class S, int KMAX, int MMAX>
+struct WarpLayout {
+  static constexpr int kTile = MMAX * KMAX;
+  static constexpr size_t raw() {
+    return sizeof(S) * (2 * kTile + 2 * KMAX * KMAX + 2 * KMAX + MMAX) + sizeof(double) * (MMAX + KMAX) +
+           idx_bytes<KMAX, MMAX>();
+  }
+  static constexpr size_t bytes() { return (raw() + 15) / 16 * 16; }  // keeps every warp's slice 16-byte aligned
+};
+
+template <class S, int KMAX, int MMAX, int ALG>
+__device__ void solve_column_warp(const ColArgs& a, int j, unsigned char* smem, int lane) {
+  using R = RealOf<S>;
+  using L = WarpLayout<S, KMAX, MMAX>;
+  S* Ts = reinterpret_cast<S*>(smem);  // original tile, MMAX x KMAX
+  S* Tw = Ts + L::kTile;               // working tile / Q rows / Q_I
+  S* Rs = Tw + L::kTile;               // R of T, later R-hat (KMAX x KMAX)
+  S* Vj = Rs + KMAX * KMAX;            // Jacobi V
+  S* wv = Vj + KMAX * KMAX;            // w (KMAX)
+  S* rinv = wv + KMAX;                 // reciprocal diagonal (KMAX)
+  S* vv = rinv + KMAX;                 // v (MMAX)
+  double* hk = reinterpret_cast<double*>(vv + MMAX);  // keys (MMAX)
+  double* sig = hk + MMAX;                            // singular values (KMAX)
+  ColumnIdx ix = carve_idx<KMAX, MMAX>(reinterpret_cast<int32_t*>(sig + KMAX));
+
+  const int k = a.Wcp[j + 1] - a.Wcp[j];
+  const int m = a.m[j];
+  const int l = a.l[j];
+  const int me = m > k ? m : k;  // rows of the working tile (zero padded)
+  uint32_t flags = 0;
+
+  gather_tile<S, KMAX, MMAX>(a, j, k, m, me, Ts, ix, lane);
+
+  // ---- QR of T, keys, I_j
   if (k > 0) {
-    // QR of T (copy) -> R
     for (int i = lane; i < me * k; i += DIAF_WARP) Tw[(i % me) + (i / me) * MMAX] = Ts[(i % me) + (i / me) * MMAX];
     __syncwarp();
     warp_householder_qr<S, MMAX>(Tw, me, k, lane);
@@ -279,93 +320,14 @@ __device__ void solve_column_warp(const ColArgs& a, int j, unsigned char* smem, 
     }
     __syncwarp();
   }
-  // pivot threshold for R (rank guard, 1e-14 of the largest |R_ii|)
   R rdmax = R(0);
-  for (int c = lane; c < k; c += DIAF_WARP) rdmax = dmax(rdmax, (R)sqrt(sc_abs2(Rs[c + c * KMAX])));
+  for (int c = lane; c < k; c += DIAF_WARP) rdmax = dmax(rdmax, sc_abs(Rs[c + c * KMAX]));
   rdmax = warp_max(rdmax);
   const R piv = R(1e-14) * rdmax;
-  if (k > 0 && (a.rule != DIAF_RULE_FIXED || ALG == DIAF_ALG_Q)) {
-    // Q = T R^-1 row by row (lane r owns tile row r); h_r = ||Q(r,:)||^2
-    for (int r = lane; r < m; r += DIAF_WARP) {
-      R h = R(0);
-      for (int c = 0; c < k; ++c) {
-        S acc = Ts[r + c * MMAX];
-        for (int p2 = 0; p2 < c; ++p2) acc -= Tw[r + p2 * MMAX] * Rs[p2 + c * KMAX];
-        S d = Rs[c + c * KMAX];
-        R ad2 = sc_abs2(d);
-        S z = sc_zero<S>();
-        if (sqrt(ad2) > piv) z = (R(1) / ad2) * (acc * sc_conj(d));
-        Tw[r + c * MMAX] = z;
-        h += sc_abs2(z);
-      }
-      hk[r] = (double)h;
-    }
-    __syncwarp();
-  }
-  if (a.rule == DIAF_RULE_FIXED) {
-    const int32_t* Vf = a.Vfri + a.Vfcp[j];
-    for (int t = lane; t < l; t += DIAF_WARP) {
-      int row = Vf[t];
-      int r = lower_bound_i32(rs, m, row);
-      int loc = (r < m && rs[r] == row) ? r : -1;
-      Is[t] = row;
-      Iloc[t] = loc;
-      if (loc >= 0) inI[loc] = t;
-      if (row == j) misc[0] = t;
-    }
-    if (lane == 0) {
-      bool has = false;
-      for (int t = 0; t < l; ++t) has |= (Vf[t] == j);
-      if (!has) misc[0] = -1;
-    }
-    __syncwarp();
-    jpos = misc[0];
-  } else {
-    const int s = l - 1;
-    for (int t = 0; t < s; ++t) {
-      double hm = -DBL_MAX;
-      for (int r = lane; r < m; r += DIAF_WARP)
-        if (!pick[r] && admissible_row(a.rule, rs[r], j)) hm = dmax(hm, hk[r]);
-      hm = warp_max(hm);
-      const double thr = hm - a.tie_tol;
-      int best = INT_MAX;
-      for (int r = lane; r < m; r += DIAF_WARP)
-        if (!pick[r] && admissible_row(a.rule, rs[r], j) && hk[r] >= thr) best = dmin(best, r);
-      best = warp_min(best);
-      if (lane == 0 && best < m) pick[best] = 1;
-      __syncwarp();
-    }
-    // compaction of {picked} U {j} in row order
-    int cnt = 0;
-    for (int r0 = 0; r0 < m; r0 += DIAF_WARP) {
-      int r = r0 + lane;
-      bool f = r < m && (pick[r] || rs[r] == j);
-      unsigned b = __ballot_sync(DIAF_FULL, f);
-      if (f) {
-        int pos = cnt + __popc(b & ((1u << lane) - 1u));
-        Is[pos] = rs[r];
-        Iloc[pos] = r;
-      }
-      cnt += __popc(b);
-    }
-    __syncwarp();
-    if (!a.jin[j]) {  // j is not a tile row: insert it (its tile row is zero)
-      if (lane == 0) {
-        int pos = 0;
-        while (pos < cnt && Is[pos] < j) ++pos;
-        for (int t = cnt; t > pos; --t) { Is[t] = Is[t - 1]; Iloc[t] = Iloc[t - 1]; }
-        Is[pos] = j;
-        Iloc[pos] = -1;
-      }
-      __syncwarp();
-    }
-    for (int t = lane; t < l; t += DIAF_WARP) {
-      if (Iloc[t] >= 0) inI[Iloc[t]] = t;
-      if (Is[t] == j) misc[0] = t;
-    }
-    __syncwarp();
-    jpos = misc[0];
-  }
+  if (k > 0 && (a.rule != DIAF_RULE_FIXED || ALG == DIAF_ALG_Q))
+    warp_leverage_rows<S, S, MMAX, KMAX>(Ts, Rs, Tw, hk, rinv, m, k, piv, lane);
+  if (a.rule != DIAF_RULE_FIXED) select_rows_greedy(ix.rs, hk, ix.pick, m, a.rule, j, l - 1, a.tie_tol, lane);
+  const int jpos = build_I(a, j, m, l, ix, lane);
 
   for (int t = lane; t < l; t += DIAF_WARP) vv[t] = sc_zero<S>();
   for (int q = lane; q < k; q += DIAF_WARP) wv[q] = sc_zero<S>();
@@ -384,7 +346,7 @@ __device__ void solve_column_warp(const ColArgs& a, int j, unsigned char* smem, 
     // ---- DIAF-S: QR of the tile without the I_j rows, Jacobi SVD of R-hat
     for (int i = lane; i < me * k; i += DIAF_WARP) {
       int r = i % me, c = i / me;
-      Tw[r + c * MMAX] = (r < m && inI[r] >= 0) ? sc_zero<S>() : Ts[r + c * MMAX];
+      Tw[r + c * MMAX] = (r < m && ix.inI[r] >= 0) ? sc_zero<S>() : Ts[r + c * MMAX];
     }
     __syncwarp();
     warp_householder_qr<S, MMAX>(Tw, me, k, lane);
@@ -397,131 +359,60 @@ __device__ void solve_column_warp(const ColArgs& a, int j, unsigned char* smem, 
     if (sw < 0) flags |= DIAF_FLAG_JACOBI_NOCONV;
     warp_col_norms<S, KMAX>(Rs, k, k, sig, lane);
     int imin = 0;
-    R smin = sig[0], smax = sig[0];
+    double smin = sig[0], smax = sig[0];
     for (int c = 1; c < k; ++c) {
       if (sig[c] < smin) { smin = sig[c]; imin = c; }
       smax = dmax(smax, sig[c]);
     }
-    R snext = R(INFINITY);
+    double snext = INFINITY;
     for (int c = 0; c < k; ++c) if (c != imin) snext = dmin(snext, sig[c]);
     int inrows = 0;
-    for (int t = 0; t < l; ++t) inrows += (Iloc[t] >= 0);
-    if (smin <= R(1e-14) * smax || m - inrows < k) flags |= DIAF_FLAG_RANK_DEFICIENT;
-    if (k > 1 && (snext - smin) <= R(1e-6) * smax) flags |= DIAF_FLAG_DEGENERATE;
+    for (int t = 0; t < l; ++t) inrows += (ix.Iloc[t] >= 0);
+    if (smin <= 1e-14 * smax || m - inrows < k) flags |= DIAF_FLAG_RANK_DEFICIENT;
+    if (k > 1 && (snext - smin) <= 1e-6 * smax) flags |= DIAF_FLAG_DEGENERATE;
     for (int q = lane; q < k; q += DIAF_WARP) wv[q] = Vj[q + imin * KMAX];
     __syncwarp();
     for (int t = lane; t < l; t += DIAF_WARP) {
       S s = sc_zero<S>();
-      int r = Iloc[t];
+      int r = ix.Iloc[t];
       if (r >= 0)
         for (int q = 0; q < k; ++q) s += Ts[r + q * MMAX] * wv[q];
       vv[t] = s;
     }
     __syncwarp();
   } else {
-    // ---- DIAF-Q: Q_I = rows I_j of Q (compacted in place to the top of Tw)
-    for (int c = 0; c < k; ++c) {
-      S tmp[MMAX / DIAF_WARP + 1];
-      int nn = 0;
-      for (int t = lane; t < l; t += DIAF_WARP) {
-        int r = Iloc[t];
-        tmp[nn++] = r >= 0 ? Tw[r + c * MMAX] : sc_zero<S>();
-      }
-      __syncwarp();
-      nn = 0;
-      for (int t = lane; t < l; t += DIAF_WARP) Tw[t + c * MMAX] = tmp[nn++];
-      __syncwarp();
-    }
+    // ---- DIAF-Q: Q_I = rows I_j of Q (compacted to the top of Tw)
+    compact_rows<S, MMAX>(Tw, ix.Iloc, l, k, lane);
     int sw = warp_jacobi<S, MMAX, KMAX, KMAX>(Tw, l, k, Vj, lane);
     if (sw < 0) flags |= DIAF_FLAG_JACOBI_NOCONV;
     warp_col_norms<S, MMAX>(Tw, l, k, sig, lane);
     int imax = 0;
-    R smax = sig[0];
+    double smax = sig[0];
     for (int c = 1; c < k; ++c) if (sig[c] > smax) { smax = sig[c]; imax = c; }
-    R snext = R(0);
+    double snext = 0.0;
     for (int c = 0; c < k; ++c) if (c != imax) snext = dmax(snext, sig[c]);
-    if (smax == R(0) || (k > 1 && (smax - snext) <= R(1e-6) * smax)) flags |= DIAF_FLAG_DEGENERATE;
-    if (smax > R(0)) {
-      for (int t = lane; t < l; t += DIAF_WARP) vv[t] = (R(1) / smax) * Tw[t + imax * MMAX];
+    if (smax == 0.0 || (k > 1 && (smax - snext) <= 1e-6 * smax)) flags |= DIAF_FLAG_DEGENERATE;
+    if (smax > 0.0) {
+      const R inv = R(1) / R(smax);
+      for (int t = lane; t < l; t += DIAF_WARP) vv[t] = inv * Tw[t + imax * MMAX];
     } else if (lane == 0) {
       vv[jpos >= 0 ? jpos : 0] = sc_real_s<S>(R(1));
     }
-    __syncwarp();
-    // w = sigma R^-1 u  (R w = Q^* v, eq. condwj)
-    if (lane == 0) {
-      bool rd = false;
-      for (int c = k - 1; c >= 0; --c) {
-        S s = smax * Vj[c + imax * KMAX];
-        for (int t = c + 1; t < k; ++t) s -= Rs[c + t * KMAX] * wv[t];
-        S d = Rs[c + c * KMAX];
-        R ad2 = sc_abs2(d);
-        if (sqrt(ad2) <= piv) { rd = true; wv[c] = sc_zero<S>(); }
-        else wv[c] = (R(1) / ad2) * (s * sc_conj(d));
-      }
-      if (rd) misc[1] = 1; else misc[1] = 0;
+    // w = sigma R^-1 u  (R w = Q^* v, eq. condwj); rinv holds R's reciprocal diagonal
+    bool rd = false;
+    for (int c = lane; c < k; c += DIAF_WARP) rd |= !(sc_abs(Rs[c + c * KMAX]) > piv);
+    rd = __any_sync(DIAF_FULL, rd);
+    if (rd) flags |= DIAF_FLAG_RANK_DEFICIENT;
+    S x = lane < k ? R(smax) * Vj[lane + imax * KMAX] : sc_zero<S>();
+    for (int c = k - 1; c >= 0; --c) {
+      S yc = shfl_idx(x * rinv[c], c);
+      if (lane < c) x -= Rs[lane + c * KMAX] * yc;
+      if (lane == c) x = yc;
     }
-    __syncwarp();
-    if (misc[1]) flags |= DIAF_FLAG_RANK_DEFICIENT;
-  }
-
-  // ---- phase: v_jj real and >= 0
-  if (k > 0 || ALG == DIAF_ALG_Q) {
-    S ph = sc_real_s<S>(R(1));
-    R vjj = jpos >= 0 ? (R)sqrt(sc_abs2(vv[jpos])) : R(0);
-    R vn2 = R(0);
-    for (int t = 0; t < l; ++t) vn2 += sc_abs2(vv[t]);
-    // v_jj counts as zero below the rounding level of the column
-    if (jpos >= 0 && vjj > R(64) * eps_of<R>() * sqrt(vn2)) {
-      ph = (R(1) / vjj) * sc_conj(vv[jpos]);
-    } else {
-      flags |= DIAF_FLAG_VJJ_ZERO;
-      R amx = R(0);
-      int imx = -1;
-      for (int q = 0; q < k; ++q) {
-        R aq = sqrt(sc_abs2(wv[q]));
-        if (aq > amx) { amx = aq; imx = q; }
-      }
-      if (imx >= 0) ph = (R(1) / amx) * sc_conj(wv[imx]);
-    }
-    __syncwarp();
-    for (int q = lane; q < k; q += DIAF_WARP) wv[q] = ph * wv[q];
-    for (int t = lane; t < l; t += DIAF_WARP) vv[t] = ph * vv[t];
+    if (lane < k) wv[lane] = x;
     __syncwarp();
   }
-
-  // ---- residual ||A_j w - v||
-  R r2 = R(0);
-  for (int r = lane; r < m; r += DIAF_WARP) {
-    S s = sc_zero<S>();
-    for (int q = 0; q < k; ++q) s += Ts[r + q * MMAX] * wv[q];
-    if (inI[r] >= 0) s -= vv[inI[r]];
-    r2 += sc_abs2(s);
-  }
-  for (int t = lane; t < l; t += DIAF_WARP)
-    if (Iloc[t] < 0) r2 += sc_abs2(vv[t]);
-  r2 = warp_sum(r2);
-  const double resj = sqrt((double)r2);
-
-  bool finite = isfinite(resj);
-  for (int q = lane; q < k; q += DIAF_WARP) finite &= isfinite(sc_real(wv[q])) && isfinite(sc_imag(wv[q]));
-  for (int t = lane; t < l; t += DIAF_WARP) finite &= isfinite(sc_real(vv[t])) && isfinite(sc_imag(vv[t]));
-  finite = __all_sync(DIAF_FULL, finite);
-  if (!finite) flags |= DIAF_FLAG_NONFINITE;
-
-  // ---- scatter
-  S* Wout = reinterpret_cast<S*>(a.Wv) + a.Wcp[j];
-  for (int q = lane; q < k; q += DIAF_WARP) Wout[q] = wv[q];
-  const int v0 = a.Vcp[j];
-  S* Vout = reinterpret_cast<S*>(a.Vv) + v0;
-  for (int t = lane; t < l; t += DIAF_WARP) {
-    a.Vri[v0 + t] = Is[t];
-    Vout[t] = vv[t];
-  }
-  if (lane == 0) {
-    a.res[j] = resj;
-    a.flags[j] = flags;
-  }
-  __syncwarp();
+  finish_column<S, MMAX>(a, j, k, m, l, jpos, Ts, wv, vv, ix, flags, k > 0 || ALG == DIAF_ALG_Q, lane);
 }
 
 template <class S, int KMAX, int MMAX, int ALG>

@@ -1,0 +1,275 @@
+// Mixed-precision per-column kernel: the tile is gathered in FP64 (complex128)
+// and copied to FP32 (complex64); QR, leverage keys and the Jacobi SVD run in
+// FP32; then (w_j, v_j) get one FP64 refinement step against the FP64 tile
+// and the residual ||A w - v|| is evaluated in FP64.
+//
+//   DIAF-S: w0 = FP32 smallest right singular vector of R-hat; one step of
+//     inverse iteration on A-hat^* A-hat in FP64 with the FP32 R-hat as the
+//     solver (y = M w0, y += M (w0 - A-hat^*(A-hat y)), M = R-hat^-1 R-hat^-*),
+//     w = y / ||y||; v = T(I_j,:) w.
+//   DIAF-Q: v0 = Q_I u / sigma from the FP32 Jacobi; w = the least-squares
+//     solution of eq. condwj for v0 in FP64 (normal equations with the FP32 R
+//     as the solver plus one correction); one power step v1 = T(I_j,:) w /
+//     ||.|| (v1 is C v0 normalised, C = T_I (T^* T)^-1 T_I^*, whose top
+//     eigenvector is the optimal v of eq. nocond), and w again for v1.
+//
+// A column goes to the FP64 kernel instead (appended to fb_list) when a
+// leverage-selection decision is closer to its threshold than the FP32 key
+// error bound (so I_j could differ from the FP64 choice), or when the tile is
+// too ill-conditioned for FP32 factors to drive the refinement.
+#pragma once
+
+#include "column.cuh"
+
+template <class S> struct DoubleOf;
+template <> struct DoubleOf<float> { using T = double; };
+template <> struct DoubleOf<Cx<float>> { using T = Cx<double>; };
+
+// Column-scaled conditioning estimate of an upper R whose columns came from a
+// tile with column norms cn: max_c cn_c / |R_cc| (1 for orthogonal columns).
+constexpr float kMixedKappaMax = 300.0f;
+
+template <class S, int KMAX, int MMAX>
+struct MixedLayout {
+  using SD = typename DoubleOf<S>::T;
+  static constexpr int kTile = MMAX * KMAX;
+  static constexpr size_t raw() {
+    return sizeof(SD) * (kTile + 3 * KMAX + 2 * MMAX) + sizeof(S) * (kTile + 3 * KMAX * KMAX + KMAX) +
+           sizeof(double) * (MMAX + 2 * KMAX) + idx_bytes<KMAX, MMAX>();
+  }
+  static constexpr size_t bytes() { return (raw() + 15) / 16 * 16; }
+};
+
+template <class S, int KMAX, int MMAX, int ALG>
+__device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem, int lane) {
+  using SD = typename DoubleOf<S>::T;
+  using R = RealOf<S>;
+  using L = MixedLayout<S, KMAX, MMAX>;
+  SD* Ts = reinterpret_cast<SD*>(smem);  // FP64 tile (MMAX x KMAX)
+  SD* rinvD = Ts + L::kTile;             // FP64 reciprocal diagonal of the FP32 factor
+  SD* wv = rinvD + KMAX;                 // w
+  SD* gg = wv + KMAX;                    // k-vector scratch
+  SD* vv = gg + KMAX;                    // v (MMAX)
+  SD* zz = vv + MMAX;                    // m-vector scratch
+  S* Tw = reinterpret_cast<S*>(zz + MMAX);  // FP32 working tile
+  S* Rs = Tw + L::kTile;                 // FP32 R of T, then R-hat (Jacobi works on it)
+  S* Rr = Rs + KMAX * KMAX;              // FP32 R-hat kept for the refinement
+  S* Vj = Rr + KMAX * KMAX;              // FP32 Jacobi V
+  S* rinv = Vj + KMAX * KMAX;            // FP32 reciprocal diagonal
+  double* hk = reinterpret_cast<double*>(rinv + KMAX);
+  double* sig = hk + MMAX;
+  double* cn = sig + KMAX;               // column norms of the tile
+  ColumnIdx ix = carve_idx<KMAX, MMAX>(reinterpret_cast<int32_t*>(cn + KMAX));
+
+  const int k = a.Wcp[j + 1] - a.Wcp[j];
+  const int m = a.m[j];
+  const int l = a.l[j];
+  const int me = m > k ? m : k;
+  uint32_t flags = 0;
+
+  auto hand_back = [&]() {
+    if (lane == 0) {
+      int pos = atomicAdd(a.fb_count, 1);
+      a.fb_list[pos] = j;
+    }
+    __syncwarp();
+  };
+  if (k == 0) {  // trivial columns: the FP64 kernel has the conventions
+    hand_back();
+    return;
+  }
+
+  gather_tile<SD, KMAX, MMAX>(a, j, k, m, me, Ts, ix, lane);
+
+  // ---- FP32 QR of T and the keys
+  for (int i = lane; i < me * k; i += DIAF_WARP) {
+    int r = i % me, c = i / me;
+    Tw[r + c * MMAX] = sc_cast<S>(Ts[r + c * MMAX]);
+  }
+  for (int c = lane; c < k; c += DIAF_WARP) {
+    double s = 0.0;
+    for (int r = 0; r < m; ++r) s += (double)sc_abs2(Ts[r + c * MMAX]);
+    cn[c] = sqrt(s);
+  }
+  __syncwarp();
+  warp_householder_qr<S, MMAX>(Tw, me, k, lane);
+  for (int i = lane; i < k * k; i += DIAF_WARP) {
+    int r = i % k, c = i / k;
+    Rs[r + c * KMAX] = (r <= c) ? Tw[r + c * MMAX] : sc_zero<S>();
+  }
+  __syncwarp();
+  float kap = 0.0f;
+  for (int c = lane; c < k; c += DIAF_WARP) {
+    float d = (float)sc_abs(Rs[c + c * KMAX]);
+    kap = fmaxf(kap, d > 0.0f ? (float)cn[c] / d : INFINITY);
+  }
+  kap = warp_max(kap);
+  if (!(kap <= kMixedKappaMax)) { hand_back(); return; }
+  warp_leverage_rows<S, SD, MMAX, KMAX>(Ts, Rs, Tw, hk, rinv, m, k, R(0), lane);
+  if (a.rule != DIAF_RULE_FIXED) {
+    const double margin = select_rows_greedy(ix.rs, hk, ix.pick, m, a.rule, j, l - 1, a.tie_tol, lane);
+    // bound on the FP32 key error: backward error of the FP32 QR and of the
+    // row solves, amplified by the (column-scaled) conditioning of T
+    const double delta = 8.0 * (m + k) * (double)FLT_EPSILON * (double)kap;
+    if (l > 1 && margin <= 2.0 * delta) { hand_back(); return; }
+  }
+  const int jpos = build_I(a, j, m, l, ix, lane);
+  for (int t = lane; t < l; t += DIAF_WARP) vv[t] = sc_zero<SD>();
+  __syncwarp();
+
+  if (ALG == DIAF_ALG_S) {
+    // ---- FP32 QR of A-hat (I_j rows zeroed) and Jacobi SVD of R-hat
+    for (int i = lane; i < me * k; i += DIAF_WARP) {
+      int r = i % me, c = i / me;
+      Tw[r + c * MMAX] = (r < m && ix.inI[r] >= 0) ? sc_zero<S>() : sc_cast<S>(Ts[r + c * MMAX]);
+    }
+    for (int c = lane; c < k; c += DIAF_WARP) {
+      double s = 0.0;
+      for (int r = 0; r < m; ++r)
+        if (ix.inI[r] < 0) s += (double)sc_abs2(Ts[r + c * MMAX]);
+      cn[c] = sqrt(s);
+    }
+    __syncwarp();
+    warp_householder_qr<S, MMAX>(Tw, me, k, lane);
+    for (int i = lane; i < k * k; i += DIAF_WARP) {
+      int r = i % k, c = i / k;
+      S x = (r <= c) ? Tw[r + c * MMAX] : sc_zero<S>();
+      Rs[r + c * KMAX] = x;
+      Rr[r + c * KMAX] = x;
+    }
+    __syncwarp();
+    float kh = 0.0f;
+    for (int c = lane; c < k; c += DIAF_WARP) {
+      float d = (float)sc_abs(Rr[c + c * KMAX]);
+      kh = fmaxf(kh, d > 0.0f ? (float)cn[c] / d : INFINITY);
+    }
+    kh = warp_max(kh);
+    if (!(kh <= kMixedKappaMax)) { hand_back(); return; }
+    int sw = warp_jacobi<S, KMAX, KMAX, KMAX>(Rs, k, k, Vj, lane);
+    if (sw < 0) flags |= DIAF_FLAG_JACOBI_NOCONV;
+    warp_col_norms<S, KMAX>(Rs, k, k, sig, lane);
+    int imin = 0;
+    double smin = sig[0], smax = sig[0];
+    for (int c = 1; c < k; ++c) {
+      if (sig[c] < smin) { smin = sig[c]; imin = c; }
+      smax = dmax(smax, sig[c]);
+    }
+    double snext = INFINITY;
+    for (int c = 0; c < k; ++c) if (c != imin) snext = dmin(snext, sig[c]);
+    if (k > 1 && (snext - smin) <= 1e-6 * smax) flags |= DIAF_FLAG_DEGENERATE;
+    // ---- FP64 refinement: one step of inverse iteration on A-hat^* A-hat
+    for (int c = lane; c < k; c += DIAF_WARP) rinvD[c] = sc_recip_or_zero(sc_cast<SD>(Rr[c + c * KMAX]), 0.0);
+    __syncwarp();
+    const SD w0 = lane < k ? sc_cast<SD>(Vj[lane + imin * KMAX]) : sc_zero<SD>();
+    SD y = warp_solve_RhR<SD, S, KMAX>(Rr, rinvD, w0, k, lane);
+    if (lane < k) gg[lane] = y;
+    __syncwarp();
+    for (int r = lane; r < m; r += DIAF_WARP) {
+      SD z = sc_zero<SD>();
+      if (ix.inI[r] < 0)
+        for (int q = 0; q < k; ++q) z += Ts[r + q * MMAX] * gg[q];
+      zz[r] = z;
+    }
+    __syncwarp();
+    SD g = sc_zero<SD>();
+    if (lane < k)
+      for (int r = 0; r < m; ++r) g += sc_cmul(Ts[r + lane * MMAX], zz[r]);
+    y += warp_solve_RhR<SD, S, KMAX>(Rr, rinvD, w0 - g, k, lane);
+    double yn2 = warp_sum(lane < k ? (double)sc_abs2(y) : 0.0);
+    const double inv = 1.0 / sqrt(yn2);
+    if (lane < k) wv[lane] = inv * y;
+    __syncwarp();
+    // v = T(I_j,:) w and the rank test on the FP64 value of ||A-hat w||
+    for (int t = lane; t < l; t += DIAF_WARP) {
+      SD s = sc_zero<SD>();
+      int r = ix.Iloc[t];
+      if (r >= 0)
+        for (int q = 0; q < k; ++q) s += Ts[r + q * MMAX] * wv[q];
+      vv[t] = s;
+    }
+    double r2 = 0.0;
+    for (int r = lane; r < m; r += DIAF_WARP)
+      if (ix.inI[r] < 0) {
+        SD s = sc_zero<SD>();
+        for (int q = 0; q < k; ++q) s += Ts[r + q * MMAX] * wv[q];
+        r2 += (double)sc_abs2(s);
+      }
+    r2 = warp_sum(r2);
+    if (sqrt(r2) <= 1e-14 * smax) flags |= DIAF_FLAG_RANK_DEFICIENT;
+    __syncwarp();
+  } else {
+    // ---- FP32 Jacobi on Q_I (FP32 rows of Q = T R^-1 in Tw)
+    compact_rows<S, MMAX>(Tw, ix.Iloc, l, k, lane);
+    int sw = warp_jacobi<S, MMAX, KMAX, KMAX>(Tw, l, k, Vj, lane);
+    if (sw < 0) flags |= DIAF_FLAG_JACOBI_NOCONV;
+    warp_col_norms<S, MMAX>(Tw, l, k, sig, lane);
+    int imax = 0;
+    double smax = sig[0];
+    for (int c = 1; c < k; ++c) if (sig[c] > smax) { smax = sig[c]; imax = c; }
+    double snext = 0.0;
+    for (int c = 0; c < k; ++c) if (c != imax) snext = dmax(snext, sig[c]);
+    if (!(smax > 0.0)) { hand_back(); return; }
+    if (k > 1 && (smax - snext) <= 1e-6 * smax) flags |= DIAF_FLAG_DEGENERATE;
+    for (int t = lane; t < l; t += DIAF_WARP) vv[t] = sc_cast<SD>(Tw[t + imax * MMAX]);
+    for (int c = lane; c < k; c += DIAF_WARP) rinvD[c] = sc_recip_or_zero(sc_cast<SD>(Rs[c + c * KMAX]), 0.0);
+    __syncwarp();
+    // two rounds: least squares for v, then the power step v <- T_I w / ||T_I w||
+    for (int round = 0; round < 2; ++round) {
+      double vn2 = 0.0;
+      for (int t = lane; t < l; t += DIAF_WARP) vn2 += (double)sc_abs2(vv[t]);
+      vn2 = warp_sum(vn2);
+      const double vinv = 1.0 / sqrt(vn2);
+      for (int t = lane; t < l; t += DIAF_WARP) vv[t] = vinv * vv[t];
+      __syncwarp();
+      // g0 = T_I^* v
+      SD g0 = sc_zero<SD>();
+      if (lane < k)
+        for (int t = 0; t < l; ++t) {
+          int r = ix.Iloc[t];
+          if (r >= 0) g0 += sc_cmul(Ts[r + lane * MMAX], vv[t]);
+        }
+      SD w = warp_solve_RhR<SD, S, KMAX>(Rs, rinvD, g0, k, lane);
+      // correction with the FP64 normal-equation residual T^* (v - T w)
+      if (lane < k) gg[lane] = w;
+      __syncwarp();
+      for (int r = lane; r < m; r += DIAF_WARP) {
+        SD z = ix.inI[r] >= 0 ? vv[ix.inI[r]] : sc_zero<SD>();
+        for (int q = 0; q < k; ++q) z -= Ts[r + q * MMAX] * gg[q];
+        zz[r] = z;
+      }
+      __syncwarp();
+      SD rn = sc_zero<SD>();
+      if (lane < k)
+        for (int r = 0; r < m; ++r) rn += sc_cmul(Ts[r + lane * MMAX], zz[r]);
+      w += warp_solve_RhR<SD, S, KMAX>(Rs, rinvD, rn, k, lane);
+      if (lane < k) wv[lane] = w;
+      __syncwarp();
+      if (round == 0) {
+        for (int t = lane; t < l; t += DIAF_WARP) {
+          SD s = sc_zero<SD>();
+          int r = ix.Iloc[t];
+          if (r >= 0)
+            for (int q = 0; q < k; ++q) s += Ts[r + q * MMAX] * wv[q];
+          vv[t] = s;
+        }
+        __syncwarp();
+      }
+    }
+  }
+  finish_column<SD, MMAX>(a, j, k, m, l, jpos, Ts, wv, vv, ix, flags, true, lane);
+}
+
+template <class S, int KMAX, int MMAX, int ALG>
+__global__ void column_mixed_kernel(ColArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char* smem = smem_raw + warp * MixedLayout<S, KMAX, MMAX>::bytes();
+  const int count = *a.list_count;
+  while (true) {
+    int idx = 0;
+    if (lane == 0) idx = atomicAdd(a.work_counter, 1);
+    idx = __shfl_sync(DIAF_FULL, idx, 0);
+    if (idx >= count) break;
+    solve_column_mixed<S, KMAX, MMAX, ALG>(a, a.list[idx], smem, lane);
+  }
+}

@@ -26,6 +26,7 @@ struct diaf_factors {
   static constexpr int kEvents = 3 + 2 * kNumBuckets;
   cudaEvent_t ev[kEvents] = {};
   bool bucket_ran[kNumBuckets] = {};
+  int32_t* fb_counts = nullptr;  // mixed precision: columns per bucket finished by the FP64 kernel
   // apply
   bool apply_ready = false;
   bool v_upper = true;

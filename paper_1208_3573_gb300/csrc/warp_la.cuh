@@ -1,0 +1,251 @@
+// Warp-cooperative dense linear algebra on small tiles in shared memory
+// (column-major), shared by the FP64 and the mixed-precision column kernels:
+// Householder QR, one-sided Jacobi SVD, leverage rows Q = T R^-1, and the
+// two triangular solves with R^* and R.
+//
+// Cost model on GB300: FP64 warp instructions are the scarce resource, so the
+// routines avoid divisions and square roots inside loops (reciprocals are
+// formed once) and use |x| / sign(x) directly for real data.
+#pragma once
+
+#include <cfloat>
+#include <climits>
+#include <type_traits>
+
+#include "common.cuh"
+
+constexpr int kMaxSweeps = 30;
+
+template <class T> __device__ __forceinline__ T eps_of();
+template <> __device__ __forceinline__ double eps_of<double>() { return DBL_EPSILON; }
+template <> __device__ __forceinline__ float eps_of<float>() { return FLT_EPSILON; }
+
+__device__ __forceinline__ double sc_abs(double a) { return fabs(a); }
+__device__ __forceinline__ float sc_abs(float a) { return fabsf(a); }
+template <class R> __device__ __forceinline__ R sc_abs(Cx<R> a) { return sqrt(sc_abs2(a)); }
+
+__device__ __forceinline__ double rsqrt_r(double a) { return rsqrt(a); }
+__device__ __forceinline__ float rsqrt_r(float a) { return rsqrtf(a); }
+
+// a / |a| (1 for a == 0)
+__device__ __forceinline__ double sc_unit(double a) { return a < 0.0 ? -1.0 : 1.0; }
+__device__ __forceinline__ float sc_unit(float a) { return a < 0.0f ? -1.0f : 1.0f; }
+template <class R> __device__ __forceinline__ Cx<R> sc_unit(Cx<R> a) {
+  R n2 = sc_abs2(a);
+  if (n2 == R(0)) return {R(1), R(0)};
+  R inv = rsqrt_r(n2);
+  return {a.re * inv, a.im * inv};
+}
+
+// 1 / d for a nonzero scalar, 0 when |d| <= piv
+template <class S>
+__device__ __forceinline__ S sc_recip_or_zero(S d, RealOf<S> piv) {
+  using R = RealOf<S>;
+  R a2 = sc_abs2(d);
+  if (!(sc_abs(d) > piv)) return sc_zero<S>();
+  return (R(1) / a2) * sc_conj(d);
+}
+
+__device__ __forceinline__ bool admissible_row(int rule, int i, int j) {
+  if (i == j) return false;
+  if (rule == DIAF_RULE_UPPER) return i < j;
+  if (rule == DIAF_RULE_LOWER) return i > j;
+  return true;
+}
+
+// ------------------------------------------------------------------ QR
+// Householder QR of the column-major m x k matrix T (leading dimension LD)
+// in place: reflector c maps x = T(c:m, c) to beta e_1 with
+// beta = -(x_0/|x_0|) ||x||, u = x - beta e_1, u^* u = 2 ||x|| (||x|| + |x_0|).
+// On return rows 0..min(m,k)-1 hold R (zeros below the diagonal).
+template <class S, int LD>
+__device__ void warp_householder_qr(S* T, int m, int k, int lane) {
+  using R = RealOf<S>;
+  int p = m < k ? m : k;
+  for (int c = 0; c < p; ++c) {
+    S* tc = T + c * LD;
+    R nrm2 = R(0);
+    for (int r = c + lane; r < m; r += DIAF_WARP) nrm2 += sc_abs2(tc[r]);
+    nrm2 = warp_sum(nrm2);
+    S alpha = tc[c];
+    __syncwarp();
+    if (nrm2 == R(0)) continue;
+    R ax = sc_abs(alpha);
+    R nrm = sqrt(nrm2);
+    S ph = sc_unit(alpha);
+    S beta = -(nrm * ph);
+    S u0 = (ax + nrm) * ph;
+    R two_uu = R(1) / (nrm * (nrm + ax));
+    for (int q = c + 1; q < k; ++q) {
+      S* tq = T + q * LD;
+      S part = sc_zero<S>();
+      for (int r = c + lane; r < m; r += DIAF_WARP) part += sc_cmul(r == c ? u0 : tc[r], tq[r]);
+      S f = two_uu * warp_sum(part);
+      for (int r = c + lane; r < m; r += DIAF_WARP) tq[r] -= f * (r == c ? u0 : tc[r]);
+    }
+    __syncwarp();
+    for (int r = c + lane; r < m; r += DIAF_WARP) tc[r] = (r == c) ? beta : sc_zero<S>();
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------ Jacobi
+// Parallel one-sided (Hestenes) Jacobi on the p x q matrix G (leading
+// dimension LDG): G V has orthogonal columns, V (q x q, leading dimension
+// LDV) unitary.  Round-robin ordering: in each of the qq-1 rounds of a sweep
+// (qq = q rounded up to even) the columns split into qq/2 disjoint pairs, one
+// group of LPP lanes per pair.  A pair (a, b) with alpha = |g_a|^2,
+// beta = |g_b|^2, gamma = g_a^* g_b is rotated when |gamma| > tol
+// sqrt(alpha beta), tol = p eps, and neither column is below p eps ||G||_F:
+// b' = e^{-i arg gamma} b, then [a b'] [[c, s], [-s, c]] with t = s / c the
+// smaller root of t^2 + 2 zeta t - 1 = 0, zeta = (beta - alpha) / (2|gamma|),
+// i.e. t = sign(d) 2|gamma| / (|d| + sqrt(d^2 + 4|gamma|^2)), d = beta - alpha.
+// Returns sweeps used, or -1 at the sweep limit.
+template <class S, int LDG, int LDV, int QMAX>
+__device__ int warp_jacobi(S* G, int p, int q, S* V, int lane) {
+  using R = RealOf<S>;
+  constexpr int kPairsMax = QMAX / 2;
+  constexpr int kGroups = kPairsMax >= 32 ? 32 : (kPairsMax >= 16 ? 16 : (kPairsMax >= 8 ? 8 : (kPairsMax >= 4 ? 4 : 2)));
+  constexpr int LPP = DIAF_WARP / kGroups;
+  for (int i = lane; i < q * q; i += DIAF_WARP) {
+    int r = i % q, c = i / q;
+    V[r + c * LDV] = (r == c) ? sc_real_s<S>(R(1)) : sc_zero<S>();
+  }
+  R nf2 = R(0);
+  for (int i = lane; i < p * q; i += DIAF_WARP) nf2 += sc_abs2(G[(i % p) + (i / p) * LDG]);
+  nf2 = warp_sum(nf2);
+  const R tol = R(p > 1 ? p : 1) * eps_of<R>();
+  const R tol2 = tol * tol;
+  const R tiny = tol2 * nf2;
+  __syncwarp();
+  if (q < 2) return 1;
+  const int qq = (q + 1) & ~1;
+  const int npairs = qq / 2;
+  const int grp = lane / LPP, sub = lane % LPP;
+  for (int sweep = 1; sweep <= kMaxSweeps; ++sweep) {
+    bool rotated = false;
+    for (int rnd = 0; rnd < qq - 1; ++rnd) {
+      for (int pr0 = 0; pr0 < npairs; pr0 += kGroups) {
+        int pr = pr0 + grp;
+        int a = -1, b = -1;
+        if (pr < npairs) {
+          int pa = pr, pb = qq - 1 - pr;
+          a = pa == 0 ? 0 : 1 + (pa - 1 + rnd) % (qq - 1);
+          b = 1 + (pb - 1 + rnd) % (qq - 1);
+          if (a > b) { int t = a; a = b; b = t; }
+          if (b >= q) a = -1;  // bye for the padding column
+        }
+        bool act = a >= 0;
+        R al = R(0), be = R(0);
+        S ga = sc_zero<S>();
+        if (act) {
+          const S* ca = G + a * LDG;
+          const S* cb = G + b * LDG;
+          for (int i = sub; i < p; i += LPP) {
+            S x = ca[i], y = cb[i];
+            al += sc_abs2(x);
+            be += sc_abs2(y);
+            ga += sc_cmul(x, y);
+          }
+        }
+        al = group_sum<LPP>(al);
+        be = group_sum<LPP>(be);
+        ga = group_sum<LPP>(ga);
+        const R ag2 = sc_abs2(ga);
+        bool rot = act && al > tiny && be > tiny && ag2 > R(0) && ag2 > tol2 * (al * be);
+        if (rot) {
+          rotated = true;
+          R ag;
+          S eph;
+          if constexpr (ScalarInfo<S>::cplx) {
+            R rinv = rsqrt_r(ag2);
+            ag = ag2 * rinv;
+            eph = rinv * sc_conj(ga);
+          } else {
+            ag = sc_abs(ga);
+            eph = sc_unit(ga);
+          }
+          const R d = be - al;
+          const R t = copysign(R(2) * ag, d) / (fabs(d) + sqrt(d * d + R(4) * ag2));
+          const R cs = rsqrt_r(R(1) + t * t), sn = cs * t;
+          S* ca = G + a * LDG;
+          S* cb = G + b * LDG;
+          for (int i = sub; i < p; i += LPP) {
+            S x = ca[i], y = eph * cb[i];
+            ca[i] = cs * x - sn * y;
+            cb[i] = sn * x + cs * y;
+          }
+          S* va = V + a * LDV;
+          S* vb = V + b * LDV;
+          for (int i = sub; i < q; i += LPP) {
+            S x = va[i], y = eph * vb[i];
+            va[i] = cs * x - sn * y;
+            vb[i] = sn * x + cs * y;
+          }
+        }
+        __syncwarp();
+      }
+    }
+    if (!__any_sync(DIAF_FULL, rotated)) return sweep;
+  }
+  return -1;
+}
+
+// column norms of G (p x q) into sigma[c] (double)
+template <class S, int LDG>
+__device__ void warp_col_norms(const S* G, int p, int q, double* sigma, int lane) {
+  using R = RealOf<S>;
+  for (int c = lane; c < q; c += DIAF_WARP) {
+    R s = R(0);
+    for (int i = 0; i < p; ++i) s += sc_abs2(G[i + c * LDG]);
+    sigma[c] = sqrt((double)s);
+  }
+  __syncwarp();
+}
+
+// ------------------------------------------------------------------ leverage
+// Q = T R^-1 row by row (lane r owns tile row r) and h_r = ||Q(r,:)||^2.
+// T: tile of type ST (leading dimension LDT), Rm: k x k upper R (type S,
+// leading dimension LDR), Qout: rows of Q (type S, leading dimension LDT),
+// rinv: KMAX scratch for the reciprocal diagonal (pivots below piv give 0).
+template <class S, class ST, int LDT, int LDR>
+__device__ void warp_leverage_rows(const ST* T, const S* Rm, S* Qout, double* hk, S* rinv, int m, int k,
+                                   RealOf<S> piv, int lane) {
+  using R = RealOf<S>;
+  for (int c = lane; c < k; c += DIAF_WARP) rinv[c] = sc_recip_or_zero(Rm[c + c * LDR], piv);
+  __syncwarp();
+  for (int r = lane; r < m; r += DIAF_WARP) {
+    R h = R(0);
+    for (int c = 0; c < k; ++c) {
+      S acc = sc_cast<S>(T[r + c * LDT]);
+      for (int p2 = 0; p2 < c; ++p2) acc -= Qout[r + p2 * LDT] * Rm[p2 + c * LDR];
+      S z = acc * rinv[c];
+      Qout[r + c * LDT] = z;
+      h += sc_abs2(z);
+    }
+    hk[r] = (double)h;
+  }
+  __syncwarp();
+}
+
+// ------------------------------------------------------------------ triangular solves
+// x := R^-1 R^-* x for the k x k upper triangular R (type S, leading dimension
+// LDR), in precision SD.  x is held one entry per lane (lane q < k owns x_q);
+// rinv: the reciprocal diagonal in SD (lane c reads rinv[c]).  Returns the
+// lane's entry.
+template <class SD, class S, int LDR>
+__device__ SD warp_solve_RhR(const S* Rm, const SD* rinv, SD x, int k, int lane) {
+  // forward: R^* u = x  (u_c = (x_c - sum_{p<c} conj(R_pc) u_p) / conj(R_cc))
+  for (int c = 0; c < k; ++c) {
+    SD uc = shfl_idx(x * sc_conj(rinv[c]), c);
+    if (lane > c && lane < k) x -= sc_conj(sc_cast<SD>(Rm[c + lane * LDR])) * uc;
+    if (lane == c) x = uc;
+  }
+  // backward: R y = u
+  for (int c = k - 1; c >= 0; --c) {
+    SD yc = shfl_idx(x * rinv[c], c);
+    if (lane < c) x -= sc_cast<SD>(Rm[lane + c * LDR]) * yc;
+    if (lane == c) x = yc;
+  }
+  return x;
+}

@@ -22,7 +22,7 @@ ALG = {"Q": 1, "S": 2}
 PREC = {"fp64": 0, "mixed32": 1}
 RULE_FIXED, RULE_UPPER, RULE_LOWER, RULE_ALL = 0, 1, 2, 3
 FLAG_RANK_DEFICIENT, FLAG_DEGENERATE, FLAG_VJJ_ZERO, FLAG_JACOBI_NOCONV = 1, 2, 4, 8
-FLAG_NONFINITE, FLAG_EMPTY, FLAG_REFINED_KEYS = 16, 32, 64
+FLAG_NONFINITE, FLAG_EMPTY, FLAG_FP64_FALLBACK = 16, 32, 64
 
 
 class DiafError(RuntimeError):
@@ -85,6 +85,7 @@ def lib() -> ctypes.CDLL:
         L.diaf_bicgstab.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_int32, vp, ctypes.POINTER(SolveInfo_t)]
         L.diaf_factor_timings.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]
         L.diaf_launch_count.restype = ctypes.c_longlong
+        L.diaf_factor_fallbacks.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]
         L.diaf_status_string.argtypes = [ctypes.c_int]
         L.diaf_status_string.restype = ctypes.c_char_p
         L.diaf_last_error.restype = ctypes.c_char_p
@@ -219,6 +220,12 @@ class Factors:
         nb = self.info.n_buckets
         return {"total_ms": buf[0], "numeric_ms": buf[1], "bucket_ms": [buf[2 + b] for b in range(nb)],
                 "bucket_cols": [self.info.bucket_cols[b] for b in range(nb)]}
+
+    def fallbacks(self) -> list:
+        """Mixed precision: columns per bucket computed by the FP64 path."""
+        buf = (ctypes.c_int32 * 8)()
+        _check(lib().diaf_factor_fallbacks(self._own.ptr, buf, 8))
+        return [buf[b] for b in range(self.info.n_buckets)]
 
     def apply(self, x: torch.Tensor, y: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """y = W V^-1 x."""

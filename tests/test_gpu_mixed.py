@@ -1,0 +1,81 @@
+"""Mixed-precision form (FP32 factorisations + one FP64 refinement step)
+against the FP64 oracle: I_j bit-exact, per-column residual within 1e-4
+relative, w_j / v_j within 1e-6 up to phase where unique; the columns the
+FP32 path could not decide (flag FP64_FALLBACK) are computed by the FP64
+kernel and must meet the same bar."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+from tests._parity import assert_parity, compare, host_factors
+from tests._problems import random_sparse
+from tests.test_gpu_parity import run_gpu
+from workloads import diagonal_pattern, make_workload, pattern_of, upper_budget
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+RTOL_RES, VEC_TOL = 1e-4, 1e-6
+
+
+@pytest.fixture(scope="module")
+def D():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1208_3573_gb300 import build, diaf
+    build.build()
+    return diaf
+
+
+@pytest.mark.parametrize("alg", ["S", "Q"])
+@pytest.mark.parametrize("name", ["convdiff32", "convdiff48_A2", "helmholtz40", "lognormal16"])
+def test_mixed_parity_workloads(D, name, alg):
+    w = make_workload(name)
+    F = run_gpu(D, w.A, w.PW, w.vrule, w.budget, alg=alg, prec="mixed32")
+    g = host_factors(F)
+    o = O.factor(w.A, w.PW, w.vrule, w.budget, alg=alg)
+    rep = compare(g, o, w.A, w.PW, alg, rtol_res=RTOL_RES, vec_tol=VEC_TOL, mixed=True)
+    assert_parity(rep)
+    fb = F.fallbacks()
+    assert sum(fb) == int(np.count_nonzero(g["flags"] & 64))
+
+
+@pytest.mark.parametrize("alg", ["S", "Q"])
+def test_mixed_parity_full_size_convdiff256(D, alg):
+    w = make_workload("convdiff256_A2")
+    F = run_gpu(D, w.A, w.PW, w.vrule, w.budget, alg=alg, prec="mixed32")
+    g = host_factors(F)
+    o = O.factor(w.A, w.PW, w.vrule, w.budget, alg=alg)
+    rep = compare(g, o, w.A, w.PW, alg, rtol_res=RTOL_RES, vec_tol=VEC_TOL, mixed=True)
+    assert_parity(rep)
+    # the FP32 path decides almost every column of this workload itself
+    assert sum(F.fallbacks()) <= 0.01 * w.n
+
+
+@pytest.mark.parametrize("alg", ["S", "Q"])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_mixed_parity_random_fixed_and_rules(D, alg, cplx):
+    A = random_sparse(300, 0.015, 17, cplx)
+    PW = pattern_of(A)
+    for vrule, budget, Vf in ((O.RULE_UPPER, upper_budget(A), None), (O.RULE_LOWER, None, None),
+                              (O.RULE_ALL, np.full(A.n, 4, np.int32), None),
+                              (O.RULE_FIXED, None, diagonal_pattern(A.n)),
+                              (O.RULE_FIXED, None, pattern_of(sp.triu(A.to_scipy())))):
+        F = run_gpu(D, A, PW, vrule, budget, Vf, alg=alg, prec="mixed32")
+        g = host_factors(F)
+        o = O.factor(A, PW, vrule, budget, Vf, alg=alg)
+        assert_parity(compare(g, o, A, PW, alg, rtol_res=RTOL_RES, vec_tol=VEC_TOL, mixed=True))
+
+
+def test_mixed_bicgstab_matches_fp64(D):
+    w = make_workload("convdiff32")
+    S = D.Solver(D.DeviceCSC.from_host(w.A))
+    b = torch.from_numpy(w.b).cuda()
+    its = {}
+    for prec in ("fp64", "mixed32"):
+        F = run_gpu(D, w.A, w.PW, w.vrule, w.budget, alg="S", prec=prec)
+        x, info = S.bicgstab(b, F, tol=1e-8, maxit=1000)
+        assert info.converged
+        its[prec] = info.iterations
+    assert abs(its["fp64"] - its["mixed32"]) <= 1

@@ -171,11 +171,13 @@ diaf_status diaf_get_factors(const diaf_factors* F, diaf_csc* W, diaf_csc* V, co
 /* y = W V^-1 x (eq. afac: A^-1 ~ W V^-1, right preconditioning, Sec. 2.3).
  * x, y: device vectors of n scalars (dtype of F), must not overlap.  V must
  * be triangular (rules UPPER / LOWER, or a fixed triangular pattern) with a
- * nonzero diagonal.  The first call on F builds row-oriented copies of W and
- * V (allocates; make it before any stream capture).  The triangular solve
- * runs in one kernel whose waits are bounded: if a wait runs out the call's
- * next diaf_sync reports DIAF_ETIMEOUT.  Errors: EINVAL (V not triangular or
- * zero diagonal -- found by the first call), ENOMEM, ECUDA. */
+ * nonzero diagonal.  The first call on F prepares the apply: row-oriented
+ * copies of W and V and the level schedule of the V solve (the depth of each
+ * row in V's dependency graph, computed on the host; this first call
+ * allocates and synchronises `stream` -- make it before any stream capture).
+ * Later calls only enqueue two kernels: the level-scheduled triangular solve
+ * (one block, a barrier between levels) and the W SpMV.  Errors: EINVAL (V not
+ * triangular or zero diagonal -- found by the first call), ENOMEM, ECUDA. */
 diaf_status diaf_apply(diaf_factors* F, const void* x, void* y, void* stream);
 
 /* y = W V^-1 x exactly as diaf_apply computes it, but allocating nothing.

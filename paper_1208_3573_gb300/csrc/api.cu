@@ -379,11 +379,39 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   if ((h & 1u) && (h & 2u)) return fail(DIAF_EINVAL, "V is not triangular");
   if (h & 4u) return fail(DIAF_EINVAL, "V has a zero or missing diagonal entry");
   F->v_upper = !(h & 1u);
-  DIAF_CU(F->alloc(&F->ready, n));
-  DIAF_CU(cudaMemsetAsync(F->ready, 0, sizeof(uint32_t) * (n > 0 ? n : 1), s));
-  DIAF_CU(F->alloc(&F->counter, 1));
+  // level schedule: depth of every row in the dependency graph of V (host, O(nnz))
+  {
+    std::vector<int32_t> rp(n + 1), ci((size_t)F->nnz_v), lev(n, 0);
+    DIAF_CU(cudaMemcpyAsync(rp.data(), F->Vr.rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+    if (F->nnz_v > 0)
+      DIAF_CU(cudaMemcpyAsync(ci.data(), F->Vr.colidx, sizeof(int32_t) * F->nnz_v, cudaMemcpyDeviceToHost, s));
+    DIAF_CU(cudaStreamSynchronize(s));
+    int nlev = 0;
+    for (int step = 0; step < n; ++step) {
+      const int i = F->v_upper ? n - 1 - step : step;
+      int L = 0;
+      for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        const int j = ci[p];
+        if (j != i && lev[j] + 1 > L) L = lev[j] + 1;
+      }
+      lev[i] = L;
+      if (L + 1 > nlev) nlev = L + 1;
+    }
+    std::vector<int32_t> ptr(nlev + 1, 0), order(n > 0 ? n : 1);
+    for (int i = 0; i < n; ++i) ptr[lev[i] + 1] += 1;
+    for (int l = 0; l < nlev; ++l) ptr[l + 1] += ptr[l];
+    std::vector<int32_t> cur(ptr.begin(), ptr.end() - 1);
+    for (int i = 0; i < n; ++i) order[cur[lev[i]]++] = i;
+    F->nlev = nlev;
+    DIAF_CU(F->alloc(&F->lvlptr, nlev + 1));
+    DIAF_CU(F->alloc(&F->order, n));
+    DIAF_CU(cudaMemcpyAsync(F->lvlptr, ptr.data(), sizeof(int32_t) * (nlev + 1), cudaMemcpyHostToDevice, s));
+    if (n > 0) DIAF_CU(cudaMemcpyAsync(F->order, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    DIAF_CU(F->alloc((char**)&F->dinv, esz * n));
+    DIAF_CU(csr_diag_inverse(F->Vr, cplx, F->dinv, s));
+    DIAF_CU(cudaStreamSynchronize(s));  // the host vectors above go out of scope
+  }
   DIAF_CU(F->alloc((char**)&F->tbuf, esz * n));
-  F->gen = 0;
   F->apply_ready = true;
   return DIAF_OK;
 }
@@ -398,12 +426,7 @@ diaf_status diaf_apply(diaf_factors* F, const void* x, void* y, void* stream) {
   }
   if (F->n == 0) return DIAF_OK;
   const bool cplx = F->dtype == DIAF_C128;
-  F->gen += 1;
-  if (F->gen == 0) {  // wrapped: clear the flags
-    DIAF_CU(cudaMemsetAsync(F->ready, 0, sizeof(uint32_t) * F->n, s));
-    F->gen = 1;
-  }
-  DIAF_CU(csr_trsv_syncfree(F->Vr, cplx, F->v_upper, x, F->tbuf, F->ready, F->counter, F->gen, F->status, s));
+  DIAF_CU(csr_trsv_levels(F->Vr, cplx, F->nlev, F->lvlptr, F->order, F->dinv, x, F->tbuf, s));
   DIAF_CU(csr_spmv(F->Wr, cplx, F->tbuf, y, s));
   return DIAF_OK;
 }

@@ -3,15 +3,22 @@
 // FP32; then (w_j, v_j) get one FP64 refinement step against the FP64 tile
 // and the residual ||A w - v|| is evaluated in FP64.
 //
-//   DIAF-S: w0 = FP32 smallest right singular vector of R-hat; one step of
-//     inverse iteration on A-hat^* A-hat in FP64 with the FP32 R-hat as the
-//     solver (y = M w0, y += M (w0 - A-hat^*(A-hat y)), M = R-hat^-1 R-hat^-*),
-//     w = y / ||y||; v = T(I_j,:) w.
-//   DIAF-Q: v0 = Q_I u / sigma from the FP32 Jacobi; w = the least-squares
-//     solution of eq. condwj for v0 in FP64 (normal equations with the FP32 R
-//     as the solver plus one correction); one power step v1 = T(I_j,:) w /
-//     ||.|| (v1 is C v0 normalised, C = T_I (T^* T)^-1 T_I^*, whose top
-//     eigenvector is the optimal v of eq. nocond), and w again for v1.
+//   DIAF-S: the FP32 Jacobi gives R-hat V = U diag(sigma); x0 = V e_min.
+//     With H = A-hat^* A-hat taken from the FP64 tile, V^* H V is diagonal to
+//     FP32 accuracy, so one correction in that basis,
+//       d = x^* H x / x^* x,  r = H x - d x,
+//       x <- x - sum_{i != min} V_i (V_i^* r) / (sigma_i^2 - d),
+//     makes x the smallest right singular vector to second order (repeated
+//     once when the relative gap is below 1e-2; columns with a gap below 1e-5
+//     go to the FP64 kernel).  w = x / ||x||, v = T(I_j,:) w.
+//   DIAF-Q: v0 = Q_I u / sigma from the FP32 Jacobi.  In FP64:
+//     X = (T^* T)^-1 T_I^* column by column (normal equations with the FP32 R
+//     as the solver plus one correction with the FP64 residual), the l x l
+//     matrix C = T_I X whose top eigenvector is the optimal v of eq. nocond
+//     (C = M_j^* M_j), one Rayleigh-quotient-iteration step from v0
+//     (mu = v0^* C v0, v = (C - mu)^-1 v0 normalised), and w = X v, the
+//     least-squares solution of eq. condwj.  Columns with l_j > 8 go to the
+//     FP64 kernel.
 //
 // A column goes to the FP64 kernel instead (appended to fb_list) when a
 // leverage-selection decision is closer to its threshold than the FP32 key
@@ -28,13 +35,15 @@ template <> struct DoubleOf<Cx<float>> { using T = Cx<double>; };
 // Column-scaled conditioning estimate of an upper R whose columns came from a
 // tile with column norms cn: max_c cn_c / |R_cc| (1 for orthogonal columns).
 constexpr float kMixedKappaMax = 300.0f;
+constexpr int kRRMax = 8;  // DIAF-Q: largest l_j refined through the explicit l x l matrix C
 
 template <class S, int KMAX, int MMAX>
 struct MixedLayout {
   using SD = typename DoubleOf<S>::T;
   static constexpr int kTile = MMAX * KMAX;
   static constexpr size_t raw() {
-    return sizeof(SD) * (kTile + 3 * KMAX + 2 * MMAX) + sizeof(S) * (kTile + 3 * KMAX * KMAX + KMAX) +
+    return sizeof(SD) * (kTile + 3 * KMAX + 2 * MMAX + kRRMax * KMAX + 2 * kRRMax * kRRMax) +
+           sizeof(S) * (kTile + 2 * KMAX * KMAX + KMAX) +
            sizeof(double) * (MMAX + 2 * KMAX) + idx_bytes<KMAX, MMAX>();
   }
   static constexpr size_t bytes() { return (raw() + 15) / 16 * 16; }
@@ -51,10 +60,12 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
   SD* gg = wv + KMAX;                    // k-vector scratch
   SD* vv = gg + KMAX;                    // v (MMAX)
   SD* zz = vv + MMAX;                    // m-vector scratch
-  S* Tw = reinterpret_cast<S*>(zz + MMAX);  // FP32 working tile
+  SD* Xs = zz + MMAX;                    // DIAF-Q: X = (T^* T)^-1 T_I^* (KMAX x kRRMax)
+  SD* Cs = Xs + kRRMax * KMAX;           // DIAF-Q: C = T_I X (kRRMax x kRRMax)
+  SD* Ms = Cs + kRRMax * kRRMax;         // DIAF-Q: C - mu I, eliminated in place
+  S* Tw = reinterpret_cast<S*>(Ms + kRRMax * kRRMax);  // FP32 working tile
   S* Rs = Tw + L::kTile;                 // FP32 R of T, then R-hat (Jacobi works on it)
-  S* Rr = Rs + KMAX * KMAX;              // FP32 R-hat kept for the refinement
-  S* Vj = Rr + KMAX * KMAX;              // FP32 Jacobi V
+  S* Vj = Rs + KMAX * KMAX;              // FP32 Jacobi V
   S* rinv = Vj + KMAX * KMAX;            // FP32 reciprocal diagonal
   double* hk = reinterpret_cast<double*>(rinv + KMAX);
   double* sig = hk + MMAX;
@@ -133,14 +144,12 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     warp_householder_qr<S, MMAX>(Tw, me, k, lane);
     for (int i = lane; i < k * k; i += DIAF_WARP) {
       int r = i % k, c = i / k;
-      S x = (r <= c) ? Tw[r + c * MMAX] : sc_zero<S>();
-      Rs[r + c * KMAX] = x;
-      Rr[r + c * KMAX] = x;
+      Rs[r + c * KMAX] = (r <= c) ? Tw[r + c * MMAX] : sc_zero<S>();
     }
     __syncwarp();
     float kh = 0.0f;
     for (int c = lane; c < k; c += DIAF_WARP) {
-      float d = (float)sc_abs(Rr[c + c * KMAX]);
+      float d = (float)sc_abs(Rs[c + c * KMAX]);
       kh = fmaxf(kh, d > 0.0f ? (float)cn[c] / d : INFINITY);
     }
     kh = warp_max(kh);
@@ -157,27 +166,44 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     double snext = INFINITY;
     for (int c = 0; c < k; ++c) if (c != imin) snext = dmin(snext, sig[c]);
     if (k > 1 && (snext - smin) <= 1e-6 * smax) flags |= DIAF_FLAG_DEGENERATE;
-    // ---- FP64 refinement: one step of inverse iteration on A-hat^* A-hat
-    for (int c = lane; c < k; c += DIAF_WARP) rinvD[c] = sc_recip_or_zero(sc_cast<SD>(Rr[c + c * KMAX]), 0.0);
-    __syncwarp();
-    const SD w0 = lane < k ? sc_cast<SD>(Vj[lane + imin * KMAX]) : sc_zero<SD>();
-    SD y = warp_solve_RhR<SD, S, KMAX>(Rr, rinvD, w0, k, lane);
-    if (lane < k) gg[lane] = y;
-    __syncwarp();
-    for (int r = lane; r < m; r += DIAF_WARP) {
-      SD z = sc_zero<SD>();
-      if (ix.inI[r] < 0)
-        for (int q = 0; q < k; ++q) z += Ts[r + q * MMAX] * gg[q];
-      zz[r] = z;
+    // ---- FP64 correction in the FP32 singular basis V (columns of Vj)
+    double gap = INFINITY;
+    for (int c = 0; c < k; ++c) if (c != imin) gap = dmin(gap, sig[c] * sig[c] - smin * smin);
+    if (k > 1 && gap <= 1e-5 * smax * smax) { hand_back(); return; }
+    const int iters = (k > 1 && gap < 1e-2 * smax * smax) ? 2 : 1;
+    SD* cc = rinvD;  // correction coefficients (KMAX)
+    SD x = lane < k ? sc_cast<SD>(Vj[lane + imin * KMAX]) : sc_zero<SD>();
+    for (int it = 0; it < iters; ++it) {
+      if (lane < k) gg[lane] = x;
+      __syncwarp();
+      for (int r = lane; r < m; r += DIAF_WARP) {
+        SD z = sc_zero<SD>();
+        if (ix.inI[r] < 0)
+          for (int q = 0; q < k; ++q) z += Ts[r + q * MMAX] * gg[q];
+        zz[r] = z;
+      }
+      __syncwarp();
+      SD g = sc_zero<SD>();  // (H x)_q = (A-hat^* (A-hat x))_q
+      if (lane < k)
+        for (int r = 0; r < m; ++r) g += sc_cmul(Ts[r + lane * MMAX], zz[r]);
+      const double xg = warp_sum(lane < k ? (double)sc_real(sc_cmul(x, g)) : 0.0);
+      const double xx = warp_sum(lane < k ? (double)sc_abs2(x) : 0.0);
+      const double d = xg / xx;
+      if (lane < k) wv[lane] = g - RealOf<SD>(d) * x;  // r = H x - d x
+      __syncwarp();
+      if (lane < k) {
+        SD vr = sc_zero<SD>();
+        for (int q = 0; q < k; ++q) vr += sc_cmul(sc_cast<SD>(Vj[q + lane * KMAX]), wv[q]);
+        const double den = sig[lane] * sig[lane] - d;
+        cc[lane] = (lane == imin) ? sc_zero<SD>() : RealOf<SD>(-1.0 / den) * vr;
+      }
+      __syncwarp();
+      if (lane < k)
+        for (int i = 0; i < k; ++i) x += sc_cast<SD>(Vj[lane + i * KMAX]) * cc[i];
+      __syncwarp();
     }
-    __syncwarp();
-    SD g = sc_zero<SD>();
-    if (lane < k)
-      for (int r = 0; r < m; ++r) g += sc_cmul(Ts[r + lane * MMAX], zz[r]);
-    y += warp_solve_RhR<SD, S, KMAX>(Rr, rinvD, w0 - g, k, lane);
-    double yn2 = warp_sum(lane < k ? (double)sc_abs2(y) : 0.0);
-    const double inv = 1.0 / sqrt(yn2);
-    if (lane < k) wv[lane] = inv * y;
+    const double xn2 = warp_sum(lane < k ? (double)sc_abs2(x) : 0.0);
+    if (lane < k) wv[lane] = RealOf<SD>(1.0 / sqrt(xn2)) * x;
     __syncwarp();
     // v = T(I_j,:) w and the rank test on the FP64 value of ||A-hat w||
     for (int t = lane; t < l; t += DIAF_WARP) {
@@ -199,6 +225,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     __syncwarp();
   } else {
     // ---- FP32 Jacobi on Q_I (FP32 rows of Q = T R^-1 in Tw)
+    if (l > kRRMax) { hand_back(); return; }
     compact_rows<S, MMAX>(Tw, ix.Iloc, l, k, lane);
     int sw = warp_jacobi<S, MMAX, KMAX, KMAX>(Tw, l, k, Vj, lane);
     if (sw < 0) flags |= DIAF_FLAG_JACOBI_NOCONV;
@@ -213,48 +240,95 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     for (int t = lane; t < l; t += DIAF_WARP) vv[t] = sc_cast<SD>(Tw[t + imax * MMAX]);
     for (int c = lane; c < k; c += DIAF_WARP) rinvD[c] = sc_recip_or_zero(sc_cast<SD>(Rs[c + c * KMAX]), 0.0);
     __syncwarp();
-    // two rounds: least squares for v, then the power step v <- T_I w / ||T_I w||
-    for (int round = 0; round < 2; ++round) {
-      double vn2 = 0.0;
-      for (int t = lane; t < l; t += DIAF_WARP) vn2 += (double)sc_abs2(vv[t]);
-      vn2 = warp_sum(vn2);
-      const double vinv = 1.0 / sqrt(vn2);
-      for (int t = lane; t < l; t += DIAF_WARP) vv[t] = vinv * vv[t];
-      __syncwarp();
-      // g0 = T_I^* v
-      SD g0 = sc_zero<SD>();
-      if (lane < k)
-        for (int t = 0; t < l; ++t) {
-          int r = ix.Iloc[t];
-          if (r >= 0) g0 += sc_cmul(Ts[r + lane * MMAX], vv[t]);
-        }
-      SD w = warp_solve_RhR<SD, S, KMAX>(Rs, rinvD, g0, k, lane);
-      // correction with the FP64 normal-equation residual T^* (v - T w)
-      if (lane < k) gg[lane] = w;
+    // X(:,t) = (T^* T)^-1 T(I_t,:)^*: one solve with the FP32 R, one correction
+    for (int t = 0; t < l; ++t) {
+      const int rI = ix.Iloc[t];
+      const SD b = (lane < k && rI >= 0) ? sc_conj(Ts[rI + lane * MMAX]) : sc_zero<SD>();
+      SD x = warp_solve_RhR<SD, S, KMAX>(Rs, rinvD, b, k, lane);
+      if (lane < k) gg[lane] = x;
       __syncwarp();
       for (int r = lane; r < m; r += DIAF_WARP) {
-        SD z = ix.inI[r] >= 0 ? vv[ix.inI[r]] : sc_zero<SD>();
+        SD z = sc_zero<SD>();
         for (int q = 0; q < k; ++q) z -= Ts[r + q * MMAX] * gg[q];
         zz[r] = z;
       }
       __syncwarp();
-      SD rn = sc_zero<SD>();
+      SD rn = b;
       if (lane < k)
         for (int r = 0; r < m; ++r) rn += sc_cmul(Ts[r + lane * MMAX], zz[r]);
-      w += warp_solve_RhR<SD, S, KMAX>(Rs, rinvD, rn, k, lane);
-      if (lane < k) wv[lane] = w;
+      x += warp_solve_RhR<SD, S, KMAX>(Rs, rinvD, rn, k, lane);
+      if (lane < k) Xs[lane + t * KMAX] = x;
       __syncwarp();
-      if (round == 0) {
-        for (int t = lane; t < l; t += DIAF_WARP) {
-          SD s = sc_zero<SD>();
-          int r = ix.Iloc[t];
-          if (r >= 0)
-            for (int q = 0; q < k; ++q) s += Ts[r + q * MMAX] * wv[q];
-          vv[t] = s;
-        }
-        __syncwarp();
-      }
     }
+    // C = T_I X (Hermitian positive semidefinite, l x l)
+    for (int e = lane; e < l * l; e += DIAF_WARP) {
+      const int s2 = e % l, t = e / l, rI = ix.Iloc[s2];
+      SD c = sc_zero<SD>();
+      if (rI >= 0)
+        for (int q = 0; q < k; ++q) c += Ts[rI + q * MMAX] * Xs[q + t * KMAX];
+      Cs[s2 + t * kRRMax] = c;
+    }
+    __syncwarp();
+    // one Rayleigh-quotient-iteration step from v0 (lane 0; l <= 8)
+    if (lane == 0) {
+      using RD = RealOf<SD>;
+      RD n2 = RD(0);
+      for (int t = 0; t < l; ++t) n2 += sc_abs2(vv[t]);
+      const RD ninv = RD(1) / sqrt(n2);
+      SD y[kRRMax];
+      for (int t = 0; t < l; ++t) y[t] = ninv * vv[t];
+      RD mu = RD(0), cmax = RD(0);
+      for (int s2 = 0; s2 < l; ++s2)
+        for (int t = 0; t < l; ++t) {
+          const SD c = Cs[s2 + t * kRRMax];
+          mu += sc_real(sc_cmul(y[s2], c * y[t]));
+          cmax = dmax(cmax, sc_abs(c));
+        }
+      for (int s2 = 0; s2 < l; ++s2)
+        for (int t = 0; t < l; ++t)
+          Ms[s2 + t * kRRMax] = Cs[s2 + t * kRRMax] - (s2 == t ? sc_real_s<SD>(mu) : sc_zero<SD>());
+      // Gaussian elimination with partial pivoting; an exactly singular pivot
+      // (v0 already an eigenvector) is replaced by eps ||C||
+      const RD tinyp = eps_of<RD>() * (cmax > RD(0) ? cmax : RD(1));
+      for (int c = 0; c < l; ++c) {
+        int pr = c;
+        RD pa = sc_abs(Ms[c + c * kRRMax]);
+        for (int r = c + 1; r < l; ++r) {
+          RD ar = sc_abs(Ms[r + c * kRRMax]);
+          if (ar > pa) { pa = ar; pr = r; }
+        }
+        if (pr != c) {
+          for (int t = 0; t < l; ++t) {
+            SD tmp = Ms[c + t * kRRMax]; Ms[c + t * kRRMax] = Ms[pr + t * kRRMax]; Ms[pr + t * kRRMax] = tmp;
+          }
+          SD tmp = y[c]; y[c] = y[pr]; y[pr] = tmp;
+        }
+        if (!(sc_abs(Ms[c + c * kRRMax]) > tinyp)) Ms[c + c * kRRMax] = sc_real_s<SD>(tinyp);
+        const SD dinv = sc_recip_or_zero(Ms[c + c * kRRMax], RD(0));
+        for (int r = c + 1; r < l; ++r) {
+          const SD f = Ms[r + c * kRRMax] * dinv;
+          for (int t = c + 1; t < l; ++t) Ms[r + t * kRRMax] -= f * Ms[c + t * kRRMax];
+          y[r] -= f * y[c];
+        }
+      }
+      for (int c = l - 1; c >= 0; --c) {
+        SD acc = y[c];
+        for (int t = c + 1; t < l; ++t) acc -= Ms[c + t * kRRMax] * y[t];
+        y[c] = acc * sc_recip_or_zero(Ms[c + c * kRRMax], RD(0));
+      }
+      RD yn2 = RD(0);
+      for (int t = 0; t < l; ++t) yn2 += sc_abs2(y[t]);
+      const RD yinv = RD(1) / sqrt(yn2);
+      for (int t = 0; t < l; ++t) vv[t] = yinv * y[t];
+    }
+    __syncwarp();
+    // w = X v (eq. condwj for the refined v)
+    if (lane < k) {
+      SD x = sc_zero<SD>();
+      for (int t = 0; t < l; ++t) x += Xs[lane + t * KMAX] * vv[t];
+      wv[lane] = x;
+    }
+    __syncwarp();
   }
   finish_column<SD, MMAX>(a, j, k, m, l, jpos, Ts, wv, vv, ix, flags, true, lane);
 }

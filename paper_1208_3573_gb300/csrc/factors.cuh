@@ -31,10 +31,12 @@ struct diaf_factors {
   bool apply_ready = false;
   bool v_upper = true;
   Csr Vr, Wr;
-  uint32_t* ready = nullptr;
-  int32_t* counter = nullptr;
-  uint32_t gen = 0;
   void* tbuf = nullptr;
+  // level schedule of the V solve
+  int nlev = 0;
+  int32_t* lvlptr = nullptr;
+  int32_t* order = nullptr;
+  void* dinv = nullptr;
 
   template <class T>
   cudaError_t alloc(T** p, size_t count) {

@@ -148,7 +148,73 @@ __global__ void trsv_syncfree_kernel(int n, const int32_t* __restrict__ rowptr, 
   }
 }
 
+constexpr int kLevelThreads = 1024;
+constexpr int kLevelPtrSmem = 8192;  // level pointers kept in shared memory up to this many levels
+
+template <class S>
+__global__ void __launch_bounds__(kLevelThreads)
+    trsv_levels_kernel(int nlev, const int32_t* __restrict__ lvlptr, const int32_t* __restrict__ order,
+                       const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                       const S* __restrict__ vals, const S* __restrict__ dinv, const S* __restrict__ x, S* t) {
+  __shared__ int32_t sptr[kLevelPtrSmem + 1];
+  const bool in_smem = nlev <= kLevelPtrSmem;
+  if (in_smem)
+    for (int i = threadIdx.x; i <= nlev; i += blockDim.x) sptr[i] = lvlptr[i];
+  __syncthreads();
+  for (int lv = 0; lv < nlev; ++lv) {
+    const int b = in_smem ? sptr[lv] : lvlptr[lv];
+    const int e = in_smem ? sptr[lv + 1] : lvlptr[lv + 1];
+    for (int idx = b + threadIdx.x; idx < e; idx += blockDim.x) {
+      const int i = order[idx];
+      S acc = x[i];
+      for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+        const int j = colidx[p];
+        if (j != i) acc -= vals[p] * t[j];
+      }
+      t[i] = acc * dinv[i];
+    }
+    __syncthreads();
+  }
+}
+
+template <class S>
+__global__ void diag_inverse_kernel(int n, const int32_t* rowptr, const int32_t* colidx, const S* vals, S* dinv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  S d = sc_zero<S>();
+  for (int p = rowptr[i]; p < rowptr[i + 1]; ++p)
+    if (colidx[p] == i) d = vals[p];
+  dinv[i] = (1.0 / sc_abs2(d)) * sc_conj(d);
+}
+
 }  // namespace
+
+cudaError_t csr_trsv_levels(const Csr& V, bool cplx, int nlev, const int32_t* lvlptr, const int32_t* order,
+                            const void* dinv, const void* x, void* t, cudaStream_t s) {
+  if (V.n <= 0) return cudaSuccess;
+  if (cplx)
+    trsv_levels_kernel<Cx<double>><<<1, kLevelThreads, 0, s>>>(nlev, lvlptr, order, V.rowptr, V.colidx,
+                                                              (const Cx<double>*)V.vals, (const Cx<double>*)dinv,
+                                                              (const Cx<double>*)x, (Cx<double>*)t);
+  else
+    trsv_levels_kernel<double><<<1, kLevelThreads, 0, s>>>(nlev, lvlptr, order, V.rowptr, V.colidx,
+                                                          (const double*)V.vals, (const double*)dinv,
+                                                          (const double*)x, (double*)t);
+  DIAF_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+cudaError_t csr_diag_inverse(const Csr& V, bool cplx, void* dinv, cudaStream_t s) {
+  if (V.n <= 0) return cudaSuccess;
+  if (cplx)
+    diag_inverse_kernel<Cx<double>><<<ceil_div(V.n, 256), 256, 0, s>>>(V.n, V.rowptr, V.colidx,
+                                                                       (const Cx<double>*)V.vals, (Cx<double>*)dinv);
+  else
+    diag_inverse_kernel<double><<<ceil_div(V.n, 256), 256, 0, s>>>(V.n, V.rowptr, V.colidx, (const double*)V.vals,
+                                                                   (double*)dinv);
+  DIAF_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
 
 cudaError_t csc_to_csr(int n, int64_t nnz, const int32_t* cp, const int32_t* ri, const void* v, bool cplx,
                        int32_t* rowptr, int32_t* colidx, void* vals, int32_t* work, cudaStream_t s) {

@@ -34,3 +34,13 @@ cudaError_t csr_triangle_check(const Csr& V, bool cplx, uint32_t* out, cudaStrea
 // DEV_ST_TIMEOUT in *status and the row is finished with what it has.
 cudaError_t csr_trsv_syncfree(const Csr& V, bool cplx, bool upper, const void* x, void* t, uint32_t* ready,
                               int32_t* counter, uint32_t gen, uint32_t* status, cudaStream_t s);
+
+// t = V^-1 x by level scheduling: rows grouped by their depth in the
+// dependency graph of the triangular V (order = rows level by level,
+// lvlptr[l]..lvlptr[l+1] the rows of level l, nlev levels), solved by one
+// 1024-thread block with a barrier between levels; dinv = 1 / diag(V).
+cudaError_t csr_trsv_levels(const Csr& V, bool cplx, int nlev, const int32_t* lvlptr, const int32_t* order,
+                            const void* dinv, const void* x, void* t, cudaStream_t s);
+
+// dinv[i] = 1 / V_ii (CSR V with a nonzero diagonal).
+cudaError_t csr_diag_inverse(const Csr& V, bool cplx, void* dinv, cudaStream_t s);

@@ -35,7 +35,7 @@ def test_mixed_parity_workloads(D, name, alg):
     F = run_gpu(D, w.A, w.PW, w.vrule, w.budget, alg=alg, prec="mixed32")
     g = host_factors(F)
     o = O.factor(w.A, w.PW, w.vrule, w.budget, alg=alg)
-    rep = compare(g, o, w.A, w.PW, alg, rtol_res=RTOL_RES, vec_tol=VEC_TOL, mixed=True)
+    rep = compare(g, o, w.A, w.PW, alg, rtol_res=RTOL_RES, vec_tol=VEC_TOL, mixed=True, floor_rel=1e-10)
     assert_parity(rep)
     fb = F.fallbacks()
     assert sum(fb) == int(np.count_nonzero(g["flags"] & 64))
@@ -47,7 +47,7 @@ def test_mixed_parity_full_size_convdiff256(D, alg):
     F = run_gpu(D, w.A, w.PW, w.vrule, w.budget, alg=alg, prec="mixed32")
     g = host_factors(F)
     o = O.factor(w.A, w.PW, w.vrule, w.budget, alg=alg)
-    rep = compare(g, o, w.A, w.PW, alg, rtol_res=RTOL_RES, vec_tol=VEC_TOL, mixed=True)
+    rep = compare(g, o, w.A, w.PW, alg, rtol_res=RTOL_RES, vec_tol=VEC_TOL, mixed=True, floor_rel=1e-10)
     assert_parity(rep)
     # the FP32 path decides almost every column of this workload itself
     assert sum(F.fallbacks()) <= 0.01 * w.n
@@ -65,7 +65,7 @@ def test_mixed_parity_random_fixed_and_rules(D, alg, cplx):
         F = run_gpu(D, A, PW, vrule, budget, Vf, alg=alg, prec="mixed32")
         g = host_factors(F)
         o = O.factor(A, PW, vrule, budget, Vf, alg=alg)
-        assert_parity(compare(g, o, A, PW, alg, rtol_res=RTOL_RES, vec_tol=VEC_TOL, mixed=True))
+        assert_parity(compare(g, o, A, PW, alg, rtol_res=RTOL_RES, vec_tol=VEC_TOL, mixed=True, floor_rel=1e-10))
 
 
 def test_mixed_bicgstab_matches_fp64(D):

@@ -42,17 +42,21 @@ def _stale(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, variant: str = "") -> str:
+    """variant: "" (the library) or "phase" (profiling build with the phase
+    timers, libdiaf_phase.so, objects in _build/phase)."""
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = [d for d in _deps() if not d.endswith(".cu")]
-    if not force and not _stale(LIB, _deps()):
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    lib_path = LIB if not variant else os.path.join(HERE, f"libdiaf_{variant}.so")
+    build_dir = BUILD if not variant else os.path.join(BUILD, variant)
+    extra = list(extra or []) + (["-DDIAF_PHASE_TIMING"] if variant == "phase" else [])
+    if not force and not _stale(lib_path, _deps()):
+        return lib_path
+    os.makedirs(build_dir, exist_ok=True)
     exe = nvcc()
-    extra = extra or []
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         if force or _stale(obj, [src] + headers):
             cmd = [exe, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
             if verbose:
@@ -66,15 +70,16 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 
     with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [exe, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
     extra = [a for a in sys.argv[1:] if a.startswith("-X")]
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, extra=extra))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, extra=extra,
+                variant="phase" if "--phase-timing" in sys.argv else ""))

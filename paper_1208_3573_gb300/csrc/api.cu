@@ -12,6 +12,18 @@
 #include "sparse.cuh"
 
 static std::atomic<long long> g_launches{0};
+#ifdef DIAF_PHASE_TIMING
+static unsigned long long* g_phase = nullptr;  // device, 32 counters
+extern "C" int diaf_phase_cycles(unsigned long long* out, int reset) {
+  if (!g_phase) {
+    for (int i = 0; i < 32; ++i) out[i] = 0;
+    return 0;
+  }
+  if (cudaMemcpy(out, g_phase, sizeof(unsigned long long) * 32, cudaMemcpyDeviceToHost) != cudaSuccess) return 1;
+  if (reset && cudaMemset(g_phase, 0, sizeof(unsigned long long) * 32) != cudaSuccess) return 1;
+  return 0;
+}
+#endif
 static thread_local std::string g_last_error;
 void diaf_set_last_error(const char* msg) { g_last_error = msg; }
 void diaf_note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -275,6 +287,13 @@ diaf_status diaf_factor(const diaf_csc* A, const diaf_pattern* PW, const diaf_vs
   ca.tie_tol = V->tie_tol > 0 ? V->tie_tol : 1e-9;
   ca.Wv = F->Wv; ca.Vri = F->Vri; ca.Vv = F->Vv;
   ca.res = F->res; ca.flags = F->flags; ca.status = status;
+#ifdef DIAF_PHASE_TIMING
+  if (!g_phase) {
+    DIAF_CU(cudaMalloc(&g_phase, sizeof(unsigned long long) * 32));
+    DIAF_CU(cudaMemset(g_phase, 0, sizeof(unsigned long long) * 32));
+  }
+  ca.phase = g_phase;
+#endif
   const bool mixed = prec == DIAF_PREC_MIXED32;
   int32_t *fb_list = nullptr, *fb_count = nullptr;
   if (mixed) {

@@ -45,6 +45,7 @@ struct ColArgs {
   double* res;
   uint32_t* flags;
   uint32_t* status;
+  unsigned long long* phase;  // profiling builds only: per-phase cycle counters (or null)
 };
 
 // ------------------------------------------------------------------ shared steps

@@ -90,7 +90,9 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     return;
   }
 
+  DIAF_PHASE_START();
   gather_tile<SD, KMAX, MMAX>(a, j, k, m, me, Ts, ix, lane);
+  DIAF_PHASE(0);
 
   // ---- FP32 QR of T and the keys
   for (int i = lane; i < me * k; i += DIAF_WARP) {
@@ -103,12 +105,14 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     cn[c] = sqrt(s);
   }
   __syncwarp();
+  DIAF_PHASE(1);
   warp_householder_qr<S, MMAX>(Tw, me, k, lane);
   for (int i = lane; i < k * k; i += DIAF_WARP) {
     int r = i % k, c = i / k;
     Rs[r + c * KMAX] = (r <= c) ? Tw[r + c * MMAX] : sc_zero<S>();
   }
   __syncwarp();
+  DIAF_PHASE(2);
   float kap = 0.0f;
   for (int c = lane; c < k; c += DIAF_WARP) {
     float d = (float)sc_abs(Rs[c + c * KMAX]);
@@ -117,6 +121,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
   kap = warp_max(kap);
   if (!(kap <= kMixedKappaMax)) { hand_back(); return; }
   warp_leverage_rows<S, SD, MMAX, KMAX>(Ts, Rs, Tw, hk, rinv, m, k, R(0), lane);
+  DIAF_PHASE(3);
   if (a.rule != DIAF_RULE_FIXED) {
     const double margin = select_rows_greedy(ix.rs, hk, ix.pick, m, a.rule, j, l - 1, a.tie_tol, lane);
     // bound on the FP32 key error: backward error of the FP32 QR and of the
@@ -127,6 +132,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
   const int jpos = build_I(a, j, m, l, ix, lane);
   for (int t = lane; t < l; t += DIAF_WARP) vv[t] = sc_zero<SD>();
   __syncwarp();
+  DIAF_PHASE(4);
 
   if (ALG == DIAF_ALG_S) {
     // ---- FP32 QR of A-hat (I_j rows zeroed) and Jacobi SVD of R-hat
@@ -141,12 +147,14 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
       cn[c] = sqrt(s);
     }
     __syncwarp();
+    DIAF_PHASE(5);
     warp_householder_qr<S, MMAX>(Tw, me, k, lane);
     for (int i = lane; i < k * k; i += DIAF_WARP) {
       int r = i % k, c = i / k;
       Rs[r + c * KMAX] = (r <= c) ? Tw[r + c * MMAX] : sc_zero<S>();
     }
     __syncwarp();
+    DIAF_PHASE(6);
     float kh = 0.0f;
     for (int c = lane; c < k; c += DIAF_WARP) {
       float d = (float)sc_abs(Rs[c + c * KMAX]);
@@ -156,6 +164,10 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     if (!(kh <= kMixedKappaMax)) { hand_back(); return; }
     int sw = warp_jacobi<S, KMAX, KMAX, KMAX>(Rs, k, k, Vj, lane);
     if (sw < 0) flags |= DIAF_FLAG_JACOBI_NOCONV;
+#ifdef DIAF_PHASE_TIMING
+    if (lane == 0 && a.phase) atomicAdd(&a.phase[20], (unsigned long long)(sw < 0 ? kMaxSweeps : sw));
+#endif
+    DIAF_PHASE(7);
     warp_col_norms<S, KMAX>(Rs, k, k, sig, lane);
     int imin = 0;
     double smin = sig[0], smax = sig[0];
@@ -205,6 +217,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     const double xn2 = warp_sum(lane < k ? (double)sc_abs2(x) : 0.0);
     if (lane < k) wv[lane] = RealOf<SD>(1.0 / sqrt(xn2)) * x;
     __syncwarp();
+    DIAF_PHASE(8);
     // v = T(I_j,:) w and the rank test on the FP64 value of ||A-hat w||
     for (int t = lane; t < l; t += DIAF_WARP) {
       SD s = sc_zero<SD>();
@@ -330,7 +343,9 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     }
     __syncwarp();
   }
+  DIAF_PHASE(9);
   finish_column<SD, MMAX>(a, j, k, m, l, jpos, Ts, wv, vv, ix, flags, true, lane);
+  DIAF_PHASE(10);
 }
 
 template <class S, int KMAX, int MMAX, int ALG>

@@ -128,6 +128,29 @@ template <int G, class R> __device__ __forceinline__ Cx<R> group_sum(Cx<R> v) {
   return v;
 }
 
+// ----------------------------------------------------------------- phase timers
+// Built only with -DDIAF_PHASE_TIMING (profiling builds): lane 0 of every warp
+// adds the clock64 cycles spent between consecutive marks to phase[id], a
+// device buffer handed to the kernel (ColArgs::phase); diaf_phase_cycles()
+// (api.cu) reads it back.  No work is skipped.
+#ifdef DIAF_PHASE_TIMING
+#define DIAF_PHASE_START() long long diaf_t0_ = clock64()
+#define DIAF_PHASE(id)                                                                               \
+  do {                                                                                               \
+    long long diaf_t1_ = clock64();                                                                  \
+    if ((threadIdx.x & 31) == 0 && a.phase)                                                          \
+      atomicAdd(&a.phase[id], (unsigned long long)(diaf_t1_ - diaf_t0_));                           \
+    diaf_t0_ = diaf_t1_;                                                                             \
+  } while (0)
+#else
+#define DIAF_PHASE_START() \
+  do {                     \
+  } while (0)
+#define DIAF_PHASE(id) \
+  do {                 \
+  } while (0)
+#endif
+
 // ----------------------------------------------------------------- misc
 // Process-wide count of kernels launched by this library (for the benchmark's
 // launch accounting); defined in api.cu.

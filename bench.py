@@ -129,7 +129,7 @@ def cpu_baseline(w, alg, seconds=12.0):
     cols = 0
     passes = 0
     while time.perf_counter() - t0 < seconds:
-        O.factor(w.A, w.PW, w.vrule, w.budget, alg=alg, nthreads=cores)
+        O.factor(w.A, w.PW, w.vrule, w.budget, alg=alg, tie_tol=w.tie_tol, nthreads=cores)
         cols += w.n
         passes += 1
     dt = time.perf_counter() - t0
@@ -147,11 +147,11 @@ def run_reference(args):
     cores = os.cpu_count() or 1
     O.factor(w.A, w.PW, w.vrule, w.budget, alg=args.alg, cols=np.arange(64, dtype=np.int32))
     for _ in range(args.warmup):
-        O.factor(w.A, w.PW, w.vrule, w.budget, alg=args.alg, nthreads=cores)
+        O.factor(w.A, w.PW, w.vrule, w.budget, alg=args.alg, tie_tol=w.tie_tol, nthreads=cores)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        O.factor(w.A, w.PW, w.vrule, w.budget, alg=args.alg, nthreads=cores)
+        O.factor(w.A, w.PW, w.vrule, w.budget, alg=args.alg, tie_tol=w.tie_tol, nthreads=cores)
         times.append(time.perf_counter() - t0)
     ms = 1e3 * float(np.mean(times))
     val = w.n / (ms / 1e3)
@@ -203,9 +203,12 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
+    do_apply = w.meta.get("apply", True)
+
     def step(Ad, PWd, budd):
-        F = diaf.factor(Ad, PWd, w.vrule, budd, alg=args.alg, prec=args.prec, stream=stream)
-        F.apply(x1, y1, stream=stream)
+        F = diaf.factor(Ad, PWd, w.vrule, budd, alg=args.alg, prec=args.prec, tie_tol=w.tie_tol, stream=stream)
+        if do_apply:
+            F.apply(x1, y1, stream=stream)
         return F
 
     def barrier():
@@ -296,9 +299,9 @@ def main():
             "kernel_ms": kern, "algorithmic_flops": flops, "peak_source": src}
 
     extras = {}
-    if not args.no_extras and rank == 0:
+    if not args.no_extras and rank == 0 and do_apply:
         # BiCGSTAB with the preconditioner (not part of the setup metric)
-        F = diaf.factor(A, PW, w.vrule, bud, alg=args.alg, prec=args.prec)
+        F = diaf.factor(A, PW, w.vrule, bud, alg=args.alg, prec=args.prec, tie_tol=w.tie_tol)
         S = diaf.Solver(A)
         b = torch.from_numpy(w.b).to(dev)
         S.bicgstab(b, F, tol=1e-8, maxit=1000)
@@ -318,11 +321,11 @@ def main():
             for _ in range(3):
                 flush.zero_()
                 torch.cuda.synchronize()
-                Fd = diaf.factor(A, PW, w.vrule, bud, alg=args.alg, prec="fp64")
+                Fd = diaf.factor(A, PW, w.vrule, bud, alg=args.alg, prec="fp64", tie_tol=w.tie_tol)
                 tt.append(Fd.timings()["total_ms"])
                 res64 = Fd.res.cpu().numpy()
                 Fd.close()
-            Fm = diaf.factor(A, PW, w.vrule, bud, alg=args.alg, prec=args.prec)
+            Fm = diaf.factor(A, PW, w.vrule, bud, alg=args.alg, prec=args.prec, tie_tol=w.tie_tol)
             resm = Fm.res.cpu().numpy()
             fb = Fm.fallbacks()
             Fm.close()
@@ -338,7 +341,7 @@ def main():
         for _ in range(3):
             flush.zero_()
             torch.cuda.synchronize()
-            Fo = diaf.factor(A, PW, w.vrule, bud, alg=other, prec=args.prec)
+            Fo = diaf.factor(A, PW, w.vrule, bud, alg=other, prec=args.prec, tie_tol=w.tie_tol)
             tt.append(Fo.timings()["total_ms"])
             Fo.close()
         extras[f"alg_{other}_factor_columns_per_s"] = w.n / (statistics.median(tt) / 1e3)
@@ -352,7 +355,8 @@ def main():
                 "config": {"workload": w.name, "n": w.n, "alg": args.alg, "prec": args.prec,
                            "nnz_A": w.A.nnz, "nnz_W": w.PW.nnz, "columns_per_step": w.n,
                            "l2": "flushed (256 MiB write) before every timed step",
-                           "step": "diaf_factor + one diaf_apply", "bucket_cols": bucket_cols,
+                           "step": "diaf_factor + one diaf_apply" if do_apply else "diaf_factor",
+                           "bucket_cols": bucket_cols, "tie_tol": w.tie_tol,
                            "parallelism": f"replicas x{world}"},
                 "setup_ms": float(np.mean(total_ms)), "numeric_pass_ms": float(np.mean(numeric_ms)),
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},

@@ -78,8 +78,8 @@ enum {
   DIAF_FLAG_NONFINITE = 16,      /* NaN or Inf in w_j, v_j or res_j */
   DIAF_FLAG_EMPTY = 32,          /* k_j = 0 (empty W column) */
   DIAF_FLAG_FP64_FALLBACK = 64   /* mixed precision: the column was computed by the FP64 path (an FP32
-                                    leverage decision within its error bound, or a tile too ill-conditioned
-                                    for FP32 factors) */
+                                    leverage decision within its error bound, a tile too ill-conditioned
+                                    for FP32 factors, or a large tile: k_j > 32 or m_j > 64) */
 };
 
 typedef struct {
@@ -154,8 +154,8 @@ diaf_status diaf_factor_info_get(const diaf_factors* F, diaf_factor_info* info);
 diaf_status diaf_factor_timings(const diaf_factors* F, float* ms, int32_t nms);
 
 /* Mixed precision: the number of columns per size bucket that the FP64 path
- * computed (flag DIAF_FLAG_FP64_FALLBACK); zeros for the FP64 form.  Waits for
- * F's stream.  nb >= n_buckets. */
+ * computed (flag DIAF_FLAG_FP64_FALLBACK; every column of the large-tile
+ * bucket); zeros for the FP64 form.  Waits for F's stream.  nb >= n_buckets. */
 diaf_status diaf_factor_fallbacks(const diaf_factors* F, int32_t* counts, int32_t nb);
 
 /* Number of CUDA kernels this library has launched in this process. */

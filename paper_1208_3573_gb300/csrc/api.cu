@@ -115,6 +115,7 @@ diaf_status diaf_factor_fallbacks(const diaf_factors* F, int32_t* counts, int32_
   if (!F->fb_counts) return DIAF_OK;
   DIAF_CU(cudaMemcpyAsync(counts, F->fb_counts, sizeof(int32_t) * kNumBuckets, cudaMemcpyDeviceToHost, F->stream));
   DIAF_CU(cudaStreamSynchronize(F->stream));
+  counts[kNumBuckets - 1] = F->info.bucket_cols[kNumBuckets - 1];  // large tiles always take the FP64 path
   return DIAF_OK;
 }
 
@@ -312,7 +313,18 @@ diaf_status diaf_factor(const diaf_csc* A, const diaf_pattern* PW, const diaf_vs
     ca.extra_flags = 0;
     DIAF_CU(cudaEventRecord(F->ev[3 + 2 * b], s));
     cudaError_t e;
-    if (mixed) {
+    if (b == kNumBuckets - 1) {
+      // large tiles: one CTA per column, FP64 in both precisions (tiles in scratch slabs)
+      CtaScratch cs{};
+      const int mk = h_stats[1] > h_stats[0] ? h_stats[1] : h_stats[0];
+      cs.ldm = (mk + 31) / 32 * 32;
+      cs.kcap = h_stats[0] > 0 ? h_stats[0] : 1;
+      const int grid = cta_columns_grid(A->dtype, alg, cs.ldm, h_bc[b]);
+      if (grid <= 0) return fail(DIAF_EUNSUPPORTED, "large-tile kernel does not fit this tile size");
+      DIAF_CU(pool.get((char**)&cs.slab, (size_t)grid * 2 * cs.ldm * cs.kcap * esz));
+      ca.extra_flags = mixed ? DIAF_FLAG_FP64_FALLBACK : 0;
+      e = launch_columns_cta(A->dtype, alg, ca, cs, grid, s);
+    } else if (mixed) {
       ca.fb_list = fb_list + (size_t)b * n;
       ca.fb_count = fb_count + b;
       e = cplx ? launch_columns_mixed_c64(b, alg, ca, h_bc[b], s) : launch_columns_mixed_f32(b, alg, ca, h_bc[b], s);

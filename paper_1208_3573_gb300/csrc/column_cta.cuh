@@ -1,0 +1,497 @@
+// Per-column kernel for large tiles (size bucket 2: k_j <= 64, m_j <= 1024),
+// FP64 (complex128), one CTA of kCtaThreads threads per column.  Same steps
+// as the warp kernel (gather, Householder QR, leverage keys, V rule, DIAF-S
+// or DIAF-Q, phase, residual, scatter); the two tiles live in a per-CTA slab
+// of global scratch (L2-resident), the k x k factors in shared memory.
+#pragma once
+
+#include "column.cuh"
+
+constexpr int kCtaThreads = 256;
+constexpr int kCtaWarps = kCtaThreads / 32;
+constexpr int kCtaKmax = 64;
+
+struct CtaScratch {
+  void* slab;     // per CTA: Ts then Tw, each ldm x kcap scalars
+  int ldm;        // leading dimension (>= every m_j, k_j of the bucket)
+  int kcap;       // columns per tile (>= every k_j of the bucket)
+};
+
+// ----------------------------------------------------------------- block reductions
+template <class T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  T s = red[0];
+  for (int w = 1; w < kCtaWarps; ++w) s += red[w];
+  return s;
+}
+template <class T>
+__device__ __forceinline__ T block_max(T v, T* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  T s = red[0];
+  for (int w = 1; w < kCtaWarps; ++w) s = red[w] > s ? red[w] : s;
+  return s;
+}
+template <class T>
+__device__ __forceinline__ T block_min(T v, T* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_min(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  T s = red[0];
+  for (int w = 1; w < kCtaWarps; ++w) s = red[w] < s ? red[w] : s;
+  return s;
+}
+
+// Householder QR of the m x k tile T (leading dimension ld, global memory):
+// the norm of column c by a block reduction, then warp w updates the
+// trailing columns q = c+1+w, c+1+w+kCtaWarps, ... (dot product by a warp
+// reduction over the rows).
+template <class S>
+__device__ void cta_householder_qr(S* T, int ld, int m, int k, RealOf<S>* redR, S* bcast) {
+  using R = RealOf<S>;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int p = m < k ? m : k;
+  for (int c = 0; c < p; ++c) {
+    S* tc = T + (size_t)c * ld;
+    R part = R(0);
+    for (int r = c + tid; r < m; r += kCtaThreads) part += sc_abs2(tc[r]);
+    const R nrm2 = block_sum(part, redR);
+    if (nrm2 == R(0)) continue;  // uniform
+    const S alpha = tc[c];
+    const R ax = sc_abs(alpha), nrm = sqrt(nrm2);
+    const S ph = sc_unit(alpha);
+    const S beta = -(nrm * ph);
+    const S u0 = (ax + nrm) * ph;
+    const R two_uu = R(1) / (nrm * (nrm + ax));
+    for (int q = c + 1 + warp; q < k; q += kCtaWarps) {
+      S* tq = T + (size_t)q * ld;
+      S d = sc_zero<S>();
+      for (int r = c + lane; r < m; r += 32) d += sc_cmul(r == c ? u0 : tc[r], tq[r]);
+      const S f = two_uu * warp_sum(d);
+      for (int r = c + lane; r < m; r += 32) tq[r] -= f * (r == c ? u0 : tc[r]);
+    }
+    __syncthreads();
+    for (int r = c + tid; r < m; r += kCtaThreads) tc[r] = (r == c) ? beta : sc_zero<S>();
+    __syncthreads();
+  }
+  (void)bcast;
+}
+
+// One-sided Jacobi on the p x q matrix G (shared memory, leading dimension
+// LDG) with V (q x q, leading dimension LDV): the same rotation as
+// warp_jacobi, the q/2 pairs of a round spread over the CTA (LPP threads per
+// pair), a barrier between rounds.
+template <class S, int LDG, int LDV>
+__device__ int cta_jacobi(S* G, int p, int q, S* V, RealOf<S>* redR) {
+  using R = RealOf<S>;
+  constexpr int LPP = kCtaThreads / (kCtaKmax / 2);  // 8 threads per pair
+  const int tid = threadIdx.x;
+  for (int i = tid; i < q * q; i += kCtaThreads) {
+    int r = i % q, c = i / q;
+    V[r + c * LDV] = (r == c) ? sc_real_s<S>(R(1)) : sc_zero<S>();
+  }
+  R part = R(0);
+  for (int i = tid; i < p * q; i += kCtaThreads) part += sc_abs2(G[(i % p) + (i / p) * LDG]);
+  const R nf2 = block_sum(part, redR);
+  const R tol = R(p > 1 ? p : 1) * eps_of<R>();
+  const R tol2 = tol * tol;
+  const R tiny = tol2 * nf2;
+  __syncthreads();
+  if (q < 2) return 1;
+  const int qq = (q + 1) & ~1;
+  const int npairs = qq / 2;
+  const int grp = tid / LPP, sub = tid % LPP;
+  for (int sweep = 1; sweep <= kMaxSweeps; ++sweep) {
+    int rotated = 0;
+    for (int rnd = 0; rnd < qq - 1; ++rnd) {
+      int a = -1, b = -1;
+      if (grp < npairs) {
+        int pa = grp, pb = qq - 1 - grp;
+        a = pa == 0 ? 0 : 1 + (pa - 1 + rnd) % (qq - 1);
+        b = 1 + (pb - 1 + rnd) % (qq - 1);
+        if (a > b) { int t = a; a = b; b = t; }
+        if (b >= q) a = -1;
+      }
+      const bool act = a >= 0;
+      R al = R(0), be = R(0);
+      S ga = sc_zero<S>();
+      if (act) {
+        const S* ca = G + a * LDG;
+        const S* cb = G + b * LDG;
+        for (int i = sub; i < p; i += LPP) {
+          S x = ca[i], y = cb[i];
+          al += sc_abs2(x);
+          be += sc_abs2(y);
+          ga += sc_cmul(x, y);
+        }
+      }
+      al = group_sum<LPP>(al);
+      be = group_sum<LPP>(be);
+      ga = group_sum<LPP>(ga);
+      const R ag2 = sc_abs2(ga);
+      const bool rot = act && al > tiny && be > tiny && ag2 > R(0) && ag2 > tol2 * (al * be);
+      if (rot) {
+        rotated = 1;
+        R ag;
+        S eph;
+        if constexpr (ScalarInfo<S>::cplx) {
+          R rinv = rsqrt_r(ag2);
+          ag = ag2 * rinv;
+          eph = rinv * sc_conj(ga);
+        } else {
+          ag = sc_abs(ga);
+          eph = sc_unit(ga);
+        }
+        const R d = be - al;
+        const R t = copysign(R(2) * ag, d) / (fabs(d) + sqrt(d * d + R(4) * ag2));
+        const R cs = rsqrt_r(R(1) + t * t), sn = cs * t;
+        S* ca = G + a * LDG;
+        S* cb = G + b * LDG;
+        for (int i = sub; i < p; i += LPP) {
+          S x = ca[i], y = eph * cb[i];
+          ca[i] = cs * x - sn * y;
+          cb[i] = sn * x + cs * y;
+        }
+        S* va = V + a * LDV;
+        S* vb = V + b * LDV;
+        for (int i = sub; i < q; i += LPP) {
+          S x = va[i], y = eph * vb[i];
+          va[i] = cs * x - sn * y;
+          vb[i] = sn * x + cs * y;
+        }
+      }
+      __syncthreads();
+    }
+    if (!__syncthreads_or(rotated)) return sweep;
+  }
+  return -1;
+}
+
+template <class S>
+struct CtaSmem {
+  static constexpr int KP = kCtaKmax + 1;  // padded leading dimension of the k x k matrices
+  static constexpr size_t bytes(int mcap) {
+    return sizeof(S) * (2 * KP * kCtaKmax + 2 * kCtaKmax + mcap + kCtaKmax * KP) +
+           sizeof(double) * (mcap + kCtaKmax + 2 * kCtaWarps) + sizeof(int32_t) * (5 * mcap + 2 * kCtaKmax + 8 + 2);
+  }
+};
+
+template <class S, int ALG>
+__device__ void solve_column_cta(const ColArgs& a, const CtaScratch& sc, int j, unsigned char* smem) {
+  using R = RealOf<S>;
+  using L = CtaSmem<S>;
+  constexpr int KP = L::KP;
+  const int tid = threadIdx.x;
+  const int mcap = sc.ldm;
+  S* Rs = reinterpret_cast<S*>(smem);   // R of T, then R-hat (KP x KMAX)
+  S* Vj = Rs + KP * kCtaKmax;           // Jacobi V
+  S* wv = Vj + KP * kCtaKmax;           // w
+  S* rinv = wv + kCtaKmax;              // reciprocal diagonal
+  S* vv = rinv + kCtaKmax;              // v (mcap)
+  S* G = vv + mcap;                     // DIAF-Q: Q_I (l <= 64 rows, KP leading dimension)
+  double* hk = reinterpret_cast<double*>(G + kCtaKmax * KP);
+  double* sig = hk + mcap;
+  double* red = sig + kCtaKmax;         // 2 x kCtaWarps
+  int32_t* ibase = reinterpret_cast<int32_t*>(red + 2 * kCtaWarps);
+  int32_t* rs = ibase;
+  int32_t* inI = rs + mcap;
+  int32_t* pick = inI + mcap;
+  int32_t* Is = pick + mcap;
+  int32_t* Iloc = Is + mcap;
+  int32_t* cst = Iloc + mcap;
+  int32_t* coff = cst + kCtaKmax;
+  int32_t* misc = coff + kCtaKmax;      // [0] jpos, [1] count, [2..] warp counts
+  R* redR = reinterpret_cast<R*>(red);
+
+  S* Ts = reinterpret_cast<S*>(sc.slab) + (size_t)blockIdx.x * 2 * sc.ldm * sc.kcap;
+  S* Tw = Ts + (size_t)sc.ldm * sc.kcap;
+  const int ld = sc.ldm;
+
+  const int k = a.Wcp[j + 1] - a.Wcp[j];
+  const int m = a.m[j];
+  const int l = a.l[j];
+  const int me = m > k ? m : k;
+  const int32_t* J = a.Wri + a.Wcp[j];
+  const int32_t* Rj = a.rows + a.Eoff[j];
+  const S* Av = reinterpret_cast<const S*>(a.Av);
+  uint32_t flags = 0;
+
+  // ---- gather
+  for (int r = tid; r < mcap; r += kCtaThreads) {
+    rs[r] = r < m ? Rj[r] : INT_MAX;
+    inI[r] = -1;
+    pick[r] = 0;
+  }
+  for (size_t i = tid; i < (size_t)me * k; i += kCtaThreads) Ts[(i % me) + (i / me) * ld] = sc_zero<S>();
+  if (tid == 0) {
+    int e = 0;
+    for (int q = 0; q < k; ++q) {
+      int c = J[q];
+      cst[q] = a.Acp[c];
+      coff[q] = e;
+      e += a.Acp[c + 1] - a.Acp[c];
+    }
+    misc[1] = e;
+  }
+  __syncthreads();
+  const int E = misc[1];
+  for (int e = tid; e < E; e += kCtaThreads) {
+    int q = upper_bound_i32(coff, k, e) - 1;
+    int p = cst[q] + (e - coff[q]);
+    int r = lower_bound_i32(rs, m, a.Ari[p]);
+    Ts[r + (size_t)q * ld] = Av[p];
+  }
+  __syncthreads();
+
+  // ---- QR of T, keys, I_j
+  if (k > 0) {
+    for (size_t i = tid; i < (size_t)me * k; i += kCtaThreads) Tw[(i % me) + (i / me) * ld] = Ts[(i % me) + (i / me) * ld];
+    __syncthreads();
+    cta_householder_qr<S>(Tw, ld, me, k, redR, nullptr);
+    for (int i = tid; i < k * k; i += kCtaThreads) {
+      int r = i % k, c = i / k;
+      Rs[r + c * KP] = (r <= c) ? Tw[r + (size_t)c * ld] : sc_zero<S>();
+    }
+    __syncthreads();
+  }
+  R part = R(0);
+  for (int c = tid; c < k; c += kCtaThreads) part = dmax(part, sc_abs(Rs[c + c * KP]));
+  const R rdmax = block_max(part, redR);
+  const R piv = R(1e-14) * rdmax;
+  for (int c = tid; c < k; c += kCtaThreads) rinv[c] = sc_recip_or_zero(Rs[c + c * KP], piv);
+  __syncthreads();
+  if (k > 0 && (a.rule != DIAF_RULE_FIXED || ALG == DIAF_ALG_Q)) {
+    for (int r = tid; r < m; r += kCtaThreads) {  // Q = T R^-1 by rows, into Tw
+      R h = R(0);
+      for (int c = 0; c < k; ++c) {
+        S acc = Ts[r + (size_t)c * ld];
+        for (int p2 = 0; p2 < c; ++p2) acc -= Tw[r + (size_t)p2 * ld] * Rs[p2 + c * KP];
+        S z = acc * rinv[c];
+        Tw[r + (size_t)c * ld] = z;
+        h += sc_abs2(z);
+      }
+      hk[r] = (double)h;
+    }
+    __syncthreads();
+  }
+  if (a.rule != DIAF_RULE_FIXED) {
+    const int s = l - 1;
+    for (int t = 0; t < s; ++t) {
+      double hm = -DBL_MAX;
+      for (int r = tid; r < m; r += kCtaThreads)
+        if (!pick[r] && admissible_row(a.rule, rs[r], j)) hm = dmax(hm, hk[r]);
+      hm = block_max(hm, red);
+      const double thr = hm - a.tie_tol;
+      int best = INT_MAX;
+      for (int r = tid; r < m; r += kCtaThreads)
+        if (!pick[r] && admissible_row(a.rule, rs[r], j) && hk[r] >= thr) best = dmin(best, r);
+      best = block_min(best, reinterpret_cast<int*>(red));
+      if (tid == 0 && best < m) pick[best] = 1;
+      __syncthreads();
+    }
+  }
+  // I_j
+  if (tid == 0) {
+    misc[0] = -1;
+    int cnt = 0;
+    if (a.rule == DIAF_RULE_FIXED) {
+      const int32_t* Vf = a.Vfri + a.Vfcp[j];
+      for (int t = 0; t < l; ++t) {
+        int row = Vf[t];
+        int r = lower_bound_i32(rs, m, row);
+        int loc = (r < m && rs[r] == row) ? r : -1;
+        Is[t] = row;
+        Iloc[t] = loc;
+        if (loc >= 0) inI[loc] = t;
+        if (row == j) misc[0] = t;
+      }
+    } else {
+      bool placed = false;
+      for (int r = 0; r < m; ++r) {
+        if (!placed && !a.jin[j] && rs[r] > j) { Is[cnt] = j; Iloc[cnt] = -1; misc[0] = cnt; ++cnt; placed = true; }
+        if (pick[r] || rs[r] == j) {
+          Is[cnt] = rs[r];
+          Iloc[cnt] = r;
+          inI[r] = cnt;
+          if (rs[r] == j) misc[0] = cnt;
+          ++cnt;
+        }
+      }
+      if (!placed && !a.jin[j]) { Is[cnt] = j; Iloc[cnt] = -1; misc[0] = cnt; ++cnt; }
+    }
+  }
+  __syncthreads();
+  const int jpos = misc[0];
+  for (int t = tid; t < l; t += kCtaThreads) vv[t] = sc_zero<S>();
+  for (int q = tid; q < k; q += kCtaThreads) wv[q] = sc_zero<S>();
+  __syncthreads();
+
+  if (k == 0) {
+    flags |= DIAF_FLAG_EMPTY;
+    if (ALG == DIAF_ALG_Q) {
+      if (tid == 0) vv[jpos >= 0 ? jpos : 0] = sc_real_s<S>(R(1));
+      flags |= DIAF_FLAG_DEGENERATE;
+    } else {
+      flags |= DIAF_FLAG_RANK_DEFICIENT;
+    }
+    __syncthreads();
+  } else if (ALG == DIAF_ALG_S) {
+    for (size_t i = tid; i < (size_t)me * k; i += kCtaThreads) {
+      int r = i % me, c = i / me;
+      Tw[r + (size_t)c * ld] = (r < m && inI[r] >= 0) ? sc_zero<S>() : Ts[r + (size_t)c * ld];
+    }
+    __syncthreads();
+    cta_householder_qr<S>(Tw, ld, me, k, redR, nullptr);
+    for (int i = tid; i < k * k; i += kCtaThreads) {
+      int r = i % k, c = i / k;
+      Rs[r + c * KP] = (r <= c) ? Tw[r + (size_t)c * ld] : sc_zero<S>();
+    }
+    __syncthreads();
+    int sw = cta_jacobi<S, KP, KP>(Rs, k, k, Vj, redR);
+    if (sw < 0) flags |= DIAF_FLAG_JACOBI_NOCONV;
+    for (int c = tid; c < k; c += kCtaThreads) {
+      R s2 = R(0);
+      for (int i = 0; i < k; ++i) s2 += sc_abs2(Rs[i + c * KP]);
+      sig[c] = sqrt((double)s2);
+    }
+    __syncthreads();
+    int imin = 0;
+    double smin = sig[0], smax = sig[0];
+    for (int c = 1; c < k; ++c) {
+      if (sig[c] < smin) { smin = sig[c]; imin = c; }
+      smax = dmax(smax, sig[c]);
+    }
+    double snext = INFINITY;
+    for (int c = 0; c < k; ++c) if (c != imin) snext = dmin(snext, sig[c]);
+    int inrows = 0;
+    for (int t = 0; t < l; ++t) inrows += (Iloc[t] >= 0);
+    if (smin <= 1e-14 * smax || m - inrows < k) flags |= DIAF_FLAG_RANK_DEFICIENT;
+    if (k > 1 && (snext - smin) <= 1e-6 * smax) flags |= DIAF_FLAG_DEGENERATE;
+    for (int q = tid; q < k; q += kCtaThreads) wv[q] = Vj[q + imin * KP];
+    __syncthreads();
+    for (int t = tid; t < l; t += kCtaThreads) {
+      S s2 = sc_zero<S>();
+      int r = Iloc[t];
+      if (r >= 0)
+        for (int q = 0; q < k; ++q) s2 += Ts[r + (size_t)q * ld] * wv[q];
+      vv[t] = s2;
+    }
+    __syncthreads();
+  } else {
+    // DIAF-Q: Q_I (rows I_j of Q, in Tw) into G, Jacobi, v, w = sigma R^-1 u
+    for (int i = tid; i < l * k; i += kCtaThreads) {
+      int t = i % l, c = i / l;
+      int r = Iloc[t];
+      G[t + c * KP] = r >= 0 ? Tw[r + (size_t)c * ld] : sc_zero<S>();
+    }
+    __syncthreads();
+    int sw = cta_jacobi<S, KP, KP>(G, l, k, Vj, redR);
+    if (sw < 0) flags |= DIAF_FLAG_JACOBI_NOCONV;
+    for (int c = tid; c < k; c += kCtaThreads) {
+      R s2 = R(0);
+      for (int i = 0; i < l; ++i) s2 += sc_abs2(G[i + c * KP]);
+      sig[c] = sqrt((double)s2);
+    }
+    __syncthreads();
+    int imax = 0;
+    double smax = sig[0];
+    for (int c = 1; c < k; ++c) if (sig[c] > smax) { smax = sig[c]; imax = c; }
+    double snext = 0.0;
+    for (int c = 0; c < k; ++c) if (c != imax) snext = dmax(snext, sig[c]);
+    if (smax == 0.0 || (k > 1 && (smax - snext) <= 1e-6 * smax)) flags |= DIAF_FLAG_DEGENERATE;
+    if (smax > 0.0) {
+      const R inv = R(1) / R(smax);
+      for (int t = tid; t < l; t += kCtaThreads) vv[t] = inv * G[t + imax * KP];
+    } else if (tid == 0) {
+      vv[jpos >= 0 ? jpos : 0] = sc_real_s<S>(R(1));
+    }
+    bool rd = false;
+    for (int c = 0; c < k; ++c) rd |= !(sc_abs(Rs[c + c * KP]) > piv);
+    if (rd) flags |= DIAF_FLAG_RANK_DEFICIENT;
+    if (tid == 0) {  // back substitution R w = sigma u
+      for (int c = k - 1; c >= 0; --c) {
+        S acc = R(smax) * Vj[c + imax * KP];
+        for (int t = c + 1; t < k; ++t) acc -= Rs[c + t * KP] * wv[t];
+        wv[c] = acc * rinv[c];
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- phase, residual, scatter
+  if (k > 0 || ALG == DIAF_ALG_Q) {
+    S ph = sc_real_s<S>(R(1));
+    R vjj = jpos >= 0 ? sc_abs(vv[jpos]) : R(0);
+    R vn2 = R(0);
+    for (int t = 0; t < l; ++t) vn2 += sc_abs2(vv[t]);
+    if (jpos >= 0 && vjj > R(64) * eps_of<R>() * sqrt(vn2)) {
+      ph = (R(1) / vjj) * sc_conj(vv[jpos]);
+    } else {
+      flags |= DIAF_FLAG_VJJ_ZERO;
+      R amx = R(0);
+      int imx = -1;
+      for (int q = 0; q < k; ++q) {
+        R aq = sc_abs(wv[q]);
+        if (aq > amx) { amx = aq; imx = q; }
+      }
+      if (imx >= 0) ph = (R(1) / amx) * sc_conj(wv[imx]);
+    }
+    __syncthreads();
+    for (int q = tid; q < k; q += kCtaThreads) wv[q] = ph * wv[q];
+    for (int t = tid; t < l; t += kCtaThreads) vv[t] = ph * vv[t];
+    __syncthreads();
+  }
+  R r2 = R(0);
+  for (int r = tid; r < m; r += kCtaThreads) {
+    S s2 = sc_zero<S>();
+    for (int q = 0; q < k; ++q) s2 += Ts[r + (size_t)q * ld] * wv[q];
+    if (inI[r] >= 0) s2 -= vv[inI[r]];
+    r2 += sc_abs2(s2);
+  }
+  for (int t = tid; t < l; t += kCtaThreads)
+    if (Iloc[t] < 0) r2 += sc_abs2(vv[t]);
+  r2 = block_sum(r2, redR);
+  const double resj = sqrt((double)r2);
+  int bad = !isfinite(resj);
+  for (int q = tid; q < k; q += kCtaThreads) bad |= !(isfinite(sc_real(wv[q])) && isfinite(sc_imag(wv[q])));
+  for (int t = tid; t < l; t += kCtaThreads) bad |= !(isfinite(sc_real(vv[t])) && isfinite(sc_imag(vv[t])));
+  if (__syncthreads_or(bad)) flags |= DIAF_FLAG_NONFINITE;
+  S* Wout = reinterpret_cast<S*>(a.Wv) + a.Wcp[j];
+  for (int q = tid; q < k; q += kCtaThreads) Wout[q] = wv[q];
+  const int v0 = a.Vcp[j];
+  S* Vout = reinterpret_cast<S*>(a.Vv) + v0;
+  for (int t = tid; t < l; t += kCtaThreads) {
+    a.Vri[v0 + t] = Is[t];
+    Vout[t] = vv[t];
+  }
+  if (tid == 0) {
+    a.res[j] = resj;
+    a.flags[j] = flags | a.extra_flags;
+  }
+  __syncthreads();
+}
+
+template <class S, int ALG>
+__global__ void __launch_bounds__(kCtaThreads) column_cta_kernel(ColArgs a, CtaScratch sc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int idx_s;
+  const int count = *a.list_count;
+  while (true) {
+    if (threadIdx.x == 0) idx_s = atomicAdd(a.work_counter, 1);
+    __syncthreads();
+    const int idx = idx_s;
+    __syncthreads();
+    if (idx >= count) break;
+    solve_column_cta<S, ALG>(a, sc, a.list[idx], smem_raw);
+  }
+}

@@ -78,7 +78,11 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
   const int me = m > k ? m : k;
   uint32_t flags = 0;
 
-  auto hand_back = [&]() {
+  auto hand_back = [&](int why) {
+#ifdef DIAF_PHASE_TIMING
+    if (lane == 0 && a.phase) atomicAdd(&a.phase[24 + why], 1ull);
+#endif
+    (void)why;
     if (lane == 0) {
       int pos = atomicAdd(a.fb_count, 1);
       a.fb_list[pos] = j;
@@ -86,7 +90,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     __syncwarp();
   };
   if (k == 0) {  // trivial columns: the FP64 kernel has the conventions
-    hand_back();
+    hand_back(0);
     return;
   }
 
@@ -119,7 +123,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     kap = fmaxf(kap, d > 0.0f ? (float)cn[c] / d : INFINITY);
   }
   kap = warp_max(kap);
-  if (!(kap <= kMixedKappaMax)) { hand_back(); return; }
+  if (!(kap <= kMixedKappaMax)) { hand_back(1); return; }
   warp_leverage_rows<S, SD, MMAX, KMAX>(Ts, Rs, Tw, hk, rinv, m, k, R(0), lane);
   DIAF_PHASE(3);
   if (a.rule != DIAF_RULE_FIXED) {
@@ -127,7 +131,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     // bound on the FP32 key error: backward error of the FP32 QR and of the
     // row solves, amplified by the (column-scaled) conditioning of T
     const double delta = 8.0 * (m + k) * (double)FLT_EPSILON * (double)kap;
-    if (l > 1 && margin <= 2.0 * delta) { hand_back(); return; }
+    if (l > 1 && margin <= 2.0 * delta) { hand_back(2); return; }
   }
   const int jpos = build_I(a, j, m, l, ix, lane);
   for (int t = lane; t < l; t += DIAF_WARP) vv[t] = sc_zero<SD>();
@@ -161,7 +165,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
       kh = fmaxf(kh, d > 0.0f ? (float)cn[c] / d : INFINITY);
     }
     kh = warp_max(kh);
-    if (!(kh <= kMixedKappaMax)) { hand_back(); return; }
+    if (!(kh <= kMixedKappaMax)) { hand_back(3); return; }
     int sw = warp_jacobi<S, KMAX, KMAX, KMAX>(Rs, k, k, Vj, lane);
     if (sw < 0) flags |= DIAF_FLAG_JACOBI_NOCONV;
 #ifdef DIAF_PHASE_TIMING
@@ -181,7 +185,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     // ---- FP64 correction in the FP32 singular basis V (columns of Vj)
     double gap = INFINITY;
     for (int c = 0; c < k; ++c) if (c != imin) gap = dmin(gap, sig[c] * sig[c] - smin * smin);
-    if (k > 1 && gap <= 1e-5 * smax * smax) { hand_back(); return; }
+    if (k > 1 && gap <= 1e-5 * smax * smax) { hand_back(4); return; }
     const int iters = (k > 1 && gap < 1e-2 * smax * smax) ? 2 : 1;
     SD* cc = rinvD;  // correction coefficients (KMAX)
     SD x = lane < k ? sc_cast<SD>(Vj[lane + imin * KMAX]) : sc_zero<SD>();
@@ -238,7 +242,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     __syncwarp();
   } else {
     // ---- FP32 Jacobi on Q_I (FP32 rows of Q = T R^-1 in Tw)
-    if (l > kRRMax) { hand_back(); return; }
+    if (l > kRRMax) { hand_back(5); return; }
     compact_rows<S, MMAX>(Tw, ix.Iloc, l, k, lane);
     int sw = warp_jacobi<S, MMAX, KMAX, KMAX>(Tw, l, k, Vj, lane);
     if (sw < 0) flags |= DIAF_FLAG_JACOBI_NOCONV;
@@ -248,7 +252,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     for (int c = 1; c < k; ++c) if (sig[c] > smax) { smax = sig[c]; imax = c; }
     double snext = 0.0;
     for (int c = 0; c < k; ++c) if (c != imax) snext = dmax(snext, sig[c]);
-    if (!(smax > 0.0)) { hand_back(); return; }
+    if (!(smax > 0.0)) { hand_back(6); return; }
     if (k > 1 && (smax - snext) <= 1e-6 * smax) flags |= DIAF_FLAG_DEGENERATE;
     for (int t = lane; t < l; t += DIAF_WARP) vv[t] = sc_cast<SD>(Tw[t + imax * MMAX]);
     for (int c = lane; c < k; c += DIAF_WARP) rinvD[c] = sc_recip_or_zero(sc_cast<SD>(Rs[c + c * KMAX]), 0.0);

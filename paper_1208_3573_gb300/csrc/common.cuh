@@ -162,6 +162,16 @@ __host__ __device__ __forceinline__ int ceil_div(int a, int b) { return (a + b -
 template <class T> __device__ __forceinline__ T dmin(T a, T b) { return a < b ? a : b; }
 template <class T> __device__ __forceinline__ T dmax(T a, T b) { return a > b ? a : b; }
 
+// first index with a[i] > key in a sorted int array
+__device__ __forceinline__ int upper_bound_i32(const int32_t* a, int n, int key) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] <= key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
 // lower_bound in a sorted int array
 __device__ __forceinline__ int lower_bound_i32(const int32_t* a, int n, int key) {
   int lo = 0, hi = n;

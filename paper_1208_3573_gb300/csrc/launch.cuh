@@ -2,6 +2,7 @@
 // value type and precision so they compile in parallel.
 #pragma once
 
+#include "column_cta.cuh"
 #include "column_mixed.cuh"
 
 // Launches the numeric pass for size bucket `bucket` over the listed columns
@@ -12,6 +13,11 @@ cudaError_t launch_columns_f64(int bucket, int alg, const ColArgs& a, int count_
 cudaError_t launch_columns_c128(int bucket, int alg, const ColArgs& a, int count_hint, cudaStream_t s);
 cudaError_t launch_columns_mixed_f32(int bucket, int alg, const ColArgs& a, int count_hint, cudaStream_t s);
 cudaError_t launch_columns_mixed_c64(int bucket, int alg, const ColArgs& a, int count_hint, cudaStream_t s);
+
+// Size bucket 2 (one CTA per column, FP64 / complex128): grid size for the
+// scratch slabs (0 on error) and the launch itself.
+int cta_columns_grid(int dtype, int alg, int ldm, int count);
+cudaError_t launch_columns_cta(int dtype, int alg, const ColArgs& a, const CtaScratch& sc, int grid, cudaStream_t s);
 
 // Persistent grid sized by occupancy; `per_warp` bytes of shared memory per warp.
 template <class Kern>

@@ -29,12 +29,12 @@ def D():
 
 
 @pytest.mark.parametrize("alg", ["S", "Q"])
-@pytest.mark.parametrize("name", ["convdiff32", "convdiff48_A2", "helmholtz40", "lognormal16"])
+@pytest.mark.parametrize("name", ["convdiff32", "convdiff48_A2", "helmholtz40", "lognormal16", "powerlaw6k"])
 def test_mixed_parity_workloads(D, name, alg):
     w = make_workload(name)
-    F = run_gpu(D, w.A, w.PW, w.vrule, w.budget, alg=alg, prec="mixed32")
+    F = run_gpu(D, w.A, w.PW, w.vrule, w.budget, alg=alg, prec="mixed32", tie_tol=w.tie_tol)
     g = host_factors(F)
-    o = O.factor(w.A, w.PW, w.vrule, w.budget, alg=alg)
+    o = O.factor(w.A, w.PW, w.vrule, w.budget, alg=alg, tie_tol=w.tie_tol)
     rep = compare(g, o, w.A, w.PW, alg, rtol_res=RTOL_RES, vec_tol=VEC_TOL, mixed=True, floor_rel=1e-10)
     assert_parity(rep)
     fb = F.fallbacks()
@@ -44,9 +44,9 @@ def test_mixed_parity_workloads(D, name, alg):
 @pytest.mark.parametrize("alg", ["S", "Q"])
 def test_mixed_parity_full_size_convdiff256(D, alg):
     w = make_workload("convdiff256_A2")
-    F = run_gpu(D, w.A, w.PW, w.vrule, w.budget, alg=alg, prec="mixed32")
+    F = run_gpu(D, w.A, w.PW, w.vrule, w.budget, alg=alg, prec="mixed32", tie_tol=w.tie_tol)
     g = host_factors(F)
-    o = O.factor(w.A, w.PW, w.vrule, w.budget, alg=alg)
+    o = O.factor(w.A, w.PW, w.vrule, w.budget, alg=alg, tie_tol=w.tie_tol)
     rep = compare(g, o, w.A, w.PW, alg, rtol_res=RTOL_RES, vec_tol=VEC_TOL, mixed=True, floor_rel=1e-10)
     assert_parity(rep)
     # the FP32 path decides almost every column of this workload itself

@@ -29,23 +29,23 @@ def D():
     return diaf
 
 
-def run_gpu(D, A, PW, vrule=O.RULE_UPPER, budget=None, Vfixed=None, alg="S", prec="fp64"):
+def run_gpu(D, A, PW, vrule=O.RULE_UPPER, budget=None, Vfixed=None, alg="S", prec="fp64", tie_tol=O.TIE_TOL):
     dA = D.DeviceCSC.from_host(A)
     dP = D.DeviceCSC.from_host(PW)
     dB = None if budget is None else torch.from_numpy(np.ascontiguousarray(budget, np.int32)).cuda()
     dV = None if Vfixed is None else D.DeviceCSC.from_host(Vfixed)
-    F = D.factor(dA, dP, vrule, dB, dV, alg=alg, prec=prec)
+    F = D.factor(dA, dP, vrule, dB, dV, alg=alg, prec=prec, tie_tol=tie_tol)
     torch.cuda.synchronize()
     return F
 
 
 @pytest.mark.parametrize("alg", ["S", "Q"])
-@pytest.mark.parametrize("name", ["convdiff32", "convdiff48_A2", "helmholtz40", "lognormal16"])
+@pytest.mark.parametrize("name", ["convdiff32", "convdiff48_A2", "helmholtz40", "lognormal16", "powerlaw6k"])
 def test_parity_workloads(D, name, alg):
     w = make_workload(name)
-    F = run_gpu(D, w.A, w.PW, w.vrule, w.budget, alg=alg)
+    F = run_gpu(D, w.A, w.PW, w.vrule, w.budget, alg=alg, tie_tol=w.tie_tol)
     g = host_factors(F)
-    o = O.factor(w.A, w.PW, w.vrule, w.budget, alg=alg)
+    o = O.factor(w.A, w.PW, w.vrule, w.budget, alg=alg, tie_tol=w.tie_tol)
     assert np.array_equal(g["Vcp"], o.voff.astype(np.int32))
     rep = compare(g, o, w.A, w.PW, alg)
     assert_parity(rep)
@@ -55,9 +55,9 @@ def test_parity_workloads(D, name, alg):
 def test_parity_full_size_convdiff256(D, alg):
     """Full 65,536-column workload in the launch configuration the benchmark uses."""
     w = make_workload("convdiff256_A2")
-    F = run_gpu(D, w.A, w.PW, w.vrule, w.budget, alg=alg)
+    F = run_gpu(D, w.A, w.PW, w.vrule, w.budget, alg=alg, tie_tol=w.tie_tol)
     g = host_factors(F)
-    o = O.factor(w.A, w.PW, w.vrule, w.budget, alg=alg)
+    o = O.factor(w.A, w.PW, w.vrule, w.budget, alg=alg, tie_tol=w.tie_tol)
     rep = compare(g, o, w.A, w.PW, alg)
     assert_parity(rep)
 
@@ -76,6 +76,25 @@ def test_parity_random_fixed_and_rules(D, alg, cplx):
         o = O.factor(A, PW, vrule, budget, Vf, alg=alg)
         rep = compare(g, o, A, PW, alg)
         assert_parity(rep)
+
+
+@pytest.mark.parametrize("alg", ["S", "Q"])
+def test_parity_full_size_powerlaw_sampled(D, alg):
+    """n = 200,000 with tiles up to 626 x 60 in all three size buckets: every
+    column of the largest bucket plus a seeded sample of the others."""
+    w = make_workload("powerlaw200k")
+    F = run_gpu(D, w.A, w.PW, w.vrule, w.budget, alg=alg, tie_tol=w.tie_tol)
+    g = host_factors(F)
+    k = w.PW.counts()
+    nnz = np.diff(w.A.colptr)
+    E = np.bincount(np.repeat(np.arange(w.n), k), weights=nnz[w.PW.rowidx], minlength=w.n)
+    big = np.nonzero((k > 32) | (E > 200))[0]
+    rng = np.random.default_rng(3)
+    cols = np.unique(np.concatenate([big[:1500], rng.choice(w.n, 1500, replace=False)])).astype(np.int32)
+    o = O.factor(w.A, w.PW, w.vrule, w.budget, alg=alg, tie_tol=w.tie_tol, cols=cols)
+    rep = compare(g, o, w.A, w.PW, alg, cols=cols)
+    assert_parity(rep)
+    assert F.info.bucket_cols[2] > 0
 
 
 def test_empty_matrix(D):

@@ -176,6 +176,7 @@ def main():
     ap.add_argument("--prec", default="mixed32", choices=["fp64", "mixed32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the solve / other-form side measurements")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch tuning instead of diaf_autotune")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -204,9 +205,13 @@ def main():
     stream = torch.cuda.current_stream()
 
     do_apply = w.meta.get("apply", True)
+    tuning, tune_ms = None, None
+    if not args.no_autotune:  # once, before the warm-up (not timed)
+        tuning, tune_ms = diaf.autotune(A, PW, w.vrule, bud, alg=args.alg, prec=args.prec, tie_tol=w.tie_tol)
 
     def step(Ad, PWd, budd):
-        F = diaf.factor(Ad, PWd, w.vrule, budd, alg=args.alg, prec=args.prec, tie_tol=w.tie_tol, stream=stream)
+        F = diaf.factor(Ad, PWd, w.vrule, budd, alg=args.alg, prec=args.prec, tie_tol=w.tie_tol, stream=stream,
+                        tuning=tuning)
         if do_apply:
             F.apply(x1, y1, stream=stream)
         return F
@@ -335,6 +340,22 @@ def main():
                                     "speedup_of_mixed": (w.n / (float(np.mean(total_ms)) / 1e3)) / c64,
                                     "res_rel_diff_max": float(rel.max()), "res_rel_diff_median": float(np.median(rel)),
                                     "mixed_fp64_fallback_columns": int(sum(fb))}
+        # numeric refactorization on a fixed structure: the CUDA-graph plan replayed
+        P = diaf.Plan(A, PW, w.vrule, bud, alg=args.alg, prec=args.prec, tie_tol=w.tie_tol, tuning=tuning)
+        P.execute()
+        torch.cuda.synchronize()
+        tr = []
+        for _ in range(5):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            P.execute(stream)
+            e1.record(stream)
+            e1.synchronize()
+            tr.append(e0.elapsed_time(e1))
+        extras["graph_replay"] = {"numeric_columns_per_s": w.n / (statistics.median(tr) / 1e3),
+                                  "ms": statistics.median(tr)}
+        del P
         # the other algorithm, same workload (factor only, median of 3)
         other = "Q" if args.alg == "S" else "S"
         tt = []
@@ -357,6 +378,7 @@ def main():
                            "l2": "flushed (256 MiB write) before every timed step",
                            "step": "diaf_factor + one diaf_apply" if do_apply else "diaf_factor",
                            "bucket_cols": bucket_cols, "tie_tol": w.tie_tol,
+                           "tuning": tuning if tuning is not None else "default", "autotune_numeric_ms": tune_ms,
                            "parallelism": f"replicas x{world}"},
                 "setup_ms": float(np.mean(total_ms)), "numeric_pass_ms": float(np.mean(numeric_ms)),
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},

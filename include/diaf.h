@@ -131,6 +131,21 @@ typedef struct diaf_factors diaf_factors; /* opaque, library-owned */
 diaf_status diaf_factor(const diaf_csc* A, const diaf_pattern* PW, const diaf_vspec* V, int32_t alg,
                         int32_t prec, void* stream, diaf_factors** out);
 
+/* Launch tuning of the numeric pass (diaf_factor_tuned, diaf_plan_create,
+ * found by diaf_autotune).  Zero fields select the defaults.
+ *   m_edge0: tiles with max(m_j, k_j) <= m_edge0 (and k_j <= 16) run in size
+ *            bucket 0 (warp per column, 32-row tile); 1..32, default 32.
+ *   m_edge1: tiles up to m_edge1 rows (k_j <= 32) run in bucket 1 (warp per
+ *            column, 64-row tile); 1..64, default 64.  Larger tiles run in
+ *            bucket 2 (one 256-thread CTA per column).
+ *   warps_per_block[b]: CTA size of the warp kernels of buckets 0 and 1
+ *            (1..8; 0 = the most warps resident per SM). */
+typedef struct {
+  int32_t m_edge0;
+  int32_t m_edge1;
+  int32_t warps_per_block[2];
+} diaf_tuning;
+
 typedef struct {
   int32_t n;
   int32_t dtype;
@@ -145,6 +160,36 @@ typedef struct {
 
 /* Sizes and bucket statistics of a factorisation (host copy; no sync). */
 diaf_status diaf_factor_info_get(const diaf_factors* F, diaf_factor_info* info);
+
+/* diaf_factor with launch tuning (NULL = defaults). */
+diaf_status diaf_factor_tuned(const diaf_csc* A, const diaf_pattern* PW, const diaf_vspec* V, int32_t alg,
+                              int32_t prec, const diaf_tuning* tuning, void* stream, diaf_factors** out);
+
+/* Times the numeric pass of diaf_factor_tuned over the bucket edges and the
+ * warp kernels' CTA sizes (coordinate descent, best of two runs per point)
+ * and returns the fastest tuning and its numeric-pass time in ms.  Runs
+ * about 15 factorisations of the given problem. */
+diaf_status diaf_autotune(const diaf_csc* A, const diaf_pattern* PW, const diaf_vspec* V, int32_t alg, int32_t prec,
+                          void* stream, diaf_tuning* best, float* best_ms);
+
+/* A factorisation plan: the symbolic pass done once, the numeric pass
+ * (gather, QR, V rule, DIAF solve, scatter -- every size bucket) captured in
+ * one CUDA graph.  For repeated factorisations of matrices with the same
+ * structure (new values written into the same A->vals buffer, e.g. a
+ * time-stepping operator), diaf_plan_execute replays the graph: one launch,
+ * no host synchronisation, no allocation.  The plan keeps A's, PW's and the
+ * V specification's device arrays by pointer: they must stay valid and
+ * unchanged except A's values.  diaf_plan_create synchronises `stream`; it
+ * does not run the numeric pass. */
+typedef struct diaf_plan diaf_plan;
+diaf_status diaf_plan_create(const diaf_csc* A, const diaf_pattern* PW, const diaf_vspec* V, int32_t alg,
+                             int32_t prec, const diaf_tuning* tuning, void* stream, diaf_plan** out);
+/* Enqueues the numeric pass on `stream` (one graph launch); the plan's
+ * factors are ready when it has run.  Executions must not overlap. */
+diaf_status diaf_plan_execute(diaf_plan* P, void* stream);
+/* The plan's factors (borrowed; freed by diaf_plan_free). */
+diaf_factors* diaf_plan_factors(diaf_plan* P);
+void diaf_plan_free(diaf_plan* P);
 
 /* Timings of a factorisation from CUDA events recorded on its stream (waits
  * for them): ms[0] the whole diaf_factor call (first to last enqueued work,

@@ -131,11 +131,28 @@ diaf_status diaf_factor_timings(const diaf_factors* F, float* ms, int32_t nms) {
   return DIAF_OK;
 }
 
-diaf_status diaf_factor(const diaf_csc* A, const diaf_pattern* PW, const diaf_vspec* V, int32_t alg, int32_t prec,
-                        void* stream, diaf_factors** out) {
-  g_last_error.clear();
-  if (!out) return fail(DIAF_EINVAL, "out is NULL");
-  *out = nullptr;
+}  // extern "C"
+
+namespace {
+
+// Everything the numeric pass needs; built by symbolic_pass.
+struct NumericPlan {
+  ColArgs ca{};
+  int32_t* bucket_list = nullptr;
+  int32_t* bucket_count = nullptr;
+  int32_t* work = nullptr;      // 2 * kNumBuckets work counters
+  int32_t* fb_list = nullptr;   // mixed: columns handed to the FP64 kernels
+  int32_t* fb_count = nullptr;
+  int h_bc[kNumBuckets] = {0};
+  CtaScratch cs{};
+  int cta_grid = 0;
+  bool mixed = false, cplx = false;
+  int alg = DIAF_ALG_S, dtype = DIAF_F64, n = 0;
+  int wpb[2] = {0, 0};
+};
+
+diaf_status check_args(const diaf_csc* A, const diaf_pattern* PW, const diaf_vspec* V, int32_t alg, int32_t prec,
+                       const diaf_tuning* tuning) {
   if (!A || !PW || !V) return fail(DIAF_EINVAL, "A, PW and V must be non-NULL");
   if (alg != DIAF_ALG_Q && alg != DIAF_ALG_S) return fail(DIAF_EINVAL, "alg must be DIAF_ALG_Q or DIAF_ALG_S");
   if (prec != DIAF_PREC_FP64 && prec != DIAF_PREC_MIXED32) return fail(DIAF_EINVAL, "unknown precision");
@@ -149,15 +166,24 @@ diaf_status diaf_factor(const diaf_csc* A, const diaf_pattern* PW, const diaf_vs
   if (A->n > 0 && (!A->colptr || !PW->colptr || (A->nnz > 0 && (!A->rowidx || !A->vals)) ||
                    (PW->nnz > 0 && !PW->rowidx)))
     return fail(DIAF_EINVAL, "NULL array in A or PW");
-  diaf_status ds = check_device();
-  if (ds != DIAF_OK) return ds;
+  if (tuning) {
+    if (tuning->m_edge0 < 0 || tuning->m_edge0 > 32 || tuning->m_edge1 < 0 || tuning->m_edge1 > 64)
+      return fail(DIAF_EINVAL, "tuning: m_edge0 must be in 0..32 and m_edge1 in 0..64");
+    for (int b = 0; b < 2; ++b)
+      if (tuning->warps_per_block[b] < 0 || tuning->warps_per_block[b] > 8)
+        return fail(DIAF_EINVAL, "tuning: warps_per_block must be in 0..8");
+  }
+  return check_device();
+}
 
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+// Symbolic pass: input checks, row unions, V counts, buckets; allocates the
+// outputs into F and the numeric pass's scratch into `scratch`.  Synchronises
+// `s` (twice: after the input check and to size V).
+diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_vspec* V, int32_t alg, int32_t prec,
+                          const diaf_tuning* tuning, cudaStream_t s, diaf_factors* F, Pool& pool, NumericPlan& np) {
   const int n = A->n;
   const bool cplx = A->dtype == DIAF_C128;
   const size_t esz = cplx ? 16 : 8;
-
-  auto F = new diaf_factors();
   F->stream = s;
   cudaGetDevice(&F->device);
   F->n = n;
@@ -166,29 +192,23 @@ diaf_status diaf_factor(const diaf_csc* A, const diaf_pattern* PW, const diaf_vs
   F->prec = prec;
   F->rule = V->rule;
   F->nnz_w = PW->nnz;
-  struct Guard {
-    diaf_factors*& f;
-    bool keep = false;
-    ~Guard() { if (!keep) diaf_free(f); }
-  } guard{F};
+  np.n = n; np.alg = alg; np.dtype = A->dtype; np.cplx = cplx;
+  np.mixed = prec == DIAF_PREC_MIXED32;
+  np.wpb[0] = tuning ? tuning->warps_per_block[0] : 0;
+  np.wpb[1] = tuning ? tuning->warps_per_block[1] : 0;
 
-  for (cudaEvent_t& e : F->ev) DIAF_CU(cudaEventCreate(&e));
-  DIAF_CU(cudaEventRecord(F->ev[0], s));
-  Pool pool(s);
-  // ---- small device words
   uint32_t* status;
-  int32_t *stats, *bucket_count, *big_count, *work;
+  int32_t *stats, *big_count;
   DIAF_CU(F->alloc(&status, 1));
   F->status = status;
   DIAF_CU(pool.get(&stats, 4));
-  DIAF_CU(pool.get(&bucket_count, kNumBuckets));
+  DIAF_CU(pool.get(&np.bucket_count, kNumBuckets));
   DIAF_CU(pool.get(&big_count, 1));
-  DIAF_CU(pool.get(&work, 2 * kNumBuckets));
+  DIAF_CU(pool.get(&np.work, 2 * kNumBuckets));
   DIAF_CU(cudaMemsetAsync(status, 0, sizeof(uint32_t), s));
   DIAF_CU(cudaMemsetAsync(stats, 0, sizeof(int32_t) * 4, s));
-  DIAF_CU(cudaMemsetAsync(bucket_count, 0, sizeof(int32_t) * kNumBuckets, s));
+  DIAF_CU(cudaMemsetAsync(np.bucket_count, 0, sizeof(int32_t) * kNumBuckets, s));
   DIAF_CU(cudaMemsetAsync(big_count, 0, sizeof(int32_t), s));
-  DIAF_CU(cudaMemsetAsync(work, 0, sizeof(int32_t) * 2 * kNumBuckets, s));
 
   // ---- input checks on the device (sorted, in range)
   DIAF_CU(check_csc(n, A->colptr, A->rowidx, A->nnz, status, s));
@@ -204,6 +224,8 @@ diaf_status diaf_factor(const diaf_csc* A, const diaf_pattern* PW, const diaf_vs
   pa.Vfcp = V->rule == DIAF_RULE_FIXED ? V->fixed->colptr : nullptr;
   pa.Vfri = V->rule == DIAF_RULE_FIXED ? V->fixed->rowidx : nullptr;
   pa.budget = V->budget;
+  pa.edge_m0 = tuning && tuning->m_edge0 > 0 ? tuning->m_edge0 : 32;
+  pa.edge_m1 = tuning && tuning->m_edge1 > 0 ? tuning->m_edge1 : 64;
   int64_t* bs64;
   int32_t* bs32;
   DIAF_CU(pool.get(&pa.k, n));
@@ -212,11 +234,12 @@ diaf_status diaf_factor(const diaf_csc* A, const diaf_pattern* PW, const diaf_vs
   DIAF_CU(pool.get(&pa.m, n));
   DIAF_CU(pool.get(&pa.l, n));
   DIAF_CU(pool.get(&pa.jin, n));
-  DIAF_CU(pool.get(&pa.bucket_list, (size_t)kNumBuckets * n));
+  DIAF_CU(pool.get(&np.bucket_list, (size_t)kNumBuckets * n));
   DIAF_CU(pool.get(&pa.big_list, n));
   DIAF_CU(pool.get(&bs64, scan_blocksums_size(n)));
   DIAF_CU(pool.get(&bs32, scan_blocksums_size(n)));
-  pa.bucket_count = bucket_count;
+  pa.bucket_list = np.bucket_list;
+  pa.bucket_count = np.bucket_count;
   pa.big_count = big_count;
   pa.stats = stats;
   pa.status = status;
@@ -241,10 +264,10 @@ diaf_status diaf_factor(const diaf_csc* A, const diaf_pattern* PW, const diaf_vs
   } else {
     DIAF_CU(cudaMemsetAsync(F->Vcp, 0, sizeof(int32_t), s));
   }
-  int32_t h_nnzv = 0, h_bc[kNumBuckets] = {0}, h_stats[4] = {0};
+  int32_t h_nnzv = 0, h_stats[4] = {0};
   if (n > 0) {
     DIAF_CU(cudaMemcpyAsync(&h_nnzv, F->Vcp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    DIAF_CU(cudaMemcpyAsync(h_bc, bucket_count, sizeof(h_bc), cudaMemcpyDeviceToHost, s));
+    DIAF_CU(cudaMemcpyAsync(np.h_bc, np.bucket_count, sizeof(np.h_bc), cudaMemcpyDeviceToHost, s));
     DIAF_CU(cudaMemcpyAsync(h_stats, stats, sizeof(h_stats), cudaMemcpyDeviceToHost, s));
     DIAF_CU(cudaMemcpyAsync(&h_status, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     DIAF_CU(cudaStreamSynchronize(s));
@@ -262,7 +285,7 @@ diaf_status diaf_factor(const diaf_csc* A, const diaf_pattern* PW, const diaf_vs
   F->info.max_m = h_stats[1];
   F->info.max_l = h_stats[2];
   F->info.n_buckets = kNumBuckets;
-  for (int b = 0; b < kNumBuckets; ++b) F->info.bucket_cols[b] = h_bc[b];
+  for (int b = 0; b < kNumBuckets; ++b) F->info.bucket_cols[b] = np.h_bc[b];
 
   // ---- outputs
   DIAF_CU(F->alloc(&F->Wcp, n + 1));
@@ -276,9 +299,8 @@ diaf_status diaf_factor(const diaf_csc* A, const diaf_pattern* PW, const diaf_vs
   if (PW->nnz > 0)
     DIAF_CU(cudaMemcpyAsync(F->Wri, PW->rowidx, sizeof(int32_t) * PW->nnz, cudaMemcpyDeviceToDevice, s));
 
-  // ---- numeric pass, one launch per bucket
-  DIAF_CU(cudaEventRecord(F->ev[1], s));
-  ColArgs ca{};
+  // ---- numeric-pass arguments and scratch
+  ColArgs& ca = np.ca;
   ca.n = n;
   ca.Acp = A->colptr; ca.Ari = A->rowidx; ca.Av = A->vals;
   ca.Wcp = PW->colptr; ca.Wri = PW->rowidx;
@@ -295,66 +317,223 @@ diaf_status diaf_factor(const diaf_csc* A, const diaf_pattern* PW, const diaf_vs
   }
   ca.phase = g_phase;
 #endif
-  const bool mixed = prec == DIAF_PREC_MIXED32;
-  int32_t *fb_list = nullptr, *fb_count = nullptr;
-  if (mixed) {
-    DIAF_CU(pool.get(&fb_list, (size_t)kNumBuckets * n));
-    DIAF_CU(pool.get(&fb_count, kNumBuckets));
-    DIAF_CU(cudaMemsetAsync(fb_count, 0, sizeof(int32_t) * kNumBuckets, s));
+  if (np.mixed) {
+    DIAF_CU(pool.get(&np.fb_list, (size_t)kNumBuckets * n));
+    DIAF_CU(pool.get(&np.fb_count, kNumBuckets));
+    DIAF_CU(F->alloc(&F->fb_counts, kNumBuckets));
   }
+  const int bl = kNumBuckets - 1;
+  if (np.h_bc[bl] > 0) {
+    // large tiles: one CTA per column, FP64 in both precisions (tiles in scratch slabs)
+    const int mk = h_stats[1] > h_stats[0] ? h_stats[1] : h_stats[0];
+    np.cs.ldm = (mk + 31) / 32 * 32;
+    np.cs.kcap = h_stats[0] > 0 ? h_stats[0] : 1;
+    np.cta_grid = cta_columns_grid(A->dtype, alg, np.cs.ldm, np.h_bc[bl]);
+    if (np.cta_grid <= 0) return fail(DIAF_EUNSUPPORTED, "large-tile kernel does not fit this tile size");
+    DIAF_CU(pool.get((char**)&np.cs.slab, (size_t)np.cta_grid * 2 * np.cs.ldm * np.cs.kcap * esz));
+  }
+  return DIAF_OK;
+}
+
+// Numeric pass: work-counter resets and one launch per non-empty bucket (plus
+// the FP64 kernel over the columns the mixed kernel handed back).  Only
+// stream work: no allocation, no synchronisation (graph-capturable).
+diaf_status enqueue_numeric(diaf_factors* F, NumericPlan& np, cudaStream_t s, bool events) {
+  const int n = np.n;
+  DIAF_CU(cudaMemsetAsync(np.work, 0, sizeof(int32_t) * 2 * kNumBuckets, s));
+  if (np.mixed) DIAF_CU(cudaMemsetAsync(np.fb_count, 0, sizeof(int32_t) * kNumBuckets, s));
+  ColArgs ca = np.ca;
   auto fp64_launch = [&](int b, const ColArgs& c, int hint) {
-    return cplx ? launch_columns_c128(b, alg, c, hint, s) : launch_columns_f64(b, alg, c, hint, s);
+    const int w = b < 2 ? np.wpb[b] : 0;
+    return np.cplx ? launch_columns_c128(b, np.alg, c, hint, w, s) : launch_columns_f64(b, np.alg, c, hint, w, s);
   };
   for (int b = 0; b < kNumBuckets; ++b) {
-    if (h_bc[b] == 0) continue;
-    ca.list = pa.bucket_list + (size_t)b * n;
-    ca.list_count = bucket_count + b;
-    ca.work_counter = work + b;
+    if (np.h_bc[b] == 0) continue;
+    ca.list = np.bucket_list + (size_t)b * n;
+    ca.list_count = np.bucket_count + b;
+    ca.work_counter = np.work + b;
     ca.extra_flags = 0;
-    DIAF_CU(cudaEventRecord(F->ev[3 + 2 * b], s));
+    if (events) DIAF_CU(cudaEventRecord(F->ev[3 + 2 * b], s));
     cudaError_t e;
     if (b == kNumBuckets - 1) {
-      // large tiles: one CTA per column, FP64 in both precisions (tiles in scratch slabs)
-      CtaScratch cs{};
-      const int mk = h_stats[1] > h_stats[0] ? h_stats[1] : h_stats[0];
-      cs.ldm = (mk + 31) / 32 * 32;
-      cs.kcap = h_stats[0] > 0 ? h_stats[0] : 1;
-      const int grid = cta_columns_grid(A->dtype, alg, cs.ldm, h_bc[b]);
-      if (grid <= 0) return fail(DIAF_EUNSUPPORTED, "large-tile kernel does not fit this tile size");
-      DIAF_CU(pool.get((char**)&cs.slab, (size_t)grid * 2 * cs.ldm * cs.kcap * esz));
-      ca.extra_flags = mixed ? DIAF_FLAG_FP64_FALLBACK : 0;
-      e = launch_columns_cta(A->dtype, alg, ca, cs, grid, s);
-    } else if (mixed) {
-      ca.fb_list = fb_list + (size_t)b * n;
-      ca.fb_count = fb_count + b;
-      e = cplx ? launch_columns_mixed_c64(b, alg, ca, h_bc[b], s) : launch_columns_mixed_f32(b, alg, ca, h_bc[b], s);
+      ca.extra_flags = np.mixed ? DIAF_FLAG_FP64_FALLBACK : 0;
+      e = launch_columns_cta(np.dtype, np.alg, ca, np.cs, np.cta_grid, s);
+    } else if (np.mixed) {
+      ca.fb_list = np.fb_list + (size_t)b * n;
+      ca.fb_count = np.fb_count + b;
+      e = np.cplx ? launch_columns_mixed_c64(b, np.alg, ca, np.h_bc[b], np.wpb[b], s)
+                  : launch_columns_mixed_f32(b, np.alg, ca, np.h_bc[b], np.wpb[b], s);
       if (e == cudaSuccess) {
         // the FP64 kernel finishes the columns the mixed kernel handed back
         ColArgs cf = ca;
         cf.list = ca.fb_list;
         cf.list_count = ca.fb_count;
-        cf.work_counter = work + kNumBuckets + b;
+        cf.work_counter = np.work + kNumBuckets + b;
         cf.extra_flags = DIAF_FLAG_FP64_FALLBACK;
-        e = fp64_launch(b, cf, h_bc[b]);
+        e = fp64_launch(b, cf, np.h_bc[b]);
       }
     } else {
-      e = fp64_launch(b, ca, h_bc[b]);
+      e = fp64_launch(b, ca, np.h_bc[b]);
     }
     if (e == cudaErrorNotSupported)
       return fail(DIAF_EUNSUPPORTED, "bucket " + std::to_string(b) + " has no kernel for this configuration yet");
     if (e != cudaSuccess) return cuda_fail(e, "column kernel launch");
-    DIAF_CU(cudaEventRecord(F->ev[4 + 2 * b], s));
+    if (events) DIAF_CU(cudaEventRecord(F->ev[4 + 2 * b], s));
     F->bucket_ran[b] = true;
   }
-  if (mixed) {
-    DIAF_CU(F->alloc(&F->fb_counts, kNumBuckets));
-    DIAF_CU(cudaMemcpyAsync(F->fb_counts, fb_count, sizeof(int32_t) * kNumBuckets, cudaMemcpyDeviceToDevice, s));
-  }
+  if (np.mixed) DIAF_CU(cudaMemcpyAsync(F->fb_counts, np.fb_count, sizeof(int32_t) * kNumBuckets,
+                                        cudaMemcpyDeviceToDevice, s));
+  return DIAF_OK;
+}
+
+}  // namespace
+
+struct diaf_plan {
+  diaf_factors* F = nullptr;
+  Pool* scratch = nullptr;
+  NumericPlan np;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+diaf_status diaf_factor_tuned(const diaf_csc* A, const diaf_pattern* PW, const diaf_vspec* V, int32_t alg,
+                              int32_t prec, const diaf_tuning* tuning, void* stream, diaf_factors** out) {
+  g_last_error.clear();
+  if (!out) return fail(DIAF_EINVAL, "out is NULL");
+  *out = nullptr;
+  diaf_status st = check_args(A, PW, V, alg, prec, tuning);
+  if (st != DIAF_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto F = new diaf_factors();
+  F->stream = s;
+  struct Guard {
+    diaf_factors*& f;
+    bool keep = false;
+    ~Guard() { if (!keep) diaf_free(f); }
+  } guard{F};
+  for (cudaEvent_t& e : F->ev) DIAF_CU(cudaEventCreate(&e));
+  DIAF_CU(cudaEventRecord(F->ev[0], s));
+  Pool pool(s);
+  NumericPlan np;
+  st = symbolic_pass(A, PW, V, alg, prec, tuning, s, F, pool, np);
+  if (st != DIAF_OK) return st;
+  DIAF_CU(cudaEventRecord(F->ev[1], s));
+  st = enqueue_numeric(F, np, s, true);
+  if (st != DIAF_OK) return st;
   DIAF_CU(cudaEventRecord(F->ev[2], s));
   pool.release();
   guard.keep = true;
   *out = F;
   return DIAF_OK;
+}
+
+diaf_status diaf_factor(const diaf_csc* A, const diaf_pattern* PW, const diaf_vspec* V, int32_t alg, int32_t prec,
+                        void* stream, diaf_factors** out) {
+  return diaf_factor_tuned(A, PW, V, alg, prec, nullptr, stream, out);
+}
+
+diaf_status diaf_plan_create(const diaf_csc* A, const diaf_pattern* PW, const diaf_vspec* V, int32_t alg,
+                             int32_t prec, const diaf_tuning* tuning, void* stream, diaf_plan** out) {
+  g_last_error.clear();
+  if (!out) return fail(DIAF_EINVAL, "out is NULL");
+  *out = nullptr;
+  diaf_status st = check_args(A, PW, V, alg, prec, tuning);
+  if (st != DIAF_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto P = new diaf_plan();
+  P->F = new diaf_factors();
+  P->F->stream = s;
+  P->scratch = new Pool(s);
+  struct Guard {
+    diaf_plan*& p;
+    bool keep = false;
+    ~Guard() { if (!keep) diaf_plan_free(p); }
+  } guard{P};
+  st = symbolic_pass(A, PW, V, alg, prec, tuning, s, P->F, *P->scratch, P->np);
+  if (st != DIAF_OK) return st;
+  DIAF_CU(cudaStreamSynchronize(s));
+  // capture the numeric pass on a private stream (the caller's may be the legacy default stream)
+  cudaStream_t cs;
+  DIAF_CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return cuda_fail(e, "cudaStreamBeginCapture");
+  }
+  st = enqueue_numeric(P->F, P->np, cs, false);
+  e = cudaStreamEndCapture(cs, &P->graph);
+  cudaStreamDestroy(cs);
+  if (st != DIAF_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  DIAF_CU(cudaGraphInstantiate(&P->exec, P->graph, 0));
+  guard.keep = true;
+  *out = P;
+  return DIAF_OK;
+}
+
+diaf_status diaf_plan_execute(diaf_plan* P, void* stream) {
+  if (!P || !P->exec) return fail(DIAF_EINVAL, "NULL plan");
+  DIAF_CU(cudaGraphLaunch(P->exec, static_cast<cudaStream_t>(stream)));
+  DIAF_COUNT_LAUNCH();
+  return DIAF_OK;
+}
+
+diaf_factors* diaf_plan_factors(diaf_plan* P) { return P ? P->F : nullptr; }
+
+diaf_status diaf_autotune(const diaf_csc* A, const diaf_pattern* PW, const diaf_vspec* V, int32_t alg, int32_t prec,
+                          void* stream, diaf_tuning* best, float* best_ms) {
+  if (!best) return fail(DIAF_EINVAL, "best is NULL");
+  diaf_tuning cur{};
+  auto time_of = [&](const diaf_tuning& t, float* ms_out) -> diaf_status {
+    float ms[2] = {0, 0};
+    for (int rep = 0; rep < 2; ++rep) {
+      diaf_factors* F = nullptr;
+      diaf_status st = diaf_factor_tuned(A, PW, V, alg, prec, &t, stream, &F);
+      if (st != DIAF_OK) return st;
+      float tm[2 + kNumBuckets];
+      st = diaf_factor_timings(F, tm, 2 + kNumBuckets);
+      diaf_free(F);
+      if (st != DIAF_OK) return st;
+      ms[rep] = tm[1];  // the numeric pass
+    }
+    *ms_out = ms[0] < ms[1] ? ms[0] : ms[1];
+    return DIAF_OK;
+  };
+  float cur_ms = 0;
+  diaf_status st = time_of(cur, &cur_ms);
+  if (st != DIAF_OK) return st;
+  // coordinate descent over the bucket edges and the CTA sizes of the warp kernels
+  const int edge0[] = {32, 24, 16}, edge1[] = {64, 48, 32}, wpbs[] = {0, 2, 4, 8};
+  for (int knob = 0; knob < 4; ++knob) {
+    const int* vals = knob == 0 ? edge0 : (knob == 1 ? edge1 : wpbs);
+    const int nv = knob < 2 ? 3 : 4;
+    for (int i = 0; i < nv; ++i) {
+      diaf_tuning t = cur;
+      int* field = knob == 0 ? &t.m_edge0 : (knob == 1 ? &t.m_edge1 : &t.warps_per_block[knob - 2]);
+      const int* curf = knob == 0 ? &cur.m_edge0 : (knob == 1 ? &cur.m_edge1 : &cur.warps_per_block[knob - 2]);
+      const int eff = (*curf == 0 && knob < 2) ? vals[0] : *curf;
+      if (vals[i] == eff) continue;
+      *field = vals[i];
+      float ms = 0;
+      st = time_of(t, &ms);
+      if (st != DIAF_OK) return st;
+      if (ms < cur_ms * 0.98f) { cur = t; cur_ms = ms; }
+    }
+  }
+  *best = cur;
+  if (best_ms) *best_ms = cur_ms;
+  return DIAF_OK;
+}
+
+void diaf_plan_free(diaf_plan* P) {
+  if (!P) return;
+  if (P->exec) cudaGraphExecDestroy(P->exec);
+  if (P->graph) cudaGraphDestroy(P->graph);
+  delete P->scratch;  // stream-ordered frees on the creation stream
+  diaf_free(P->F);
+  delete P;
 }
 
 diaf_status diaf_factor_info_get(const diaf_factors* F, diaf_factor_info* info) {

@@ -78,7 +78,7 @@ __device__ ColumnIdx carve_idx(int32_t* base) {
 }
 
 // Loads R_j and gathers T = A(R_j, J_j) (zero padded to me rows) into Ts.
-template <class SD, int KMAX, int MMAX>
+template <class SD, int KMAX, int MMAX, int LDT>
 __device__ void gather_tile(const ColArgs& a, int j, int k, int m, int me, SD* Ts, const ColumnIdx& ix, int lane) {
   const int32_t* Rj = a.rows + a.Eoff[j];
   const int32_t* J = a.Wri + a.Wcp[j];
@@ -88,7 +88,7 @@ __device__ void gather_tile(const ColArgs& a, int j, int k, int m, int me, SD* T
     ix.inI[r] = -1;
     ix.pick[r] = 0;
   }
-  for (int i = lane; i < me * k; i += DIAF_WARP) Ts[(i % me) + (i / me) * MMAX] = sc_zero<SD>();
+  for (int i = lane; i < me * k; i += DIAF_WARP) Ts[(i % me) + (i / me) * LDT] = sc_zero<SD>();
   int len = 0;
   if (lane < k) {
     int c = J[lane];
@@ -109,7 +109,7 @@ __device__ void gather_tile(const ColArgs& a, int j, int k, int m, int me, SD* T
     while (q + 1 < k && ix.coff[q + 1] <= e) ++q;
     int p = ix.cst[q] + (e - ix.coff[q]);
     int r = lower_bound_i32(ix.rs, m, a.Ari[p]);
-    Ts[r + q * MMAX] = Av[p];
+    Ts[r + q * LDT] = Av[p];
   }
   __syncwarp();
 }
@@ -199,7 +199,7 @@ __device__ inline int build_I(const ColArgs& a, int j, int m, int l, const Colum
 
 // Phase (v_jj real >= 0, else the largest |w_q| real), residual
 // ||A_j w - v||, finiteness, and the scatter of column j.
-template <class SD, int MMAX>
+template <class SD, int LDT>
 __device__ void finish_column(const ColArgs& a, int j, int k, int m, int l, int jpos, const SD* Ts, SD* wv, SD* vv,
                               const ColumnIdx& ix, uint32_t flags, bool do_phase, int lane) {
   using R = RealOf<SD>;
@@ -229,7 +229,7 @@ __device__ void finish_column(const ColArgs& a, int j, int k, int m, int l, int 
   R r2 = R(0);
   for (int r = lane; r < m; r += DIAF_WARP) {
     SD s = sc_zero<SD>();
-    for (int q = 0; q < k; ++q) s += Ts[r + q * MMAX] * wv[q];
+    for (int q = 0; q < k; ++q) s += Ts[r + q * LDT] * wv[q];
     if (ix.inI[r] >= 0) s -= vv[ix.inI[r]];
     r2 += sc_abs2(s);
   }
@@ -279,9 +279,11 @@ __device__ void compact_rows(S* Tw, const int32_t* Iloc, int l, int k, int lane)
 // ------------------------------------------------------------------ FP64 kernel
 template <class S, int KMAX, int MMAX>
 struct WarpLayout {
-  static constexpr int kTile = MMAX * KMAX;
+  static constexpr int LDT = MMAX + 1;  // odd leading dimensions: no bank conflicts between columns
+  static constexpr int KP = KMAX + 1;
+  static constexpr int kTile = LDT * KMAX;
   static constexpr size_t raw() {
-    return sizeof(S) * (2 * kTile + 2 * KMAX * KMAX + 2 * KMAX + MMAX) + sizeof(double) * (MMAX + KMAX) +
+    return sizeof(S) * (2 * kTile + 2 * KP * KMAX + 2 * KMAX + MMAX) + sizeof(double) * (MMAX + KMAX) +
            idx_bytes<KMAX, MMAX>();
   }
   static constexpr size_t bytes() { return (raw() + 15) / 16 * 16; }  // keeps every warp's slice 16-byte aligned
@@ -291,11 +293,12 @@ template <class S, int KMAX, int MMAX, int ALG>
 __device__ void solve_column_warp(const ColArgs& a, int j, unsigned char* smem, int lane) {
   using R = RealOf<S>;
   using L = WarpLayout<S, KMAX, MMAX>;
-  S* Ts = reinterpret_cast<S*>(smem);  // original tile, MMAX x KMAX
+  constexpr int LDT = L::LDT, KP = L::KP;
+  S* Ts = reinterpret_cast<S*>(smem);  // original tile, LDT x KMAX
   S* Tw = Ts + L::kTile;               // working tile / Q rows / Q_I
-  S* Rs = Tw + L::kTile;               // R of T, later R-hat (KMAX x KMAX)
-  S* Vj = Rs + KMAX * KMAX;            // Jacobi V
-  S* wv = Vj + KMAX * KMAX;            // w (KMAX)
+  S* Rs = Tw + L::kTile;               // R of T, later R-hat (KP x KMAX)
+  S* Vj = Rs + KP * KMAX;              // Jacobi V
+  S* wv = Vj + KP * KMAX;              // w (KMAX)
   S* rinv = wv + KMAX;                 // reciprocal diagonal (KMAX)
   S* vv = rinv + KMAX;                 // v (MMAX)
   double* hk = reinterpret_cast<double*>(vv + MMAX);  // keys (MMAX)
@@ -308,25 +311,25 @@ __device__ void solve_column_warp(const ColArgs& a, int j, unsigned char* smem, 
   const int me = m > k ? m : k;  // rows of the working tile (zero padded)
   uint32_t flags = 0;
 
-  gather_tile<S, KMAX, MMAX>(a, j, k, m, me, Ts, ix, lane);
+  gather_tile<S, KMAX, MMAX, LDT>(a, j, k, m, me, Ts, ix, lane);
 
   // ---- QR of T, keys, I_j
   if (k > 0) {
-    for (int i = lane; i < me * k; i += DIAF_WARP) Tw[(i % me) + (i / me) * MMAX] = Ts[(i % me) + (i / me) * MMAX];
+    for (int i = lane; i < me * k; i += DIAF_WARP) Tw[(i % me) + (i / me) * LDT] = Ts[(i % me) + (i / me) * LDT];
     __syncwarp();
-    warp_householder_qr<S, MMAX>(Tw, me, k, lane);
+    warp_householder_qr<S, LDT>(Tw, me, k, lane);
     for (int i = lane; i < k * k; i += DIAF_WARP) {
       int r = i % k, c = i / k;
-      Rs[r + c * KMAX] = (r <= c) ? Tw[r + c * MMAX] : sc_zero<S>();
+      Rs[r + c * KP] = (r <= c) ? Tw[r + c * LDT] : sc_zero<S>();
     }
     __syncwarp();
   }
   R rdmax = R(0);
-  for (int c = lane; c < k; c += DIAF_WARP) rdmax = dmax(rdmax, sc_abs(Rs[c + c * KMAX]));
+  for (int c = lane; c < k; c += DIAF_WARP) rdmax = dmax(rdmax, sc_abs(Rs[c + c * KP]));
   rdmax = warp_max(rdmax);
   const R piv = R(1e-14) * rdmax;
   if (k > 0 && (a.rule != DIAF_RULE_FIXED || ALG == DIAF_ALG_Q))
-    warp_leverage_rows<S, S, MMAX, KMAX>(Ts, Rs, Tw, hk, rinv, m, k, piv, lane);
+    warp_leverage_rows<S, S, LDT, KP>(Ts, Rs, Tw, hk, rinv, m, k, piv, lane);
   if (a.rule != DIAF_RULE_FIXED) select_rows_greedy(ix.rs, hk, ix.pick, m, a.rule, j, l - 1, a.tie_tol, lane);
   const int jpos = build_I(a, j, m, l, ix, lane);
 
@@ -347,18 +350,18 @@ __device__ void solve_column_warp(const ColArgs& a, int j, unsigned char* smem, 
     // ---- DIAF-S: QR of the tile without the I_j rows, Jacobi SVD of R-hat
     for (int i = lane; i < me * k; i += DIAF_WARP) {
       int r = i % me, c = i / me;
-      Tw[r + c * MMAX] = (r < m && ix.inI[r] >= 0) ? sc_zero<S>() : Ts[r + c * MMAX];
+      Tw[r + c * LDT] = (r < m && ix.inI[r] >= 0) ? sc_zero<S>() : Ts[r + c * LDT];
     }
     __syncwarp();
-    warp_householder_qr<S, MMAX>(Tw, me, k, lane);
+    warp_householder_qr<S, LDT>(Tw, me, k, lane);
     for (int i = lane; i < k * k; i += DIAF_WARP) {
       int r = i % k, c = i / k;
-      Rs[r + c * KMAX] = (r <= c) ? Tw[r + c * MMAX] : sc_zero<S>();
+      Rs[r + c * KP] = (r <= c) ? Tw[r + c * LDT] : sc_zero<S>();
     }
     __syncwarp();
-    int sw = warp_jacobi<S, KMAX, KMAX, KMAX>(Rs, k, k, Vj, lane);
+    int sw = warp_jacobi<S, KP, KP, KMAX>(Rs, k, k, Vj, lane);
     if (sw < 0) flags |= DIAF_FLAG_JACOBI_NOCONV;
-    warp_col_norms<S, KMAX>(Rs, k, k, sig, lane);
+    warp_col_norms<S, KP>(Rs, k, k, sig, lane);
     int imin = 0;
     double smin = sig[0], smax = sig[0];
     for (int c = 1; c < k; ++c) {
@@ -371,22 +374,22 @@ __device__ void solve_column_warp(const ColArgs& a, int j, unsigned char* smem, 
     for (int t = 0; t < l; ++t) inrows += (ix.Iloc[t] >= 0);
     if (smin <= 1e-14 * smax || m - inrows < k) flags |= DIAF_FLAG_RANK_DEFICIENT;
     if (k > 1 && (snext - smin) <= 1e-6 * smax) flags |= DIAF_FLAG_DEGENERATE;
-    for (int q = lane; q < k; q += DIAF_WARP) wv[q] = Vj[q + imin * KMAX];
+    for (int q = lane; q < k; q += DIAF_WARP) wv[q] = Vj[q + imin * KP];
     __syncwarp();
     for (int t = lane; t < l; t += DIAF_WARP) {
       S s = sc_zero<S>();
       int r = ix.Iloc[t];
       if (r >= 0)
-        for (int q = 0; q < k; ++q) s += Ts[r + q * MMAX] * wv[q];
+        for (int q = 0; q < k; ++q) s += Ts[r + q * LDT] * wv[q];
       vv[t] = s;
     }
     __syncwarp();
   } else {
     // ---- DIAF-Q: Q_I = rows I_j of Q (compacted to the top of Tw)
-    compact_rows<S, MMAX>(Tw, ix.Iloc, l, k, lane);
-    int sw = warp_jacobi<S, MMAX, KMAX, KMAX>(Tw, l, k, Vj, lane);
+    compact_rows<S, LDT>(Tw, ix.Iloc, l, k, lane);
+    int sw = warp_jacobi<S, LDT, KP, KMAX>(Tw, l, k, Vj, lane);
     if (sw < 0) flags |= DIAF_FLAG_JACOBI_NOCONV;
-    warp_col_norms<S, MMAX>(Tw, l, k, sig, lane);
+    warp_col_norms<S, LDT>(Tw, l, k, sig, lane);
     int imax = 0;
     double smax = sig[0];
     for (int c = 1; c < k; ++c) if (sig[c] > smax) { smax = sig[c]; imax = c; }
@@ -395,25 +398,25 @@ __device__ void solve_column_warp(const ColArgs& a, int j, unsigned char* smem, 
     if (smax == 0.0 || (k > 1 && (smax - snext) <= 1e-6 * smax)) flags |= DIAF_FLAG_DEGENERATE;
     if (smax > 0.0) {
       const R inv = R(1) / R(smax);
-      for (int t = lane; t < l; t += DIAF_WARP) vv[t] = inv * Tw[t + imax * MMAX];
+      for (int t = lane; t < l; t += DIAF_WARP) vv[t] = inv * Tw[t + imax * LDT];
     } else if (lane == 0) {
       vv[jpos >= 0 ? jpos : 0] = sc_real_s<S>(R(1));
     }
     // w = sigma R^-1 u  (R w = Q^* v, eq. condwj); rinv holds R's reciprocal diagonal
     bool rd = false;
-    for (int c = lane; c < k; c += DIAF_WARP) rd |= !(sc_abs(Rs[c + c * KMAX]) > piv);
+    for (int c = lane; c < k; c += DIAF_WARP) rd |= !(sc_abs(Rs[c + c * KP]) > piv);
     rd = __any_sync(DIAF_FULL, rd);
     if (rd) flags |= DIAF_FLAG_RANK_DEFICIENT;
-    S x = lane < k ? R(smax) * Vj[lane + imax * KMAX] : sc_zero<S>();
+    S x = lane < k ? R(smax) * Vj[lane + imax * KP] : sc_zero<S>();
     for (int c = k - 1; c >= 0; --c) {
       S yc = shfl_idx(x * rinv[c], c);
-      if (lane < c) x -= Rs[lane + c * KMAX] * yc;
+      if (lane < c) x -= Rs[lane + c * KP] * yc;
       if (lane == c) x = yc;
     }
     if (lane < k) wv[lane] = x;
     __syncwarp();
   }
-  finish_column<S, MMAX>(a, j, k, m, l, jpos, Ts, wv, vv, ix, flags, k > 0 || ALG == DIAF_ALG_Q, lane);
+  finish_column<S, LDT>(a, j, k, m, l, jpos, Ts, wv, vv, ix, flags, k > 0 || ALG == DIAF_ALG_Q, lane);
 }
 
 template <class S, int KMAX, int MMAX, int ALG>

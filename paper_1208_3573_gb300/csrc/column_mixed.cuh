@@ -37,13 +37,16 @@ template <> struct DoubleOf<Cx<float>> { using T = Cx<double>; };
 constexpr float kMixedKappaMax = 300.0f;
 constexpr int kRRMax = 8;  // DIAF-Q: largest l_j refined through the explicit l x l matrix C
 
-template <class S, int KMAX, int MMAX>
+template <class S, int KMAX, int MMAX, int ALG>
 struct MixedLayout {
   using SD = typename DoubleOf<S>::T;
-  static constexpr int kTile = MMAX * KMAX;
+  static constexpr int LDT = MMAX + 1;  // odd leading dimensions: no bank conflicts between columns
+  static constexpr int KP = KMAX + 1;
+  static constexpr int kTile = LDT * KMAX;
+  static constexpr int kRR = ALG == DIAF_ALG_Q ? kRRMax : 0;  // DIAF-Q only: X, C, C - mu I
   static constexpr size_t raw() {
-    return sizeof(SD) * (kTile + 3 * KMAX + 2 * MMAX + kRRMax * KMAX + 2 * kRRMax * kRRMax) +
-           sizeof(S) * (kTile + 2 * KMAX * KMAX + KMAX) +
+    return sizeof(SD) * (kTile + 3 * KMAX + 2 * MMAX + kRR * KP + 2 * kRR * kRR) +
+           sizeof(S) * (kTile + 2 * KP * KMAX + KMAX) +
            sizeof(double) * (MMAX + 2 * KMAX) + idx_bytes<KMAX, MMAX>();
   }
   static constexpr size_t bytes() { return (raw() + 15) / 16 * 16; }
@@ -53,20 +56,21 @@ template <class S, int KMAX, int MMAX, int ALG>
 __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem, int lane) {
   using SD = typename DoubleOf<S>::T;
   using R = RealOf<S>;
-  using L = MixedLayout<S, KMAX, MMAX>;
-  SD* Ts = reinterpret_cast<SD*>(smem);  // FP64 tile (MMAX x KMAX)
+  using L = MixedLayout<S, KMAX, MMAX, ALG>;
+  constexpr int LDT = L::LDT, KP = L::KP, kRR = L::kRR;
+  SD* Ts = reinterpret_cast<SD*>(smem);  // FP64 tile (LDT x KMAX)
   SD* rinvD = Ts + L::kTile;             // FP64 reciprocal diagonal of the FP32 factor
   SD* wv = rinvD + KMAX;                 // w
   SD* gg = wv + KMAX;                    // k-vector scratch
   SD* vv = gg + KMAX;                    // v (MMAX)
   SD* zz = vv + MMAX;                    // m-vector scratch
-  SD* Xs = zz + MMAX;                    // DIAF-Q: X = (T^* T)^-1 T_I^* (KMAX x kRRMax)
-  SD* Cs = Xs + kRRMax * KMAX;           // DIAF-Q: C = T_I X (kRRMax x kRRMax)
-  SD* Ms = Cs + kRRMax * kRRMax;         // DIAF-Q: C - mu I, eliminated in place
-  S* Tw = reinterpret_cast<S*>(Ms + kRRMax * kRRMax);  // FP32 working tile
+  SD* Xs = zz + MMAX;                    // DIAF-Q: X = (T^* T)^-1 T_I^* (KP x kRR)
+  SD* Cs = Xs + kRR * KP;                // DIAF-Q: C = T_I X (kRRMax x kRRMax)
+  SD* Ms = Cs + kRR * kRR;               // DIAF-Q: C - mu I, eliminated in place
+  S* Tw = reinterpret_cast<S*>(Ms + kRR * kRR);  // FP32 working tile
   S* Rs = Tw + L::kTile;                 // FP32 R of T, then R-hat (Jacobi works on it)
-  S* Vj = Rs + KMAX * KMAX;              // FP32 Jacobi V
-  S* rinv = Vj + KMAX * KMAX;            // FP32 reciprocal diagonal
+  S* Vj = Rs + KP * KMAX;                // FP32 Jacobi V
+  S* rinv = Vj + KP * KMAX;              // FP32 reciprocal diagonal
   double* hk = reinterpret_cast<double*>(rinv + KMAX);
   double* sig = hk + MMAX;
   double* cn = sig + KMAX;               // column norms of the tile
@@ -95,36 +99,36 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
   }
 
   DIAF_PHASE_START();
-  gather_tile<SD, KMAX, MMAX>(a, j, k, m, me, Ts, ix, lane);
+  gather_tile<SD, KMAX, MMAX, LDT>(a, j, k, m, me, Ts, ix, lane);
   DIAF_PHASE(0);
 
   // ---- FP32 QR of T and the keys
   for (int i = lane; i < me * k; i += DIAF_WARP) {
     int r = i % me, c = i / me;
-    Tw[r + c * MMAX] = sc_cast<S>(Ts[r + c * MMAX]);
+    Tw[r + c * LDT] = sc_cast<S>(Ts[r + c * LDT]);
   }
   for (int c = lane; c < k; c += DIAF_WARP) {
-    double s = 0.0;
-    for (int r = 0; r < m; ++r) s += (double)sc_abs2(Ts[r + c * MMAX]);
-    cn[c] = sqrt(s);
+    double s2 = 0.0;
+    for (int r = 0; r < m; ++r) s2 += (double)sc_abs2(Ts[r + c * LDT]);
+    cn[c] = sqrt(s2);
   }
   __syncwarp();
   DIAF_PHASE(1);
-  warp_householder_qr<S, MMAX>(Tw, me, k, lane);
+  warp_householder_qr<S, LDT>(Tw, me, k, lane);
   for (int i = lane; i < k * k; i += DIAF_WARP) {
     int r = i % k, c = i / k;
-    Rs[r + c * KMAX] = (r <= c) ? Tw[r + c * MMAX] : sc_zero<S>();
+    Rs[r + c * KP] = (r <= c) ? Tw[r + c * LDT] : sc_zero<S>();
   }
   __syncwarp();
   DIAF_PHASE(2);
   float kap = 0.0f;
   for (int c = lane; c < k; c += DIAF_WARP) {
-    float d = (float)sc_abs(Rs[c + c * KMAX]);
+    float d = (float)sc_abs(Rs[c + c * KP]);
     kap = fmaxf(kap, d > 0.0f ? (float)cn[c] / d : INFINITY);
   }
   kap = warp_max(kap);
   if (!(kap <= kMixedKappaMax)) { hand_back(1); return; }
-  warp_leverage_rows<S, SD, MMAX, KMAX>(Ts, Rs, Tw, hk, rinv, m, k, R(0), lane);
+  warp_leverage_rows<S, SD, LDT, KP>(Ts, Rs, Tw, hk, rinv, m, k, R(0), lane);
   DIAF_PHASE(3);
   if (a.rule != DIAF_RULE_FIXED) {
     const double margin = select_rows_greedy(ix.rs, hk, ix.pick, m, a.rule, j, l - 1, a.tie_tol, lane);
@@ -139,40 +143,40 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
   DIAF_PHASE(4);
 
   if (ALG == DIAF_ALG_S) {
-    // ---- FP32 QR of A-hat (I_j rows zeroed) and Jacobi SVD of R-hat
+    // ---- FP32 QR of A-hat (I_j rows zeroed); Jacobi SVD of R-hat in registers
     for (int i = lane; i < me * k; i += DIAF_WARP) {
       int r = i % me, c = i / me;
-      Tw[r + c * MMAX] = (r < m && ix.inI[r] >= 0) ? sc_zero<S>() : sc_cast<S>(Ts[r + c * MMAX]);
+      Tw[r + c * LDT] = (r < m && ix.inI[r] >= 0) ? sc_zero<S>() : sc_cast<S>(Ts[r + c * LDT]);
     }
     for (int c = lane; c < k; c += DIAF_WARP) {
-      double s = 0.0;
+      double s2 = 0.0;
       for (int r = 0; r < m; ++r)
-        if (ix.inI[r] < 0) s += (double)sc_abs2(Ts[r + c * MMAX]);
-      cn[c] = sqrt(s);
+        if (ix.inI[r] < 0) s2 += (double)sc_abs2(Ts[r + c * LDT]);
+      cn[c] = sqrt(s2);
     }
     __syncwarp();
     DIAF_PHASE(5);
-    warp_householder_qr<S, MMAX>(Tw, me, k, lane);
-    for (int i = lane; i < k * k; i += DIAF_WARP) {
-      int r = i % k, c = i / k;
-      Rs[r + c * KMAX] = (r <= c) ? Tw[r + c * MMAX] : sc_zero<S>();
-    }
-    __syncwarp();
+    warp_householder_qr<S, LDT>(Tw, me, k, lane);
     DIAF_PHASE(6);
     float kh = 0.0f;
     for (int c = lane; c < k; c += DIAF_WARP) {
-      float d = (float)sc_abs(Rs[c + c * KMAX]);
+      const float d = (float)sc_abs(Tw[c + c * LDT]);
       kh = fmaxf(kh, d > 0.0f ? (float)cn[c] / d : INFINITY);
     }
     kh = warp_max(kh);
     if (!(kh <= kMixedKappaMax)) { hand_back(3); return; }
-    int sw = warp_jacobi<S, KMAX, KMAX, KMAX>(Rs, k, k, Vj, lane);
+    for (int i = lane; i < k * k; i += DIAF_WARP) {
+      int r = i % k, c = i / k;
+      Rs[r + c * KP] = (r <= c) ? Tw[r + c * LDT] : sc_zero<S>();
+    }
+    __syncwarp();
+    int sw = warp_jacobi<S, KP, KP, KMAX>(Rs, k, k, Vj, lane);
     if (sw < 0) flags |= DIAF_FLAG_JACOBI_NOCONV;
 #ifdef DIAF_PHASE_TIMING
     if (lane == 0 && a.phase) atomicAdd(&a.phase[20], (unsigned long long)(sw < 0 ? kMaxSweeps : sw));
 #endif
     DIAF_PHASE(7);
-    warp_col_norms<S, KMAX>(Rs, k, k, sig, lane);
+    warp_col_norms<S, KP>(Rs, k, k, sig, lane);
     int imin = 0;
     double smin = sig[0], smax = sig[0];
     for (int c = 1; c < k; ++c) {
@@ -188,20 +192,20 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     if (k > 1 && gap <= 1e-5 * smax * smax) { hand_back(4); return; }
     const int iters = (k > 1 && gap < 1e-2 * smax * smax) ? 2 : 1;
     SD* cc = rinvD;  // correction coefficients (KMAX)
-    SD x = lane < k ? sc_cast<SD>(Vj[lane + imin * KMAX]) : sc_zero<SD>();
+    SD x = lane < k ? sc_cast<SD>(Vj[lane + imin * KP]) : sc_zero<SD>();
     for (int it = 0; it < iters; ++it) {
       if (lane < k) gg[lane] = x;
       __syncwarp();
       for (int r = lane; r < m; r += DIAF_WARP) {
         SD z = sc_zero<SD>();
         if (ix.inI[r] < 0)
-          for (int q = 0; q < k; ++q) z += Ts[r + q * MMAX] * gg[q];
+          for (int q = 0; q < k; ++q) z += Ts[r + q * LDT] * gg[q];
         zz[r] = z;
       }
       __syncwarp();
       SD g = sc_zero<SD>();  // (H x)_q = (A-hat^* (A-hat x))_q
       if (lane < k)
-        for (int r = 0; r < m; ++r) g += sc_cmul(Ts[r + lane * MMAX], zz[r]);
+        for (int r = 0; r < m; ++r) g += sc_cmul(Ts[r + lane * LDT], zz[r]);
       const double xg = warp_sum(lane < k ? (double)sc_real(sc_cmul(x, g)) : 0.0);
       const double xx = warp_sum(lane < k ? (double)sc_abs2(x) : 0.0);
       const double d = xg / xx;
@@ -209,13 +213,13 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
       __syncwarp();
       if (lane < k) {
         SD vr = sc_zero<SD>();
-        for (int q = 0; q < k; ++q) vr += sc_cmul(sc_cast<SD>(Vj[q + lane * KMAX]), wv[q]);
+        for (int q = 0; q < k; ++q) vr += sc_cmul(sc_cast<SD>(Vj[q + lane * KP]), wv[q]);
         const double den = sig[lane] * sig[lane] - d;
         cc[lane] = (lane == imin) ? sc_zero<SD>() : RealOf<SD>(-1.0 / den) * vr;
       }
       __syncwarp();
       if (lane < k)
-        for (int i = 0; i < k; ++i) x += sc_cast<SD>(Vj[lane + i * KMAX]) * cc[i];
+        for (int i = 0; i < k; ++i) x += sc_cast<SD>(Vj[lane + i * KP]) * cc[i];
       __syncwarp();
     }
     const double xn2 = warp_sum(lane < k ? (double)sc_abs2(x) : 0.0);
@@ -227,14 +231,14 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
       SD s = sc_zero<SD>();
       int r = ix.Iloc[t];
       if (r >= 0)
-        for (int q = 0; q < k; ++q) s += Ts[r + q * MMAX] * wv[q];
+        for (int q = 0; q < k; ++q) s += Ts[r + q * LDT] * wv[q];
       vv[t] = s;
     }
     double r2 = 0.0;
     for (int r = lane; r < m; r += DIAF_WARP)
       if (ix.inI[r] < 0) {
         SD s = sc_zero<SD>();
-        for (int q = 0; q < k; ++q) s += Ts[r + q * MMAX] * wv[q];
+        for (int q = 0; q < k; ++q) s += Ts[r + q * LDT] * wv[q];
         r2 += (double)sc_abs2(s);
       }
     r2 = warp_sum(r2);
@@ -243,10 +247,10 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
   } else {
     // ---- FP32 Jacobi on Q_I (FP32 rows of Q = T R^-1 in Tw)
     if (l > kRRMax) { hand_back(5); return; }
-    compact_rows<S, MMAX>(Tw, ix.Iloc, l, k, lane);
-    int sw = warp_jacobi<S, MMAX, KMAX, KMAX>(Tw, l, k, Vj, lane);
+    compact_rows<S, LDT>(Tw, ix.Iloc, l, k, lane);
+    int sw = warp_jacobi<S, LDT, KP, KMAX>(Tw, l, k, Vj, lane);
     if (sw < 0) flags |= DIAF_FLAG_JACOBI_NOCONV;
-    warp_col_norms<S, MMAX>(Tw, l, k, sig, lane);
+    warp_col_norms<S, LDT>(Tw, l, k, sig, lane);
     int imax = 0;
     double smax = sig[0];
     for (int c = 1; c < k; ++c) if (sig[c] > smax) { smax = sig[c]; imax = c; }
@@ -254,27 +258,27 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     for (int c = 0; c < k; ++c) if (c != imax) snext = dmax(snext, sig[c]);
     if (!(smax > 0.0)) { hand_back(6); return; }
     if (k > 1 && (smax - snext) <= 1e-6 * smax) flags |= DIAF_FLAG_DEGENERATE;
-    for (int t = lane; t < l; t += DIAF_WARP) vv[t] = sc_cast<SD>(Tw[t + imax * MMAX]);
-    for (int c = lane; c < k; c += DIAF_WARP) rinvD[c] = sc_recip_or_zero(sc_cast<SD>(Rs[c + c * KMAX]), 0.0);
+    for (int t = lane; t < l; t += DIAF_WARP) vv[t] = sc_cast<SD>(Tw[t + imax * LDT]);
+    for (int c = lane; c < k; c += DIAF_WARP) rinvD[c] = sc_recip_or_zero(sc_cast<SD>(Rs[c + c * KP]), 0.0);
     __syncwarp();
     // X(:,t) = (T^* T)^-1 T(I_t,:)^*: one solve with the FP32 R, one correction
     for (int t = 0; t < l; ++t) {
       const int rI = ix.Iloc[t];
-      const SD b = (lane < k && rI >= 0) ? sc_conj(Ts[rI + lane * MMAX]) : sc_zero<SD>();
-      SD x = warp_solve_RhR<SD, S, KMAX>(Rs, rinvD, b, k, lane);
+      const SD b = (lane < k && rI >= 0) ? sc_conj(Ts[rI + lane * LDT]) : sc_zero<SD>();
+      SD x = warp_solve_RhR<SD, S, KP>(Rs, rinvD, b, k, lane);
       if (lane < k) gg[lane] = x;
       __syncwarp();
       for (int r = lane; r < m; r += DIAF_WARP) {
         SD z = sc_zero<SD>();
-        for (int q = 0; q < k; ++q) z -= Ts[r + q * MMAX] * gg[q];
+        for (int q = 0; q < k; ++q) z -= Ts[r + q * LDT] * gg[q];
         zz[r] = z;
       }
       __syncwarp();
       SD rn = b;
       if (lane < k)
-        for (int r = 0; r < m; ++r) rn += sc_cmul(Ts[r + lane * MMAX], zz[r]);
-      x += warp_solve_RhR<SD, S, KMAX>(Rs, rinvD, rn, k, lane);
-      if (lane < k) Xs[lane + t * KMAX] = x;
+        for (int r = 0; r < m; ++r) rn += sc_cmul(Ts[r + lane * LDT], zz[r]);
+      x += warp_solve_RhR<SD, S, KP>(Rs, rinvD, rn, k, lane);
+      if (lane < k) Xs[lane + t * KP] = x;
       __syncwarp();
     }
     // C = T_I X (Hermitian positive semidefinite, l x l)
@@ -282,7 +286,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
       const int s2 = e % l, t = e / l, rI = ix.Iloc[s2];
       SD c = sc_zero<SD>();
       if (rI >= 0)
-        for (int q = 0; q < k; ++q) c += Ts[rI + q * MMAX] * Xs[q + t * KMAX];
+        for (int q = 0; q < k; ++q) c += Ts[rI + q * LDT] * Xs[q + t * KP];
       Cs[s2 + t * kRRMax] = c;
     }
     __syncwarp();
@@ -342,13 +346,13 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     // w = X v (eq. condwj for the refined v)
     if (lane < k) {
       SD x = sc_zero<SD>();
-      for (int t = 0; t < l; ++t) x += Xs[lane + t * KMAX] * vv[t];
+      for (int t = 0; t < l; ++t) x += Xs[lane + t * KP] * vv[t];
       wv[lane] = x;
     }
     __syncwarp();
   }
   DIAF_PHASE(9);
-  finish_column<SD, MMAX>(a, j, k, m, l, jpos, Ts, wv, vv, ix, flags, true, lane);
+  finish_column<SD, LDT>(a, j, k, m, l, jpos, Ts, wv, vv, ix, flags, true, lane);
   DIAF_PHASE(10);
 }
 
@@ -356,7 +360,7 @@ template <class S, int KMAX, int MMAX, int ALG>
 __global__ void column_mixed_kernel(ColArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned char* smem = smem_raw + warp * MixedLayout<S, KMAX, MMAX>::bytes();
+  unsigned char* smem = smem_raw + warp * MixedLayout<S, KMAX, MMAX, ALG>::bytes();
   const int count = *a.list_count;
   while (true) {
     int idx = 0;

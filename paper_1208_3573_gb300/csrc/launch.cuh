@@ -9,10 +9,11 @@
 // (count_hint: an upper bound of the device-side count, for grid sizing).
 // The work counter in `a` must be zero.  cudaErrorNotSupported: no kernel for
 // this bucket.
-cudaError_t launch_columns_f64(int bucket, int alg, const ColArgs& a, int count_hint, cudaStream_t s);
-cudaError_t launch_columns_c128(int bucket, int alg, const ColArgs& a, int count_hint, cudaStream_t s);
-cudaError_t launch_columns_mixed_f32(int bucket, int alg, const ColArgs& a, int count_hint, cudaStream_t s);
-cudaError_t launch_columns_mixed_c64(int bucket, int alg, const ColArgs& a, int count_hint, cudaStream_t s);
+// wpb: warps per block (0 = the most warps resident per SM).
+cudaError_t launch_columns_f64(int bucket, int alg, const ColArgs& a, int count_hint, int wpb, cudaStream_t s);
+cudaError_t launch_columns_c128(int bucket, int alg, const ColArgs& a, int count_hint, int wpb, cudaStream_t s);
+cudaError_t launch_columns_mixed_f32(int bucket, int alg, const ColArgs& a, int count_hint, int wpb, cudaStream_t s);
+cudaError_t launch_columns_mixed_c64(int bucket, int alg, const ColArgs& a, int count_hint, int wpb, cudaStream_t s);
 
 // Size bucket 2 (one CTA per column, FP64 / complex128): grid size for the
 // scratch slabs (0 on error) and the launch itself.
@@ -21,16 +22,24 @@ cudaError_t launch_columns_cta(int dtype, int alg, const ColArgs& a, const CtaSc
 
 // Persistent grid sized by occupancy; `per_warp` bytes of shared memory per warp.
 template <class Kern>
-cudaError_t launch_persistent_warps(Kern kern, size_t per_warp, bool& configured, const ColArgs& a, int count_hint,
-                                    cudaStream_t s) {
+cudaError_t launch_persistent_warps(Kern kern, size_t per_warp, size_t& configured, const ColArgs& a, int count_hint,
+                                    int wpb_req, cudaStream_t s) {
   if (count_hint <= 0) return cudaSuccess;
-  int wpb = (int)((96 * 1024) / per_warp);
-  wpb = wpb < 1 ? 1 : (wpb > 8 ? 8 : wpb);
+  // warps per block: the most warps resident per SM (228 KB of shared memory,
+  // 1 KB reserved per block), ties to the smaller block -- unless requested
+  int wpb = 1, best = 0;
+  for (int w = 1; w <= 8; ++w) {
+    const size_t blk = per_warp * w + 1024;
+    if (per_warp * w > 227 * 1024) break;
+    const int resident = (int)((228 * 1024) / blk) * w;
+    if (resident > best) { best = resident; wpb = w; }
+  }
+  if (wpb_req > 0 && per_warp * wpb_req <= 227 * 1024) wpb = wpb_req;
   const size_t smem = per_warp * wpb;
-  if (!configured) {  // one attribute call per instantiation and process
+  if (configured < smem) {  // attribute raised once per instantiation and size
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    configured = true;
+    configured = smem;
   }
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
@@ -45,15 +54,15 @@ cudaError_t launch_persistent_warps(Kern kern, size_t per_warp, bool& configured
 }
 
 template <class S, int KMAX, int MMAX, int ALG>
-cudaError_t launch_warp_columns(const ColArgs& a, int count_hint, cudaStream_t s) {
-  static bool configured = false;
+cudaError_t launch_warp_columns(const ColArgs& a, int count_hint, int wpb, cudaStream_t s) {
+  static size_t configured = 0;
   return launch_persistent_warps(column_warp_kernel<S, KMAX, MMAX, ALG>, WarpLayout<S, KMAX, MMAX>::bytes(),
-                                 configured, a, count_hint, s);
+                                 configured, a, count_hint, wpb, s);
 }
 
 template <class S, int KMAX, int MMAX, int ALG>
-cudaError_t launch_mixed_columns(const ColArgs& a, int count_hint, cudaStream_t s) {
-  static bool configured = false;
-  return launch_persistent_warps(column_mixed_kernel<S, KMAX, MMAX, ALG>, MixedLayout<S, KMAX, MMAX>::bytes(),
-                                 configured, a, count_hint, s);
+cudaError_t launch_mixed_columns(const ColArgs& a, int count_hint, int wpb, cudaStream_t s) {
+  static size_t configured = 0;
+  return launch_persistent_warps(column_mixed_kernel<S, KMAX, MMAX, ALG>, MixedLayout<S, KMAX, MMAX, ALG>::bytes(),
+                                 configured, a, count_hint, wpb, s);
 }

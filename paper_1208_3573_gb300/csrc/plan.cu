@@ -132,7 +132,8 @@ __device__ void finish_column(const PlanArgs& a, int j, const int32_t* s, int E,
     for (int t = 0; t < kNumBuckets; ++t) {
       int mm = m > k ? m : k;
       BucketCap cap = bucket_cap(t);
-      if (k <= cap.kmax && mm <= cap.mmax && l <= cap.lmax) { b = t; break; }
+      const int medge = t == 0 ? a.edge_m0 : (t == 1 ? a.edge_m1 : cap.mmax);
+      if (k <= cap.kmax && mm <= cap.mmax && mm <= medge && l <= cap.lmax) { b = t; break; }
     }
     if (b < 0) {
       atomicOr(a.status, DEV_ST_CAPACITY);

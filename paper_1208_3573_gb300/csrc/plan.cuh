@@ -28,6 +28,8 @@ struct PlanArgs {
   const int32_t* Vfcp;
   const int32_t* Vfri;
   const int32_t* budget;
+  int edge_m0;      // size-bucket edges (tuning): max(m, k) <= edge_m0 -> bucket 0, <= edge_m1 -> bucket 1
+  int edge_m1;
   // outputs
   int32_t* k;       // [n]
   int32_t* E;       // [n]

@@ -27,6 +27,11 @@ template <class R> __device__ __forceinline__ R sc_abs(Cx<R> a) { return sqrt(sc
 __device__ __forceinline__ double rsqrt_r(double a) { return rsqrt(a); }
 __device__ __forceinline__ float rsqrt_r(float a) { return rsqrtf(a); }
 
+// a / b: IEEE in FP64; the fast approximate division in FP32 (about 2 ulp),
+// whose results only seed the FP64 refinement of the mixed form
+__device__ __forceinline__ double div_r(double a, double b) { return a / b; }
+__device__ __forceinline__ float div_r(float a, float b) { return __fdividef(a, b); }
+
 // a / |a| (1 for a == 0)
 __device__ __forceinline__ double sc_unit(double a) { return a < 0.0 ? -1.0 : 1.0; }
 __device__ __forceinline__ float sc_unit(float a) { return a < 0.0f ? -1.0f : 1.0f; }
@@ -43,7 +48,7 @@ __device__ __forceinline__ S sc_recip_or_zero(S d, RealOf<S> piv) {
   using R = RealOf<S>;
   R a2 = sc_abs2(d);
   if (!(sc_abs(d) > piv)) return sc_zero<S>();
-  return (R(1) / a2) * sc_conj(d);
+  return div_r(R(1), a2) * sc_conj(d);
 }
 
 __device__ __forceinline__ bool admissible_row(int rule, int i, int j) {
@@ -75,7 +80,7 @@ __device__ void warp_householder_qr(S* T, int m, int k, int lane) {
     S ph = sc_unit(alpha);
     S beta = -(nrm * ph);
     S u0 = (ax + nrm) * ph;
-    R two_uu = R(1) / (nrm * (nrm + ax));
+    R two_uu = div_r(R(1), nrm * (nrm + ax));
     for (int q = c + 1; q < k; ++q) {
       S* tq = T + q * LD;
       S part = sc_zero<S>();
@@ -122,16 +127,21 @@ __device__ int warp_jacobi(S* G, int p, int q, S* V, int lane) {
   const int qq = (q + 1) & ~1;
   const int npairs = qq / 2;
   const int grp = lane / LPP, sub = lane % LPP;
+  const int L = qq - 1;
   for (int sweep = 1; sweep <= kMaxSweeps; ++sweep) {
     bool rotated = false;
-    for (int rnd = 0; rnd < qq - 1; ++rnd) {
+    for (int rnd = 0; rnd < L; ++rnd) {
       for (int pr0 = 0; pr0 < npairs; pr0 += kGroups) {
         int pr = pr0 + grp;
         int a = -1, b = -1;
         if (pr < npairs) {
-          int pa = pr, pb = qq - 1 - pr;
-          a = pa == 0 ? 0 : 1 + (pa - 1 + rnd) % (qq - 1);
-          b = 1 + (pb - 1 + rnd) % (qq - 1);
+          // position p >= 1 holds column 1 + ((p - 1 + rnd) mod L)
+          int pb = qq - 1 - pr;
+          int ea = pr - 1 + rnd, eb = pb - 1 + rnd;
+          if (ea >= L) ea -= L;
+          if (eb >= L) eb -= L;
+          a = pr == 0 ? 0 : 1 + ea;
+          b = 1 + eb;
           if (a > b) { int t = a; a = b; b = t; }
           if (b >= q) a = -1;  // bye for the padding column
         }
@@ -166,7 +176,7 @@ __device__ int warp_jacobi(S* G, int p, int q, S* V, int lane) {
             eph = sc_unit(ga);
           }
           const R d = be - al;
-          const R t = copysign(R(2) * ag, d) / (fabs(d) + sqrt(d * d + R(4) * ag2));
+          const R t = div_r(copysign(R(2) * ag, d), fabs(d) + sqrt(d * d + R(4) * ag2));
           const R cs = rsqrt_r(R(1) + t * t), sn = cs * t;
           S* ca = G + a * LDG;
           S* cb = G + b * LDG;

@@ -46,6 +46,20 @@ class VSpec_t(ctypes.Structure):
                 ("tie_tol", ctypes.c_double)]
 
 
+class Tuning_t(ctypes.Structure):
+    _fields_ = [("m_edge0", ctypes.c_int32), ("m_edge1", ctypes.c_int32), ("warps_per_block", ctypes.c_int32 * 2)]
+
+    def as_dict(self) -> dict:
+        return {"m_edge0": self.m_edge0, "m_edge1": self.m_edge1, "warps_per_block": list(self.warps_per_block)}
+
+    @staticmethod
+    def from_dict(d: dict | None) -> "Tuning_t | None":
+        if d is None:
+            return None
+        w = d.get("warps_per_block", [0, 0])
+        return Tuning_t(d.get("m_edge0", 0), d.get("m_edge1", 0), (ctypes.c_int32 * 2)(*w))
+
+
 class Info_t(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("dtype", ctypes.c_int32), ("alg", ctypes.c_int32), ("prec", ctypes.c_int32),
                 ("nnz_w", ctypes.c_int64), ("nnz_v", ctypes.c_int64), ("max_k", ctypes.c_int32),
@@ -71,6 +85,20 @@ def lib() -> ctypes.CDLL:
         vp = ctypes.c_void_p
         L.diaf_factor.argtypes = [ctypes.POINTER(CSC_t), ctypes.POINTER(Pattern_t), ctypes.POINTER(VSpec_t),
                                   ctypes.c_int32, ctypes.c_int32, vp, ctypes.POINTER(vp)]
+        L.diaf_factor_tuned.argtypes = [ctypes.POINTER(CSC_t), ctypes.POINTER(Pattern_t), ctypes.POINTER(VSpec_t),
+                                        ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(Tuning_t), vp,
+                                        ctypes.POINTER(vp)]
+        L.diaf_autotune.argtypes = [ctypes.POINTER(CSC_t), ctypes.POINTER(Pattern_t), ctypes.POINTER(VSpec_t),
+                                    ctypes.c_int32, ctypes.c_int32, vp, ctypes.POINTER(Tuning_t),
+                                    ctypes.POINTER(ctypes.c_float)]
+        L.diaf_plan_create.argtypes = [ctypes.POINTER(CSC_t), ctypes.POINTER(Pattern_t), ctypes.POINTER(VSpec_t),
+                                       ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(Tuning_t), vp,
+                                       ctypes.POINTER(vp)]
+        L.diaf_plan_execute.argtypes = [vp, vp]
+        L.diaf_plan_factors.argtypes = [vp]
+        L.diaf_plan_factors.restype = vp
+        L.diaf_plan_free.argtypes = [vp]
+        L.diaf_plan_free.restype = None
         L.diaf_factor_info_get.argtypes = [vp, ctypes.POINTER(Info_t)]
         L.diaf_get_factors.argtypes = [vp, ctypes.POINTER(CSC_t), ctypes.POINTER(CSC_t),
                                        ctypes.POINTER(vp), ctypes.POINTER(vp)]
@@ -163,15 +191,17 @@ def _view(ptr, count, typestr, owner, torch_dtype):
 
 
 class _Handle:
-    """Owns one diaf_factors*; freed when the last view or Factors drops it."""
+    """Owns one diaf_factors* (freed when the last view or Factors drops it),
+    or borrows it from an owner kept alive here (a plan's factors)."""
 
-    def __init__(self, ptr: int):
+    def __init__(self, ptr: int, owner=None):
         self.ptr = ctypes.c_void_p(ptr)
+        self.owner = owner
 
     def free(self):
-        if self.ptr.value:
+        if self.ptr.value and self.owner is None:
             lib().diaf_free(self.ptr)
-            self.ptr = ctypes.c_void_p(0)
+        self.ptr = ctypes.c_void_p(0)
 
     def __del__(self):
         try:
@@ -187,8 +217,8 @@ class Factors:
     handle alive.  close() frees the buffers at once (the views must not be
     used afterwards)."""
 
-    def __init__(self, handle: int, stream: int):
-        self._own = _Handle(handle)
+    def __init__(self, handle: int, stream: int, owner=None):
+        self._own = _Handle(handle, owner)
         self._stream = stream
         L = lib()
         info = Info_t()
@@ -252,20 +282,69 @@ def launch_count() -> int:
     return int(lib().diaf_launch_count())
 
 
-def factor(A: DeviceCSC, PW: DeviceCSC, vrule: int = RULE_UPPER, budget: torch.Tensor | None = None,
-           Vfixed: DeviceCSC | None = None, alg: str = "S", prec: str = "fp64", tie_tol: float = 1e-9,
-           stream=None) -> Factors:
-    """Columnwise W, V with A W ~ V (diaf_factor)."""
-    L = lib()
+def _args(A, PW, vrule, budget, Vfixed, tie_tol):
     a = A.csc_t()
     pw = PW.pattern_t()
     fixed = Vfixed.pattern_t() if Vfixed is not None else None
     vs = VSpec_t(vrule, ctypes.pointer(fixed) if fixed is not None else None, _ptr(budget), tie_tol)
+    return a, pw, vs, fixed
+
+
+def factor(A: DeviceCSC, PW: DeviceCSC, vrule: int = RULE_UPPER, budget: torch.Tensor | None = None,
+           Vfixed: DeviceCSC | None = None, alg: str = "S", prec: str = "fp64", tie_tol: float = 1e-9,
+           stream=None, tuning: dict | None = None) -> Factors:
+    """Columnwise W, V with A W ~ V (diaf_factor / diaf_factor_tuned)."""
+    L = lib()
+    a, pw, vs, _keep = _args(A, PW, vrule, budget, Vfixed, tie_tol)
     h = ctypes.c_void_p()
     s = _stream(stream)
-    _check(L.diaf_factor(ctypes.byref(a), ctypes.byref(pw), ctypes.byref(vs), ALG[alg], PREC[prec], s,
-                         ctypes.byref(h)))
+    t = Tuning_t.from_dict(tuning)
+    _check(L.diaf_factor_tuned(ctypes.byref(a), ctypes.byref(pw), ctypes.byref(vs), ALG[alg], PREC[prec],
+                               ctypes.byref(t) if t is not None else None, s, ctypes.byref(h)))
     return Factors(h.value, s)
+
+
+def autotune(A: DeviceCSC, PW: DeviceCSC, vrule: int = RULE_UPPER, budget: torch.Tensor | None = None,
+             Vfixed: DeviceCSC | None = None, alg: str = "S", prec: str = "fp64", tie_tol: float = 1e-9,
+             stream=None) -> tuple[dict, float]:
+    """Fastest launch tuning of the numeric pass (diaf_autotune) and its time in ms."""
+    L = lib()
+    a, pw, vs, _keep = _args(A, PW, vrule, budget, Vfixed, tie_tol)
+    best = Tuning_t()
+    ms = ctypes.c_float()
+    _check(L.diaf_autotune(ctypes.byref(a), ctypes.byref(pw), ctypes.byref(vs), ALG[alg], PREC[prec],
+                           _stream(stream), ctypes.byref(best), ctypes.byref(ms)))
+    return best.as_dict(), float(ms.value)
+
+
+class Plan:
+    """Symbolic pass once, numeric pass captured in a CUDA graph
+    (diaf_plan_create); execute() replays it on the current values of A."""
+
+    def __init__(self, A: DeviceCSC, PW: DeviceCSC, vrule: int = RULE_UPPER, budget: torch.Tensor | None = None,
+                 Vfixed: DeviceCSC | None = None, alg: str = "S", prec: str = "fp64", tie_tol: float = 1e-9,
+                 stream=None, tuning: dict | None = None):
+        L = lib()
+        self._inputs = (A, PW, budget, Vfixed)  # the plan reads these buffers by pointer
+        a, pw, vs, _keep = _args(A, PW, vrule, budget, Vfixed, tie_tol)
+        t = Tuning_t.from_dict(tuning)
+        h = ctypes.c_void_p()
+        s = _stream(stream)
+        _check(L.diaf_plan_create(ctypes.byref(a), ctypes.byref(pw), ctypes.byref(vs), ALG[alg], PREC[prec],
+                                  ctypes.byref(t) if t is not None else None, s, ctypes.byref(h)))
+        self._h = h
+        self.factors = Factors(L.diaf_plan_factors(h), s, owner=self)
+
+    def execute(self, stream=None) -> Factors:
+        _check(lib().diaf_plan_execute(self._h, _stream(stream)))
+        return self.factors
+
+    def __del__(self):
+        try:
+            if self._h.value:
+                lib().diaf_plan_free(self._h)
+        except Exception:
+            pass
 
 
 class Solver:

@@ -165,6 +165,80 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def learned_report(dev, keep=12, train_N=40, train_seeds=(11, 12), eval_N=64, epochs=20):
+    """The learned J_j proposal against the fixed sparsified-powers rule at
+    equal nnz(W): trained from scratch on the GPU (targets from FP64 solves
+    on train_N^3 instances), evaluated on the eval_N^3 lognormal operator with
+    candidates pattern(A^2) and V diagonal."""
+    import torch
+    from paper_1208_3573_gb300 import diaf
+    from paper_1208_3573_gb300.learned import Proposer, toggle_targets, scaled_residuals
+    from workloads import patterns as pats
+    from workloads.configs import lognormal
+
+    def wl(N, seed):
+        w = lognormal(N, seed)
+        w.budget = np.ones(w.n, dtype=np.int32)
+        return w
+
+    t0 = time.perf_counter()
+    feats, targs = [], []
+    for seed in train_seeds:
+        w = wl(train_N, seed)
+        CAND = pats.pattern_power(w.A, 2)
+        Ad = diaf.DeviceCSC.from_host(w.A, dev)
+        T = toggle_targets(Ad, CAND, pats.neumann_pattern(w.A, 2, 0, keep), torch.from_numpy(w.budget).to(dev),
+                           w.vrule, w.tie_tol)
+        feats.append(diaf.propose_features(Ad, diaf.DeviceCSC.from_host(CAND, dev)))
+        targs.append(T.value)
+    torch.cuda.synchronize()
+    t_targets = time.perf_counter() - t0
+    net = Proposer(seed=0, device=dev)
+    t0 = time.perf_counter()
+    hist = net.fit(feats, targs, epochs=epochs, batch=4096, lr=3e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    w = wl(eval_N, 0)
+    Ad = diaf.DeviceCSC.from_host(w.A, dev)
+    CAND = diaf.DeviceCSC.from_host(pats.pattern_power(w.A, 2), dev)
+    bud = torch.from_numpy(w.budget).to(dev)
+    b = torch.from_numpy(w.b).to(dev)
+    S = diaf.Solver(Ad)
+
+    def events(fn, reps=5):
+        out, ts = None, []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(); out = fn(); e1.record(); e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return out, statistics.median(ts)
+
+    J, propose_ms = events(lambda: net.propose(Ad, CAND, keep))
+    rules = {"learned": J, "fixed_sparsified_powers": diaf.DeviceCSC.from_host(pats.neumann_pattern(w.A, 2, 0, keep), dev)}
+    out = {"workload": w.name, "V": "diagonal (l_j = 1)", "candidates": "pattern(A^2)", "keep": keep,
+           "train": {"instances": f"{train_N}^3 seeds {list(train_seeds)}", "targets_s": t_targets, "train_s": t_train,
+                     "rows": int(sum(np.isfinite(t).sum() for t in targs)), "loss_first": hist[0],
+                     "loss_last": hist[-1]},
+           "propose_ms": propose_ms}
+    for name, P in rules.items():
+        r = {"nnz_W": P.nnz}
+        for prec in ("mixed32", "fp64"):
+            F, ms = events(lambda: diaf.factor(Ad, P, w.vrule, bud, alg="S", prec=prec, tie_tol=w.tie_tol), 3)
+            r[f"factor_ms_{prec}"] = ms
+        sr = scaled_residuals(F)
+        r["fro2_AWVinv_minus_I"] = float(np.sum(sr ** 2))
+        r["colres_median"] = float(np.median(sr))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, info = S.bicgstab(b, F, tol=1e-8, maxit=2000)
+        torch.cuda.synchronize()
+        r.update(bicgstab_its=info.iterations, converged=bool(info.converged),
+                 solve_ms=1e3 * (time.perf_counter() - t0))
+        F.close()
+        out[name] = r
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -177,6 +251,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the solve / other-form side measurements")
     ap.add_argument("--no-autotune", action="store_true", help="default launch tuning instead of diaf_autotune")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned J_j proposal report")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -366,6 +441,11 @@ def main():
             tt.append(Fo.timings()["total_ms"])
             Fo.close()
         extras[f"alg_{other}_factor_columns_per_s"] = w.n / (statistics.median(tt) / 1e3)
+    if not args.no_extras and not args.no_learned and rank == 0:
+        try:
+            extras["learned_proposal"] = learned_report(dev)
+        except Exception as e:  # reported, not fatal: the setup metric above stands on its own
+            extras["learned_proposal"] = {"error": f"{type(e).__name__}: {e}"[:300]}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

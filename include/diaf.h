@@ -272,6 +272,46 @@ typedef struct {
 diaf_status diaf_bicgstab(diaf_solver* S, diaf_factors* F, const void* b, void* x, double tol, int32_t maxit,
                           void* stream, diaf_solve_info* info);
 
+/* ---- Learned proposal of the W pattern J_j ----------------------------------
+ * Not in the paper: Sec. 4 chooses J_j by fixed rules (pattern(A), powers of
+ * A, dropping by position).  Here a small network scores every candidate row
+ * c of a candidate pattern CAND(:,j) (typically pattern(A^2)) and the best
+ * ones are kept.  Features per candidate (DIAF_PROP_NFEAT floats, row-major
+ * [CAND->nnz][8], in CAND's entry order):
+ *   0 c == j   1 c is a row of A(:,j)   2 |A_cj| / max_i |A_ij|
+ *   3 |(A^2)_cj| / max over CAND(:,j) of |(A^2)_c'j|
+ *   4 log(|a_cc| / |a_jj|) clamped to [-10, 10] (0 if either is zero)
+ *   5 |A_jc| / |a_jj|   6 nnz(A(:,c)) / nnz(A(:,j))   7 sign(j - c)
+ * The network is 8 -> 32 -> 32 -> 1 with ReLU after both hidden layers;
+ * parameters are DIAF_PROP_NPARAM floats: W1[32][8], b1[32], W2[32][32],
+ * b2[32], w3[32], b3.  All pointers below are device pointers. */
+#define DIAF_PROP_NFEAT 8
+#define DIAF_PROP_HIDDEN 32
+#define DIAF_PROP_NPARAM 1377
+
+/* Features of every entry of CAND (same n as A, sorted columns of at most 32
+ * rows; DIAF_EUNSUPPORTED for a longer column).  Synchronises `stream`. */
+diaf_status diaf_propose_features(const diaf_csc* A, const diaf_pattern* CAND, float* feat, void* stream);
+
+/* out[s] = network(feat[s]) for s < nrows.  Stream-ordered, allocates nothing. */
+diaf_status diaf_mlp_forward(const float* params, const float* feat, int64_t nrows, float* out, void* stream);
+
+/* grad = d/dparams of loss = (1/nrows) sum_s (network(feat[s]) - target[s])^2,
+ * *loss = that loss (both overwritten; grad has DIAF_PROP_NPARAM floats).
+ * Sums are formed with float atomics: the order, and so the last bits, vary. */
+diaf_status diaf_mlp_grad(const float* params, const float* feat, const float* target, int64_t nrows, float* grad,
+                          float* loss, void* stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on params with moment
+ * buffers m, v (DIAF_PROP_NPARAM floats each, zero before step 1); step >= 1. */
+diaf_status diaf_mlp_adam(float* params, const float* grad, float* m, float* v, int32_t step, float lr, void* stream);
+
+/* Keeps, per column j, min(keep, |CAND(:,j)|) rows: j itself when it is a
+ * candidate, then the best scores (ties to the lower row; NaN ranks last).
+ * colptr (n+1) and rowidx (at most n*keep) are written; rows come out sorted. */
+diaf_status diaf_propose_select(const diaf_pattern* CAND, const float* score, int32_t keep, int32_t* colptr,
+                                int32_t* rowidx, void* stream);
+
 const char* diaf_status_string(diaf_status s);
 const char* diaf_last_error(void);
 

@@ -114,6 +114,11 @@ def lib() -> ctypes.CDLL:
         L.diaf_factor_timings.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]
         L.diaf_launch_count.restype = ctypes.c_longlong
         L.diaf_factor_fallbacks.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]
+        L.diaf_propose_features.argtypes = [ctypes.POINTER(CSC_t), ctypes.POINTER(Pattern_t), vp, vp]
+        L.diaf_mlp_forward.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
+        L.diaf_mlp_grad.argtypes = [vp, vp, vp, ctypes.c_int64, vp, vp, vp]
+        L.diaf_mlp_adam.argtypes = [vp, vp, vp, vp, ctypes.c_int32, ctypes.c_float, vp]
+        L.diaf_propose_select.argtypes = [ctypes.POINTER(Pattern_t), vp, ctypes.c_int32, vp, vp, vp]
         L.diaf_status_string.argtypes = [ctypes.c_int]
         L.diaf_status_string.restype = ctypes.c_char_p
         L.diaf_last_error.restype = ctypes.c_char_p
@@ -370,3 +375,55 @@ class Solver:
                 lib().diaf_solver_free(self._h)
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- learned proposal of J_j
+PROP_NFEAT, PROP_HIDDEN, PROP_NPARAM = 8, 32, 1377
+
+
+def propose_features(A: DeviceCSC, CAND: DeviceCSC, stream=None) -> torch.Tensor:
+    """[CAND.nnz, 8] float32 candidate features (diaf_propose_features)."""
+    feat = torch.empty((CAND.nnz, PROP_NFEAT), dtype=torch.float32, device=A.colptr.device)
+    a, c = A.csc_t(), CAND.pattern_t()
+    _check(lib().diaf_propose_features(ctypes.byref(a), ctypes.byref(c), _ptr(feat), _stream(stream)))
+    return feat
+
+
+def mlp_forward(params: torch.Tensor, feat: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    """Scores of the network on every feature row (diaf_mlp_forward)."""
+    assert params.dtype == torch.float32 and params.numel() == PROP_NPARAM and feat.dtype == torch.float32
+    n = feat.shape[0]
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=feat.device)
+    _check(lib().diaf_mlp_forward(_ptr(params), _ptr(feat), n, _ptr(out), _stream(stream)))
+    return out
+
+
+def mlp_grad(params: torch.Tensor, feat: torch.Tensor, target: torch.Tensor, grad: torch.Tensor | None = None,
+             loss: torch.Tensor | None = None, stream=None):
+    """(grad, loss) of the mean squared error (diaf_mlp_grad); loss stays on the device."""
+    assert target.dtype == torch.float32 and target.numel() == feat.shape[0]
+    if grad is None:
+        grad = torch.empty(PROP_NPARAM, dtype=torch.float32, device=feat.device)
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float32, device=feat.device)
+    _check(lib().diaf_mlp_grad(_ptr(params), _ptr(feat), _ptr(target), feat.shape[0], _ptr(grad), _ptr(loss),
+                               _stream(stream)))
+    return grad, loss
+
+
+def mlp_adam(params, grad, m, v, step: int, lr: float, stream=None) -> None:
+    """One Adam step in place on params, m, v (diaf_mlp_adam)."""
+    _check(lib().diaf_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), step, lr, _stream(stream)))
+
+
+def propose_select(CAND: DeviceCSC, score: torch.Tensor, keep: int, stream=None) -> DeviceCSC:
+    """Kept pattern (diagonal + best scores, at most `keep` per column) as a DeviceCSC pattern."""
+    dev = CAND.colptr.device
+    colptr = torch.empty(CAND.n + 1, dtype=torch.int32, device=dev)
+    rowidx = torch.empty(max(1, min(CAND.nnz, CAND.n * keep)), dtype=torch.int32, device=dev)
+    c = CAND.pattern_t()
+    _check(lib().diaf_propose_select(ctypes.byref(c), _ptr(score), keep, _ptr(colptr), _ptr(rowidx),
+                                     _stream(stream)))
+    nnz = int(colptr[-1].item())
+    return DeviceCSC(CAND.n, colptr, rowidx[:nnz].clone())

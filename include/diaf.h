@@ -77,9 +77,10 @@ enum {
   DIAF_FLAG_JACOBI_NOCONV = 8,   /* the Jacobi SVD hit its 30-sweep limit */
   DIAF_FLAG_NONFINITE = 16,      /* NaN or Inf in w_j, v_j or res_j */
   DIAF_FLAG_EMPTY = 32,          /* k_j = 0 (empty W column) */
-  DIAF_FLAG_FP64_FALLBACK = 64   /* mixed precision: the column was computed by the FP64 path (an FP32
+  DIAF_FLAG_FP64_FALLBACK = 64,  /* mixed precision: the column was computed by the FP64 path (an FP32
                                     leverage decision within its error bound, a tile too ill-conditioned
                                     for FP32 factors, or a large tile: k_j > 32 or m_j > 64) */
+  DIAF_FLAG_STABILISED = 128     /* DIAF-Q: v_jj was imposed (stabilised column of Sec. 3.2) */
 };
 
 typedef struct {
@@ -105,6 +106,16 @@ typedef struct {
                                  capped by 1 + the number of admissible rows; NULL = all admissible */
   double tie_tol;             /* leverage keys within tie_tol of the current largest count as tied and the
                                  lower row is taken; <= 0 selects the default 1e-9 */
+  /* Stabilised DIAF-Q (Sec. 3.2; ignored by DIAF-S): where the unit v_j of
+   * eq. nocond has |v_jj| < stab_tol, v_jj is imposed as stab_r (<= 0: 2, the
+   * value of the paper's experiments) and the other entries are the top
+   * singular vector of Q(I_j without j, :)^* with the phase that maximises
+   * ||Q(I_j,:)^* v_j||; v_j is then scaled to unit norm and w_j solves
+   * eq. condwj as before (flag DIAF_FLAG_STABILISED).  stab_tol <= 0 turns it
+   * off; the paper's experiments use 1e-2.  Zero-initialised structs keep
+   * the plain method. */
+  double stab_tol;
+  double stab_r;
 } diaf_vspec;
 
 typedef struct diaf_factors diaf_factors; /* opaque, library-owned */

@@ -30,6 +30,14 @@
  *   5b. DIAF-Q (Sec. 2.1): M_j = Q(I_j,:)^* (k x l); v_j = top right singular
  *       vector of M_j (eq. nocond), via one-sided Jacobi; w_j solves the
  *       least-squares problem eq. condwj, R w = Q^* v = M_j v.
+ *   5c. Stabilised DIAF-Q (Sec. 3.2, optional): when |v_jj| < stab_tol
+ *       (v_j of unit norm), the j-th component is imposed as r > 0 and the
+ *       rest is taken from the SVD of M_hat = the columns of M_j other than
+ *       j: v_hat = e^{i theta} z, z its top right singular vector, theta the
+ *       argument of the first component of U_hat^* p (p = column j of M_j);
+ *       v_j = r e_j + v_hat, scaled to unit norm; w_j from eq. condwj as
+ *       before.  Flag STABILISED (and DEGENERATE where z or theta is not
+ *       unique).
  *   6. Phase: scale (w_j, v_j) by a unit scalar so that v_jj is real >= 0
  *      (allowed by the scaling-invariance theorem of Sec. 2.1).  When v_jj is
  *      zero to rounding (|v_jj| <= 64 eps ||v_j||) the flag VJJ_ZERO is set
@@ -52,7 +60,7 @@ enum { RULE_FIXED = 0, RULE_UPPER = 1, RULE_LOWER = 2, RULE_ALL = 3 };
 enum { ALG_Q = 1, ALG_S = 2 };
 enum {
     F_RANK_DEFICIENT = 1u, F_DEGENERATE = 2u, F_VJJ_ZERO = 4u,
-    F_JACOBI_NOCONV = 8u, F_NONFINITE = 16u, F_EMPTY = 32u
+    F_JACOBI_NOCONV = 8u, F_NONFINITE = 16u, F_EMPTY = 32u, F_STABILISED = 128u
 };
 #define MAX_SWEEPS 30
 
@@ -268,6 +276,7 @@ typedef struct {
     const int *Vcp, *Vri, *budget;
     int alg;
     double tie_tol;
+    double stab_tol, stab_r;  /* stabilised DIAF-Q: trigger |v_jj| < stab_tol (0: off), imposed v_jj = r */
 } problem;
 
 typedef struct {
@@ -399,6 +408,47 @@ static void solve_column(const problem *P, int j, colout *out, double *h_dbg, in
         out->sig_next = l > 1 ? snext : 0.0;
         if (sg[imax] == 0.0 || (l > 1 && (sg[imax] - snext) <= 1e-6 * sg[imax])) flags |= F_DEGENERATE;
         for (int t = 0; t < l; ++t) v[t] = Vm[t + (size_t)imax * l];
+        /* 5c. stabilisation (Sec. 3.2): v_jj too small -> impose it */
+        if (P->stab_tol > 0.0 && jpos >= 0 && l > 1 && cabs(v[jpos]) < P->stab_tol) {
+            int lh = l - 1;
+            zd *Mh = (zd *)malloc(sizeof(zd) * ((size_t)k * lh + 1));
+            for (int t = 0, u = 0; t < l; ++t) {
+                if (t == jpos) continue;
+                for (int c = 0; c < k; ++c) Mh[c + (size_t)u * k] = M[c + (size_t)t * k];
+                ++u;
+            }
+            zd *Vh = (zd *)malloc(sizeof(zd) * ((size_t)lh * lh + 1));
+            double *sh = (double *)malloc(sizeof(double) * (lh + 1));
+            /* one-sided Jacobi on M_hat: its columns become U_hat Sigma_hat, Vh = V_hat */
+            if (jacobi_svd(k, lh, Mh, Vh, sh) < 0) flags |= F_JACOBI_NOCONV;
+            int i1 = 0;
+            for (int i = 1; i < lh; ++i) if (sh[i] > sh[i1]) i1 = i;
+            double s2 = -INFINITY;
+            for (int i = 0; i < lh; ++i) if (i != i1 && sh[i] > s2) s2 = sh[i];
+            /* the DEGENERATE flag now describes the stabilised problem */
+            flags &= ~F_DEGENERATE;
+            if (sh[i1] == 0.0 || (lh > 1 && (sh[i1] - s2) <= 1e-6 * sh[i1])) flags |= F_DEGENERATE;
+            /* first component of U_hat^* p, U_hat(:,1) = M_hat(:,i1) / sigma_1 */
+            zd pt = 0.0;
+            for (int c = 0; c < k; ++c) pt += conj(Mh[c + (size_t)i1 * k]) * M[c + (size_t)jpos * k];
+            /* p_tilde_1 = 0: every theta gives the same objective (the paper: any
+             * theta will do); theta = 0 is taken and the column is DEGENERATE */
+            double pn = 0.0;
+            for (int c = 0; c < k; ++c) pn += abs2(M[c + (size_t)jpos * k]);
+            if (cabs(pt) <= 1e-10 * sh[i1] * sqrt(pn)) flags |= F_DEGENERATE;
+            zd eth = cabs(pt) > 0.0 ? pt / cabs(pt) : 1.0;
+            double r = P->stab_r > 0.0 ? P->stab_r : 2.0;
+            double sc = 1.0 / sqrt(r * r + 1.0);
+            for (int t = 0, u = 0; t < l; ++t) {
+                if (t == jpos) { v[t] = r * sc; continue; }
+                v[t] = sc * eth * Vh[u + (size_t)i1 * lh];
+                ++u;
+            }
+            out->sig_sel = sh[i1];
+            out->sig_next = lh > 1 ? s2 : 0.0;
+            flags |= F_STABILISED;
+            free(Mh); free(Vh); free(sh);
+        }
         /* eq. condwj: R w = Q^* v_full = M v */
         zd *z = (zd *)calloc(k + 1, sizeof(zd));
         for (int c = 0; c < k; ++c)
@@ -458,8 +508,9 @@ static void solve_column(const problem *P, int j, colout *out, double *h_dbg, in
 /* ------------------------------------------------------------ ABI ---- */
 static problem make_problem(int n, const int *Acp, const int *Ari, const double *Av,
                             const int *Wcp, const int *Wri, int rule, const int *Vcp,
-                            const int *Vri, const int *budget, int alg, double tie_tol) {
-    problem P = {n, Acp, Ari, (const zd *)Av, Wcp, Wri, rule, Vcp, Vri, budget, alg, tie_tol};
+                            const int *Vri, const int *budget, int alg, double tie_tol,
+                            double stab_tol, double stab_r) {
+    problem P = {n, Acp, Ari, (const zd *)Av, Wcp, Wri, rule, Vcp, Vri, budget, alg, tie_tol, stab_tol, stab_r};
     return P;
 }
 
@@ -467,7 +518,7 @@ static problem make_problem(int n, const int *Acp, const int *Ari, const double 
 int diaf_oracle_vcount(int n, const int *Acp, const int *Ari, const int *Wcp, const int *Wri,
                        int rule, const int *Vcp, const int *Vri, const int *budget,
                        int ncols, const int *cols, int *lcount, int nthreads) {
-    problem P = make_problem(n, Acp, Ari, NULL, Wcp, Wri, rule, Vcp, Vri, budget, ALG_S, 0.0);
+    problem P = make_problem(n, Acp, Ari, NULL, Wcp, Wri, rule, Vcp, Vri, budget, ALG_S, 0.0, 0.0, 0.0);
     if (nthreads <= 0) nthreads = 1;
 #pragma omp parallel for schedule(dynamic, 256) num_threads(nthreads)
     for (int t = 0; t < ncols; ++t) lcount[t] = count_l(&P, cols ? cols[t] : t);
@@ -480,10 +531,11 @@ int diaf_oracle_vcount(int n, const int *Acp, const int *Ari, const int *Wcp, co
 int diaf_oracle_factor(int n, const int *Acp, const int *Ari, const double *Av,
                        const int *Wcp, const int *Wri, int rule, const int *Vcp,
                        const int *Vri, const int *budget, int alg, double tie_tol,
+                       double stab_tol, double stab_r,
                        int ncols, const int *cols, const long long *voff,
                        double *Wv, int *Vri_out, double *Vv, double *res,
                        unsigned *flags, double *margin, double *sig, int nthreads) {
-    problem P = make_problem(n, Acp, Ari, Av, Wcp, Wri, rule, Vcp, Vri, budget, alg, tie_tol);
+    problem P = make_problem(n, Acp, Ari, Av, Wcp, Wri, rule, Vcp, Vri, budget, alg, tie_tol, stab_tol, stab_r);
     if (nthreads <= 0) nthreads = 1;
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads)
     for (int t = 0; t < ncols; ++t) {
@@ -505,10 +557,11 @@ int diaf_oracle_factor(int n, const int *Acp, const int *Ari, const double *Av,
 /* Single column with its tile rows and leverage (for tests). */
 int diaf_oracle_column(int n, const int *Acp, const int *Ari, const double *Av,
                        const int *Wcp, const int *Wri, int rule, const int *Vcp,
-                       const int *Vri, const int *budget, int alg, double tie_tol, int j,
+                       const int *Vri, const int *budget, int alg, double tie_tol,
+                       double stab_tol, double stab_r, int j,
                        double *w, int *Irows, double *v, double *res, unsigned *flags,
                        double *margin, double *sig, int *m, int *rows, double *h) {
-    problem P = make_problem(n, Acp, Ari, Av, Wcp, Wri, rule, Vcp, Vri, budget, alg, tie_tol);
+    problem P = make_problem(n, Acp, Ari, Av, Wcp, Wri, rule, Vcp, Vri, budget, alg, tie_tol, stab_tol, stab_r);
     colout o = {(zd *)w, Irows, (zd *)v, 0, 0, 0, 0, 0};
     solve_column(&P, j, &o, h, rows, m);
     *res = o.res; *flags = o.flags; *margin = o.margin;

@@ -20,6 +20,7 @@ from . import build as _build
 RULE_FIXED, RULE_UPPER, RULE_LOWER, RULE_ALL = 0, 1, 2, 3
 ALG = {"Q": 1, "S": 2}
 F_RANK_DEFICIENT, F_DEGENERATE, F_VJJ_ZERO, F_JACOBI_NOCONV, F_NONFINITE, F_EMPTY = 1, 2, 4, 8, 16, 32
+F_STABILISED = 128
 TIE_TOL = 1e-9  # leverage keys within this distance of the largest count as tied (lower row wins)
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -36,10 +37,12 @@ def _load():
         L.diaf_oracle_vcount.argtypes = [ctypes.c_int, _i32p, _i32p, _i32p, _i32p, ctypes.c_int, _i32p, _i32p,
                                          _i32p, ctypes.c_int, _i32p, _i32p, ctypes.c_int]
         L.diaf_oracle_factor.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _i32p, _i32p, ctypes.c_int, _i32p,
-                                         _i32p, _i32p, ctypes.c_int, ctypes.c_double, ctypes.c_int, _i32p, _i64p,
+                                         _i32p, _i32p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_int, _i32p, _i64p,
                                          _f64p, _i32p, _f64p, _f64p, _u32p, _f64p, _f64p, ctypes.c_int]
         L.diaf_oracle_column.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _i32p, _i32p, ctypes.c_int, _i32p,
-                                         _i32p, _i32p, ctypes.c_int, ctypes.c_double, ctypes.c_int, _f64p, _i32p,
+                                         _i32p, _i32p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_int, _f64p, _i32p,
                                          _f64p, _f64p, _u32p, _f64p, _f64p, _i32p, _i32p, _f64p]
         L.diaf_oracle_qr.argtypes = [ctypes.c_int, ctypes.c_int, _f64p, _f64p, _f64p]
         L.diaf_oracle_jacobi_svd.argtypes = [ctypes.c_int, ctypes.c_int, _f64p, _f64p, _f64p]
@@ -130,9 +133,10 @@ def vcount(A, PW, vrule=RULE_UPPER, budget=None, Vfixed=None, cols=None, nthread
 
 
 def factor(A, PW, vrule=RULE_UPPER, budget=None, Vfixed=None, alg="S", tie_tol=TIE_TOL, cols=None,
-           nthreads=None) -> OracleResult:
+           nthreads=None, stab_tol=0.0, stab_r=2.0) -> OracleResult:
     """Columnwise W, V (Sec. 2.1 / 2.2 with the V rule of Sec. 3.1) for the
-    listed columns (all when cols is None)."""
+    listed columns (all when cols is None).  stab_tol > 0 turns on the
+    stabilised DIAF-Q of Sec. 3.2 (|v_jj| < stab_tol -> v_jj imposed as stab_r)."""
     L = _load()
     x = _Inputs(A, PW, vrule, budget, Vfixed)
     cl = np.arange(A.n, dtype=np.int32) if cols is None else np.ascontiguousarray(cols, np.int32)
@@ -144,7 +148,8 @@ def factor(A, PW, vrule=RULE_UPPER, budget=None, Vfixed=None, alg="S", tie_tol=T
     Vri = np.zeros(int(voff[-1]), np.int32)
     Vv = np.zeros(int(voff[-1]), np.complex128)
     res = np.zeros(nc); flags = np.zeros(nc, np.uint32); margin = np.zeros(nc); sig = np.zeros((nc, 2))
-    L.diaf_oracle_factor(*x.head(), _p(x.Av, _f64p), *x.wv(), ALG[alg], float(tie_tol), nc, _p(cl, _i32p),
+    L.diaf_oracle_factor(*x.head(), _p(x.Av, _f64p), *x.wv(), ALG[alg], float(tie_tol), float(stab_tol),
+                         float(stab_r), nc, _p(cl, _i32p),
                          _p(voff, _i64p), _p(Wv.view(np.float64), _f64p), _p(Vri, _i32p),
                          _p(Vv.view(np.float64), _f64p), _p(res, _f64p), _p(flags, _u32p), _p(margin, _f64p),
                          _p(sig, _f64p), _nthreads(nthreads))
@@ -168,7 +173,8 @@ class ColumnInfo:
     sig: np.ndarray
 
 
-def column(A, PW, j, vrule=RULE_UPPER, budget=None, Vfixed=None, alg="S", tie_tol=TIE_TOL) -> ColumnInfo:
+def column(A, PW, j, vrule=RULE_UPPER, budget=None, Vfixed=None, alg="S", tie_tol=TIE_TOL, stab_tol=0.0,
+           stab_r=2.0) -> ColumnInfo:
     L = _load()
     x = _Inputs(A, PW, vrule, budget, Vfixed)
     k = int(PW.colptr[j + 1] - PW.colptr[j])
@@ -177,7 +183,8 @@ def column(A, PW, j, vrule=RULE_UPPER, budget=None, Vfixed=None, alg="S", tie_to
     w = np.zeros(max(k, 1), np.complex128); Ir = np.zeros(max(l, 1), np.int32); v = np.zeros(max(l, 1), np.complex128)
     res = ctypes.c_double(); fl = ctypes.c_uint32(); mg = ctypes.c_double(); sig = np.zeros(2)
     m = ctypes.c_int32(); rows = np.zeros(mcap, np.int32); h = np.zeros(mcap)
-    L.diaf_oracle_column(*x.head(), _p(x.Av, _f64p), *x.wv(), ALG[alg], float(tie_tol), int(j),
+    L.diaf_oracle_column(*x.head(), _p(x.Av, _f64p), *x.wv(), ALG[alg], float(tie_tol), float(stab_tol),
+                         float(stab_r), int(j),
                          _p(w.view(np.float64), _f64p), _p(Ir, _i32p), _p(v.view(np.float64), _f64p),
                          ctypes.byref(res), ctypes.byref(fl), ctypes.byref(mg), _p(sig, _f64p), ctypes.byref(m),
                          _p(rows, _i32p), _p(h, _f64p))

@@ -308,6 +308,8 @@ diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_
   ca.rule = V->rule; ca.Vfcp = pa.Vfcp; ca.Vfri = pa.Vfri;
   ca.Vcp = F->Vcp;
   ca.tie_tol = V->tie_tol > 0 ? V->tie_tol : 1e-9;
+  ca.stab_tol = (alg == DIAF_ALG_Q && V->stab_tol > 0) ? V->stab_tol : 0.0;
+  ca.stab_r = V->stab_r > 0 ? V->stab_r : 2.0;
   ca.Wv = F->Wv; ca.Vri = F->Vri; ca.Vv = F->Vv;
   ca.res = F->res; ca.flags = F->flags; ca.status = status;
 #ifdef DIAF_PHASE_TIMING

@@ -33,6 +33,8 @@ struct ColArgs {
   const int32_t* Vfri;
   const int32_t* Vcp;
   double tie_tol;
+  double stab_tol;            // stabilised DIAF-Q: trigger |v_jj| < stab_tol (0: off)
+  double stab_r;              // stabilised DIAF-Q: imposed v_jj before scaling to unit norm
   const int32_t* list;        // bucket's columns
   const int32_t* list_count;  // device count of the list
   int32_t* work_counter;      // zeroed before launch
@@ -289,6 +291,75 @@ struct WarpLayout {
   static constexpr size_t bytes() { return (raw() + 15) / 16 * 16; }  // keeps every warp's slice 16-byte aligned
 };
 
+// Stabilised DIAF-Q (Sec. 3.2).  On entry Tw holds Q_I V1 (the rows I_j of Q
+// after the first Jacobi, l x k) and vv the unit v_j of eq. nocond with
+// |v_jj| < stab_tol.  The j-th component is imposed as r and the rest is the
+// top singular vector z of M_hat = Q_I'^* (I' = I_j without j) with the phase
+// e^{i theta}, theta = arg of the first component of U_hat^* p, p = Q(j,:)^*.
+// Rotating Q_I by V1 changes neither z nor U_hat^* p: B = Q_I' V1 = Z S Y^*
+// gives M_hat = (V1 Y) S Z^*, so z = B Y(:,1)/s_1 and U_hat(:,1)^* p =
+// conj(sum_c Y(c,1) q_c) with q = row j of Q_I V1.  v_j = (r e_j + e^{i theta}
+// z) / sqrt(r^2 + 1); the lane's entry of Q_I^* v_j = R^-* T_I^* v_j is
+// returned, ready for the back substitution of eq. condwj.
+template <class S, int LDT, int KP, int KMAX>
+__device__ S stabilise_q_warp(const ColArgs& a, const S* Ts, S* Tw, const S* Rs, const S* rinv, S* Vj, S* wv,
+                              S* vv, double* sig, const ColumnIdx& ix, int k, int l, int jpos, uint32_t& flags,
+                              int lane) {
+  using R = RealOf<S>;
+  for (int q = lane; q < k; q += DIAF_WARP) wv[q] = Tw[jpos + q * LDT];  // q = row j of Q_I V1
+  __syncwarp();
+  for (int c = 0; c < k; ++c) {  // drop row jpos: rows below move up by one
+    S tmp[(LDT + DIAF_WARP - 1) / DIAF_WARP];
+    int nn = 0;
+    for (int t = jpos + lane; t < l - 1; t += DIAF_WARP) tmp[nn++] = Tw[t + 1 + c * LDT];
+    __syncwarp();
+    nn = 0;
+    for (int t = jpos + lane; t < l - 1; t += DIAF_WARP) Tw[t + c * LDT] = tmp[nn++];
+    __syncwarp();
+  }
+  const int lh = l - 1;
+  if (warp_jacobi<S, LDT, KP, KMAX>(Tw, lh, k, Vj, lane) < 0) flags |= DIAF_FLAG_JACOBI_NOCONV;
+  warp_col_norms<S, LDT>(Tw, lh, k, sig, lane);
+  int i1 = 0;
+  double s1 = sig[0];
+  for (int c = 1; c < k; ++c) if (sig[c] > s1) { s1 = sig[c]; i1 = c; }
+  double s2 = 0.0;
+  for (int c = 0; c < k; ++c) if (c != i1) s2 = dmax(s2, sig[c]);
+  flags &= ~DIAF_FLAG_DEGENERATE;  // now describes the stabilised problem
+  if (s1 == 0.0 || (lh > 1 && k > 1 && (s1 - s2) <= 1e-6 * s1)) flags |= DIAF_FLAG_DEGENERATE;
+  S pt = sc_zero<S>();
+  R pn = R(0);
+  for (int q = lane; q < k; q += DIAF_WARP) {
+    pt += Vj[q + i1 * KP] * wv[q];
+    pn += sc_abs2(wv[q]);
+  }
+  pt = sc_conj(warp_sum(pt));
+  pn = warp_sum(pn);
+  const R apt = sc_abs(pt);
+  if (!(apt > R(1e-10) * sqrt(pn))) flags |= DIAF_FLAG_DEGENERATE;  // any theta will do; theta = 0
+  const S eth = apt > R(0) ? (R(1) / apt) * pt : sc_real_s<S>(R(1));
+  const R r = a.stab_r > 0.0 ? R(a.stab_r) : R(2);
+  const R scl = R(1) / sqrt(r * r + R(1));
+  const R zs = s1 > 0.0 ? scl / R(s1) : R(0);
+  for (int u = lane; u < lh; u += DIAF_WARP) vv[u < jpos ? u : u + 1] = (zs * eth) * Tw[u + i1 * LDT];
+  if (lane == 0) vv[jpos] = sc_real_s<S>(r * scl);
+  __syncwarp();
+  // Q_I^* v = R^-* T_I^* v
+  S y = sc_zero<S>();
+  if (lane < k)
+    for (int t = 0; t < l; ++t) {
+      const int rr = ix.Iloc[t];
+      if (rr >= 0) y += sc_conj(Ts[rr + lane * LDT]) * vv[t];
+    }
+  for (int c = 0; c < k; ++c) {  // forward substitution R^* x = y
+    S uc = shfl_idx(y * sc_conj(rinv[c]), c);
+    if (lane > c && lane < k) y -= sc_conj(Rs[c + lane * KP]) * uc;
+    if (lane == c) y = uc;
+  }
+  flags |= DIAF_FLAG_STABILISED;
+  return y;
+}
+
 template <class S, int KMAX, int MMAX, int ALG>
 __device__ void solve_column_warp(const ColArgs& a, int j, unsigned char* smem, int lane) {
   using R = RealOf<S>;
@@ -402,12 +473,15 @@ __device__ void solve_column_warp(const ColArgs& a, int j, unsigned char* smem, 
     } else if (lane == 0) {
       vv[jpos >= 0 ? jpos : 0] = sc_real_s<S>(R(1));
     }
+    __syncwarp();
     // w = sigma R^-1 u  (R w = Q^* v, eq. condwj); rinv holds R's reciprocal diagonal
     bool rd = false;
     for (int c = lane; c < k; c += DIAF_WARP) rd |= !(sc_abs(Rs[c + c * KP]) > piv);
     rd = __any_sync(DIAF_FULL, rd);
     if (rd) flags |= DIAF_FLAG_RANK_DEFICIENT;
     S x = lane < k ? R(smax) * Vj[lane + imax * KP] : sc_zero<S>();
+    if (a.stab_tol > 0.0 && jpos >= 0 && l > 1 && (double)sc_abs(vv[jpos]) < a.stab_tol)
+      x = stabilise_q_warp<S, LDT, KP, KMAX>(a, Ts, Tw, Rs, rinv, Vj, wv, vv, sig, ix, k, l, jpos, flags, lane);
     for (int c = k - 1; c >= 0; --c) {
       S yc = shfl_idx(x * rinv[c], c);
       if (lane < c) x -= Rs[lane + c * KP] * yc;

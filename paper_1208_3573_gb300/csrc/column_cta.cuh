@@ -418,9 +418,70 @@ __device__ void solve_column_cta(const ColArgs& a, const CtaScratch& sc, int j, 
     bool rd = false;
     for (int c = 0; c < k; ++c) rd |= !(sc_abs(Rs[c + c * KP]) > piv);
     if (rd) flags |= DIAF_FLAG_RANK_DEFICIENT;
-    if (tid == 0) {  // back substitution R w = sigma u
+    __syncthreads();
+    const bool stab = a.stab_tol > 0.0 && jpos >= 0 && l > 1 && (double)sc_abs(vv[jpos]) < a.stab_tol;
+    if (stab) {
+      // Stabilised DIAF-Q (Sec. 3.2), as in the warp kernel: G = Q_I V1; drop
+      // row j, Jacobi of the rest gives z = B Y(:,1)/s_1 and the phase from
+      // conj(sum_c Y(c,1) q_c), q = row j of Q_I V1; v = (r e_j + e^{i theta} z)
+      // / sqrt(r^2 + 1); the right-hand side of eq. condwj is R^-* T_I^* v.
+      for (int q = tid; q < k; q += kCtaThreads) wv[q] = G[jpos + q * KP];
+      __syncthreads();
+      for (int c = tid; c < k; c += kCtaThreads)
+        for (int t = jpos; t < l - 1; ++t) G[t + c * KP] = G[t + 1 + c * KP];
+      __syncthreads();
+      const int lh = l - 1;
+      if (cta_jacobi<S, KP, KP>(G, lh, k, Vj, redR) < 0) flags |= DIAF_FLAG_JACOBI_NOCONV;
+      for (int c = tid; c < k; c += kCtaThreads) {
+        R s2 = R(0);
+        for (int i = 0; i < lh; ++i) s2 += sc_abs2(G[i + c * KP]);
+        sig[c] = sqrt((double)s2);
+      }
+      __syncthreads();
+      int i1 = 0;
+      double s1 = sig[0];
+      for (int c = 1; c < k; ++c) if (sig[c] > s1) { s1 = sig[c]; i1 = c; }
+      double sn = 0.0;
+      for (int c = 0; c < k; ++c) if (c != i1) sn = dmax(sn, sig[c]);
+      flags &= ~DIAF_FLAG_DEGENERATE;
+      if (s1 == 0.0 || (lh > 1 && k > 1 && (s1 - sn) <= 1e-6 * s1)) flags |= DIAF_FLAG_DEGENERATE;
+      S pt = sc_zero<S>();
+      R pn = R(0);
+      for (int q = 0; q < k; ++q) {  // every thread: a uniform result without another reduction
+        pt += Vj[q + i1 * KP] * wv[q];
+        pn += sc_abs2(wv[q]);
+      }
+      pt = sc_conj(pt);
+      const R apt = sc_abs(pt);
+      if (!(apt > R(1e-10) * sqrt(pn))) flags |= DIAF_FLAG_DEGENERATE;
+      const S eth = apt > R(0) ? (R(1) / apt) * pt : sc_real_s<S>(R(1));
+      const R r = a.stab_r > 0.0 ? R(a.stab_r) : R(2);
+      const R scl = R(1) / sqrt(r * r + R(1));
+      const R zs = s1 > 0.0 ? scl / R(s1) : R(0);
+      for (int u = tid; u < lh; u += kCtaThreads) vv[u < jpos ? u : u + 1] = (zs * eth) * G[u + i1 * KP];
+      if (tid == 0) vv[jpos] = sc_real_s<S>(r * scl);
+      __syncthreads();
+      for (int c = tid; c < k; c += kCtaThreads) {  // T_I^* v
+        S y = sc_zero<S>();
+        for (int t = 0; t < l; ++t)
+          if (Iloc[t] >= 0) y += sc_conj(Ts[Iloc[t] + (size_t)c * ld]) * vv[t];
+        wv[c] = y;
+      }
+      __syncthreads();
+      flags |= DIAF_FLAG_STABILISED;
+    }
+    if (tid == 0) {  // R w = Q_I^* v: sigma u, or R^-* T_I^* v when stabilised
+      if (stab) {
+        for (int c = 0; c < k; ++c) {
+          S acc = wv[c];
+          for (int p = 0; p < c; ++p) acc -= sc_conj(Rs[p + c * KP]) * wv[p];
+          wv[c] = acc * sc_conj(rinv[c]);
+        }
+      } else {
+        for (int c = 0; c < k; ++c) wv[c] = R(smax) * Vj[c + imax * KP];
+      }
       for (int c = k - 1; c >= 0; --c) {
-        S acc = R(smax) * Vj[c + imax * KP];
+        S acc = wv[c];
         for (int t = c + 1; t < k; ++t) acc -= Rs[c + t * KP] * wv[t];
         wv[c] = acc * rinv[c];
       }

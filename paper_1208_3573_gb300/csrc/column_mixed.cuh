@@ -343,6 +343,12 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
       for (int t = 0; t < l; ++t) vv[t] = yinv * y[t];
     }
     __syncwarp();
+    // stabilised DIAF-Q (Sec. 3.2): the FP64 kernel takes every column at or
+    // near the trigger, so the decision is the FP64 one
+    if (a.stab_tol > 0.0 && jpos >= 0 && l > 1 && (double)sc_abs(vv[jpos]) < a.stab_tol * (1.0 + 1e-6)) {
+      hand_back(7);
+      return;
+    }
     // w = X v (eq. condwj for the refined v)
     if (lane < k) {
       SD x = sc_zero<SD>();

@@ -22,7 +22,7 @@ ALG = {"Q": 1, "S": 2}
 PREC = {"fp64": 0, "mixed32": 1}
 RULE_FIXED, RULE_UPPER, RULE_LOWER, RULE_ALL = 0, 1, 2, 3
 FLAG_RANK_DEFICIENT, FLAG_DEGENERATE, FLAG_VJJ_ZERO, FLAG_JACOBI_NOCONV = 1, 2, 4, 8
-FLAG_NONFINITE, FLAG_EMPTY, FLAG_FP64_FALLBACK = 16, 32, 64
+FLAG_NONFINITE, FLAG_EMPTY, FLAG_FP64_FALLBACK, FLAG_STABILISED = 16, 32, 64, 128
 
 
 class DiafError(RuntimeError):
@@ -43,7 +43,7 @@ class Pattern_t(ctypes.Structure):
 
 class VSpec_t(ctypes.Structure):
     _fields_ = [("rule", ctypes.c_int32), ("fixed", ctypes.POINTER(Pattern_t)), ("budget", ctypes.c_void_p),
-                ("tie_tol", ctypes.c_double)]
+                ("tie_tol", ctypes.c_double), ("stab_tol", ctypes.c_double), ("stab_r", ctypes.c_double)]
 
 
 class Tuning_t(ctypes.Structure):
@@ -287,20 +287,22 @@ def launch_count() -> int:
     return int(lib().diaf_launch_count())
 
 
-def _args(A, PW, vrule, budget, Vfixed, tie_tol):
+def _args(A, PW, vrule, budget, Vfixed, tie_tol, stab=(0.0, 2.0)):
     a = A.csc_t()
     pw = PW.pattern_t()
     fixed = Vfixed.pattern_t() if Vfixed is not None else None
-    vs = VSpec_t(vrule, ctypes.pointer(fixed) if fixed is not None else None, _ptr(budget), tie_tol)
+    vs = VSpec_t(vrule, ctypes.pointer(fixed) if fixed is not None else None, _ptr(budget), tie_tol,
+                 float(stab[0]), float(stab[1]))
     return a, pw, vs, fixed
 
 
 def factor(A: DeviceCSC, PW: DeviceCSC, vrule: int = RULE_UPPER, budget: torch.Tensor | None = None,
            Vfixed: DeviceCSC | None = None, alg: str = "S", prec: str = "fp64", tie_tol: float = 1e-9,
-           stream=None, tuning: dict | None = None) -> Factors:
-    """Columnwise W, V with A W ~ V (diaf_factor / diaf_factor_tuned)."""
+           stream=None, tuning: dict | None = None, stab_tol: float = 0.0, stab_r: float = 2.0) -> Factors:
+    """Columnwise W, V with A W ~ V (diaf_factor / diaf_factor_tuned); stab_tol > 0
+    turns on the stabilised DIAF-Q."""
     L = lib()
-    a, pw, vs, _keep = _args(A, PW, vrule, budget, Vfixed, tie_tol)
+    a, pw, vs, _keep = _args(A, PW, vrule, budget, Vfixed, tie_tol, (stab_tol, stab_r))
     h = ctypes.c_void_p()
     s = _stream(stream)
     t = Tuning_t.from_dict(tuning)
@@ -311,10 +313,10 @@ def factor(A: DeviceCSC, PW: DeviceCSC, vrule: int = RULE_UPPER, budget: torch.T
 
 def autotune(A: DeviceCSC, PW: DeviceCSC, vrule: int = RULE_UPPER, budget: torch.Tensor | None = None,
              Vfixed: DeviceCSC | None = None, alg: str = "S", prec: str = "fp64", tie_tol: float = 1e-9,
-             stream=None) -> tuple[dict, float]:
+             stream=None, stab_tol: float = 0.0, stab_r: float = 2.0) -> tuple[dict, float]:
     """Fastest launch tuning of the numeric pass (diaf_autotune) and its time in ms."""
     L = lib()
-    a, pw, vs, _keep = _args(A, PW, vrule, budget, Vfixed, tie_tol)
+    a, pw, vs, _keep = _args(A, PW, vrule, budget, Vfixed, tie_tol, (stab_tol, stab_r))
     best = Tuning_t()
     ms = ctypes.c_float()
     _check(L.diaf_autotune(ctypes.byref(a), ctypes.byref(pw), ctypes.byref(vs), ALG[alg], PREC[prec],
@@ -328,10 +330,10 @@ class Plan:
 
     def __init__(self, A: DeviceCSC, PW: DeviceCSC, vrule: int = RULE_UPPER, budget: torch.Tensor | None = None,
                  Vfixed: DeviceCSC | None = None, alg: str = "S", prec: str = "fp64", tie_tol: float = 1e-9,
-                 stream=None, tuning: dict | None = None):
+                 stream=None, tuning: dict | None = None, stab_tol: float = 0.0, stab_r: float = 2.0):
         L = lib()
         self._inputs = (A, PW, budget, Vfixed)  # the plan reads these buffers by pointer
-        a, pw, vs, _keep = _args(A, PW, vrule, budget, Vfixed, tie_tol)
+        a, pw, vs, _keep = _args(A, PW, vrule, budget, Vfixed, tie_tol, (stab_tol, stab_r))
         t = Tuning_t.from_dict(tuning)
         h = ctypes.c_void_p()
         s = _stream(stream)

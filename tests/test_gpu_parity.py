@@ -29,12 +29,13 @@ def D():
     return diaf
 
 
-def run_gpu(D, A, PW, vrule=O.RULE_UPPER, budget=None, Vfixed=None, alg="S", prec="fp64", tie_tol=O.TIE_TOL):
+def run_gpu(D, A, PW, vrule=O.RULE_UPPER, budget=None, Vfixed=None, alg="S", prec="fp64", tie_tol=O.TIE_TOL,
+            stab_tol=0.0):
     dA = D.DeviceCSC.from_host(A)
     dP = D.DeviceCSC.from_host(PW)
     dB = None if budget is None else torch.from_numpy(np.ascontiguousarray(budget, np.int32)).cuda()
     dV = None if Vfixed is None else D.DeviceCSC.from_host(Vfixed)
-    F = D.factor(dA, dP, vrule, dB, dV, alg=alg, prec=prec, tie_tol=tie_tol)
+    F = D.factor(dA, dP, vrule, dB, dV, alg=alg, prec=prec, tie_tol=tie_tol, stab_tol=stab_tol)
     torch.cuda.synchronize()
     return F
 

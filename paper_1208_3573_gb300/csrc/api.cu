@@ -585,44 +585,55 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   DIAF_CU(F->alloc(&tri, 1));
   DIAF_CU(cudaMemsetAsync(tri, 0, sizeof(uint32_t), s));
   DIAF_CU(csr_triangle_check(F->Vr, cplx, tri, s));
+  // one synchronisation: the triangle check and V's structure for the level schedule
   uint32_t h = 0;
+  std::vector<int32_t> rp(n + 1), ci((size_t)F->nnz_v);
   DIAF_CU(cudaMemcpyAsync(&h, tri, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  DIAF_CU(cudaMemcpyAsync(rp.data(), F->Vr.rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+  if (F->nnz_v > 0)
+    DIAF_CU(cudaMemcpyAsync(ci.data(), F->Vr.colidx, sizeof(int32_t) * F->nnz_v, cudaMemcpyDeviceToHost, s));
   DIAF_CU(cudaStreamSynchronize(s));
   if ((h & 1u) && (h & 2u)) return fail(DIAF_EINVAL, "V is not triangular");
   if (h & 4u) return fail(DIAF_EINVAL, "V has a zero or missing diagonal entry");
   F->v_upper = !(h & 1u);
-  // level schedule: depth of every row in the dependency graph of V (host, O(nnz))
-  {
-    std::vector<int32_t> rp(n + 1), ci((size_t)F->nnz_v), lev(n, 0);
-    DIAF_CU(cudaMemcpyAsync(rp.data(), F->Vr.rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, s));
-    if (F->nnz_v > 0)
-      DIAF_CU(cudaMemcpyAsync(ci.data(), F->Vr.colidx, sizeof(int32_t) * F->nnz_v, cudaMemcpyDeviceToHost, s));
-    DIAF_CU(cudaStreamSynchronize(s));
-    int nlev = 0;
-    for (int step = 0; step < n; ++step) {
-      const int i = F->v_upper ? n - 1 - step : step;
-      int L = 0;
-      for (int p = rp[i]; p < rp[i + 1]; ++p) {
-        const int j = ci[p];
-        if (j != i && lev[j] + 1 > L) L = lev[j] + 1;
-      }
-      lev[i] = L;
-      if (L + 1 > nlev) nlev = L + 1;
+  // level of every row: its depth in the dependency graph of V (host, O(nnz))
+  std::vector<int32_t> lev(n, 0);
+  int nlev = 0;
+  for (int step = 0; step < n; ++step) {
+    const int i = F->v_upper ? n - 1 - step : step;
+    int L = 0;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      const int j = ci[p];
+      if (j != i && lev[j] + 1 > L) L = lev[j] + 1;
     }
-    std::vector<int32_t> ptr(nlev + 1, 0), order(n > 0 ? n : 1);
-    for (int i = 0; i < n; ++i) ptr[lev[i] + 1] += 1;
-    for (int l = 0; l < nlev; ++l) ptr[l + 1] += ptr[l];
-    std::vector<int32_t> cur(ptr.begin(), ptr.end() - 1);
-    for (int i = 0; i < n; ++i) order[cur[lev[i]]++] = i;
-    F->nlev = nlev;
-    DIAF_CU(F->alloc(&F->lvlptr, nlev + 1));
-    DIAF_CU(F->alloc(&F->order, n));
-    DIAF_CU(cudaMemcpyAsync(F->lvlptr, ptr.data(), sizeof(int32_t) * (nlev + 1), cudaMemcpyHostToDevice, s));
-    if (n > 0) DIAF_CU(cudaMemcpyAsync(F->order, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
-    DIAF_CU(F->alloc((char**)&F->dinv, esz * n));
-    DIAF_CU(csr_diag_inverse(F->Vr, cplx, F->dinv, s));
-    DIAF_CU(cudaStreamSynchronize(s));  // the host vectors above go out of scope
+    lev[i] = L;
+    if (L + 1 > nlev) nlev = L + 1;
   }
+  std::vector<int32_t> ptr(nlev + 1, 0), order(n > 0 ? n : 1);
+  for (int i = 0; i < n; ++i) ptr[lev[i] + 1] += 1;
+  for (int l = 0; l < nlev; ++l) ptr[l + 1] += ptr[l];
+  std::vector<int32_t> cur(ptr.begin(), ptr.end() - 1);
+  for (int i = 0; i < n; ++i) order[cur[lev[i]]++] = i;
+  LevelCsr& Vl = F->Vl;
+  Vl.n = n;
+  Vl.nlev = nlev;
+  Vl.nnz = F->nnz_v - n;
+  int32_t *dorder, *pos;
+  DIAF_CU(F->alloc(&Vl.lvlptr, nlev + 1));
+  DIAF_CU(F->alloc(&dorder, n));
+  DIAF_CU(F->alloc(&pos, n));
+  DIAF_CU(F->alloc(&Vl.rowptr, n + 1));
+  DIAF_CU(F->alloc(&Vl.colidx, Vl.nnz));
+  DIAF_CU(F->alloc((char**)&Vl.vals, esz * Vl.nnz));
+  DIAF_CU(F->alloc((char**)&Vl.dinv, esz * n));
+  DIAF_CU(F->alloc(&Vl.xrow, n));
+  // pageable host sources: each copy has taken its data when the call returns
+  DIAF_CU(cudaMemcpyAsync(Vl.lvlptr, ptr.data(), sizeof(int32_t) * (nlev + 1), cudaMemcpyHostToDevice, s));
+  if (n > 0) DIAF_CU(cudaMemcpyAsync(dorder, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+  DIAF_CU(csr_level_permute(F->Vr, cplx, dorder, pos, work, Vl, s));
+  F->Wl = F->Wr;
+  DIAF_CU(F->alloc(&F->Wl.colidx, F->nnz_w));
+  DIAF_CU(remap_columns(F->nnz_w, pos, F->Wr.colidx, F->Wl.colidx, s));
   DIAF_CU(F->alloc((char**)&F->tbuf, esz * n));
   F->apply_ready = true;
   return DIAF_OK;
@@ -638,8 +649,8 @@ diaf_status diaf_apply(diaf_factors* F, const void* x, void* y, void* stream) {
   }
   if (F->n == 0) return DIAF_OK;
   const bool cplx = F->dtype == DIAF_C128;
-  DIAF_CU(csr_trsv_levels(F->Vr, cplx, F->nlev, F->lvlptr, F->order, F->dinv, x, F->tbuf, s));
-  DIAF_CU(csr_spmv(F->Wr, cplx, F->tbuf, y, s));
+  DIAF_CU(trsv_levels_perm(F->Vl, cplx, x, F->tbuf, s));
+  DIAF_CU(csr_spmv(F->Wl, cplx, F->tbuf, y, s));
   return DIAF_OK;
 }
 

@@ -32,11 +32,9 @@ struct diaf_factors {
   bool v_upper = true;
   Csr Vr, Wr;
   void* tbuf = nullptr;
-  // level schedule of the V solve
-  int nlev = 0;
-  int32_t* lvlptr = nullptr;
-  int32_t* order = nullptr;
-  void* dinv = nullptr;
+  // level-scheduled V solve: V in level order, W's columns renumbered to it
+  LevelCsr Vl;
+  Csr Wl;
 
   template <class T>
   cudaError_t alloc(T** p, size_t count) {

@@ -150,70 +150,182 @@ __global__ void trsv_syncfree_kernel(int n, const int32_t* __restrict__ rowptr, 
 
 constexpr int kLevelThreads = 1024;
 constexpr int kLevelPtrSmem = 8192;  // level pointers kept in shared memory up to this many levels
+constexpr int kPrefetch = 4;         // off-diagonal entries of a row held in registers ahead of its level
+
+__global__ void scatter_pos_kernel(int n, const int32_t* __restrict__ order, const int32_t* __restrict__ rowptr,
+                                   int32_t* __restrict__ pos, int32_t* __restrict__ len) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int i = order[p];
+  pos[i] = p;
+  len[p] = rowptr[i + 1] - rowptr[i] - 1;  // off-diagonal entries (the diagonal is present: checked)
+}
 
 template <class S>
-__global__ void __launch_bounds__(kLevelThreads)
-    trsv_levels_kernel(int nlev, const int32_t* __restrict__ lvlptr, const int32_t* __restrict__ order,
-                       const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                       const S* __restrict__ vals, const S* __restrict__ dinv, const S* __restrict__ x, S* t) {
+__global__ void fill_levels_kernel(int n, const int32_t* __restrict__ order, const int32_t* __restrict__ pos,
+                                   const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                   const S* __restrict__ vals, const int32_t* __restrict__ prow,
+                                   int32_t* __restrict__ pcol, S* __restrict__ pval, S* __restrict__ pdinv,
+                                   int32_t* __restrict__ xrow) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int i = order[p];
+  int k = prow[p];
+  S d = sc_zero<S>();
+  for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+    const int c = colidx[e];
+    if (c == i) {
+      d = vals[e];
+    } else {
+      pcol[k] = pos[c];
+      pval[k] = vals[e];
+      ++k;
+    }
+  }
+  pdinv[p] = (1.0 / sc_abs2(d)) * sc_conj(d);
+  xrow[p] = i;
+}
+
+__global__ void remap_cols_kernel(int64_t nnz, const int32_t* __restrict__ pos, const int32_t* __restrict__ cin,
+                                  int32_t* __restrict__ cout) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+    cout[e] = pos[cin[e]];
+}
+
+// Level-scheduled solve on the level-ordered matrix: the rows of level l are
+// the contiguous positions lvlptr[l]..lvlptr[l+1], their off-diagonal
+// entries point at positions of earlier levels, t is kept in level order.
+// Nothing a row needs except t depends on the solve, so every thread loads
+// its next row (bounds, x, 1/diag and the first kPrefetch entries) before the
+// barrier that ends the current level; after the barrier only the loads of t
+// remain on the critical path.  Those come from a ring of the last kWin
+// positions of t in shared memory: while level [b, e) is written, slots of
+// positions >= e - kWin are not overwritten, so reads of such positions use
+// the ring and older ones use t in global memory (written too).
+template <class S>
+constexpr int level_window() { return 131072 / (int)sizeof(S); }  // 128 KB ring
+
+template <class S>
+__global__ void __launch_bounds__(kLevelThreads, 1)
+    trsv_levels_perm_kernel(int nlev, const int32_t* __restrict__ lvlptr, const int32_t* __restrict__ rowptr,
+                            const int32_t* __restrict__ colidx, const S* __restrict__ vals,
+                            const S* __restrict__ dinv, const int32_t* __restrict__ xrow, const S* __restrict__ x,
+                            S* t) {
+  constexpr int kWin = level_window<S>();
+  static_assert((kWin & (kWin - 1)) == 0, "ring size must be a power of two");
+  extern __shared__ __align__(16) unsigned char level_ring[];
+  S* tw = reinterpret_cast<S*>(level_ring);
   __shared__ int32_t sptr[kLevelPtrSmem + 1];
   const bool in_smem = nlev <= kLevelPtrSmem;
   if (in_smem)
     for (int i = threadIdx.x; i <= nlev; i += blockDim.x) sptr[i] = lvlptr[i];
   __syncthreads();
+#define DIAF_LP(l) (in_smem ? sptr[(l)] : lvlptr[(l)])
+  // registers for the first row this thread takes in the coming level
+  int rb = 0, re = 0;
+  S xb = sc_zero<S>(), db = sc_zero<S>();
+  int pc[kPrefetch];
+  S pv[kPrefetch];
+#define DIAF_FETCH(pp)                                 \
+  do {                                                 \
+    const int p_ = (pp);                               \
+    rb = rowptr[p_];                                   \
+    re = rowptr[p_ + 1];                               \
+    xb = x[xrow[p_]];                                  \
+    db = dinv[p_];                                     \
+    _Pragma("unroll") for (int q = 0; q < kPrefetch; ++q) { \
+      const bool in = rb + q < re;                     \
+      pc[q] = in ? colidx[rb + q] : 0;                 \
+      pv[q] = in ? vals[rb + q] : sc_zero<S>();        \
+    }                                                  \
+  } while (0)
+  if (nlev > 0 && DIAF_LP(0) + (int)threadIdx.x < DIAF_LP(1)) DIAF_FETCH(DIAF_LP(0) + (int)threadIdx.x);
   for (int lv = 0; lv < nlev; ++lv) {
-    const int b = in_smem ? sptr[lv] : lvlptr[lv];
-    const int e = in_smem ? sptr[lv + 1] : lvlptr[lv + 1];
-    for (int idx = b + threadIdx.x; idx < e; idx += blockDim.x) {
-      const int i = order[idx];
-      S acc = x[i];
-      for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
-        const int j = colidx[p];
-        if (j != i) acc -= vals[p] * t[j];
-      }
-      t[i] = acc * dinv[i];
+    const int b = DIAF_LP(lv), e = DIAF_LP(lv + 1);
+    const int lo = e - kWin;  // ring holds positions >= lo unchanged during this level
+#define DIAF_TGET(c) ((c) >= lo ? tw[(c) & (kWin - 1)] : t[(c)])
+    int p = b + threadIdx.x;
+    if (p < e) {
+      S acc = xb;
+#pragma unroll
+      for (int q = 0; q < kPrefetch; ++q)
+        if (rb + q < re) acc -= pv[q] * DIAF_TGET(pc[q]);
+      for (int k = rb + kPrefetch; k < re; ++k) acc -= vals[k] * DIAF_TGET(colidx[k]);
+      const S tv = acc * db;
+      t[p] = tv;
+      tw[p & (kWin - 1)] = tv;
+    }
+    for (p += blockDim.x; p < e; p += blockDim.x) {  // levels wider than the block
+      S acc = x[xrow[p]];
+      for (int k = rowptr[p]; k < rowptr[p + 1]; ++k) acc -= vals[k] * DIAF_TGET(colidx[k]);
+      const S tv = acc * dinv[p];
+      t[p] = tv;
+      tw[p & (kWin - 1)] = tv;
+    }
+    if (lv + 1 < nlev) {
+      const int nb = e, ne = DIAF_LP(lv + 2);
+      if (nb + (int)threadIdx.x < ne) DIAF_FETCH(nb + (int)threadIdx.x);
     }
     __syncthreads();
+#undef DIAF_TGET
   }
-}
-
-template <class S>
-__global__ void diag_inverse_kernel(int n, const int32_t* rowptr, const int32_t* colidx, const S* vals, S* dinv) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  S d = sc_zero<S>();
-  for (int p = rowptr[i]; p < rowptr[i + 1]; ++p)
-    if (colidx[p] == i) d = vals[p];
-  dinv[i] = (1.0 / sc_abs2(d)) * sc_conj(d);
+#undef DIAF_FETCH
+#undef DIAF_LP
 }
 
 }  // namespace
 
-cudaError_t csr_trsv_levels(const Csr& V, bool cplx, int nlev, const int32_t* lvlptr, const int32_t* order,
-                            const void* dinv, const void* x, void* t, cudaStream_t s) {
-  if (V.n <= 0) return cudaSuccess;
+cudaError_t csr_level_permute(const Csr& V, bool cplx, const int32_t* order, int32_t* pos, int32_t* work,
+                              LevelCsr& L, cudaStream_t s) {
+  const int n = V.n;
+  if (n <= 0) return cudaSuccess;
+  int32_t* len = work;
+  int32_t* bs = work + n;
+  scatter_pos_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, order, V.rowptr, pos, len);
+  DIAF_COUNT_LAUNCH();
+  exclusive_scan_i32(len, L.rowptr, n, bs, s);
   if (cplx)
-    trsv_levels_kernel<Cx<double>><<<1, kLevelThreads, 0, s>>>(nlev, lvlptr, order, V.rowptr, V.colidx,
-                                                              (const Cx<double>*)V.vals, (const Cx<double>*)dinv,
-                                                              (const Cx<double>*)x, (Cx<double>*)t);
+    fill_levels_kernel<Cx<double>><<<ceil_div(n, 256), 256, 0, s>>>(
+        n, order, pos, V.rowptr, V.colidx, (const Cx<double>*)V.vals, L.rowptr, L.colidx, (Cx<double>*)L.vals,
+        (Cx<double>*)L.dinv, L.xrow);
   else
-    trsv_levels_kernel<double><<<1, kLevelThreads, 0, s>>>(nlev, lvlptr, order, V.rowptr, V.colidx,
-                                                          (const double*)V.vals, (const double*)dinv,
-                                                          (const double*)x, (double*)t);
+    fill_levels_kernel<double><<<ceil_div(n, 256), 256, 0, s>>>(n, order, pos, V.rowptr, V.colidx,
+                                                              (const double*)V.vals, L.rowptr, L.colidx,
+                                                              (double*)L.vals, (double*)L.dinv, L.xrow);
   DIAF_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
-cudaError_t csr_diag_inverse(const Csr& V, bool cplx, void* dinv, cudaStream_t s) {
-  if (V.n <= 0) return cudaSuccess;
-  if (cplx)
-    diag_inverse_kernel<Cx<double>><<<ceil_div(V.n, 256), 256, 0, s>>>(V.n, V.rowptr, V.colidx,
-                                                                       (const Cx<double>*)V.vals, (Cx<double>*)dinv);
-  else
-    diag_inverse_kernel<double><<<ceil_div(V.n, 256), 256, 0, s>>>(V.n, V.rowptr, V.colidx, (const double*)V.vals,
-                                                                   (double*)dinv);
+cudaError_t remap_columns(int64_t nnz, const int32_t* pos, const int32_t* cin, int32_t* cout, cudaStream_t s) {
+  if (nnz <= 0) return cudaSuccess;
+  int blocks = (int)((nnz + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  remap_cols_kernel<<<blocks, 256, 0, s>>>(nnz, pos, cin, cout);
   DIAF_COUNT_LAUNCH();
   return cudaGetLastError();
+}
+
+template <class S>
+static cudaError_t trsv_levels_perm_t(const LevelCsr& L, const void* x, void* t, cudaStream_t s) {
+  constexpr size_t ring = sizeof(S) * level_window<S>();
+  static int configured_device = -1;  // the attribute is per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured_device != dev) {
+    cudaError_t e = cudaFuncSetAttribute(trsv_levels_perm_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ring);
+    if (e != cudaSuccess) return e;
+    configured_device = dev;
+  }
+  trsv_levels_perm_kernel<S><<<1, kLevelThreads, ring, s>>>(L.nlev, L.lvlptr, L.rowptr, L.colidx, (const S*)L.vals,
+                                                            (const S*)L.dinv, L.xrow, (const S*)x, (S*)t);
+  DIAF_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+cudaError_t trsv_levels_perm(const LevelCsr& L, bool cplx, const void* x, void* t, cudaStream_t s) {
+  if (L.n <= 0) return cudaSuccess;
+  return cplx ? trsv_levels_perm_t<Cx<double>>(L, x, t, s) : trsv_levels_perm_t<double>(L, x, t, s);
 }
 
 cudaError_t csc_to_csr(int n, int64_t nnz, const int32_t* cp, const int32_t* ri, const void* v, bool cplx,

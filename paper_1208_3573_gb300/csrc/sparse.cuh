@@ -35,12 +35,32 @@ cudaError_t csr_triangle_check(const Csr& V, bool cplx, uint32_t* out, cudaStrea
 cudaError_t csr_trsv_syncfree(const Csr& V, bool cplx, bool upper, const void* x, void* t, uint32_t* ready,
                               int32_t* counter, uint32_t gen, uint32_t* status, cudaStream_t s);
 
-// t = V^-1 x by level scheduling: rows grouped by their depth in the
-// dependency graph of the triangular V (order = rows level by level,
-// lvlptr[l]..lvlptr[l+1] the rows of level l, nlev levels), solved by one
-// 1024-thread block with a barrier between levels; dinv = 1 / diag(V).
-cudaError_t csr_trsv_levels(const Csr& V, bool cplx, int nlev, const int32_t* lvlptr, const int32_t* order,
-                            const void* dinv, const void* x, void* t, cudaStream_t s);
+// V in level order for the level-scheduled solve: position p holds row
+// xrow[p] of V; the rows of level l (their depth in V's dependency graph) are
+// positions lvlptr[l]..lvlptr[l+1]; rowptr/colidx/vals hold each row's
+// off-diagonal entries with columns renumbered to positions; dinv = 1 / diag.
+struct LevelCsr {
+  int n = 0;
+  int nlev = 0;
+  int64_t nnz = 0;              // off-diagonal entries
+  int32_t* lvlptr = nullptr;    // nlev + 1
+  int32_t* rowptr = nullptr;    // n + 1
+  int32_t* colidx = nullptr;    // nnz
+  void* vals = nullptr;         // nnz
+  void* dinv = nullptr;         // n
+  int32_t* xrow = nullptr;      // n
+};
 
-// dinv[i] = 1 / V_ii (CSR V with a nonzero diagonal).
-cudaError_t csr_diag_inverse(const Csr& V, bool cplx, void* dinv, cudaStream_t s);
+// Builds L (buffers allocated by the caller; L.n, L.nlev, L.lvlptr set) from
+// the triangular CSR V (every diagonal entry present) and the level order
+// `order` (rows level by level); pos[i] receives the position of row i;
+// work needs n + scan_blocksums_size(n) int32.
+cudaError_t csr_level_permute(const Csr& V, bool cplx, const int32_t* order, int32_t* pos, int32_t* work,
+                              LevelCsr& L, cudaStream_t s);
+
+// cout[e] = pos[cin[e]] (column indices renumbered to level positions).
+cudaError_t remap_columns(int64_t nnz, const int32_t* pos, const int32_t* cin, int32_t* cout, cudaStream_t s);
+
+// t = V^-1 x by level scheduling on L: one 1024-thread block, a barrier
+// between levels; t in level order (t[p] belongs to row xrow[p]).
+cudaError_t trsv_levels_perm(const LevelCsr& L, bool cplx, const void* x, void* t, cudaStream_t s);

@@ -239,6 +239,35 @@ def learned_report(dev, keep=12, train_N=40, train_seeds=(11, 12), eval_N=64, ep
     return out
 
 
+def kv_sweep(w, A, PW, alg, prec, dev, budgets=(1, 2, 3, 4, 6, 8, 13)):
+    """The k_V sweep of Sec. 5 on this workload: at most k_V entries per
+    column of V (upper rule): ||A W - V||_F, setup time, BiCGSTAB to 1e-8."""
+    import torch
+    from paper_1208_3573_gb300 import diaf
+    S = diaf.Solver(A)
+    b = torch.from_numpy(w.b).to(dev)
+    out = []
+    for kv in budgets:
+        bud = torch.full((w.n,), kv, dtype=torch.int32, device=dev)
+        F = diaf.factor(A, PW, w.vrule, bud, alg=alg, prec=prec, tie_tol=w.tie_tol)
+        ms = F.timings()["total_ms"]
+        res = F.res.cpu().numpy()
+        row = {"k_V": kv, "nnz_V": int(F.V.nnz), "nrm_AW_minus_V": float(np.sqrt(np.sum(res ** 2))),
+               "setup_ms": ms}
+        try:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, info = S.bicgstab(b, F, tol=1e-8, maxit=1000)
+            torch.cuda.synchronize()
+            row.update(bicgstab_its=info.iterations, converged=bool(info.converged),
+                       solve_ms=1e3 * (time.perf_counter() - t0))
+        except diaf.DiafError as e:
+            row["solve"] = str(e)[:80]
+        F.close()
+        out.append(row)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -394,6 +423,13 @@ def main():
         extras["bicgstab"] = {"its": info.iterations, "converged": bool(info.converged), "relres": info.relres,
                               "solve_ms": solve_ms, "its_unpreconditioned": info0.iterations,
                               "err_inf": float((x - 1).abs().max().item())}
+        # GMRES(50) to 1e-6 (the paper's solver for the complex problems)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xg, ig = S.gmres(b, F, tol=1e-6, restart=50, maxit=2000)
+        torch.cuda.synchronize()
+        extras["gmres50"] = {"its": ig.iterations, "converged": bool(ig.converged), "relres": ig.relres,
+                             "solve_ms": 1e3 * (time.perf_counter() - t0)}
         F.close()
         # the plain FP64 form on the same workload: columns/s and residual agreement
         if args.prec != "fp64":
@@ -441,6 +477,11 @@ def main():
             tt.append(Fo.timings()["total_ms"])
             Fo.close()
         extras[f"alg_{other}_factor_columns_per_s"] = w.n / (statistics.median(tt) / 1e3)
+    if not args.no_extras and rank == 0 and do_apply:
+        try:
+            extras["kv_sweep"] = kv_sweep(w, A, PW, args.alg, args.prec, dev)
+        except Exception as e:
+            extras["kv_sweep"] = {"error": f"{type(e).__name__}: {e}"[:300]}
     if not args.no_extras and not args.no_learned and rank == 0:
         try:
             extras["learned_proposal"] = learned_report(dev)

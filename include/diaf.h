@@ -323,6 +323,17 @@ diaf_status diaf_mlp_adam(float* params, const float* grad, float* m, float* v, 
 diaf_status diaf_propose_select(const diaf_pattern* CAND, const float* score, int32_t keep, int32_t* colptr,
                                 int32_t* rowidx, void* stream);
 
+/* Right-preconditioned restarted GMRES(restart) on A x = b (Sec. 5's solver
+ * for the complex problems): x0 = 0, Arnoldi with classical Gram-Schmidt
+ * applied twice, Givens rotations on the device, stop when the residual
+ * estimate |g_{j+1}| <= tol ||b|| (the true residual is recomputed at every
+ * restart), at most maxit inner iterations; 1 <= restart <= 64 (DIAF_EINVAL
+ * otherwise).  F == NULL solves without preconditioner.  Allocates
+ * (restart + 6) vectors of n scalars for the call.  info->breakdown is set
+ * on a non-finite residual estimate. */
+diaf_status diaf_gmres(diaf_solver* S, diaf_factors* F, const void* b, void* x, double tol, int32_t restart,
+                       int32_t maxit, void* stream, diaf_solve_info* info);
+
 const char* diaf_status_string(diaf_status s);
 const char* diaf_last_error(void);
 

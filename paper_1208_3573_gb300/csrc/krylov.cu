@@ -276,6 +276,292 @@ diaf_status bicgstab_t(diaf_solver* SV, diaf_factors* F, const S* b, S* xout, do
   return DIAF_OK;
 }
 
+// ------------------------------------------------------------------ GMRES(m)
+// Right-preconditioned restarted GMRES (the solver of Sec. 5 for the complex
+// problems): Arnoldi with classical Gram-Schmidt applied twice (two passes
+// of one multi-dot and one multi-update each, so an iteration costs a fixed
+// number of launches), Givens rotations on the device, x += M (V y) at the
+// end of every cycle.  One device-to-host read per iteration: |g_{j+1}|.
+constexpr int kGmresMax = 64;
+
+template <class S>
+struct GState {
+  S H[(kGmresMax + 1) * kGmresMax];  // Hessenberg, column-major (ld kGmresMax + 1), rotated in place
+  double cs[kGmresMax];              // rotations [c, s; -conj(s), c], c real
+  S sn[kGmresMax];
+  S g[kGmresMax + 1];
+  S y[kGmresMax];
+  S h[kGmresMax + 1];                // current Gram-Schmidt coefficients
+  S dot;                             // scratch result
+  double resid;                      // |g_{j+1}|
+  double hnext;                      // H(j+1, j) (read together with resid)
+};
+
+// part[i * nb + block] = partial sum of conj(V_i) w over the block's elements
+template <class S>
+__global__ void k_mdot_partial(int n, const S* __restrict__ V, int cnt, const S* __restrict__ w, S* part) {
+  __shared__ S sh[kRedThreads / 32];
+  for (int i = 0; i < cnt; ++i) {
+    const S* vi = V + (size_t)i * n;
+    S acc = sc_zero<S>();
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+      acc += sc_cmul(vi[e], w[e]);
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      S t = sc_zero<S>();
+      for (int k = 0; k < kRedThreads / 32; ++k) t += sh[k];
+      part[(size_t)i * gridDim.x + blockIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// out[i] (+)= sum of part[i * nb ..]; one block per i
+template <class S>
+__global__ void k_mdot_final(const S* part, int nb, S* out, int accumulate) {
+  __shared__ S sh[kRedThreads / 32];
+  const int i = blockIdx.x;
+  S acc = sc_zero<S>();
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += part[(size_t)i * nb + b];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    S t = sc_zero<S>();
+    for (int k = 0; k < kRedThreads / 32; ++k) t += sh[k];
+    out[i] = accumulate ? out[i] + t : t;
+  }
+}
+
+// w -= sum_i c[i] V_i
+template <class S>
+__global__ void k_mupdate(int n, const S* __restrict__ V, int cnt, const S* __restrict__ c, S* w) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    S acc = sc_zero<S>();
+    for (int i = 0; i < cnt; ++i) acc += c[i] * V[(size_t)i * n + e];
+    w[e] -= acc;
+  }
+}
+
+// u = sum_i c[i] V_i
+template <class S>
+__global__ void k_combine(int n, const S* __restrict__ V, int cnt, const S* __restrict__ c, S* u) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    S acc = sc_zero<S>();
+    for (int i = 0; i < cnt; ++i) acc += c[i] * V[(size_t)i * n + e];
+    u[e] = acc;
+  }
+}
+
+// v = w / ||w|| from the reduction result (||w||^2 in st->dot); H(j+1, j) = ||w||
+template <class S>
+__global__ void k_normalize(int n, GState<S>* st, int j, const S* w, S* v) {
+  const double nrm = sqrt(fmax(sc_real(st->dot), 0.0));
+  const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) v[e] = inv * w[e];
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->hnext = nrm;
+}
+
+// column j of H from h and hnext; old rotations, a new one, g updated
+template <class S>
+__global__ void k_givens(GState<S>* st, int j) {
+  constexpr int LD = kGmresMax + 1;
+  S* col = st->H + (size_t)j * LD;
+  for (int i = 0; i <= j; ++i) col[i] = st->h[i];
+  col[j + 1] = sc_real_s<S>(st->hnext);
+  for (int i = 0; i < j; ++i) {
+    const S a = col[i], b = col[i + 1];
+    col[i] = st->cs[i] * a + st->sn[i] * b;
+    col[i + 1] = st->cs[i] * b - sc_conj(st->sn[i]) * a;
+  }
+  const S a = col[j];
+  const double bb = sc_real(col[j + 1]);  // a norm: real, >= 0
+  const double aa = sqrt((double)sc_abs2(a));
+  const double t = sqrt(aa * aa + bb * bb);
+  double c;
+  S sv;
+  if (t == 0.0) {
+    c = 1.0; sv = sc_zero<S>();
+  } else if (aa == 0.0) {
+    c = 0.0; sv = sc_real_s<S>(1.0);
+  } else {
+    c = aa / t;
+    sv = (bb / (aa * t)) * a;  // (a / |a|) (b / t)
+  }
+  st->cs[j] = c;
+  st->sn[j] = sv;
+  col[j] = c * a + sv * col[j + 1];
+  col[j + 1] = sc_zero<S>();
+  const S gj = st->g[j];
+  st->g[j + 1] = -(sc_conj(sv) * gj);
+  st->g[j] = c * gj;
+  st->resid = sqrt((double)sc_abs2(st->g[j + 1]));
+}
+
+// y = R^-1 g for the rotated k x k upper triangle; zero pivots give 0
+template <class S>
+__global__ void k_backsolve(GState<S>* st, int k) {
+  constexpr int LD = kGmresMax + 1;
+  for (int i = k - 1; i >= 0; --i) {
+    S acc = st->g[i];
+    for (int t = i + 1; t < k; ++t) acc -= st->H[i + (size_t)t * LD] * st->y[t];
+    const S d = st->H[i + (size_t)i * LD];
+    st->y[i] = sc_abs2(d) > 0.0 ? sdiv(acc, d) : sc_zero<S>();
+  }
+}
+
+// start of a cycle: g = (beta, 0, ...), v_0 = r / beta (beta from st->dot)
+template <class S>
+__global__ void k_cycle_start(int n, GState<S>* st, const S* r, S* v0) {
+  const double beta = sqrt(fmax(sc_real(st->dot), 0.0));
+  const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) v0[e] = inv * r[e];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int i = 0; i <= kGmresMax; ++i) st->g[i] = sc_zero<S>();
+    st->g[0] = sc_real_s<S>(beta);
+    st->resid = beta;
+  }
+}
+
+template <class S>
+__global__ void k_add_small(int cnt, const S* a, S* h) {  // h += a (cnt <= blockDim)
+  if ((int)threadIdx.x < cnt) h[threadIdx.x] += a[threadIdx.x];
+}
+
+template <class S>
+__global__ void k_axpy1(int n, const S* a, S* x) {  // x += a
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) x[e] += a[e];
+}
+template <class S>
+__global__ void k_sub(int n, const S* a, const S* b, S* out) {  // out = a - b
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) out[e] = a[e] - b[e];
+}
+
+template <class S>
+diaf_status gmres_t(diaf_solver* SV, diaf_factors* F, const S* b, S* xout, double tol, int m, int maxit,
+                    cudaStream_t s, diaf_solve_info* info) {
+  const int n = SV->n;
+  const int vb = 304, vt = 256;
+  std::vector<void*> tmp;
+  struct Free {
+    std::vector<void*>& v;
+    cudaStream_t s;
+    ~Free() { for (void* p : v) cudaFreeAsync(p, s); }
+  } fr{tmp, s};
+  auto get = [&](void** q, size_t bytes) -> bool {
+    void* z = nullptr;
+    if (cudaMallocAsync(&z, bytes > 0 ? bytes : 1, s) != cudaSuccess) return false;
+    tmp.push_back(z);
+    *q = z;
+    return true;
+  };
+  S *V, *w, *x, *r, *u, *z, *part;
+  GState<S>* st;
+  const size_t nv = sizeof(S) * (size_t)(n > 0 ? n : 1);
+  if (!get((void**)&V, nv * (m + 1)) || !get((void**)&w, nv) || !get((void**)&x, nv) || !get((void**)&r, nv) ||
+      !get((void**)&u, nv) || !get((void**)&z, nv) ||
+      !get((void**)&part, sizeof(S) * (size_t)kRedBlocks * (kGmresMax + 1)) || !get((void**)&st, sizeof(GState<S>)))
+    return DIAF_ENOMEM;
+  cudaMemsetAsync(st, 0, sizeof(GState<S>), s);
+  info->iterations = 0; info->converged = 0; info->breakdown = 0; info->relres = 0.0;
+  auto M = [&](const S* in, S* out) -> diaf_status {
+    if (F) return diaf_apply(F, in, out, s);
+    k_copy<S><<<vb, vt, 0, s>>>(n, in, out);
+    DIAF_COUNT_LAUNCH();
+    return DIAF_OK;
+  };
+  auto norm2_to_dot = [&](const S* a) {
+    dot2<S>(n, a, a, nullptr, nullptr, part, &st->dot, nullptr, s);
+  };
+  auto read = [&](const double* dp) -> double {
+    double h = 0.0;
+    cudaMemcpyAsync(&h, dp, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return NAN;
+    return h;
+  };
+  k_zero<S><<<vb, vt, 0, s>>>(n, x);
+  DIAF_COUNT_LAUNCH();
+  k_copy<S><<<vb, vt, 0, s>>>(n, b, r);
+  DIAF_COUNT_LAUNCH();
+  norm2_to_dot(r);
+  k_cycle_start<S><<<vb, vt, 0, s>>>(n, st, r, V);
+  DIAF_COUNT_LAUNCH();
+  const double bn = read(&st->resid);
+  if (!(bn == bn)) return DIAF_ECUDA;
+  if (bn == 0.0) {
+    k_copy<S><<<vb, vt, 0, s>>>(n, x, xout);
+    DIAF_COUNT_LAUNCH();
+    info->converged = 1;
+    return cudaStreamSynchronize(s) == cudaSuccess ? DIAF_OK : DIAF_ECUDA;
+  }
+  int its = 0;
+  double rel = 1.0;
+  while (its < maxit) {
+    int kdone = 0;
+    bool happy = false;
+    for (int j = 0; j < m && its < maxit; ++j) {
+      S* vj = V + (size_t)j * n;
+      diaf_status ms = M(vj, z);
+      if (ms != DIAF_OK) return ms;
+      csr_spmv(SV->A, SV->dtype == DIAF_C128, z, w, s);
+      // classical Gram-Schmidt, twice: h = V^* w, w -= V h; c = V^* w, w -= V c, h += c
+      k_mdot_partial<S><<<kRedBlocks, kRedThreads, 0, s>>>(n, V, j + 1, w, part);
+      DIAF_COUNT_LAUNCH();
+      k_mdot_final<S><<<j + 1, kRedThreads, 0, s>>>(part, kRedBlocks, st->h, 0);
+      DIAF_COUNT_LAUNCH();
+      k_mupdate<S><<<vb, vt, 0, s>>>(n, V, j + 1, st->h, w);
+      DIAF_COUNT_LAUNCH();
+      k_mdot_partial<S><<<kRedBlocks, kRedThreads, 0, s>>>(n, V, j + 1, w, part);
+      DIAF_COUNT_LAUNCH();
+      k_mdot_final<S><<<j + 1, kRedThreads, 0, s>>>(part, kRedBlocks, st->y, 0);  // y: scratch until the cycle ends
+      DIAF_COUNT_LAUNCH();
+      k_mupdate<S><<<vb, vt, 0, s>>>(n, V, j + 1, st->y, w);
+      DIAF_COUNT_LAUNCH();
+      k_add_small<S><<<1, kGmresMax, 0, s>>>(j + 1, st->y, st->h);
+      DIAF_COUNT_LAUNCH();
+      norm2_to_dot(w);
+      k_normalize<S><<<vb, vt, 0, s>>>(n, st, j, w, V + (size_t)(j + 1) * n);
+      DIAF_COUNT_LAUNCH();
+      k_givens<S><<<1, 1, 0, s>>>(st, j);
+      DIAF_COUNT_LAUNCH();
+      ++its;
+      kdone = j + 1;
+      double rh[2] = {NAN, NAN};  // resid and hnext are adjacent: one read
+      cudaMemcpyAsync(rh, &st->resid, sizeof(double) * 2, cudaMemcpyDeviceToHost, s);
+      if (cudaStreamSynchronize(s) != cudaSuccess) return DIAF_ECUDA;
+      if (!(rh[0] == rh[0])) { info->breakdown = 1; break; }
+      rel = rh[0] / bn;
+      if (rel <= tol || rh[1] == 0.0) { happy = rh[1] == 0.0; break; }
+    }
+    if (info->breakdown) break;
+    k_backsolve<S><<<1, 1, 0, s>>>(st, kdone);
+    DIAF_COUNT_LAUNCH();
+    k_combine<S><<<vb, vt, 0, s>>>(n, V, kdone, st->y, u);
+    DIAF_COUNT_LAUNCH();
+    diaf_status ms = M(u, z);
+    if (ms != DIAF_OK) return ms;
+    k_axpy1<S><<<vb, vt, 0, s>>>(n, z, x);
+    DIAF_COUNT_LAUNCH();
+    // true residual, next cycle
+    csr_spmv(SV->A, SV->dtype == DIAF_C128, x, w, s);
+    k_sub<S><<<vb, vt, 0, s>>>(n, b, w, r);
+    DIAF_COUNT_LAUNCH();
+    norm2_to_dot(r);
+    k_cycle_start<S><<<vb, vt, 0, s>>>(n, st, r, V);
+    DIAF_COUNT_LAUNCH();
+    rel = read(&st->resid) / bn;
+    if (rel <= tol) { info->converged = 1; break; }
+    if (happy) break;
+  }
+  info->iterations = its;
+  info->relres = rel;
+  k_copy<S><<<vb, vt, 0, s>>>(n, x, xout);
+  DIAF_COUNT_LAUNCH();
+  return cudaStreamSynchronize(s) == cudaSuccess ? DIAF_OK : DIAF_ECUDA;
+}
+
 }  // namespace
 
 extern "C" {
@@ -310,6 +596,15 @@ void diaf_solver_free(diaf_solver* S) {
   if (!S) return;
   for (void* p : S->owned) cudaFreeAsync(p, S->stream);
   delete S;
+}
+
+diaf_status diaf_gmres(diaf_solver* S, diaf_factors* F, const void* b, void* x, double tol, int32_t restart,
+                       int32_t maxit, void* stream, diaf_solve_info* info) {
+  if (!S || !b || !x || !info || maxit < 0 || restart < 1 || restart > kGmresMax) return DIAF_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (S->dtype == DIAF_C128)
+    return gmres_t<Cx<double>>(S, F, (const Cx<double>*)b, (Cx<double>*)x, tol, restart, maxit, s, info);
+  return gmres_t<double>(S, F, (const double*)b, (double*)x, tol, restart, maxit, s, info);
 }
 
 diaf_status diaf_bicgstab(diaf_solver* S, diaf_factors* F, const void* b, void* x, double tol, int32_t maxit,

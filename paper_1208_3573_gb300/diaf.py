@@ -111,6 +111,8 @@ def lib() -> ctypes.CDLL:
         L.diaf_solver_free.argtypes = [vp]
         L.diaf_solver_free.restype = None
         L.diaf_bicgstab.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_int32, vp, ctypes.POINTER(SolveInfo_t)]
+        L.diaf_gmres.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, vp,
+                                 ctypes.POINTER(SolveInfo_t)]
         L.diaf_factor_timings.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]
         L.diaf_launch_count.restype = ctypes.c_longlong
         L.diaf_factor_fallbacks.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]
@@ -369,6 +371,15 @@ class Solver:
         info = SolveInfo_t()
         _check(lib().diaf_bicgstab(self._h, M.handle if M is not None else None, _ptr(b), _ptr(x), tol, maxit,
                                    _stream(stream), ctypes.byref(info)))
+        return x, info
+
+    def gmres(self, b: torch.Tensor, M: Factors | None = None, tol=1e-6, restart=50, maxit=2000, x=None,
+              stream=None):
+        if x is None:
+            x = torch.empty_like(b)
+        info = SolveInfo_t()
+        _check(lib().diaf_gmres(self._h, M.handle if M is not None else None, _ptr(b), _ptr(x), tol, restart,
+                                maxit, _stream(stream), ctypes.byref(info)))
         return x, info
 
     def __del__(self):

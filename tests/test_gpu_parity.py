@@ -163,3 +163,29 @@ def test_bicgstab_iterations_match_oracle(D, alg):
     assert np.allclose(x.cpu().numpy(), 1.0, atol=1e-5)
     x0, info0 = S.bicgstab(b, None, tol=1e-8, maxit=1000)
     assert info0.converged and info.iterations < info0.iterations
+
+
+@pytest.mark.parametrize("name", ["helmholtz40", "convdiff32"])
+def test_gmres_matches_oracle(D, name):
+    """GMRES(50) to 1e-6 with the preconditioner (the solver of Sec. 5 for
+    the complex problem): iteration count within 2 of the oracle's GMRES."""
+    w = make_workload(name)
+    F = run_gpu(D, w.A, w.PW, w.vrule, w.budget, alg="S", tie_tol=w.tie_tol)
+    S = D.Solver(D.DeviceCSC.from_host(w.A))
+    b = torch.from_numpy(w.b).cuda()
+    x, info = S.gmres(b, F, tol=1e-6, restart=50, maxit=2000)
+    o = O.factor(w.A, w.PW, w.vrule, w.budget, alg="S", tie_tol=w.tie_tol)
+    xo, its, rr, st = O.gmres(w.A.to_scipy(), w.b, O.Preconditioner(o.W_csc(), o.V_csc()), restart=50, tol=1e-6)
+    assert info.converged == 1 and st == "ok"
+    assert abs(info.iterations - its) <= 2, (info.iterations, its)
+    r = w.b - w.A.to_scipy() @ x.cpu().numpy()
+    assert np.linalg.norm(r) <= 1.01e-6 * np.linalg.norm(w.b)
+    # a short restart length forces several cycles
+    x5, info5 = S.gmres(b, F, tol=1e-6, restart=5, maxit=5000)
+    xo5, its5, _, st5 = O.gmres(w.A.to_scipy(), w.b, O.Preconditioner(o.W_csc(), o.V_csc()), restart=5, tol=1e-6,
+                                maxit=5000)
+    assert info5.converged == (st5 == "ok")
+    if st5 == "ok":
+        assert abs(info5.iterations - its5) <= max(3, its5 // 20), (info5.iterations, its5)
+    x0, info0 = S.gmres(b, None, tol=1e-6, restart=50, maxit=4000)
+    assert info.iterations < info0.iterations

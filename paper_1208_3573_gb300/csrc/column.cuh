@@ -388,7 +388,7 @@ __device__ void solve_column_warp(const ColArgs& a, int j, unsigned char* smem, 
   if (k > 0) {
     for (int i = lane; i < me * k; i += DIAF_WARP) Tw[(i % me) + (i / me) * LDT] = Ts[(i % me) + (i / me) * LDT];
     __syncwarp();
-    warp_householder_qr<S, LDT>(Tw, me, k, lane);
+    warp_householder_qr_rs<S, LDT, KMAX, MMAX / DIAF_WARP>(Tw, me, k, lane);
     for (int i = lane; i < k * k; i += DIAF_WARP) {
       int r = i % k, c = i / k;
       Rs[r + c * KP] = (r <= c) ? Tw[r + c * LDT] : sc_zero<S>();
@@ -424,7 +424,7 @@ __device__ void solve_column_warp(const ColArgs& a, int j, unsigned char* smem, 
       Tw[r + c * LDT] = (r < m && ix.inI[r] >= 0) ? sc_zero<S>() : Ts[r + c * LDT];
     }
     __syncwarp();
-    warp_householder_qr<S, LDT>(Tw, me, k, lane);
+    warp_householder_qr_rs<S, LDT, KMAX, MMAX / DIAF_WARP>(Tw, me, k, lane);
     for (int i = lane; i < k * k; i += DIAF_WARP) {
       int r = i % k, c = i / k;
       Rs[r + c * KP] = (r <= c) ? Tw[r + c * LDT] : sc_zero<S>();

@@ -114,7 +114,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
   }
   __syncwarp();
   DIAF_PHASE(1);
-  warp_householder_qr<S, LDT>(Tw, me, k, lane);
+  warp_householder_qr_rs<S, LDT, KMAX, MMAX / DIAF_WARP>(Tw, me, k, lane);
   for (int i = lane; i < k * k; i += DIAF_WARP) {
     int r = i % k, c = i / k;
     Rs[r + c * KP] = (r <= c) ? Tw[r + c * LDT] : sc_zero<S>();
@@ -156,7 +156,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     }
     __syncwarp();
     DIAF_PHASE(5);
-    warp_householder_qr<S, LDT>(Tw, me, k, lane);
+    warp_householder_qr_rs<S, LDT, KMAX, MMAX / DIAF_WARP>(Tw, me, k, lane);
     DIAF_PHASE(6);
     float kh = 0.0f;
     for (int c = lane; c < k; c += DIAF_WARP) {

@@ -94,6 +94,105 @@ __device__ void warp_householder_qr(S* T, int m, int k, int lane) {
   }
 }
 
+// Butterfly reduce-scatter of NQ values (NQ a power of two, 2..32) across the
+// warp: at each of the log2(NQ) steps a lane keeps one half of its values
+// (the upper half when its lane bit is set) and adds the partner's copy of
+// that half, received for the half it gives away; the lane bits left over
+// finish with a plain butterfly sum.  On return lane L holds the warp-wide
+// sum of value L >> (5 - log2 NQ), with log2(NQ) + 1 ... 5 dependent
+// shuffles instead of 5 per value.
+constexpr int ilog2_c(int x) { return x <= 1 ? 0 : 1 + ilog2_c(x / 2); }
+
+template <class S, int NQ>
+__device__ __forceinline__ S warp_reduce_scatter(S (&v)[NQ], int lane) {
+  constexpr int LOG = ilog2_c(NQ);
+  static_assert((1 << LOG) == NQ && NQ >= 2 && NQ <= 32, "NQ must be a power of two in [2, 32]");
+#pragma unroll
+  for (int t = 0; t < LOG; ++t) {
+    const int mask = 16 >> t;
+    const int half = NQ >> (t + 1);
+    const bool upper = (lane & mask) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const S give = upper ? v[i] : v[i + half];
+      const S keep = upper ? v[i + half] : v[i];
+      v[i] = keep + shfl_xor(give, mask);
+    }
+  }
+#pragma unroll
+  for (int t = LOG; t < 5; ++t) v[0] += shfl_xor(v[0], 16 >> t);
+  return v[0];
+}
+
+// Householder QR as warp_householder_qr (same reflectors), with all the
+// trailing-column products of one reflector formed together: lane r owns rows
+// r, r + 32, ... (MR rows, m <= 32 MR), the k <= NQ partial sums go through one
+// reduce-scatter and come back by one broadcast each.
+template <class S, int LD, int NQ, int MR>
+__device__ void warp_householder_qr_rs(S* T, int m, int k, int lane) {
+  using R = RealOf<S>;
+  constexpr int LOG = ilog2_c(NQ);
+  const int p = m < k ? m : k;
+  for (int c = 0; c < p; ++c) {
+    S* tc = T + c * LD;
+    S ur[MR];
+    R nrm2 = R(0);
+#pragma unroll
+    for (int i = 0; i < MR; ++i) {
+      const int r = lane + DIAF_WARP * i;
+      ur[i] = (r >= c && r < m) ? tc[r] : sc_zero<S>();
+      nrm2 += sc_abs2(ur[i]);
+    }
+    nrm2 = warp_sum(nrm2);
+    const S alpha = tc[c];
+    __syncwarp();
+    if (nrm2 == R(0)) continue;
+    const R ax = sc_abs(alpha);
+    const R nrm = sqrt(nrm2);
+    const S ph = sc_unit(alpha);
+    const S beta = -(nrm * ph);
+    const S u0 = (ax + nrm) * ph;
+    const R two_uu = div_r(R(1), nrm * (nrm + ax));
+#pragma unroll
+    for (int i = 0; i < MR; ++i)
+      if (lane + DIAF_WARP * i == c) ur[i] = u0;
+    if (c + 1 < k) {
+      S v[NQ];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        S acc = sc_zero<S>();
+        if (q > c && q < k) {
+#pragma unroll
+          for (int i = 0; i < MR; ++i) {
+            const int r = lane + DIAF_WARP * i;
+            if (r < m) acc += sc_cmul(ur[i], T[r + q * LD]);
+          }
+        }
+        v[q] = acc;
+      }
+      const S fmine = two_uu * warp_reduce_scatter<S, NQ>(v, lane);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        if (q > c && q < k) {  // warp-uniform
+          const S fq = shfl_idx(fmine, q << (5 - LOG));
+#pragma unroll
+          for (int i = 0; i < MR; ++i) {
+            const int r = lane + DIAF_WARP * i;
+            if (r >= c && r < m) T[r + q * LD] -= fq * ur[i];
+          }
+        }
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < MR; ++i) {
+      const int r = lane + DIAF_WARP * i;
+      if (r >= c && r < m) tc[r] = (r == c) ? beta : sc_zero<S>();
+    }
+    __syncwarp();
+  }
+}
+
 // ------------------------------------------------------------------ Jacobi
 // Parallel one-sided (Hestenes) Jacobi on the p x q matrix G (leading
 // dimension LDG): G V has orthogonal columns, V (q x q, leading dimension

@@ -309,7 +309,9 @@ diaf_status diaf_mlp_forward(const float* params, const float* feat, int64_t nro
 
 /* grad = d/dparams of loss = (1/nrows) sum_s (network(feat[s]) - target[s])^2,
  * *loss = that loss (both overwritten; grad has DIAF_PROP_NPARAM floats).
- * Sums are formed with float atomics: the order, and so the last bits, vary. */
+ * Per-block partial sums are added in block order: the result is reproducible.
+ * Allocates (stream-ordered) one scratch row of DIAF_PROP_NPARAM + 1 floats
+ * per 128 rows. */
 diaf_status diaf_mlp_grad(const float* params, const float* feat, const float* target, int64_t nrows, float* grad,
                           float* loss, void* stream);
 

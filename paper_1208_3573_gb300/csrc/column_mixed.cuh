@@ -170,7 +170,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
       Rs[r + c * KP] = (r <= c) ? Tw[r + c * LDT] : sc_zero<S>();
     }
     __syncwarp();
-    int sw = warp_jacobi<S, KP, KP, KMAX>(Rs, k, k, Vj, lane);
+    int sw = warp_jacobi<S, KP, KP, KMAX, true>(Rs, k, k, Vj, lane);
     if (sw < 0) flags |= DIAF_FLAG_JACOBI_NOCONV;
 #ifdef DIAF_PHASE_TIMING
     if (lane == 0 && a.phase) atomicAdd(&a.phase[20], (unsigned long long)(sw < 0 ? kMaxSweeps : sw));
@@ -248,7 +248,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     // ---- FP32 Jacobi on Q_I (FP32 rows of Q = T R^-1 in Tw)
     if (l > kRRMax) { hand_back(5); return; }
     compact_rows<S, LDT>(Tw, ix.Iloc, l, k, lane);
-    int sw = warp_jacobi<S, LDT, KP, KMAX>(Tw, l, k, Vj, lane);
+    int sw = warp_jacobi<S, LDT, KP, KMAX, true>(Tw, l, k, Vj, lane);
     if (sw < 0) flags |= DIAF_FLAG_JACOBI_NOCONV;
     warp_col_norms<S, LDT>(Tw, l, k, sig, lane);
     int imax = 0;

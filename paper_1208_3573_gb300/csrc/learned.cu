@@ -154,12 +154,15 @@ __global__ void mlp_forward_kernel(const float* __restrict__ params, const float
 
 // Gradient of L = (1/nrows) sum_s (y_s - t_s)^2 for a block of kGradRows
 // samples: per-sample backward into shared memory, then every parameter's
-// gradient as a sum over the block's samples, added to grad with atomics.
+// gradient as a sum over the block's samples, written to the block's row of
+// `part` (NPARAM + 1 floats: the gradient, then the loss); the blocks' rows
+// are summed in block order afterwards, so the result is reproducible.
 constexpr int kGradRows = 128;
+constexpr int kPartLd = NPARAM + 1;
 
 __global__ void __launch_bounds__(kGradRows)
     mlp_grad_kernel(const float* __restrict__ params, const float* __restrict__ feat, const float* __restrict__ target,
-                    int64_t nrows, float* __restrict__ grad, float* __restrict__ loss) {
+                    int64_t nrows, float* __restrict__ part) {
   extern __shared__ float sm[];
   float* P = sm;                        // NPARAM
   float* sF = P + NPARAM;               // [kGradRows][F]
@@ -227,9 +230,8 @@ __global__ void __launch_bounds__(kGradRows)
     } else {
       for (int r = 0; r < rows; ++r) g += sDy[r];
     }
-    atomicAdd(&grad[p], g);
+    part[(size_t)blockIdx.x * kPartLd + p] = g;
   }
-  // loss: block sum then one atomic
   l2 = warp_sum(l2);
   __shared__ float red[kGradRows / 32];
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l2;
@@ -237,8 +239,19 @@ __global__ void __launch_bounds__(kGradRows)
   if (threadIdx.x == 0) {
     float tot = 0.0f;
     for (int w = 0; w < kGradRows / 32; ++w) tot += red[w];
-    atomicAdd(loss, tot / (float)nrows);
+    part[(size_t)blockIdx.x * kPartLd + NPARAM] = tot / (float)nrows;
   }
+}
+
+// grad[p] = sum over blocks of part[b][p] (in block order); loss likewise
+__global__ void grad_reduce_kernel(const float* __restrict__ part, int nblocks, float* __restrict__ grad,
+                                   float* __restrict__ loss) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p > NPARAM) return;
+  float acc = 0.0f;
+  for (int b = 0; b < nblocks; ++b) acc += part[(size_t)b * kPartLd + p];
+  if (p < NPARAM) grad[p] = acc;
+  else *loss = acc;
 }
 
 __global__ void adam_kernel(float* __restrict__ params, const float* __restrict__ grad, float* __restrict__ m,
@@ -340,8 +353,6 @@ diaf_status diaf_mlp_grad(const float* d_params, const float* d_feat, const floa
                           float* d_grad, float* d_loss, void* stream) {
   if (nrows <= 0 || !d_params || !d_feat || !d_target || !d_grad || !d_loss) return DIAF_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaMemsetAsync(d_grad, 0, sizeof(float) * NPARAM, s);
-  cudaMemsetAsync(d_loss, 0, sizeof(float), s);
   const size_t smem = sizeof(float) * (NPARAM + kGradRows * (F + 4 * H + 1));
   static bool configured = false;
   if (!configured) {
@@ -349,9 +360,16 @@ diaf_status diaf_mlp_grad(const float* d_params, const float* d_feat, const floa
       return DIAF_ECUDA;
     configured = true;
   }
-  const int blocks = (int)((nrows + kGradRows - 1) / kGradRows);
-  mlp_grad_kernel<<<blocks, kGradRows, smem, s>>>(d_params, d_feat, d_target, nrows, d_grad, d_loss);
+  const int64_t nb64 = (nrows + kGradRows - 1) / kGradRows;
+  if (nb64 > INT_MAX) return DIAF_EINVAL;
+  const int blocks = (int)nb64;
+  float* part = nullptr;
+  if (cudaMallocAsync(&part, sizeof(float) * (size_t)blocks * kPartLd, s) != cudaSuccess) return DIAF_ENOMEM;
+  mlp_grad_kernel<<<blocks, kGradRows, smem, s>>>(d_params, d_feat, d_target, nrows, part);
   DIAF_COUNT_LAUNCH();
+  grad_reduce_kernel<<<ceil_div(kPartLd, 256), 256, 0, s>>>(part, blocks, d_grad, d_loss);
+  DIAF_COUNT_LAUNCH();
+  cudaFreeAsync(part, s);
   return cudaGetLastError() == cudaSuccess ? DIAF_OK : DIAF_ECUDA;
 }
 

@@ -205,7 +205,11 @@ __device__ void warp_householder_qr_rs(S* T, int m, int k, int lane) {
 // smaller root of t^2 + 2 zeta t - 1 = 0, zeta = (beta - alpha) / (2|gamma|),
 // i.e. t = sign(d) 2|gamma| / (|d| + sqrt(d^2 + 4|gamma|^2)), d = beta - alpha.
 // Returns sweeps used, or -1 at the sweep limit.
-template <class S, int LDG, int LDV, int QMAX>
+// PREDICT (reduced-precision callers whose result is refined afterwards):
+// the sweep that would only confirm convergence is skipped -- once every
+// rotation of a sweep had |gamma| < sqrt(tol) sqrt(alpha beta), Jacobi's
+// quadratic convergence leaves the next sweep's ratios near tol.
+template <class S, int LDG, int LDV, int QMAX, bool PREDICT = false>
 __device__ int warp_jacobi(S* G, int p, int q, S* V, int lane) {
   using R = RealOf<S>;
   constexpr int kPairsMax = QMAX / 2;
@@ -229,6 +233,7 @@ __device__ int warp_jacobi(S* G, int p, int q, S* V, int lane) {
   const int L = qq - 1;
   for (int sweep = 1; sweep <= kMaxSweeps; ++sweep) {
     bool rotated = false;
+    bool large = false;  // PREDICT: a rotation with |gamma|^2 >= tol alpha beta
     for (int rnd = 0; rnd < L; ++rnd) {
       for (int pr0 = 0; pr0 < npairs; pr0 += kGroups) {
         int pr = pr0 + grp;
@@ -264,6 +269,7 @@ __device__ int warp_jacobi(S* G, int p, int q, S* V, int lane) {
         bool rot = act && al > tiny && be > tiny && ag2 > R(0) && ag2 > tol2 * (al * be);
         if (rot) {
           rotated = true;
+          if (PREDICT && ag2 >= tol * (al * be)) large = true;
           R ag;
           S eph;
           if constexpr (ScalarInfo<S>::cplx) {
@@ -296,6 +302,7 @@ __device__ int warp_jacobi(S* G, int p, int q, S* V, int lane) {
       }
     }
     if (!__any_sync(DIAF_FULL, rotated)) return sweep;
+    if (PREDICT && !__any_sync(DIAF_FULL, large)) return sweep;
   }
   return -1;
 }

@@ -97,6 +97,16 @@ def test_adam_matches_oracle(D):
     np.testing.assert_allclose(P.cpu().numpy(), to, rtol=1e-6, atol=1e-6)
 
 
+def test_gradient_is_reproducible(D):
+    th = torch.from_numpy(_params(12)).cuda()
+    X = torch.from_numpy(_feat(13, 50000)).cuda()
+    t = torch.from_numpy(np.random.default_rng(14).normal(0, 1, 50000).astype(np.float32)).cuda()
+    g1, l1 = D.mlp_grad(th, X, t)
+    g1, l1 = g1.clone(), l1.clone()
+    g2, l2 = D.mlp_grad(th, X, t)
+    assert torch.equal(g1, g2) and torch.equal(l1, l2)
+
+
 def test_training_steps_match_oracle(D):
     # ten full-batch gradient + Adam steps, GPU against the oracle in FP64
     th = _params(7, 0.3)
@@ -187,5 +197,5 @@ def test_trained_network_beats_fixed_rule(D, alg):
     r_f, its_f, ok_f = _quality(D, w, fixed, alg)
     print(f"{alg}: learned ||AWV^-1 - I||_F^2 {r_l:.4e} its {its_l}; fixed {r_f:.4e} its {its_f}")
     assert ok_l and ok_f
-    assert r_l < 0.98 * r_f       # measured: about 4% lower at 16^3, 5-6% at 64^3
-    assert its_l <= its_f + 2     # iteration counts agree within BiCGSTAB's own +-2 jitter
+    assert r_l < 0.98 * r_f                # measured: about 4% lower at 16^3, 5-6% at 64^3
+    assert its_l <= int(1.15 * its_f) + 1  # about 20 iterations at 16^3: equal within a few

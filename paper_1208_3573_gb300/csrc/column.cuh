@@ -203,7 +203,8 @@ __device__ inline int build_I(const ColArgs& a, int j, int m, int l, const Colum
 // ||A_j w - v||, finiteness, and the scatter of column j.
 template <class SD, int LDT>
 __device__ void finish_column(const ColArgs& a, int j, int k, int m, int l, int jpos, const SD* Ts, SD* wv, SD* vv,
-                              const ColumnIdx& ix, uint32_t flags, bool do_phase, int lane) {
+                              const ColumnIdx& ix, uint32_t flags, bool do_phase, int lane,
+                              double rank_thr = -1.0) {
   using R = RealOf<SD>;
   if (do_phase) {
     SD ph = sc_real_s<SD>(R(1));
@@ -239,6 +240,7 @@ __device__ void finish_column(const ColArgs& a, int j, int k, int m, int l, int 
     if (ix.Iloc[t] < 0) r2 += sc_abs2(vv[t]);
   r2 = warp_sum(r2);
   const double resj = sqrt((double)r2);
+  if (resj <= rank_thr) flags |= DIAF_FLAG_RANK_DEFICIENT;  // DIAF-S: res = ||A-hat w|| = sigma_min
   bool finite = isfinite(resj);
   for (int q = lane; q < k; q += DIAF_WARP) finite &= isfinite(sc_real(wv[q])) && isfinite(sc_imag(wv[q]));
   for (int t = lane; t < l; t += DIAF_WARP) finite &= isfinite(sc_real(vv[t])) && isfinite(sc_imag(vv[t]));

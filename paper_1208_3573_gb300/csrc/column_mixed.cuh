@@ -107,10 +107,11 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     int r = i % me, c = i / me;
     Tw[r + c * LDT] = sc_cast<S>(Ts[r + c * LDT]);
   }
-  for (int c = lane; c < k; c += DIAF_WARP) {
-    double s2 = 0.0;
-    for (int r = 0; r < m; ++r) s2 += (double)sc_abs2(Ts[r + c * LDT]);
-    cn[c] = sqrt(s2);
+  __syncwarp();
+  for (int c = lane; c < k; c += DIAF_WARP) {  // column norms for the kappa estimate: FP32 is enough
+    R s2 = R(0);
+    for (int r = 0; r < m; ++r) s2 += sc_abs2(Tw[r + c * LDT]);
+    cn[c] = (double)sqrt(s2);
   }
   __syncwarp();
   DIAF_PHASE(1);
@@ -138,6 +139,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     if (l > 1 && margin <= 2.0 * delta) { hand_back(2); return; }
   }
   const int jpos = build_I(a, j, m, l, ix, lane);
+  double rank_thr = -1.0;
   for (int t = lane; t < l; t += DIAF_WARP) vv[t] = sc_zero<SD>();
   __syncwarp();
   DIAF_PHASE(4);
@@ -148,11 +150,11 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
       int r = i % me, c = i / me;
       Tw[r + c * LDT] = (r < m && ix.inI[r] >= 0) ? sc_zero<S>() : sc_cast<S>(Ts[r + c * LDT]);
     }
+    __syncwarp();
     for (int c = lane; c < k; c += DIAF_WARP) {
-      double s2 = 0.0;
-      for (int r = 0; r < m; ++r)
-        if (ix.inI[r] < 0) s2 += (double)sc_abs2(Ts[r + c * LDT]);
-      cn[c] = sqrt(s2);
+      R s2 = R(0);
+      for (int r = 0; r < m; ++r) s2 += sc_abs2(Tw[r + c * LDT]);
+      cn[c] = (double)sqrt(s2);
     }
     __syncwarp();
     DIAF_PHASE(5);
@@ -191,7 +193,11 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     for (int c = 0; c < k; ++c) if (c != imin) gap = dmin(gap, sig[c] * sig[c] - smin * smin);
     if (k > 1 && gap <= 1e-5 * smax * smax) { hand_back(4); return; }
     const int iters = (k > 1 && gap < 1e-2 * smax * smax) ? 2 : 1;
-    SD* cc = rinvD;  // correction coefficients (KMAX)
+    // the correction itself is small: its projection runs in FP32 (relative
+    // error ~1e-7 of a correction of relative size <~1e-5), the Rayleigh
+    // quotient and the residual r = H x - d x in FP64
+    S* cc = reinterpret_cast<S*>(rinvD);  // correction coefficients (KMAX)
+    S* rf = reinterpret_cast<S*>(wv);     // r in FP32 (KMAX)
     SD x = lane < k ? sc_cast<SD>(Vj[lane + imin * KP]) : sc_zero<SD>();
     for (int it = 0; it < iters; ++it) {
       if (lane < k) gg[lane] = x;
@@ -209,17 +215,21 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
       const double xg = warp_sum(lane < k ? (double)sc_real(sc_cmul(x, g)) : 0.0);
       const double xx = warp_sum(lane < k ? (double)sc_abs2(x) : 0.0);
       const double d = xg / xx;
-      if (lane < k) wv[lane] = g - RealOf<SD>(d) * x;  // r = H x - d x
+      if (lane < k) rf[lane] = sc_cast<S>(g - RealOf<SD>(d) * x);  // r = H x - d x
       __syncwarp();
       if (lane < k) {
-        SD vr = sc_zero<SD>();
-        for (int q = 0; q < k; ++q) vr += sc_cmul(sc_cast<SD>(Vj[q + lane * KP]), wv[q]);
-        const double den = sig[lane] * sig[lane] - d;
-        cc[lane] = (lane == imin) ? sc_zero<SD>() : RealOf<SD>(-1.0 / den) * vr;
+        S vr = sc_zero<S>();
+        for (int q = 0; q < k; ++q) vr += sc_cmul(Vj[q + lane * KP], rf[q]);
+        const R sl = R(sig[lane]);
+        const R den = sl * sl - R(d);
+        cc[lane] = (lane == imin) ? sc_zero<S>() : (R(-1) / den) * vr;
       }
       __syncwarp();
-      if (lane < k)
-        for (int i = 0; i < k; ++i) x += sc_cast<SD>(Vj[lane + i * KP]) * cc[i];
+      if (lane < k) {
+        S dx = sc_zero<S>();
+        for (int i = 0; i < k; ++i) dx += Vj[lane + i * KP] * cc[i];
+        x += sc_cast<SD>(dx);
+      }
       __syncwarp();
     }
     const double xn2 = warp_sum(lane < k ? (double)sc_abs2(x) : 0.0);
@@ -234,15 +244,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
         for (int q = 0; q < k; ++q) s += Ts[r + q * LDT] * wv[q];
       vv[t] = s;
     }
-    double r2 = 0.0;
-    for (int r = lane; r < m; r += DIAF_WARP)
-      if (ix.inI[r] < 0) {
-        SD s = sc_zero<SD>();
-        for (int q = 0; q < k; ++q) s += Ts[r + q * LDT] * wv[q];
-        r2 += (double)sc_abs2(s);
-      }
-    r2 = warp_sum(r2);
-    if (sqrt(r2) <= 1e-14 * smax) flags |= DIAF_FLAG_RANK_DEFICIENT;
+    rank_thr = 1e-14 * smax;  // tested on res = ||A-hat w|| in finish_column
     __syncwarp();
   } else {
     // ---- FP32 Jacobi on Q_I (FP32 rows of Q = T R^-1 in Tw)
@@ -358,7 +360,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     __syncwarp();
   }
   DIAF_PHASE(9);
-  finish_column<SD, LDT>(a, j, k, m, l, jpos, Ts, wv, vv, ix, flags, true, lane);
+  finish_column<SD, LDT>(a, j, k, m, l, jpos, Ts, wv, vv, ix, flags, true, lane, rank_thr);
   DIAF_PHASE(10);
 }
 

@@ -314,7 +314,7 @@ __device__ void warp_col_norms(const S* G, int p, int q, double* sigma, int lane
   for (int c = lane; c < q; c += DIAF_WARP) {
     R s = R(0);
     for (int i = 0; i < p; ++i) s += sc_abs2(G[i + c * LDG]);
-    sigma[c] = sqrt((double)s);
+    sigma[c] = (double)sqrt(s);  // in the factor's own precision
   }
   __syncwarp();
 }

@@ -172,7 +172,7 @@ def learned_report(dev, keep=12, train_N=40, train_seeds=(11, 12), eval_N=64, ep
     candidates pattern(A^2) and V diagonal."""
     import torch
     from paper_1208_3573_gb300 import diaf
-    from paper_1208_3573_gb300.learned import Proposer, toggle_targets, scaled_residuals
+    from paper_1208_3573_gb300.learned import Proposer, fixed_rule, host_pattern, toggle_targets, scaled_residuals
     from workloads import patterns as pats
     from workloads.configs import lognormal
 
@@ -187,7 +187,7 @@ def learned_report(dev, keep=12, train_N=40, train_seeds=(11, 12), eval_N=64, ep
         w = wl(train_N, seed)
         CAND = pats.pattern_power(w.A, 2)
         Ad = diaf.DeviceCSC.from_host(w.A, dev)
-        T = toggle_targets(Ad, CAND, pats.neumann_pattern(w.A, 2, 0, keep), torch.from_numpy(w.budget).to(dev),
+        T = toggle_targets(Ad, CAND, host_pattern(fixed_rule(Ad, keep)), torch.from_numpy(w.budget).to(dev),
                            w.vrule, w.tie_tol)
         feats.append(diaf.propose_features(Ad, diaf.DeviceCSC.from_host(CAND, dev)))
         targs.append(T.value)
@@ -214,12 +214,13 @@ def learned_report(dev, keep=12, train_N=40, train_seeds=(11, 12), eval_N=64, ep
         return out, statistics.median(ts)
 
     J, propose_ms = events(lambda: net.propose(Ad, CAND, keep))
-    rules = {"learned": J, "fixed_sparsified_powers": diaf.DeviceCSC.from_host(pats.neumann_pattern(w.A, 2, 0, keep), dev)}
+    FR, fixed_ms = events(lambda: fixed_rule(Ad, keep))
+    rules = {"learned": J, "fixed_sparsified_powers": FR}
     out = {"workload": w.name, "V": "diagonal (l_j = 1)", "candidates": "pattern(A^2)", "keep": keep,
            "train": {"instances": f"{train_N}^3 seeds {list(train_seeds)}", "targets_s": t_targets, "train_s": t_train,
                      "rows": int(sum(np.isfinite(t).sum() for t in targs)), "loss_first": hist[0],
                      "loss_last": hist[-1]},
-           "propose_ms": propose_ms}
+           "propose_ms": propose_ms, "fixed_rule_ms": fixed_ms}
     for name, P in rules.items():
         r = {"nnz_W": P.nnz}
         for prec in ("mixed32", "fp64"):

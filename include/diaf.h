@@ -283,6 +283,26 @@ typedef struct {
 diaf_status diaf_bicgstab(diaf_solver* S, diaf_factors* F, const void* b, void* x, double tol, int32_t maxit,
                           void* stream, diaf_solve_info* info);
 
+/* ---- Sparsified powers (Sec. 4.1, Algorithm 3) --------------------------------
+ * The W pattern from the truncated Neumann series with the diagonal initial
+ * subspace V_0: S = -D^-1 (A - D) (so that A = D (I - S); the structure does
+ * not depend on the sign), per column s = t = e_j, then k times t = S t,
+ * t dropped by count p_l, s = s + t; finally s dropped by count to `keep`
+ * entries, the diagonal included.  Dropping by count keeps the p largest-
+ * modulus off-diagonal entries (ties to the lower row; p_l <= 0 and keep <= 0
+ * keep everything); the diagonal is never dropped and not counted; exact-zero
+ * sums are not stored.  Sums are formed in a fixed order (row-sorted products,
+ * separately rounded), so the pattern is reproducible.  A needs a zero-free
+ * diagonal (DIAF_EINVAL otherwise); a column whose product list exceeds 512
+ * entries gives DIAF_EUNSUPPORTED (use p_l).
+ * Two calls: diaf_sparsified_count writes colptr (device, n + 1) and the
+ * total to *nnz (host; synchronises `stream`); the caller allocates nnz rows
+ * and diaf_sparsified_fill writes the sorted rows of every column. */
+diaf_status diaf_sparsified_count(const diaf_csc* A, int32_t k, int32_t p_l, int32_t keep, int32_t* colptr,
+                                  int64_t* nnz, void* stream);
+diaf_status diaf_sparsified_fill(const diaf_csc* A, int32_t k, int32_t p_l, int32_t keep, const int32_t* colptr,
+                                 int32_t* rowidx, void* stream);
+
 /* ---- Learned proposal of the W pattern J_j ----------------------------------
  * Not in the paper: Sec. 4 chooses J_j by fixed rules (pattern(A), powers of
  * A, dropping by position).  Here a small network scores every candidate row

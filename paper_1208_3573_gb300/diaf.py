@@ -121,6 +121,10 @@ def lib() -> ctypes.CDLL:
         L.diaf_mlp_grad.argtypes = [vp, vp, vp, ctypes.c_int64, vp, vp, vp]
         L.diaf_mlp_adam.argtypes = [vp, vp, vp, vp, ctypes.c_int32, ctypes.c_float, vp]
         L.diaf_propose_select.argtypes = [ctypes.POINTER(Pattern_t), vp, ctypes.c_int32, vp, vp, vp]
+        L.diaf_sparsified_count.argtypes = [ctypes.POINTER(CSC_t), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                            vp, ctypes.POINTER(ctypes.c_int64), vp]
+        L.diaf_sparsified_fill.argtypes = [ctypes.POINTER(CSC_t), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           vp, vp, vp]
         L.diaf_status_string.argtypes = [ctypes.c_int]
         L.diaf_status_string.restype = ctypes.c_char_p
         L.diaf_last_error.restype = ctypes.c_char_p
@@ -440,3 +444,16 @@ def propose_select(CAND: DeviceCSC, score: torch.Tensor, keep: int, stream=None)
                                      _stream(stream)))
     nnz = int(colptr[-1].item())
     return DeviceCSC(CAND.n, colptr, rowidx[:nnz].clone())
+
+
+def sparsified_powers(A: DeviceCSC, k: int = 2, p_l: int = 0, keep: int = 0, stream=None) -> DeviceCSC:
+    """W pattern by sparsified powers (diaf_sparsified_count / _fill)."""
+    L = lib()
+    a = A.csc_t()
+    s = _stream(stream)
+    colptr = torch.empty(A.n + 1, dtype=torch.int32, device=A.colptr.device)
+    nnz = ctypes.c_int64()
+    _check(L.diaf_sparsified_count(ctypes.byref(a), k, p_l, keep, _ptr(colptr), ctypes.byref(nnz), s))
+    rowidx = torch.empty(max(int(nnz.value), 1), dtype=torch.int32, device=A.colptr.device)
+    _check(L.diaf_sparsified_fill(ctypes.byref(a), k, p_l, keep, _ptr(colptr), _ptr(rowidx), s))
+    return DeviceCSC(A.n, colptr, rowidx[:int(nnz.value)])

@@ -57,6 +57,18 @@ def _subpattern(CAND, mask: np.ndarray, device) -> diaf.DeviceCSC:
     return diaf.DeviceCSC(CAND.n, torch.from_numpy(colptr).to(device), torch.from_numpy(rowidx).to(device))
 
 
+def host_pattern(P: diaf.DeviceCSC):
+    """A device pattern as a host workloads.Pattern (numpy arrays)."""
+    from workloads.csc import Pattern
+    return Pattern(P.n, P.colptr.cpu().numpy().astype(np.int32), P.rowidx.cpu().numpy().astype(np.int32))
+
+
+def fixed_rule(A_dev: diaf.DeviceCSC, keep: int, k: int = 2) -> diaf.DeviceCSC:
+    """The fixed rule the proposal is compared with: sparsified powers of
+    order k (Sec. 4.1) dropped by count to `keep` entries per column."""
+    return diaf.sparsified_powers(A_dev, k, 0, keep)
+
+
 @dataclass
 class Targets:
     """Per-candidate training targets of one instance (CAND's entry order)."""

@@ -172,14 +172,14 @@ def test_trained_network_beats_fixed_rule(D, alg):
     """Candidates pattern(A^2) (25 per interior column); the learned rule and
     the fixed sparsified-powers rule both keep 12 (equal nnz(W)).  Trained on
     two 16^3 instances, evaluated on a 16^3 instance of another seed."""
-    from paper_1208_3573_gb300.learned import Proposer, toggle_targets
+    from paper_1208_3573_gb300.learned import Proposer, fixed_rule, host_pattern, toggle_targets
     keep = 12
     feats, targs = [], []
     for seed in (11, 12):
         w = _lognormal_diagV(16, seed)
         CAND = pats.pattern_power(w.A, 2)
-        base = pats.neumann_pattern(w.A, 2, 0, keep)
         Ad = D.DeviceCSC.from_host(w.A)
+        base = host_pattern(fixed_rule(Ad, keep))
         T = toggle_targets(Ad, CAND, base, torch.from_numpy(w.budget).cuda(), w.vrule, w.tie_tol, alg=alg)
         assert np.mean(T.value[T.in_base & np.isfinite(T.value)] > 0) > 0.9  # dropping a kept row costs
         feats.append(D.propose_features(Ad, D.DeviceCSC.from_host(CAND)))
@@ -191,7 +191,7 @@ def test_trained_network_beats_fixed_rule(D, alg):
     Ad = D.DeviceCSC.from_host(w.A)
     CAND = D.DeviceCSC.from_host(pats.pattern_power(w.A, 2))
     J = net.propose(Ad, CAND, keep)
-    fixed = D.DeviceCSC.from_host(pats.neumann_pattern(w.A, 2, 0, keep))
+    fixed = fixed_rule(Ad, keep)
     assert J.nnz == fixed.nnz  # equal nnz(W)
     r_l, its_l, ok_l = _quality(D, w, J, alg)
     r_f, its_f, ok_f = _quality(D, w, fixed, alg)

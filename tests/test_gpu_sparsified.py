@@ -1,0 +1,92 @@
+"""Sparsified powers (Sec. 4.1, Algorithm 3) on the GPU against the oracle.
+
+Real operators: the sums are formed in the same order with separately
+rounded operations on both sides, so the patterns must agree exactly.
+Complex operators: 1/d and the complex products may round differently, so a
+column may differ only where the dropping cut falls between entries whose
+moduli agree to 1e-12; every other entry must agree and the kept set must be
+a valid choice."""
+import numpy as np
+import pytest
+
+from oracle.sparsified import sparsified_powers as oracle_sp
+from workloads import make_workload, operators as ops, patterns as pats
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def D():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1208_3573_gb300 import build, diaf
+    build.build()
+    return diaf
+
+
+def _host(P):
+    return P.colptr.cpu().numpy(), P.rowidx.cpu().numpy()
+
+
+@pytest.mark.parametrize("k,p_l,keep", [(1, 0, 0), (2, 0, 0), (2, 0, 12), (3, 4, 0), (3, 3, 10), (2, 0, 1)])
+@pytest.mark.parametrize("name", ["lognormal8", "convdiff24", "powerlaw"])
+def test_sparsified_matches_oracle_real(D, name, k, p_l, keep):
+    if name == "lognormal8":
+        A = ops.lognormal3d(8, seed=4)
+    elif name == "convdiff24":
+        A = ops.convdiff2d(24)
+    else:
+        A = ops.powerlaw_random(400, 3)
+        if k >= 2 and p_l == 0:
+            pytest.skip("columns of up to 60 entries: products beyond the list capacity without dropping")
+    P = D.sparsified_powers(D.DeviceCSC.from_host(A), k, p_l, keep)
+    o = oracle_sp(A, k, p_l, keep)
+    cp, ri = _host(P)
+    np.testing.assert_array_equal(cp, o.colptr)
+    np.testing.assert_array_equal(ri, o.rowidx)
+
+
+def test_sparsified_complex_valid(D):
+    A = ops.helmholtz2d(16, ops.helmholtz_wavenumber(16))
+    keep = 7
+    P = D.sparsified_powers(D.DeviceCSC.from_host(A), 2, 0, keep)
+    cp, ri = _host(P)
+    full = oracle_sp(A, 2, 0, 0)
+    o = oracle_sp(A, 2, 0, keep)
+    np.testing.assert_array_equal(np.diff(cp), np.diff(o.colptr))  # same counts
+    # candidate magnitudes from the oracle's undropped s_j, to judge near-ties at the cut
+    import scipy.sparse as sp
+    M = A.to_scipy()
+    d = M.diagonal()
+    S = (-(sp.diags(1.0 / d) @ (M - sp.diags(d)))).tocsc()
+    Wv = (sp.identity(A.n, dtype=complex) + S + S @ S).tocsc()
+    bad = 0
+    for j in range(A.n):
+        g = set(ri[cp[j]:cp[j + 1]])
+        e = set(o.rowidx[o.colptr[j]:o.colptr[j + 1]])
+        if g == e:
+            continue
+        col = Wv[:, j].toarray().ravel()
+        mags = {r: abs(col[r]) for r in set(full.col(j))}
+        cut = min(mags[r] for r in e if r != j)
+        for r in g ^ e:
+            assert abs(mags[r] - cut) <= 1e-12 * max(cut, 1e-300), (j, r, mags[r], cut)
+        bad += 1
+    assert bad <= A.n // 20
+
+
+def test_sparsified_rejects_zero_diagonal_and_overflow(D):
+    A = ops.powerlaw_random(300, 1)
+    Ad = D.DeviceCSC.from_host(A)
+    with pytest.raises(D.DiafError) as e:
+        D.sparsified_powers(Ad, 4, 0, 0)  # dense fill: product lists beyond the capacity
+    assert e.value.status == D.DIAF_EUNSUPPORTED
+    vals = A.vals.copy()
+    col0 = A.rowidx[A.colptr[0]:A.colptr[1]]
+    vals[A.colptr[0] + int(np.nonzero(col0 == 0)[0][0])] = 0.0
+    Az = D.DeviceCSC(A.n, torch.from_numpy(A.colptr).cuda(), torch.from_numpy(A.rowidx).cuda(),
+                     torch.from_numpy(vals).cuda())
+    with pytest.raises(D.DiafError) as e:
+        D.sparsified_powers(Az, 2, 0, 0)
+    assert e.value.status == D.DIAF_EINVAL

@@ -1,5 +1,5 @@
-"""Pins of the learned-proposal oracle and of the fixed W rule it is compared
-with (CPU only).
+"""Pins of the learned-proposal oracle and of the sparsified-powers W rule it
+is compared with (CPU only).
 
 The proposal network is not in the paper; its oracle is pinned against
 hand-worked features, finite differences, Adam's closed-form first steps and
@@ -13,6 +13,7 @@ import pytest
 import scipy.sparse as sp
 
 from oracle import learned as L
+from oracle.sparsified import sparsified_powers
 from workloads.csc import CSC, Pattern
 from workloads import patterns as pats
 
@@ -139,22 +140,38 @@ def test_neumann_pattern_1d_expansion():
     # S^2 e_j = 0.0625 e_{j-2} + 0.375 e_j + 0.5625 e_{j+2};
     # s_j = 1.375 e_j + 0.25 e_{j-1} + 0.75 e_{j+1} + 0.0625 e_{j-2} + 0.5625 e_{j+2}
     A = _csc(_tridiag(9, -1.5, np.full(9, 2.0), -0.5))
-    full = pats.neumann_pattern(A, k=2)
+    full = sparsified_powers(A, k=2)
     np.testing.assert_array_equal(full.colptr, pats.pattern_power(A, 2).colptr)
     np.testing.assert_array_equal(full.rowidx, pats.pattern_power(A, 2).rowidx)
     j = 4
-    P3 = pats.neumann_pattern(A, k=2, keep=3)
+    P3 = sparsified_powers(A, k=2, keep=3)
     assert list(P3.col(j)) == [4, 5, 6]
-    P4 = pats.neumann_pattern(A, k=2, keep=4)
+    P4 = sparsified_powers(A, k=2, keep=4)
     assert list(P4.col(j)) == [3, 4, 5, 6]
     # dropping by count inside the expansion: t_1 keeps only e_{j+1}, so
     # t_2 = S e_{j+1} = 0.25 e_j + 0.75 e_{j+2}; e_{j-1}, e_{j-2} never appear
-    Pd = pats.neumann_pattern(A, k=2, p_l=1)
+    Pd = sparsified_powers(A, k=2, p_l=1)
     assert list(Pd.col(j)) == [4, 5, 6]
 
 
 def test_neumann_pattern_keeps_diagonal():
     A = _csc(_tridiag(6, -3.0, np.full(6, 0.1), -3.0))  # tiny diagonal: off-diagonal terms dominate
-    P = pats.neumann_pattern(A, k=2, keep=1)
+    P = sparsified_powers(A, k=2, keep=1)
     for j in range(6):
         assert list(P.col(j)) == [j]
+
+
+def test_sparsified_powers_matches_dense_series():
+    # without dropping, the structure is that of I + S + S^2 (dense, no cancellation on random values)
+    g = np.random.default_rng(21)
+    M = sp.random(30, 30, density=0.08, random_state=21, format="csc")
+    M.data = g.normal(size=M.data.size)
+    M = (M + sp.identity(30) * 3.0).tocsc()
+    A = _csc(M)
+    P = sparsified_powers(A, k=2)
+    D = np.diag(M.diagonal())
+    S = -np.linalg.solve(D, M.toarray() - D)
+    Wd = np.eye(30) + S + S @ S
+    for j in range(30):
+        want = np.nonzero(np.abs(Wd[:, j]) > 1e-14)[0]
+        assert list(P.col(j)) == list(want)

@@ -64,51 +64,3 @@ def gauss_seidel_upper(A: CSC | Pattern) -> Pattern:
     M.sort_indices()
     return Pattern(A.n, M.indptr.astype(np.int32), M.indices.astype(np.int32))
 
-
-def _keep_top(M: sp.csc_matrix, count: int) -> sp.csc_matrix:
-    """Numerical dropping by count (Sec. 4.1): per column the `count` entries
-    of largest magnitude survive, ties to the lower row; the diagonal is not
-    subject to dropping and does not use up the count.  count < 0 keeps all."""
-    M = sp.csc_matrix(M)
-    M.sort_indices()
-    if count < 0:
-        return M
-    n = M.shape[0]
-    col = np.repeat(np.arange(n), np.diff(M.indptr))
-    diag = M.indices == col
-    order = np.lexsort((M.indices, -np.abs(M.data), col))  # by column, |value| desc, row
-    rank = np.empty(order.size, dtype=np.int64)
-    starts = M.indptr[:-1]
-    # rank among the off-diagonal entries of its column
-    od = ~diag[order]
-    csum = np.cumsum(od)
-    first = np.concatenate([[0], csum])[starts[col[order]]]
-    rank[order] = csum - first - 1
-    keep = diag | (rank < count)
-    K = sp.csc_matrix((M.data[keep], M.indices[keep], np.concatenate([[0], np.cumsum(
-        np.bincount(col[keep], minlength=n))])), shape=M.shape)
-    K.sort_indices()
-    return K
-
-
-def neumann_pattern(A: CSC, k: int = 2, p_l: int = 0, keep: int = 0) -> Pattern:
-    """W structure by sparsified powers (Algorithm 3 of Sec. 4.1) with the
-    diagonal initial subspace V_0 = diag(A): S = -D^{-1}(A - D), so that
-    A = D (I - S) and A^{-1} D = I + S + S^2 + ...; per column s_j = e_j +
-    t_1 + ... + t_k with t_l = S t_{l-1} (t_0 = e_j) dropped by count p_l.
-    `keep` > 0 then drops s_j itself by count to `keep` entries, the diagonal
-    included (the fixed rule at a given nnz(W) per column)."""
-    M = A.to_scipy()
-    d = M.diagonal()
-    if np.any(d == 0):
-        raise ValueError("sparsified powers with V_0 = diag(A) need a zero-free diagonal")
-    Dinv = sp.diags(1.0 / d)
-    S = (-(Dinv @ (M - sp.diags(d)))).tocsc()
-    t = sp.identity(A.n, dtype=M.dtype, format="csc")
-    s = t.copy()
-    for _ in range(k):
-        t = _keep_top(S @ t, p_l if p_l > 0 else -1)
-        s = (s + t).tocsc()
-    s = _keep_top(s, keep - 1 if keep > 0 else -1)
-    s.sort_indices()
-    return Pattern(A.n, s.indptr.astype(np.int32), s.indices.astype(np.int32))

@@ -446,7 +446,10 @@ def main():
             resm = Fm.res.cpu().numpy()
             fb = Fm.fallbacks()
             Fm.close()
-            rel = np.abs(resm - res64) / np.maximum(np.abs(res64), 1e-300)
+            # relative difference where the residual is above the rounding floor of the column
+            # (1e-10 of max |a_ij|: below it both are zero to the rounding of w)
+            floor = 1e-10 * float(np.abs(w.A.vals).max())
+            rel = np.abs(resm - res64) / np.maximum(np.abs(res64), floor)
             c64 = w.n / (statistics.median(tt) / 1e3)
             extras["fp64_plain"] = {"factor_columns_per_s": c64, "factor_ms": statistics.median(tt),
                                     "speedup_of_mixed": (w.n / (float(np.mean(total_ms)) / 1e3)) / c64,

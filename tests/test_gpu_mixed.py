@@ -79,3 +79,18 @@ def test_mixed_bicgstab_matches_fp64(D):
         assert info.converged
         its[prec] = info.iterations
     assert abs(its["fp64"] - its["mixed32"]) <= 1
+
+
+@pytest.mark.parametrize("alg", ["S", "Q"])
+def test_mixed_parity_full_size_convdiff256(D, alg):
+    """The benchmark's workload (65,536 columns) in mixed precision, every column."""
+    w = make_workload("convdiff256_A2")
+    F = run_gpu(D, w.A, w.PW, w.vrule, w.budget, alg=alg, prec="mixed32", tie_tol=w.tie_tol)
+    g = host_factors(F)
+    o = O.factor(w.A, w.PW, w.vrule, w.budget, alg=alg, tie_tol=w.tie_tol)
+    rep = compare(g, o, w.A, w.PW, alg, rtol_res=RTOL_RES, vec_tol=VEC_TOL, mixed=True, floor_rel=1e-10)
+    assert_parity(rep)
+    # the largest residual difference, over columns whose residual is above the rounding floor
+    resg, reso = g["res"], o.res
+    big = reso > 1e-10 * np.abs(w.A.vals).max()
+    print(alg, "max rel res diff", float(np.max(np.abs(resg[big] - reso[big]) / reso[big])), "cols", int(big.sum()))

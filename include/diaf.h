@@ -210,8 +210,9 @@ void diaf_plan_free(diaf_plan* P);
 diaf_status diaf_factor_timings(const diaf_factors* F, float* ms, int32_t nms);
 
 /* Mixed precision: the number of columns per size bucket that the FP64 path
- * computed (flag DIAF_FLAG_FP64_FALLBACK; every column of the large-tile
- * bucket); zeros for the FP64 form.  Waits for F's stream.  nb >= n_buckets. */
+ * computed (flag DIAF_FLAG_FP64_FALLBACK; in the large-tile bucket every
+ * column for complex A or DIAF-Q, the handed-back ones for real DIAF-S);
+ * zeros for the FP64 form.  Waits for F's stream.  nb >= n_buckets. */
 diaf_status diaf_factor_fallbacks(const diaf_factors* F, int32_t* counts, int32_t nb);
 
 /* Number of CUDA kernels this library has launched in this process. */

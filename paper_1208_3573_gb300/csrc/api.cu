@@ -115,7 +115,7 @@ diaf_status diaf_factor_fallbacks(const diaf_factors* F, int32_t* counts, int32_
   if (!F->fb_counts) return DIAF_OK;
   DIAF_CU(cudaMemcpyAsync(counts, F->fb_counts, sizeof(int32_t) * kNumBuckets, cudaMemcpyDeviceToHost, F->stream));
   DIAF_CU(cudaStreamSynchronize(F->stream));
-  counts[kNumBuckets - 1] = F->info.bucket_cols[kNumBuckets - 1];  // large tiles always take the FP64 path
+
   return DIAF_OK;
 }
 
@@ -358,8 +358,27 @@ diaf_status enqueue_numeric(diaf_factors* F, NumericPlan& np, cudaStream_t s, bo
     if (events) DIAF_CU(cudaEventRecord(F->ev[3 + 2 * b], s));
     cudaError_t e;
     if (b == kNumBuckets - 1) {
-      ca.extra_flags = np.mixed ? DIAF_FLAG_FP64_FALLBACK : 0;
-      e = launch_columns_cta(np.dtype, np.alg, ca, np.cs, np.cta_grid, s);
+      e = cudaErrorNotSupported;
+      if (np.mixed) {
+        ca.fb_list = np.fb_list + (size_t)b * n;
+        ca.fb_count = np.fb_count + b;
+        e = launch_columns_cta_mixed(np.dtype, np.alg, ca, np.cs, np.cta_grid, s);
+        if (e == cudaSuccess) {  // the FP64 kernel finishes the handed-back columns
+          ColArgs cf = ca;
+          cf.list = ca.fb_list;
+          cf.list_count = ca.fb_count;
+          cf.work_counter = np.work + kNumBuckets + b;
+          cf.extra_flags = DIAF_FLAG_FP64_FALLBACK;
+          e = launch_columns_cta(np.dtype, np.alg, cf, np.cs, np.cta_grid, s);
+        }
+      }
+      if (e == cudaErrorNotSupported) {  // every large column on the FP64 kernel
+        (void)cudaGetLastError();
+        ca.extra_flags = np.mixed ? DIAF_FLAG_FP64_FALLBACK : 0;
+        if (np.mixed) DIAF_CU(cudaMemcpyAsync(np.fb_count + b, np.bucket_count + b, sizeof(int32_t),
+                                              cudaMemcpyDeviceToDevice, s));
+        e = launch_columns_cta(np.dtype, np.alg, ca, np.cs, np.cta_grid, s);
+      }
     } else if (np.mixed) {
       ca.fb_list = np.fb_list + (size_t)b * n;
       ca.fb_count = np.fb_count + b;

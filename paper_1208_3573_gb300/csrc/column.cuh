@@ -16,6 +16,10 @@
 
 #include "warp_la.cuh"
 
+// Column-scaled conditioning estimate of an upper R whose columns came from a
+// tile with column norms cn: max_c cn_c / |R_cc| (1 for orthogonal columns).
+constexpr float kMixedKappaMax = 300.0f;
+
 struct ColArgs {
   int n;
   const int32_t* Acp;

@@ -1,4 +1,6 @@
-// Size bucket 2: one CTA per column for large tiles (FP64 and complex128).
+// Size bucket 2: one CTA per column for large tiles (FP64 and complex128;
+// mixed precision for real DIAF-S).
+#include "column_cta_mixed.cuh"
 #include "launch.cuh"
 
 namespace {
@@ -54,4 +56,21 @@ cudaError_t launch_columns_cta(int dtype, int alg, const ColArgs& a, const CtaSc
   if (dtype == DIAF_C128)
     return alg == DIAF_ALG_S ? launch<Cx<double>, DIAF_ALG_S>(a, sc, grid, s) : launch<Cx<double>, DIAF_ALG_Q>(a, sc, grid, s);
   return alg == DIAF_ALG_S ? launch<double, DIAF_ALG_S>(a, sc, grid, s) : launch<double, DIAF_ALG_Q>(a, sc, grid, s);
+}
+
+cudaError_t launch_columns_cta_mixed(int dtype, int alg, const ColArgs& a, const CtaScratch& sc, int grid,
+                                     cudaStream_t s) {
+  if (dtype != DIAF_F64 || alg != DIAF_ALG_S) return cudaErrorNotSupported;
+  if (grid <= 0) return cudaSuccess;
+  const size_t smem = CtaMixedSmem::bytes(sc.ldm);
+  if (smem > 227 * 1024) return cudaErrorNotSupported;
+  static int configured_for = -1;
+  if (configured_for < (int)smem) {
+    cudaError_t e = cudaFuncSetAttribute(column_cta_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured_for = (int)smem;
+  }
+  column_cta_mixed_kernel<<<grid, kCtaThreads, smem, s>>>(a, sc);
+  DIAF_COUNT_LAUNCH();
+  return cudaGetLastError();
 }

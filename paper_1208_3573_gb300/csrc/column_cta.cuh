@@ -186,6 +186,69 @@ struct CtaSmem {
   }
 };
 
+// Phase (v_jj real >= 0), residual ||A w_j - v_j|| from its definition (in
+// the tile's precision), NaN/Inf check and scatter of column j -- the end of
+// every CTA column kernel.  rank_thr: a residual at or below it marks the
+// column RANK_DEFICIENT (DIAF-S, where res = ||A-hat w|| = sigma_min).
+template <class S>
+__device__ void cta_finish(const ColArgs& a, int j, int k, int m, int l, int jpos, const S* Ts, int ld, S* wv, S* vv,
+                           const int32_t* Is, const int32_t* Iloc, const int32_t* inI, uint32_t flags, bool do_phase,
+                           RealOf<S>* redR, double rank_thr = -1.0) {
+  using R = RealOf<S>;
+  const int tid = threadIdx.x;
+  if (do_phase) {
+    S ph = sc_real_s<S>(R(1));
+    R vjj = jpos >= 0 ? sc_abs(vv[jpos]) : R(0);
+    R vn2 = R(0);
+    for (int t = 0; t < l; ++t) vn2 += sc_abs2(vv[t]);
+    if (jpos >= 0 && vjj > R(64) * eps_of<R>() * sqrt(vn2)) {
+      ph = (R(1) / vjj) * sc_conj(vv[jpos]);
+    } else {
+      flags |= DIAF_FLAG_VJJ_ZERO;
+      R amx = R(0);
+      int imx = -1;
+      for (int q = 0; q < k; ++q) {
+        R aq = sc_abs(wv[q]);
+        if (aq > amx) { amx = aq; imx = q; }
+      }
+      if (imx >= 0) ph = (R(1) / amx) * sc_conj(wv[imx]);
+    }
+    __syncthreads();
+    for (int q = tid; q < k; q += kCtaThreads) wv[q] = ph * wv[q];
+    for (int t = tid; t < l; t += kCtaThreads) vv[t] = ph * vv[t];
+    __syncthreads();
+  }
+  R r2 = R(0);
+  for (int r = tid; r < m; r += kCtaThreads) {
+    S s2 = sc_zero<S>();
+    for (int q = 0; q < k; ++q) s2 += Ts[r + (size_t)q * ld] * wv[q];
+    if (inI[r] >= 0) s2 -= vv[inI[r]];
+    r2 += sc_abs2(s2);
+  }
+  for (int t = tid; t < l; t += kCtaThreads)
+    if (Iloc[t] < 0) r2 += sc_abs2(vv[t]);
+  r2 = block_sum(r2, redR);
+  const double resj = sqrt((double)r2);
+  if (resj <= rank_thr) flags |= DIAF_FLAG_RANK_DEFICIENT;
+  int bad = !isfinite(resj);
+  for (int q = tid; q < k; q += kCtaThreads) bad |= !(isfinite(sc_real(wv[q])) && isfinite(sc_imag(wv[q])));
+  for (int t = tid; t < l; t += kCtaThreads) bad |= !(isfinite(sc_real(vv[t])) && isfinite(sc_imag(vv[t])));
+  if (__syncthreads_or(bad)) flags |= DIAF_FLAG_NONFINITE;
+  S* Wout = reinterpret_cast<S*>(a.Wv) + a.Wcp[j];
+  for (int q = tid; q < k; q += kCtaThreads) Wout[q] = wv[q];
+  const int v0 = a.Vcp[j];
+  S* Vout = reinterpret_cast<S*>(a.Vv) + v0;
+  for (int t = tid; t < l; t += kCtaThreads) {
+    a.Vri[v0 + t] = Is[t];
+    Vout[t] = vv[t];
+  }
+  if (tid == 0) {
+    a.res[j] = resj;
+    a.flags[j] = flags | a.extra_flags;
+  }
+  __syncthreads();
+}
+
 template <class S, int ALG>
 __device__ void solve_column_cta(const ColArgs& a, const CtaScratch& sc, int j, unsigned char* smem) {
   using R = RealOf<S>;
@@ -489,57 +552,7 @@ __device__ void solve_column_cta(const ColArgs& a, const CtaScratch& sc, int j, 
     __syncthreads();
   }
 
-  // ---- phase, residual, scatter
-  if (k > 0 || ALG == DIAF_ALG_Q) {
-    S ph = sc_real_s<S>(R(1));
-    R vjj = jpos >= 0 ? sc_abs(vv[jpos]) : R(0);
-    R vn2 = R(0);
-    for (int t = 0; t < l; ++t) vn2 += sc_abs2(vv[t]);
-    if (jpos >= 0 && vjj > R(64) * eps_of<R>() * sqrt(vn2)) {
-      ph = (R(1) / vjj) * sc_conj(vv[jpos]);
-    } else {
-      flags |= DIAF_FLAG_VJJ_ZERO;
-      R amx = R(0);
-      int imx = -1;
-      for (int q = 0; q < k; ++q) {
-        R aq = sc_abs(wv[q]);
-        if (aq > amx) { amx = aq; imx = q; }
-      }
-      if (imx >= 0) ph = (R(1) / amx) * sc_conj(wv[imx]);
-    }
-    __syncthreads();
-    for (int q = tid; q < k; q += kCtaThreads) wv[q] = ph * wv[q];
-    for (int t = tid; t < l; t += kCtaThreads) vv[t] = ph * vv[t];
-    __syncthreads();
-  }
-  R r2 = R(0);
-  for (int r = tid; r < m; r += kCtaThreads) {
-    S s2 = sc_zero<S>();
-    for (int q = 0; q < k; ++q) s2 += Ts[r + (size_t)q * ld] * wv[q];
-    if (inI[r] >= 0) s2 -= vv[inI[r]];
-    r2 += sc_abs2(s2);
-  }
-  for (int t = tid; t < l; t += kCtaThreads)
-    if (Iloc[t] < 0) r2 += sc_abs2(vv[t]);
-  r2 = block_sum(r2, redR);
-  const double resj = sqrt((double)r2);
-  int bad = !isfinite(resj);
-  for (int q = tid; q < k; q += kCtaThreads) bad |= !(isfinite(sc_real(wv[q])) && isfinite(sc_imag(wv[q])));
-  for (int t = tid; t < l; t += kCtaThreads) bad |= !(isfinite(sc_real(vv[t])) && isfinite(sc_imag(vv[t])));
-  if (__syncthreads_or(bad)) flags |= DIAF_FLAG_NONFINITE;
-  S* Wout = reinterpret_cast<S*>(a.Wv) + a.Wcp[j];
-  for (int q = tid; q < k; q += kCtaThreads) Wout[q] = wv[q];
-  const int v0 = a.Vcp[j];
-  S* Vout = reinterpret_cast<S*>(a.Vv) + v0;
-  for (int t = tid; t < l; t += kCtaThreads) {
-    a.Vri[v0 + t] = Is[t];
-    Vout[t] = vv[t];
-  }
-  if (tid == 0) {
-    a.res[j] = resj;
-    a.flags[j] = flags | a.extra_flags;
-  }
-  __syncthreads();
+  cta_finish<S>(a, j, k, m, l, jpos, Ts, ld, wv, vv, Is, Iloc, inI, flags, k > 0 || ALG == DIAF_ALG_Q, redR);
 }
 
 template <class S, int ALG>

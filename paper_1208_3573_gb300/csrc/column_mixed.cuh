@@ -32,9 +32,6 @@ template <class S> struct DoubleOf;
 template <> struct DoubleOf<float> { using T = double; };
 template <> struct DoubleOf<Cx<float>> { using T = Cx<double>; };
 
-// Column-scaled conditioning estimate of an upper R whose columns came from a
-// tile with column norms cn: max_c cn_c / |R_cc| (1 for orthogonal columns).
-constexpr float kMixedKappaMax = 300.0f;
 constexpr int kRRMax = 8;  // DIAF-Q: largest l_j refined through the explicit l x l matrix C
 
 template <class S, int KMAX, int MMAX, int ALG>

@@ -19,6 +19,10 @@ cudaError_t launch_columns_mixed_c64(int bucket, int alg, const ColArgs& a, int 
 // scratch slabs (0 on error) and the launch itself.
 int cta_columns_grid(int dtype, int alg, int ldm, int count);
 cudaError_t launch_columns_cta(int dtype, int alg, const ColArgs& a, const CtaScratch& sc, int grid, cudaStream_t s);
+// mixed precision for bucket 2 (real DIAF-S; cudaErrorNotSupported otherwise):
+// hands columns back through a.fb_list / a.fb_count
+cudaError_t launch_columns_cta_mixed(int dtype, int alg, const ColArgs& a, const CtaScratch& sc, int grid,
+                                     cudaStream_t s);
 
 // Persistent grid sized by occupancy; `per_warp` bytes of shared memory per warp.
 template <class Kern>

@@ -94,3 +94,24 @@ def test_mixed_parity_full_size_convdiff256(D, alg):
     resg, reso = g["res"], o.res
     big = reso > 1e-10 * np.abs(w.A.vals).max()
     print(alg, "max rel res diff", float(np.max(np.abs(resg[big] - reso[big]) / reso[big])), "cols", int(big.sum()))
+
+
+def test_mixed_parity_full_size_powerlaw_sampled(D):
+    """n = 200,000, all three buckets in mixed precision (the large tiles in the
+    mixed CTA kernel): every column of the largest bucket up to 1,500 plus a
+    seeded sample of the others."""
+    w = make_workload("powerlaw200k")
+    F = run_gpu(D, w.A, w.PW, w.vrule, w.budget, alg="S", prec="mixed32", tie_tol=w.tie_tol)
+    g = host_factors(F)
+    k = w.PW.counts()
+    nnz = np.diff(w.A.colptr)
+    E = np.bincount(np.repeat(np.arange(w.n), k), weights=nnz[w.PW.rowidx], minlength=w.n)
+    big = np.nonzero((k > 32) | (E > 200))[0]
+    rng = np.random.default_rng(5)
+    cols = np.unique(np.concatenate([big[:1500], rng.choice(w.n, 1500, replace=False)])).astype(np.int32)
+    o = O.factor(w.A, w.PW, w.vrule, w.budget, alg="S", tie_tol=w.tie_tol, cols=cols)
+    rep = compare(g, o, w.A, w.PW, "S", rtol_res=RTOL_RES, vec_tol=VEC_TOL, mixed=True, floor_rel=1e-10, cols=cols)
+    assert_parity(rep)
+    fb = F.fallbacks()
+    assert fb[2] < F.info.bucket_cols[2]  # the mixed CTA kernel finished part of the large bucket
+    print("fallbacks per bucket", fb, "of", list(F.info.bucket_cols))

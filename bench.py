@@ -404,8 +404,11 @@ def main():
         peak, src, kname = FP64_NOMINAL_TFLOPS * 1e12, "FP64 nominal 1.25 TFLOP/s", "column_warp_kernel"
     else:
         peak, src, kname = FP32_TFLOPS * 1e12, "FP32 152 SMs x 128 lanes x 2 flop x 2.07 GHz", "column_mixed_kernel"
+    # DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu
+    # capture of the current kernel on this workload; None where none was taken
+    traffic = 24363264 if (w.name == "convdiff2d_256x256_Wp2" and args.prec == "mixed32" and args.alg == "S") else None
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None, "kernel": f"{kname} (numeric pass, all buckets)",
+            "frac": achieved / peak, "traffic": traffic, "kernel": f"{kname} (numeric pass, all buckets)",
             "kernel_ms": kern, "algorithmic_flops": flops, "peak_source": src}
 
     extras = {}

@@ -65,7 +65,7 @@ enum { DIAF_PREC_FP64 = 0, DIAF_PREC_MIXED32 = 1 };
  * h_i = ||Q_j(i,:)||^2 (the columns of Q_j^* of largest norm).  Admissible
  * rows: i < j (UPPER, V upper triangular as in the Gauss-Seidel structure of
  * Sec. 4.2), i > j (LOWER), any i != j (ALL); always rows of the tile. */
-enum { DIAF_RULE_FIXED = 0, DIAF_RULE_UPPER = 1, DIAF_RULE_LOWER = 2, DIAF_RULE_ALL = 3 };
+enum { DIAF_RULE_FIXED = 0, DIAF_RULE_UPPER = 1, DIAF_RULE_LOWER = 2, DIAF_RULE_ALL = 3, DIAF_RULE_BLOCK = 4 };
 
 /* Per-column flag bits (col_flags). */
 enum {
@@ -116,6 +116,13 @@ typedef struct {
    * the plain method. */
   double stab_tol;
   double stab_r;
+  /* DIAF_RULE_BLOCK (block-diagonal V, Sec. 5's experiments): device int32[n],
+   * the block of every row, non-decreasing in row order (so every block is a
+   * contiguous range of rows); the admissible rows of column j are the other
+   * rows of j's block.  diaf_apply then factors each diagonal block of V by
+   * dense LU with partial pivoting (blocks of at most 64 rows; larger ones make
+   * diaf_apply return DIAF_EUNSUPPORTED).  Copied at factorisation. */
+  const int32_t* blocks;
 } diaf_vspec;
 
 typedef struct diaf_factors diaf_factors; /* opaque, library-owned */
@@ -255,6 +262,7 @@ diaf_status diaf_apply(diaf_factors* F, const void* x, void* y, void* stream);
  * contents in it, so calls that overlap on the GPU (different streams, or
  * several host threads) race; serialise them.  x, y as for diaf_apply. */
 diaf_status diaf_apply_static(diaf_factors* F, const void* x, void* y, void* stream);
+/* (Triangular V only: factors of DIAF_RULE_BLOCK give DIAF_EUNSUPPORTED.) */
 
 /* Waits for `stream` and reports device-side errors recorded by earlier
  * calls on F (bounded-wait timeouts, capacity overflows) as a status. */

@@ -56,7 +56,7 @@
 
 typedef double complex zd;
 
-enum { RULE_FIXED = 0, RULE_UPPER = 1, RULE_LOWER = 2, RULE_ALL = 3 };
+enum { RULE_FIXED = 0, RULE_UPPER = 1, RULE_LOWER = 2, RULE_ALL = 3, RULE_BLOCK = 4 };
 enum { ALG_Q = 1, ALG_S = 2 };
 enum {
     F_RANK_DEFICIENT = 1u, F_DEGENERATE = 2u, F_VJJ_ZERO = 4u,
@@ -216,16 +216,20 @@ static rowset row_union(const int *Acp, const int *Ari, const int *Jr, int k) {
     return rs;
 }
 
-static int admissible(int rule, int i, int j) {
+/* Admissible rows of column j: upper (i < j) or lower (i > j) triangular V
+ * (the Gauss-Seidel structures of Sec. 4.2), any row, or the rows of j's
+ * diagonal block (block-diagonal V, the structure of Sec. 5's experiments). */
+static int admissible(int rule, int i, int j, const int *blk) {
     if (i == j) return 0; /* the diagonal is always in I_j, never a candidate */
     if (rule == RULE_UPPER) return i < j;
     if (rule == RULE_LOWER) return i > j;
+    if (rule == RULE_BLOCK) return blk[i] == blk[j];
     return 1;
 }
 
-static int n_candidates(const rowset *rs, int rule, int j) {
+static int n_candidates(const rowset *rs, int rule, int j, const int *blk) {
     int c = 0;
-    for (int i = 0; i < rs->m; ++i) c += admissible(rule, rs->rows[i], j);
+    for (int i = 0; i < rs->m; ++i) c += admissible(rule, rs->rows[i], j, blk);
     return c;
 }
 
@@ -242,18 +246,18 @@ static int extra_count(int ncand, const int *budget, int j) {
  * candidate's key (other than the current maximum itself) to a pick
  * threshold: how close a decision came to flipping under rounding. */
 static void select_rows(const rowset *rs, const double *h, int rule, int j, int s,
-                        double tie_tol, int *picked, double *margin) {
+                        double tie_tol, int *picked, double *margin, const int *blk) {
     int m = rs->m;
     char *used = (char *)calloc(m > 0 ? m : 1, 1);
     double mg = INFINITY;
     for (int t = 0; t < s; ++t) {
         double hmax = -INFINITY;
         for (int i = 0; i < m; ++i)
-            if (!used[i] && admissible(rule, rs->rows[i], j) && h[i] > hmax) hmax = h[i];
+            if (!used[i] && admissible(rule, rs->rows[i], j, blk) && h[i] > hmax) hmax = h[i];
         double thr = hmax - tie_tol;
         int best = -1;
         for (int i = 0; i < m; ++i) {
-            if (used[i] || !admissible(rule, rs->rows[i], j)) continue;
+            if (used[i] || !admissible(rule, rs->rows[i], j, blk)) continue;
             double d = fabs(h[i] - thr);
             if (h[i] != hmax && d < mg) mg = d;
             if (best < 0 && h[i] >= thr) best = i;
@@ -274,6 +278,7 @@ typedef struct {
     const int *Wcp, *Wri;
     int rule;
     const int *Vcp, *Vri, *budget;
+    const int *blk;           /* RULE_BLOCK: block of every row */
     int alg;
     double tie_tol;
     double stab_tol, stab_r;  /* stabilised DIAF-Q: trigger |v_jj| < stab_tol (0: off), imposed v_jj = r */
@@ -292,7 +297,7 @@ static int count_l(const problem *P, int j) {
     const int *Jr = P->Wri + P->Wcp[j];
     int k = P->Wcp[j + 1] - P->Wcp[j];
     rowset rs = row_union(P->Acp, P->Ari, Jr, k);
-    int s = extra_count(n_candidates(&rs, P->rule, j), P->budget, j);
+    int s = extra_count(n_candidates(&rs, P->rule, j, P->blk), P->budget, j);
     free(rs.rows);
     return 1 + s;
 }
@@ -333,10 +338,10 @@ static void solve_column(const problem *P, int j, colout *out, double *h_dbg, in
         l = P->Vcp[j + 1] - P->Vcp[j];
         memcpy(out->Irows, P->Vri + P->Vcp[j], sizeof(int) * l);
     } else {
-        int s = extra_count(n_candidates(&rs, P->rule, j), P->budget, j);
+        int s = extra_count(n_candidates(&rs, P->rule, j, P->blk), P->budget, j);
         l = 1 + s;
         out->Irows[0] = j;
-        select_rows(&rs, h, P->rule, j, s, P->tie_tol, out->Irows + 1, &out->margin);
+        select_rows(&rs, h, P->rule, j, s, P->tie_tol, out->Irows + 1, &out->margin, P->blk);
         qsort(out->Irows, l, sizeof(int), cmp_int);
     }
     int *Iloc = (int *)malloc(sizeof(int) * (l + 1));
@@ -508,17 +513,17 @@ static void solve_column(const problem *P, int j, colout *out, double *h_dbg, in
 /* ------------------------------------------------------------ ABI ---- */
 static problem make_problem(int n, const int *Acp, const int *Ari, const double *Av,
                             const int *Wcp, const int *Wri, int rule, const int *Vcp,
-                            const int *Vri, const int *budget, int alg, double tie_tol,
+                            const int *Vri, const int *budget, const int *blk, int alg, double tie_tol,
                             double stab_tol, double stab_r) {
-    problem P = {n, Acp, Ari, (const zd *)Av, Wcp, Wri, rule, Vcp, Vri, budget, alg, tie_tol, stab_tol, stab_r};
+    problem P = {n, Acp, Ari, (const zd *)Av, Wcp, Wri, rule, Vcp, Vri, budget, blk, alg, tie_tol, stab_tol, stab_r};
     return P;
 }
 
 /* l_j for each listed column (cols == NULL: all n columns). */
 int diaf_oracle_vcount(int n, const int *Acp, const int *Ari, const int *Wcp, const int *Wri,
-                       int rule, const int *Vcp, const int *Vri, const int *budget,
+                       int rule, const int *Vcp, const int *Vri, const int *budget, const int *blk,
                        int ncols, const int *cols, int *lcount, int nthreads) {
-    problem P = make_problem(n, Acp, Ari, NULL, Wcp, Wri, rule, Vcp, Vri, budget, ALG_S, 0.0, 0.0, 0.0);
+    problem P = make_problem(n, Acp, Ari, NULL, Wcp, Wri, rule, Vcp, Vri, budget, blk, ALG_S, 0.0, 0.0, 0.0);
     if (nthreads <= 0) nthreads = 1;
 #pragma omp parallel for schedule(dynamic, 256) num_threads(nthreads)
     for (int t = 0; t < ncols; ++t) lcount[t] = count_l(&P, cols ? cols[t] : t);
@@ -530,12 +535,12 @@ int diaf_oracle_vcount(int n, const int *Acp, const int *Ari, const int *Wcp, co
  * res, flags, margin, sig (2 per column) indexed by t. */
 int diaf_oracle_factor(int n, const int *Acp, const int *Ari, const double *Av,
                        const int *Wcp, const int *Wri, int rule, const int *Vcp,
-                       const int *Vri, const int *budget, int alg, double tie_tol,
+                       const int *Vri, const int *budget, const int *blk, int alg, double tie_tol,
                        double stab_tol, double stab_r,
                        int ncols, const int *cols, const long long *voff,
                        double *Wv, int *Vri_out, double *Vv, double *res,
                        unsigned *flags, double *margin, double *sig, int nthreads) {
-    problem P = make_problem(n, Acp, Ari, Av, Wcp, Wri, rule, Vcp, Vri, budget, alg, tie_tol, stab_tol, stab_r);
+    problem P = make_problem(n, Acp, Ari, Av, Wcp, Wri, rule, Vcp, Vri, budget, blk, alg, tie_tol, stab_tol, stab_r);
     if (nthreads <= 0) nthreads = 1;
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads)
     for (int t = 0; t < ncols; ++t) {
@@ -557,11 +562,11 @@ int diaf_oracle_factor(int n, const int *Acp, const int *Ari, const double *Av,
 /* Single column with its tile rows and leverage (for tests). */
 int diaf_oracle_column(int n, const int *Acp, const int *Ari, const double *Av,
                        const int *Wcp, const int *Wri, int rule, const int *Vcp,
-                       const int *Vri, const int *budget, int alg, double tie_tol,
+                       const int *Vri, const int *budget, const int *blk, int alg, double tie_tol,
                        double stab_tol, double stab_r, int j,
                        double *w, int *Irows, double *v, double *res, unsigned *flags,
                        double *margin, double *sig, int *m, int *rows, double *h) {
-    problem P = make_problem(n, Acp, Ari, Av, Wcp, Wri, rule, Vcp, Vri, budget, alg, tie_tol, stab_tol, stab_r);
+    problem P = make_problem(n, Acp, Ari, Av, Wcp, Wri, rule, Vcp, Vri, budget, blk, alg, tie_tol, stab_tol, stab_r);
     colout o = {(zd *)w, Irows, (zd *)v, 0, 0, 0, 0, 0};
     solve_column(&P, j, &o, h, rows, m);
     *res = o.res; *flags = o.flags; *margin = o.margin;

@@ -17,7 +17,7 @@ import numpy as np
 
 from . import build as _build
 
-RULE_FIXED, RULE_UPPER, RULE_LOWER, RULE_ALL = 0, 1, 2, 3
+RULE_FIXED, RULE_UPPER, RULE_LOWER, RULE_ALL, RULE_BLOCK = 0, 1, 2, 3, 4
 ALG = {"Q": 1, "S": 2}
 F_RANK_DEFICIENT, F_DEGENERATE, F_VJJ_ZERO, F_JACOBI_NOCONV, F_NONFINITE, F_EMPTY = 1, 2, 4, 8, 16, 32
 F_STABILISED = 128
@@ -35,13 +35,13 @@ def _load():
     if _lib is None:
         L = ctypes.CDLL(_build.build())
         L.diaf_oracle_vcount.argtypes = [ctypes.c_int, _i32p, _i32p, _i32p, _i32p, ctypes.c_int, _i32p, _i32p,
-                                         _i32p, ctypes.c_int, _i32p, _i32p, ctypes.c_int]
+                                         _i32p, _i32p, ctypes.c_int, _i32p, _i32p, ctypes.c_int]
         L.diaf_oracle_factor.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _i32p, _i32p, ctypes.c_int, _i32p,
-                                         _i32p, _i32p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                         _i32p, _i32p, _i32p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_int, _i32p, _i64p,
                                          _f64p, _i32p, _f64p, _f64p, _u32p, _f64p, _f64p, ctypes.c_int]
         L.diaf_oracle_column.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _i32p, _i32p, ctypes.c_int, _i32p,
-                                         _i32p, _i32p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                         _i32p, _i32p, _i32p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_int, _f64p, _i32p,
                                          _f64p, _f64p, _u32p, _f64p, _f64p, _i32p, _i32p, _f64p]
         L.diaf_oracle_qr.argtypes = [ctypes.c_int, ctypes.c_int, _f64p, _f64p, _f64p]
@@ -62,7 +62,7 @@ def _nthreads(nthreads):
 class _Inputs:
     """Keeps contiguous copies alive for the duration of a call."""
 
-    def __init__(self, A, PW, vrule, budget, Vfixed):
+    def __init__(self, A, PW, vrule, budget, Vfixed, blocks=None):
         self.n = A.n
         self.Acp = np.ascontiguousarray(A.colptr, np.int32)
         self.Ari = np.ascontiguousarray(A.rowidx, np.int32)
@@ -76,6 +76,9 @@ class _Inputs:
         else:
             self.Vcp = self.Vri = None
         self.budget = None if budget is None else np.ascontiguousarray(budget, np.int32)
+        if self.rule == RULE_BLOCK and blocks is None:
+            raise ValueError("RULE_BLOCK needs the block of every row")
+        self.blk = None if blocks is None else np.ascontiguousarray(blocks, np.int32)
         self.real = not np.iscomplexobj(A.vals)
 
     def head(self):
@@ -83,7 +86,7 @@ class _Inputs:
 
     def wv(self):
         return (_p(self.Wcp, _i32p), _p(self.Wri, _i32p), self.rule, _p(self.Vcp, _i32p), _p(self.Vri, _i32p),
-                _p(self.budget, _i32p))
+                _p(self.budget, _i32p), _p(self.blk, _i32p))
 
 
 @dataclass
@@ -122,9 +125,9 @@ class OracleResult:
         return sp.csc_matrix((self.Vvals, self.Vrowidx, self.voff), shape=(self.n, self.n))
 
 
-def vcount(A, PW, vrule=RULE_UPPER, budget=None, Vfixed=None, cols=None, nthreads=None) -> np.ndarray:
+def vcount(A, PW, vrule=RULE_UPPER, budget=None, Vfixed=None, cols=None, nthreads=None, blocks=None) -> np.ndarray:
     L = _load()
-    x = _Inputs(A, PW, vrule, budget, Vfixed)
+    x = _Inputs(A, PW, vrule, budget, Vfixed, blocks)
     cl = None if cols is None else np.ascontiguousarray(cols, np.int32)
     nc = A.n if cl is None else cl.size
     out = np.zeros(nc, np.int32)
@@ -133,15 +136,16 @@ def vcount(A, PW, vrule=RULE_UPPER, budget=None, Vfixed=None, cols=None, nthread
 
 
 def factor(A, PW, vrule=RULE_UPPER, budget=None, Vfixed=None, alg="S", tie_tol=TIE_TOL, cols=None,
-           nthreads=None, stab_tol=0.0, stab_r=2.0) -> OracleResult:
+           nthreads=None, stab_tol=0.0, stab_r=2.0, blocks=None) -> OracleResult:
     """Columnwise W, V (Sec. 2.1 / 2.2 with the V rule of Sec. 3.1) for the
     listed columns (all when cols is None).  stab_tol > 0 turns on the
-    stabilised DIAF-Q of Sec. 3.2 (|v_jj| < stab_tol -> v_jj imposed as stab_r)."""
+    stabilised DIAF-Q of Sec. 3.2 (|v_jj| < stab_tol -> v_jj imposed as stab_r).
+    vrule RULE_BLOCK: `blocks` gives the block of every row (block-diagonal V)."""
     L = _load()
-    x = _Inputs(A, PW, vrule, budget, Vfixed)
+    x = _Inputs(A, PW, vrule, budget, Vfixed, blocks)
     cl = np.arange(A.n, dtype=np.int32) if cols is None else np.ascontiguousarray(cols, np.int32)
     nc = cl.size
-    lc = vcount(A, PW, vrule, budget, Vfixed, cl, nthreads)
+    lc = vcount(A, PW, vrule, budget, Vfixed, cl, nthreads, blocks)
     voff = np.zeros(nc + 1, np.int64)
     np.cumsum(lc, out=voff[1:])
     Wv = np.zeros(PW.nnz, np.complex128)
@@ -174,11 +178,11 @@ class ColumnInfo:
 
 
 def column(A, PW, j, vrule=RULE_UPPER, budget=None, Vfixed=None, alg="S", tie_tol=TIE_TOL, stab_tol=0.0,
-           stab_r=2.0) -> ColumnInfo:
+           stab_r=2.0, blocks=None) -> ColumnInfo:
     L = _load()
-    x = _Inputs(A, PW, vrule, budget, Vfixed)
+    x = _Inputs(A, PW, vrule, budget, Vfixed, blocks)
     k = int(PW.colptr[j + 1] - PW.colptr[j])
-    l = int(vcount(A, PW, vrule, budget, Vfixed, [j])[0])
+    l = int(vcount(A, PW, vrule, budget, Vfixed, [j], blocks=blocks)[0])
     mcap = int(sum(A.colptr[c + 1] - A.colptr[c] for c in PW.rowidx[PW.colptr[j]:PW.colptr[j + 1]])) + 1
     w = np.zeros(max(k, 1), np.complex128); Ir = np.zeros(max(l, 1), np.int32); v = np.zeros(max(l, 1), np.complex128)
     res = ctypes.c_double(); fl = ctypes.c_uint32(); mg = ctypes.c_double(); sig = np.zeros(2)

@@ -160,7 +160,9 @@ diaf_status check_args(const diaf_csc* A, const diaf_pattern* PW, const diaf_vsp
   if (A->n < 0 || PW->n != A->n) return fail(DIAF_EINVAL, "PW->n must equal A->n >= 0");
   if (A->nnz < 0 || PW->nnz < 0 || A->nnz >= (1ll << 31) || PW->nnz >= (1ll << 31))
     return fail(DIAF_EINVAL, "nnz out of range");
-  if (V->rule < DIAF_RULE_FIXED || V->rule > DIAF_RULE_ALL) return fail(DIAF_EINVAL, "unknown V rule");
+  if (V->rule < DIAF_RULE_FIXED || V->rule > DIAF_RULE_BLOCK) return fail(DIAF_EINVAL, "unknown V rule");
+  if (V->rule == DIAF_RULE_BLOCK && A->n > 0 && !V->blocks)
+    return fail(DIAF_EINVAL, "DIAF_RULE_BLOCK needs the block of every row (V->blocks)");
   if (V->rule == DIAF_RULE_FIXED && (!V->fixed || V->fixed->n != A->n || !V->fixed->colptr))
     return fail(DIAF_EINVAL, "fixed V pattern missing or of the wrong size");
   if (A->n > 0 && (!A->colptr || !PW->colptr || (A->nnz > 0 && (!A->rowidx || !A->vals)) ||
@@ -191,6 +193,10 @@ diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_
   F->alg = alg;
   F->prec = prec;
   F->rule = V->rule;
+  if (V->rule == DIAF_RULE_BLOCK && n > 0) {  // the apply needs the blocks after the caller's buffer is gone
+    DIAF_CU(F->alloc(&F->blk, n));
+    DIAF_CU(cudaMemcpyAsync(F->blk, V->blocks, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+  }
   F->nnz_w = PW->nnz;
   np.n = n; np.alg = alg; np.dtype = A->dtype; np.cplx = cplx;
   np.mixed = prec == DIAF_PREC_MIXED32;
@@ -224,6 +230,7 @@ diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_
   pa.Vfcp = V->rule == DIAF_RULE_FIXED ? V->fixed->colptr : nullptr;
   pa.Vfri = V->rule == DIAF_RULE_FIXED ? V->fixed->rowidx : nullptr;
   pa.budget = V->budget;
+  pa.blk = V->rule == DIAF_RULE_BLOCK ? V->blocks : nullptr;
   pa.edge_m0 = tuning && tuning->m_edge0 > 0 ? tuning->m_edge0 : 32;
   pa.edge_m1 = tuning && tuning->m_edge1 > 0 ? tuning->m_edge1 : 64;
   int64_t* bs64;
@@ -306,6 +313,7 @@ diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_
   ca.Wcp = PW->colptr; ca.Wri = PW->rowidx;
   ca.Eoff = pa.Eoff; ca.rows = pa.rows; ca.m = pa.m; ca.l = pa.l; ca.jin = pa.jin;
   ca.rule = V->rule; ca.Vfcp = pa.Vfcp; ca.Vfri = pa.Vfri;
+  ca.blk = pa.blk;
   ca.Vcp = F->Vcp;
   ca.tie_tol = V->tie_tol > 0 ? V->tie_tol : 1e-9;
   ca.stab_tol = (alg == DIAF_ALG_Q && V->stab_tol > 0) ? V->stab_tol : 0.0;
@@ -584,7 +592,39 @@ diaf_status diaf_sync(diaf_factors* F, void* stream) {
   return DIAF_OK;
 }
 
+// Block-diagonal V: W in CSR for the SpMV, the blocks of V factored by LU.
+static diaf_status prepare_apply_blocks(diaf_factors* F, cudaStream_t s) {
+  const int n = F->n;
+  const bool cplx = F->dtype == DIAF_C128;
+  const size_t esz = cplx ? 16 : 8;
+  int32_t* work;
+  DIAF_CU(F->alloc(&work, 2 * n + scan_blocksums_size(n)));
+  F->Wr.n = n; F->Wr.nnz = F->nnz_w;
+  DIAF_CU(F->alloc(&F->Wr.rowptr, n + 1));
+  DIAF_CU(F->alloc(&F->Wr.colidx, F->nnz_w));
+  DIAF_CU(F->alloc((char**)&F->Wr.vals, esz * F->nnz_w));
+  DIAF_CU(csc_to_csr(n, F->nnz_w, F->Wcp, F->Wri, F->Wv, cplx, F->Wr.rowptr, F->Wr.colidx, F->Wr.vals, work, s));
+  DIAF_CU(F->alloc(&F->Vb.bstart, n + 1));
+  DIAF_CU(F->alloc((char**)&F->Vb.lu, esz * block_lu_elems(n)));
+  DIAF_CU(F->alloc(&F->Vb.piv, n));
+  uint32_t* st;
+  DIAF_CU(F->alloc(&st, 1));
+  DIAF_CU(cudaMemsetAsync(st, 0, sizeof(uint32_t), s));
+  DIAF_CU(block_prepare(n, cplx, F->blk, F->Vcp, F->Vri, F->Vv, F->Vb, work, st, s));
+  uint32_t h = 0;
+  DIAF_CU(cudaMemcpyAsync(&h, st, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  DIAF_CU(cudaStreamSynchronize(s));
+  if (h & DEV_ST_BAD_INPUT) return fail(DIAF_EINVAL, "block ids decrease, or V has an entry outside its block");
+  if (h & DEV_ST_CAPACITY) return fail(DIAF_EUNSUPPORTED, "a block of V has more than 64 rows");
+  if (h & DEV_ST_SINGULAR) return fail(DIAF_EINVAL, "V has a singular diagonal block");
+  DIAF_CU(F->alloc((char**)&F->tbuf, esz * n));
+  F->v_block = true;
+  F->apply_ready = true;
+  return DIAF_OK;
+}
+
 static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
+  if (F->rule == DIAF_RULE_BLOCK) return prepare_apply_blocks(F, s);
   const int n = F->n;
   const bool cplx = F->dtype == DIAF_C128;
   const size_t esz = cplx ? 16 : 8;
@@ -668,6 +708,11 @@ diaf_status diaf_apply(diaf_factors* F, const void* x, void* y, void* stream) {
   }
   if (F->n == 0) return DIAF_OK;
   const bool cplx = F->dtype == DIAF_C128;
+  if (F->v_block) {
+    DIAF_CU(block_solve(F->Vb, cplx, x, F->tbuf, s));
+    DIAF_CU(csr_spmv(F->Wr, cplx, F->tbuf, y, s));
+    return DIAF_OK;
+  }
   DIAF_CU(trsv_levels_perm(F->Vl, cplx, x, F->tbuf, s));
   DIAF_CU(csr_spmv(F->Wl, cplx, F->tbuf, y, s));
   return DIAF_OK;

@@ -51,6 +51,7 @@ extern "C" diaf_status diaf_apply_static(diaf_factors* F, const void* x, void* y
   diaf_set_last_error("");
   if (!F || (F->n > 0 && (!x || !y))) return fail(DIAF_EINVAL, "NULL argument");
   if (x == y) return fail(DIAF_EINVAL, "x and y must not overlap");
+  if (F->rule == DIAF_RULE_BLOCK) return fail(DIAF_EUNSUPPORTED, "block-diagonal V: use diaf_apply");
   if (F->n > kStaticMaxN)
     return fail(DIAF_EINVAL, "n = " + std::to_string(F->n) + " exceeds the static scratch limit of " +
                                  std::to_string(kStaticMaxN) + " rows");

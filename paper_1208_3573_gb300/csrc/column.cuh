@@ -37,6 +37,7 @@ struct ColArgs {
   const int32_t* Vfri;
   const int32_t* Vcp;
   double tie_tol;
+  const int32_t* blk;         // DIAF_RULE_BLOCK: block of every row
   double stab_tol;            // stabilised DIAF-Q: trigger |v_jj| < stab_tol (0: off)
   double stab_r;              // stabilised DIAF-Q: imposed v_jj before scaling to unit norm
   const int32_t* list;        // bucket's columns
@@ -126,23 +127,23 @@ __device__ void gather_tile(const ColArgs& a, int j, int k, int m, int me, SD* T
 // excluded (it passes the threshold by construction): how close a decision
 // came to flipping when the keys carry an error.
 __device__ inline double select_rows_greedy(const int32_t* rs, const double* hk, int32_t* pick, int m, int rule,
-                                            int j, int s, double tau, int lane) {
+                                            int j, int s, double tau, int lane, const int32_t* blk) {
   double margin = DBL_MAX;
   for (int r = lane; r < m; r += DIAF_WARP) pick[r] = 0;
   __syncwarp();
   for (int t = 0; t < s; ++t) {
     double hm = -DBL_MAX;
     for (int r = lane; r < m; r += DIAF_WARP)
-      if (!pick[r] && admissible_row(rule, rs[r], j)) hm = dmax(hm, hk[r]);
+      if (!pick[r] && admissible_row(rule, rs[r], j, blk)) hm = dmax(hm, hk[r]);
     hm = warp_max(hm);
     int rmax = INT_MAX;
     for (int r = lane; r < m; r += DIAF_WARP)
-      if (!pick[r] && admissible_row(rule, rs[r], j) && hk[r] == hm) rmax = dmin(rmax, r);
+      if (!pick[r] && admissible_row(rule, rs[r], j, blk) && hk[r] == hm) rmax = dmin(rmax, r);
     rmax = warp_min(rmax);
     const double thr = hm - tau;
     int best = INT_MAX;
     for (int r = lane; r < m; r += DIAF_WARP)
-      if (!pick[r] && admissible_row(rule, rs[r], j)) {
+      if (!pick[r] && admissible_row(rule, rs[r], j, blk)) {
         if (r != rmax) margin = dmin(margin, fabs(hk[r] - thr));
         if (hk[r] >= thr) best = dmin(best, r);
       }
@@ -407,7 +408,7 @@ __device__ void solve_column_warp(const ColArgs& a, int j, unsigned char* smem, 
   const R piv = R(1e-14) * rdmax;
   if (k > 0 && (a.rule != DIAF_RULE_FIXED || ALG == DIAF_ALG_Q))
     warp_leverage_rows<S, S, LDT, KP>(Ts, Rs, Tw, hk, rinv, m, k, piv, lane);
-  if (a.rule != DIAF_RULE_FIXED) select_rows_greedy(ix.rs, hk, ix.pick, m, a.rule, j, l - 1, a.tie_tol, lane);
+  if (a.rule != DIAF_RULE_FIXED) select_rows_greedy(ix.rs, hk, ix.pick, m, a.rule, j, l - 1, a.tie_tol, lane, a.blk);
   const int jpos = build_I(a, j, m, l, ix, lane);
 
   for (int t = lane; t < l; t += DIAF_WARP) vv[t] = sc_zero<S>();

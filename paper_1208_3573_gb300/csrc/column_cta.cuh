@@ -352,12 +352,12 @@ __device__ void solve_column_cta(const ColArgs& a, const CtaScratch& sc, int j, 
     for (int t = 0; t < s; ++t) {
       double hm = -DBL_MAX;
       for (int r = tid; r < m; r += kCtaThreads)
-        if (!pick[r] && admissible_row(a.rule, rs[r], j)) hm = dmax(hm, hk[r]);
+        if (!pick[r] && admissible_row(a.rule, rs[r], j, a.blk)) hm = dmax(hm, hk[r]);
       hm = block_max(hm, red);
       const double thr = hm - a.tie_tol;
       int best = INT_MAX;
       for (int r = tid; r < m; r += kCtaThreads)
-        if (!pick[r] && admissible_row(a.rule, rs[r], j) && hk[r] >= thr) best = dmin(best, r);
+        if (!pick[r] && admissible_row(a.rule, rs[r], j, a.blk) && hk[r] >= thr) best = dmin(best, r);
       best = block_min(best, reinterpret_cast<int*>(red));
       if (tid == 0 && best < m) pick[best] = 1;
       __syncthreads();

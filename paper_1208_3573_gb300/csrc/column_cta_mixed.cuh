@@ -30,22 +30,22 @@ struct CtaMixedSmem {
 // Returns the smallest distance of a non-leading candidate key from a
 // threshold it was compared with (the FP32 decision margin).
 __device__ inline double cta_select_rows(const int32_t* rs, const double* hk, int32_t* pick, int m, int rule, int j,
-                                         int s, double tau, double* red) {
+                                         int s, double tau, double* red, const int32_t* blk) {
   const int tid = threadIdx.x;
   double margin = DBL_MAX;
   for (int t = 0; t < s; ++t) {
     double hm = -DBL_MAX;
     for (int r = tid; r < m; r += kCtaThreads)
-      if (!pick[r] && admissible_row(rule, rs[r], j)) hm = dmax(hm, hk[r]);
+      if (!pick[r] && admissible_row(rule, rs[r], j, blk)) hm = dmax(hm, hk[r]);
     hm = block_max(hm, red);
     int rmax = INT_MAX;
     for (int r = tid; r < m; r += kCtaThreads)
-      if (!pick[r] && admissible_row(rule, rs[r], j) && hk[r] == hm) rmax = dmin(rmax, r);
+      if (!pick[r] && admissible_row(rule, rs[r], j, blk) && hk[r] == hm) rmax = dmin(rmax, r);
     rmax = block_min(rmax, reinterpret_cast<int*>(red));
     const double thr = hm - tau;
     int best = INT_MAX;
     for (int r = tid; r < m; r += kCtaThreads)
-      if (!pick[r] && admissible_row(rule, rs[r], j)) {
+      if (!pick[r] && admissible_row(rule, rs[r], j, blk)) {
         if (r != rmax) margin = dmin(margin, fabs(hk[r] - thr));
         if (hk[r] >= thr) best = dmin(best, r);
       }
@@ -174,7 +174,7 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
       hk[r] = (double)h;
     }
     __syncthreads();
-    const double margin = cta_select_rows(rs, hk, pick, m, a.rule, j, l - 1, a.tie_tol, red);
+    const double margin = cta_select_rows(rs, hk, pick, m, a.rule, j, l - 1, a.tie_tol, red, a.blk);
     const double delta = 8.0 * (m + k) * (double)FLT_EPSILON * (double)kap;
     if (l > 1 && margin <= 2.0 * delta) return false;
   }

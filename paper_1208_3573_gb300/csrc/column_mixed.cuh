@@ -129,7 +129,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
   warp_leverage_rows<S, SD, LDT, KP>(Ts, Rs, Tw, hk, rinv, m, k, R(0), lane);
   DIAF_PHASE(3);
   if (a.rule != DIAF_RULE_FIXED) {
-    const double margin = select_rows_greedy(ix.rs, hk, ix.pick, m, a.rule, j, l - 1, a.tie_tol, lane);
+    const double margin = select_rows_greedy(ix.rs, hk, ix.pick, m, a.rule, j, l - 1, a.tie_tol, lane, a.blk);
     // bound on the FP32 key error: backward error of the FP32 QR and of the
     // row solves, amplified by the (column-scaled) conditioning of T
     const double delta = 8.0 * (m + k) * (double)FLT_EPSILON * (double)kap;
@@ -257,6 +257,10 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     for (int c = 0; c < k; ++c) if (c != imax) snext = dmax(snext, sig[c]);
     if (!(smax > 0.0)) { hand_back(6); return; }
     if (k > 1 && (smax - snext) <= 1e-6 * smax) flags |= DIAF_FLAG_DEGENERATE;
+    // one Rayleigh-quotient step refines v0 to FP64 accuracy only when v0's
+    // FP32 error (about eps_32 / relative gap) is small against the gap to the
+    // second eigenvalue of Q_I Q_I^*: closer gaps go to the FP64 kernel
+    if (k > 1 && (smax * smax - snext * snext) < 1e-3 * smax * smax) { hand_back(4); return; }
     for (int t = lane; t < l; t += DIAF_WARP) vv[t] = sc_cast<SD>(Tw[t + imax * LDT]);
     for (int c = lane; c < k; c += DIAF_WARP) rinvD[c] = sc_recip_or_zero(sc_cast<SD>(Rs[c + c * KP]), 0.0);
     __syncwarp();

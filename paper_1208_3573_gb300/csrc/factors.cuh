@@ -35,6 +35,10 @@ struct diaf_factors {
   // level-scheduled V solve: V in level order, W's columns renumbered to it
   LevelCsr Vl;
   Csr Wl;
+  // block-diagonal V (DIAF_RULE_BLOCK): dense LU of every diagonal block
+  int32_t* blk = nullptr;        // block of every row (owned copy)
+  bool v_block = false;
+  BlockLu Vb;
 
   template <class T>
   cudaError_t alloc(T** p, size_t count) {

@@ -9,10 +9,11 @@ constexpr int kWarpGather = 256;  // E_j capacity of the warp path
 constexpr int kPlanWarps = 8;     // warps per CTA in the warp path
 constexpr int kPlanCtaThreads = 256;
 
-__device__ __forceinline__ bool admissible(int rule, int i, int j) {
+__device__ __forceinline__ bool admissible(int rule, int i, int j, const int32_t* blk) {
   if (i == j) return false;
   if (rule == DIAF_RULE_UPPER) return i < j;
   if (rule == DIAF_RULE_LOWER) return i > j;
+  if (rule == DIAF_RULE_BLOCK) return blk[i] == blk[j];
   return true;
 }
 
@@ -75,7 +76,7 @@ __device__ void finish_column(const PlanArgs& a, int j, const int32_t* s, int E,
       int pos = base + __popc(b & ((1u << tid) - 1u));
       if (f) {
         out[pos] = r;
-        ncand += admissible(a.rule, r, j);
+        ncand += admissible(a.rule, r, j, a.blk);
         jin |= (r == j);
       }
       base += __popc(b);
@@ -93,7 +94,7 @@ __device__ void finish_column(const PlanArgs& a, int j, const int32_t* s, int E,
       int pos = base + before + __popc(b & ((1u << lane) - 1u));
       if (f) {
         out[pos] = r;
-        ncand += admissible(a.rule, r, j);
+        ncand += admissible(a.rule, r, j, a.blk);
         jin |= (r == j);
       }
       base += tot;

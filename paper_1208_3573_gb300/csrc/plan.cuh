@@ -28,6 +28,7 @@ struct PlanArgs {
   const int32_t* Vfcp;
   const int32_t* Vfri;
   const int32_t* budget;
+  const int32_t* blk;  // DIAF_RULE_BLOCK: block of every row
   int edge_m0;      // size-bucket edges (tuning): max(m, k) <= edge_m0 -> bucket 0, <= edge_m1 -> bucket 1
   int edge_m1;
   // outputs

@@ -64,3 +64,21 @@ cudaError_t remap_columns(int64_t nnz, const int32_t* pos, const int32_t* cin, i
 // t = V^-1 x by level scheduling on L: one 1024-thread block, a barrier
 // between levels; t in level order (t[p] belongs to row xrow[p]).
 cudaError_t trsv_levels_perm(const LevelCsr& L, bool cplx, const void* x, void* t, cudaStream_t s);
+
+// Block-diagonal V: dense LU with partial pivoting of every diagonal block
+// (blocks = runs of equal, non-decreasing block ids; at most 64 rows each).
+struct BlockLu {
+  int nblocks = 0;
+  int32_t* bstart = nullptr;  // nblocks + 1 (capacity n + 1)
+  void* lu = nullptr;         // block_lu_elems(n) scalars: column c of a block at (first row + c) * 64
+  int32_t* piv = nullptr;     // n: block-local pivot row of every elimination step
+};
+size_t block_lu_elems(int n);
+// Finds the blocks and factors them; `work` needs 2 n + scan_blocksums_size(n)
+// int32; synchronises `s` once (the block count).  *status receives
+// DEV_ST_BAD_INPUT (decreasing ids, or an entry of V outside its block),
+// DEV_ST_CAPACITY (a block above 64 rows), DEV_ST_SINGULAR (a zero pivot).
+cudaError_t block_prepare(int n, bool cplx, const int32_t* blk, const int32_t* Vcp, const int32_t* Vri,
+                          const void* Vv, BlockLu& B, int32_t* work, uint32_t* status, cudaStream_t s);
+// t = V^-1 x with the factored blocks.
+cudaError_t block_solve(const BlockLu& B, bool cplx, const void* x, void* t, cudaStream_t s);

@@ -51,10 +51,11 @@ __device__ __forceinline__ S sc_recip_or_zero(S d, RealOf<S> piv) {
   return div_r(R(1), a2) * sc_conj(d);
 }
 
-__device__ __forceinline__ bool admissible_row(int rule, int i, int j) {
+__device__ __forceinline__ bool admissible_row(int rule, int i, int j, const int32_t* blk) {
   if (i == j) return false;
   if (rule == DIAF_RULE_UPPER) return i < j;
   if (rule == DIAF_RULE_LOWER) return i > j;
+  if (rule == DIAF_RULE_BLOCK) return blk[i] == blk[j];
   return true;
 }
 

@@ -20,7 +20,7 @@ DIAF_OK, DIAF_EINVAL, DIAF_ENOMEM, DIAF_ECUDA, DIAF_ENUMERIC, DIAF_ETIMEOUT, DIA
 DIAF_F64, DIAF_C128 = 0, 1
 ALG = {"Q": 1, "S": 2}
 PREC = {"fp64": 0, "mixed32": 1}
-RULE_FIXED, RULE_UPPER, RULE_LOWER, RULE_ALL = 0, 1, 2, 3
+RULE_FIXED, RULE_UPPER, RULE_LOWER, RULE_ALL, RULE_BLOCK = 0, 1, 2, 3, 4
 FLAG_RANK_DEFICIENT, FLAG_DEGENERATE, FLAG_VJJ_ZERO, FLAG_JACOBI_NOCONV = 1, 2, 4, 8
 FLAG_NONFINITE, FLAG_EMPTY, FLAG_FP64_FALLBACK, FLAG_STABILISED = 16, 32, 64, 128
 
@@ -43,7 +43,8 @@ class Pattern_t(ctypes.Structure):
 
 class VSpec_t(ctypes.Structure):
     _fields_ = [("rule", ctypes.c_int32), ("fixed", ctypes.POINTER(Pattern_t)), ("budget", ctypes.c_void_p),
-                ("tie_tol", ctypes.c_double), ("stab_tol", ctypes.c_double), ("stab_r", ctypes.c_double)]
+                ("tie_tol", ctypes.c_double), ("stab_tol", ctypes.c_double), ("stab_r", ctypes.c_double),
+                ("blocks", ctypes.c_void_p)]
 
 
 class Tuning_t(ctypes.Structure):
@@ -293,22 +294,24 @@ def launch_count() -> int:
     return int(lib().diaf_launch_count())
 
 
-def _args(A, PW, vrule, budget, Vfixed, tie_tol, stab=(0.0, 2.0)):
+def _args(A, PW, vrule, budget, Vfixed, tie_tol, stab=(0.0, 2.0), blocks=None):
     a = A.csc_t()
     pw = PW.pattern_t()
     fixed = Vfixed.pattern_t() if Vfixed is not None else None
     vs = VSpec_t(vrule, ctypes.pointer(fixed) if fixed is not None else None, _ptr(budget), tie_tol,
-                 float(stab[0]), float(stab[1]))
+                 float(stab[0]), float(stab[1]), _ptr(blocks))
     return a, pw, vs, fixed
 
 
 def factor(A: DeviceCSC, PW: DeviceCSC, vrule: int = RULE_UPPER, budget: torch.Tensor | None = None,
            Vfixed: DeviceCSC | None = None, alg: str = "S", prec: str = "fp64", tie_tol: float = 1e-9,
-           stream=None, tuning: dict | None = None, stab_tol: float = 0.0, stab_r: float = 2.0) -> Factors:
+           stream=None, tuning: dict | None = None, stab_tol: float = 0.0, stab_r: float = 2.0,
+           blocks: torch.Tensor | None = None) -> Factors:
     """Columnwise W, V with A W ~ V (diaf_factor / diaf_factor_tuned); stab_tol > 0
-    turns on the stabilised DIAF-Q."""
+    turns on the stabilised DIAF-Q; vrule RULE_BLOCK with `blocks` (int32 block
+    of every row, non-decreasing) gives a block-diagonal V."""
     L = lib()
-    a, pw, vs, _keep = _args(A, PW, vrule, budget, Vfixed, tie_tol, (stab_tol, stab_r))
+    a, pw, vs, _keep = _args(A, PW, vrule, budget, Vfixed, tie_tol, (stab_tol, stab_r), blocks)
     h = ctypes.c_void_p()
     s = _stream(stream)
     t = Tuning_t.from_dict(tuning)
@@ -457,3 +460,8 @@ def sparsified_powers(A: DeviceCSC, k: int = 2, p_l: int = 0, keep: int = 0, str
     rowidx = torch.empty(max(int(nnz.value), 1), dtype=torch.int32, device=A.colptr.device)
     _check(L.diaf_sparsified_fill(ctypes.byref(a), k, p_l, keep, _ptr(colptr), _ptr(rowidx), s))
     return DeviceCSC(A.n, colptr, rowidx[:int(nnz.value)])
+
+
+def contiguous_blocks(n: int, size: int, device="cuda") -> torch.Tensor:
+    """Block ids for DIAF_RULE_BLOCK: consecutive runs of `size` rows."""
+    return (torch.arange(n, dtype=torch.int32, device=device) // size).contiguous()

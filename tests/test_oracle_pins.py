@@ -426,3 +426,28 @@ def test_gmres_reference():
     M = O.Preconditioner(r.W_csc(), r.V_csc())
     x, its, rr, st = O.gmres(A, w_.b, M, restart=50, tol=1e-6)
     assert st == "ok" and np.linalg.norm(w_.b - A @ x) <= 1e-6 * np.linalg.norm(w_.b) * 1.0001
+
+
+def test_block_rule_reductions():
+    """Block-diagonal V (RULE_BLOCK): blocks of one row reduce to the diagonal
+    V; one block holding every row reduces to RULE_ALL; every entry of V lies
+    in its column's block."""
+    from tests._problems import random_sparse
+    from workloads import diagonal_pattern, pattern_of
+    A = random_sparse(120, 0.04, 31, False)
+    PW = pattern_of(A)
+    n = A.n
+    for alg in ("S", "Q"):
+        one = O.factor(A, PW, O.RULE_BLOCK, np.full(n, 3, np.int32), None, alg=alg, blocks=np.arange(n))
+        diag = O.factor(A, PW, O.RULE_FIXED, None, diagonal_pattern(n), alg=alg)
+        np.testing.assert_array_equal(one.Vrowidx, diag.Vrowidx)
+        np.testing.assert_allclose(one.res, diag.res, rtol=0, atol=0)
+        allb = O.factor(A, PW, O.RULE_BLOCK, np.full(n, 4, np.int32), None, alg=alg, blocks=np.zeros(n))
+        ref = O.factor(A, PW, O.RULE_ALL, np.full(n, 4, np.int32), None, alg=alg)
+        np.testing.assert_array_equal(allb.Vrowidx, ref.Vrowidx)
+        np.testing.assert_allclose(allb.res, ref.res, rtol=0, atol=0)
+        blocks = np.arange(n) // 16
+        b16 = O.factor(A, PW, O.RULE_BLOCK, np.full(n, 5, np.int32), None, alg=alg, blocks=blocks)
+        for j in range(n):
+            assert np.all(blocks[b16.I(j)] == blocks[j])
+            assert j in b16.I(j)

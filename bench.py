@@ -269,6 +269,41 @@ def kv_sweep(w, A, PW, alg, prec, dev, budgets=(1, 2, 3, 4, 6, 8, 13)):
     return out
 
 
+def block_v_report(w, A, PW, alg, prec, dev, bsize=64, budgets=(4, 8, 16)):
+    """Block-diagonal V (the V structure of the paper's experiments, Sec. 5)
+    on this workload: contiguous blocks of `bsize` rows, at most k_V entries
+    per column chosen by the leverage rule inside the block."""
+    import torch
+    from paper_1208_3573_gb300 import diaf
+    S = diaf.Solver(A)
+    b = torch.from_numpy(w.b).to(dev)
+    blk = diaf.contiguous_blocks(w.n, bsize, device=dev)
+    x = torch.ones(w.n, dtype=b.dtype, device=dev)
+    y = torch.empty_like(x)
+    out = []
+    for kv in budgets:
+        bud = torch.full((w.n,), kv, dtype=torch.int32, device=dev)
+        F = diaf.factor(A, PW, diaf.RULE_BLOCK, bud, alg=alg, prec=prec, tie_tol=w.tie_tol, blocks=blk)
+        row = {"block_rows": bsize, "k_V": kv, "setup_ms": F.timings()["total_ms"], "nnz_V": int(F.V.nnz),
+               "nrm_AW_minus_V": float(np.sqrt(np.sum(F.res.cpu().numpy() ** 2)))}
+        try:
+            F.apply(x, y)  # prepares the block LU
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(); F.apply(x, y); e1.record(); e1.synchronize()
+            row["apply_ms"] = e0.elapsed_time(e1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, info = S.bicgstab(b, F, tol=1e-8, maxit=1000)
+            torch.cuda.synchronize()
+            row.update(bicgstab_its=info.iterations, converged=bool(info.converged),
+                       solve_ms=1e3 * (time.perf_counter() - t0))
+        except diaf.DiafError as e:
+            row["solve"] = str(e)[:80]
+        F.close()
+        out.append(row)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -489,6 +524,11 @@ def main():
             extras["kv_sweep"] = kv_sweep(w, A, PW, args.alg, args.prec, dev)
         except Exception as e:
             extras["kv_sweep"] = {"error": f"{type(e).__name__}: {e}"[:300]}
+    if not args.no_extras and rank == 0 and do_apply:
+        try:
+            extras["block_v"] = block_v_report(w, A, PW, args.alg, args.prec, dev)
+        except Exception as e:
+            extras["block_v"] = {"error": f"{type(e).__name__}: {e}"[:300]}
     if not args.no_extras and not args.no_learned and rank == 0:
         try:
             extras["learned_proposal"] = learned_report(dev)

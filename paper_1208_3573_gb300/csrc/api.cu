@@ -146,6 +146,7 @@ struct NumericPlan {
   int h_bc[kNumBuckets] = {0};
   CtaScratch cs{};
   int cta_grid = 0;
+  int cta_grid_mixed = 0;  // mixed large-tile kernel (0: not used)
   bool mixed = false, cplx = false;
   int alg = DIAF_ALG_S, dtype = DIAF_F64, n = 0;
   int wpb[2] = {0, 0};
@@ -340,7 +341,10 @@ diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_
     np.cs.kcap = h_stats[0] > 0 ? h_stats[0] : 1;
     np.cta_grid = cta_columns_grid(A->dtype, alg, np.cs.ldm, np.h_bc[bl]);
     if (np.cta_grid <= 0) return fail(DIAF_EUNSUPPORTED, "large-tile kernel does not fit this tile size");
-    DIAF_CU(pool.get((char**)&np.cs.slab, (size_t)np.cta_grid * 2 * np.cs.ldm * np.cs.kcap * esz));
+    // the mixed kernel needs less shared memory: its own occupancy-sized grid
+    np.cta_grid_mixed = np.mixed ? cta_columns_grid_mixed(A->dtype, alg, np.cs.ldm, np.h_bc[bl]) : 0;
+    const int slabs = np.cta_grid > np.cta_grid_mixed ? np.cta_grid : np.cta_grid_mixed;
+    DIAF_CU(pool.get((char**)&np.cs.slab, (size_t)slabs * 2 * np.cs.ldm * np.cs.kcap * esz));
   }
   return DIAF_OK;
 }
@@ -370,7 +374,8 @@ diaf_status enqueue_numeric(diaf_factors* F, NumericPlan& np, cudaStream_t s, bo
       if (np.mixed) {
         ca.fb_list = np.fb_list + (size_t)b * n;
         ca.fb_count = np.fb_count + b;
-        e = launch_columns_cta_mixed(np.dtype, np.alg, ca, np.cs, np.cta_grid, s);
+        e = np.cta_grid_mixed > 0 ? launch_columns_cta_mixed(np.dtype, np.alg, ca, np.cs, np.cta_grid_mixed, s)
+                                  : cudaErrorNotSupported;
         if (e == cudaSuccess) {  // the FP64 kernel finishes the handed-back columns
           ColArgs cf = ca;
           cf.list = ca.fb_list;

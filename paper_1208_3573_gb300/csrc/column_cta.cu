@@ -58,11 +58,8 @@ cudaError_t launch_columns_cta(int dtype, int alg, const ColArgs& a, const CtaSc
   return alg == DIAF_ALG_S ? launch<double, DIAF_ALG_S>(a, sc, grid, s) : launch<double, DIAF_ALG_Q>(a, sc, grid, s);
 }
 
-cudaError_t launch_columns_cta_mixed(int dtype, int alg, const ColArgs& a, const CtaScratch& sc, int grid,
-                                     cudaStream_t s) {
-  if (dtype != DIAF_F64 || alg != DIAF_ALG_S) return cudaErrorNotSupported;
-  if (grid <= 0) return cudaSuccess;
-  const size_t smem = CtaMixedSmem::bytes(sc.ldm);
+static cudaError_t configure_mixed(int ldm, size_t* smem_out) {
+  const size_t smem = CtaMixedSmem::bytes(ldm);
   if (smem > 227 * 1024) return cudaErrorNotSupported;
   static int configured_for = -1;
   if (configured_for < (int)smem) {
@@ -70,6 +67,30 @@ cudaError_t launch_columns_cta_mixed(int dtype, int alg, const ColArgs& a, const
     if (e != cudaSuccess) return e;
     configured_for = (int)smem;
   }
+  *smem_out = smem;
+  return cudaSuccess;
+}
+
+int cta_columns_grid_mixed(int dtype, int alg, int ldm, int count) {
+  if (count <= 0 || dtype != DIAF_F64 || alg != DIAF_ALG_S) return 0;
+  size_t smem = 0;
+  if (configure_mixed(ldm, &smem) != cudaSuccess) return 0;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, column_cta_mixed_kernel, kCtaThreads, smem);
+  if (per_sm < 1) return 0;
+  const int grid = sms * per_sm;
+  return count < grid ? count : grid;
+}
+
+cudaError_t launch_columns_cta_mixed(int dtype, int alg, const ColArgs& a, const CtaScratch& sc, int grid,
+                                     cudaStream_t s) {
+  if (dtype != DIAF_F64 || alg != DIAF_ALG_S) return cudaErrorNotSupported;
+  if (grid <= 0) return cudaSuccess;
+  size_t smem = 0;
+  cudaError_t ce = configure_mixed(sc.ldm, &smem);
+  if (ce != cudaSuccess) return ce;
   column_cta_mixed_kernel<<<grid, kCtaThreads, smem, s>>>(a, sc);
   DIAF_COUNT_LAUNCH();
   return cudaGetLastError();

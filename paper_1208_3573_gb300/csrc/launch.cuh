@@ -23,6 +23,8 @@ cudaError_t launch_columns_cta(int dtype, int alg, const ColArgs& a, const CtaSc
 // hands columns back through a.fb_list / a.fb_count
 cudaError_t launch_columns_cta_mixed(int dtype, int alg, const ColArgs& a, const CtaScratch& sc, int grid,
                                      cudaStream_t s);
+// its persistent grid (resident CTAs, capped by count); 0 when not available
+int cta_columns_grid_mixed(int dtype, int alg, int ldm, int count);
 
 // Persistent grid sized by occupancy; `per_warp` bytes of shared memory per warp.
 template <class Kern>

@@ -304,6 +304,26 @@ def block_v_report(w, A, PW, alg, prec, dev, bsize=64, budgets=(4, 8, 16)):
     return out
 
 
+def rank_max(x: float, world: int) -> float:
+    """The largest value of x over the ranks (the slowest rank's time); the
+    process group's backend decides where the reduction tensor lives."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, ms_local: float, world: int) -> tuple[float, float]:
+    """(units/s of the whole job, step ms): every rank processes units_per_rank
+    in ms_local; the job takes as long as its slowest rank."""
+    ms = rank_max(ms_local, world)
+    return world * units_per_rank / (ms / 1e3), ms
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -391,12 +411,7 @@ def main():
         barrier()
     launches = diaf.launch_count() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = float(np.mean(step_ms))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * w.n / (ms / 1e3)
+    value, ms = whole_job_rate(w.n, float(np.mean(step_ms)), world)
 
     # ---- e2e through the public API from pinned host buffers
     def pin(a):
@@ -427,7 +442,7 @@ def main():
         F.close()
         if i > 0:
             e2e_ms.append(s0.elapsed_time(s1))
-    e2e_val = world * w.n / (float(np.mean(e2e_ms)) / 1e3)
+    e2e_val, _ = whole_job_rate(w.n, float(np.mean(e2e_ms)), world)
 
     # ---- roofline of the dominant kernel (the numeric column kernel)
     peaks, peak_src = _peaks()

@@ -19,6 +19,13 @@
 // Column-scaled conditioning estimate of an upper R whose columns came from a
 // tile with column norms cn: max_c cn_c / |R_cc| (1 for orthogonal columns).
 constexpr float kMixedKappaMax = 300.0f;
+// Bound on an FP32 leverage key's error: delta = kMixedDeltaScale (m + k) eps_32 kappa
+// (the backward error of the FP32 QR and row solves, amplified by the column-scaled
+// conditioning); a decision within 2 delta of its threshold is left to the FP64 kernel.
+#ifndef DIAF_MIXED_DELTA_SCALE
+#define DIAF_MIXED_DELTA_SCALE 1.0
+#endif
+constexpr double kMixedDeltaScale = DIAF_MIXED_DELTA_SCALE;
 
 struct ColArgs {
   int n;

@@ -175,7 +175,7 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
     }
     __syncthreads();
     const double margin = cta_select_rows(rs, hk, pick, m, a.rule, j, l - 1, a.tie_tol, red, a.blk);
-    const double delta = 8.0 * (m + k) * (double)FLT_EPSILON * (double)kap;
+    const double delta = kMixedDeltaScale * (m + k) * (double)FLT_EPSILON * (double)kap;
     if (l > 1 && margin <= 2.0 * delta) return false;
   }
   // I_j

@@ -132,7 +132,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     const double margin = select_rows_greedy(ix.rs, hk, ix.pick, m, a.rule, j, l - 1, a.tie_tol, lane, a.blk);
     // bound on the FP32 key error: backward error of the FP32 QR and of the
     // row solves, amplified by the (column-scaled) conditioning of T
-    const double delta = 8.0 * (m + k) * (double)FLT_EPSILON * (double)kap;
+    const double delta = kMixedDeltaScale * (m + k) * (double)FLT_EPSILON * (double)kap;
     if (l > 1 && margin <= 2.0 * delta) { hand_back(2); return; }
   }
   const int jpos = build_I(a, j, m, l, ix, lane);

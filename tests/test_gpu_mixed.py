@@ -115,3 +115,14 @@ def test_mixed_parity_full_size_powerlaw_sampled(D):
     fb = F.fallbacks()
     assert fb[2] < F.info.bucket_cols[2]  # the mixed CTA kernel finished part of the large bucket
     print("fallbacks per bucket", fb, "of", list(F.info.bucket_cols))
+
+
+@pytest.mark.parametrize("alg", ["S", "Q"])
+def test_mixed_parity_full_size_lognormal64(D, alg):
+    """262,144 columns with k = 25 tiles: every I_j of the mixed form must be the
+    FP64 choice (the key-error bound decides which columns the FP64 kernel takes)."""
+    w = make_workload("lognormal64")
+    F = run_gpu(D, w.A, w.PW, w.vrule, w.budget, alg=alg, prec="mixed32", tie_tol=w.tie_tol)
+    g = host_factors(F)
+    o = O.factor(w.A, w.PW, w.vrule, w.budget, alg=alg, tie_tol=w.tie_tol)
+    assert_parity(compare(g, o, w.A, w.PW, alg, rtol_res=RTOL_RES, vec_tol=VEC_TOL, mixed=True, floor_rel=1e-10))

@@ -223,9 +223,9 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
   cta_col_norms_f(Tw, ld, m, k, cn);
   cta_householder_qr<float>(Tw, ld, me, k, redF, nullptr);
   float kh = 0.0f;
-  for (int c = tid; c < k; c += kCtaThreads) {
+  for (int c = tid; c < k; c += kCtaThreads) {  // exact zero columns of A-hat: exact zero singular values
     const float d = fabsf(Tw[c + (size_t)c * ld]);
-    kh = fmaxf(kh, d > 0.0f ? (float)cn[c] / d : INFINITY);
+    kh = fmaxf(kh, d > 0.0f ? (float)cn[c] / d : (cn[c] > 0.0 ? INFINITY : 0.0f));
   }
   if (!(block_max(kh, redF) <= kMixedKappaMax)) return false;
   for (int i = tid; i < k * k; i += kCtaThreads) {

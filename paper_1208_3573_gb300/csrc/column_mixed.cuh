@@ -157,10 +157,13 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     DIAF_PHASE(5);
     warp_householder_qr_rs<S, LDT, KMAX, MMAX / DIAF_WARP>(Tw, me, k, lane);
     DIAF_PHASE(6);
+    // an exactly zero column of A-hat (all its tile entries in I_j) is no
+    // conditioning problem: it is an exact zero singular value, which the FP32
+    // Jacobi keeps exact (w = e_c, residual 0, flagged from the residual)
     float kh = 0.0f;
     for (int c = lane; c < k; c += DIAF_WARP) {
       const float d = (float)sc_abs(Tw[c + c * LDT]);
-      kh = fmaxf(kh, d > 0.0f ? (float)cn[c] / d : INFINITY);
+      kh = fmaxf(kh, d > 0.0f ? (float)cn[c] / d : (cn[c] > 0.0 ? INFINITY : 0.0f));
     }
     kh = warp_max(kh);
     if (!(kh <= kMixedKappaMax)) { hand_back(3); return; }

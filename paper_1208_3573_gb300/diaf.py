@@ -4,6 +4,26 @@ Every computation runs in the CUDA library.  PyTorch provides device memory
 and streams; outputs owned by the library are exposed to PyTorch as
 zero-copy views (through __cuda_array_interface__) that keep their factor
 handle alive.  There is no CPU path: a missing library or GPU raises.
+
+Typical use (A in CSC, int32 indices, float64 or complex128 values)::
+
+    from paper_1208_3573_gb300 import diaf
+    A  = diaf.DeviceCSC.from_host(A_host)                 # or DeviceCSC(n, colptr, rowidx, vals)
+    PW = diaf.DeviceCSC.from_host(W_pattern_host)         # the W pattern, e.g. pattern(A^2)
+    l  = torch.full((n,), 3, dtype=torch.int32, device="cuda")   # entries per column of V
+    F  = diaf.factor(A, PW, diaf.RULE_UPPER, l, alg="S", prec="mixed32")
+    F.W, F.V, F.res, F.flags                              # CSC factors, per-column residuals, flags
+    y  = F.apply(x)                                       # y = W V^-1 x
+    S  = diaf.Solver(A)
+    x, info = S.bicgstab(b, F, tol=1e-8)                  # or S.gmres(b, F, tol=1e-6, restart=50)
+
+Variants: alg "Q" (unit v_j) or "S" (unit w_j); prec "fp64" or "mixed32";
+V by rule (RULE_UPPER / LOWER / ALL, or RULE_BLOCK with `blocks`) or a fixed
+pattern (RULE_FIXED, Vfixed=...); stab_tol for the stabilised DIAF-Q;
+Plan(...) for numeric refactorisation on new values of A by CUDA-graph
+replay; autotune(...) for the launch tuning; sparsified_powers(...) for the
+Neumann-series W pattern; propose_features / mlp_* / propose_select (and
+learned.Proposer) for the learned W pattern.
 """
 from __future__ import annotations
 

@@ -14,6 +14,8 @@
 // The same kernel finishes the columns the mixed-precision kernel hands back.
 #pragma once
 
+#include <limits>
+
 #include "warp_la.cuh"
 
 // Column-scaled conditioning estimate of an upper R whose columns came from a
@@ -133,13 +135,16 @@ __device__ void gather_tile(const ColArgs& a, int j, int k, int m, int me, SD* T
 // candidate's key to a pick threshold, the candidate holding the maximum
 // excluded (it passes the threshold by construction): how close a decision
 // came to flipping when the keys carry an error.
-__device__ inline double select_rows_greedy(const int32_t* rs, const double* hk, int32_t* pick, int m, int rule,
+// K: the key type (double in the FP64 kernels; float in the mixed ones, whose
+// keys are FP32 values and are compared as such).
+template <class K>
+__device__ inline double select_rows_greedy(const int32_t* rs, const K* hk, int32_t* pick, int m, int rule,
                                             int j, int s, double tau, int lane, const int32_t* blk) {
-  double margin = DBL_MAX;
+  K margin = std::numeric_limits<K>::max();
   for (int r = lane; r < m; r += DIAF_WARP) pick[r] = 0;
   __syncwarp();
   for (int t = 0; t < s; ++t) {
-    double hm = -DBL_MAX;
+    K hm = -std::numeric_limits<K>::max();
     for (int r = lane; r < m; r += DIAF_WARP)
       if (!pick[r] && admissible_row(rule, rs[r], j, blk)) hm = dmax(hm, hk[r]);
     hm = warp_max(hm);
@@ -147,18 +152,18 @@ __device__ inline double select_rows_greedy(const int32_t* rs, const double* hk,
     for (int r = lane; r < m; r += DIAF_WARP)
       if (!pick[r] && admissible_row(rule, rs[r], j, blk) && hk[r] == hm) rmax = dmin(rmax, r);
     rmax = warp_min(rmax);
-    const double thr = hm - tau;
+    const K thr = hm - K(tau);
     int best = INT_MAX;
     for (int r = lane; r < m; r += DIAF_WARP)
       if (!pick[r] && admissible_row(rule, rs[r], j, blk)) {
-        if (r != rmax) margin = dmin(margin, fabs(hk[r] - thr));
+        if (r != rmax) margin = dmin(margin, (K)fabs(hk[r] - thr));
         if (hk[r] >= thr) best = dmin(best, r);
       }
     best = warp_min(best);
     if (lane == 0 && best < m) pick[best] = 1;
     __syncwarp();
   }
-  return warp_min(margin);
+  return (double)warp_min(margin);
 }
 
 // I_j from the picks (rule) or the fixed pattern; fills Is, Iloc, inI; returns
@@ -220,12 +225,14 @@ __device__ void finish_column(const ColArgs& a, int j, int k, int m, int l, int 
   using R = RealOf<SD>;
   if (do_phase) {
     SD ph = sc_real_s<SD>(R(1));
-    R vjj = jpos >= 0 ? sc_abs(vv[jpos]) : R(0);
+    const R vjj2 = jpos >= 0 ? sc_abs2(vv[jpos]) : R(0);
     R vn2 = R(0);
     for (int t = 0; t < l; ++t) vn2 += sc_abs2(vv[t]);
-    // v_jj counts as zero below the rounding level of the column
-    if (jpos >= 0 && vjj > R(64) * eps_of<R>() * sqrt(vn2)) {
-      ph = (R(1) / vjj) * sc_conj(vv[jpos]);
+    // v_jj counts as zero below the rounding level of the column (|v_jj| <= 64 eps ||v||)
+    const R zl = R(64) * eps_of<R>();
+    if (jpos >= 0 && vjj2 > zl * zl * vn2) {
+      if constexpr (ScalarInfo<SD>::cplx) ph = (R(1) / sqrt(vjj2)) * sc_conj(vv[jpos]);
+      else ph = vv[jpos] < R(0) ? sc_real_s<SD>(R(-1)) : sc_real_s<SD>(R(1));  // v_jj / |v_jj|, exactly
     } else {
       flags |= DIAF_FLAG_VJJ_ZERO;
       R amx = R(0);

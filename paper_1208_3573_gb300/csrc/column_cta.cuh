@@ -198,11 +198,13 @@ __device__ void cta_finish(const ColArgs& a, int j, int k, int m, int l, int jpo
   const int tid = threadIdx.x;
   if (do_phase) {
     S ph = sc_real_s<S>(R(1));
-    R vjj = jpos >= 0 ? sc_abs(vv[jpos]) : R(0);
+    const R vjj2 = jpos >= 0 ? sc_abs2(vv[jpos]) : R(0);
     R vn2 = R(0);
     for (int t = 0; t < l; ++t) vn2 += sc_abs2(vv[t]);
-    if (jpos >= 0 && vjj > R(64) * eps_of<R>() * sqrt(vn2)) {
-      ph = (R(1) / vjj) * sc_conj(vv[jpos]);
+    const R zl = R(64) * eps_of<R>();
+    if (jpos >= 0 && vjj2 > zl * zl * vn2) {
+      if constexpr (ScalarInfo<S>::cplx) ph = (R(1) / sqrt(vjj2)) * sc_conj(vv[jpos]);
+      else ph = vv[jpos] < R(0) ? sc_real_s<S>(R(-1)) : sc_real_s<S>(R(1));  // v_jj / |v_jj|, exactly
     } else {
       flags |= DIAF_FLAG_VJJ_ZERO;
       R amx = R(0);

@@ -68,8 +68,8 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
   S* Rs = Tw + L::kTile;                 // FP32 R of T, then R-hat (Jacobi works on it)
   S* Vj = Rs + KP * KMAX;                // FP32 Jacobi V
   S* rinv = Vj + KP * KMAX;              // FP32 reciprocal diagonal
-  double* hk = reinterpret_cast<double*>(rinv + KMAX);
-  double* sig = hk + MMAX;
+  float* hk = reinterpret_cast<float*>(rinv + KMAX);  // FP32 keys (MMAX; 2 MMAX floats reserved)
+  double* sig = reinterpret_cast<double*>(hk + 2 * MMAX);
   double* cn = sig + KMAX;               // column norms of the tile
   ColumnIdx ix = carve_idx<KMAX, MMAX>(reinterpret_cast<int32_t*>(cn + KMAX));
 

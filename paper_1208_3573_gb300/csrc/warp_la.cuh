@@ -325,8 +325,8 @@ __device__ void warp_col_norms(const S* G, int p, int q, double* sigma, int lane
 // T: tile of type ST (leading dimension LDT), Rm: k x k upper R (type S,
 // leading dimension LDR), Qout: rows of Q (type S, leading dimension LDT),
 // rinv: KMAX scratch for the reciprocal diagonal (pivots below piv give 0).
-template <class S, class ST, int LDT, int LDR>
-__device__ void warp_leverage_rows(const ST* T, const S* Rm, S* Qout, double* hk, S* rinv, int m, int k,
+template <class S, class ST, int LDT, int LDR, class K>
+__device__ void warp_leverage_rows(const ST* T, const S* Rm, S* Qout, K* hk, S* rinv, int m, int k,
                                    RealOf<S> piv, int lane) {
   using R = RealOf<S>;
   for (int c = lane; c < k; c += DIAF_WARP) rinv[c] = sc_recip_or_zero(Rm[c + c * LDR], piv);
@@ -340,7 +340,7 @@ __device__ void warp_leverage_rows(const ST* T, const S* Rm, S* Qout, double* hk
       Qout[r + c * LDT] = z;
       h += sc_abs2(z);
     }
-    hk[r] = (double)h;
+    hk[r] = (K)h;
   }
   __syncwarp();
 }

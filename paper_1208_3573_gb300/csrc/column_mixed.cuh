@@ -11,14 +11,18 @@
 //     makes x the smallest right singular vector to second order (repeated
 //     once when the relative gap is below 1e-2; columns with a gap below 1e-5
 //     go to the FP64 kernel).  w = x / ||x||, v = T(I_j,:) w.
-//   DIAF-Q: v0 = Q_I u / sigma from the FP32 Jacobi.  In FP64:
-//     X = (T^* T)^-1 T_I^* column by column (normal equations with the FP32 R
-//     as the solver plus one correction with the FP64 residual), the l x l
-//     matrix C = T_I X whose top eigenvector is the optimal v of eq. nocond
-//     (C = M_j^* M_j), one Rayleigh-quotient-iteration step from v0
-//     (mu = v0^* C v0, v = (C - mu)^-1 v0 normalised), and w = X v, the
-//     least-squares solution of eq. condwj.  Columns with l_j > 8 go to the
-//     FP64 kernel.
+//   DIAF-Q: the optimal v of eq. nocond is the top eigenvector of
+//     C = Q_I Q_I^* = T_I (T^* T)^-1 T_I^* (C = M_j^* M_j).  The FP32 Jacobi on
+//     Q_I gives C's eigenvectors U_c and values s_c^2 and v0 = U_max.  C v is
+//     applied in FP64 without forming C: y = (T^* T)^-1 T_I^* v by the FP32 R
+//     and corrections with the FP64 residual, C v = T_I y.  (When l < k the
+//     Jacobi runs on the smaller Q_I^*.)  With
+//     mu = v^* C v / v^* v and r = C v - mu v the same second-order correction
+//     as for DIAF-S, v <- v - sum_{c != max} U_c (U_c^* r) / (s_c^2 - mu)
+//     + r_perp / mu (r_perp: the part of r in C's null space), repeated until
+//     the predicted error is below 1e-11 (at most four times, else the column
+//     goes to FP64); w = (T^* T)^-1 T_I^* v, the least-squares solution of
+//     eq. condwj, is the y that follows v through the updates.
 //
 // A column goes to the FP64 kernel instead (appended to fb_list) when a
 // leverage-selection decision is closer to its threshold than the FP32 key
@@ -32,7 +36,8 @@ template <class S> struct DoubleOf;
 template <> struct DoubleOf<float> { using T = double; };
 template <> struct DoubleOf<Cx<float>> { using T = Cx<double>; };
 
-constexpr int kRRMax = 8;  // DIAF-Q: largest l_j refined through the explicit l x l matrix C
+constexpr int kQRefineMax = 4;  // DIAF-Q: most corrections before the column goes to FP64
+constexpr int kRRMax = 8;  // DIAF-Q: sizes of the refinement's scratch (KP x 8 and 2 x 64 scalars)
 
 template <class S, int KMAX, int MMAX, int ALG>
 struct MixedLayout {
@@ -40,7 +45,7 @@ struct MixedLayout {
   static constexpr int LDT = MMAX + 1;  // odd leading dimensions: no bank conflicts between columns
   static constexpr int KP = KMAX + 1;
   static constexpr int kTile = LDT * KMAX;
-  static constexpr int kRR = ALG == DIAF_ALG_Q ? kRRMax : 0;  // DIAF-Q only: X, C, C - mu I
+  static constexpr int kRR = ALG == DIAF_ALG_Q ? kRRMax : 0;  // DIAF-Q only: scratch for C v, r, coefficients
   static constexpr size_t raw() {
     return sizeof(SD) * (kTile + 3 * KMAX + 2 * MMAX + kRR * KP + 2 * kRR * kRR) +
            sizeof(S) * (kTile + 2 * KP * KMAX + KMAX) +
@@ -61,9 +66,9 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
   SD* gg = wv + KMAX;                    // k-vector scratch
   SD* vv = gg + KMAX;                    // v (MMAX)
   SD* zz = vv + MMAX;                    // m-vector scratch
-  SD* Xs = zz + MMAX;                    // DIAF-Q: X = (T^* T)^-1 T_I^* (KP x kRR)
-  SD* Cs = Xs + kRR * KP;                // DIAF-Q: C = T_I X (kRRMax x kRRMax)
-  SD* Ms = Cs + kRR * kRR;               // DIAF-Q: C - mu I, eliminated in place
+  SD* Xs = zz + MMAX;                    // DIAF-Q scratch: C v (KP x kRR >= MMAX)
+  SD* Cs = Xs + kRR * KP;                // DIAF-Q scratch: correction coefficients (as FP32)
+  SD* Ms = Cs + kRR * kRR;               // DIAF-Q scratch: r = C v - mu v (as FP32)
   S* Tw = reinterpret_cast<S*>(Ms + kRR * kRR);  // FP32 working tile
   S* Rs = Tw + L::kTile;                 // FP32 R of T, then R-hat (Jacobi works on it)
   S* Vj = Rs + KP * KMAX;                // FP32 Jacobi V
@@ -247,106 +252,165 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     rank_thr = 1e-14 * smax;  // tested on res = ||A-hat w|| in finish_column
     __syncwarp();
   } else {
-    // ---- FP32 Jacobi on Q_I (FP32 rows of Q = T R^-1 in Tw)
-    if (l > kRRMax) { hand_back(5); return; }
-    compact_rows<S, LDT>(Tw, ix.Iloc, l, k, lane);
-    int sw = warp_jacobi<S, LDT, KP, KMAX, true>(Tw, l, k, Vj, lane);
+    // ---- eigenpairs of C = Q_I Q_I^* by an FP32 one-sided Jacobi (the rows of
+    // Q = T R^-1 are in Tw).  l >= k: on Q_I itself, Q_I V = U S.  l < k: on
+    // the smaller M = Q_I^* (k x l), whose right singular vectors are C's
+    // eigenvectors.  Either way column c < kc of Tw ends as U_c s_c.
+    int kc = k, sw;
+    if (l < k && l <= kRRMax) {
+      S* M = reinterpret_cast<S*>(Xs);  // k x l, leading dimension KP
+      for (int i = lane; i < k * l; i += DIAF_WARP) {
+        const int c = i % k, t = i / k, r = ix.Iloc[t];
+        M[c + t * KP] = r >= 0 ? sc_conj(Tw[r + c * LDT]) : sc_zero<S>();
+      }
+      __syncwarp();
+      sw = warp_jacobi<S, KP, KP, kRRMax, true>(M, k, l, Vj, lane);
+      warp_col_norms<S, KP>(M, k, l, sig, lane);
+      for (int i = lane; i < l * l; i += DIAF_WARP) {
+        const int t = i % l, c = i / l;
+        Tw[t + c * LDT] = R(sig[c]) * Vj[t + c * KP];
+      }
+      __syncwarp();
+      kc = l;
+    } else {
+      compact_rows<S, LDT>(Tw, ix.Iloc, l, k, lane);
+      sw = warp_jacobi<S, LDT, KP, KMAX, true>(Tw, l, k, Vj, lane);
+      warp_col_norms<S, LDT>(Tw, l, k, sig, lane);
+    }
     if (sw < 0) flags |= DIAF_FLAG_JACOBI_NOCONV;
-    warp_col_norms<S, LDT>(Tw, l, k, sig, lane);
+    DIAF_PHASE(7);
     int imax = 0;
     double smax = sig[0];
-    for (int c = 1; c < k; ++c) if (sig[c] > smax) { smax = sig[c]; imax = c; }
+    for (int c = 1; c < kc; ++c) if (sig[c] > smax) { smax = sig[c]; imax = c; }
     double snext = 0.0;
-    for (int c = 0; c < k; ++c) if (c != imax) snext = dmax(snext, sig[c]);
+    for (int c = 0; c < kc; ++c) if (c != imax) snext = dmax(snext, sig[c]);
     if (!(smax > 0.0)) { hand_back(6); return; }
-    if (k > 1 && (smax - snext) <= 1e-6 * smax) flags |= DIAF_FLAG_DEGENERATE;
-    // one Rayleigh-quotient step refines v0 to FP64 accuracy only when v0's
-    // FP32 error (about eps_32 / relative gap) is small against the gap to the
-    // second eigenvalue of Q_I Q_I^*: closer gaps go to the FP64 kernel
-    if (k > 1 && (smax * smax - snext * snext) < 1e-3 * smax * smax) { hand_back(4); return; }
-    for (int t = lane; t < l; t += DIAF_WARP) vv[t] = sc_cast<SD>(Tw[t + imax * LDT]);
-    for (int c = lane; c < k; c += DIAF_WARP) rinvD[c] = sc_recip_or_zero(sc_cast<SD>(Rs[c + c * KP]), 0.0);
+    if (kc > 1 && (smax - snext) <= 1e-6 * smax) flags |= DIAF_FLAG_DEGENERATE;
+    // the correction below converges from v0's FP32 error (about eps_32 / relative
+    // gap) only when that error is small against the gap: closer gaps go to FP64
+    const double gap2 = smax * smax - snext * snext;
+    if (kc > 1 && gap2 < 1e-3 * smax * smax) { hand_back(4); return; }
+    // the FP32 factors perturb C (norm <= 1) by about eps_32 kappa(T), so each
+    // correction shrinks v's error by about rho = eps_32 kappa(T) / gap (a Newton
+    // step with an FP32 Jacobian): iterate until the predicted error rho ||dv||
+    // is below 1e-11 ||v||, at most kQRefineMax times
+    const double rho = 8.0 * 1.1920929e-7 * (double)kap / gap2;
+    {
+      const RealOf<SD> inv = RealOf<SD>(1) / RealOf<SD>(smax);
+      for (int t = lane; t < l; t += DIAF_WARP) vv[t] = inv * sc_cast<SD>(Tw[t + imax * LDT]);
+    }
     __syncwarp();
-    // X(:,t) = (T^* T)^-1 T(I_t,:)^*: one solve with the FP32 R, one correction
-    for (int t = 0; t < l; ++t) {
-      const int rI = ix.Iloc[t];
-      const SD b = (lane < k && rI >= 0) ? sc_conj(Ts[rI + lane * LDT]) : sc_zero<SD>();
-      SD x = warp_solve_RhR<SD, S, KP>(Rs, rinvD, b, k, lane);
-      if (lane < k) gg[lane] = x;
+    // lane c < k: (T^* T)^-1 T_I^* x for an l-vector x, with the FP32 factor
+    // in FP32 arithmetic (a first guess, or the image of a small update)
+    auto solve32 = [&](const SD* x) -> SD {
+      SD b = sc_zero<SD>();
+      if (lane < k)
+        for (int t = 0; t < l; ++t) {
+          const int rI = ix.Iloc[t];
+          if (rI >= 0) b += sc_cmul(Ts[rI + lane * LDT], x[t]);
+        }
+      return sc_cast<SD>(warp_solve_RhR<S, S, KP>(Rs, rinv, sc_cast<S>(b), k, lane));
+    };
+    // one correction of y for the current v: the residual T^* (v_I - T y) on
+    // the FP64 tile (v_I: v on the rows of I_j, zero elsewhere), solved with
+    // the FP32 factor; it shrinks y's error by about eps_32 kappa(T)^2
+    auto correct = [&](SD y) -> SD {
+      if (lane < k) gg[lane] = y;
       __syncwarp();
       for (int r = lane; r < m; r += DIAF_WARP) {
-        SD z = sc_zero<SD>();
+        const int t = ix.inI[r];
+        SD z = t >= 0 ? vv[t] : sc_zero<SD>();
         for (int q = 0; q < k; ++q) z -= Ts[r + q * LDT] * gg[q];
         zz[r] = z;
       }
       __syncwarp();
-      SD rn = b;
+      SD rn = sc_zero<SD>();
       if (lane < k)
         for (int r = 0; r < m; ++r) rn += sc_cmul(Ts[r + lane * LDT], zz[r]);
-      x += warp_solve_RhR<SD, S, KP>(Rs, rinvD, rn, k, lane);
-      if (lane < k) Xs[lane + t * KP] = x;
+      y += sc_cast<SD>(warp_solve_RhR<S, S, KP>(Rs, rinv, sc_cast<S>(rn), k, lane));
       __syncwarp();
-    }
-    // C = T_I X (Hermitian positive semidefinite, l x l)
-    for (int e = lane; e < l * l; e += DIAF_WARP) {
-      const int s2 = e % l, t = e / l, rI = ix.Iloc[s2];
-      SD c = sc_zero<SD>();
-      if (rI >= 0)
-        for (int q = 0; q < k; ++q) c += Ts[rI + q * LDT] * Xs[q + t * KP];
-      Cs[s2 + t * kRRMax] = c;
-    }
-    __syncwarp();
-    // one Rayleigh-quotient-iteration step from v0 (lane 0; l <= 8)
-    if (lane == 0) {
-      using RD = RealOf<SD>;
-      RD n2 = RD(0);
-      for (int t = 0; t < l; ++t) n2 += sc_abs2(vv[t]);
-      const RD ninv = RD(1) / sqrt(n2);
-      SD y[kRRMax];
-      for (int t = 0; t < l; ++t) y[t] = ninv * vv[t];
-      RD mu = RD(0), cmax = RD(0);
-      for (int s2 = 0; s2 < l; ++s2)
-        for (int t = 0; t < l; ++t) {
-          const SD c = Cs[s2 + t * kRRMax];
-          mu += sc_real(sc_cmul(y[s2], c * y[t]));
-          cmax = dmax(cmax, sc_abs(c));
-        }
-      for (int s2 = 0; s2 < l; ++s2)
-        for (int t = 0; t < l; ++t)
-          Ms[s2 + t * kRRMax] = Cs[s2 + t * kRRMax] - (s2 == t ? sc_real_s<SD>(mu) : sc_zero<SD>());
-      // Gaussian elimination with partial pivoting; an exactly singular pivot
-      // (v0 already an eigenvector) is replaced by eps ||C||
-      const RD tinyp = eps_of<RD>() * (cmax > RD(0) ? cmax : RD(1));
-      for (int c = 0; c < l; ++c) {
-        int pr = c;
-        RD pa = sc_abs(Ms[c + c * kRRMax]);
-        for (int r = c + 1; r < l; ++r) {
-          RD ar = sc_abs(Ms[r + c * kRRMax]);
-          if (ar > pa) { pa = ar; pr = r; }
-        }
-        if (pr != c) {
-          for (int t = 0; t < l; ++t) {
-            SD tmp = Ms[c + t * kRRMax]; Ms[c + t * kRRMax] = Ms[pr + t * kRRMax]; Ms[pr + t * kRRMax] = tmp;
-          }
-          SD tmp = y[c]; y[c] = y[pr]; y[pr] = tmp;
-        }
-        if (!(sc_abs(Ms[c + c * kRRMax]) > tinyp)) Ms[c + c * kRRMax] = sc_real_s<SD>(tinyp);
-        const SD dinv = sc_recip_or_zero(Ms[c + c * kRRMax], RD(0));
-        for (int r = c + 1; r < l; ++r) {
-          const SD f = Ms[r + c * kRRMax] * dinv;
-          for (int t = c + 1; t < l; ++t) Ms[r + t * kRRMax] -= f * Ms[c + t * kRRMax];
-          y[r] -= f * y[c];
-        }
+      return y;
+    };
+    // y = (T^* T)^-1 T_I^* v (lane c holds y_c): C v = T_I y, and for the final
+    // v this y is the least-squares w of eq. condwj.  From scratch once (FP32
+    // solve + two corrections); afterwards y follows each update dv of v by the
+    // FP32 solve for dv (dv is small) plus one correction.
+    SD y = solve32(vv);
+    y = correct(y);
+    y = correct(y);
+    SD* cvv = Xs;                              // C v, then the update dv (l)
+    S* rl = reinterpret_cast<S*>(Ms);          // r = C v - mu v in FP32 (l)
+    S* ac = reinterpret_cast<S*>(Cs);          // U_c^* r / (s_c^2 - mu) (kc)
+    S* bc = ac + KMAX;                         // U_c^* r (kc)
+    bool converged = false;
+    int it = 0;
+    while (true) {
+      if (lane < k) gg[lane] = y;
+      __syncwarp();
+      RealOf<SD> vcv = 0, vvn = 0;
+      for (int t = lane; t < l; t += DIAF_WARP) {
+        SD cv = sc_zero<SD>();
+        const int rI = ix.Iloc[t];
+        if (rI >= 0)
+          for (int q = 0; q < k; ++q) cv += Ts[rI + q * LDT] * gg[q];
+        cvv[t] = cv;
+        vcv += sc_real(sc_cmul(vv[t], cv));
+        vvn += sc_abs2(vv[t]);
       }
-      for (int c = l - 1; c >= 0; --c) {
-        SD acc = y[c];
-        for (int t = c + 1; t < l; ++t) acc -= Ms[c + t * kRRMax] * y[t];
-        y[c] = acc * sc_recip_or_zero(Ms[c + c * kRRMax], RD(0));
+      vcv = warp_sum(vcv);
+      vvn = warp_sum(vvn);
+      const double mu = (double)vcv / (double)vvn;
+      for (int t = lane; t < l; t += DIAF_WARP) rl[t] = sc_cast<S>(cvv[t] - RealOf<SD>(mu) * vv[t]);
+      __syncwarp();
+      for (int c = lane; c < kc; c += DIAF_WARP) {  // projections on U_c = Tw(:,c) / s_c
+        const R sc = R(sig[c]);
+        S p = sc_zero<S>();
+        if (sc > R(0))
+          for (int t = 0; t < l; ++t) p += sc_cmul(Tw[t + c * LDT], rl[t]);
+        p = sc > R(0) ? (R(1) / sc) * p : sc_zero<S>();
+        bc[c] = p;
+        ac[c] = (c == imax || !(sc > R(0))) ? sc_zero<S>() : (R(1) / (sc * sc - R(mu))) * p;
       }
-      RD yn2 = RD(0);
-      for (int t = 0; t < l; ++t) yn2 += sc_abs2(y[t]);
-      const RD yinv = RD(1) / sqrt(yn2);
-      for (int t = 0; t < l; ++t) vv[t] = yinv * y[t];
+      __syncwarp();
+      // v <- v - sum_{c != max} U_c a_c + r_perp / mu  (r_perp: the part of r outside
+      // the span of the U_c, C's null space when Q_I has rank below l)
+      R dn = 0;
+      for (int t = lane; t < l; t += DIAF_WARP) {
+        S dv = sc_zero<S>(), rin = sc_zero<S>();
+        for (int c = 0; c < kc; ++c) {
+          const R sc = R(sig[c]);
+          if (!(sc > R(0))) continue;
+          const S u = (R(1) / sc) * Tw[t + c * LDT];
+          dv += u * ac[c];
+          rin += u * bc[c];
+        }
+        const S rperp = rl[t] - rin;
+        const S step = (R(1) / R(mu)) * rperp - dv;
+        dn += sc_abs2(step);
+        const SD stepd = sc_cast<SD>(step);
+        vv[t] += stepd;
+        cvv[t] = stepd;
+      }
+      dn = warp_sum(dn);
+      converged = rho * rho * (double)dn <= 1e-22 * (double)vvn;
+      __syncwarp();
+      y += solve32(cvv);
+      ++it;
+      if (converged || it == kQRefineMax) break;
+      y = correct(y);
+    }
+#ifdef DIAF_PHASE_TIMING
+    if (lane == 0 && a.phase) atomicAdd(&a.phase[20], (unsigned long long)it);
+#endif
+    DIAF_PHASE(8);
+    if (!converged) { hand_back(5); return; }
+    RealOf<SD> vn = 0;
+    for (int t = lane; t < l; t += DIAF_WARP) vn += sc_abs2(vv[t]);
+    vn = warp_sum(vn);
+    {
+      const RealOf<SD> inv = RealOf<SD>(1) / sqrt(vn);
+      for (int t = lane; t < l; t += DIAF_WARP) vv[t] = inv * vv[t];
+      if (lane < k) wv[lane] = inv * y;  // w: eq. condwj for the normalised v
     }
     __syncwarp();
     // stabilised DIAF-Q (Sec. 3.2): the FP64 kernel takes every column at or
@@ -355,13 +419,6 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
       hand_back(7);
       return;
     }
-    // w = X v (eq. condwj for the refined v)
-    if (lane < k) {
-      SD x = sc_zero<SD>();
-      for (int t = 0; t < l; ++t) x += Xs[lane + t * KP] * vv[t];
-      wv[lane] = x;
-    }
-    __syncwarp();
   }
   DIAF_PHASE(9);
   finish_column<SD, LDT>(a, j, k, m, l, jpos, Ts, wv, vv, ix, flags, true, lane, rank_thr);

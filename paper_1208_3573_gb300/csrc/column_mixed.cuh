@@ -54,6 +54,24 @@ struct MixedLayout {
   static constexpr size_t bytes() { return (raw() + 15) / 16 * 16; }
 };
 
+// lane c < k: (T^* z)_c in FP64 over the m tile rows.  Tiles of up to 16
+// columns split the rows between the two half-warps (alternate rows, one
+// shuffle to combine), halving the FP64 instructions of the product.
+template <class SD, int LDT, int KMAX>
+__device__ __forceinline__ SD tile_adj_mul(const SD* Ts, const SD* zz, int m, int k, int lane) {
+  SD g = sc_zero<SD>();
+  if constexpr (KMAX <= 16) {
+    const int c = lane & 15;
+    if (c < k)
+      for (int r = lane >> 4; r < m; r += 2) g += sc_cmul(Ts[r + c * LDT], zz[r]);
+    g += shfl_xor(g, 16);
+  } else {
+    if (lane < k)
+      for (int r = 0; r < m; ++r) g += sc_cmul(Ts[r + lane * LDT], zz[r]);
+  }
+  return g;
+}
+
 template <class S, int KMAX, int MMAX, int ALG>
 __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem, int lane) {
   using SD = typename DoubleOf<S>::T;
@@ -177,7 +195,13 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
       Rs[r + c * KP] = (r <= c) ? Tw[r + c * LDT] : sc_zero<S>();
     }
     __syncwarp();
-    int sw = warp_jacobi<S, KP, KP, KMAX, true>(Rs, k, k, Vj, lane);
+    // register-resident pairs for the warp-per-column tiles of up to 16
+    // columns; the wider tiles (fewer warps per SM) keep the plain form
+    int sw;
+    if constexpr (KMAX <= 16)
+      sw = warp_jacobi_reg<S, KP, KP, KMAX, KMAX>(Rs, k, k, Vj, reinterpret_cast<R*>(sig), lane);
+    else
+      sw = warp_jacobi<S, KP, KP, KMAX, true>(Rs, k, k, Vj, lane);
     if (sw < 0) flags |= DIAF_FLAG_JACOBI_NOCONV;
 #ifdef DIAF_PHASE_TIMING
     if (lane == 0 && a.phase) atomicAdd(&a.phase[20], (unsigned long long)(sw < 0 ? kMaxSweeps : sw));
@@ -214,9 +238,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
         zz[r] = z;
       }
       __syncwarp();
-      SD g = sc_zero<SD>();  // (H x)_q = (A-hat^* (A-hat x))_q
-      if (lane < k)
-        for (int r = 0; r < m; ++r) g += sc_cmul(Ts[r + lane * LDT], zz[r]);
+      const SD g = tile_adj_mul<SD, LDT, KMAX>(Ts, zz, m, k, lane);  // (H x)_q = (A-hat^* (A-hat x))_q
       const double xg = warp_sum(lane < k ? (double)sc_real(sc_cmul(x, g)) : 0.0);
       const double xx = warp_sum(lane < k ? (double)sc_abs2(x) : 0.0);
       const double d = xg / xx;
@@ -264,7 +286,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
         M[c + t * KP] = r >= 0 ? sc_conj(Tw[r + c * LDT]) : sc_zero<S>();
       }
       __syncwarp();
-      sw = warp_jacobi<S, KP, KP, kRRMax, true>(M, k, l, Vj, lane);
+      sw = warp_jacobi_reg<S, KP, KP, kRRMax, KMAX>(M, k, l, Vj, reinterpret_cast<R*>(sig), lane);
       warp_col_norms<S, KP>(M, k, l, sig, lane);
       for (int i = lane; i < l * l; i += DIAF_WARP) {
         const int t = i % l, c = i / l;
@@ -324,9 +346,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
         zz[r] = z;
       }
       __syncwarp();
-      SD rn = sc_zero<SD>();
-      if (lane < k)
-        for (int r = 0; r < m; ++r) rn += sc_cmul(Ts[r + lane * LDT], zz[r]);
+      const SD rn = tile_adj_mul<SD, LDT, KMAX>(Ts, zz, m, k, lane);
       y += sc_cast<SD>(warp_solve_RhR<S, S, KP>(Rs, rinv, sc_cast<S>(rn), k, lane));
       __syncwarp();
       return y;

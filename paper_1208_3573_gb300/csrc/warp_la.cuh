@@ -308,6 +308,131 @@ __device__ int warp_jacobi(S* G, int p, int q, S* V, int lane) {
   return -1;
 }
 
+// The same Jacobi for reduced-precision callers whose result is refined
+// afterwards (PREDICT behaviour), tuned for small tiles: p <= PMAX rows, so a
+// lane keeps its share of the pair's two columns in registers between the
+// inner product and the rotation, and the squared column norms live in nrm
+// (q scratch values of the real type): exact at the start of every sweep,
+// then updated per rotation by alpha' = alpha - t |gamma|,
+// beta' = beta + t |gamma| (the rotated pair's norms in exact arithmetic), so
+// a pair needs only gamma = g_a^* g_b.
+template <class S, int LDG, int LDV, int QMAX, int PMAX>
+__device__ int warp_jacobi_reg(S* G, int p, int q, S* V, RealOf<S>* nrm, int lane) {
+  using R = RealOf<S>;
+  constexpr int kPairsMax = QMAX / 2;
+  constexpr int kGroups = kPairsMax >= 32 ? 32 : (kPairsMax >= 16 ? 16 : (kPairsMax >= 8 ? 8 : (kPairsMax >= 4 ? 4 : 2)));
+  constexpr int LPP = DIAF_WARP / kGroups;
+  constexpr int PER = (PMAX + LPP - 1) / LPP;
+  constexpr int VPER = (QMAX + LPP - 1) / LPP;
+  for (int i = lane; i < q * q; i += DIAF_WARP) {
+    int r = i % q, c = i / q;
+    V[r + c * LDV] = (r == c) ? sc_real_s<S>(R(1)) : sc_zero<S>();
+  }
+  R nf2 = R(0);
+  for (int i = lane; i < p * q; i += DIAF_WARP) nf2 += sc_abs2(G[(i % p) + (i / p) * LDG]);
+  nf2 = warp_sum(nf2);
+  const R tol = R(p > 1 ? p : 1) * eps_of<R>();
+  const R tol2 = tol * tol;
+  const R tiny = tol2 * nf2;
+  __syncwarp();
+  if (q < 2) return 1;
+  const int qq = (q + 1) & ~1;
+  const int npairs = qq / 2;
+  const int grp = lane / LPP, sub = lane % LPP;
+  const int L = qq - 1;
+  for (int sweep = 1; sweep <= kMaxSweeps; ++sweep) {
+    for (int c = lane; c < q; c += DIAF_WARP) {
+      R s2 = R(0);
+      for (int i = 0; i < p; ++i) s2 += sc_abs2(G[i + c * LDG]);
+      nrm[c] = s2;
+    }
+    __syncwarp();
+    bool rotated = false, large = false;
+    for (int rnd = 0; rnd < L; ++rnd) {
+      for (int pr0 = 0; pr0 < npairs; pr0 += kGroups) {
+        const int pr = pr0 + grp;
+        int a = -1, b = -1;
+        if (pr < npairs) {
+          int pb = qq - 1 - pr;
+          int ea = pr - 1 + rnd, eb = pb - 1 + rnd;
+          if (ea >= L) ea -= L;
+          if (eb >= L) eb -= L;
+          a = pr == 0 ? 0 : 1 + ea;
+          b = 1 + eb;
+          if (a > b) { int t = a; a = b; b = t; }
+          if (b >= q) a = -1;
+        }
+        const bool act = a >= 0;
+        S xa[PER], xb[PER];
+        S ga = sc_zero<S>();
+        S* ca = G + (act ? a : 0) * LDG;
+        S* cb = G + (act ? b : 0) * LDG;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+          const int i = sub + u * LPP;
+          xa[u] = sc_zero<S>();
+          xb[u] = sc_zero<S>();
+          if (act && i < p) {
+            xa[u] = ca[i];
+            xb[u] = cb[i];
+            ga += sc_cmul(xa[u], xb[u]);
+          }
+        }
+        ga = group_sum<LPP>(ga);
+        const R al = act ? nrm[a] : R(0), be = act ? nrm[b] : R(0);
+        const R ag2 = sc_abs2(ga);
+        const bool rot = act && al > tiny && be > tiny && ag2 > R(0) && ag2 > tol2 * (al * be);
+        __syncwarp();
+        if (rot) {
+          rotated = true;
+          if (ag2 >= tol * (al * be)) large = true;
+          R ag;
+          S eph;
+          if constexpr (ScalarInfo<S>::cplx) {
+            R ri = rsqrt_r(ag2);
+            ag = ag2 * ri;
+            eph = ri * sc_conj(ga);
+          } else {
+            ag = sc_abs(ga);
+            eph = sc_unit(ga);
+          }
+          const R d = be - al;
+          const R t = div_r(copysign(R(2) * ag, d), fabs(d) + sqrt(d * d + R(4) * ag2));
+          const R cs = rsqrt_r(R(1) + t * t), sn = cs * t;
+#pragma unroll
+          for (int u = 0; u < PER; ++u) {
+            const int i = sub + u * LPP;
+            if (i < p) {
+              const S x = xa[u], y = eph * xb[u];
+              ca[i] = cs * x - sn * y;
+              cb[i] = sn * x + cs * y;
+            }
+          }
+          S* va = V + a * LDV;
+          S* vb = V + b * LDV;
+#pragma unroll
+          for (int u = 0; u < VPER; ++u) {
+            const int i = sub + u * LPP;
+            if (i < q) {
+              const S x = va[i], y = eph * vb[i];
+              va[i] = cs * x - sn * y;
+              vb[i] = sn * x + cs * y;
+            }
+          }
+          if (sub == 0) {
+            nrm[a] = al - t * ag;
+            nrm[b] = be + t * ag;
+          }
+        }
+        __syncwarp();
+      }
+    }
+    if (!__any_sync(DIAF_FULL, rotated)) return sweep;
+    if (!__any_sync(DIAF_FULL, large)) return sweep;
+  }
+  return -1;
+}
+
 // column norms of G (p x q) into sigma[c] (double)
 template <class S, int LDG>
 __device__ void warp_col_norms(const S* G, int p, int q, double* sigma, int lane) {

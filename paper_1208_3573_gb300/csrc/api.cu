@@ -332,6 +332,16 @@ diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_
     DIAF_CU(pool.get(&np.fb_list, (size_t)kNumBuckets * n));
     DIAF_CU(pool.get(&np.fb_count, kNumBuckets));
     DIAF_CU(F->alloc(&F->fb_counts, kNumBuckets));
+    // the warp buckets' FP64 tiles: one per warp of the larger persistent grid
+    // (the buckets run one after the other on the stream)
+    size_t tiles = 0;
+    for (int b = 0; b < 2; ++b) {
+      if (np.h_bc[b] == 0) continue;
+      const size_t t = np.cplx ? mixed_tile_scratch_c64(b, alg, np.h_bc[b], np.wpb[b])
+                               : mixed_tile_scratch_f32(b, alg, np.h_bc[b], np.wpb[b]);
+      if (t > tiles) tiles = t;
+    }
+    if (tiles > 0) DIAF_CU(pool.get((char**)&ca.tile_scratch, tiles));
   }
   const int bl = kNumBuckets - 1;
   if (np.h_bc[bl] > 0) {

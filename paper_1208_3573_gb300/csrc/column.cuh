@@ -62,6 +62,7 @@ struct ColArgs {
   uint32_t* flags;
   uint32_t* status;
   unsigned long long* phase;  // profiling builds only: per-phase cycle counters (or null)
+  void* tile_scratch;         // mixed warp kernels: one FP64 tile per resident warp (global memory)
 };
 
 // ------------------------------------------------------------------ shared steps

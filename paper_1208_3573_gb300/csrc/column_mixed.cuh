@@ -46,8 +46,16 @@ struct MixedLayout {
   static constexpr int KP = KMAX + 1;
   static constexpr int kTile = LDT * KMAX;
   static constexpr int kRR = ALG == DIAF_ALG_Q ? kRRMax : 0;  // DIAF-Q only: scratch for C v, r, coefficients
+  // The FP64 tile of the complex and the wide tiles lives in global memory
+  // (ColArgs::tile_scratch, one per resident warp, mostly L1/L2 hits): their
+  // shared memory then holds only the FP32 working set and the vectors, which
+  // raises the warps resident per SM (measured: 11 -> 18 for complex 16-column
+  // tiles, 6 -> 11 for real 32-column ones).  The real 16-column tile keeps it
+  // in shared memory: there the extra warps did not pay for the slower loads.
+  static constexpr bool kTileGlobal = sizeof(S) > 4 || KMAX > 16;
+  static constexpr size_t tile_bytes() { return kTileGlobal ? sizeof(SD) * kTile : 0; }
   static constexpr size_t raw() {
-    return sizeof(SD) * (kTile + 3 * KMAX + 2 * MMAX + kRR * KP + 2 * kRR * kRR) +
+    return sizeof(SD) * ((kTileGlobal ? 0 : kTile) + 3 * KMAX + 2 * MMAX + kRR * KP + 2 * kRR * kRR) +
            sizeof(S) * (kTile + 2 * KP * KMAX + KMAX) +
            sizeof(double) * (MMAX + 2 * KMAX) + idx_bytes<KMAX, MMAX>();
   }
@@ -73,13 +81,14 @@ __device__ __forceinline__ SD tile_adj_mul(const SD* Ts, const SD* zz, int m, in
 }
 
 template <class S, int KMAX, int MMAX, int ALG>
-__device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem, int lane) {
+__device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
+                                   typename DoubleOf<S>::T* Ts, int lane) {
   using SD = typename DoubleOf<S>::T;
   using R = RealOf<S>;
   using L = MixedLayout<S, KMAX, MMAX, ALG>;
   constexpr int LDT = L::LDT, KP = L::KP, kRR = L::kRR;
-  SD* Ts = reinterpret_cast<SD*>(smem);  // FP64 tile (LDT x KMAX)
-  SD* rinvD = Ts + L::kTile;             // FP64 reciprocal diagonal of the FP32 factor
+  // Ts: the FP64 tile (LDT x KMAX), in global or shared memory (kTileGlobal)
+  SD* rinvD = reinterpret_cast<SD*>(smem) + (L::kTileGlobal ? 0 : L::kTile);  // FP64 reciprocal diagonal of the FP32 factor
   SD* wv = rinvD + KMAX;                 // w
   SD* gg = wv + KMAX;                    // k-vector scratch
   SD* vv = gg + KMAX;                    // v (MMAX)
@@ -449,13 +458,17 @@ template <class S, int KMAX, int MMAX, int ALG>
 __global__ void column_mixed_kernel(ColArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned char* smem = smem_raw + warp * MixedLayout<S, KMAX, MMAX, ALG>::bytes();
+  using L = MixedLayout<S, KMAX, MMAX, ALG>;
+  unsigned char* smem = smem_raw + warp * L::bytes();
+  typename L::SD* Ts = L::kTileGlobal ? reinterpret_cast<typename L::SD*>(a.tile_scratch) +
+                                            (size_t)(blockIdx.x * (blockDim.x >> 5) + warp) * L::kTile
+                                      : reinterpret_cast<typename L::SD*>(smem);
   const int count = *a.list_count;
   while (true) {
     int idx = 0;
     if (lane == 0) idx = atomicAdd(a.work_counter, 1);
     idx = __shfl_sync(DIAF_FULL, idx, 0);
     if (idx >= count) break;
-    solve_column_mixed<S, KMAX, MMAX, ALG>(a, a.list[idx], smem, lane);
+    solve_column_mixed<S, KMAX, MMAX, ALG>(a, a.list[idx], smem, Ts, lane);
   }
 }

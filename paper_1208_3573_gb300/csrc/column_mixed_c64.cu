@@ -11,3 +11,14 @@ cudaError_t launch_columns_mixed_c64(int bucket, int alg, const ColArgs& a, int 
   }
   return cudaErrorNotSupported;
 }
+
+size_t mixed_tile_scratch_c64(int bucket, int alg, int count_hint, int wpb) {
+  if (alg == DIAF_ALG_S) {
+    if (bucket == 0) return MixedLaunch<Cx<float>, 16, 32, DIAF_ALG_S>::scratch(count_hint, wpb);
+    if (bucket == 1) return MixedLaunch<Cx<float>, 32, 64, DIAF_ALG_S>::scratch(count_hint, wpb);
+  } else {
+    if (bucket == 0) return MixedLaunch<Cx<float>, 16, 32, DIAF_ALG_Q>::scratch(count_hint, wpb);
+    if (bucket == 1) return MixedLaunch<Cx<float>, 32, 64, DIAF_ALG_Q>::scratch(count_hint, wpb);
+  }
+  return 0;
+}

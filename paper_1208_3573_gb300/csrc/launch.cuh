@@ -26,10 +26,19 @@ cudaError_t launch_columns_cta_mixed(int dtype, int alg, const ColArgs& a, const
 // its persistent grid (resident CTAs, capped by count); 0 when not available
 int cta_columns_grid_mixed(int dtype, int alg, int ldm, int count);
 
-// Persistent grid sized by occupancy; `per_warp` bytes of shared memory per warp.
+// Bytes of the mixed warp kernels' global tile scratch (ColArgs::tile_scratch)
+// for this bucket's launch: one FP64 tile per warp of the persistent grid
+// (0: no mixed kernel for the bucket, or nothing to do).
+size_t mixed_tile_scratch_f32(int bucket, int alg, int count_hint, int wpb);
+size_t mixed_tile_scratch_c64(int bucket, int alg, int count_hint, int wpb);
+
+// Persistent grid sized by occupancy; `per_warp` bytes of shared memory per
+// warp.  Sets *grid and *wpb (the block's warps); the launch below uses it.
 template <class Kern>
-cudaError_t launch_persistent_warps(Kern kern, size_t per_warp, size_t& configured, const ColArgs& a, int count_hint,
-                                    int wpb_req, cudaStream_t s) {
+cudaError_t persistent_warps_shape(Kern kern, size_t per_warp, size_t& configured, int count_hint, int wpb_req,
+                                   int* grid_out, int* wpb_out) {
+  *grid_out = 0;
+  *wpb_out = 1;
   if (count_hint <= 0) return cudaSuccess;
   // warps per block: the most warps resident per SM (228 KB of shared memory,
   // 1 KB reserved per block), ties to the smaller block -- unless requested
@@ -54,7 +63,18 @@ cudaError_t launch_persistent_warps(Kern kern, size_t per_warp, size_t& configur
   if (per_sm < 1) per_sm = 1;
   int grid = ceil_div(count_hint, wpb);
   if (grid > sms * per_sm) grid = sms * per_sm;
-  kern<<<grid, wpb * 32, smem, s>>>(a);
+  *grid_out = grid;
+  *wpb_out = wpb;
+  return cudaSuccess;
+}
+
+template <class Kern>
+cudaError_t launch_persistent_warps(Kern kern, size_t per_warp, size_t& configured, const ColArgs& a, int count_hint,
+                                    int wpb_req, cudaStream_t s) {
+  int grid = 0, wpb = 1;
+  cudaError_t e = persistent_warps_shape(kern, per_warp, configured, count_hint, wpb_req, &grid, &wpb);
+  if (e != cudaSuccess || grid == 0) return e;
+  kern<<<grid, wpb * 32, per_warp * wpb, s>>>(a);
   DIAF_COUNT_LAUNCH();
   return cudaGetLastError();
 }
@@ -67,8 +87,23 @@ cudaError_t launch_warp_columns(const ColArgs& a, int count_hint, int wpb, cudaS
 }
 
 template <class S, int KMAX, int MMAX, int ALG>
+struct MixedLaunch {
+  static inline size_t configured = 0;
+  static cudaError_t launch(const ColArgs& a, int count_hint, int wpb, cudaStream_t s) {
+    if (MixedLayout<S, KMAX, MMAX, ALG>::kTileGlobal && !a.tile_scratch && count_hint > 0) return cudaErrorInvalidValue;
+    return launch_persistent_warps(column_mixed_kernel<S, KMAX, MMAX, ALG>, MixedLayout<S, KMAX, MMAX, ALG>::bytes(),
+                                   configured, a, count_hint, wpb, s);
+  }
+  static size_t scratch(int count_hint, int wpb_req) {
+    int grid = 0, wpb = 1;
+    if (persistent_warps_shape(column_mixed_kernel<S, KMAX, MMAX, ALG>, MixedLayout<S, KMAX, MMAX, ALG>::bytes(),
+                               configured, count_hint, wpb_req, &grid, &wpb) != cudaSuccess)
+      return 0;
+    return (size_t)grid * wpb * MixedLayout<S, KMAX, MMAX, ALG>::tile_bytes();
+  }
+};
+
+template <class S, int KMAX, int MMAX, int ALG>
 cudaError_t launch_mixed_columns(const ColArgs& a, int count_hint, int wpb, cudaStream_t s) {
-  static size_t configured = 0;
-  return launch_persistent_warps(column_mixed_kernel<S, KMAX, MMAX, ALG>, MixedLayout<S, KMAX, MMAX, ALG>::bytes(),
-                                 configured, a, count_hint, wpb, s);
+  return MixedLaunch<S, KMAX, MMAX, ALG>::launch(a, count_hint, wpb, s);
 }

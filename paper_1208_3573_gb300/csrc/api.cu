@@ -1,8 +1,10 @@
 // C ABI of the DIAF library: argument checks, the symbolic pass, bucketed
 // numeric launches, output ownership, and the preconditioner apply.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -638,6 +640,55 @@ static diaf_status prepare_apply_blocks(diaf_factors* F, cudaStream_t s) {
   return DIAF_OK;
 }
 
+// Pinned host staging for prepare_apply's copies of V's structure (to the
+// host) and of the level order (back): pageable copies go through the
+// driver's bounce buffer at a fraction of the bandwidth and block the host.
+// One buffer per process, grown as needed and reused; `done` (one event per
+// device) marks the end of the last copy out of it.
+namespace {
+constexpr int kStageDevices = 64;
+struct PinnedStage {
+  std::mutex mu;
+  unsigned char* buf = nullptr;
+  size_t cap = 0;
+  cudaEvent_t done[kStageDevices] = {};
+};
+PinnedStage g_stage;
+
+// Waits for the previous user's copies and returns at least `bytes` of
+// pinned memory (nullptr on failure).  Call with g_stage.mu held.
+unsigned char* stage_get(size_t bytes) {
+  for (int d = 0; d < kStageDevices; ++d)
+    if (g_stage.done[d]) cudaEventSynchronize(g_stage.done[d]);
+  if (bytes > g_stage.cap) {
+    if (g_stage.buf) cudaFreeHost(g_stage.buf);
+    g_stage.buf = nullptr;
+    g_stage.cap = 0;
+    const size_t want = bytes + bytes / 4;
+    if (cudaHostAlloc((void**)&g_stage.buf, want, cudaHostAllocPortable) != cudaSuccess) {
+      (void)cudaGetLastError();
+      g_stage.buf = nullptr;
+      return nullptr;
+    }
+    g_stage.cap = want;
+  }
+  return g_stage.buf;
+}
+
+// Marks the end of the copies out of the staging buffer on stream s.
+cudaError_t stage_release(cudaStream_t s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kStageDevices) return cudaStreamSynchronize(s);
+  if (!g_stage.done[dev]) {
+    e = cudaEventCreateWithFlags(&g_stage.done[dev], cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaEventRecord(g_stage.done[dev], s);
+}
+}  // namespace
+
 static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   if (F->rule == DIAF_RULE_BLOCK) return prepare_apply_blocks(F, s);
   const int n = F->n;
@@ -650,23 +701,41 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   DIAF_CU(F->alloc(&F->Vr.colidx, F->nnz_v));
   DIAF_CU(F->alloc((char**)&F->Vr.vals, esz * F->nnz_v));
   DIAF_CU(csc_to_csr(n, F->nnz_v, F->Vcp, F->Vri, F->Vv, cplx, F->Vr.rowptr, F->Vr.colidx, F->Vr.vals, work, s));
-  F->Wr.n = n; F->Wr.nnz = F->nnz_w;
-  DIAF_CU(F->alloc(&F->Wr.rowptr, n + 1));
-  DIAF_CU(F->alloc(&F->Wr.colidx, F->nnz_w));
-  DIAF_CU(F->alloc((char**)&F->Wr.vals, esz * F->nnz_w));
-  DIAF_CU(csc_to_csr(n, F->nnz_w, F->Wcp, F->Wri, F->Wv, cplx, F->Wr.rowptr, F->Wr.colidx, F->Wr.vals, work, s));
   uint32_t* tri;
   DIAF_CU(F->alloc(&tri, 1));
   DIAF_CU(cudaMemsetAsync(tri, 0, sizeof(uint32_t), s));
   DIAF_CU(csr_triangle_check(F->Vr, cplx, tri, s));
-  // one synchronisation: the triangle check and V's structure for the level schedule
-  uint32_t h = 0;
-  std::vector<int32_t> rp(n + 1), ci((size_t)F->nnz_v);
-  DIAF_CU(cudaMemcpyAsync(&h, tri, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-  DIAF_CU(cudaMemcpyAsync(rp.data(), F->Vr.rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+  // one synchronisation: the triangle check and V's structure for the level
+  // schedule, copied into pinned staging (rp, ci; then ptr and order on the
+  // way back); W's row-oriented copy is built meanwhile, after the copies
+  std::lock_guard<std::mutex> stage_lock(g_stage.mu);
+  const size_t n1 = (size_t)n + 1;
+  unsigned char* stage = stage_get(sizeof(int32_t) * (3 * n1 + (size_t)F->nnz_v) + sizeof(uint32_t));
+  if (!stage) return fail(DIAF_ENOMEM, "pinned host staging for the level schedule");
+  int32_t* rp = reinterpret_cast<int32_t*>(stage);
+  int32_t* ci = rp + n1;
+  int32_t* ptr = ci + F->nnz_v;     // level pointers (at most n + 1)
+  int32_t* order = ptr + n1;        // rows level by level (n)
+  uint32_t* hp = reinterpret_cast<uint32_t*>(order + n1);
+  DIAF_CU(cudaMemcpyAsync(hp, tri, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  DIAF_CU(cudaMemcpyAsync(rp, F->Vr.rowptr, sizeof(int32_t) * n1, cudaMemcpyDeviceToHost, s));
   if (F->nnz_v > 0)
-    DIAF_CU(cudaMemcpyAsync(ci.data(), F->Vr.colidx, sizeof(int32_t) * F->nnz_v, cudaMemcpyDeviceToHost, s));
-  DIAF_CU(cudaStreamSynchronize(s));
+    DIAF_CU(cudaMemcpyAsync(ci, F->Vr.colidx, sizeof(int32_t) * F->nnz_v, cudaMemcpyDeviceToHost, s));
+  cudaEvent_t copied;
+  DIAF_CU(cudaEventCreateWithFlags(&copied, cudaEventDisableTiming));
+  cudaError_t ce = cudaEventRecord(copied, s);
+  F->Wr.n = n; F->Wr.nnz = F->nnz_w;
+  if (ce == cudaSuccess) ce = F->alloc(&F->Wr.rowptr, n + 1);
+  if (ce == cudaSuccess) ce = F->alloc(&F->Wr.colidx, F->nnz_w);
+  if (ce == cudaSuccess) ce = F->alloc((char**)&F->Wr.vals, esz * F->nnz_w);
+  if (ce == cudaSuccess)
+    ce = csc_to_csr(n, F->nnz_w, F->Wcp, F->Wri, F->Wv, cplx, F->Wr.rowptr, F->Wr.colidx, F->Wr.vals, work, s);
+  // wait for the copies even after an error: they write into the staging buffer
+  const cudaError_t se = cudaEventSynchronize(copied);
+  cudaEventDestroy(copied);
+  DIAF_CU(ce);
+  DIAF_CU(se);
+  const uint32_t h = *hp;
   if ((h & 1u) && (h & 2u)) return fail(DIAF_EINVAL, "V is not triangular");
   if (h & 4u) return fail(DIAF_EINVAL, "V has a zero or missing diagonal entry");
   F->v_upper = !(h & 1u);
@@ -683,15 +752,17 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
     lev[i] = L;
     if (L + 1 > nlev) nlev = L + 1;
   }
-  std::vector<int32_t> ptr(nlev + 1, 0), order(n > 0 ? n : 1);
+  for (int l = 0; l <= nlev; ++l) ptr[l] = 0;
   for (int i = 0; i < n; ++i) ptr[lev[i] + 1] += 1;
   for (int l = 0; l < nlev; ++l) ptr[l + 1] += ptr[l];
-  std::vector<int32_t> cur(ptr.begin(), ptr.end() - 1);
+  std::vector<int32_t> cur(ptr, ptr + nlev);
   for (int i = 0; i < n; ++i) order[cur[lev[i]]++] = i;
   LevelCsr& Vl = F->Vl;
   Vl.n = n;
   Vl.nlev = nlev;
   Vl.nnz = F->nnz_v - n;
+  Vl.maxw = 0;
+  for (int l = 0; l < nlev; ++l) Vl.maxw = std::max(Vl.maxw, ptr[l + 1] - ptr[l]);
   int32_t *dorder, *pos;
   DIAF_CU(F->alloc(&Vl.lvlptr, nlev + 1));
   DIAF_CU(F->alloc(&dorder, n));
@@ -701,9 +772,9 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   DIAF_CU(F->alloc((char**)&Vl.vals, esz * Vl.nnz));
   DIAF_CU(F->alloc((char**)&Vl.dinv, esz * n));
   DIAF_CU(F->alloc(&Vl.xrow, n));
-  // pageable host sources: each copy has taken its data when the call returns
-  DIAF_CU(cudaMemcpyAsync(Vl.lvlptr, ptr.data(), sizeof(int32_t) * (nlev + 1), cudaMemcpyHostToDevice, s));
-  if (n > 0) DIAF_CU(cudaMemcpyAsync(dorder, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+  DIAF_CU(cudaMemcpyAsync(Vl.lvlptr, ptr, sizeof(int32_t) * (nlev + 1), cudaMemcpyHostToDevice, s));
+  if (n > 0) DIAF_CU(cudaMemcpyAsync(dorder, order, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+  DIAF_CU(stage_release(s));  // the next user of the staging buffer waits for these copies
   DIAF_CU(csr_level_permute(F->Vr, cplx, dorder, pos, work, Vl, s));
   F->Wl = F->Wr;
   DIAF_CU(F->alloc(&F->Wl.colidx, F->nnz_w));

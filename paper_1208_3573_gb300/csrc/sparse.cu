@@ -273,6 +273,100 @@ __global__ void __launch_bounds__(kLevelThreads, 1)
 #undef DIAF_LP
 }
 
+// The same solve for matrices whose levels are at most kDeepThreads rows
+// wide, with the row data fetched kDeep levels ahead instead of one.  A
+// thread keeps its rows of the next kDeep levels in kDeep register sets (set
+// k: the levels lv with lv mod kDeep = k).  A row's loads form two dependent
+// round trips (rowptr, xrow and 1/diag; then the entries and x), issued one
+// level apart -- the first right after the set's previous level is done, the
+// second one level later -- so no thread waits on a load before a barrier.
+constexpr int kDeepThreads = 256;
+constexpr int kDeep = 4;
+
+template <class S>
+__global__ void __launch_bounds__(kDeepThreads, 1)
+    trsv_levels_deep_kernel(int nlev, const int32_t* __restrict__ lvlptr, const int32_t* __restrict__ rowptr,
+                            const int32_t* __restrict__ colidx, const S* __restrict__ vals,
+                            const S* __restrict__ dinv, const int32_t* __restrict__ xrow, const S* __restrict__ x,
+                            S* t) {
+  constexpr int kWin = level_window<S>();
+  extern __shared__ __align__(16) unsigned char level_ring[];
+  S* tw = reinterpret_cast<S*>(level_ring);
+  __shared__ int32_t sptr[kLevelPtrSmem + 1];
+  const bool in_smem = nlev <= kLevelPtrSmem;
+  if (in_smem)
+    for (int i = threadIdx.x; i <= nlev; i += blockDim.x) sptr[i] = lvlptr[i];
+  __syncthreads();
+#define DIAF_LP(l) (in_smem ? sptr[(l)] : lvlptr[(l)])
+  int rb[kDeep], re[kDeep], xr[kDeep];
+  S xb[kDeep], db[kDeep];
+  int pc[kDeep][kPrefetch];
+  S pv[kDeep][kPrefetch];
+  // first round trip: the row's bounds, its x index and 1/diag (xr = -1: no row)
+#define DIAF_STAGE_A(k, lvl)                                      \
+  do {                                                            \
+    rb[k] = 0;                                                    \
+    re[k] = 0;                                                    \
+    xr[k] = -1;                                                   \
+    const int p_ = DIAF_LP(lvl) + (int)threadIdx.x;               \
+    if (p_ < DIAF_LP((lvl) + 1)) {                                \
+      rb[k] = rowptr[p_];                                         \
+      re[k] = rowptr[p_ + 1];                                     \
+      xr[k] = xrow[p_];                                           \
+      db[k] = dinv[p_];                                           \
+    }                                                             \
+  } while (0)
+  // second round trip: x and the first kPrefetch entries
+#define DIAF_STAGE_B(k)                                           \
+  do {                                                            \
+    if (xr[k] >= 0) {                                             \
+      xb[k] = x[xr[k]];                                           \
+      _Pragma("unroll") for (int q = 0; q < kPrefetch; ++q) {     \
+        const bool in = rb[k] + q < re[k];                        \
+        pc[k][q] = in ? colidx[rb[k] + q] : 0;                    \
+        pv[k][q] = in ? vals[rb[k] + q] : sc_zero<S>();           \
+      }                                                           \
+    }                                                             \
+  } while (0)
+#pragma unroll
+  for (int k = 0; k < kDeep; ++k)
+    if (k < nlev) DIAF_STAGE_A(k, k);
+#pragma unroll
+  for (int k = 0; k < kDeep; ++k)
+    if (k < nlev) DIAF_STAGE_B(k);
+  for (int lv0 = 0; lv0 < nlev; lv0 += kDeep) {
+#pragma unroll
+    for (int k = 0; k < kDeep; ++k) {
+      const int lv = lv0 + k;
+      if (lv < nlev) {  // uniform over the block
+        const int b = DIAF_LP(lv), e = DIAF_LP(lv + 1);
+        const int lo = e - kWin;
+#define DIAF_TGET(c) ((c) >= lo ? tw[(c) & (kWin - 1)] : t[(c)])
+        const int p = b + (int)threadIdx.x;
+        if (p < e) {
+          S acc = xb[k];
+#pragma unroll
+          for (int q = 0; q < kPrefetch; ++q)
+            if (rb[k] + q < re[k]) acc -= pv[k][q] * DIAF_TGET(pc[k][q]);
+          for (int j = rb[k] + kPrefetch; j < re[k]; ++j) acc -= vals[j] * DIAF_TGET(colidx[j]);
+          const S tv = acc * db[k];
+          t[p] = tv;
+          tw[p & (kWin - 1)] = tv;
+        }
+#undef DIAF_TGET
+        if (lv + kDeep < nlev) DIAF_STAGE_A(k, lv + kDeep);
+        // the set whose first round trip was issued one level ago
+        const int kb = (k + kDeep - 1) % kDeep;
+        if (lv >= 1 && lv + kDeep - 1 < nlev) DIAF_STAGE_B(kb);
+        __syncthreads();
+      }
+    }
+  }
+#undef DIAF_STAGE_A
+#undef DIAF_STAGE_B
+#undef DIAF_LP
+}
+
 }  // namespace
 
 cudaError_t csr_level_permute(const Csr& V, bool cplx, const int32_t* order, int32_t* pos, int32_t* work,
@@ -315,10 +409,18 @@ static cudaError_t trsv_levels_perm_t(const LevelCsr& L, const void* x, void* t,
     cudaError_t e = cudaFuncSetAttribute(trsv_levels_perm_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)ring);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(trsv_levels_deep_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring);
+    if (e != cudaSuccess) return e;
     configured_device = dev;
   }
-  trsv_levels_perm_kernel<S><<<1, kLevelThreads, ring, s>>>(L.nlev, L.lvlptr, L.rowptr, L.colidx, (const S*)L.vals,
-                                                            (const S*)L.dinv, L.xrow, (const S*)x, (S*)t);
+  if (L.maxw <= kDeepThreads)
+    trsv_levels_deep_kernel<S><<<1, kDeepThreads, ring, s>>>(L.nlev, L.lvlptr, L.rowptr, L.colidx,
+                                                             (const S*)L.vals, (const S*)L.dinv, L.xrow,
+                                                             (const S*)x, (S*)t);
+  else
+    trsv_levels_perm_kernel<S><<<1, kLevelThreads, ring, s>>>(L.nlev, L.lvlptr, L.rowptr, L.colidx,
+                                                              (const S*)L.vals, (const S*)L.dinv, L.xrow,
+                                                              (const S*)x, (S*)t);
   DIAF_COUNT_LAUNCH();
   return cudaGetLastError();
 }

@@ -49,6 +49,7 @@ struct LevelCsr {
   void* vals = nullptr;         // nnz
   void* dinv = nullptr;         // n
   int32_t* xrow = nullptr;      // n
+  int maxw = 0;                 // rows of the widest level (picks the solve kernel)
 };
 
 // Builds L (buffers allocated by the caller; L.n, L.nlev, L.lvlptr set) from

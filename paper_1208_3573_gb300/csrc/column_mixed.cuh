@@ -53,6 +53,9 @@ struct MixedLayout {
   // tiles, 6 -> 11 for real 32-column ones).  The real 16-column tile keeps it
   // in shared memory: there the extra warps did not pay for the slower loads.
   static constexpr bool kTileGlobal = sizeof(S) > 4 || KMAX > 16;
+  // Householder QR with the tile in registers (one row per lane): real tiles
+  // of up to 32 rows and 16 columns
+  static constexpr bool kRegQR = sizeof(S) == 4 && KMAX <= 16 && MMAX <= 32;
   static constexpr size_t tile_bytes() { return kTileGlobal ? sizeof(SD) * kTile : 0; }
   static constexpr size_t raw() {
     return sizeof(SD) * ((kTileGlobal ? 0 : kTile) + 3 * KMAX + 2 * MMAX + kRR * KP + 2 * kRR * kRR) +
@@ -132,24 +135,30 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
   DIAF_PHASE(0);
 
   // ---- FP32 QR of T and the keys
-  for (int i = lane; i < me * k; i += DIAF_WARP) {
-    int r = i % me, c = i / me;
-    Tw[r + c * LDT] = sc_cast<S>(Ts[r + c * LDT]);
+  if constexpr (L::kRegQR) {
+    // the tile in registers, one row per lane: R and the column norms directly
+    DIAF_PHASE(1);
+    warp_qr_rows<S, SD, LDT, KP, KMAX>(Ts, nullptr, m, k, Rs, cn, lane);
+  } else {
+    for (int i = lane; i < me * k; i += DIAF_WARP) {
+      int r = i % me, c = i / me;
+      Tw[r + c * LDT] = sc_cast<S>(Ts[r + c * LDT]);
+    }
+    __syncwarp();
+    for (int c = lane; c < k; c += DIAF_WARP) {  // column norms for the kappa estimate: FP32 is enough
+      R s2 = R(0);
+      for (int r = 0; r < m; ++r) s2 += sc_abs2(Tw[r + c * LDT]);
+      cn[c] = (double)sqrt(s2);
+    }
+    __syncwarp();
+    DIAF_PHASE(1);
+    warp_householder_qr_rs<S, LDT, KMAX, MMAX / DIAF_WARP>(Tw, me, k, lane);
+    for (int i = lane; i < k * k; i += DIAF_WARP) {
+      int r = i % k, c = i / k;
+      Rs[r + c * KP] = (r <= c) ? Tw[r + c * LDT] : sc_zero<S>();
+    }
+    __syncwarp();
   }
-  __syncwarp();
-  for (int c = lane; c < k; c += DIAF_WARP) {  // column norms for the kappa estimate: FP32 is enough
-    R s2 = R(0);
-    for (int r = 0; r < m; ++r) s2 += sc_abs2(Tw[r + c * LDT]);
-    cn[c] = (double)sqrt(s2);
-  }
-  __syncwarp();
-  DIAF_PHASE(1);
-  warp_householder_qr_rs<S, LDT, KMAX, MMAX / DIAF_WARP>(Tw, me, k, lane);
-  for (int i = lane; i < k * k; i += DIAF_WARP) {
-    int r = i % k, c = i / k;
-    Rs[r + c * KP] = (r <= c) ? Tw[r + c * LDT] : sc_zero<S>();
-  }
-  __syncwarp();
   DIAF_PHASE(2);
   float kap = 0.0f;
   for (int c = lane; c < k; c += DIAF_WARP) {
@@ -174,36 +183,41 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
   DIAF_PHASE(4);
 
   if (ALG == DIAF_ALG_S) {
-    // ---- FP32 QR of A-hat (I_j rows zeroed); Jacobi SVD of R-hat in registers
-    for (int i = lane; i < me * k; i += DIAF_WARP) {
-      int r = i % me, c = i / me;
-      Tw[r + c * LDT] = (r < m && ix.inI[r] >= 0) ? sc_zero<S>() : sc_cast<S>(Ts[r + c * LDT]);
+    // ---- FP32 QR of A-hat (I_j rows zeroed) into Rs; then the Jacobi SVD of R-hat
+    if constexpr (L::kRegQR) {
+      DIAF_PHASE(5);
+      warp_qr_rows<S, SD, LDT, KP, KMAX>(Ts, ix.inI, m, k, Rs, cn, lane);
+    } else {
+      for (int i = lane; i < me * k; i += DIAF_WARP) {
+        int r = i % me, c = i / me;
+        Tw[r + c * LDT] = (r < m && ix.inI[r] >= 0) ? sc_zero<S>() : sc_cast<S>(Ts[r + c * LDT]);
+      }
+      __syncwarp();
+      for (int c = lane; c < k; c += DIAF_WARP) {
+        R s2 = R(0);
+        for (int r = 0; r < m; ++r) s2 += sc_abs2(Tw[r + c * LDT]);
+        cn[c] = (double)sqrt(s2);
+      }
+      __syncwarp();
+      DIAF_PHASE(5);
+      warp_householder_qr_rs<S, LDT, KMAX, MMAX / DIAF_WARP>(Tw, me, k, lane);
+      for (int i = lane; i < k * k; i += DIAF_WARP) {
+        int r = i % k, c = i / k;
+        Rs[r + c * KP] = (r <= c) ? Tw[r + c * LDT] : sc_zero<S>();
+      }
+      __syncwarp();
     }
-    __syncwarp();
-    for (int c = lane; c < k; c += DIAF_WARP) {
-      R s2 = R(0);
-      for (int r = 0; r < m; ++r) s2 += sc_abs2(Tw[r + c * LDT]);
-      cn[c] = (double)sqrt(s2);
-    }
-    __syncwarp();
-    DIAF_PHASE(5);
-    warp_householder_qr_rs<S, LDT, KMAX, MMAX / DIAF_WARP>(Tw, me, k, lane);
     DIAF_PHASE(6);
     // an exactly zero column of A-hat (all its tile entries in I_j) is no
     // conditioning problem: it is an exact zero singular value, which the FP32
     // Jacobi keeps exact (w = e_c, residual 0, flagged from the residual)
     float kh = 0.0f;
     for (int c = lane; c < k; c += DIAF_WARP) {
-      const float d = (float)sc_abs(Tw[c + c * LDT]);
+      const float d = (float)sc_abs(Rs[c + c * KP]);
       kh = fmaxf(kh, d > 0.0f ? (float)cn[c] / d : (cn[c] > 0.0 ? INFINITY : 0.0f));
     }
     kh = warp_max(kh);
     if (!(kh <= kMixedKappaMax)) { hand_back(3); return; }
-    for (int i = lane; i < k * k; i += DIAF_WARP) {
-      int r = i % k, c = i / k;
-      Rs[r + c * KP] = (r <= c) ? Tw[r + c * LDT] : sc_zero<S>();
-    }
-    __syncwarp();
     // register-resident pairs for the warp-per-column tiles of up to 16
     // columns; the wider tiles (fewer warps per SM) keep the plain form
     int sw;

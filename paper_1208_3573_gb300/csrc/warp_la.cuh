@@ -194,6 +194,76 @@ __device__ void warp_householder_qr_rs(S* T, int m, int k, int lane) {
   }
 }
 
+// The same Householder QR for tiles of at most 32 rows and NQ <= 16
+// columns with the tile in registers: lane r holds row r (converted from the
+// tile T of type ST, leading dimension LDT; rows with mask[r] >= 0 read as
+// zero when mask is given), so no trailing-column loads or stores go through
+// shared memory.  Writes the k x k upper R to Rout (leading dimension LDR;
+// it must not alias T)
+// and the FP64 value of the column norms ||T(:,c)|| (of the masked tile) to
+// cn[c].
+template <class S, class ST, int LDT, int LDR, int NQ>
+__device__ void warp_qr_rows(const ST* T, const int32_t* mask, int m, int k, S* Rout, double* cn, int lane) {
+  using R = RealOf<S>;
+  static_assert(NQ >= 2 && NQ <= 16, "row-register QR: at most 16 columns");
+  constexpr int LOG = ilog2_c(NQ);
+  S x[NQ];
+  const bool live = lane < m && !(mask && mask[lane] >= 0);
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) x[q] = (live && q < k) ? sc_cast<S>(T[lane + q * LDT]) : sc_zero<S>();
+  {
+    R v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = sc_abs2(x[q]);
+    const R tot = warp_reduce_scatter<R, NQ>(v, lane);  // lane L: column L >> (5 - LOG)
+    const int q = lane >> (5 - LOG);
+    if ((lane & ((1 << (5 - LOG)) - 1)) == 0 && q < k) cn[q] = (double)sqrt(tot);
+  }
+  // R starts as zeros; row c is written by lane c once reflector c is applied
+  for (int i = lane; i < k * k; i += DIAF_WARP) Rout[(i % k) + (i / k) * LDR] = sc_zero<S>();
+  __syncwarp();
+  // step c works on x[0] = column c: after it the row's entries shift down by
+  // one, so every step runs the same code (no unrolling over c: small code)
+  const int p = m < k ? m : k;
+  for (int c = 0; c < p; ++c) {
+    const R nrm2 = warp_sum(lane >= c ? sc_abs2(x[0]) : R(0));
+    const S alpha = shfl_idx(x[0], c);
+    if (nrm2 != R(0)) {
+      const R ax = sc_abs(alpha);
+      const R nrm = sqrt(nrm2);
+      const S ph = sc_unit(alpha);
+      const S beta = -(nrm * ph);
+      const S u0 = (ax + nrm) * ph;
+      const R two_uu = div_r(R(1), nrm * (nrm + ax));
+      const S u = lane > c ? x[0] : (lane == c ? u0 : sc_zero<S>());
+      const int rest = k - c;  // columns c .. k-1 are x[0 .. rest-1]
+      if (rest > 1) {
+        S v[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) v[q] = (q >= 1 && q < rest) ? sc_cmul(u, x[q]) : sc_zero<S>();
+        const S fmine = two_uu * warp_reduce_scatter<S, NQ>(v, lane);
+#pragma unroll
+        for (int q = 1; q < NQ; ++q) {
+          if (q < rest) {  // warp-uniform
+            const S fq = shfl_idx(fmine, q << (5 - LOG));
+            x[q] -= fq * u;
+          }
+        }
+      }
+      if (lane == c) x[0] = beta;
+    }
+    if (lane == c) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q)
+        if (q < k - c) Rout[c + (c + q) * LDR] = x[q];
+    }
+#pragma unroll
+    for (int q = 0; q + 1 < NQ; ++q) x[q] = x[q + 1];
+    x[NQ - 1] = sc_zero<S>();
+  }
+  __syncwarp();
+}
+
 // ------------------------------------------------------------------ Jacobi
 // Parallel one-sided (Hestenes) Jacobi on the p x q matrix G (leading
 // dimension LDG): G V has orthogonal columns, V (q x q, leading dimension

@@ -46,16 +46,15 @@ struct MixedLayout {
   static constexpr int KP = KMAX + 1;
   static constexpr int kTile = LDT * KMAX;
   static constexpr int kRR = ALG == DIAF_ALG_Q ? kRRMax : 0;  // DIAF-Q only: scratch for C v, r, coefficients
-  // The FP64 tile of the complex and the wide tiles lives in global memory
-  // (ColArgs::tile_scratch, one per resident warp, mostly L1/L2 hits): their
-  // shared memory then holds only the FP32 working set and the vectors, which
-  // raises the warps resident per SM (measured: 11 -> 18 for complex 16-column
-  // tiles, 6 -> 11 for real 32-column ones).  The real 16-column tile keeps it
-  // in shared memory: there the extra warps did not pay for the slower loads.
-  static constexpr bool kTileGlobal = sizeof(S) > 4 || KMAX > 16;
-  // Householder QR with the tile in registers (one row per lane): real tiles
-  // of up to 32 rows and 16 columns
-  static constexpr bool kRegQR = sizeof(S) == 4 && KMAX <= 16 && MMAX <= 32;
+  // The FP64 tile lives in global memory (ColArgs::tile_scratch, one per
+  // resident warp, mostly L1/L2 hits): shared memory holds only the FP32
+  // working set and the vectors, which raises the warps resident per SM
+  // (measured: 11 -> 18 for complex 16-column tiles, 6 -> 11 for real
+  // 32-column ones, 21 -> 28 by shared memory for real 16-column ones).
+  static constexpr bool kTileGlobal = true;
+  // Householder QR with the tile in registers (one row per lane): tiles of
+  // up to 32 rows and 16 columns
+  static constexpr bool kRegQR = KMAX <= 16 && MMAX <= 32;
   static constexpr size_t tile_bytes() { return kTileGlobal ? sizeof(SD) * kTile : 0; }
   static constexpr size_t raw() {
     return sizeof(SD) * ((kTileGlobal ? 0 : kTile) + 3 * KMAX + 2 * MMAX + kRR * KP + 2 * kRR * kRR) +

@@ -257,14 +257,14 @@ diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_
   uint32_t h_status = 0;
   int64_t h_Etot = 0;
   if (n > 0) {
-    // the planner reads J_j only after the input check passed: sync first
-    DIAF_CU(cudaMemcpyAsync(&h_status, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    DIAF_CU(cudaStreamSynchronize(s));
-    if (h_status & DEV_ST_BAD_INPUT) return fail(DIAF_EINVAL, "unsorted or out-of-range indices in A, PW or V");
+    // the count kernel reads J_j only when the input check (earlier on the
+    // stream) passed: it tests the status flag itself, so no sync here
     DIAF_CU(plan_count(pa, s));
     DIAF_CU(exclusive_scan_i32_to_i64(pa.E, pa.Eoff, n, bs64, s));
     DIAF_CU(cudaMemcpyAsync(&h_Etot, pa.Eoff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    DIAF_CU(cudaMemcpyAsync(&h_status, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     DIAF_CU(cudaStreamSynchronize(s));
+    if (h_status & DEV_ST_BAD_INPUT) return fail(DIAF_EINVAL, "unsorted or out-of-range indices in A, PW or V");
   }
   DIAF_CU(pool.get(&pa.rows, (size_t)h_Etot));
   DIAF_CU(F->alloc(&F->Vcp, n + 1));
@@ -696,62 +696,101 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   const size_t esz = cplx ? 16 : 8;
   int32_t* work;
   DIAF_CU(F->alloc(&work, n + scan_blocksums_size(n)));
-  F->Vr.n = n; F->Vr.nnz = F->nnz_v;
-  DIAF_CU(F->alloc(&F->Vr.rowptr, n + 1));
-  DIAF_CU(F->alloc(&F->Vr.colidx, F->nnz_v));
-  DIAF_CU(F->alloc((char**)&F->Vr.vals, esz * F->nnz_v));
-  DIAF_CU(csc_to_csr(n, F->nnz_v, F->Vcp, F->Vri, F->Vv, cplx, F->Vr.rowptr, F->Vr.colidx, F->Vr.vals, work, s));
-  uint32_t* tri;
-  DIAF_CU(F->alloc(&tri, 1));
-  DIAF_CU(cudaMemsetAsync(tri, 0, sizeof(uint32_t), s));
-  DIAF_CU(csr_triangle_check(F->Vr, cplx, tri, s));
-  // one synchronisation: the triangle check and V's structure for the level
-  // schedule, copied into pinned staging (rp, ci; then ptr and order on the
-  // way back); W's row-oriented copy is built meanwhile, after the copies
+  // V's column structure goes to the host first (pinned staging: cp, ri;
+  // then ptr and order on the way back): the level schedule is computed from
+  // it on the host while the device builds the row-oriented copies of V and
+  // W and checks V's diagonal
   std::lock_guard<std::mutex> stage_lock(g_stage.mu);
   const size_t n1 = (size_t)n + 1;
   unsigned char* stage = stage_get(sizeof(int32_t) * (3 * n1 + (size_t)F->nnz_v) + sizeof(uint32_t));
   if (!stage) return fail(DIAF_ENOMEM, "pinned host staging for the level schedule");
-  int32_t* rp = reinterpret_cast<int32_t*>(stage);
-  int32_t* ci = rp + n1;
-  int32_t* ptr = ci + F->nnz_v;     // level pointers (at most n + 1)
+  int32_t* cp = reinterpret_cast<int32_t*>(stage);
+  int32_t* ri = cp + n1;
+  int32_t* ptr = ri + F->nnz_v;     // level pointers (at most n + 1)
   int32_t* order = ptr + n1;        // rows level by level (n)
   uint32_t* hp = reinterpret_cast<uint32_t*>(order + n1);
-  DIAF_CU(cudaMemcpyAsync(hp, tri, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-  DIAF_CU(cudaMemcpyAsync(rp, F->Vr.rowptr, sizeof(int32_t) * n1, cudaMemcpyDeviceToHost, s));
-  if (F->nnz_v > 0)
-    DIAF_CU(cudaMemcpyAsync(ci, F->Vr.colidx, sizeof(int32_t) * F->nnz_v, cudaMemcpyDeviceToHost, s));
-  cudaEvent_t copied;
-  DIAF_CU(cudaEventCreateWithFlags(&copied, cudaEventDisableTiming));
-  cudaError_t ce = cudaEventRecord(copied, s);
+  DIAF_CU(cudaMemcpyAsync(cp, F->Vcp, sizeof(int32_t) * n1, cudaMemcpyDeviceToHost, s));
+  if (F->nnz_v > 0) DIAF_CU(cudaMemcpyAsync(ri, F->Vri, sizeof(int32_t) * F->nnz_v, cudaMemcpyDeviceToHost, s));
+  cudaEvent_t ev[2];
+  DIAF_CU(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+  cudaError_t ce = cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(ev[0]);
+    DIAF_CU(cudaStreamSynchronize(s));  // the copies write into the staging buffer
+    DIAF_CU(ce);
+  }
+  ce = cudaEventRecord(ev[0], s);
+  uint32_t* tri = nullptr;
+  F->Vr.n = n; F->Vr.nnz = F->nnz_v;
   F->Wr.n = n; F->Wr.nnz = F->nnz_w;
+  if (ce == cudaSuccess) ce = F->alloc(&F->Vr.rowptr, n + 1);
+  if (ce == cudaSuccess) ce = F->alloc(&F->Vr.colidx, F->nnz_v);
+  if (ce == cudaSuccess) ce = F->alloc((char**)&F->Vr.vals, esz * F->nnz_v);
+  if (ce == cudaSuccess)
+    ce = csc_to_csr(n, F->nnz_v, F->Vcp, F->Vri, F->Vv, cplx, F->Vr.rowptr, F->Vr.colidx, F->Vr.vals, work, s);
+  if (ce == cudaSuccess) ce = F->alloc(&tri, 1);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(tri, 0, sizeof(uint32_t), s);
+  if (ce == cudaSuccess) ce = csr_triangle_check(F->Vr, cplx, tri, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(hp, tri, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaEventRecord(ev[1], s);
   if (ce == cudaSuccess) ce = F->alloc(&F->Wr.rowptr, n + 1);
   if (ce == cudaSuccess) ce = F->alloc(&F->Wr.colidx, F->nnz_w);
   if (ce == cudaSuccess) ce = F->alloc((char**)&F->Wr.vals, esz * F->nnz_w);
   if (ce == cudaSuccess)
     ce = csc_to_csr(n, F->nnz_w, F->Wcp, F->Wri, F->Wv, cplx, F->Wr.rowptr, F->Wr.colidx, F->Wr.vals, work, s);
   // wait for the copies even after an error: they write into the staging buffer
-  const cudaError_t se = cudaEventSynchronize(copied);
-  cudaEventDestroy(copied);
-  DIAF_CU(ce);
-  DIAF_CU(se);
-  const uint32_t h = *hp;
-  if ((h & 1u) && (h & 2u)) return fail(DIAF_EINVAL, "V is not triangular");
-  if (h & 4u) return fail(DIAF_EINVAL, "V has a zero or missing diagonal entry");
-  F->v_upper = !(h & 1u);
-  // level of every row: its depth in the dependency graph of V (host, O(nnz))
+  cudaError_t se = cudaEventSynchronize(ev[0]);
+  if (ce != cudaSuccess || se != cudaSuccess) {
+    (void)cudaStreamSynchronize(s);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    DIAF_CU(ce);
+    DIAF_CU(se);
+  }
+  // level of every row: its depth in the dependency graph of V (host, O(nnz)),
+  // pushed column by column in the solve's order: lev[j] is final when column
+  // j is reached, and row i of column j (i != j) waits for t_j.  The pass
+  // assumes an upper V (columns descending) and checks the structure on the
+  // way: an entry below the diagonal restarts it for a lower V (ascending),
+  // where an entry above the diagonal means V is not triangular.  The device
+  // checks the diagonal's values meanwhile.
   std::vector<int32_t> lev(n, 0);
   int nlev = 0;
-  for (int step = 0; step < n; ++step) {
-    const int i = F->v_upper ? n - 1 - step : step;
-    int L = 0;
-    for (int p = rp[i]; p < rp[i + 1]; ++p) {
-      const int j = ci[p];
-      if (j != i && lev[j] + 1 > L) L = lev[j] + 1;
+  bool nodiag = false;
+  auto level_pass = [&](bool upper) -> bool {
+    std::fill(lev.begin(), lev.end(), 0);
+    nlev = n > 0 ? 1 : 0;
+    nodiag = false;
+    for (int step = 0; step < n; ++step) {
+      const int j = upper ? n - 1 - step : step;
+      const int lj = lev[j] + 1;
+      if (lj > nlev) nlev = lj;
+      bool d = false;
+      for (int p = cp[j]; p < cp[j + 1]; ++p) {
+        const int i = ri[p];
+        if (i == j) { d = true; continue; }
+        if (upper ? i > j : i < j) return false;
+        if (lev[i] < lj) lev[i] = lj;
+      }
+      nodiag |= !d;
     }
-    lev[i] = L;
-    if (L + 1 > nlev) nlev = L + 1;
+    return true;
+  };
+  F->v_upper = true;
+  if (!level_pass(true)) {
+    F->v_upper = false;
+    if (!level_pass(false)) {
+      (void)cudaStreamSynchronize(s);
+      cudaEventDestroy(ev[0]);
+      cudaEventDestroy(ev[1]);
+      return fail(DIAF_EINVAL, "V is not triangular");
+    }
   }
+  se = cudaEventSynchronize(ev[1]);
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  DIAF_CU(se);
+  if (nodiag || (*hp & 4u)) return fail(DIAF_EINVAL, "V has a zero or missing diagonal entry");
   for (int l = 0; l <= nlev; ++l) ptr[l] = 0;
   for (int i = 0; i < n; ++i) ptr[lev[i] + 1] += 1;
   for (int l = 0; l < nlev; ++l) ptr[l + 1] += ptr[l];

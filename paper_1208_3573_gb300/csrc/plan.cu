@@ -39,6 +39,9 @@ __global__ void check_csc_kernel(int n, const int32_t* __restrict__ cp, const in
 __global__ void plan_count_kernel(PlanArgs a) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= a.n) return;
+  // the input check ran before on the stream: with bad indices, read nothing
+  // (E stays unset; the host sees the status before it uses E)
+  if (*(volatile const uint32_t*)a.status & DEV_ST_BAD_INPUT) return;
   int w0 = a.Wcp[j], w1 = a.Wcp[j + 1];
   int E = 0;
   for (int p = w0; p < w1; ++p) {
@@ -57,8 +60,11 @@ __global__ void plan_count_kernel(PlanArgs a) {
 
 // Finishes column j once its sorted gathered rows are in s[0..E): writes the
 // unique rows R_j, counts admissible candidates, l_j, bucket.
+// mx: null, or (warp path) a thread-0 accumulator of max m (mx[0]) and
+// max l (mx[1]) that the caller publishes once instead of per column.
 template <int NT>
-__device__ void finish_column(const PlanArgs& a, int j, const int32_t* s, int E, int tid, int* sh_cnt) {
+__device__ void finish_column(const PlanArgs& a, int j, const int32_t* s, int E, int tid, int* sh_cnt,
+                              int* mx = nullptr) {
   // unique + compaction (NT threads cooperating; s is sorted)
   int32_t* out = a.rows + a.Eoff[j];
   int base = 0, ncand = 0, jin = 0;
@@ -142,8 +148,13 @@ __device__ void finish_column(const PlanArgs& a, int j, const int32_t* s, int E,
       int pos = atomicAdd(&a.bucket_count[b], 1);
       a.bucket_list[b * a.n + pos] = j;
     }
-    atomicMax(&a.stats[1], m);
-    atomicMax(&a.stats[2], l);
+    if (mx) {
+      mx[0] = m > mx[0] ? m : mx[0];
+      mx[1] = l > mx[1] ? l : mx[1];
+    } else {
+      atomicMax(&a.stats[1], m);
+      atomicMax(&a.stats[2], l);
+    }
   }
 }
 
@@ -177,19 +188,54 @@ __device__ void gather_rows(const PlanArgs& a, int j, int32_t* s, int N, int tid
   if (NT == 32) __syncwarp(); else __syncthreads();
 }
 
+// The warp path's gather: lane p takes entry p of W(:,j) (its A column's
+// start and length load in parallel), a warp scan of the lengths places each
+// column's run, and each lane copies its run -- a few dependent round trips
+// per column instead of three per entry of W(:,j).
+__device__ void gather_rows_warp(const PlanArgs& a, int j, int32_t* s, int N, int lane) {
+  const int w0 = a.Wcp[j], w1 = a.Wcp[j + 1];
+  int e0 = 0;
+  for (int p0 = w0; p0 < w1; p0 += 32) {
+    const int p = p0 + lane;
+    int c0 = 0, len = 0;
+    if (p < w1) {
+      const int c = a.Wri[p];
+      c0 = a.Acp[c];
+      len = a.Acp[c + 1] - c0;
+    }
+    int inc = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(DIAF_FULL, inc, o);
+      if (lane >= o) inc += y;
+    }
+    const int off = e0 + inc - len;
+#pragma unroll 4
+    for (int t = 0; t < len; ++t) s[off + t] = a.Ari[c0 + t];
+    e0 += __shfl_sync(DIAF_FULL, inc, 31);
+  }
+  for (int t = e0 + lane; t < N; t += 32) s[t] = INT_MAX;
+  __syncwarp();
+}
+
 __global__ void __launch_bounds__(kPlanWarps * 32) plan_rows_warp_kernel(PlanArgs a) {
   __shared__ int32_t sbuf[kPlanWarps][kWarpGather];
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int gw = blockIdx.x * kPlanWarps + warp, nw = gridDim.x * kPlanWarps;
+  int mx[2] = {0, 0};
   for (int j = gw; j < a.n; j += nw) {
     int E = a.E[j];
     if (E > kWarpGather) continue;
     int N = 2;
     while (N < E) N <<= 1;
-    gather_rows<32>(a, j, sbuf[warp], N, lane);
+    gather_rows_warp(a, j, sbuf[warp], N, lane);
     bitonic_sort<32>(sbuf[warp], N, lane);
-    finish_column<32>(a, j, sbuf[warp], E, lane, nullptr);
+    finish_column<32>(a, j, sbuf[warp], E, lane, nullptr, mx);
     __syncwarp();
+  }
+  if (lane == 0 && (mx[0] | mx[1])) {
+    atomicMax(&a.stats[1], mx[0]);
+    atomicMax(&a.stats[2], mx[1]);
   }
 }
 

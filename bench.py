@@ -90,10 +90,17 @@ class ClockSampler:
         self.proc = None
 
     def __enter__(self):
+        # returns once the sampler has printed its first line, so that it is
+        # live when the timed region starts; that line (taken before the
+        # region) is kept only as a fallback for regions shorter than a period
+        self.first = ""
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            import select
+            if select.select([self.proc.stdout], [], [], 10.0)[0]:
+                self.first = self.proc.stdout.readline()
         except Exception:
             self.proc = None
         return self
@@ -109,6 +116,9 @@ class ClockSampler:
 
     def summary(self):
         rows = [r.split(", ") for r in (self.out or "").strip().splitlines() if r.count(",") >= 8]
+        during = len(rows)
+        if not rows:
+            rows = [r.split(", ") for r in (self.first or "").strip().splitlines() if r.count(",") >= 8]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
@@ -116,7 +126,9 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": during,
+                **({} if during else {"note": "timed region shorter than the 100 ms sampling period: "
+                                              "the sample taken just before it"})}
 
 
 def cpu_baseline(w, alg, seconds=12.0):
@@ -327,7 +339,7 @@ def whole_job_rate(units_per_rank: int, ms_local: float, world: int) -> tuple[fl
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="diaf", choices=["diaf", "reference"])
     ap.add_argument("--workload", default="convdiff256_A2")
@@ -455,8 +467,9 @@ def main():
     else:
         peak, src, kname = FP32_TFLOPS * 1e12, "FP32 152 SMs x 128 lanes x 2 flop x 2.07 GHz", "column_mixed_kernel"
     # DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu
-    # capture of the current kernel on this workload; None where none was taken
-    traffic = 24363264 if (w.name == "convdiff2d_256x256_Wp2" and args.prec == "mixed32" and args.alg == "S") else None
+    # capture of the current kernel on this workload (dram__bytes_read.sum
+    # 28,351,232 + dram__bytes_write.sum 1,634,304); None where none was taken
+    traffic = 29985536 if (w.name == "convdiff2d_256x256_Wp2" and args.prec == "mixed32" and args.alg == "S") else None
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic, "kernel": f"{kname} (numeric pass, all buckets)",
             "kernel_ms": kern, "algorithmic_flops": flops, "peak_source": src}

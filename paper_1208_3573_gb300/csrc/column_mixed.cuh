@@ -24,10 +24,12 @@
 //     goes to FP64); w = (T^* T)^-1 T_I^* v, the least-squares solution of
 //     eq. condwj, is the y that follows v through the updates.
 //
-// A column goes to the FP64 kernel instead (appended to fb_list) when a
-// leverage-selection decision is closer to its threshold than the FP32 key
-// error bound (so I_j could differ from the FP64 choice), or when the tile is
-// too ill-conditioned for FP32 factors to drive the refinement.
+// When a leverage-selection decision is closer to its threshold than the FP32
+// key error bound (so I_j could differ from the FP64 choice), the kernel
+// recomputes that column's keys in FP64 with the FP64 kernel's own QR and
+// leverage routines and selects with those.  A column goes to the FP64 kernel
+// instead (appended to fb_list) when the tile is too ill-conditioned for FP32
+// factors to drive the refinement, or the refinement cannot converge.
 #pragma once
 
 #include "column.cuh"
@@ -46,18 +48,19 @@ struct MixedLayout {
   static constexpr int KP = KMAX + 1;
   static constexpr int kTile = LDT * KMAX;
   static constexpr int kRR = ALG == DIAF_ALG_Q ? kRRMax : 0;  // DIAF-Q only: scratch for C v, r, coefficients
-  // The FP64 tile lives in global memory (ColArgs::tile_scratch, one per
-  // resident warp, mostly L1/L2 hits): shared memory holds only the FP32
+  // The FP64 tile lives in global memory (ColArgs::tile_scratch, one slab
+  // per resident warp, mostly L1/L2 hits): shared memory holds only the FP32
   // working set and the vectors, which raises the warps resident per SM
   // (measured: 11 -> 18 for complex 16-column tiles, 6 -> 11 for real
-  // 32-column ones, 21 -> 28 by shared memory for real 16-column ones).
-  static constexpr bool kTileGlobal = true;
+  // 32-column ones, 21 -> 28 by shared memory for real 16-column ones).  A
+  // slab holds the tile and two tiles of scratch for the FP64 keys of the
+  // columns whose FP32 keys cannot decide.
+  static constexpr size_t tile_bytes() { return 3 * sizeof(SD) * kTile; }
   // Householder QR with the tile in registers (one row per lane): tiles of
   // up to 32 rows and 16 columns
   static constexpr bool kRegQR = KMAX <= 16 && MMAX <= 32;
-  static constexpr size_t tile_bytes() { return kTileGlobal ? sizeof(SD) * kTile : 0; }
   static constexpr size_t raw() {
-    return sizeof(SD) * ((kTileGlobal ? 0 : kTile) + 3 * KMAX + 2 * MMAX + kRR * KP + 2 * kRR * kRR) +
+    return sizeof(SD) * (3 * KMAX + 2 * MMAX + kRR * KP + 2 * kRR * kRR) +
            sizeof(S) * (kTile + 2 * KP * KMAX + KMAX) +
            sizeof(double) * (MMAX + 2 * KMAX) + idx_bytes<KMAX, MMAX>();
   }
@@ -84,13 +87,13 @@ __device__ __forceinline__ SD tile_adj_mul(const SD* Ts, const SD* zz, int m, in
 
 template <class S, int KMAX, int MMAX, int ALG>
 __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
-                                   typename DoubleOf<S>::T* Ts, int lane) {
+                                   typename DoubleOf<S>::T* Ts, typename DoubleOf<S>::T* Tx, int lane) {
   using SD = typename DoubleOf<S>::T;
   using R = RealOf<S>;
   using L = MixedLayout<S, KMAX, MMAX, ALG>;
   constexpr int LDT = L::LDT, KP = L::KP, kRR = L::kRR;
-  // Ts: the FP64 tile (LDT x KMAX), in global or shared memory (kTileGlobal)
-  SD* rinvD = reinterpret_cast<SD*>(smem) + (L::kTileGlobal ? 0 : L::kTile);  // FP64 reciprocal diagonal of the FP32 factor
+  // Ts: the FP64 tile (LDT x KMAX) and Tx: two tiles of scratch, in the slab
+  SD* rinvD = reinterpret_cast<SD*>(smem);  // FP64 reciprocal diagonal of the FP32 factor
   SD* wv = rinvD + KMAX;                 // w
   SD* gg = wv + KMAX;                    // k-vector scratch
   SD* vv = gg + KMAX;                    // v (MMAX)
@@ -173,7 +176,31 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     // bound on the FP32 key error: backward error of the FP32 QR and of the
     // row solves, amplified by the (column-scaled) conditioning of T
     const double delta = kMixedDeltaScale * (m + k) * (double)FLT_EPSILON * (double)kap;
-    if (l > 1 && margin <= 2.0 * delta) { hand_back(2); return; }
+    if (l > 1 && margin <= 2.0 * delta) {
+      // the FP32 keys cannot decide this column: recompute them the way the
+      // FP64 kernel does -- its Householder QR and leverage routines, in FP64,
+      // on a copy of the tile in the slab -- and select with those, so I_j is
+      // the FP64 kernel's choice; the rest of the column stays mixed
+      SD* Tq = Tx;             // QR workspace, then the FP64 rows of Q (LDT x KMAX)
+      SD* Rq = Tx + L::kTile;  // the FP64 R (KP x KMAX)
+      double* hd = reinterpret_cast<double*>(hk);  // FP64 keys (the 2 MMAX floats reserved)
+      for (int i = lane; i < me * k; i += DIAF_WARP) Tq[(i % me) + (i / me) * LDT] = Ts[(i % me) + (i / me) * LDT];
+      __syncwarp();
+      warp_householder_qr_rs<SD, LDT, KMAX, MMAX / DIAF_WARP>(Tq, me, k, lane);
+      for (int i = lane; i < k * k; i += DIAF_WARP) {
+        const int r = i % k, c = i / k;
+        Rq[r + c * KP] = (r <= c) ? Tq[r + c * LDT] : sc_zero<SD>();
+      }
+      __syncwarp();
+      RealOf<SD> rdmax = RealOf<SD>(0);
+      for (int c = lane; c < k; c += DIAF_WARP) rdmax = dmax(rdmax, sc_abs(Rq[c + c * KP]));
+      rdmax = warp_max(rdmax);
+      warp_leverage_rows<SD, SD, LDT, KP>(Ts, Rq, Tq, hd, rinvD, m, k, RealOf<SD>(1e-14) * rdmax, lane);
+      select_rows_greedy(ix.rs, hd, ix.pick, m, a.rule, j, l - 1, a.tie_tol, lane, a.blk);
+#ifdef DIAF_PHASE_TIMING
+      if (lane == 0 && a.phase) atomicAdd(&a.phase[24 + 2], 1ull);
+#endif
+    }
   }
   const int jpos = build_I(a, j, m, l, ix, lane);
   double rank_thr = -1.0;
@@ -473,15 +500,14 @@ __global__ void column_mixed_kernel(ColArgs a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   using L = MixedLayout<S, KMAX, MMAX, ALG>;
   unsigned char* smem = smem_raw + warp * L::bytes();
-  typename L::SD* Ts = L::kTileGlobal ? reinterpret_cast<typename L::SD*>(a.tile_scratch) +
-                                            (size_t)(blockIdx.x * (blockDim.x >> 5) + warp) * L::kTile
-                                      : reinterpret_cast<typename L::SD*>(smem);
+  typename L::SD* Ts = reinterpret_cast<typename L::SD*>(a.tile_scratch) +
+                       (size_t)(blockIdx.x * (blockDim.x >> 5) + warp) * 3 * L::kTile;
   const int count = *a.list_count;
   while (true) {
     int idx = 0;
     if (lane == 0) idx = atomicAdd(a.work_counter, 1);
     idx = __shfl_sync(DIAF_FULL, idx, 0);
     if (idx >= count) break;
-    solve_column_mixed<S, KMAX, MMAX, ALG>(a, a.list[idx], smem, Ts, lane);
+    solve_column_mixed<S, KMAX, MMAX, ALG>(a, a.list[idx], smem, Ts, Ts + L::kTile, lane);
   }
 }

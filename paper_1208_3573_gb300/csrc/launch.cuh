@@ -90,7 +90,7 @@ template <class S, int KMAX, int MMAX, int ALG>
 struct MixedLaunch {
   static inline size_t configured = 0;
   static cudaError_t launch(const ColArgs& a, int count_hint, int wpb, cudaStream_t s) {
-    if (MixedLayout<S, KMAX, MMAX, ALG>::kTileGlobal && !a.tile_scratch && count_hint > 0) return cudaErrorInvalidValue;
+    if (!a.tile_scratch && count_hint > 0) return cudaErrorInvalidValue;
     return launch_persistent_warps(column_mixed_kernel<S, KMAX, MMAX, ALG>, MixedLayout<S, KMAX, MMAX, ALG>::bytes(),
                                    configured, a, count_hint, wpb, s);
   }

@@ -8,11 +8,13 @@
 // the FP64 tile; twice when the gap is below 1e-2).  v_j = T(I_j,:) w_j and the
 // residual are evaluated in FP64.
 //
-// A column goes back to the FP64 CTA kernel (flag FP64_FALLBACK) whenever the
-// FP32 result could differ from the FP64 one: column-scaled kappa(T) or
-// kappa(A-hat) above 300, a leverage decision within 2 delta of its threshold
-// (delta = 8 (m + k) eps_32 kappa), a singular gap below 1e-5, fewer rows
-// outside I_j than k_j, or an empty W column.
+// A leverage decision within 2 delta of its threshold (delta = (m + k) eps_32
+// kappa) makes the kernel recompute the column's keys in FP64 with the FP64
+// CTA kernel's own QR and key computation and select with those.  A column
+// goes back to the FP64 CTA kernel (flag FP64_FALLBACK) whenever the FP32
+// result could differ from the FP64 one otherwise: column-scaled kappa(T) or
+// kappa(A-hat) above 300, a singular gap below 1e-5, fewer rows outside I_j
+// than k_j, or an empty W column.
 #pragma once
 
 #include "column_cta.cuh"
@@ -176,7 +178,42 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
     __syncthreads();
     const double margin = cta_select_rows(rs, hk, pick, m, a.rule, j, l - 1, a.tie_tol, red, a.blk);
     const double delta = kMixedDeltaScale * (m + k) * (double)FLT_EPSILON * (double)kap;
-    if (l > 1 && margin <= 2.0 * delta) return false;
+    if (l > 1 && margin <= 2.0 * delta) {
+      // the FP32 keys cannot decide this column: the FP64 CTA kernel's QR and
+      // key computation on an FP64 copy of the tile (in the FP32 tile's slab
+      // space, rewritten for A-hat below), then the selection with those keys,
+      // so I_j is the FP64 kernel's choice
+      double* Tq = reinterpret_cast<double*>(Tw);
+      double* Rq = reinterpret_cast<double*>(Rs);  // KP x KMAX doubles over Rs and Vj (both free here)
+      double* rq = wv;                              // reciprocal diagonal
+      for (size_t i = tid; i < (size_t)me * k; i += kCtaThreads) Tq[(i % me) + (i / me) * ld] = Ts[(i % me) + (i / me) * ld];
+      __syncthreads();
+      cta_householder_qr<double>(Tq, ld, me, k, red, nullptr);
+      for (int i = tid; i < k * k; i += kCtaThreads) {
+        const int r = i % k, c = i / k;
+        Rq[r + c * KP] = (r <= c) ? Tq[r + (size_t)c * ld] : 0.0;
+      }
+      __syncthreads();
+      double part = 0.0;
+      for (int c = tid; c < k; c += kCtaThreads) part = dmax(part, fabs(Rq[c + c * KP]));
+      const double piv = 1e-14 * block_max(part, red);
+      for (int c = tid; c < k; c += kCtaThreads) rq[c] = sc_recip_or_zero(Rq[c + c * KP], piv);
+      for (int r = tid; r < mcap; r += kCtaThreads) pick[r] = 0;
+      __syncthreads();
+      for (int r = tid; r < m; r += kCtaThreads) {  // Q = T R^-1 by rows, into Tq
+        double h = 0.0;
+        for (int c = 0; c < k; ++c) {
+          double acc = Ts[r + (size_t)c * ld];
+          for (int p2 = 0; p2 < c; ++p2) acc -= Tq[r + (size_t)p2 * ld] * Rq[p2 + c * KP];
+          const double z = acc * rq[c];
+          Tq[r + (size_t)c * ld] = z;
+          h += z * z;
+        }
+        hk[r] = h;
+      }
+      __syncthreads();
+      cta_select_rows(rs, hk, pick, m, a.rule, j, l - 1, a.tie_tol, red, a.blk);
+    }
   }
   // I_j
   if (tid == 0) {

@@ -468,8 +468,8 @@ def main():
         peak, src, kname = FP32_TFLOPS * 1e12, "FP32 152 SMs x 128 lanes x 2 flop x 2.07 GHz", "column_mixed_kernel"
     # DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu
     # capture of the current kernel on this workload (dram__bytes_read.sum
-    # 28,351,232 + dram__bytes_write.sum 1,634,304); None where none was taken
-    traffic = 29985536 if (w.name == "convdiff2d_256x256_Wp2" and args.prec == "mixed32" and args.alg == "S") else None
+    # 28,361,472 + dram__bytes_write.sum 1,534,720); None where none was taken
+    traffic = 29896192 if (w.name == "convdiff2d_256x256_Wp2" and args.prec == "mixed32" and args.alg == "S") else None
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic, "kernel": f"{kname} (numeric pass, all buckets)",
             "kernel_ms": kern, "algorithmic_flops": flops, "peak_source": src}

@@ -55,7 +55,7 @@ def test_sparsified_complex_valid(D):
     full = oracle_sp(A, 2, 0, 0)
     o = oracle_sp(A, 2, 0, keep)
     np.testing.assert_array_equal(np.diff(cp), np.diff(o.colptr))  # same counts
-    # candidate magnitudes from the oracle's undropped s_j, to judge near-ties at the cut
+    # candidate magnitudes from the oracle's undropped s_j, to recognise near-ties at the cut
     import scipy.sparse as sp
     M = A.to_scipy()
     d = M.diagonal()

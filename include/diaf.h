@@ -52,11 +52,13 @@ enum { DIAF_ALG_Q = 1, DIAF_ALG_S = 2 };
 
 /* Arithmetic of the numeric phase.  DIAF_PREC_FP64: everything in FP64
  * (complex128 for DIAF_C128).  DIAF_PREC_MIXED32: QR, leverage keys and
- * Jacobi in FP32 (complex64) on an FP64 tile, then one FP64 refinement step
- * of (w_j, v_j) against the FP64 tile and an FP64 residual.  A column whose
- * FP32 leverage decision lies within the FP32 error bound of its threshold,
- * or whose tile is too ill-conditioned for FP32 factors, is computed by the
- * FP64 path instead (flag DIAF_FLAG_FP64_FALLBACK), so I_j is the FP64 choice. */
+ * Jacobi in FP32 (complex64) on an FP64 tile, then an FP64 refinement of
+ * (w_j, v_j) against the FP64 tile and an FP64 residual.  A column whose FP32
+ * leverage decision lies within the FP32 error bound of its threshold gets
+ * its leverage keys recomputed in FP64 (the FP64 path's own QR and key
+ * routines), so I_j is the FP64 choice; a column whose tile is too
+ * ill-conditioned for FP32 factors, or whose refinement cannot converge, is
+ * computed by the FP64 path instead (flag DIAF_FLAG_FP64_FALLBACK). */
 enum { DIAF_PREC_FP64 = 0, DIAF_PREC_MIXED32 = 1 };
 
 /* How I_j (the pattern of column j of V) is obtained.  FIXED: given pattern.
@@ -77,9 +79,9 @@ enum {
   DIAF_FLAG_JACOBI_NOCONV = 8,   /* the Jacobi SVD hit its 30-sweep limit */
   DIAF_FLAG_NONFINITE = 16,      /* NaN or Inf in w_j, v_j or res_j */
   DIAF_FLAG_EMPTY = 32,          /* k_j = 0 (empty W column) */
-  DIAF_FLAG_FP64_FALLBACK = 64,  /* mixed precision: the column was computed by the FP64 path (an FP32
-                                    leverage decision within its error bound, a tile too ill-conditioned
-                                    for FP32 factors, or a large tile: k_j > 32 or m_j > 64) */
+  DIAF_FLAG_FP64_FALLBACK = 64,  /* mixed precision: the column was computed by the FP64 path (a tile
+                                    too ill-conditioned for FP32 factors, a refinement that cannot
+                                    converge, or a large tile of complex A or DIAF-Q) */
   DIAF_FLAG_STABILISED = 128     /* DIAF-Q: v_jj was imposed (stabilised column of Sec. 3.2) */
 };
 

@@ -188,6 +188,55 @@ __device__ void gather_rows(const PlanArgs& a, int j, int32_t* s, int N, int tid
   if (NT == 32) __syncwarp(); else __syncthreads();
 }
 
+// Bitonic sort of s[0..N) (N a power of two, 2 <= N <= 32 PER) by one warp
+// with the keys in registers: element e = 32 i + lane sits in register i of
+// its lane, so compare-exchange partners at distance >= 32 are two registers
+// of one lane and those at distance < 32 are one register of two lanes (a
+// shuffle).  Same network and result as bitonic_sort; reads s once and writes
+// it back once instead of two loads and stores per stage.
+template <int PER>
+__device__ void bitonic_sort_regs(int32_t* s, int N, int lane) {
+  int32_t x[PER];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) x[i] = (32 * i + lane < N) ? s[32 * i + lane] : INT_MAX;
+  for (int k = 2; k <= N; k <<= 1) {
+    // partners at distance 32 JJ (JJ = PER / 2 .. 1, those below k): registers i and i + JJ
+#pragma unroll
+    for (int JJ = PER / 2; JJ >= 1; JJ >>= 1) {
+      if (32 * JJ < k) {
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+          if ((i & JJ) == 0) {
+            const int e = 32 * i + lane;
+            const bool asc = (e & k) == 0;
+            const int32_t a = x[i], b = x[i + JJ];
+            const bool sw = asc ? (a > b) : (a < b);
+            x[i] = sw ? b : a;
+            x[i + JJ] = sw ? a : b;
+          }
+        }
+      }
+    }
+    // partners at distance j < 32: the same register of lanes lane and lane ^ j
+    for (int j = (k >> 1) < 16 ? (k >> 1) : 16; j > 0; j >>= 1) {
+      const bool lower = (lane & j) == 0;
+#pragma unroll
+      for (int i = 0; i < PER; ++i) {
+        const int e = 32 * i + lane;
+        const bool asc = (e & k) == 0;
+        const int32_t p = __shfl_xor_sync(DIAF_FULL, x[i], j);
+        const int32_t lo = x[i] < p ? x[i] : p, hi = x[i] < p ? p : x[i];
+        x[i] = (lower == asc) ? lo : hi;
+      }
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < PER; ++i)
+    if (32 * i + lane < N) s[32 * i + lane] = x[i];
+  __syncwarp();
+}
+
 // The warp path's gather: lane p takes entry p of W(:,j) (its A column's
 // start and length load in parallel), a warp scan of the lengths places each
 // column's run, and each lane copies its run -- a few dependent round trips
@@ -229,7 +278,10 @@ __global__ void __launch_bounds__(kPlanWarps * 32) plan_rows_warp_kernel(PlanArg
     int N = 2;
     while (N < E) N <<= 1;
     gather_rows_warp(a, j, sbuf[warp], N, lane);
-    bitonic_sort<32>(sbuf[warp], N, lane);
+    if (N <= 32) bitonic_sort_regs<1>(sbuf[warp], N, lane);
+    else if (N <= 64) bitonic_sort_regs<2>(sbuf[warp], N, lane);
+    else if (N <= 128) bitonic_sort_regs<4>(sbuf[warp], N, lane);
+    else bitonic_sort_regs<8>(sbuf[warp], N, lane);
     finish_column<32>(a, j, sbuf[warp], E, lane, nullptr, mx);
     __syncwarp();
   }

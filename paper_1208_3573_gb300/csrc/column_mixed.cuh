@@ -107,6 +107,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
   S* rinv = Vj + KP * KMAX;              // FP32 reciprocal diagonal
   float* hk = reinterpret_cast<float*>(rinv + KMAX);  // FP32 keys (MMAX; 2 MMAX floats reserved)
   double* sig = reinterpret_cast<double*>(hk + 2 * MMAX);
+  R* sg = reinterpret_cast<R*>(sig);     // singular values / column norms in the FP32 type (KMAX)
   double* cn = sig + KMAX;               // column norms of the tile
   ColumnIdx ix = carve_idx<KMAX, MMAX>(reinterpret_cast<int32_t*>(cn + KMAX));
 
@@ -256,6 +257,9 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
     if (lane == 0 && a.phase) atomicAdd(&a.phase[20], (unsigned long long)(sw < 0 ? kMaxSweeps : sw));
 #endif
     DIAF_PHASE(7);
+    // (FP32 scans here measured slower: they raised this branch's registers,
+    // 80 -> 86 on the real 16-column tile, which cost more warps per SM than
+    // the FP64 instructions they saved)
     warp_col_norms<S, KP>(Rs, k, k, sig, lane);
     int imin = 0;
     double smin = sig[0], smax = sig[0];
@@ -336,27 +340,28 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
       }
       __syncwarp();
       sw = warp_jacobi_reg<S, KP, KP, kRRMax, KMAX>(M, k, l, Vj, reinterpret_cast<R*>(sig), lane);
-      warp_col_norms<S, KP>(M, k, l, sig, lane);
+      warp_col_norms_r<S, KP>(M, k, l, sg, lane);
       for (int i = lane; i < l * l; i += DIAF_WARP) {
         const int t = i % l, c = i / l;
-        Tw[t + c * LDT] = R(sig[c]) * Vj[t + c * KP];
+        Tw[t + c * LDT] = sg[c] * Vj[t + c * KP];
       }
       __syncwarp();
       kc = l;
     } else {
       compact_rows<S, LDT>(Tw, ix.Iloc, l, k, lane);
       sw = warp_jacobi<S, LDT, KP, KMAX, true>(Tw, l, k, Vj, lane);
-      warp_col_norms<S, LDT>(Tw, l, k, sig, lane);
+      warp_col_norms_r<S, LDT>(Tw, l, k, sg, lane);
     }
     if (sw < 0) flags |= DIAF_FLAG_JACOBI_NOCONV;
     DIAF_PHASE(7);
     int imax = 0;
-    double smax = sig[0];
-    for (int c = 1; c < kc; ++c) if (sig[c] > smax) { smax = sig[c]; imax = c; }
-    double snext = 0.0;
-    for (int c = 0; c < kc; ++c) if (c != imax) snext = dmax(snext, sig[c]);
-    if (!(smax > 0.0)) { hand_back(6); return; }
-    if (kc > 1 && (smax - snext) <= 1e-6 * smax) flags |= DIAF_FLAG_DEGENERATE;
+    R smaxf = sg[0];
+    for (int c = 1; c < kc; ++c) if (sg[c] > smaxf) { smaxf = sg[c]; imax = c; }
+    R snextf = R(0);
+    for (int c = 0; c < kc; ++c) if (c != imax) snextf = fmaxf(snextf, sg[c]);
+    if (!(smaxf > R(0))) { hand_back(6); return; }
+    if (kc > 1 && (smaxf - snextf) <= R(1e-6) * smaxf) flags |= DIAF_FLAG_DEGENERATE;
+    const double smax = smaxf, snext = snextf;
     // the correction below converges from v0's FP32 error (about eps_32 / relative
     // gap) only when that error is small against the gap: closer gaps go to FP64
     const double gap2 = smax * smax - snext * snext;
@@ -432,7 +437,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
       for (int t = lane; t < l; t += DIAF_WARP) rl[t] = sc_cast<S>(cvv[t] - RealOf<SD>(mu) * vv[t]);
       __syncwarp();
       for (int c = lane; c < kc; c += DIAF_WARP) {  // projections on U_c = Tw(:,c) / s_c
-        const R sc = R(sig[c]);
+        const R sc = sg[c];
         S p = sc_zero<S>();
         if (sc > R(0))
           for (int t = 0; t < l; ++t) p += sc_cmul(Tw[t + c * LDT], rl[t]);
@@ -447,7 +452,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
       for (int t = lane; t < l; t += DIAF_WARP) {
         S dv = sc_zero<S>(), rin = sc_zero<S>();
         for (int c = 0; c < kc; ++c) {
-          const R sc = R(sig[c]);
+          const R sc = sg[c];
           if (!(sc > R(0))) continue;
           const S u = (R(1) / sc) * Tw[t + c * LDT];
           dv += u * ac[c];

@@ -503,6 +503,19 @@ __device__ int warp_jacobi_reg(S* G, int p, int q, S* V, RealOf<S>* nrm, int lan
   return -1;
 }
 
+// column norms of G (p x q) into sigma[c], kept in the factor's own real type
+// (reduced-precision callers scan and compare them without FP64 instructions)
+template <class S, int LDG>
+__device__ void warp_col_norms_r(const S* G, int p, int q, RealOf<S>* sigma, int lane) {
+  using R = RealOf<S>;
+  for (int c = lane; c < q; c += DIAF_WARP) {
+    R s = R(0);
+    for (int i = 0; i < p; ++i) s += sc_abs2(G[i + c * LDG]);
+    sigma[c] = sqrt(s);
+  }
+  __syncwarp();
+}
+
 // column norms of G (p x q) into sigma[c] (double)
 template <class S, int LDG>
 __device__ void warp_col_norms(const S* G, int p, int q, double* sigma, int lane) {

@@ -89,14 +89,18 @@ cudaError_t launch_warp_columns(const ColArgs& a, int count_hint, int wpb, cudaS
 template <class S, int KMAX, int MMAX, int ALG>
 struct MixedLaunch {
   static inline size_t configured = 0;
+  static constexpr auto kernel() {
+    if constexpr (mixed_capped<S, KMAX, ALG>()) return column_mixed_kernel_r72<S, KMAX, MMAX, ALG>;
+    else return column_mixed_kernel<S, KMAX, MMAX, ALG>;
+  }
   static cudaError_t launch(const ColArgs& a, int count_hint, int wpb, cudaStream_t s) {
     if (!a.tile_scratch && count_hint > 0) return cudaErrorInvalidValue;
-    return launch_persistent_warps(column_mixed_kernel<S, KMAX, MMAX, ALG>, MixedLayout<S, KMAX, MMAX, ALG>::bytes(),
+    return launch_persistent_warps(kernel(), MixedLayout<S, KMAX, MMAX, ALG>::bytes(),
                                    configured, a, count_hint, wpb, s);
   }
   static size_t scratch(int count_hint, int wpb_req) {
     int grid = 0, wpb = 1;
-    if (persistent_warps_shape(column_mixed_kernel<S, KMAX, MMAX, ALG>, MixedLayout<S, KMAX, MMAX, ALG>::bytes(),
+    if (persistent_warps_shape(kernel(), MixedLayout<S, KMAX, MMAX, ALG>::bytes(),
                                configured, count_hint, wpb_req, &grid, &wpb) != cudaSuccess)
       return 0;
     return (size_t)grid * wpb * MixedLayout<S, KMAX, MMAX, ALG>::tile_bytes();

@@ -524,14 +524,18 @@ __global__ void column_mixed_kernel(ColArgs a) {
   column_mixed_loop<S, KMAX, MMAX, ALG>(a);
 }
 
-// The same kernel capped at 72 registers: the real 16-column DIAF-Q tiles run
-// 5 % faster so (27 instead of 24 warps per SM, no spills).  The DIAF-S one
-// did not gain from a cap; an explicit cap on the others raised their
-// register counts (the compiler's own choice is the better one there).
-template <class S, int KMAX, int MMAX, int ALG>
-__global__ void __maxnreg__(72) column_mixed_kernel_r72(ColArgs a) {
+// The same kernel with a register cap CAP: the real 16-column DIAF-Q tiles
+// run 5 % faster at 72 (27 instead of 24 warps per SM, no spills).  The
+// DIAF-S one did not gain from a cap; an explicit cap on the others raised
+// their register counts (the compiler's own choice is the better one there).
+template <class S, int KMAX, int MMAX, int ALG, int CAP>
+__global__ void __maxnreg__((CAP)) column_mixed_kernel_cap(ColArgs a) {
   column_mixed_loop<S, KMAX, MMAX, ALG>(a);
 }
 
+// 0: no cap (a cap of 112 on the complex 16-column tiles, 18 instead of 16
+// warps per SM, measured no faster)
 template <class S, int KMAX, int ALG>
-constexpr bool mixed_capped() { return sizeof(S) == 4 && KMAX <= 16 && ALG == DIAF_ALG_Q; }
+constexpr int mixed_reg_cap() {
+  return (sizeof(S) == 4 && KMAX <= 16 && ALG == DIAF_ALG_Q) ? 72 : 0;
+}

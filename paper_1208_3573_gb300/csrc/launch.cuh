@@ -90,7 +90,8 @@ template <class S, int KMAX, int MMAX, int ALG>
 struct MixedLaunch {
   static inline size_t configured = 0;
   static constexpr auto kernel() {
-    if constexpr (mixed_capped<S, KMAX, ALG>()) return column_mixed_kernel_r72<S, KMAX, MMAX, ALG>;
+    constexpr int cap = mixed_reg_cap<S, KMAX, ALG>();
+    if constexpr (cap > 0) return column_mixed_kernel_cap<S, KMAX, MMAX, ALG, (cap > 0 ? cap : 255)>;
     else return column_mixed_kernel<S, KMAX, MMAX, ALG>;
   }
   static cudaError_t launch(const ColArgs& a, int count_hint, int wpb, cudaStream_t s) {

@@ -1,7 +1,9 @@
 // Mixed-precision per-column kernel: the tile is gathered in FP64 (complex128)
-// and copied to FP32 (complex64); QR, leverage keys and the Jacobi SVD run in
-// FP32; then (w_j, v_j) get one FP64 refinement step against the FP64 tile
-// and the residual ||A w - v|| is evaluated in FP64.
+// into the warp's slab in global memory and factorised in FP32 (complex64):
+// Householder QR (tile rows in registers for tiles of up to 32 x 16, in
+// shared memory otherwise), leverage keys and the one-sided Jacobi SVD; then
+// (w_j, v_j) are refined in FP64 against the FP64 tile and the residual
+// ||A w - v|| is evaluated in FP64.
 //
 //   DIAF-S: the FP32 Jacobi gives R-hat V = U diag(sigma); x0 = V e_min.
 //     With H = A-hat^* A-hat taken from the FP64 tile, V^* H V is diagonal to

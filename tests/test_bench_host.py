@@ -1,0 +1,55 @@
+"""Host logic of bench.py that needs no GPU: the clock sampler's summary of
+nvidia-smi lines (reasons, medians, the fallback to the sample taken before a
+short timed region) and the algorithmic flop count's closed form."""
+import os
+import sys
+
+import numpy as np
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def _line(sm, mx, hw="Not Active", hwt="Not Active", swt="Not Active", cap="Not Active"):
+    return f"0, {sm}, {mx}, 900.00, 0x0000000000000000, {hw}, {hwt}, {swt}, {cap}"
+
+
+def test_clock_summary_during_region():
+    c = bench.ClockSampler(0)
+    c.first = _line(2070, 2070) + "\n"
+    c.out = "\n".join([_line(2070, 2070), _line(2055, 2070, cap="Active"), _line(2070, 2070)]) + "\n"
+    s = c.summary()
+    assert s["samples"] == 3 and s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"] and "note" not in s
+
+
+def test_clock_summary_flags_throttling():
+    c = bench.ClockSampler(0)
+    c.first = ""
+    c.out = _line(1500, 2070, hwt="Active") + "\n"
+    s = c.summary()
+    assert s["reasons"] == ["hw_thermal_slowdown"] and s["sm_mhz"] == 1500.0
+
+
+def test_clock_summary_short_region_falls_back_to_the_first_sample():
+    c = bench.ClockSampler(0)
+    c.first = _line(2070, 2070) + "\n"
+    c.out = ""
+    s = c.summary()
+    assert s["samples"] == 0 and s["sm_mhz"] == 2070.0 and "note" in s
+
+
+def test_clock_summary_without_sampler():
+    c = bench.ClockSampler(0)
+    c.first, c.out = "", ""
+    assert c.summary()["reasons"] == ["unsampled"]
+
+
+def test_algorithmic_flops_closed_form():
+    # one column, k = 2, m = 3, l = 1, real DIAF-S: QR of T 2k^2(m - k/3), leverage m k^2,
+    # QR of A-hat 2k^2(max(m - l, k) - k/3), SVD 12 k^3, v 2 l k, residual 2 m k
+    m, k, l = np.array([3]), np.array([2]), np.array([1])
+    want = 2 * 4 * (3 - 2 / 3) + 3 * 4 + 2 * 4 * (max(3 - 1, 2) - 2 / 3) + 12 * 8 + 2 * 1 * 2 + 2 * 3 * 2
+    got = bench.algorithmic_flops(m, k, l, "S", False)
+    assert abs(got - want) < 1e-9 * want
+    assert abs(bench.algorithmic_flops(m, k, l, "S", True) - 4 * want) < 1e-9 * want

@@ -13,7 +13,8 @@
  *    the work enqueued on `stream` has finished.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
  *    Calls enqueue their work on it in order.  Calls that must size their
- *    outputs from the data (diaf_factor) synchronise `stream` once, as noted.
+ *    outputs from the data (diaf_factor, the first diaf_apply) synchronise
+ *    `stream`, as noted.
  *  - Complex values are interleaved (re, im) doubles (DIAF_C128).
  *  - Every function returns diaf_status; nothing throws across the ABI.
  *    After a non-OK status, diaf_last_error() gives a one-line reason
@@ -142,7 +143,8 @@ typedef struct diaf_factors diaf_factors; /* opaque, library-owned */
  *   V       : V pattern specification.
  *   alg     : DIAF_ALG_Q or DIAF_ALG_S.   prec: DIAF_PREC_*.
  *   out     : receives a new handle; free with diaf_free.
- * Synchronises `stream` once (after the symbolic pass, to size V).  The
+ * Synchronises `stream` twice (in the symbolic pass: to size the row-union
+ * storage, then V and the size buckets).  The
  * numeric work is enqueued on `stream`; the outputs are ready when it has
  * run.  Errors: EINVAL (arguments, unsorted / out-of-range indices),
  * ENOMEM, ECUDA, EUNSUPPORTED (a column needs more than 4096 gathered
@@ -245,6 +247,21 @@ diaf_status diaf_get_factors(const diaf_factors* F, diaf_csc* W, diaf_csc* V, co
  * (one block, a barrier between levels) and the W SpMV.  Errors: EINVAL (V not
  * triangular or zero diagonal -- found by the first call), ENOMEM, ECUDA. */
 diaf_status diaf_apply(diaf_factors* F, const void* x, void* y, void* stream);
+
+/* The level schedule of the apply's triangular solve, on the host (no GPU
+ * call): V given by its columns in host arrays (colptr int32[n+1] with
+ * colptr[0] = 0, rowidx int32[colptr[n]], rows in any order within a
+ * column; the values are not looked at).  level[i] (host int32[n], written)
+ * receives the depth of row i in V's dependency graph -- row i waits for t_j
+ * when V(i,j) != 0, i != j, so rows of one level are independent (the
+ * level-scheduled form of the substitution in eq. afac's V^-1, Sec. 2.3);
+ * *nlev the number of levels (max level + 1, 0 when n = 0); *upper 1 for an
+ * upper (or diagonal) V, 0 for a lower one.  This is the pass diaf_apply
+ * runs when it prepares the solve.  Errors: EINVAL -- NULL pointer, n < 0,
+ * malformed colptr, a row index out of range, V neither upper nor lower
+ * triangular, or a missing diagonal entry. */
+diaf_status diaf_level_schedule(int32_t n, const int32_t* colptr, const int32_t* rowidx, int32_t* level,
+                                int32_t* nlev, int32_t* upper);
 
 /* y = W V^-1 x exactly as diaf_apply computes it, but allocating nothing.
  * (The paper has no counterpart: this is an interface for callers that must

@@ -675,6 +675,44 @@ unsigned char* stage_get(size_t bytes) {
   return g_stage.buf;
 }
 
+// The level schedule of a triangular V given by its columns (host arrays):
+// lev[i] = depth of row i in V's dependency graph (row i waits for t_j when
+// V(i,j) != 0, i != j), pushed column by column in the solve's order (lev[j]
+// is final when column j is reached).  The pass assumes an upper V (columns
+// descending) and checks the structure on the way: an entry below the
+// diagonal restarts it for a lower V (ascending), where an entry above the
+// diagonal means V is not triangular.  Returns 0, 1 (not triangular), 2 (a
+// diagonal entry missing) or 3 (a row index out of range).
+int level_schedule_host(int n, const int32_t* cp, const int32_t* ri, int32_t* lev, int* nlev, bool* upper) {
+  auto pass = [&](bool up) -> int {
+    for (int i = 0; i < n; ++i) lev[i] = 0;
+    *nlev = n > 0 ? 1 : 0;
+    bool nodiag = false;
+    for (int step = 0; step < n; ++step) {
+      const int j = up ? n - 1 - step : step;
+      const int lj = lev[j] + 1;
+      if (lj > *nlev) *nlev = lj;
+      bool d = false;
+      for (int p = cp[j]; p < cp[j + 1]; ++p) {
+        const int i = ri[p];
+        if (i < 0 || i >= n) return 3;
+        if (i == j) { d = true; continue; }
+        if (up ? i > j : i < j) return 1;
+        if (lev[i] < lj) lev[i] = lj;
+      }
+      nodiag |= !d;
+    }
+    return nodiag ? 2 : 0;
+  };
+  *upper = true;
+  int r = pass(true);
+  if (r == 1) {
+    *upper = false;
+    r = pass(false);
+  }
+  return r;
+}
+
 // Marks the end of the copies out of the staging buffer on stream s.
 cudaError_t stage_release(cudaStream_t s) {
   int dev = 0;
@@ -747,45 +785,19 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
     DIAF_CU(ce);
     DIAF_CU(se);
   }
-  // level of every row: its depth in the dependency graph of V (host, O(nnz)),
-  // pushed column by column in the solve's order: lev[j] is final when column
-  // j is reached, and row i of column j (i != j) waits for t_j.  The pass
-  // assumes an upper V (columns descending) and checks the structure on the
-  // way: an entry below the diagonal restarts it for a lower V (ascending),
-  // where an entry above the diagonal means V is not triangular.  The device
-  // checks the diagonal's values meanwhile.
+  // level of every row (host, O(nnz)); the device checks the diagonal's values meanwhile
   std::vector<int32_t> lev(n, 0);
   int nlev = 0;
-  bool nodiag = false;
-  auto level_pass = [&](bool upper) -> bool {
-    std::fill(lev.begin(), lev.end(), 0);
-    nlev = n > 0 ? 1 : 0;
-    nodiag = false;
-    for (int step = 0; step < n; ++step) {
-      const int j = upper ? n - 1 - step : step;
-      const int lj = lev[j] + 1;
-      if (lj > nlev) nlev = lj;
-      bool d = false;
-      for (int p = cp[j]; p < cp[j + 1]; ++p) {
-        const int i = ri[p];
-        if (i == j) { d = true; continue; }
-        if (upper ? i > j : i < j) return false;
-        if (lev[i] < lj) lev[i] = lj;
-      }
-      nodiag |= !d;
-    }
-    return true;
-  };
-  F->v_upper = true;
-  if (!level_pass(true)) {
-    F->v_upper = false;
-    if (!level_pass(false)) {
-      (void)cudaStreamSynchronize(s);
-      cudaEventDestroy(ev[0]);
-      cudaEventDestroy(ev[1]);
-      return fail(DIAF_EINVAL, "V is not triangular");
-    }
+  bool vup = true;
+  const int ls = level_schedule_host(n, cp, ri, lev.data(), &nlev, &vup);
+  F->v_upper = vup;
+  if (ls == 1 || ls == 3) {
+    (void)cudaStreamSynchronize(s);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    return fail(DIAF_EINVAL, ls == 1 ? "V is not triangular" : "V has a row index out of range");
   }
+  const bool nodiag = ls == 2;
   se = cudaEventSynchronize(ev[1]);
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
@@ -820,6 +832,26 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   DIAF_CU(remap_columns(F->nnz_w, pos, F->Wr.colidx, F->Wl.colidx, s));
   DIAF_CU(F->alloc((char**)&F->tbuf, esz * n));
   F->apply_ready = true;
+  return DIAF_OK;
+}
+
+diaf_status diaf_level_schedule(int32_t n, const int32_t* colptr, const int32_t* rowidx, int32_t* level,
+                                int32_t* nlev, int32_t* upper) {
+  g_last_error.clear();
+  if (n < 0) return fail(DIAF_EINVAL, "n must be >= 0");
+  if (!colptr || !level || !nlev || !upper || (n > 0 && colptr[n] > 0 && !rowidx))
+    return fail(DIAF_EINVAL, "NULL argument");
+  if (colptr[0] != 0) return fail(DIAF_EINVAL, "colptr[0] must be 0");
+  for (int32_t j = 0; j < n; ++j)
+    if (colptr[j + 1] < colptr[j]) return fail(DIAF_EINVAL, "colptr must be non-decreasing");
+  int nl = 0;
+  bool up = true;
+  const int r = level_schedule_host(n, colptr, rowidx, level, &nl, &up);
+  if (r == 1) return fail(DIAF_EINVAL, "V is not triangular");
+  if (r == 2) return fail(DIAF_EINVAL, "V has a missing diagonal entry");
+  if (r == 3) return fail(DIAF_EINVAL, "V has a row index out of range");
+  *nlev = nl;
+  *upper = up ? 1 : 0;
   return DIAF_OK;
 }
 

@@ -146,6 +146,8 @@ def lib() -> ctypes.CDLL:
                                             vp, ctypes.POINTER(ctypes.c_int64), vp]
         L.diaf_sparsified_fill.argtypes = [ctypes.POINTER(CSC_t), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                            vp, vp, vp]
+        L.diaf_level_schedule.argtypes = [ctypes.c_int32, vp, vp, vp, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int32)]
         L.diaf_status_string.argtypes = [ctypes.c_int]
         L.diaf_status_string.restype = ctypes.c_char_p
         L.diaf_last_error.restype = ctypes.c_char_p
@@ -480,6 +482,20 @@ def sparsified_powers(A: DeviceCSC, k: int = 2, p_l: int = 0, keep: int = 0, str
     rowidx = torch.empty(max(int(nnz.value), 1), dtype=torch.int32, device=A.colptr.device)
     _check(L.diaf_sparsified_fill(ctypes.byref(a), k, p_l, keep, _ptr(colptr), _ptr(rowidx), s))
     return DeviceCSC(A.n, colptr, rowidx[:int(nnz.value)])
+
+
+def level_schedule(colptr, rowidx):
+    """Host-side level schedule of a triangular V given by its columns (numpy
+    int32 arrays): (level per row, number of levels, upper?).  No GPU call."""
+    import numpy as np
+    cp = np.ascontiguousarray(colptr, dtype=np.int32)
+    ri = np.ascontiguousarray(rowidx, dtype=np.int32)
+    n = cp.size - 1
+    lev = np.zeros(max(n, 1), dtype=np.int32)
+    nlev, up = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(lib().diaf_level_schedule(n, cp.ctypes.data, ri.ctypes.data if ri.size else None, lev.ctypes.data,
+                                     ctypes.byref(nlev), ctypes.byref(up)))
+    return lev[:n], int(nlev.value), bool(up.value)
 
 
 def contiguous_blocks(n: int, size: int, device="cuda") -> torch.Tensor:

@@ -95,7 +95,7 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
   using L = MixedLayout<S, KMAX, MMAX, ALG>;
   constexpr int LDT = L::LDT, KP = L::KP, kRR = L::kRR;
   // Ts: the FP64 tile (LDT x KMAX) and Tx: two tiles of scratch, in the slab
-  SD* rinvD = reinterpret_cast<SD*>(smem);  // FP64 reciprocal diagonal of the FP32 factor
+  SD* rinvD = reinterpret_cast<SD*>(smem);  // KMAX FP64 scratch: FP64-key reciprocal diagonal, DIAF-S coefficients
   SD* wv = rinvD + KMAX;                 // w
   SD* gg = wv + KMAX;                    // k-vector scratch
   SD* vv = gg + KMAX;                    // v (MMAX)

@@ -180,17 +180,24 @@ typedef struct {
   int32_t bucket_cols[8];
 } diaf_factor_info;
 
-/* Sizes and bucket statistics of a factorisation (host copy; no sync). */
+/* Sizes and bucket statistics of a factorisation (host copy; no sync):
+ * bookkeeping of the column-wise setup of Sec. 2, no passage of its own.
+ * Errors: EINVAL (NULL F or info). */
 diaf_status diaf_factor_info_get(const diaf_factors* F, diaf_factor_info* info);
 
-/* diaf_factor with launch tuning (NULL = defaults). */
+/* diaf_factor (Sec. 2.1, 2.2, 3.1) with launch tuning (NULL = defaults);
+ * the tuning changes only how the independent columns are batched, never a
+ * result.  Arguments, ownership and errors as diaf_factor, plus EINVAL for
+ * tuning values out of range. */
 diaf_status diaf_factor_tuned(const diaf_csc* A, const diaf_pattern* PW, const diaf_vspec* V, int32_t alg,
                               int32_t prec, const diaf_tuning* tuning, void* stream, diaf_factors** out);
 
 /* Times the numeric pass of diaf_factor_tuned over the bucket edges and the
  * warp kernels' CTA sizes (coordinate descent, best of two runs per point)
- * and returns the fastest tuning and its numeric-pass time in ms.  Runs
- * about 15 factorisations of the given problem. */
+ * and returns the fastest tuning (*best, host) and its numeric-pass time in
+ * ms (*best_ms, host).  Runs about 15 factorisations of the given problem.
+ * Launch tuning of the column-parallel setup (Sec. 2), not a passage of the
+ * paper.  Errors as diaf_factor. */
 diaf_status diaf_autotune(const diaf_csc* A, const diaf_pattern* PW, const diaf_vspec* V, int32_t alg, int32_t prec,
                           void* stream, diaf_tuning* best, float* best_ms);
 
@@ -204,20 +211,25 @@ diaf_status diaf_autotune(const diaf_csc* A, const diaf_pattern* PW, const diaf_
  * unchanged except A's values.  diaf_plan_create synchronises `stream`; it
  * does not run the numeric pass. */
 typedef struct diaf_plan diaf_plan;
+/* Errors of diaf_plan_create as diaf_factor (*out receives the plan; free
+ * with diaf_plan_free). */
 diaf_status diaf_plan_create(const diaf_csc* A, const diaf_pattern* PW, const diaf_vspec* V, int32_t alg,
                              int32_t prec, const diaf_tuning* tuning, void* stream, diaf_plan** out);
 /* Enqueues the numeric pass on `stream` (one graph launch); the plan's
- * factors are ready when it has run.  Executions must not overlap. */
+ * factors are ready when it has run.  Executions must not overlap.
+ * Errors: EINVAL (NULL plan), ECUDA (graph launch). */
 diaf_status diaf_plan_execute(diaf_plan* P, void* stream);
-/* The plan's factors (borrowed; freed by diaf_plan_free). */
+/* The plan's factors (borrowed; freed by diaf_plan_free; NULL for NULL). */
 diaf_factors* diaf_plan_factors(diaf_plan* P);
+/* Frees the plan, its graph and its factors.  NULL is ignored. */
 void diaf_plan_free(diaf_plan* P);
 
 /* Timings of a factorisation from CUDA events recorded on its stream (waits
  * for them): ms[0] the whole diaf_factor call (first to last enqueued work,
  * host synchronisations included), ms[1] the numeric pass, ms[2 + b] the
  * numeric kernel of size bucket b (0 when the bucket was empty).  nms is the
- * capacity of ms and must be >= 2 + n_buckets. */
+ * capacity of ms (host floats) and must be >= 2 + n_buckets.  Measurement,
+ * not a passage of the paper.  Errors: EINVAL (NULL, nms too small), ECUDA. */
 diaf_status diaf_factor_timings(const diaf_factors* F, float* ms, int32_t nms);
 
 /* Mixed precision: the number of columns per size bucket that the FP64 path
@@ -226,13 +238,16 @@ diaf_status diaf_factor_timings(const diaf_factors* F, float* ms, int32_t nms);
  * zeros for the FP64 form.  Waits for F's stream.  nb >= n_buckets. */
 diaf_status diaf_factor_fallbacks(const diaf_factors* F, int32_t* counts, int32_t nb);
 
-/* Number of CUDA kernels this library has launched in this process. */
+/* Number of CUDA kernels this library has launched in this process
+ * (instrumentation; never fails). */
 long long diaf_launch_count(void);
 
-/* Borrowed device views of the outputs (valid until diaf_free):
- * W: colptr/rowidx = copies of PW, vals nnz_w scalars;  V: CSC with column j
- * on I_j (sorted), vals nnz_v scalars;  col_res: double[n];  col_flags:
- * uint32[n] (DIAF_FLAG_* bits).  Any output pointer may be NULL. */
+/* Borrowed device views of the outputs (valid until diaf_free): the W and V
+ * of eq. afac (Sec. 2.3), column j of each from Sec. 2.1 / 2.2, and
+ * res_j = ||A w_j - v_j||.  W: colptr/rowidx = copies of PW, vals nnz_w
+ * scalars;  V: CSC with column j on I_j (sorted), vals nnz_v scalars;
+ * col_res: double[n];  col_flags: uint32[n] (DIAF_FLAG_* bits).  Any output
+ * pointer may be NULL.  Errors: EINVAL (NULL F). */
 diaf_status diaf_get_factors(const diaf_factors* F, diaf_csc* W, diaf_csc* V, const double** col_res,
                              const uint32_t** col_flags);
 
@@ -284,17 +299,22 @@ diaf_status diaf_apply_static(diaf_factors* F, const void* x, void* y, void* str
 /* (Triangular V only: factors of DIAF_RULE_BLOCK give DIAF_EUNSUPPORTED.) */
 
 /* Waits for `stream` and reports device-side errors recorded by earlier
- * calls on F (bounded-wait timeouts, capacity overflows) as a status. */
+ * calls on F (bounded-wait timeouts, capacity overflows) as a status
+ * (infrastructure, no passage of the paper).  Errors: EINVAL (NULL F),
+ * ETIMEOUT / EUNSUPPORTED as recorded, ECUDA. */
 diaf_status diaf_sync(diaf_factors* F, void* stream);
 
 /* Frees F and every device buffer it owns (stream-ordered on the stream F was
- * created on; that stream must still exist).  NULL is ignored. */
+ * created on; that stream must still exist).  NULL is ignored.  Never fails. */
 void diaf_free(diaf_factors* F);
 
 typedef struct diaf_solver diaf_solver; /* opaque: A in row-oriented form for Krylov solves */
 
-/* Prepares A for the Krylov solvers (row-oriented copy; allocates). */
+/* Prepares A for the Krylov solvers of Sec. 5 (row-oriented copy of the
+ * caller's CSC, owned by the solver; allocates).  Errors: EINVAL (NULL, bad
+ * sizes), ENOMEM, ECUDA. */
 diaf_status diaf_solver_create(const diaf_csc* A, void* stream, diaf_solver** out);
+/* Frees the solver.  NULL is ignored. */
 void diaf_solver_free(diaf_solver* S);
 
 typedef struct {
@@ -328,6 +348,8 @@ diaf_status diaf_bicgstab(diaf_solver* S, diaf_factors* F, const void* b, void* 
  * and diaf_sparsified_fill writes the sorted rows of every column. */
 diaf_status diaf_sparsified_count(const diaf_csc* A, int32_t k, int32_t p_l, int32_t keep, int32_t* colptr,
                                   int64_t* nnz, void* stream);
+/* Second pass of the sparsified-powers pattern (Sec. 4.1): writes the rows of
+ * every column into rowidx (device, *nnz from the count) at colptr. */
 diaf_status diaf_sparsified_fill(const diaf_csc* A, int32_t k, int32_t p_l, int32_t keep, const int32_t* colptr,
                                  int32_t* rowidx, void* stream);
 
@@ -348,14 +370,19 @@ diaf_status diaf_sparsified_fill(const diaf_csc* A, int32_t k, int32_t p_l, int3
 #define DIAF_PROP_HIDDEN 32
 #define DIAF_PROP_NPARAM 1377
 
-/* Features of every entry of CAND (same n as A, sorted columns of at most 32
- * rows; DIAF_EUNSUPPORTED for a longer column).  Synchronises `stream`. */
+/* (Not in the paper: the learned proposal.)  Features of every entry of CAND
+ * (same n as A, sorted columns of at most 32 rows; DIAF_EUNSUPPORTED for a
+ * longer column) into feat (device, [CAND->nnz][8]).  Synchronises `stream`.
+ * Errors: EINVAL (NULL, sizes), EUNSUPPORTED, ECUDA. */
 diaf_status diaf_propose_features(const diaf_csc* A, const diaf_pattern* CAND, float* feat, void* stream);
 
-/* out[s] = network(feat[s]) for s < nrows.  Stream-ordered, allocates nothing. */
+/* (Not in the paper.)  out[s] = network(feat[s]) for s < nrows (device
+ * arrays).  Stream-ordered, allocates nothing.  Errors: EINVAL (NULL,
+ * nrows < 0), ECUDA. */
 diaf_status diaf_mlp_forward(const float* params, const float* feat, int64_t nrows, float* out, void* stream);
 
-/* grad = d/dparams of loss = (1/nrows) sum_s (network(feat[s]) - target[s])^2,
+/* (Not in the paper.)
+ * grad = d/dparams of loss = (1/nrows) sum_s (network(feat[s]) - target[s])^2,
  * *loss = that loss (both overwritten; grad has DIAF_PROP_NPARAM floats).
  * Per-block partial sums are added in block order: the result is reproducible.
  * Allocates (stream-ordered) one scratch row of DIAF_PROP_NPARAM + 1 floats
@@ -363,12 +390,15 @@ diaf_status diaf_mlp_forward(const float* params, const float* feat, int64_t nro
 diaf_status diaf_mlp_grad(const float* params, const float* feat, const float* target, int64_t nrows, float* grad,
                           float* loss, void* stream);
 
-/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on params with moment
- * buffers m, v (DIAF_PROP_NPARAM floats each, zero before step 1); step >= 1. */
+/* (Not in the paper.)  One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on
+ * params with moment buffers m, v (DIAF_PROP_NPARAM device floats each, zero
+ * before step 1); step >= 1 (EINVAL otherwise). */
 diaf_status diaf_mlp_adam(float* params, const float* grad, float* m, float* v, int32_t step, float lr, void* stream);
 
-/* Keeps, per column j, min(keep, |CAND(:,j)|) rows: j itself when it is a
- * candidate, then the best scores (ties to the lower row; NaN ranks last).
+/* (Not in the paper: the learned proposal's J_j, in place of the fixed rules
+ * of Sec. 4.)  Keeps, per column j, min(keep, |CAND(:,j)|) rows: j itself
+ * when it is a candidate, then the best scores (ties to the lower row; NaN
+ * ranks last).
  * colptr (n+1) and rowidx (at most n*keep) are written; rows come out sorted. */
 diaf_status diaf_propose_select(const diaf_pattern* CAND, const float* score, int32_t keep, int32_t* colptr,
                                 int32_t* rowidx, void* stream);
@@ -384,6 +414,9 @@ diaf_status diaf_propose_select(const diaf_pattern* CAND, const float* score, in
 diaf_status diaf_gmres(diaf_solver* S, diaf_factors* F, const void* b, void* x, double tol, int32_t restart,
                        int32_t maxit, void* stream, diaf_solve_info* info);
 
+/* Infrastructure: a static name for a status (never NULL), and the calling
+ * thread's one-line reason for its last non-OK status ("" if none; valid
+ * until that thread's next call). */
 const char* diaf_status_string(diaf_status s);
 const char* diaf_last_error(void);
 

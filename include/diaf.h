@@ -242,6 +242,21 @@ diaf_status diaf_factor_fallbacks(const diaf_factors* F, int32_t* counts, int32_
  * (instrumentation; never fails). */
 long long diaf_launch_count(void);
 
+/* Caps the device memory that the setup and apply paths (diaf_factor,
+ * diaf_factor_tuned, diaf_plan_*, diaf_apply and the factor handles they
+ * keep) may hold at one time, over all handles of the process: bytes > 0 is
+ * the cap, 0 removes it (the default).  An allocation that would exceed the
+ * cap is not attempted: the call that needed it frees what it had taken and
+ * returns DIAF_ENOMEM.  Lowering the cap below the bytes already held frees
+ * nothing; only later allocations are refused.  (Resource control, no passage
+ * of the paper; the Krylov solvers, the learned proposal and the sparsified
+ * powers are not counted.)  Errors: EINVAL (bytes < 0). */
+diaf_status diaf_set_device_memory_limit(int64_t bytes);
+
+/* Device bytes the setup and apply paths hold now (what the cap above
+ * counts).  Never fails. */
+int64_t diaf_device_memory_in_use(void);
+
 /* Borrowed device views of the outputs (valid until diaf_free): the W and V
  * of eq. afac (Sec. 2.3), column j of each from Sec. 2.1 / 2.2, and
  * res_j = ||A w_j - v_j||.  W: colptr/rowidx = copies of PW, vals nnz_w
@@ -281,9 +296,9 @@ diaf_status diaf_level_schedule(int32_t n, const int32_t* colptr, const int32_t*
 /* y = W V^-1 x exactly as diaf_apply computes it, but allocating nothing.
  * (The paper has no counterpart: this is an interface for callers that must
  * not allocate device memory when they apply the preconditioner -- code
- * running inside a device-memory budget fixed at start-up, a Krylov loop
- * being recorded into a CUDA graph, where plain cudaMalloc cannot be
- * captured, or a host framework whose allocator owns all device memory.)
+ * running inside a device-memory budget fixed at start-up, or a host
+ * framework whose allocator owns all device memory and forbids allocations
+ * by the libraries it calls.)
  * Such callers set up beforehand: diaf_factor, then one diaf_apply on F,
  * which builds the row-oriented copies of W and V.  Without that first
  * diaf_apply this call returns DIAF_EINVAL.
@@ -291,10 +306,15 @@ diaf_status diaf_level_schedule(int32_t n, const int32_t* colptr, const int32_t*
  * is one fixed device array of about 5.3 MB inside the library, held by
  * every GPU that loads it until the process exits; n is limited to 262,144
  * rows (DIAF_EINVAL beyond).  The first call on each device looks up the
- * array's device address and clears its flags: make that first call before
- * any stream capture.  All calls on a device share the array and leave their
- * contents in it, so calls that overlap on the GPU (different streams, or
- * several host threads) race; serialise them.  x, y as for diaf_apply. */
+ * array's device address (cached for the process: do not use this entry
+ * point across a cudaDeviceReset); make that first call before any stream
+ * capture.  Every call clears the flags of its n rows and the counter on
+ * `stream` before the solve.  All calls on a device share the array and
+ * leave their contents in it, so calls that overlap on the GPU (different
+ * streams, or several host threads) race; serialise them.  The solve's
+ * waits are bounded: one that runs out leaves y wrong but still returns
+ * DIAF_OK here; it is reported by the next diaf_sync(F, stream)
+ * (DIAF_ETIMEOUT), so check that after the apply.  x, y as for diaf_apply. */
 diaf_status diaf_apply_static(diaf_factors* F, const void* x, void* y, void* stream);
 /* (Triangular V only: factors of DIAF_RULE_BLOCK give DIAF_EUNSUPPORTED.) */
 
@@ -331,7 +351,7 @@ typedef struct {
 diaf_status diaf_bicgstab(diaf_solver* S, diaf_factors* F, const void* b, void* x, double tol, int32_t maxit,
                           void* stream, diaf_solve_info* info);
 
-/* ---- Sparsified powers (Sec. 4.1, Algorithm 3) --------------------------------
+/* ---- Sparsified powers (Sec. 4.1, Algorithm 1) --------------------------------
  * The W pattern from the truncated Neumann series with the diagonal initial
  * subspace V_0: S = -D^-1 (A - D) (so that A = D (I - S); the structure does
  * not depend on the sign), per column s = t = e_j, then k times t = S t,

@@ -1,4 +1,4 @@
-"""CPU oracle of the sparsified-powers W pattern (Sec. 4.1, Algorithm 3) --
+"""CPU oracle of the sparsified-powers W pattern (Sec. 4.1, Algorithm 1) --
 TEST INFRASTRUCTURE ONLY.
 
 Initial subspace V_0 = diagonal matrices, so S = -D^{-1}(A - D) (the sign

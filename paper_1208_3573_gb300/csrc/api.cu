@@ -6,6 +6,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "factors.cuh"
@@ -28,6 +29,46 @@ extern "C" int diaf_phase_cycles(unsigned long long* out, int reset) {
 #endif
 static thread_local std::string g_last_error;
 void diaf_set_last_error(const char* msg) { g_last_error = msg; }
+
+namespace {
+// Device bytes held by the setup and apply paths, and the cap on them.
+std::mutex g_mem_mu;
+std::unordered_map<void*, size_t> g_mem_held;
+size_t g_mem_total = 0;
+size_t g_mem_cap = 0;  // 0: no cap
+}  // namespace
+
+cudaError_t diaf_dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_mem_mu);
+    if (g_mem_cap && g_mem_total + bytes > g_mem_cap) return cudaErrorMemoryAllocation;
+    g_mem_total += bytes;  // reserved before the call, so concurrent requests see it
+  }
+  void* q = nullptr;
+  cudaError_t e = cudaMallocAsync(&q, bytes, s);
+  std::lock_guard<std::mutex> lock(g_mem_mu);
+  if (e != cudaSuccess) {
+    g_mem_total -= bytes;
+    return e;
+  }
+  g_mem_held[q] = bytes;
+  *p = q;
+  return cudaSuccess;
+}
+
+void diaf_dev_free(void* p, cudaStream_t s) {
+  if (!p) return;
+  {
+    std::lock_guard<std::mutex> lock(g_mem_mu);
+    auto it = g_mem_held.find(p);
+    if (it != g_mem_held.end()) {
+      g_mem_total -= it->second;
+      g_mem_held.erase(it);
+    }
+  }
+  cudaFreeAsync(p, s);
+}
 void diaf_note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 namespace {
@@ -57,14 +98,14 @@ struct Pool {
   cudaError_t get(T** p, size_t count) {
     size_t bytes = sizeof(T) * (count > 0 ? count : 1);
     void* q = nullptr;
-    cudaError_t e = cudaMallocAsync(&q, bytes, s);
+    cudaError_t e = diaf_dev_alloc(&q, bytes, s);
     if (e != cudaSuccess) return e;
     ptrs.push_back(q);
     *p = static_cast<T*>(q);
     return cudaSuccess;
   }
   void release() {
-    for (void* p : ptrs) cudaFreeAsync(p, s);
+    for (void* p : ptrs) diaf_dev_free(p, s);
     ptrs.clear();
   }
   ~Pool() { release(); }
@@ -103,13 +144,25 @@ const char* diaf_last_error(void) { return g_last_error.c_str(); }
 
 void diaf_free(diaf_factors* F) {
   if (!F) return;
-  for (void* p : F->owned) cudaFreeAsync(p, F->stream);
+  for (void* p : F->owned) diaf_dev_free(p, F->stream);
   for (cudaEvent_t e : F->ev)
     if (e) cudaEventDestroy(e);
   delete F;
 }
 
 long long diaf_launch_count(void) { return g_launches.load(); }
+
+diaf_status diaf_set_device_memory_limit(int64_t bytes) {
+  if (bytes < 0) return fail(DIAF_EINVAL, "the limit must be >= 0 (0: no limit)");
+  std::lock_guard<std::mutex> lock(g_mem_mu);
+  g_mem_cap = static_cast<size_t>(bytes);
+  return DIAF_OK;
+}
+
+int64_t diaf_device_memory_in_use(void) {
+  std::lock_guard<std::mutex> lock(g_mem_mu);
+  return static_cast<int64_t>(g_mem_total);
+}
 
 diaf_status diaf_factor_fallbacks(const diaf_factors* F, int32_t* counts, int32_t nb) {
   if (!F || !counts || nb < kNumBuckets) return fail(DIAF_EINVAL, "need a handle and room for n_buckets counts");

@@ -2,17 +2,18 @@
 //
 // For callers that may not allocate device memory at the point where they
 // apply the preconditioner: code running under a fixed device-memory budget
-// reserved at start-up, a solver loop being recorded into a CUDA graph (plain
-// cudaMalloc cannot be captured), or a host framework whose own allocator
-// owns all device memory and forbids other allocations.  Such callers set
-// the factors up beforehand (diaf_factor, and one diaf_apply, which builds
-// the row-oriented copies of W and V), and from then on apply through this
-// entry point.
+// reserved at start-up, or a host framework whose own allocator owns all
+// device memory and forbids allocations by the libraries it calls.  Such
+// callers set the factors up beforehand (diaf_factor, and one diaf_apply,
+// which builds the row-oriented copies of W and V), and from then on apply
+// through this entry point.
 //
 // The scratch the triangular solve needs -- one ready flag per row, the
 // ticket counter, and the intermediate vector t = V^-1 x -- lives in one
 // file-scope __device__ array of fixed size, which every GPU that loads the
-// library keeps until the process exits.
+// library keeps until the process exits.  Every call clears the ready flags
+// of its rows and the ticket counter on the stream before the solve, so what
+// an earlier call left in the array never counts as ready.
 #include <mutex>
 #include <string>
 
@@ -33,11 +34,9 @@ constexpr size_t kScratchBytes = kCounterBytes + kFlagBytes + kVecBytes;
 static __device__ __align__(256) unsigned char g_apply_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
-struct DeviceScratch {
-  unsigned char* base = nullptr;  // device address of g_apply_scratch on this device
-  uint32_t gen = 0;               // last generation written into the ready flags
-};
-DeviceScratch g_dev[kMaxDevices];
+// Device address of g_apply_scratch per device, looked up on the first call
+// made with that device current.
+unsigned char* g_base[kMaxDevices] = {};
 std::mutex g_mu;
 
 diaf_status fail(diaf_status st, const std::string& why) {
@@ -65,32 +64,26 @@ extern "C" diaf_status diaf_apply_static(diaf_factors* F, const void* x, void* y
   if (dev < 0 || dev >= kMaxDevices) return fail(DIAF_ECUDA, "device index beyond the static table");
 
   unsigned char* base;
-  uint32_t gen;
   {
     std::lock_guard<std::mutex> lock(g_mu);
-    DeviceScratch& d = g_dev[dev];
-    if (!d.base) {
+    if (!g_base[dev]) {
       // once per device, with that device current: the device address of the array
       void* ptr = nullptr;
       e = cudaGetSymbolAddress(&ptr, g_apply_scratch);
       if (e != cudaSuccess) return fail(DIAF_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      d.base = static_cast<unsigned char*>(ptr);
-      d.gen = 0;
+      g_base[dev] = static_cast<unsigned char*>(ptr);
     }
-    if (d.gen == 0 || d.gen == 0xffffffffu) {
-      // flags must not hold the generation about to be used: clear them
-      e = cudaMemsetAsync(d.base + kCounterBytes, 0, kFlagBytes, s);
-      if (e != cudaSuccess) return fail(DIAF_ECUDA, cudaGetErrorString(e));
-      d.gen = 0;
-    }
-    gen = ++d.gen;
-    base = d.base;
+    base = g_base[dev];
   }
   int32_t* counter = reinterpret_cast<int32_t*>(base);
   uint32_t* ready = reinterpret_cast<uint32_t*>(base + kCounterBytes);
   void* t = base + kCounterBytes + kFlagBytes;
   const bool cplx = F->dtype == DIAF_C128;
-  e = csr_trsv_syncfree(F->Vr, cplx, F->v_upper, x, t, ready, counter, gen, F->status, s);
+  // the array keeps the previous call's flags: clear this call's rows (the
+  // solve clears the ticket counter itself), then wait on flag value 1
+  e = cudaMemsetAsync(ready, 0, sizeof(uint32_t) * (size_t)F->n, s);
+  if (e != cudaSuccess) return fail(DIAF_ECUDA, cudaGetErrorString(e));
+  e = csr_trsv_syncfree(F->Vr, cplx, F->v_upper, x, t, ready, counter, 1u, F->status, s);
   if (e != cudaSuccess) return fail(DIAF_ECUDA, cudaGetErrorString(e));
   e = csr_spmv(F->Wr, cplx, t, y, s);
   if (e != cudaSuccess) return fail(DIAF_ECUDA, cudaGetErrorString(e));

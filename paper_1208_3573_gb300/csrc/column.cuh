@@ -161,6 +161,11 @@ __device__ inline double select_rows_greedy(const int32_t* rs, const K* hk, int3
         if (hk[r] >= thr) best = dmin(best, r);
       }
     best = warp_min(best);
+    if (best == INT_MAX) {  // no key reaches the threshold (non-finite keys): the lowest remaining admissible row
+      for (int r = lane; r < m; r += DIAF_WARP)
+        if (!pick[r] && admissible_row(rule, rs[r], j, blk)) best = dmin(best, r);
+      best = warp_min(best);
+    }
     if (lane == 0 && best < m) pick[best] = 1;
     __syncwarp();
   }

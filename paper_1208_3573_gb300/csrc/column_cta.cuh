@@ -361,6 +361,11 @@ __device__ void solve_column_cta(const ColArgs& a, const CtaScratch& sc, int j, 
       for (int r = tid; r < m; r += kCtaThreads)
         if (!pick[r] && admissible_row(a.rule, rs[r], j, a.blk) && hk[r] >= thr) best = dmin(best, r);
       best = block_min(best, reinterpret_cast<int*>(red));
+      if (best == INT_MAX) {  // no key reaches the threshold (non-finite keys): the lowest remaining admissible row
+        for (int r = tid; r < m; r += kCtaThreads)
+          if (!pick[r] && admissible_row(a.rule, rs[r], j, a.blk)) best = dmin(best, r);
+        best = block_min(best, reinterpret_cast<int*>(red));
+      }
       if (tid == 0 && best < m) pick[best] = 1;
       __syncthreads();
     }

@@ -52,6 +52,11 @@ __device__ inline double cta_select_rows(const int32_t* rs, const double* hk, in
         if (hk[r] >= thr) best = dmin(best, r);
       }
     best = block_min(best, reinterpret_cast<int*>(red));
+    if (best == INT_MAX) {  // no key reaches the threshold (non-finite keys): the lowest remaining admissible row
+      for (int r = tid; r < m; r += kCtaThreads)
+        if (!pick[r] && admissible_row(rule, rs[r], j, blk)) best = dmin(best, r);
+      best = block_min(best, reinterpret_cast<int*>(red));
+    }
     if (tid == 0 && best < m) pick[best] = 1;
     __syncthreads();
   }

@@ -9,6 +9,13 @@
 // Sets the thread's diaf_last_error() text (api.cu).
 void diaf_set_last_error(const char* msg);
 
+// Stream-ordered device allocations of the setup and apply paths, counted
+// against the process-wide cap of diaf_set_device_memory_limit (api.cu).  A
+// request beyond the cap fails with cudaErrorMemoryAllocation without
+// reaching the allocator.
+cudaError_t diaf_dev_alloc(void** p, size_t bytes, cudaStream_t s);
+void diaf_dev_free(void* p, cudaStream_t s);
+
 struct diaf_factors {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -43,7 +50,7 @@ struct diaf_factors {
   template <class T>
   cudaError_t alloc(T** p, size_t count) {
     void* q = nullptr;
-    cudaError_t e = cudaMallocAsync(&q, sizeof(T) * (count > 0 ? count : 1), stream);
+    cudaError_t e = diaf_dev_alloc(&q, sizeof(T) * (count > 0 ? count : 1), stream);
     if (e != cudaSuccess) return e;
     owned.push_back(q);
     *p = static_cast<T*>(q);

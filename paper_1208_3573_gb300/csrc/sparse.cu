@@ -106,7 +106,12 @@ __device__ __forceinline__ Cx<double> ld_cg(const Cx<double>* p) {
   return {v.x, v.y};
 }
 
-constexpr long long kSpinLimit = 1ll << 22;  // polls of one flag before giving up (~seconds)
+// Polls of one flag before giving up (~seconds); a test build lowers it to
+// check the timeout path.
+#ifndef DIAF_SPIN_LIMIT
+#define DIAF_SPIN_LIMIT (1ll << 22)
+#endif
+constexpr long long kSpinLimit = DIAF_SPIN_LIMIT;
 
 template <class S>
 __global__ void trsv_syncfree_kernel(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
@@ -466,10 +471,12 @@ cudaError_t csr_triangle_check(const Csr& V, bool cplx, uint32_t* out, cudaStrea
 cudaError_t csr_trsv_syncfree(const Csr& V, bool cplx, bool upper, const void* x, void* t, uint32_t* ready,
                               int32_t* counter, uint32_t gen, uint32_t* status, cudaStream_t s) {
   if (V.n <= 0) return cudaSuccess;
-  cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
   int threads = 256;
   int blocks = ceil_div(V.n, threads / 32);
   if (blocks > sms * 8) blocks = sms * 8;

@@ -1,4 +1,4 @@
-// Sparsified powers (Sec. 4.1, Algorithm 3): the W pattern from the
+// Sparsified powers (Sec. 4.1, Algorithm 1): the W pattern from the
 // truncated Neumann series of A^-1 D with the diagonal initial subspace,
 // S = -D^-1 (A - D) (so that A = D (I - S)).  One warp per column j:
 //

@@ -14,7 +14,11 @@
 
 #include "common.cuh"
 
-constexpr int kMaxSweeps = 30;
+// Jacobi sweep limit (a test build lowers it to check the flag it sets).
+#ifndef DIAF_MAX_SWEEPS
+#define DIAF_MAX_SWEEPS 30
+#endif
+constexpr int kMaxSweeps = DIAF_MAX_SWEEPS;
 
 template <class T> __device__ __forceinline__ T eps_of();
 template <> __device__ __forceinline__ double eps_of<double>() { return DBL_EPSILON; }

@@ -136,6 +136,8 @@ def lib() -> ctypes.CDLL:
                                  ctypes.POINTER(SolveInfo_t)]
         L.diaf_factor_timings.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]
         L.diaf_launch_count.restype = ctypes.c_longlong
+        L.diaf_set_device_memory_limit.argtypes = [ctypes.c_int64]
+        L.diaf_device_memory_in_use.restype = ctypes.c_int64
         L.diaf_factor_fallbacks.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]
         L.diaf_propose_features.argtypes = [ctypes.POINTER(CSC_t), ctypes.POINTER(Pattern_t), vp, vp]
         L.diaf_mlp_forward.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
@@ -314,6 +316,17 @@ class Factors:
 def launch_count() -> int:
     """Kernels launched by libdiaf.so in this process so far."""
     return int(lib().diaf_launch_count())
+
+
+def set_device_memory_limit(nbytes: int) -> None:
+    """Caps the device bytes the setup and apply paths may hold at once
+    (0: no cap); a call that would exceed it raises DiafError (DIAF_ENOMEM)."""
+    _check(lib().diaf_set_device_memory_limit(int(nbytes)))
+
+
+def device_memory_in_use() -> int:
+    """Device bytes the setup and apply paths hold now."""
+    return int(lib().diaf_device_memory_in_use())
 
 
 def _args(A, PW, vrule, budget, Vfixed, tie_tol, stab=(0.0, 2.0), blocks=None):

@@ -41,11 +41,21 @@ def test_tuned_buckets_match_oracle(D, prec, tuning):
 
 @pytest.mark.parametrize("alg", ["S", "Q"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed32"])
-def test_plan_replay_matches_factor_and_tracks_new_values(D, alg, prec):
-    w = make_workload("convdiff48_A2")
+@pytest.mark.parametrize("name,tuned", [("convdiff48_A2", False), ("powerlaw6k", False), ("powerlaw6k", True)])
+def test_plan_replay_matches_factor_and_tracks_new_values(D, name, tuned, alg, prec):
+    """One graph over the size buckets (with the default edges the power-law
+    operator fills all three), with the default or the autotuner's launch
+    tuning, replayed on new values."""
+    w = make_workload(name)
     A, PW, bud = _dev(D, w)
-    ref = host_factors(D.factor(A, PW, w.vrule, bud, alg=alg, prec=prec, tie_tol=w.tie_tol))
-    P = D.Plan(A, PW, w.vrule, bud, alg=alg, prec=prec, tie_tol=w.tie_tol)
+    tuning = None
+    if tuned:
+        tuning, _ = D.autotune(A, PW, w.vrule, bud, alg=alg, prec=prec, tie_tol=w.tie_tol)
+    ref = host_factors(D.factor(A, PW, w.vrule, bud, alg=alg, prec=prec, tie_tol=w.tie_tol, tuning=tuning))
+    P = D.Plan(A, PW, w.vrule, bud, alg=alg, prec=prec, tie_tol=w.tie_tol, tuning=tuning)
+    if name == "powerlaw6k" and not tuned:
+        info = P.execute().info
+        assert all(info.bucket_cols[b] > 0 for b in range(info.n_buckets))
     g = host_factors(P.execute())
     for key in ("Vcp", "Vri", "flags"):
         assert np.array_equal(g[key], ref[key])

@@ -1,4 +1,4 @@
-"""Sparsified powers (Sec. 4.1, Algorithm 3) on the GPU against the oracle.
+"""Sparsified powers (Sec. 4.1, Algorithm 1) on the GPU against the oracle.
 
 Real operators: the sums are formed in the same order with separately
 rounded operations on both sides, so the patterns must agree exactly.

@@ -1,14 +1,19 @@
 """diaf_apply_static -- the preconditioner apply for callers that cannot
-allocate device memory when they apply it (fixed memory budgets, solver loops
-recorded into CUDA graphs, host frameworks that own all device memory).  Its
-scratch is a fixed array inside the library instead of buffers of the factor
-handle.  Checked through the C ABI against diaf_apply on the same factors,
-on two calls in a row with different inputs (the second call reuses the
-array the first one left behind)."""
+allocate device memory when they apply it: code held to a device-memory
+budget fixed at start-up, or a host framework whose allocator owns all device
+memory and forbids allocations by the libraries it calls.  Its scratch is a
+fixed array inside the library instead of buffers of the factor handle.
+
+Checked through the C ABI against diaf_apply on the same factors and against
+the oracle's W V^-1 (a sparse LU of the oracle's V), on two calls in a row
+with different inputs (the second call reuses the array the first one left
+behind, so its cleared flags are what makes it right), for upper and lower
+triangular V, real and complex."""
 import numpy as np
 import pytest
 
-from workloads import make_workload
+import oracle as O
+from workloads import lower_budget, make_workload
 
 pytestmark = pytest.mark.gpu
 
@@ -24,29 +29,33 @@ def D():
     return diaf
 
 
-@pytest.mark.parametrize("name", ["convdiff32", "helmholtz40"])
-def test_apply_static_matches_apply(D, name):
+@pytest.mark.parametrize("name,lower", [("convdiff32", False), ("helmholtz40", False), ("convdiff32", True)])
+def test_apply_static_matches_apply(D, name, lower):
     w = make_workload(name)
-    F = D.factor(D.DeviceCSC.from_host(w.A), D.DeviceCSC.from_host(w.PW), w.vrule,
-                 torch.from_numpy(w.budget).cuda(), alg="S")
+    rule, budget = (O.RULE_LOWER, lower_budget(w.A)) if lower else (w.vrule, w.budget)
+    F = D.factor(D.DeviceCSC.from_host(w.A), D.DeviceCSC.from_host(w.PW), rule,
+                 torch.from_numpy(budget).cuda(), alg="S", tie_tol=w.tie_tol)
+    o = O.factor(w.A, w.PW, rule, budget, alg="S", tie_tol=w.tie_tol)
+    M = O.Preconditioner(o.W_csc(), o.V_csc())
     rng = np.random.default_rng(7)
     dt = torch.complex128 if w.A.is_complex else torch.float64
 
     def vec():
-        x = rng.standard_normal(w.n) + (1j * rng.standard_normal(w.n) if w.A.is_complex else 0)
-        return torch.from_numpy(x).to("cuda", dt)
+        return rng.standard_normal(w.n) + (1j * rng.standard_normal(w.n) if w.A.is_complex else 0)
 
     y = torch.empty(w.n, dtype=dt, device="cuda")
     with pytest.raises(D.DiafError):  # no row-oriented copies yet: it will not build (allocate) them
-        F.apply_static(vec(), y)
+        F.apply_static(torch.from_numpy(vec()).to("cuda", dt), y)
     for _ in range(2):
-        x = vec()
+        xh = vec()
+        x = torch.from_numpy(xh).to("cuda", dt)
         ref = F.apply(x)
         out = torch.full_like(ref, float("nan"))
         F.apply_static(x, out)
-        F.sync()
-        r = ref.cpu().numpy(); o = out.cpu().numpy()
-        assert np.linalg.norm(o - r) <= 1e-10 * np.linalg.norm(r)
+        F.sync()  # a wait that ran out would be reported here (DIAF_ETIMEOUT)
+        r = ref.cpu().numpy(); got = out.cpu().numpy(); yo = M(xh)
+        assert np.linalg.norm(got - r) <= 1e-10 * np.linalg.norm(r)
+        assert np.linalg.norm(got - yo) <= 1e-10 * np.linalg.norm(yo)
 
 
 def test_apply_static_rejects_oversize(D):

@@ -161,11 +161,16 @@ diaf_status diaf_factor(const diaf_csc* A, const diaf_pattern* PW, const diaf_vs
  *            column, 64-row tile); 1..64, default 64.  Larger tiles run in
  *            bucket 2 (one 256-thread CTA per column).
  *   warps_per_block[b]: CTA size of the warp kernels of buckets 0 and 1
- *            (1..8; 0 = the most warps resident per SM). */
+ *            (1..8; 0 = the most warps resident per SM).
+ *   small_tiles: bucket 0 of real DIAF-S in mixed precision: 0 (default) or
+ *            1 = one thread per column (a warp runs 32 columns; columns it
+ *            cannot finish in FP32 go on to the warp kernel), 2 = one warp
+ *            per column. */
 typedef struct {
   int32_t m_edge0;
   int32_t m_edge1;
   int32_t warps_per_block[2];
+  int32_t small_tiles;
 } diaf_tuning;
 
 typedef struct {

@@ -195,7 +195,8 @@ struct NumericPlan {
   ColArgs ca{};
   int32_t* bucket_list = nullptr;
   int32_t* bucket_count = nullptr;
-  int32_t* work = nullptr;      // 2 * kNumBuckets work counters
+  int32_t* work = nullptr;      // kWorkCounters: per bucket the main, FP64 hand-back and deferred
+                                // launches' work counters, then the defer count
   int32_t* fb_list = nullptr;   // mixed: columns handed to the FP64 kernels
   int32_t* fb_count = nullptr;
   int h_bc[kNumBuckets] = {0};
@@ -205,7 +206,12 @@ struct NumericPlan {
   bool mixed = false, cplx = false;
   int alg = DIAF_ALG_S, dtype = DIAF_F64, n = 0;
   int wpb[2] = {0, 0};
+  // bucket 0 of real mixed DIAF-S: four lanes per column, deferred columns to the warp kernel
+  bool thread_cols = false;
+  ThreadArgs ta{};
+  ThreadShape tsh{};
 };
+constexpr int kWorkCounters = 3 * kNumBuckets + 1;
 
 diaf_status check_args(const diaf_csc* A, const diaf_pattern* PW, const diaf_vspec* V, int32_t alg, int32_t prec,
                        const diaf_tuning* tuning) {
@@ -230,6 +236,7 @@ diaf_status check_args(const diaf_csc* A, const diaf_pattern* PW, const diaf_vsp
     for (int b = 0; b < 2; ++b)
       if (tuning->warps_per_block[b] < 0 || tuning->warps_per_block[b] > 8)
         return fail(DIAF_EINVAL, "tuning: warps_per_block must be in 0..8");
+    if (tuning->small_tiles < 0 || tuning->small_tiles > 2) return fail(DIAF_EINVAL, "tuning: small_tiles must be 0, 1 or 2");
   }
   return check_device();
 }
@@ -266,7 +273,7 @@ diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_
   DIAF_CU(pool.get(&stats, 4));
   DIAF_CU(pool.get(&np.bucket_count, kNumBuckets));
   DIAF_CU(pool.get(&big_count, 1));
-  DIAF_CU(pool.get(&np.work, 2 * kNumBuckets));
+  DIAF_CU(pool.get(&np.work, kWorkCounters));
   DIAF_CU(cudaMemsetAsync(status, 0, sizeof(uint32_t), s));
   DIAF_CU(cudaMemsetAsync(stats, 0, sizeof(int32_t) * 4, s));
   DIAF_CU(cudaMemsetAsync(np.bucket_count, 0, sizeof(int32_t) * kNumBuckets, s));
@@ -397,6 +404,23 @@ diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_
       if (t > tiles) tiles = t;
     }
     if (tiles > 0) DIAF_CU(pool.get((char**)&ca.tile_scratch, tiles));
+    // bucket 0 of real DIAF-S: four lanes per column (unless the tuning asks for the warp kernel)
+    const int small = tuning ? tuning->small_tiles : 0;
+    if (!np.cplx && alg == DIAF_ALG_S && np.h_bc[0] > 0 && small != 2 && V->rule != DIAF_RULE_FIXED) {
+      const int M = h_stats[1] < pa.edge_m0 ? h_stats[1] : pa.edge_m0;
+      const int K = h_stats[0] < kThreadKMax ? h_stats[0] : kThreadKMax;
+      if (M >= 1 && K >= 1) {
+        DIAF_CU(thread_columns_shape(M, K, np.h_bc[0], &np.tsh));
+        np.ta.M = M;
+        np.ta.K = K;
+        np.ta.arena = thread_arena_floats(M, K);
+        np.ta.nquads = np.tsh.nquads;
+        DIAF_CU(pool.get(&np.ta.slab, (size_t)np.tsh.nquads * ((M * K + 3) / 4 * 4)));
+        DIAF_CU(pool.get(&np.ta.defer_list, np.h_bc[0]));
+        np.ta.defer_count = np.work + 3 * kNumBuckets;
+        np.thread_cols = np.tsh.grid > 0;
+      }
+    }
   }
   const int bl = kNumBuckets - 1;
   if (np.h_bc[bl] > 0) {
@@ -419,7 +443,7 @@ diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_
 // stream work: no allocation, no synchronisation (graph-capturable).
 diaf_status enqueue_numeric(diaf_factors* F, NumericPlan& np, cudaStream_t s, bool events) {
   const int n = np.n;
-  DIAF_CU(cudaMemsetAsync(np.work, 0, sizeof(int32_t) * 2 * kNumBuckets, s));
+  DIAF_CU(cudaMemsetAsync(np.work, 0, sizeof(int32_t) * kWorkCounters, s));
   if (np.mixed) DIAF_CU(cudaMemsetAsync(np.fb_count, 0, sizeof(int32_t) * kNumBuckets, s));
   ColArgs ca = np.ca;
   auto fp64_launch = [&](int b, const ColArgs& c, int hint) {
@@ -460,8 +484,17 @@ diaf_status enqueue_numeric(diaf_factors* F, NumericPlan& np, cudaStream_t s, bo
     } else if (np.mixed) {
       ca.fb_list = np.fb_list + (size_t)b * n;
       ca.fb_count = np.fb_count + b;
-      e = np.cplx ? launch_columns_mixed_c64(b, np.alg, ca, np.h_bc[b], np.wpb[b], s)
-                  : launch_columns_mixed_f32(b, np.alg, ca, np.h_bc[b], np.wpb[b], s);
+      e = cudaSuccess;
+      if (b == 0 && np.thread_cols) {
+        // four lanes per column; the columns it defers run in the warp kernel
+        e = launch_columns_thread_f32(ca, np.ta, np.tsh, s);
+        ca.list = np.ta.defer_list;
+        ca.list_count = np.ta.defer_count;
+        ca.work_counter = np.work + 2 * kNumBuckets + b;
+      }
+      if (e == cudaSuccess)
+        e = np.cplx ? launch_columns_mixed_c64(b, np.alg, ca, np.h_bc[b], np.wpb[b], s)
+                    : launch_columns_mixed_f32(b, np.alg, ca, np.h_bc[b], np.wpb[b], s);
       if (e == cudaSuccess) {
         // the FP64 kernel finishes the columns the mixed kernel handed back
         ColArgs cf = ca;
@@ -603,16 +636,20 @@ diaf_status diaf_autotune(const diaf_csc* A, const diaf_pattern* PW, const diaf_
   float cur_ms = 0;
   diaf_status st = time_of(cur, &cur_ms);
   if (st != DIAF_OK) return st;
-  // coordinate descent over the bucket edges and the CTA sizes of the warp kernels
-  const int edge0[] = {32, 24, 16}, edge1[] = {64, 48, 32}, wpbs[] = {0, 2, 4, 8};
-  for (int knob = 0; knob < 4; ++knob) {
-    const int* vals = knob == 0 ? edge0 : (knob == 1 ? edge1 : wpbs);
-    const int nv = knob < 2 ? 3 : 4;
+  // coordinate descent over the bucket edges, the CTA sizes of the warp
+  // kernels and the small-tile kernel (thread or warp per column)
+  const int edge0[] = {32, 24, 16}, edge1[] = {64, 48, 32}, wpbs[] = {0, 2, 4, 8}, smalls[] = {1, 2};
+  for (int knob = 0; knob < 5; ++knob) {
+    const int* vals = knob == 0 ? edge0 : (knob == 1 ? edge1 : (knob == 4 ? smalls : wpbs));
+    const int nv = knob < 2 ? 3 : (knob == 4 ? 2 : 4);
     for (int i = 0; i < nv; ++i) {
       diaf_tuning t = cur;
-      int* field = knob == 0 ? &t.m_edge0 : (knob == 1 ? &t.m_edge1 : &t.warps_per_block[knob - 2]);
-      const int* curf = knob == 0 ? &cur.m_edge0 : (knob == 1 ? &cur.m_edge1 : &cur.warps_per_block[knob - 2]);
-      const int eff = (*curf == 0 && knob < 2) ? vals[0] : *curf;
+      int* field = knob == 0 ? &t.m_edge0
+                             : (knob == 1 ? &t.m_edge1 : (knob == 4 ? &t.small_tiles : &t.warps_per_block[knob - 2]));
+      const int* curf = knob == 0 ? &cur.m_edge0
+                                  : (knob == 1 ? &cur.m_edge1
+                                               : (knob == 4 ? &cur.small_tiles : &cur.warps_per_block[knob - 2]));
+      const int eff = (*curf == 0 && (knob < 2 || knob == 4)) ? vals[0] : *curf;
       if (vals[i] == eff) continue;
       *field = vals[i];
       float ms = 0;

@@ -4,6 +4,7 @@
 
 #include "column_cta.cuh"
 #include "column_mixed.cuh"
+#include "column_thread.cuh"
 
 // Launches the numeric pass for size bucket `bucket` over the listed columns
 // (count_hint: an upper bound of the device-side count, for grid sizing).
@@ -25,6 +26,17 @@ cudaError_t launch_columns_cta_mixed(int dtype, int alg, const ColArgs& a, const
                                      cudaStream_t s);
 // its persistent grid (resident CTAs, capped by count); 0 when not available
 int cta_columns_grid_mixed(int dtype, int alg, int ldm, int count);
+
+// Four lanes per column (size bucket 0, real DIAF-S, mixed precision): the
+// launch shape for tiles of at most M rows and K columns (grid, block, shared
+// memory, quads of the grid; grid 0 when count_hint is 0), and the launch.
+// Columns it leaves go to ta.defer_list for the warp kernel.
+struct ThreadShape {
+  int grid = 0, block = 0, nquads = 0;
+  size_t smem = 0;
+};
+cudaError_t thread_columns_shape(int M, int K, int count_hint, ThreadShape* out);
+cudaError_t launch_columns_thread_f32(const ColArgs& a, const ThreadArgs& ta, const ThreadShape& sh, cudaStream_t s);
 
 // Bytes of the mixed warp kernels' global tile scratch (ColArgs::tile_scratch)
 // for this bucket's launch: one FP64 tile per warp of the persistent grid

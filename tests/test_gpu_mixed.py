@@ -116,3 +116,21 @@ def test_mixed_parity_full_size_lognormal64(D, alg):
     g = host_factors(F)
     o = O.factor(w.A, w.PW, w.vrule, w.budget, alg=alg, tie_tol=w.tie_tol)
     assert_parity(compare(g, o, w.A, w.PW, alg, rtol_res=RTOL_RES, vec_tol=VEC_TOL, mixed=True, floor_rel=1e-10))
+
+
+@pytest.mark.parametrize("small", [1, 2])
+@pytest.mark.parametrize("name", ["convdiff32", "convdiff48_A2", "powerlaw6k", "lognormal16", "convdiff256_A2"])
+def test_small_tile_kernels_at_parity(D, name, small):
+    """Size bucket 0 of real DIAF-S in mixed precision runs one thread per
+    column (small_tiles 1, the default; columns it cannot finish in FP32 go on
+    to the warp kernel) or one warp per column (2): both at parity with the
+    oracle on every column."""
+    w = make_workload(name)
+    dA = D.DeviceCSC.from_host(w.A)
+    dP = D.DeviceCSC.from_host(w.PW)
+    dB = torch.from_numpy(w.budget).cuda()
+    F = D.factor(dA, dP, w.vrule, dB, alg="S", prec="mixed32", tie_tol=w.tie_tol, tuning={"small_tiles": small})
+    torch.cuda.synchronize()
+    g = host_factors(F)
+    o = O.factor(w.A, w.PW, w.vrule, w.budget, alg="S", tie_tol=w.tie_tol)
+    assert_parity(compare(g, o, w.A, w.PW, "S", rtol_res=RTOL_RES, vec_tol=VEC_TOL, mixed=True, floor_rel=1e-10))

@@ -48,10 +48,18 @@ constexpr int kQuadWarps = 1;       // warps per block
 __host__ __device__ constexpr int thread_arena_floats(int M, int K) {
   return ((M * K > 2 * K * K ? M * K : 2 * K * K) + M + K + 3) / 4 * 4;
 }
+// FP64 shared-memory scratch per column: the refined vector x (K) and
+// z = A-hat x (M), each rounded up to whole rows of 4.
+__host__ __device__ constexpr int thread_arena_doubles(int M, int K) { return (K + 3) / 4 * 4 + (M + 3) / 4 * 4; }
+// Shared-memory bytes of one warp (eight columns).
+__host__ __device__ constexpr size_t thread_warp_smem(int M, int K) {
+  return sizeof(float) * (size_t)thread_arena_floats(M, K) * 8 + sizeof(double) * (size_t)thread_arena_doubles(M, K) * 8;
+}
 
 // Element e of this quad's interleaved shared-memory array (base already
 // offset by the quad's slot); element e + 4u lies at qptr(base, e)[32 u].
 __device__ __forceinline__ float* qptr(float* base, int e) { return base + ((e >> 2) * 32 + (e & 3) * 8); }
+__device__ __forceinline__ double* qptr(double* base, int e) { return base + ((e >> 2) * 32 + (e & 3) * 8); }
 #define QS(base, e) (*qptr((base), (e)))
 
 __device__ __forceinline__ float qsum(float v, unsigned qm) {
@@ -64,6 +72,12 @@ __device__ __forceinline__ double qsum(double v, unsigned qm) {
   v += __shfl_xor_sync(qm, v, 2);
   return v;
 }
+
+// Round-robin Jacobi schedule of the warp kernels for qq = 2, 4, ..., 16
+// columns (k rounded up to even): kPairTab[qq/2 - 1][round][pair] = (a << 4) | b,
+// with b >= k marking a bye; filled once on the host.
+constexpr int kPairRounds = kThreadKMax - 1, kPairSlots = kThreadKMax / 2;
+static __constant__ uint8_t kPairTab[kThreadKMax / 2][kPairRounds][kPairSlots];
 
 constexpr int kQR = kThreadMMax / 4;  // most rows a lane owns in a column of the tile
 constexpr int kQK = kThreadKMax / 4;  // most rows a lane owns in a column of a k x k matrix
@@ -114,8 +128,8 @@ __device__ __forceinline__ void quad_qr(float* W, int m, int k, int sub, unsigne
 }
 
 template <int KMAX>
-__device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j, float* S, double* G, int sub,
-                                  unsigned qm) {
+__device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j, float* S, double* D, double* G,
+                                  int sub, unsigned qm) {
   static_assert(KMAX <= kThreadKMax, "tile capacity");
   const int k = a.Wcp[j + 1] - a.Wcp[j];
   const int m = a.m[j];
@@ -141,6 +155,7 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
   auto gptr = [&](int e) { return G + (size_t)(e >> 2) * gstride + (e & 3); };
   auto T = [&](int e) -> double& { return *gptr(e); };
   const int nown = (m - sub + 3) >> 2;  // own tile rows: sub, sub + 4, ...
+  DIAF_PHASE_START();
 
   // ---- gather T = A(R_j, J_j): own rows zeroed, then each lane places every
   // fourth entry of the J_j columns by a binary search in R_j
@@ -179,10 +194,12 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
       for (int t = 0; t < kQR; ++t)
         if (t < nown) s2 = fmaf(wq[32 * t], wq[32 * t], s2);
     }
-    cn[q] = sqrtf(qsum(s2, qm));
+    cn[q] = 0.0f;
+    if (q < k) cn[q] = sqrtf(qsum(s2, qm));  // k is the same in the whole quad
   }
 
   // ---- FP32 QR of T and the conditioning estimate
+  DIAF_PHASE(0);
   quad_qr(W, m, k, sub, qm);
   float kap = 0.0f;
   float rinv[KMAX];
@@ -198,6 +215,7 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
   if (!(kap <= kMixedKappaMax)) { defer(); return; }
 
   // ---- leverage keys h_r = ||Q(r,:)||^2, Q = T R^-1 by rows (own rows; R's
+  DIAF_PHASE(2);
   // column c read through four pointers, element c m + 4u + v at P[v][32 u])
   for (int t = 0; t < nown; ++t) {
     const int r = sub + 4 * t;
@@ -226,6 +244,7 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
   __syncwarp(qm);
 
   // ---- I_j: the diagonal plus the l - 1 admissible rows of largest key
+  DIAF_PHASE(3);
   // (ties within tau to the lower row), as select_rows_greedy; every lane of
   // the quad takes the same decisions (picks as bits)
   uint32_t adm = 0;
@@ -279,6 +298,7 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
     if ((inI >> r) & 1u) a.Vri[v0 + pos_of(r)] = Rj[r];
 
   // ---- FP32 QR of A-hat (the I_j rows zeroed), its conditioning
+  DIAF_PHASE(4);
   float ch[KMAX];
 #pragma unroll
   for (int q = 0; q < KMAX; ++q) {
@@ -294,7 +314,8 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
           s2 = fmaf(f, f, s2);
         }
     }
-    ch[q] = sqrtf(qsum(s2, qm));
+    ch[q] = 0.0f;
+    if (q < k) ch[q] = sqrtf(qsum(s2, qm));
   }
   __syncwarp(qm);
   quad_qr(W, m, k, sub, qm);
@@ -308,6 +329,7 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
   if (!(kh <= kMixedKappaMax)) { defer(); return; }
 
   // ---- R-hat to ld k at W[0, k^2) column by column (a column's new place
+  DIAF_PHASE(6);
   // lies below every later column's old one), V = I at W[k^2, 2k^2).  Lane
   // `sub` owns rows sub + 4u (u < nk) of every k x k column.
   const int nk = (k - sub + 3) >> 2;
@@ -331,10 +353,14 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
       if (u < nk) dst[32 * u] = sub + 4 * u == c ? 1.0f : 0.0f;
   }
 
-  // ---- cyclic one-sided Jacobi on R-hat (the warp kernels' rotation and
-  // stopping rules: skip below tol = k eps_32, stop after a sweep without a
-  // rotation of |gamma|^2 >= tol alpha beta; norms carried through rotations;
-  // every lane of the quad writes the same norms)
+  // ---- one-sided Jacobi on R-hat in the warp kernels' round-robin order
+  DIAF_PHASE(5);
+  // (in round rnd, position p >= 1 holds column 1 + ((p - 1 + rnd) mod L) and
+  // positions p, qq - 1 - p pair up), with their rotation and stopping rules:
+  // skip below tol = k eps_32, stop after a sweep without a rotation of
+  // |gamma|^2 >= tol alpha beta; norms carried through rotations.  The pairs
+  // of a round are disjoint: two are rotated together (independent chains).
+  // Every lane of the quad writes the same norms.
   uint32_t flags = 0;
   {
     float nf2 = 0.0f;
@@ -348,6 +374,16 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
     const float tol = (float)k * FLT_EPSILON;
     const float tol2 = tol * tol;
     const float tiny = tol2 * nf2;
+    const int qq = (k + 1) & ~1;
+    const int npairs = qq / 2;
+    const int L = qq - 1;
+    const uint8_t* tab = &kPairTab[npairs - 1][0][0];
+    auto pair_of = [&](int pr, int rnd) -> int2 {
+      if (pr >= npairs) return make_int2(-1, -1);
+      const int ab = tab[rnd * kPairSlots + pr];
+      const int x = ab >> 4, y = ab & 15;
+      return y < k ? make_int2(x, y) : make_int2(-1, -1);  // a bye for the padding column
+    };
     int sweep = 1;
     for (; sweep <= kMaxSweeps; ++sweep) {
       for (int c = 0; c < k; ++c) {
@@ -359,41 +395,57 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
         QS(W, NR + c) = qsum(s2, qm);
       }
       bool large = false;
-      for (int pa = 0; pa + 1 < k; ++pa) {
-        float* ga = qptr(W, pa * k + sub);
-        float* va = qptr(W, VO + pa * k + sub);
-        for (int pb = pa + 1; pb < k; ++pb) {
-          float* gb = qptr(W, pb * k + sub);
-          float xa[kQK], xb[kQK];
-          float g = 0.0f;
+      if (k >= 2) {
+        for (int rnd = 0; rnd < L; ++rnd) {
+          for (int pr = 0; pr < npairs; pr += 2) {
+            const int2 p0 = pair_of(pr, rnd), p1 = pair_of(pr + 1, rnd);
+            const int pa[2] = {p0.x, p1.x}, pb[2] = {p0.y, p1.y};
+            float xa[2][kQK], xb[2][kQK], g[2];
+            float *ga[2], *gb[2];
 #pragma unroll
-          for (int u = 0; u < kQK; ++u) {
-            xa[u] = u < nk ? ga[32 * u] : 0.0f;
-            xb[u] = u < nk ? gb[32 * u] : 0.0f;
-            g = fmaf(xa[u], xb[u], g);
-          }
-          g = qsum(g, qm);
-          const float al = QS(W, NR + pa), be = QS(W, NR + pb);
-          const float g2 = g * g;
-          if (!(al > tiny && be > tiny && g2 > 0.0f && g2 > tol2 * (al * be))) continue;
-          if (g2 >= tol * (al * be)) large = true;
-          const float ag = fabsf(g);
-          const float d = be - al;
-          const float t = __fdividef(copysignf(2.0f * ag, d), fabsf(d) + sqrtf(d * d + 4.0f * g2));
-          const float cs = rsqrtf(1.0f + t * t), sn = cs * t;
-          const float ssn = g < 0.0f ? -sn : sn, scs = g < 0.0f ? -cs : cs;  // y = sign(g) b folded in
-          float* vb = qptr(W, VO + pb * k + sub);
+            for (int h = 0; h < 2; ++h) {
+              const bool act = pb[h] >= 0;
+              ga[h] = qptr(W, (act ? pa[h] : 0) * k + sub);
+              gb[h] = qptr(W, (act ? pb[h] : 0) * k + sub);
+              g[h] = 0.0f;
 #pragma unroll
-          for (int u = 0; u < kQK; ++u)
-            if (u < nk) {
-              ga[32 * u] = fmaf(-ssn, xb[u], cs * xa[u]);
-              gb[32 * u] = fmaf(scs, xb[u], sn * xa[u]);
-              const float xv = va[32 * u], yv = vb[32 * u];
-              va[32 * u] = fmaf(-ssn, yv, cs * xv);
-              vb[32 * u] = fmaf(scs, yv, sn * xv);
+              for (int u = 0; u < kQK; ++u) {
+                xa[h][u] = (act && u < nk) ? ga[h][32 * u] : 0.0f;
+                xb[h][u] = (act && u < nk) ? gb[h][32 * u] : 0.0f;
+                g[h] = fmaf(xa[h][u], xb[h][u], g[h]);
+              }
             }
-          QS(W, NR + pa) = al - t * ag;
-          QS(W, NR + pb) = be + t * ag;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) g[h] += __shfl_xor_sync(qm, g[h], 1);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) g[h] += __shfl_xor_sync(qm, g[h], 2);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              if (pb[h] < 0) continue;
+              const float al = QS(W, NR + pa[h]), be = QS(W, NR + pb[h]);
+              const float g2 = g[h] * g[h];
+              if (!(al > tiny && be > tiny && g2 > 0.0f && g2 > tol2 * (al * be))) continue;
+              if (g2 >= tol * (al * be)) large = true;
+              const float ag = fabsf(g[h]);
+              const float d = be - al;
+              const float t = __fdividef(copysignf(2.0f * ag, d), fabsf(d) + sqrtf(d * d + 4.0f * g2));
+              const float cs = rsqrtf(1.0f + t * t), sn = cs * t;
+              const float ssn = g[h] < 0.0f ? -sn : sn, scs = g[h] < 0.0f ? -cs : cs;  // y = sign(g) b
+              float* va = qptr(W, VO + pa[h] * k + sub);
+              float* vb = qptr(W, VO + pb[h] * k + sub);
+#pragma unroll
+              for (int u = 0; u < kQK; ++u)
+                if (u < nk) {
+                  ga[h][32 * u] = fmaf(-ssn, xb[h][u], cs * xa[h][u]);
+                  gb[h][32 * u] = fmaf(scs, xb[h][u], sn * xa[h][u]);
+                  const float xv = va[32 * u], yv = vb[32 * u];
+                  va[32 * u] = fmaf(-ssn, yv, cs * xv);
+                  vb[32 * u] = fmaf(scs, yv, sn * xv);
+                }
+              QS(W, NR + pa[h]) = al - t * ag;
+              QS(W, NR + pb[h]) = be + t * ag;
+            }
+          }
         }
       }
       if (!large) break;
@@ -403,6 +455,7 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
   __syncwarp(qm);
 
   // ---- singular values (column norms of R-hat V), the smallest and its gap
+  DIAF_PHASE(7);
   for (int c = 0; c < k; ++c) {
     const float* pc = qptr(W, c * k + sub);
     float s2 = 0.0f;
@@ -429,45 +482,55 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
   if (k > 1 && gap <= 1e-5 * smax * smax) { defer(); return; }
   const int iters = (k > 1 && gap < 1e-2 * smax * smax) ? 2 : 1;
 
-  // ---- FP64 correction in the FP32 singular basis V: x (k entries) in every
-  // lane; d = x^T H x / x^T x, r = H x - d x (H = A-hat^T A-hat from the FP64
-  // tile), x <- x - sum_{i != imin} V_i (V_i^T r) / (sigma_i^2 - d).  The lane
-  // owning row q of V keeps the sum for x_q; x is exchanged after each step.
-  double x[KMAX];
+  // ---- FP64 correction in the FP32 singular basis V: d = x^T H x / x^T x,
+  // r = H x - d x (H = A-hat^T A-hat from the FP64 tile),
+  // x <- x - sum_{i != imin} V_i (V_i^T r) / (sigma_i^2 - d).  x (k) and
+  // z = A-hat x (m) in the quad's FP64 shared scratch: lane `sub` computes z
+  // on its tile rows and (A-hat^T z)_q, r_q and the update of x_q on its rows
+  // q of V.
+  double* X = D;       // x, element q
+  double* Z = D + 32 * ((K + 3) / 4);  // z, element r (after x's rows of 4)
   {
-    const float* vmin = qptr(W, VO + imin * k);
+    const float* vmin = qptr(W, VO + imin * k + sub);
+    double* xs = qptr(X, sub);
 #pragma unroll
-    for (int q = 0; q < KMAX; ++q) x[q] = q < k ? (double)vmin[32 * (q >> 2) + 8 * (q & 3)] : 0.0;
+    for (int u = 0; u < kQK; ++u)
+      if (u < nk) xs[32 * u] = (double)vmin[32 * u];
   }
+  __syncwarp(qm);
   for (int it = 0; it < iters; ++it) {
-    double g[KMAX];
-#pragma unroll
-    for (int q = 0; q < KMAX; ++q) g[q] = 0.0;
+    double zz = 0.0;
     for (int t = 0; t < nown; ++t) {
       const int r = sub + 4 * t;
-      if ((inI >> r) & 1u) continue;
       double z = 0.0;
-#pragma unroll
-      for (int q = 0; q < KMAX; ++q)
-        if (q < k) z = fma(T(r + q * m), x[q], z);
-#pragma unroll
-      for (int q = 0; q < KMAX; ++q)
-        if (q < k) g[q] = fma(T(r + q * m), z, g[q]);
+      if (!((inI >> r) & 1u))
+        for (int q = 0; q < k; ++q) z = fma(T(r + q * m), QS(X, q), z);
+      QS(Z, r) = z;
+      zz = fma(z, z, zz);
     }
-    double xg = 0.0, xx = 0.0;
+    double xx = 0.0;
+    {
+      const double* xs = qptr(X, sub);
 #pragma unroll
-    for (int q = 0; q < KMAX; ++q)
-      if (q < k) {
-        g[q] = qsum(g[q], qm);
-        xg = fma(x[q], g[q], xg);
-        xx = fma(x[q], x[q], xx);
+      for (int u = 0; u < kQK; ++u)
+        if (u < nk) xx = fma(xs[32 * u], xs[32 * u], xx);
+    }
+    const double d = qsum(zz, qm) / qsum(xx, qm);
+    __syncwarp(qm);  // z complete
+    float rfo[kQK];  // r on the lane's rows of V, in FP32
+    double xo[kQK];
+#pragma unroll
+    for (int u = 0; u < kQK; ++u) {
+      const int q = sub + 4 * u;
+      rfo[u] = 0.0f;
+      xo[u] = 0.0;
+      if (u < nk) {
+        double gq = 0.0;
+        for (int r = 0; r < m; ++r) gq = fma(T(r + q * m), QS(Z, r), gq);  // rows in I_j have z_r = 0
+        xo[u] = QS(X, q);
+        rfo[u] = (float)(gq - d * xo[u]);
       }
-    const double d = xg / xx;
-    float rf[KMAX];  // r = H x - d x, in FP32
-#pragma unroll
-    for (int q = 0; q < KMAX; ++q) rf[q] = q < k ? (float)(g[q] - d * x[q]) : 0.0f;
-    // dx = V c with c_i = -(V_i^T r) / (sigma_i^2 - d): the lane's rows of
-    // every V_i give partial inner products; x's entries are the lane's rows
+    }
     float dxo[kQK];
 #pragma unroll
     for (int u = 0; u < kQK; ++u) dxo[u] = 0.0f;
@@ -478,11 +541,7 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
 #pragma unroll
       for (int u = 0; u < kQK; ++u) {
         vo[u] = u < nk ? vi[32 * u] : 0.0f;
-        float rq = 0.0f;
-#pragma unroll
-        for (int q = 0; q < KMAX; ++q)
-          if (q == sub + 4 * u) rq = rf[q];
-        vr = fmaf(vo[u], rq, vr);
+        vr = fmaf(vo[u], rfo[u], vr);
       }
       vr = qsum(vr, qm);
       if (i == imin) continue;
@@ -491,28 +550,31 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
 #pragma unroll
       for (int u = 0; u < kQK; ++u) dxo[u] = fmaf(vo[u], ci, dxo[u]);
     }
-    // every lane adds the owners' updates to its copy of x
-#pragma unroll
-    for (int q = 0; q < KMAX; ++q) {
-      float mine = 0.0f;
+    __syncwarp(qm);  // every lane has read x and z
+    {
+      double* xs = qptr(X, sub);
 #pragma unroll
       for (int u = 0; u < kQK; ++u)
-        if (q == 4 * u + sub) mine = dxo[u];
-      const float dq = __shfl_sync(qm, mine, (q & 3) | ((threadIdx.x & 31) & ~3));
-      if (q < k) x[q] += (double)dq;
+        if (u < nk) xs[32 * u] = xo[u] + (double)dxo[u];
     }
+    __syncwarp(qm);
   }
   {
     double xn2 = 0.0;
+    double* xs = qptr(X, sub);
 #pragma unroll
-    for (int q = 0; q < KMAX; ++q)
-      if (q < k) xn2 = fma(x[q], x[q], xn2);
-    const double inv = 1.0 / sqrt(xn2);
+    for (int u = 0; u < kQK; ++u)
+      if (u < nk) xn2 = fma(xs[32 * u], xs[32 * u], xn2);
+    const double inv = 1.0 / sqrt(qsum(xn2, qm));
+    __syncwarp(qm);
 #pragma unroll
-    for (int q = 0; q < KMAX; ++q) x[q] *= inv;
+    for (int u = 0; u < kQK; ++u)
+      if (u < nk) xs[32 * u] *= inv;
+    __syncwarp(qm);
   }
 
   // ---- v = T(I_j,:) w (into V's values by the row owners), phase v_jj >= 0,
+  DIAF_PHASE(8);
   // FP64 residual
   double* Vout = reinterpret_cast<double*>(a.Vv) + v0;
   double vn2 = 0.0, vjj = 0.0, r2 = 0.0;
@@ -522,9 +584,7 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
   for (int t = 0; t < nown; ++t) {
     const int r = sub + 4 * t;
     double sv = 0.0;
-#pragma unroll
-    for (int q = 0; q < KMAX; ++q)
-      if (q < k) sv = fma(T(r + q * m), x[q], sv);
+    for (int q = 0; q < k; ++q) sv = fma(T(r + q * m), QS(X, q), sv);
     if ((inI >> r) & 1u) {
       Vout[pos_of(r)] = sv;
       vn2 = fma(sv, sv, vn2);
@@ -542,9 +602,10 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
   } else {
     flags |= DIAF_FLAG_VJJ_ZERO;
     double amx = 0.0, wsel = 1.0;
-#pragma unroll
-    for (int q = 0; q < KMAX; ++q)
-      if (q < k && fabs(x[q]) > amx) { amx = fabs(x[q]); wsel = x[q]; }
+    for (int q = 0; q < k; ++q) {
+      const double xq = QS(X, q);
+      if (fabs(xq) > amx) { amx = fabs(xq); wsel = xq; }
+    }
     ph = wsel < 0.0 ? -1.0 : 1.0;
   }
   bool finite = true;
@@ -562,19 +623,18 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
   if (resj <= 1e-14 * smax) flags |= DIAF_FLAG_RANK_DEFICIENT;
   finite &= isfinite(resj);
   double* Wout = reinterpret_cast<double*>(a.Wv) + a.Wcp[j];
-#pragma unroll
-  for (int q = 0; q < KMAX; ++q)
-    if (q < k) {
-      const double wq = ph * x[q];
-      finite &= isfinite(wq);
-      if ((q & 3) == sub) Wout[q] = wq;
-    }
+  for (int q = sub; q < k; q += 4) {
+    const double wq = ph * QS(X, q);
+    finite &= isfinite(wq);
+    Wout[q] = wq;
+  }
   const unsigned fin = __ballot_sync(qm, finite) & qm;
   if (fin != qm) flags |= DIAF_FLAG_NONFINITE;
   if (sub == 0) {
     a.res[j] = resj;
     a.flags[j] = flags | a.extra_flags;
   }
+  DIAF_PHASE(9);
 }
 
 // The persistent loop: each warp takes eight columns of the list at a time,
@@ -587,7 +647,10 @@ __global__ void __launch_bounds__(32 * kQuadWarps, 12) column_thread_kernel(ColA
   const int sub = lane & 3, slot = lane >> 2;
   const unsigned qm = 0xFu << (lane & ~3);
   const int gq = (blockIdx.x * kQuadWarps + warp) * kQuadCols + slot;  // quad index in the grid
-  float* S = tsmem + (size_t)warp * (ta.arena / 4) * 32 + slot;
+  const int M = ta.M, K = ta.K;
+  unsigned char* wbase = reinterpret_cast<unsigned char*>(tsmem) + (size_t)warp * thread_warp_smem(M, K);
+  float* S = reinterpret_cast<float*>(wbase) + slot;
+  double* D = reinterpret_cast<double*>(wbase + sizeof(float) * (size_t)thread_arena_floats(M, K) * 8) + slot;
   double* G = ta.slab + (size_t)4 * gq;  // element e of the quad's tile at G[(e/4) 4 nquads + (e mod 4)]
   const int count = *a.list_count;
   while (true) {
@@ -596,7 +659,7 @@ __global__ void __launch_bounds__(32 * kQuadWarps, 12) column_thread_kernel(ColA
     base = __shfl_sync(DIAF_FULL, base, 0);
     if (base >= count) break;
     const int idx = base + slot;
-    if (idx < count) solve_column_quad<KMAX>(a, ta, a.list[idx], S, G, sub, qm);
+    if (idx < count) solve_column_quad<KMAX>(a, ta, a.list[idx], S, D, G, sub, qm);
     __syncwarp();
   }
 }

@@ -33,8 +33,26 @@ sys.path.insert(0, ROOT)
 
 from workloads import make_workload  # noqa: E402
 
-METRIC = "W,V setup columns/s (DIAF-S, 256x256 convection-diffusion, W = pattern(A^2)); vs plain FP64 GPU form"
 UNIT = "columns/s"
+# the workloads in words, for the metric string
+WORKLOAD_TEXT = {
+    "convdiff32": "32x32 convection-diffusion, W = pattern(A)",
+    "convdiff256_A2": "256x256 convection-diffusion, W = pattern(A^2)",
+    "powerlaw200k": "power-law random n = 200,000, W = pattern(A)",
+    "helmholtz512": "512x512 complex shifted Helmholtz, W = pattern(A)",
+    "lognormal64": "64^3 lognormal diffusion-convection, W = pattern(A^2)",
+}
+
+
+def metric_name(workload: str, alg: str) -> str:
+    return (f"W,V setup columns/s (DIAF-{alg}, {WORKLOAD_TEXT.get(workload, workload)}); "
+            "vs plain FP64 GPU form")
+
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the dominant numeric kernel, from one ncu capture of the current kernel on
+# the workload (workload name, alg, prec); other configurations report None.
+TRAFFIC = {}
 
 
 def _peaks():
@@ -52,20 +70,37 @@ FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_NOMINAL_TFLOPS = 1.25
 
 
-def algorithmic_flops(m: np.ndarray, k: np.ndarray, l: np.ndarray, alg: str, cplx: bool) -> float:
-    """Real flops the method needs per column (the SVD counted as the
-    textbook 4pq^2 + 8q^3 for singular values and right vectors of a p x q
-    matrix): QR of the m x k tile 2k^2(m - k/3), leverage m k^2, then
-    DIAF-S: QR of the tile without I_j rows + SVD of its k x k R;
-    DIAF-Q: SVD of the l x k Q_I + triangular solve k^2; plus v and the
-    residual 2lk + 2mk.  Complex arithmetic counts 4x."""
+JACOBI_SWEEPS = 5  # mean sweeps of the FP32 Jacobi on the headline workload (phase-timer build)
+
+
+def algorithmic_flops(m: np.ndarray, k: np.ndarray, l: np.ndarray, alg: str, cplx: bool,
+                      sweeps: float = JACOBI_SWEEPS) -> tuple[float, float]:
+    """(all flops, FP64 flops) the method does per factorisation, summed over
+    the columns: QR of the m x k tile 2k^2(m - k/3), leverage keys m k^2,
+    then DIAF-S: QR of the tile without the I_j rows, one-sided Jacobi on its
+    k x k R -- `sweeps` sweeps of k(k-1)/2 rotations, each a 2k-flop inner
+    product and two 6k-flop column-pair updates (R and V) --, the FP64
+    correction (H x = A-hat^T A-hat x: 4 m k) and v, residual (2 m k);
+    DIAF-Q: Jacobi on the l x k Q_I, the FP64 correction and solves
+    (4 m k + 2 k^2), v, residual.  Complex arithmetic counts 4x."""
     m = m.astype(np.float64); k = k.astype(np.float64); l = l.astype(np.float64)
-    f = 2 * k**2 * (m - k / 3) + m * k**2 + 2 * l * k + 2 * m * k
+    f32 = 2 * k**2 * (m - k / 3) + m * k**2
     if alg == "S":
-        f += 2 * k**2 * (np.maximum(m - l, k) - k / 3) + 12 * k**3
+        f32 += 2 * k**2 * (np.maximum(m - l, k) - k / 3) + sweeps * k * (k - 1) / 2 * 14 * k
+        f64 = 4 * m * k + 2 * m * k
     else:
-        f += 4 * l * k**2 + 8 * k**3 + k**2
-    return float(f.sum() * (4 if cplx else 1))
+        f32 += sweeps * k * (k - 1) / 2 * (8 * l + 6 * k)
+        f64 = 4 * m * k + 2 * k**2 + 2 * m * k
+    c = 4 if cplx else 1
+    return float((f32 + f64).sum() * c), float(f64.sum() * c)
+
+
+def gathered_bytes(w) -> float:
+    """Bytes the gather of every tile reads: each J_j column's entries of A
+    (value and row index) once per column j that uses it."""
+    nnz = np.diff(w.A.colptr).astype(np.float64)
+    per = 16.0 + 4.0 if w.A.is_complex else 8.0 + 4.0
+    return float(nnz[w.PW.rowidx].sum() * per)
 
 
 def tile_sizes(w):
@@ -167,7 +202,7 @@ def run_reference(args):
         times.append(time.perf_counter() - t0)
     ms = 1e3 * float(np.mean(times))
     val = w.n / (ms / 1e3)
-    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": metric_name(args.workload, args.alg), "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "n": w.n, "alg": args.alg, "columns_per_step": w.n},
@@ -254,19 +289,23 @@ def learned_report(dev, keep=12, train_N=40, train_seeds=(11, 12), eval_N=64, ep
 
 def kv_sweep(w, A, PW, alg, prec, dev, budgets=(1, 2, 3, 4, 6, 8, 13)):
     """The k_V sweep of Sec. 5 on this workload: at most k_V entries per
-    column of V (upper rule): ||A W - V||_F, setup time, BiCGSTAB to 1e-8."""
+    column of V (upper rule): ||A W - V||_F, setup time, BiCGSTAB to 1e-8 --
+    for the configured algorithm and for the stabilised DIAF-Q of Sec. 3.2
+    (trigger |v_jj| < 1e-2, v_jj imposed as 2: the paper's Table 6 setting),
+    with the number of stabilised columns."""
     import torch
     from paper_1208_3573_gb300 import diaf
     S = diaf.Solver(A)
     b = torch.from_numpy(w.b).to(dev)
-    out = []
-    for kv in budgets:
-        bud = torch.full((w.n,), kv, dtype=torch.int32, device=dev)
-        F = diaf.factor(A, PW, w.vrule, bud, alg=alg, prec=prec, tie_tol=w.tie_tol)
-        ms = F.timings()["total_ms"]
+
+    def run(bud, a, stab):
+        F = diaf.factor(A, PW, w.vrule, bud, alg=a, prec=prec, tie_tol=w.tie_tol, stab_tol=stab, stab_r=2.0)
         res = F.res.cpu().numpy()
-        row = {"k_V": kv, "nnz_V": int(F.V.nnz), "nrm_AW_minus_V": float(np.sqrt(np.sum(res ** 2))),
-               "setup_ms": ms}
+        fl = F.flags.cpu().numpy()
+        row = {"nnz_V": int(F.V.nnz), "nrm_AW_minus_V": float(np.sqrt(np.sum(res ** 2))),
+               "setup_ms": F.timings()["total_ms"], "vjj_zero_columns": int(np.count_nonzero(fl & 4))}
+        if stab > 0:
+            row["stabilised_columns"] = int(np.count_nonzero(fl & 128))
         try:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -277,7 +316,12 @@ def kv_sweep(w, A, PW, alg, prec, dev, budgets=(1, 2, 3, 4, 6, 8, 13)):
         except diaf.DiafError as e:
             row["solve"] = str(e)[:80]
         F.close()
-        out.append(row)
+        return row
+
+    out = []
+    for kv in budgets:
+        bud = torch.full((w.n,), kv, dtype=torch.int32, device=dev)
+        out.append({"k_V": kv, f"DIAF-{alg}": run(bud, alg, 0.0), "DIAF-Q stabilised": run(bud, "Q", 1e-2)})
     return out
 
 
@@ -459,20 +503,29 @@ def main():
     # ---- roofline of the dominant kernel (the numeric column kernel)
     peaks, peak_src = _peaks()
     m, k = tile_sizes(w)
-    flops = algorithmic_flops(m, k, lcount, args.alg, cplx)
+    flops, flops64 = algorithmic_flops(m, k, lcount, args.alg, cplx)
     kern = float(np.mean([sum(x) for x in kern_ms]))
     achieved = flops / (kern / 1e3)
+    small_quad = args.prec == "mixed32" and not cplx and args.alg == "S"
     if args.prec == "fp64":
         peak, src, kname = FP64_NOMINAL_TFLOPS * 1e12, "FP64 nominal 1.25 TFLOP/s", "column_warp_kernel"
     else:
-        peak, src, kname = FP32_TFLOPS * 1e12, "FP32 152 SMs x 128 lanes x 2 flop x 2.07 GHz", "column_mixed_kernel"
+        peak, src = FP32_TFLOPS * 1e12, "FP32 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
+        kname = "column_thread_kernel (four lanes per column)" if small_quad else "column_mixed_kernel"
     # DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu
-    # capture of the current kernel on this workload (dram__bytes_read.sum
-    # 28,361,472 + dram__bytes_write.sum 1,534,720); None where none was taken
-    traffic = 29896192 if (w.name == "convdiff2d_256x256_Wp2" and args.prec == "mixed32" and args.alg == "S") else None
+    # capture of the current kernel on this workload; None where none was taken
+    traffic = TRAFFIC.get((w.name, args.alg, args.prec))
+    gbytes = gathered_bytes(w)
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic, "kernel": f"{kname} (numeric pass, all buckets)",
-            "kernel_ms": kern, "algorithmic_flops": flops, "peak_source": src}
+            "kernel_ms": kern, "algorithmic_flops": flops, "jacobi_sweeps_assumed": JACOBI_SWEEPS,
+            "peak_source": src,
+            "fp64": {"flops": flops64, "achieved": flops64 / (kern / 1e3) / 1e12, "peak": FP64_NOMINAL_TFLOPS,
+                     "unit": "TFLOP/s", "frac": flops64 / (kern / 1e3) / (FP64_NOMINAL_TFLOPS * 1e12)},
+            "gather": {"bytes": gbytes, "achieved": gbytes / (kern / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+                       "unit": "GB/s", "frac": gbytes / (kern / 1e3) / 1e9 / peaks["hbm_gbs"],
+                       "note": "gathered entries (value + row index) per launch over the numeric pass time, "
+                               "against the measured HBM copy bandwidth"}}
 
     extras = {}
     if not args.no_extras and rank == 0 and do_apply:
@@ -498,6 +551,19 @@ def main():
         extras["gmres50"] = {"its": ig.iterations, "converged": bool(ig.converged), "relres": ig.relres,
                              "solve_ms": 1e3 * (time.perf_counter() - t0)}
         F.close()
+        # the stabilised DIAF-Q of Sec. 3.2 (trigger |v_jj| < 1e-2, r = 2, the
+        # paper's experiments) on the same V pattern rule
+        Fs = diaf.factor(A, PW, w.vrule, bud, alg="Q", prec=args.prec, tie_tol=w.tie_tol, stab_tol=1e-2, stab_r=2.0)
+        stab = int(np.count_nonzero(Fs.flags.cpu().numpy() & 128))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xs, isb = S.bicgstab(b, Fs, tol=1e-8, maxit=1000)
+        torch.cuda.synchronize()
+        extras["bicgstab_stabilised_q"] = {"its": isb.iterations, "converged": bool(isb.converged),
+                                           "relres": isb.relres, "solve_ms": 1e3 * (time.perf_counter() - t0),
+                                           "stabilised_columns": stab, "setup_ms": Fs.timings()["total_ms"]}
+        Fs.close()
+    if not args.no_extras and rank == 0:
         # the plain FP64 form on the same workload: columns/s and residual agreement
         if args.prec != "fp64":
             tt = []
@@ -564,7 +630,7 @@ def main():
             extras["learned_proposal"] = {"error": f"{type(e).__name__}: {e}"[:300]}
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        line = {"metric": metric_name(args.workload, args.alg), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None,
                 "dtype": ("c64+c128" if cplx else "f32+f64") if args.prec == "mixed32" else ("c128" if cplx else "f64"),

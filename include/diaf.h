@@ -163,14 +163,19 @@ diaf_status diaf_factor(const diaf_csc* A, const diaf_pattern* PW, const diaf_vs
  *   warps_per_block[b]: CTA size of the warp kernels of buckets 0 and 1
  *            (1..8; 0 = the most warps resident per SM).
  *   small_tiles: bucket 0 of real DIAF-S in mixed precision: 0 (default) or
- *            1 = one thread per column (a warp runs 32 columns; columns it
+ *            1 = four lanes per column (a warp runs eight columns; columns it
  *            cannot finish in FP32 go on to the warp kernel), 2 = one warp
- *            per column. */
+ *            per column.
+ *   large_tiles: bucket 2 of real DIAF-S in mixed precision: 0 (default) or
+ *            1 = the tensor-core Gram path (G = T^T T on the tensor cores,
+ *            Cholesky factors, for column-scaled kappa <= 30; other tiles
+ *            keep the Householder QRs), 2 = Householder QRs only. */
 typedef struct {
   int32_t m_edge0;
   int32_t m_edge1;
   int32_t warps_per_block[2];
   int32_t small_tiles;
+  int32_t large_tiles;
 } diaf_tuning;
 
 typedef struct {

@@ -237,6 +237,7 @@ diaf_status check_args(const diaf_csc* A, const diaf_pattern* PW, const diaf_vsp
       if (tuning->warps_per_block[b] < 0 || tuning->warps_per_block[b] > 8)
         return fail(DIAF_EINVAL, "tuning: warps_per_block must be in 0..8");
     if (tuning->small_tiles < 0 || tuning->small_tiles > 2) return fail(DIAF_EINVAL, "tuning: small_tiles must be 0, 1 or 2");
+    if (tuning->large_tiles < 0 || tuning->large_tiles > 2) return fail(DIAF_EINVAL, "tuning: large_tiles must be 0, 1 or 2");
   }
   return check_device();
 }
@@ -428,6 +429,7 @@ diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_
     const int mk = h_stats[1] > h_stats[0] ? h_stats[1] : h_stats[0];
     np.cs.ldm = (mk + 31) / 32 * 32;
     np.cs.kcap = h_stats[0] > 0 ? h_stats[0] : 1;
+    np.cs.gram = (tuning && tuning->large_tiles == 2) ? 0 : 1;  // the tensor-core Gram path unless asked off
     np.cta_grid = cta_columns_grid(A->dtype, alg, np.cs.ldm, np.h_bc[bl]);
     if (np.cta_grid <= 0) return fail(DIAF_EUNSUPPORTED, "large-tile kernel does not fit this tile size");
     // the mixed kernel needs less shared memory: its own occupancy-sized grid
@@ -638,18 +640,23 @@ diaf_status diaf_autotune(const diaf_csc* A, const diaf_pattern* PW, const diaf_
   if (st != DIAF_OK) return st;
   // coordinate descent over the bucket edges, the CTA sizes of the warp
   // kernels and the small-tile kernel (thread or warp per column)
-  const int edge0[] = {32, 24, 16}, edge1[] = {64, 48, 32}, wpbs[] = {0, 2, 4, 8}, smalls[] = {1, 2};
-  for (int knob = 0; knob < 5; ++knob) {
-    const int* vals = knob == 0 ? edge0 : (knob == 1 ? edge1 : (knob == 4 ? smalls : wpbs));
-    const int nv = knob < 2 ? 3 : (knob == 4 ? 2 : 4);
+  const int edge0[] = {32, 24, 16}, edge1[] = {64, 48, 32}, wpbs[] = {0, 2, 4, 8}, kernels[] = {1, 2};
+  for (int knob = 0; knob < 6; ++knob) {
+    const int* vals = knob == 0 ? edge0 : (knob == 1 ? edge1 : (knob >= 4 ? kernels : wpbs));
+    const int nv = knob < 2 ? 3 : (knob >= 4 ? 2 : 4);
     for (int i = 0; i < nv; ++i) {
       diaf_tuning t = cur;
-      int* field = knob == 0 ? &t.m_edge0
-                             : (knob == 1 ? &t.m_edge1 : (knob == 4 ? &t.small_tiles : &t.warps_per_block[knob - 2]));
-      const int* curf = knob == 0 ? &cur.m_edge0
-                                  : (knob == 1 ? &cur.m_edge1
-                                               : (knob == 4 ? &cur.small_tiles : &cur.warps_per_block[knob - 2]));
-      const int eff = (*curf == 0 && (knob < 2 || knob == 4)) ? vals[0] : *curf;
+      int* field = knob == 0   ? &t.m_edge0
+                   : knob == 1 ? &t.m_edge1
+                   : knob == 4 ? &t.small_tiles
+                   : knob == 5 ? &t.large_tiles
+                               : &t.warps_per_block[knob - 2];
+      const int* curf = knob == 0   ? &cur.m_edge0
+                        : knob == 1 ? &cur.m_edge1
+                        : knob == 4 ? &cur.small_tiles
+                        : knob == 5 ? &cur.large_tiles
+                                    : &cur.warps_per_block[knob - 2];
+      const int eff = (*curf == 0 && (knob < 2 || knob >= 4)) ? vals[0] : *curf;
       if (vals[i] == eff) continue;
       *field = vals[i];
       float ms = 0;

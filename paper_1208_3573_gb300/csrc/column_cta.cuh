@@ -15,6 +15,7 @@ struct CtaScratch {
   void* slab;     // per CTA: Ts then Tw, each ldm x kcap scalars
   int ldm;        // leading dimension (>= every m_j, k_j of the bucket)
   int kcap;       // columns per tile (>= every k_j of the bucket)
+  int gram;       // mixed real DIAF-S: 1 = tensor-core Gram + Cholesky where the tile is well conditioned
 };
 
 // ----------------------------------------------------------------- block reductions
@@ -50,6 +51,58 @@ __device__ __forceinline__ T block_min(T v, T* red) {
   T s = red[0];
   for (int w = 1; w < kCtaWarps; ++w) s = red[w] < s ? red[w] : s;
   return s;
+}
+
+// Greedy V rule of Sec. 3.1 (as select_rows_greedy: s picks among the
+// admissible rows, at each pick the lowest row whose key is within tau of
+// the largest remaining key) run by warp 0 alone -- rows r = lane + 32 i as
+// bits of a register, warp reductions instead of CTA barriers -- while the
+// other warps wait.  Writes pick[r] for r < m (m <= 1024) and returns, to
+// every thread, the smallest distance of a non-leading candidate key from a
+// threshold it was compared with.  red: one double of shared scratch.
+template <class K>
+__device__ double cta_select_rows_w0(const int32_t* rs, const K* hk, int32_t* pick, int m, int rule, int j, int s,
+                                     double tau, const int32_t* blk, double* red) {
+  if ((threadIdx.x >> 5) == 0) {
+    const int lane = threadIdx.x & 31;
+    uint32_t adm = 0, picked = 0;
+    for (int i = 0; i < 32 && lane + 32 * i < m; ++i)
+      if (admissible_row(rule, rs[lane + 32 * i], j, blk)) adm |= 1u << i;
+    K margin = std::numeric_limits<K>::max();
+    for (int t = 0; t < s; ++t) {
+      const uint32_t cand = adm & ~picked;
+      K hm = -std::numeric_limits<K>::max();
+      for (uint32_t b = cand; b; b &= b - 1) hm = dmax(hm, hk[lane + 32 * (__ffs(b) - 1)]);
+      hm = warp_max(hm);
+      int rmax = INT_MAX;
+      for (uint32_t b = cand; b && rmax == INT_MAX; b &= b - 1) {
+        const int r = lane + 32 * (__ffs(b) - 1);
+        if (hk[r] == hm) rmax = r;
+      }
+      rmax = warp_min(rmax);
+      const K thr = hm - K(tau);
+      int best = INT_MAX;
+      for (uint32_t b = cand; b; b &= b - 1) {
+        const int r = lane + 32 * (__ffs(b) - 1);
+        const K h = hk[r];
+        if (r != rmax) margin = dmin(margin, (K)fabs(h - thr));
+        if (h >= thr && best == INT_MAX) best = r;
+      }
+      best = warp_min(best);
+      if (best == INT_MAX) {  // no key reaches the threshold (non-finite keys): the lowest remaining admissible row
+        const int lo = cand ? lane + 32 * (__ffs(cand) - 1) : INT_MAX;
+        best = warp_min(lo);
+      }
+      if (best < m && (best & 31) == lane) picked |= 1u << (best >> 5);
+    }
+    margin = warp_min(margin);
+    for (int i = 0; i < 32 && lane + 32 * i < m; ++i) pick[lane + 32 * i] = (picked >> i) & 1u;
+    if (lane == 0) red[0] = (double)margin;
+  }
+  __syncthreads();
+  const double mg = red[0];
+  __syncthreads();  // red is free again
+  return mg;
 }
 
 // Householder QR of the m x k tile T (leading dimension ld, global memory):
@@ -350,25 +403,8 @@ __device__ void solve_column_cta(const ColArgs& a, const CtaScratch& sc, int j, 
     __syncthreads();
   }
   if (a.rule != DIAF_RULE_FIXED) {
-    const int s = l - 1;
-    for (int t = 0; t < s; ++t) {
-      double hm = -DBL_MAX;
-      for (int r = tid; r < m; r += kCtaThreads)
-        if (!pick[r] && admissible_row(a.rule, rs[r], j, a.blk)) hm = dmax(hm, hk[r]);
-      hm = block_max(hm, red);
-      const double thr = hm - a.tie_tol;
-      int best = INT_MAX;
-      for (int r = tid; r < m; r += kCtaThreads)
-        if (!pick[r] && admissible_row(a.rule, rs[r], j, a.blk) && hk[r] >= thr) best = dmin(best, r);
-      best = block_min(best, reinterpret_cast<int*>(red));
-      if (best == INT_MAX) {  // no key reaches the threshold (non-finite keys): the lowest remaining admissible row
-        for (int r = tid; r < m; r += kCtaThreads)
-          if (!pick[r] && admissible_row(a.rule, rs[r], j, a.blk)) best = dmin(best, r);
-        best = block_min(best, reinterpret_cast<int*>(red));
-      }
-      if (tid == 0 && best < m) pick[best] = 1;
-      __syncthreads();
-    }
+    double* redD = reinterpret_cast<double*>(red);
+    cta_select_rows_w0(rs, hk, pick, m, a.rule, j, l - 1, a.tie_tol, a.blk, redD);
   }
   // I_j
   if (tid == 0) {

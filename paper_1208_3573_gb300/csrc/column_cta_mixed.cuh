@@ -27,6 +27,169 @@ struct CtaMixedSmem {
   }
 };
 
+// ---------------------------------------------------------------- tensor-core Gram path
+// For a well-conditioned tile the two Householder QRs (of T for the keys, of
+// A-hat for the SVD) are replaced by the Gram matrix on the tensor cores and
+// Cholesky factorisations: G = T^T T by mma.m16n8k8 in TF32 with each FP32
+// value split into a TF32 head and tail (head*head + head*tail + tail*head,
+// FP32 accumulation: about FP32 accuracy); R_s = chol(D G D), D = diag(1 /
+// ||T(:,c)||), so R = R_s D^-1 is T's R up to the signs of its rows; the keys
+// h_r = ||T(r,:) R^-1||^2 = ||T(r,:) D R_s^-1||^2 by a second tensor-core
+// product; the R of A-hat from G minus the I_j rows' outer products.  The
+// error of a Gram-based factor grows with kappa^2 instead of kappa, so the
+// path is taken only for column-scaled kappa <= kGramKappaMax (and the key
+// decisions use the kappa^2 bound); other tiles keep the Householder QRs.
+constexpr float kGramKappaMax = 30.0f;
+
+__device__ __forceinline__ uint32_t tf32_head(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void mma_tf32_16x8x8(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// d += a b with a, b split into TF32 head and tail (the tail*tail term dropped)
+__device__ __forceinline__ void mma_3xtf32(float (&d)[4], const float (&av)[4], const float (&bv)[2]) {
+  uint32_t ah[4], at[4], bh[2], bt[2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    ah[i] = tf32_head(av[i]);
+    at[i] = tf32_head(av[i] - __uint_as_float(ah[i]));
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    bh[i] = tf32_head(bv[i]);
+    bt[i] = tf32_head(bv[i] - __uint_as_float(bh[i]));
+  }
+  mma_tf32_16x8x8(d, at, bh);
+  mma_tf32_16x8x8(d, ah, bt);
+  mma_tf32_16x8x8(d, ah, bh);
+}
+
+// G (k x k, leading dimension ldg) = T^T T for the m x k FP32 tile T (leading
+// dimension ld).  Output tiles of 16 x 8 over the CTA's warps; fragment
+// layout of mma.m16n8k8: lane = 4 g + t holds A(g, t), A(g + 8, t),
+// A(g, t + 4), A(g + 8, t + 4), B(t, g), B(t + 4, g) and D(g, 2t),
+// D(g, 2t + 1), D(g + 8, 2t), D(g + 8, 2t + 1).
+__device__ void cta_gram_tc(const float* T, int ld, int m, int k, float* G, int ldg) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int mt = (k + 15) / 16, nt = (k + 7) / 8;
+  for (int tile = warp; tile < mt * nt; tile += kCtaWarps) {
+    const int i0 = 16 * (tile / nt), j0 = 8 * (tile % nt);
+    float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    const int ca0 = i0 + g, ca1 = i0 + g + 8, cb = j0 + g;
+    const float* pa0 = T + (size_t)(ca0 < k ? ca0 : 0) * ld;
+    const float* pa1 = T + (size_t)(ca1 < k ? ca1 : 0) * ld;
+    const float* pb = T + (size_t)(cb < k ? cb : 0) * ld;
+    for (int r0 = 0; r0 < m; r0 += 8) {
+      const int r = r0 + t, r4 = r0 + t + 4;
+      const bool in = r < m, in4 = r4 < m;
+      const float av[4] = {(in && ca0 < k) ? pa0[r] : 0.0f, (in && ca1 < k) ? pa1[r] : 0.0f,
+                           (in4 && ca0 < k) ? pa0[r4] : 0.0f, (in4 && ca1 < k) ? pa1[r4] : 0.0f};
+      const float bv[2] = {(in && cb < k) ? pb[r] : 0.0f, (in4 && cb < k) ? pb[r4] : 0.0f};
+      mma_3xtf32(d, av, bv);
+    }
+    const int c0 = j0 + 2 * t;
+    if (ca0 < k && c0 < k) G[ca0 + c0 * ldg] = d[0];
+    if (ca0 < k && c0 + 1 < k) G[ca0 + (c0 + 1) * ldg] = d[1];
+    if (ca1 < k && c0 < k) G[ca1 + c0 * ldg] = d[2];
+    if (ca1 < k && c0 + 1 < k) G[ca1 + (c0 + 1) * ldg] = d[3];
+  }
+  __syncthreads();
+}
+
+// In place: the upper triangle of the k x k symmetric positive definite G
+// (leading dimension ldg, scaled by D = diag(sc) on both sides first) becomes
+// R_s with D G D = R_s^T R_s (right-looking, one column per step); the strict
+// lower triangle is zeroed.  Returns false (uniformly) at a pivot <= 0.
+__device__ bool cta_cholesky_scaled(float* G, int ldg, int k, const float* sc, float* redF) {
+  const int tid = threadIdx.x;
+  for (int i = tid; i < k * k; i += kCtaThreads) {
+    const int p = i % k, q = i / k;
+    G[p + q * ldg] = p <= q ? G[p + q * ldg] * sc[p] * sc[q] : 0.0f;
+  }
+  __syncthreads();
+  for (int c = 0; c < k; ++c) {
+    const float d = G[c + c * ldg];
+    if (!(d > 0.0f)) return false;  // uniform: every thread read the same pivot
+    const float rcc = sqrtf(d), rinv = 1.0f / rcc;
+    __syncthreads();  // every thread has read the pivot
+    for (int q = c + tid; q < k; q += kCtaThreads) G[c + q * ldg] = q == c ? rcc : G[c + q * ldg] * rinv;
+    __syncthreads();
+    const int w = k - c - 1;  // trailing block (c+1..k-1)^2, upper triangle
+    for (int i = tid; i < w * w; i += kCtaThreads) {
+      const int p = c + 1 + i % w, q = c + 1 + i / w;
+      if (p <= q) G[p + q * ldg] -= G[c + p * ldg] * G[c + q * ldg];
+    }
+    __syncthreads();
+  }
+  (void)redF;
+  return true;
+}
+
+// hk[r] = ||T(r,:) B||^2 for r < m, B (k x k, leading dimension ldb) in shared
+// memory: tensor-core product of the tile with B (TF32 head/tail split),
+// rows of 16 per warp task, squares summed from the accumulators.
+__device__ void cta_row_norms_tc(const float* T, int ld, int m, int k, const float* B, int ldb, double* hk) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int mt = (m + 15) / 16, nt = (k + 7) / 8, kt = (k + 7) / 8;
+  for (int task = warp; task < mt; task += kCtaWarps) {
+    const int r0 = 16 * task;
+    const int ra = r0 + g, rb = r0 + g + 8;
+    float h0 = 0.0f, h1 = 0.0f;
+    for (int jn = 0; jn < nt; ++jn) {
+      const int cb = 8 * jn + g;
+      float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      for (int kk = 0; kk < kt; ++kk) {
+        const int q = 8 * kk + t, q4 = 8 * kk + t + 4;
+        const float av[4] = {(ra < m && q < k) ? T[ra + (size_t)q * ld] : 0.0f,
+                             (rb < m && q < k) ? T[rb + (size_t)q * ld] : 0.0f,
+                             (ra < m && q4 < k) ? T[ra + (size_t)q4 * ld] : 0.0f,
+                             (rb < m && q4 < k) ? T[rb + (size_t)q4 * ld] : 0.0f};
+        const float bv[2] = {(q < k && cb < k) ? B[q + cb * ldb] : 0.0f, (q4 < k && cb < k) ? B[q4 + cb * ldb] : 0.0f};
+        mma_3xtf32(d, av, bv);
+      }
+      h0 += d[0] * d[0] + d[1] * d[1];
+      h1 += d[2] * d[2] + d[3] * d[3];
+    }
+    h0 += __shfl_xor_sync(DIAF_FULL, h0, 1);
+    h0 += __shfl_xor_sync(DIAF_FULL, h0, 2);
+    h1 += __shfl_xor_sync(DIAF_FULL, h1, 1);
+    h1 += __shfl_xor_sync(DIAF_FULL, h1, 2);
+    if (t == 0) {
+      if (ra < m) hk[ra] = (double)h0;
+      if (rb < m) hk[rb] = (double)h1;
+    }
+  }
+  __syncthreads();
+}
+
+// X (k x k, leading dimension ldx) = D R_s^-1 for the upper triangular R_s
+// (leading dimension ldr): one column of the inverse per thread, back
+// substitution, rows scaled by D = diag(sc).
+__device__ void cta_upper_inverse_scaled(const float* Rsm, int ldr, int k, const float* sc, float* X, int ldx) {
+  for (int jc = threadIdx.x; jc < k; jc += kCtaThreads) {
+    for (int i = k - 1; i >= 0; --i) {
+      float acc = i == jc ? 1.0f : 0.0f;
+      if (i < jc)
+        for (int p = i + 1; p <= jc; ++p) acc -= Rsm[i + p * ldr] * X[p + jc * ldx];
+      X[i + jc * ldx] = i <= jc ? acc / Rsm[i + i * ldr] : 0.0f;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < k * k; i += kCtaThreads) {
+    const int p = i % k, q = i / k;
+    X[p + q * ldx] *= sc[p];
+  }
+  __syncthreads();
+}
+
 // Greedy V rule of Sec. 3.1 on the keys hk (as select_rows_greedy, at CTA
 // level): s picks among the admissible rows, ties within tau to the lower row.
 // Returns the smallest distance of a non-leading candidate key from a
@@ -82,7 +245,7 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int mcap = sc.ldm;
   float* Rs = reinterpret_cast<float*>(smem);  // R of T, then R-hat (KP x KMAX)
-  float* Vj = Rs + KP * kCtaKmax;               // Jacobi V
+  float* Vj = Rs + KP * kCtaKmax;               // Jacobi V (Gram path: first D R_s^-1)
   float* rinv = Vj + KP * kCtaKmax;             // reciprocal diagonal (FP32)
   float* rf = rinv + kCtaKmax;                  // correction: r in FP32
   float* cc = rf + kCtaKmax;                    // correction coefficients
@@ -105,9 +268,12 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
   int32_t* misc = coff + kCtaKmax;  // [0] jpos, [1] count
   float* redF = reinterpret_cast<float*>(red);
 
-  // the slab holds two tiles of the FP64 kernel's size: the FP64 tile, then the FP32 one
+  // the slab holds two tiles of the FP64 kernel's size: the FP64 tile, then
+  // the FP32 one and (Gram path) G = T^T T (k x k, leading dimension kcap:
+  // kcap^2 <= ldm kcap floats fit the tile's unused second half)
   double* Ts = reinterpret_cast<double*>(sc.slab) + (size_t)blockIdx.x * 2 * sc.ldm * sc.kcap;
   float* Tw = reinterpret_cast<float*>(Ts + (size_t)sc.ldm * sc.kcap);
+  float* Gm = Tw + (size_t)sc.ldm * sc.kcap;
   const int ld = sc.ldm;
 
   const int k = a.Wcp[j + 1] - a.Wcp[j];
@@ -120,6 +286,7 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
   const double* Av = reinterpret_cast<const double*>(a.Av);
   uint32_t flags = 0;
 
+  DIAF_PHASE_START();
   // ---- gather (FP64) and the FP32 copy
   for (int r = tid; r < mcap; r += kCtaThreads) {
     rs[r] = r < m ? Rj[r] : INT_MAX;
@@ -153,36 +320,79 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
   __syncthreads();
   cta_col_norms_f(Tw, ld, m, k, cn);
 
-  // ---- FP32 QR of T, kappa estimate, FP32 keys
-  cta_householder_qr<float>(Tw, ld, me, k, redF, nullptr);
-  for (int i = tid; i < k * k; i += kCtaThreads) {
-    const int r = i % k, c = i / k;
-    Rs[r + c * KP] = (r <= c) ? Tw[r + (size_t)c * ld] : 0.0f;
-  }
-  __syncthreads();
-  float kp = 0.0f;
-  for (int c = tid; c < k; c += kCtaThreads) {
-    const float d = fabsf(Rs[c + c * KP]);
-    kp = fmaxf(kp, d > 0.0f ? (float)cn[c] / d : INFINITY);
-    rinv[c] = d > 0.0f ? 1.0f / Rs[c + c * KP] : 0.0f;
-  }
-  const float kap = block_max(kp, redF);
-  if (!(kap <= kMixedKappaMax)) return false;
-  if (a.rule != DIAF_RULE_FIXED) {
-    for (int r = tid; r < m; r += kCtaThreads) {  // Q = T R^-1 by rows (FP32), into Tw
-      float h = 0.0f;
-      for (int c = 0; c < k; ++c) {
-        float acc = (float)Ts[r + (size_t)c * ld];
-        for (int p2 = 0; p2 < c; ++p2) acc -= Tw[r + (size_t)p2 * ld] * Rs[p2 + c * KP];
-        const float z = acc * rinv[c];
-        Tw[r + (size_t)c * ld] = z;
-        h += z * z;
+  DIAF_PHASE(0);
+  // ---- tensor-core Gram path: G, R_s = chol(D G D), kappa, keys by a second product
+  bool gram = false;      // the keys (and G) came from the Gram path
+  bool tw_intact = true;  // Tw still holds the FP32 tile
+  float kap = 0.0f;
+  if (sc.gram && m >= k) {
+    int zero = 0;
+    for (int c = tid; c < k; c += kCtaThreads) {
+      rf[c] = cn[c] > 0.0 ? (float)(1.0 / cn[c]) : 0.0f;
+      zero |= !(cn[c] > 0.0);
+    }
+    if (!__syncthreads_or(zero)) {
+      DIAF_PHASE(11);
+      cta_gram_tc(Tw, ld, m, k, Gm, sc.kcap);
+      DIAF_PHASE(12);
+      for (int i = tid; i < k * k; i += kCtaThreads) Rs[(i % k) + (i / k) * KP] = Gm[(i % k) + (i / k) * sc.kcap];
+      __syncthreads();
+      if (cta_cholesky_scaled(Rs, KP, k, rf, redF)) {
+        float kp = 0.0f;  // column-scaled kappa: ||T(:,c)|| / |R_cc| = 1 / |R_s,cc|
+        for (int c = tid; c < k; c += kCtaThreads) kp = fmaxf(kp, 1.0f / fabsf(Rs[c + c * KP]));
+        kap = block_max(kp, redF);
+        gram = kap <= kGramKappaMax;
       }
-      hk[r] = (double)h;
+      DIAF_PHASE(13);
+    }
+  }
+  if (gram) {
+#ifdef DIAF_PHASE_TIMING
+    if (threadIdx.x == 0 && a.phase) atomicAdd(&a.phase[29], 1ull);
+#endif
+    if (a.rule != DIAF_RULE_FIXED) {
+      cta_upper_inverse_scaled(Rs, KP, k, rf, Vj, KP);  // D R_s^-1 = R^-1
+      DIAF_PHASE(14);
+      cta_row_norms_tc(Tw, ld, m, k, Vj, KP, hk);       // h_r = ||T(r,:) R^-1||^2
+      DIAF_PHASE(15);
+    }
+  } else {
+    // ---- FP32 QR of T, kappa estimate, FP32 keys
+    cta_householder_qr<float>(Tw, ld, me, k, redF, nullptr);
+    for (int i = tid; i < k * k; i += kCtaThreads) {
+      const int r = i % k, c = i / k;
+      Rs[r + c * KP] = (r <= c) ? Tw[r + (size_t)c * ld] : 0.0f;
     }
     __syncthreads();
-    const double margin = cta_select_rows(rs, hk, pick, m, a.rule, j, l - 1, a.tie_tol, red, a.blk);
-    const double delta = kMixedDeltaScale * (m + k) * (double)FLT_EPSILON * (double)kap;
+    float kp = 0.0f;
+    for (int c = tid; c < k; c += kCtaThreads) {
+      const float d = fabsf(Rs[c + c * KP]);
+      kp = fmaxf(kp, d > 0.0f ? (float)cn[c] / d : INFINITY);
+      rinv[c] = d > 0.0f ? 1.0f / Rs[c + c * KP] : 0.0f;
+    }
+    kap = block_max(kp, redF);
+    if (!(kap <= kMixedKappaMax)) return false;
+    if (a.rule != DIAF_RULE_FIXED) {
+      for (int r = tid; r < m; r += kCtaThreads) {  // Q = T R^-1 by rows (FP32), into Tw
+        float h = 0.0f;
+        for (int c = 0; c < k; ++c) {
+          float acc = (float)Ts[r + (size_t)c * ld];
+          for (int p2 = 0; p2 < c; ++p2) acc -= Tw[r + (size_t)p2 * ld] * Rs[p2 + c * KP];
+          const float z = acc * rinv[c];
+          Tw[r + (size_t)c * ld] = z;
+          h += z * z;
+        }
+        hk[r] = (double)h;
+      }
+      __syncthreads();
+    }
+  }
+  DIAF_PHASE(2);
+  if (a.rule != DIAF_RULE_FIXED) {
+    const double margin = cta_select_rows_w0(rs, hk, pick, m, a.rule, j, l - 1, a.tie_tol, a.blk, red);
+    // key error bound: the FP32 QR's backward error amplified by kappa, or
+    // kappa^2 for keys from the Gram matrix
+    const double delta = kMixedDeltaScale * (m + k) * (double)FLT_EPSILON * (double)kap * (gram ? (double)kap : 1.0);
     if (l > 1 && margin <= 2.0 * delta) {
       // the FP32 keys cannot decide this column: the FP64 CTA kernel's QR and
       // key computation on an FP64 copy of the tile (in the FP32 tile's slab
@@ -190,6 +400,10 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
       // so I_j is the FP64 kernel's choice
       double* Tq = reinterpret_cast<double*>(Tw);
       double* Rq = reinterpret_cast<double*>(Rs);  // KP x KMAX doubles over Rs and Vj (both free here)
+      tw_intact = false;
+#ifdef DIAF_PHASE_TIMING
+      if (threadIdx.x == 0 && a.phase) atomicAdd(&a.phase[gram ? 31 : 28], 1ull);
+#endif
       double* rq = wv;                              // reciprocal diagonal
       for (size_t i = tid; i < (size_t)me * k; i += kCtaThreads) Tq[(i % me) + (i / me) * ld] = Ts[(i % me) + (i / me) * ld];
       __syncthreads();
@@ -217,9 +431,10 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
         hk[r] = h;
       }
       __syncthreads();
-      cta_select_rows(rs, hk, pick, m, a.rule, j, l - 1, a.tie_tol, red, a.blk);
+      cta_select_rows_w0(rs, hk, pick, m, a.rule, j, l - 1, a.tie_tol, a.blk, red);
     }
   }
+  DIAF_PHASE(3);
   // I_j
   if (tid == 0) {
     misc[0] = -1;
@@ -256,26 +471,72 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
   for (int t = 0; t < l; ++t) inrows += (Iloc[t] >= 0);
   if (m - inrows < k) return false;  // A-hat has fewer rows than columns
 
-  // ---- FP32 QR of A-hat, Jacobi SVD of R-hat
-  for (size_t i = tid; i < (size_t)me * k; i += kCtaThreads) {
-    const int r = i % me, c = i / me;
-    Tw[r + (size_t)c * ld] = (r < m && inI[r] >= 0) ? 0.0f : (float)Ts[r + (size_t)c * ld];
+  DIAF_PHASE(4);
+  // ---- R-hat: from G on the Gram path (G minus the I_j rows' outer
+  // products, Cholesky of its column-scaled form), else FP32 QR of A-hat
+  bool gram_hat = false;
+  if (gram && tw_intact) {
+    int zc = 0;  // an exactly zero column of A-hat (all its entries in I_j rows) keeps the QR path
+    for (int c = tid; c < k; c += kCtaThreads) {
+      bool nz = false;
+      for (int r = 0; r < m && !nz; ++r) nz = inI[r] < 0 && Tw[r + (size_t)c * ld] != 0.0f;
+      zc |= !nz;
+    }
+    if (!__syncthreads_or(zc)) {
+      for (int i = tid; i < k * k; i += kCtaThreads) {
+        const int p = i % k, q = i / k;
+        float gpq = Gm[p + q * sc.kcap];
+        for (int t = 0; t < l; ++t) {
+          const int r = Iloc[t];
+          if (r >= 0) gpq -= Tw[r + (size_t)p * ld] * Tw[r + (size_t)q * ld];
+        }
+        Rs[p + q * KP] = gpq;
+      }
+      __syncthreads();
+      for (int c = tid; c < k; c += kCtaThreads) {
+        const float gc = Rs[c + c * KP];
+        cn[c] = gc > 0.0f ? (double)sqrtf(gc) : 0.0;  // column norms of A-hat
+        rf[c] = gc > 0.0f ? 1.0f / sqrtf(gc) : 0.0f;
+      }
+      __syncthreads();
+      if (cta_cholesky_scaled(Rs, KP, k, rf, redF)) {
+        float kp = 0.0f;
+        for (int c = tid; c < k; c += kCtaThreads) kp = fmaxf(kp, 1.0f / fabsf(Rs[c + c * KP]));
+        if (block_max(kp, redF) <= kGramKappaMax) {
+          gram_hat = true;
+#ifdef DIAF_PHASE_TIMING
+          if (threadIdx.x == 0 && a.phase) atomicAdd(&a.phase[30], 1ull);
+#endif
+          for (int i = tid; i < k * k; i += kCtaThreads) Rs[(i % k) + (i / k) * KP] *= (float)cn[i / k];
+          __syncthreads();
+        }
+      }
+    }
   }
-  __syncthreads();
-  cta_col_norms_f(Tw, ld, m, k, cn);
-  cta_householder_qr<float>(Tw, ld, me, k, redF, nullptr);
-  float kh = 0.0f;
-  for (int c = tid; c < k; c += kCtaThreads) {  // exact zero columns of A-hat: exact zero singular values
-    const float d = fabsf(Tw[c + (size_t)c * ld]);
-    kh = fmaxf(kh, d > 0.0f ? (float)cn[c] / d : (cn[c] > 0.0 ? INFINITY : 0.0f));
+  if (!gram_hat) {
+    // ---- FP32 QR of A-hat
+    for (size_t i = tid; i < (size_t)me * k; i += kCtaThreads) {
+      const int r = i % me, c = i / me;
+      Tw[r + (size_t)c * ld] = (r < m && inI[r] >= 0) ? 0.0f : (float)Ts[r + (size_t)c * ld];
+    }
+    __syncthreads();
+    cta_col_norms_f(Tw, ld, m, k, cn);
+    cta_householder_qr<float>(Tw, ld, me, k, redF, nullptr);
+    float kh = 0.0f;
+    for (int c = tid; c < k; c += kCtaThreads) {  // exact zero columns of A-hat: exact zero singular values
+      const float d = fabsf(Tw[c + (size_t)c * ld]);
+      kh = fmaxf(kh, d > 0.0f ? (float)cn[c] / d : (cn[c] > 0.0 ? INFINITY : 0.0f));
+    }
+    if (!(block_max(kh, redF) <= kMixedKappaMax)) return false;
+    for (int i = tid; i < k * k; i += kCtaThreads) {
+      const int r = i % k, c = i / k;
+      Rs[r + c * KP] = (r <= c) ? Tw[r + (size_t)c * ld] : 0.0f;
+    }
+    __syncthreads();
   }
-  if (!(block_max(kh, redF) <= kMixedKappaMax)) return false;
-  for (int i = tid; i < k * k; i += kCtaThreads) {
-    const int r = i % k, c = i / k;
-    Rs[r + c * KP] = (r <= c) ? Tw[r + (size_t)c * ld] : 0.0f;
-  }
-  __syncthreads();
+  DIAF_PHASE(6);
   if (cta_jacobi<float, KP, KP>(Rs, k, k, Vj, redF) < 0) flags |= DIAF_FLAG_JACOBI_NOCONV;
+  DIAF_PHASE(7);
   for (int c = tid; c < k; c += kCtaThreads) {
     float s2 = 0.0f;
     for (int i = 0; i < k; ++i) s2 += Rs[i + c * KP] * Rs[i + c * KP];
@@ -347,6 +608,7 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
   const double inv = 1.0 / sqrt(xn);
   for (int c = tid; c < k; c += kCtaThreads) wv[c] *= inv;
   __syncthreads();
+  DIAF_PHASE(8);
   // v = T(I_j,:) w in FP64
   for (int t = tid; t < l; t += kCtaThreads) {
     double s2 = 0.0;
@@ -357,6 +619,7 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
   }
   __syncthreads();
   cta_finish<double>(a, j, k, m, l, jpos, Ts, ld, wv, vv, Is, Iloc, inI, flags, true, red, 1e-14 * smax);
+  DIAF_PHASE(9);
   return true;
 }
 

@@ -69,18 +69,19 @@ class VSpec_t(ctypes.Structure):
 
 class Tuning_t(ctypes.Structure):
     _fields_ = [("m_edge0", ctypes.c_int32), ("m_edge1", ctypes.c_int32), ("warps_per_block", ctypes.c_int32 * 2),
-                ("small_tiles", ctypes.c_int32)]
+                ("small_tiles", ctypes.c_int32), ("large_tiles", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {"m_edge0": self.m_edge0, "m_edge1": self.m_edge1, "warps_per_block": list(self.warps_per_block),
-                "small_tiles": self.small_tiles}
+                "small_tiles": self.small_tiles, "large_tiles": self.large_tiles}
 
     @staticmethod
     def from_dict(d: dict | None) -> "Tuning_t | None":
         if d is None:
             return None
         w = d.get("warps_per_block", [0, 0])
-        return Tuning_t(d.get("m_edge0", 0), d.get("m_edge1", 0), (ctypes.c_int32 * 2)(*w), d.get("small_tiles", 0))
+        return Tuning_t(d.get("m_edge0", 0), d.get("m_edge1", 0), (ctypes.c_int32 * 2)(*w), d.get("small_tiles", 0),
+                        d.get("large_tiles", 0))
 
 
 class Info_t(ctypes.Structure):

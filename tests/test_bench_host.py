@@ -46,10 +46,25 @@ def test_clock_summary_without_sampler():
 
 
 def test_algorithmic_flops_closed_form():
-    # one column, k = 2, m = 3, l = 1, real DIAF-S: QR of T 2k^2(m - k/3), leverage m k^2,
-    # QR of A-hat 2k^2(max(m - l, k) - k/3), SVD 12 k^3, v 2 l k, residual 2 m k
+    # one column, k = 2, m = 3, l = 1, real DIAF-S with 5 Jacobi sweeps: QR of T
+    # 2k^2(m - k/3), leverage m k^2, QR of A-hat 2k^2(max(m - l, k) - k/3), Jacobi
+    # 5 sweeps x k(k-1)/2 pairs x 14 k, FP64 correction 4 m k, v and residual 2 m k
     m, k, l = np.array([3]), np.array([2]), np.array([1])
-    want = 2 * 4 * (3 - 2 / 3) + 3 * 4 + 2 * 4 * (max(3 - 1, 2) - 2 / 3) + 12 * 8 + 2 * 1 * 2 + 2 * 3 * 2
-    got = bench.algorithmic_flops(m, k, l, "S", False)
-    assert abs(got - want) < 1e-9 * want
-    assert abs(bench.algorithmic_flops(m, k, l, "S", True) - 4 * want) < 1e-9 * want
+    f64 = 4 * 3 * 2 + 2 * 3 * 2
+    want = 2 * 4 * (3 - 2 / 3) + 3 * 4 + 2 * 4 * (max(3 - 1, 2) - 2 / 3) + 5 * 1 * 14 * 2 + f64
+    got, got64 = bench.algorithmic_flops(m, k, l, "S", False, sweeps=5)
+    assert abs(got - want) < 1e-9 * want and abs(got64 - f64) < 1e-9 * f64
+    got_c, got64_c = bench.algorithmic_flops(m, k, l, "S", True, sweeps=5)
+    assert abs(got_c - 4 * want) < 1e-9 * want and abs(got64_c - 4 * f64) < 1e-9 * f64
+
+
+def test_gathered_bytes():
+    from workloads import CSC, Pattern
+    # 3 x 3: column nnz 2, 1, 3; W pattern uses column 0 twice and column 2 once
+    A = CSC(3, np.array([0, 2, 3, 6], np.int32), np.array([0, 1, 1, 0, 1, 2], np.int32), np.ones(6))
+    P = Pattern(3, np.array([0, 1, 2, 3], np.int32), np.array([0, 0, 2], np.int32))
+
+    class Wl:
+        pass
+    w = Wl(); w.A, w.PW = A, P
+    assert bench.gathered_bytes(w) == (2 + 2 + 3) * 12.0

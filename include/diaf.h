@@ -36,7 +36,7 @@ typedef enum {
   DIAF_ENOMEM = 2,       /* device allocation failed */
   DIAF_ECUDA = 3,        /* CUDA runtime error (no device, launch failure, ...) */
   DIAF_ENUMERIC = 4,     /* non-finite values produced */
-  DIAF_ETIMEOUT = 5,     /* a bounded device-side wait ran out */
+  DIAF_ETIMEOUT = 5,     /* a bounded device-side wait ran out (no current call waits on the device) */
   DIAF_EUNSUPPORTED = 6  /* a column's tile exceeds every compiled kernel's capacity */
 } diaf_status;
 
@@ -312,26 +312,22 @@ diaf_status diaf_level_schedule(int32_t n, const int32_t* colptr, const int32_t*
  * Such callers set up beforehand: diaf_factor, then one diaf_apply on F,
  * which builds the row-oriented copies of W and V.  Without that first
  * diaf_apply this call returns DIAF_EINVAL.
- * The solve's scratch (a ready flag per row, a ticket counter, t = V^-1 x)
- * is one fixed device array of about 5.3 MB inside the library, held by
- * every GPU that loads it until the process exits; n is limited to 262,144
- * rows (DIAF_EINVAL beyond).  The first call on each device looks up the
- * array's device address (cached for the process: do not use this entry
- * point across a cudaDeviceReset); make that first call before any stream
- * capture.  Every call clears the flags of its n rows and the counter on
- * `stream` before the solve.  All calls on a device share the array and
- * leave their contents in it, so calls that overlap on the GPU (different
- * streams, or several host threads) race; serialise them.  The solve's
- * waits are bounded: one that runs out leaves y wrong but still returns
- * DIAF_OK here; it is reported by the next diaf_sync(F, stream)
- * (DIAF_ETIMEOUT), so check that after the apply.  x, y as for diaf_apply. */
+ * Its one piece of scratch, t = V^-1 x, is a fixed device array of 4 MB
+ * inside the library, held by every GPU that loads it until the process
+ * exits; n is limited to 262,144 rows (DIAF_EINVAL beyond).  The solve is
+ * diaf_apply's level-scheduled one and writes all of t before reading it, so
+ * nothing has to be cleared between calls.  The first call on each device
+ * looks up the array's device address (cached for the process: do not use
+ * this entry point across a cudaDeviceReset); make that first call before
+ * any stream capture.  All calls on a device share the array, so calls that
+ * overlap on the GPU (different streams, or several host threads) race:
+ * serialise them.  x, y as for diaf_apply. */
 diaf_status diaf_apply_static(diaf_factors* F, const void* x, void* y, void* stream);
 /* (Triangular V only: factors of DIAF_RULE_BLOCK give DIAF_EUNSUPPORTED.) */
 
 /* Waits for `stream` and reports device-side errors recorded by earlier
- * calls on F (bounded-wait timeouts, capacity overflows) as a status
- * (infrastructure, no passage of the paper).  Errors: EINVAL (NULL F),
- * ETIMEOUT / EUNSUPPORTED as recorded, ECUDA. */
+ * calls on F (capacity overflows) as a status (infrastructure, no passage of
+ * the paper).  Errors: EINVAL (NULL F), EUNSUPPORTED as recorded, ECUDA. */
 diaf_status diaf_sync(diaf_factors* F, void* stream);
 
 /* Frees F and every device buffer it owns (stream-ordered on the stream F was

@@ -416,7 +416,7 @@ diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_
         np.ta.K = K;
         np.ta.arena = thread_arena_floats(M, K);
         np.ta.nquads = np.tsh.nquads;
-        DIAF_CU(pool.get(&np.ta.slab, (size_t)np.tsh.nquads * ((M * K + 3) / 4 * 4)));
+        DIAF_CU(pool.get(&np.ta.slab, (size_t)np.tsh.nquads * thread_slab_doubles(M, K)));
         DIAF_CU(pool.get(&np.ta.defer_list, np.h_bc[0]));
         np.ta.defer_count = np.work + 3 * kNumBuckets;
         np.thread_cols = np.tsh.grid > 0;
@@ -701,7 +701,6 @@ diaf_status diaf_sync(diaf_factors* F, void* stream) {
   uint32_t h = 0;
   DIAF_CU(cudaMemcpyAsync(&h, F->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   DIAF_CU(cudaStreamSynchronize(s));
-  if (h & DEV_ST_TIMEOUT) return fail(DIAF_ETIMEOUT, "a bounded wait in the triangular solve ran out");
   if (h & DEV_ST_CAPACITY) return fail(DIAF_EUNSUPPORTED, "capacity exceeded on the device");
   return DIAF_OK;
 }
@@ -824,8 +823,41 @@ cudaError_t stage_release(cudaStream_t s) {
 }
 }  // namespace
 
+#ifdef DIAF_PREP_TIMING
+#include <chrono>
+namespace {
+struct PrepTimer {
+  cudaEvent_t ev[8];
+  double host[8];
+  int ne = 0, nh = 0;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  PrepTimer() { for (auto& e : ev) cudaEventCreate(&e); }
+  void dev(cudaStream_t s) { cudaEventRecord(ev[ne++], s); }
+  void hst() { host[nh++] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count(); }
+  ~PrepTimer() {
+    cudaDeviceSynchronize();
+    fprintf(stderr, "prep dev:");
+    for (int i = 1; i < ne; ++i) { float ms = 0; cudaEventElapsedTime(&ms, ev[0], ev[i]); fprintf(stderr, " %.3f", ms); }
+    fprintf(stderr, " | host:");
+    for (int i = 0; i < nh; ++i) fprintf(stderr, " %.3f", host[i]);
+    fprintf(stderr, "\n");
+    for (auto& e : ev) cudaEventDestroy(e);
+  }
+};
+}  // namespace
+#define PT_DEV(s) pt.dev(s)
+#define PT_HOST() pt.hst()
+#else
+#define PT_DEV(s) (void)0
+#define PT_HOST() (void)0
+#endif
+
 static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   if (F->rule == DIAF_RULE_BLOCK) return prepare_apply_blocks(F, s);
+#ifdef DIAF_PREP_TIMING
+  PrepTimer pt;
+#endif
+  PT_DEV(s);
   const int n = F->n;
   const bool cplx = F->dtype == DIAF_C128;
   const size_t esz = cplx ? 16 : 8;
@@ -846,6 +878,7 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   uint32_t* hp = reinterpret_cast<uint32_t*>(order + n1);
   DIAF_CU(cudaMemcpyAsync(cp, F->Vcp, sizeof(int32_t) * n1, cudaMemcpyDeviceToHost, s));
   if (F->nnz_v > 0) DIAF_CU(cudaMemcpyAsync(ri, F->Vri, sizeof(int32_t) * F->nnz_v, cudaMemcpyDeviceToHost, s));
+  PT_DEV(s);
   cudaEvent_t ev[2];
   DIAF_CU(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
   cudaError_t ce = cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
@@ -868,13 +901,17 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   if (ce == cudaSuccess) ce = csr_triangle_check(F->Vr, cplx, tri, s);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(hp, tri, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
   if (ce == cudaSuccess) ce = cudaEventRecord(ev[1], s);
+  PT_DEV(s);
   if (ce == cudaSuccess) ce = F->alloc(&F->Wr.rowptr, n + 1);
   if (ce == cudaSuccess) ce = F->alloc(&F->Wr.colidx, F->nnz_w);
   if (ce == cudaSuccess) ce = F->alloc((char**)&F->Wr.vals, esz * F->nnz_w);
   if (ce == cudaSuccess)
     ce = csc_to_csr(n, F->nnz_w, F->Wcp, F->Wri, F->Wv, cplx, F->Wr.rowptr, F->Wr.colidx, F->Wr.vals, work, s);
+  PT_DEV(s);
+  PT_HOST();
   // wait for the copies even after an error: they write into the staging buffer
   cudaError_t se = cudaEventSynchronize(ev[0]);
+  PT_HOST();
   if (ce != cudaSuccess || se != cudaSuccess) {
     (void)cudaStreamSynchronize(s);
     cudaEventDestroy(ev[0]);
@@ -895,6 +932,7 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
     return fail(DIAF_EINVAL, ls == 1 ? "V is not triangular" : "V has a row index out of range");
   }
   const bool nodiag = ls == 2;
+  PT_HOST();
   se = cudaEventSynchronize(ev[1]);
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
@@ -905,6 +943,7 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   for (int l = 0; l < nlev; ++l) ptr[l + 1] += ptr[l];
   std::vector<int32_t> cur(ptr, ptr + nlev);
   for (int i = 0; i < n; ++i) order[cur[lev[i]]++] = i;
+  PT_HOST();
   LevelCsr& Vl = F->Vl;
   Vl.n = n;
   Vl.nlev = nlev;
@@ -922,12 +961,15 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   DIAF_CU(F->alloc(&Vl.xrow, n));
   DIAF_CU(cudaMemcpyAsync(Vl.lvlptr, ptr, sizeof(int32_t) * (nlev + 1), cudaMemcpyHostToDevice, s));
   if (n > 0) DIAF_CU(cudaMemcpyAsync(dorder, order, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+  PT_DEV(s);
   DIAF_CU(stage_release(s));  // the next user of the staging buffer waits for these copies
   DIAF_CU(csr_level_permute(F->Vr, cplx, dorder, pos, work, Vl, s));
   F->Wl = F->Wr;
   DIAF_CU(F->alloc(&F->Wl.colidx, F->nnz_w));
   DIAF_CU(remap_columns(F->nnz_w, pos, F->Wr.colidx, F->Wl.colidx, s));
   DIAF_CU(F->alloc((char**)&F->tbuf, esz * n));
+  PT_DEV(s);
+  PT_HOST();
   F->apply_ready = true;
   return DIAF_OK;
 }

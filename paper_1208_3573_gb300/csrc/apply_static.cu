@@ -8,12 +8,13 @@
 // which builds the row-oriented copies of W and V), and from then on apply
 // through this entry point.
 //
-// The scratch the triangular solve needs -- one ready flag per row, the
-// ticket counter, and the intermediate vector t = V^-1 x -- lives in one
-// file-scope __device__ array of fixed size, which every GPU that loads the
-// library keeps until the process exits.  Every call clears the ready flags
-// of its rows and the ticket counter on the stream before the solve, so what
-// an earlier call left in the array never counts as ready.
+// The one piece of scratch the apply needs -- the intermediate vector
+// t = V^-1 x, in the level order of the solve -- lives in a file-scope
+// __device__ array of fixed size, which every GPU that loads the library
+// keeps until the process exits.  The solve is the level-scheduled one of
+// diaf_apply (one block, a barrier between levels, no waits on flags), and
+// it writes every entry of t before the SpMV reads it, so nothing in the
+// array has to start at zero and nothing an earlier call left there is read.
 #include <mutex>
 #include <string>
 
@@ -21,11 +22,8 @@
 
 namespace {
 
-constexpr int kStaticMaxN = 1 << 18;  // rows; the array below is about 5.3 MB
-constexpr size_t kCounterBytes = 256;
-constexpr size_t kFlagBytes = (sizeof(uint32_t) * kStaticMaxN + 255) / 256 * 256;
-constexpr size_t kVecBytes = 16 * (size_t)kStaticMaxN;  // complex128 worst case
-constexpr size_t kScratchBytes = kCounterBytes + kFlagBytes + kVecBytes;
+constexpr int kStaticMaxN = 1 << 18;             // rows
+constexpr size_t kScratchBytes = 16 * (size_t)kStaticMaxN;  // t, complex128 worst case: 4 MB
 
 // Device-side scratch shared by every call on a device.  In host code this
 // name is only a stand-in for the symbol, not a device address: the address
@@ -75,17 +73,11 @@ extern "C" diaf_status diaf_apply_static(diaf_factors* F, const void* x, void* y
     }
     base = g_base[dev];
   }
-  int32_t* counter = reinterpret_cast<int32_t*>(base);
-  uint32_t* ready = reinterpret_cast<uint32_t*>(base + kCounterBytes);
-  void* t = base + kCounterBytes + kFlagBytes;
+  void* t = base;
   const bool cplx = F->dtype == DIAF_C128;
-  // the array keeps the previous call's flags: clear this call's rows (the
-  // solve clears the ticket counter itself), then wait on flag value 1
-  e = cudaMemsetAsync(ready, 0, sizeof(uint32_t) * (size_t)F->n, s);
+  e = trsv_levels_perm(F->Vl, cplx, x, t, s);
   if (e != cudaSuccess) return fail(DIAF_ECUDA, cudaGetErrorString(e));
-  e = csr_trsv_syncfree(F->Vr, cplx, F->v_upper, x, t, ready, counter, 1u, F->status, s);
-  if (e != cudaSuccess) return fail(DIAF_ECUDA, cudaGetErrorString(e));
-  e = csr_spmv(F->Wr, cplx, t, y, s);
+  e = csr_spmv(F->Wl, cplx, t, y, s);
   if (e != cudaSuccess) return fail(DIAF_ECUDA, cudaGetErrorString(e));
   return DIAF_OK;
 }

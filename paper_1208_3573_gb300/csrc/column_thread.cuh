@@ -32,7 +32,7 @@
 struct ThreadArgs {
   int M, K;              // capacity of this launch (rows, columns)
   int arena;             // shared-memory floats per column
-  double* slab;          // FP64 tiles: M * K doubles per quad of the grid
+  double* slab;          // FP64 per quad of the grid: the tile T (M * K) and z (M), thread_slab_doubles
   int nquads;            // quads of the grid (the slab's interleave)
   int32_t* defer_list;   // columns left to the warp kernel
   int32_t* defer_count;
@@ -48,9 +48,12 @@ constexpr int kQuadWarps = 1;       // warps per block
 __host__ __device__ constexpr int thread_arena_floats(int M, int K) {
   return ((M * K > 2 * K * K ? M * K : 2 * K * K) + M + K + 3) / 4 * 4;
 }
-// FP64 shared-memory scratch per column: the refined vector x (K) and
-// z = A-hat x (M), each rounded up to whole rows of 4.
-__host__ __device__ constexpr int thread_arena_doubles(int M, int K) { return (K + 3) / 4 * 4 + (M + 3) / 4 * 4; }
+// FP64 shared-memory scratch per column: the refined vector x (K), rounded
+// up to whole rows of 4.
+__host__ __device__ constexpr int thread_arena_doubles(int M, int K) { return (void)M, (K + 3) / 4 * 4; }
+// FP64 slab doubles per quad: the tile T (M K) and z = A-hat x (M), each
+// rounded up to whole rows of 4.
+__host__ __device__ constexpr int thread_slab_doubles(int M, int K) { return (M * K + 3) / 4 * 4 + (M + 3) / 4 * 4; }
 // Shared-memory bytes of one warp (eight columns).
 __host__ __device__ constexpr size_t thread_warp_smem(int M, int K) {
   return sizeof(float) * (size_t)thread_arena_floats(M, K) * 8 + sizeof(double) * (size_t)thread_arena_doubles(M, K) * 8;
@@ -488,8 +491,8 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
   // z = A-hat x (m) in the quad's FP64 shared scratch: lane `sub` computes z
   // on its tile rows and (A-hat^T z)_q, r_q and the update of x_q on its rows
   // q of V.
-  double* X = D;       // x, element q
-  double* Z = D + 32 * ((K + 3) / 4);  // z, element r (after x's rows of 4)
+  double* X = D;  // x, element q
+  const int zo = (M * K + 3) / 4 * 4;  // z, element r: slab element zo + r
   {
     const float* vmin = qptr(W, VO + imin * k + sub);
     double* xs = qptr(X, sub);
@@ -505,7 +508,7 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
       double z = 0.0;
       if (!((inI >> r) & 1u))
         for (int q = 0; q < k; ++q) z = fma(T(r + q * m), QS(X, q), z);
-      QS(Z, r) = z;
+      T(zo + r) = z;
       zz = fma(z, z, zz);
     }
     double xx = 0.0;
@@ -518,17 +521,23 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
     const double d = qsum(zz, qm) / qsum(xx, qm);
     __syncwarp(qm);  // z complete
     float rfo[kQK];  // r on the lane's rows of V, in FP32
-    double xo[kQK];
+    double xo[kQK], gq[kQK];
+#pragma unroll
+    for (int u = 0; u < kQK; ++u) gq[u] = 0.0;
+    for (int r = 0; r < m; ++r) {  // rows in I_j have z_r = 0
+      const double zr = T(zo + r);
+#pragma unroll
+      for (int u = 0; u < kQK; ++u)
+        if (u < nk) gq[u] = fma(T(r + (sub + 4 * u) * m), zr, gq[u]);
+    }
 #pragma unroll
     for (int u = 0; u < kQK; ++u) {
       const int q = sub + 4 * u;
       rfo[u] = 0.0f;
       xo[u] = 0.0;
       if (u < nk) {
-        double gq = 0.0;
-        for (int r = 0; r < m; ++r) gq = fma(T(r + q * m), QS(Z, r), gq);  // rows in I_j have z_r = 0
         xo[u] = QS(X, q);
-        rfo[u] = (float)(gq - d * xo[u]);
+        rfo[u] = (float)(gq[u] - d * xo[u]);
       }
     }
     float dxo[kQK];
@@ -640,7 +649,7 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
 // The persistent loop: each warp takes eight columns of the list at a time,
 // one per quad.
 template <int KMAX>
-__global__ void __launch_bounds__(32 * kQuadWarps, 12) column_thread_kernel(ColArgs a, ThreadArgs ta) {
+__global__ void __launch_bounds__(32 * kQuadWarps, 16) column_thread_kernel(ColArgs a, ThreadArgs ta) {
   extern __shared__ __align__(16) float tsmem[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;

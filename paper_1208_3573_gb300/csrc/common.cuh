@@ -13,7 +13,6 @@
 // Device status bits (a uint32 in device memory, OR-ed by kernels).
 enum : uint32_t {
   DEV_ST_CAPACITY = 1u,     // a column exceeded the capacity of the kernel that got it
-  DEV_ST_TIMEOUT = 2u,      // a bounded wait ran out
   DEV_ST_BAD_INPUT = 4u,    // index out of range / unsorted column found on the device
   DEV_ST_SINGULAR = 8u,     // a zero pivot (block LU of V)
 };

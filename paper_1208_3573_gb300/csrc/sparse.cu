@@ -91,68 +91,6 @@ __global__ void tri_check_kernel(int n, const int32_t* rowptr, const int32_t* co
   if (f) atomicOr(out, f);
 }
 
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
-__device__ __forceinline__ Cx<double> ld_cg(const Cx<double>* p) {
-  double2 v = __ldcg(reinterpret_cast<const double2*>(p));
-  return {v.x, v.y};
-}
-
-// Polls of one flag before giving up (~seconds); a test build lowers it to
-// check the timeout path.
-#ifndef DIAF_SPIN_LIMIT
-#define DIAF_SPIN_LIMIT (1ll << 22)
-#endif
-constexpr long long kSpinLimit = DIAF_SPIN_LIMIT;
-
-template <class S>
-__global__ void trsv_syncfree_kernel(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                                     const S* __restrict__ vals, const S* __restrict__ x, S* t, uint32_t* ready,
-                                     int32_t* counter, uint32_t gen, int upper, uint32_t* status) {
-  const int lane = threadIdx.x & 31;
-  while (true) {
-    int tk = 0;
-    if (lane == 0) tk = atomicAdd(counter, 1);
-    tk = __shfl_sync(DIAF_FULL, tk, 0);
-    if (tk >= n) return;
-    const int i = upper ? (n - 1 - tk) : tk;
-    S acc = sc_zero<S>();
-    S diag = sc_zero<S>();
-    bool timed_out = false;
-    for (int p = rowptr[i] + lane; p < rowptr[i + 1]; p += DIAF_WARP) {
-      int c = colidx[p];
-      S v = vals[p];
-      if (c == i) { diag = v; continue; }
-      long long it = 0;
-      while (ld_acquire(ready + c) != gen) {
-        if (++it > kSpinLimit) { timed_out = true; break; }
-        __nanosleep(64);
-      }
-      acc += v * ld_cg(t + c);
-    }
-    acc = warp_sum(acc);
-    diag = warp_sum(diag);
-    if (__any_sync(DIAF_FULL, timed_out) && lane == 0) atomicOr(status, DEV_ST_TIMEOUT);
-    if (lane == 0) {
-      S b = x[i] - acc;
-      double d2 = sc_abs2(diag);
-      S ti = (1.0 / d2) * (b * sc_conj(diag));
-      t[i] = ti;
-      __threadfence();
-      st_release(ready + i, gen);
-    }
-    __syncwarp();
-  }
-}
-
 constexpr int kLevelThreads = 1024;
 constexpr int kLevelPtrSmem = 8192;  // level pointers kept in shared memory up to this many levels
 constexpr int kPrefetch = 4;         // off-diagonal entries of a row held in registers ahead of its level
@@ -468,26 +406,3 @@ cudaError_t csr_triangle_check(const Csr& V, bool cplx, uint32_t* out, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t csr_trsv_syncfree(const Csr& V, bool cplx, bool upper, const void* x, void* t, uint32_t* ready,
-                              int32_t* counter, uint32_t gen, uint32_t* status, cudaStream_t s) {
-  if (V.n <= 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
-  if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0;
-  e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return e;
-  int threads = 256;
-  int blocks = ceil_div(V.n, threads / 32);
-  if (blocks > sms * 8) blocks = sms * 8;
-  if (cplx)
-    trsv_syncfree_kernel<Cx<double>><<<blocks, threads, 0, s>>>(V.n, V.rowptr, V.colidx, (const Cx<double>*)V.vals,
-                                                                (const Cx<double>*)x, (Cx<double>*)t, ready, counter,
-                                                                gen, upper ? 1 : 0, status);
-  else
-    trsv_syncfree_kernel<double><<<blocks, threads, 0, s>>>(V.n, V.rowptr, V.colidx, (const double*)V.vals,
-                                                            (const double*)x, (double*)t, ready, counter, gen,
-                                                            upper ? 1 : 0, status);
-  DIAF_COUNT_LAUNCH();
-  return cudaGetLastError();
-}

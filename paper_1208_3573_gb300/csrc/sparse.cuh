@@ -26,15 +26,6 @@ cudaError_t csr_spmv(const Csr& M, bool cplx, const void* x, void* y, cudaStream
 // 2 = has strictly upper entries, 4 = missing or zero diagonal.
 cudaError_t csr_triangle_check(const Csr& V, bool cplx, uint32_t* out, cudaStream_t s);
 
-// t = V^-1 x for upper (upper=true) or lower triangular CSR V.  Sync-free:
-// each warp takes the next row by an atomic ticket, in dependency order, and
-// waits (bounded) for the rows it needs.  `ready` holds one flag per row,
-// `counter` one ticket counter (zeroed here); `gen` must differ from every
-// value left in `ready` by earlier solves.  A wait that runs out sets
-// DEV_ST_TIMEOUT in *status and the row is finished with what it has.
-cudaError_t csr_trsv_syncfree(const Csr& V, bool cplx, bool upper, const void* x, void* t, uint32_t* ready,
-                              int32_t* counter, uint32_t gen, uint32_t* status, cudaStream_t s);
-
 // V in level order for the level-scheduled solve: position p holds row
 // xrow[p] of V; the rows of level l (their depth in V's dependency graph) are
 // positions lvlptr[l]..lvlptr[l+1]; rowptr/colidx/vals hold each row's

@@ -161,10 +161,13 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
   DIAF_PHASE_START();
 
   // ---- gather T = A(R_j, J_j): own rows zeroed, then each lane places every
-  // fourth entry of the J_j columns by a binary search in R_j
+  // fourth entry of the J_j columns by a binary search in R_j (a copy of R_j
+  // in the keys' shared-memory slots, which are free until the keys)
   const int32_t* Rj = a.rows + a.Eoff[j];
   const int32_t* J = a.Wri + a.Wcp[j];
   const double* Av = reinterpret_cast<const double*>(a.Av);
+  auto RS = [&](int r) -> int32_t& { return *reinterpret_cast<int32_t*>(qptr(W, HK + r)); };
+  for (int r = sub; r < m; r += 4) RS(r) = Rj[r];
   for (int q = 0; q < k; ++q) {
     double* gq = gptr(q * m + sub);
     float* wq = qptr(W, q * m + sub);
@@ -180,7 +183,17 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
     const int c = J[q];
     const int pe = a.Acp[c + 1];
     for (int p = a.Acp[c] + sub; p < pe; p += 4) {
-      const int r = lower_bound_i32(Rj, m, a.Ari[p]);
+      const int32_t row = a.Ari[p];
+      int r = 0;  // first position of R_j holding a row >= row (row is in R_j)
+      for (int len = m; len > 0;) {
+        const int half = len >> 1;
+        if (RS(r + half) < row) {
+          r += half + 1;
+          len -= half + 1;
+        } else {
+          len = half;
+        }
+      }
       const double v = Av[p];
       T(r + q * m) = v;
       QS(W, r + q * m) = (float)v;
@@ -323,18 +336,21 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
   __syncwarp(qm);
   quad_qr(W, m, k, sub, qm);
   float kh = 0.0f;
+  bool zdiag = false;  // a zero column of A-hat: R-hat is singular and V cannot come from R0^-1 B
 #pragma unroll
   for (int q = 0; q < KMAX; ++q)
     if (q < k) {
       const float d = fabsf(QS(W, q + q * m));
       kh = fmaxf(kh, d > 0.0f ? ch[q] / d : (ch[q] > 0.0f ? INFINITY : 0.0f));
+      zdiag |= d == 0.0f;
     }
-  if (!(kh <= kMixedKappaMax)) { defer(); return; }
+  if (!(kh <= kMixedKappaMax) || zdiag) { defer(); return; }
 
   // ---- R-hat to ld k at W[0, k^2) column by column (a column's new place
   DIAF_PHASE(6);
-  // lies below every later column's old one), V = I at W[k^2, 2k^2).  Lane
-  // `sub` owns rows sub + 4u (u < nk) of every k x k column.
+  // lies below every later column's old one), and a copy R0 of it at
+  // W[k^2, 2k^2) for recovering V after the sweeps.  Lane `sub` owns rows
+  // sub + 4u (u < nk) of every k x k column.
   const int nk = (k - sub + 3) >> 2;
   for (int c = 0; c < k; ++c) {
     const float* src = qptr(W, c * m + sub);
@@ -350,14 +366,18 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
   }
   const int VO = k * k;
   for (int c = 0; c < k; ++c) {
+    const float* src = qptr(W, c * k + sub);
     float* dst = qptr(W, VO + c * k + sub);
 #pragma unroll
     for (int u = 0; u < kQK; ++u)
-      if (u < nk) dst[32 * u] = sub + 4 * u == c ? 1.0f : 0.0f;
+      if (u < nk) dst[32 * u] = src[32 * u];
   }
 
   // ---- one-sided Jacobi on R-hat in the warp kernels' round-robin order
   DIAF_PHASE(5);
+  // (the rotations are applied to R-hat only: V is recovered afterwards from
+  // R-hat V = B as R0^-1 B, which costs one triangular solve per column
+  // instead of a second pair of column updates per rotation)
   // (in round rnd, position p >= 1 holds column 1 + ((p - 1 + rnd) mod L) and
   // positions p, qq - 1 - p pair up), with their rotation and stopping rules:
   // skip below tol = k eps_32, stop after a sweep without a rotation of
@@ -434,16 +454,11 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
               const float t = __fdividef(copysignf(2.0f * ag, d), fabsf(d) + sqrtf(d * d + 4.0f * g2));
               const float cs = rsqrtf(1.0f + t * t), sn = cs * t;
               const float ssn = g[h] < 0.0f ? -sn : sn, scs = g[h] < 0.0f ? -cs : cs;  // y = sign(g) b
-              float* va = qptr(W, VO + pa[h] * k + sub);
-              float* vb = qptr(W, VO + pb[h] * k + sub);
 #pragma unroll
               for (int u = 0; u < kQK; ++u)
                 if (u < nk) {
                   ga[h][32 * u] = fmaf(-ssn, xb[h][u], cs * xa[h][u]);
                   gb[h][32 * u] = fmaf(scs, xb[h][u], sn * xa[h][u]);
-                  const float xv = va[32 * u], yv = vb[32 * u];
-                  va[32 * u] = fmaf(-ssn, yv, cs * xv);
-                  vb[32 * u] = fmaf(scs, yv, sn * xv);
                 }
               QS(W, NR + pa[h]) = al - t * ag;
               QS(W, NR + pb[h]) = be + t * ag;
@@ -481,20 +496,62 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
       snext = fmin(snext, sv);
       gap = fmin(gap, sv * sv - smin * smin);
     }
+  // V = R0^-1 B in place of B: lane `sub` solves for the columns sub + 4v,
+  // column-oriented back substitution (column jj of R0 read through four
+  // pointers, element jj k + 4u + w at P[w][32 u])
+  __syncwarp(qm);  // every lane has read B for the norms
+  for (int c = sub; c < k; c += 4) {
+    float bv[KMAX];
+    const float* P0 = qptr(W, c * k);
+    const float* P1 = qptr(W, c * k + 1);
+    const float* P2 = qptr(W, c * k + 2);
+    const float* P3 = qptr(W, c * k + 3);
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i) {
+      const float* P = (i & 3) == 0 ? P0 : ((i & 3) == 1 ? P1 : ((i & 3) == 2 ? P2 : P3));
+      bv[i] = i < k ? P[32 * (i >> 2)] : 0.0f;
+    }
+#pragma unroll
+    for (int jj = KMAX - 1; jj >= 0; --jj) {
+      if (jj < k) {
+        const float* R0 = qptr(W, VO + jj * k);
+        const float* R1 = qptr(W, VO + jj * k + 1);
+        const float* R2 = qptr(W, VO + jj * k + 2);
+        const float* R3 = qptr(W, VO + jj * k + 3);
+        const float* Rd = (jj & 3) == 0 ? R0 : ((jj & 3) == 1 ? R1 : ((jj & 3) == 2 ? R2 : R3));
+        bv[jj] = bv[jj] / Rd[32 * (jj >> 2)];
+#pragma unroll
+        for (int i = 0; i < jj; ++i) {
+          const float* R = (i & 3) == 0 ? R0 : ((i & 3) == 1 ? R1 : ((i & 3) == 2 ? R2 : R3));
+          bv[i] = fmaf(-R[32 * (i >> 2)], bv[jj], bv[i]);
+        }
+      }
+    }
+    float* Q0 = qptr(W, c * k);
+    float* Q1 = qptr(W, c * k + 1);
+    float* Q2 = qptr(W, c * k + 2);
+    float* Q3 = qptr(W, c * k + 3);
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i) {
+      float* Q = (i & 3) == 0 ? Q0 : ((i & 3) == 1 ? Q1 : ((i & 3) == 2 ? Q2 : Q3));
+      if (i < k) Q[32 * (i >> 2)] = bv[i];
+    }
+  }
+  __syncwarp(qm);
   if (k > 1 && (snext - smin) <= 1e-6 * smax) flags |= DIAF_FLAG_DEGENERATE;
   if (k > 1 && gap <= 1e-5 * smax * smax) { defer(); return; }
   const int iters = (k > 1 && gap < 1e-2 * smax * smax) ? 2 : 1;
 
   // ---- FP64 correction in the FP32 singular basis V: d = x^T H x / x^T x,
   // r = H x - d x (H = A-hat^T A-hat from the FP64 tile),
-  // x <- x - sum_{i != imin} V_i (V_i^T r) / (sigma_i^2 - d).  x (k) and
-  // z = A-hat x (m) in the quad's FP64 shared scratch: lane `sub` computes z
+  // x <- x - sum_{i != imin} V_i (V_i^T r) / (sigma_i^2 - d).  x (k) in the
+  // quad's FP64 shared scratch, z = A-hat x (m) in its slab: lane `sub` computes z
   // on its tile rows and (A-hat^T z)_q, r_q and the update of x_q on its rows
   // q of V.
   double* X = D;  // x, element q
   const int zo = (M * K + 3) / 4 * 4;  // z, element r: slab element zo + r
   {
-    const float* vmin = qptr(W, VO + imin * k + sub);
+    const float* vmin = qptr(W, imin * k + sub);
     double* xs = qptr(X, sub);
 #pragma unroll
     for (int u = 0; u < kQK; ++u)
@@ -544,7 +601,7 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
 #pragma unroll
     for (int u = 0; u < kQK; ++u) dxo[u] = 0.0f;
     for (int i = 0; i < k; ++i) {
-      const float* vi = qptr(W, VO + i * k + sub);
+      const float* vi = qptr(W, i * k + sub);
       float vo[kQK];
       float vr = 0.0f;
 #pragma unroll

@@ -168,6 +168,13 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
   const double* Av = reinterpret_cast<const double*>(a.Av);
   auto RS = [&](int r) -> int32_t& { return *reinterpret_cast<int32_t*>(qptr(W, HK + r)); };
   for (int r = sub; r < m; r += 4) RS(r) = Rj[r];
+  // the entry range of A(:, J_j[q]) as an int pair in FP64 scratch slot q
+  // (free until the correction)
+  auto CR = [&](int q) -> int2& { return *reinterpret_cast<int2*>(qptr(D, q)); };
+  for (int q = sub; q < k; q += 4) {
+    const int c = J[q];
+    CR(q) = make_int2(a.Acp[c], a.Acp[c + 1]);
+  }
   for (int q = 0; q < k; ++q) {
     double* gq = gptr(q * m + sub);
     float* wq = qptr(W, q * m + sub);
@@ -180,9 +187,8 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
   }
   __syncwarp(qm);
   for (int q = 0; q < k; ++q) {
-    const int c = J[q];
-    const int pe = a.Acp[c + 1];
-    for (int p = a.Acp[c] + sub; p < pe; p += 4) {
+    const int2 be = CR(q);
+    for (int p = be.x + sub; p < be.y; p += 4) {
       const int32_t row = a.Ari[p];
       int r = 0;  // first position of R_j holding a row >= row (row is in R_j)
       for (int len = m; len > 0;) {

@@ -83,6 +83,10 @@ constexpr int kPairRounds = kThreadKMax - 1, kPairSlots = kThreadKMax / 2;
 static __constant__ uint8_t kPairTab[kThreadKMax / 2][kPairRounds][kPairSlots];
 
 constexpr int kQR = kThreadMMax / 4;  // most rows a lane owns in a column of the tile
+#ifndef DIAF_QUAD_JACOBI_PAIRS
+#define DIAF_QUAD_JACOBI_PAIRS 4
+#endif
+constexpr int kJP = DIAF_QUAD_JACOBI_PAIRS;  // disjoint pairs of a round rotated together
 constexpr int kQK = kThreadKMax / 4;  // most rows a lane owns in a column of a k x k matrix
 
 // Householder QR in place of the m x k column-major matrix at W (ld m,
@@ -239,29 +243,39 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
   // ---- leverage keys h_r = ||Q(r,:)||^2, Q = T R^-1 by rows (own rows; R's
   DIAF_PHASE(2);
   // column c read through four pointers, element c m + 4u + v at P[v][32 u])
-  for (int t = 0; t < nown; ++t) {
+  // two rows at a time: the loads of R are shared and the two solves are
+  // independent chains
+  for (int t = 0; t < nown; t += 2) {
     const int r = sub + 4 * t;
-    float z[KMAX];
-    float h = 0.0f;
+    const bool two = t + 1 < nown;
+    float z[KMAX], y[KMAX];
+    float h = 0.0f, h1 = 0.0f;
 #pragma unroll
     for (int c = 0; c < KMAX; ++c) {
       z[c] = 0.0f;
+      y[c] = 0.0f;
       if (c < k) {
         const float* P0 = qptr(W, c * m);
         const float* P1 = qptr(W, c * m + 1);
         const float* P2 = qptr(W, c * m + 2);
         const float* P3 = qptr(W, c * m + 3);
         float acc = (float)T(r + c * m);
+        float acc1 = two ? (float)T(r + 4 + c * m) : 0.0f;
 #pragma unroll
         for (int p2 = 0; p2 < c; ++p2) {
           const float* P = (p2 & 3) == 0 ? P0 : ((p2 & 3) == 1 ? P1 : ((p2 & 3) == 2 ? P2 : P3));
-          acc = fmaf(-z[p2], P[32 * (p2 >> 2)], acc);
+          const float rv = P[32 * (p2 >> 2)];
+          acc = fmaf(-z[p2], rv, acc);
+          acc1 = fmaf(-y[p2], rv, acc1);
         }
         z[c] = acc * rinv[c];
+        y[c] = acc1 * rinv[c];
         h = fmaf(z[c], z[c], h);
+        h1 = fmaf(y[c], y[c], h1);
       }
     }
     QS(W, HK + r) = h;
+    if (two) QS(W, HK + r + 4) = h1;
   }
   __syncwarp(qm);
 
@@ -322,19 +336,26 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
   // ---- FP32 QR of A-hat (the I_j rows zeroed), its conditioning
   DIAF_PHASE(4);
   float ch[KMAX];
+  // own rows of every column first (independent loads), the column norms
+  // from shared memory after
+  for (int q = 0; q < k; ++q) {
+    const double* gq = gptr(q * m + sub);
+    float* wq = qptr(W, q * m + sub);
+    float f[kQR];
+#pragma unroll
+    for (int t = 0; t < kQR; ++t) f[t] = (t < nown && !((inI >> (sub + 4 * t)) & 1u)) ? (float)gq[t * gstride] : 0.0f;
+#pragma unroll
+    for (int t = 0; t < kQR; ++t)
+      if (t < nown) wq[32 * t] = f[t];
+  }
 #pragma unroll
   for (int q = 0; q < KMAX; ++q) {
     float s2 = 0.0f;
     if (q < k) {
-      const double* gq = gptr(q * m + sub);
-      float* wq = qptr(W, q * m + sub);
+      const float* wq = qptr(W, q * m + sub);
 #pragma unroll
       for (int t = 0; t < kQR; ++t)
-        if (t < nown) {
-          const float f = (inI >> (sub + 4 * t)) & 1u ? 0.0f : (float)gq[t * gstride];
-          wq[32 * t] = f;
-          s2 = fmaf(f, f, s2);
-        }
+        if (t < nown) s2 = fmaf(wq[32 * t], wq[32 * t], s2);
     }
     ch[q] = 0.0f;
     if (q < k) ch[q] = sqrtf(qsum(s2, qm));
@@ -388,7 +409,8 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
   // positions p, qq - 1 - p pair up), with their rotation and stopping rules:
   // skip below tol = k eps_32, stop after a sweep without a rotation of
   // |gamma|^2 >= tol alpha beta; norms carried through rotations.  The pairs
-  // of a round are disjoint: two are rotated together (independent chains).
+  // of a round are disjoint: kJP of them are rotated together (independent
+  // chains).
   // Every lane of the quad writes the same norms.
   uint32_t flags = 0;
   {
@@ -426,13 +448,18 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
       bool large = false;
       if (k >= 2) {
         for (int rnd = 0; rnd < L; ++rnd) {
-          for (int pr = 0; pr < npairs; pr += 2) {
-            const int2 p0 = pair_of(pr, rnd), p1 = pair_of(pr + 1, rnd);
-            const int pa[2] = {p0.x, p1.x}, pb[2] = {p0.y, p1.y};
-            float xa[2][kQK], xb[2][kQK], g[2];
-            float *ga[2], *gb[2];
+          for (int pr = 0; pr < npairs; pr += kJP) {
+            int pa[kJP], pb[kJP];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < kJP; ++h) {
+              const int2 ph = pair_of(pr + h, rnd);
+              pa[h] = ph.x;
+              pb[h] = ph.y;
+            }
+            float xa[kJP][kQK], xb[kJP][kQK], g[kJP];
+            float *ga[kJP], *gb[kJP];
+#pragma unroll
+            for (int h = 0; h < kJP; ++h) {
               const bool act = pb[h] >= 0;
               ga[h] = qptr(W, (act ? pa[h] : 0) * k + sub);
               gb[h] = qptr(W, (act ? pb[h] : 0) * k + sub);
@@ -445,11 +472,11 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
               }
             }
 #pragma unroll
-            for (int h = 0; h < 2; ++h) g[h] += __shfl_xor_sync(qm, g[h], 1);
+            for (int h = 0; h < kJP; ++h) g[h] += __shfl_xor_sync(qm, g[h], 1);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) g[h] += __shfl_xor_sync(qm, g[h], 2);
+            for (int h = 0; h < kJP; ++h) g[h] += __shfl_xor_sync(qm, g[h], 2);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < kJP; ++h) {
               if (pb[h] < 0) continue;
               const float al = QS(W, NR + pa[h]), be = QS(W, NR + pb[h]);
               const float g2 = g[h] * g[h];

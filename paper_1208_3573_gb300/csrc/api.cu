@@ -14,6 +14,36 @@
 #include "plan.cuh"
 #include "sparse.cuh"
 
+#ifdef DIAF_PREP_TIMING
+#include <chrono>
+namespace {
+struct PrepTimer {
+  const char* tag;
+  explicit PrepTimer(const char* t) : tag(t) { for (auto& e : ev) cudaEventCreate(&e); }
+  cudaEvent_t ev[8];
+  double host[8];
+  int ne = 0, nh = 0;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  void dev(cudaStream_t s) { cudaEventRecord(ev[ne++], s); }
+  void hst() { host[nh++] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count(); }
+  ~PrepTimer() {
+    cudaDeviceSynchronize();
+    fprintf(stderr, "%s dev:", tag);
+    for (int i = 1; i < ne; ++i) { float ms = 0; cudaEventElapsedTime(&ms, ev[0], ev[i]); fprintf(stderr, " %.3f", ms); }
+    fprintf(stderr, " | host:");
+    for (int i = 0; i < nh; ++i) fprintf(stderr, " %.3f", host[i]);
+    fprintf(stderr, "\n");
+    for (auto& e : ev) cudaEventDestroy(e);
+  }
+};
+}  // namespace
+#define PT_DEV(s) pt.dev(s)
+#define PT_HOST() pt.hst()
+#else
+#define PT_DEV(s) (void)0
+#define PT_HOST() (void)0
+#endif
+
 static std::atomic<long long> g_launches{0};
 #ifdef DIAF_PHASE_TIMING
 static unsigned long long* g_phase = nullptr;  // device, 32 counters
@@ -36,6 +66,40 @@ std::mutex g_mem_mu;
 std::unordered_map<void*, size_t> g_mem_held;
 size_t g_mem_total = 0;
 size_t g_mem_cap = 0;  // 0: no cap
+
+// The library's own stream-ordered memory pool per device.  Its release
+// threshold is unlimited, so memory freed by one setup stays in the pool
+// for the next instead of going back to the driver at every synchronisation
+// (the default pool's behaviour), which would make every allocation map
+// fresh pages.  The pool holds the high-water mark of the library's use.
+constexpr int kPoolDevices = 64;
+cudaMemPool_t g_pool[kPoolDevices] = {};
+
+cudaError_t library_pool(cudaMemPool_t* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kPoolDevices) return cudaErrorInvalidDevice;
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = UINT64_MAX;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(pool);
+      return e;
+    }
+    g_pool[dev] = pool;
+  }
+  *out = g_pool[dev];
+  return cudaSuccess;
+}
 }  // namespace
 
 cudaError_t diaf_dev_alloc(void** p, size_t bytes, cudaStream_t s) {
@@ -46,7 +110,13 @@ cudaError_t diaf_dev_alloc(void** p, size_t bytes, cudaStream_t s) {
     g_mem_total += bytes;  // reserved before the call, so concurrent requests see it
   }
   void* q = nullptr;
-  cudaError_t e = cudaMallocAsync(&q, bytes, s);
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e;
+  {
+    std::lock_guard<std::mutex> lock(g_mem_mu);
+    e = library_pool(&pool);
+  }
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&q, bytes, pool, s);
   std::lock_guard<std::mutex> lock(g_mem_mu);
   if (e != cudaSuccess) {
     g_mem_total -= bytes;
@@ -247,6 +317,11 @@ diaf_status check_args(const diaf_csc* A, const diaf_pattern* PW, const diaf_vsp
 // `s` (twice: after the input check and to size V).
 diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_vspec* V, int32_t alg, int32_t prec,
                           const diaf_tuning* tuning, cudaStream_t s, diaf_factors* F, Pool& pool, NumericPlan& np) {
+#ifdef DIAF_PREP_TIMING
+  PrepTimer pt("symbolic");
+#endif
+  PT_DEV(s);
+  PT_HOST();
   const int n = A->n;
   const bool cplx = A->dtype == DIAF_C128;
   const size_t esz = cplx ? 16 : 8;
@@ -324,7 +399,10 @@ diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_
     DIAF_CU(exclusive_scan_i32_to_i64(pa.E, pa.Eoff, n, bs64, s));
     DIAF_CU(cudaMemcpyAsync(&h_Etot, pa.Eoff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     DIAF_CU(cudaMemcpyAsync(&h_status, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    PT_DEV(s);
+    PT_HOST();
     DIAF_CU(cudaStreamSynchronize(s));
+    PT_HOST();
     if (h_status & DEV_ST_BAD_INPUT) return fail(DIAF_EINVAL, "unsorted or out-of-range indices in A, PW or V");
   }
   DIAF_CU(pool.get(&pa.rows, (size_t)h_Etot));
@@ -341,7 +419,10 @@ diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_
     DIAF_CU(cudaMemcpyAsync(np.h_bc, np.bucket_count, sizeof(np.h_bc), cudaMemcpyDeviceToHost, s));
     DIAF_CU(cudaMemcpyAsync(h_stats, stats, sizeof(h_stats), cudaMemcpyDeviceToHost, s));
     DIAF_CU(cudaMemcpyAsync(&h_status, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    PT_DEV(s);
+    PT_HOST();
     DIAF_CU(cudaStreamSynchronize(s));
+    PT_HOST();
   }
   if (h_status & DEV_ST_CAPACITY)
     return fail(DIAF_EUNSUPPORTED, "a column needs more than 4096 gathered entries or a tile beyond 1024 x 64");
@@ -437,6 +518,8 @@ diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_
     const int slabs = np.cta_grid > np.cta_grid_mixed ? np.cta_grid : np.cta_grid_mixed;
     DIAF_CU(pool.get((char**)&np.cs.slab, (size_t)slabs * 2 * np.cs.ldm * np.cs.kcap * esz));
   }
+  PT_DEV(s);
+  PT_HOST();
   return DIAF_OK;
 }
 
@@ -823,39 +906,11 @@ cudaError_t stage_release(cudaStream_t s) {
 }
 }  // namespace
 
-#ifdef DIAF_PREP_TIMING
-#include <chrono>
-namespace {
-struct PrepTimer {
-  cudaEvent_t ev[8];
-  double host[8];
-  int ne = 0, nh = 0;
-  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
-  PrepTimer() { for (auto& e : ev) cudaEventCreate(&e); }
-  void dev(cudaStream_t s) { cudaEventRecord(ev[ne++], s); }
-  void hst() { host[nh++] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count(); }
-  ~PrepTimer() {
-    cudaDeviceSynchronize();
-    fprintf(stderr, "prep dev:");
-    for (int i = 1; i < ne; ++i) { float ms = 0; cudaEventElapsedTime(&ms, ev[0], ev[i]); fprintf(stderr, " %.3f", ms); }
-    fprintf(stderr, " | host:");
-    for (int i = 0; i < nh; ++i) fprintf(stderr, " %.3f", host[i]);
-    fprintf(stderr, "\n");
-    for (auto& e : ev) cudaEventDestroy(e);
-  }
-};
-}  // namespace
-#define PT_DEV(s) pt.dev(s)
-#define PT_HOST() pt.hst()
-#else
-#define PT_DEV(s) (void)0
-#define PT_HOST() (void)0
-#endif
 
 static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   if (F->rule == DIAF_RULE_BLOCK) return prepare_apply_blocks(F, s);
 #ifdef DIAF_PREP_TIMING
-  PrepTimer pt;
+  PrepTimer pt("prep");
 #endif
   PT_DEV(s);
   const int n = F->n;

@@ -267,6 +267,16 @@ diaf_status diaf_set_device_memory_limit(int64_t bytes);
  * counts).  Never fails. */
 int64_t diaf_device_memory_in_use(void);
 
+/* The setup and apply paths allocate from a stream-ordered memory pool of
+ * the library's own (one per device) that keeps what they free, so that the
+ * next setup reuses it without mapping new pages; the pool therefore holds
+ * the high-water mark of the library's use.  This call returns the pool's
+ * unused memory on the current device to the driver (memory still held by
+ * live handles stays).  Call it with no setup or apply of the library in
+ * flight on that device.  (Resource control, no passage of the paper.)
+ * Errors: ECUDA. */
+diaf_status diaf_release_pool_memory(void);
+
 /* Borrowed device views of the outputs (valid until diaf_free): the W and V
  * of eq. afac (Sec. 2.3), column j of each from Sec. 2.1 / 2.2, and
  * res_j = ||A w_j - v_j||.  W: colptr/rowidx = copies of PW, vals nnz_w

@@ -229,6 +229,20 @@ diaf_status diaf_set_device_memory_limit(int64_t bytes) {
   return DIAF_OK;
 }
 
+diaf_status diaf_release_pool_memory(void) {
+  g_last_error.clear();
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e;
+  {
+    std::lock_guard<std::mutex> lock(g_mem_mu);
+    e = library_pool(&pool);
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "diaf_release_pool_memory");
+  return DIAF_OK;
+}
+
 int64_t diaf_device_memory_in_use(void) {
   std::lock_guard<std::mutex> lock(g_mem_mu);
   return static_cast<int64_t>(g_mem_total);

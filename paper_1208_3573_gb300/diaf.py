@@ -332,6 +332,11 @@ def device_memory_in_use() -> int:
     return int(lib().diaf_device_memory_in_use())
 
 
+def release_pool_memory() -> None:
+    """Returns the unused memory of the library's pool on the current device."""
+    _check(lib().diaf_release_pool_memory())
+
+
 def _args(A, PW, vrule, budget, Vfixed, tie_tol, stab=(0.0, 2.0), blocks=None):
     a = A.csc_t()
     pw = PW.pattern_t()

@@ -88,6 +88,11 @@ def test_device_memory_cap_gives_enomem(D):
     assert torch.isfinite(y).all()
     F.close()
     assert D.device_memory_in_use() == held
+    D.release_pool_memory()  # returns the pool's free memory; the next setup still works
+    F = run_gpu(D, w.A, w.PW, w.vrule, w.budget, alg="S", prec="mixed32")
+    F.sync()
+    F.close()
+    assert D.device_memory_in_use() == held
     with pytest.raises(D.DiafError):
         D.set_device_memory_limit(-1)
 

@@ -363,7 +363,7 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
   __syncwarp(qm);
   quad_qr(W, m, k, sub, qm);
   float kh = 0.0f;
-  bool zdiag = false;  // a zero column of A-hat: R-hat is singular and V cannot come from R0^-1 B
+  bool zdiag = false;  // R-hat singular (A-hat rank deficient): V is accumulated in the sweeps instead
 #pragma unroll
   for (int q = 0; q < KMAX; ++q)
     if (q < k) {
@@ -371,7 +371,7 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
       kh = fmaxf(kh, d > 0.0f ? ch[q] / d : (ch[q] > 0.0f ? INFINITY : 0.0f));
       zdiag |= d == 0.0f;
     }
-  if (!(kh <= kMixedKappaMax) || zdiag) { defer(); return; }
+  if (!(kh <= kMixedKappaMax)) { defer(); return; }
 
   // ---- R-hat to ld k at W[0, k^2) column by column (a column's new place
   DIAF_PHASE(6);
@@ -391,20 +391,21 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
       if (u < nk) dst[32 * u] = t4[u];
     __syncwarp(qm);
   }
-  const int VO = k * k;
+  const int VO = k * k;  // R0, or V = I when R-hat is singular
   for (int c = 0; c < k; ++c) {
     const float* src = qptr(W, c * k + sub);
     float* dst = qptr(W, VO + c * k + sub);
 #pragma unroll
     for (int u = 0; u < kQK; ++u)
-      if (u < nk) dst[32 * u] = src[32 * u];
+      if (u < nk) dst[32 * u] = zdiag ? (sub + 4 * u == c ? 1.0f : 0.0f) : src[32 * u];
   }
 
   // ---- one-sided Jacobi on R-hat in the warp kernels' round-robin order
   DIAF_PHASE(5);
   // (the rotations are applied to R-hat only: V is recovered afterwards from
   // R-hat V = B as R0^-1 B, which costs one triangular solve per column
-  // instead of a second pair of column updates per rotation)
+  // instead of a second pair of column updates per rotation; a singular
+  // R-hat has no R0^-1, and then V is accumulated in the rotations)
   // (in round rnd, position p >= 1 holds column 1 + ((p - 1 + rnd) mod L) and
   // positions p, qq - 1 - p pair up), with their rotation and stopping rules:
   // skip below tol = k eps_32, stop after a sweep without a rotation of
@@ -493,6 +494,17 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
                   ga[h][32 * u] = fmaf(-ssn, xb[h][u], cs * xa[h][u]);
                   gb[h][32 * u] = fmaf(scs, xb[h][u], sn * xa[h][u]);
                 }
+              if (zdiag) {  // V accumulated: R0^-1 B does not exist
+                float* va = qptr(W, VO + pa[h] * k + sub);
+                float* vb = qptr(W, VO + pb[h] * k + sub);
+#pragma unroll
+                for (int u = 0; u < kQK; ++u)
+                  if (u < nk) {
+                    const float xv = va[32 * u], yv = vb[32 * u];
+                    va[32 * u] = fmaf(-ssn, yv, cs * xv);
+                    vb[32 * u] = fmaf(scs, yv, sn * xv);
+                  }
+              }
               QS(W, NR + pa[h]) = al - t * ag;
               QS(W, NR + pb[h]) = be + t * ag;
             }
@@ -529,11 +541,11 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
       snext = fmin(snext, sv);
       gap = fmin(gap, sv * sv - smin * smin);
     }
-  // V = R0^-1 B in place of B: lane `sub` solves for the columns sub + 4v,
+  // V = R0^-1 B in place of B (R-hat regular): lane `sub` solves for the columns sub + 4v,
   // column-oriented back substitution (column jj of R0 read through four
   // pointers, element jj k + 4u + w at P[w][32 u])
   __syncwarp(qm);  // every lane has read B for the norms
-  for (int c = sub; c < k; c += 4) {
+  for (int c = zdiag ? k : sub; c < k; c += 4) {
     float bv[KMAX];
     const float* P0 = qptr(W, c * k);
     const float* P1 = qptr(W, c * k + 1);
@@ -584,7 +596,7 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
   double* X = D;  // x, element q
   const int zo = (M * K + 3) / 4 * 4;  // z, element r: slab element zo + r
   {
-    const float* vmin = qptr(W, imin * k + sub);
+    const float* vmin = qptr(W, (zdiag ? VO : 0) + imin * k + sub);
     double* xs = qptr(X, sub);
 #pragma unroll
     for (int u = 0; u < kQK; ++u)
@@ -634,7 +646,7 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
 #pragma unroll
     for (int u = 0; u < kQK; ++u) dxo[u] = 0.0f;
     for (int i = 0; i < k; ++i) {
-      const float* vi = qptr(W, i * k + sub);
+      const float* vi = qptr(W, (zdiag ? VO : 0) + i * k + sub);
       float vo[kQK];
       float vr = 0.0f;
 #pragma unroll

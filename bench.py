@@ -212,45 +212,20 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def learned_report(dev, keep=12, train_N=40, train_seeds=(11, 12), eval_N=64, epochs=20):
+def learned_report(dev, keep=12, train_N=40, train_seeds=(11, 12), eval_N=64, epochs=20, powers=(2, 3)):
     """The learned J_j proposal against the fixed sparsified-powers rule at
-    equal nnz(W): trained from scratch on the GPU (targets from FP64 solves
-    on train_N^3 instances), evaluated on the eval_N^3 lognormal operator with
-    candidates pattern(A^2) and V diagonal."""
+    equal nnz(W), on the eval_N^3 lognormal operator: one network per
+    candidate set pattern(A^p), trained from scratch on the GPU (targets from
+    FP64 solves with a diagonal V on train_N^3 instances of other seeds), and
+    every rule evaluated with a diagonal V and with the configuration's own
+    upper-triangular V: ||A W V^-1 - I||_F^2 (diagonal V), median scaled
+    column residual, setup time, BiCGSTAB to 1e-8 (iterations counted as
+    differing only when they differ by more than 2)."""
     import torch
     from paper_1208_3573_gb300 import diaf
     from paper_1208_3573_gb300.learned import Proposer, fixed_rule, host_pattern, toggle_targets, scaled_residuals
     from workloads import patterns as pats
     from workloads.configs import lognormal
-
-    def wl(N, seed):
-        w = lognormal(N, seed)
-        w.budget = np.ones(w.n, dtype=np.int32)
-        return w
-
-    t0 = time.perf_counter()
-    feats, targs = [], []
-    for seed in train_seeds:
-        w = wl(train_N, seed)
-        CAND = pats.pattern_power(w.A, 2)
-        Ad = diaf.DeviceCSC.from_host(w.A, dev)
-        T = toggle_targets(Ad, CAND, host_pattern(fixed_rule(Ad, keep)), torch.from_numpy(w.budget).to(dev),
-                           w.vrule, w.tie_tol)
-        feats.append(diaf.propose_features(Ad, diaf.DeviceCSC.from_host(CAND, dev)))
-        targs.append(T.value)
-    torch.cuda.synchronize()
-    t_targets = time.perf_counter() - t0
-    net = Proposer(seed=0, device=dev)
-    t0 = time.perf_counter()
-    hist = net.fit(feats, targs, epochs=epochs, batch=4096, lr=3e-3)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
-    w = wl(eval_N, 0)
-    Ad = diaf.DeviceCSC.from_host(w.A, dev)
-    CAND = diaf.DeviceCSC.from_host(pats.pattern_power(w.A, 2), dev)
-    bud = torch.from_numpy(w.budget).to(dev)
-    b = torch.from_numpy(w.b).to(dev)
-    S = diaf.Solver(Ad)
 
     def events(fn, reps=5):
         out, ts = None, []
@@ -260,30 +235,72 @@ def learned_report(dev, keep=12, train_N=40, train_seeds=(11, 12), eval_N=64, ep
             ts.append(e0.elapsed_time(e1))
         return out, statistics.median(ts)
 
-    J, propose_ms = events(lambda: net.propose(Ad, CAND, keep))
+    w = lognormal(eval_N, 0)
+    Ad = diaf.DeviceCSC.from_host(w.A, dev)
+    b = torch.from_numpy(w.b).to(dev)
+    S = diaf.Solver(Ad)
     FR, fixed_ms = events(lambda: fixed_rule(Ad, keep))
-    rules = {"learned": J, "fixed_sparsified_powers": FR}
-    out = {"workload": w.name, "V": "diagonal (l_j = 1)", "candidates": "pattern(A^2)", "keep": keep,
-           "train": {"instances": f"{train_N}^3 seeds {list(train_seeds)}", "targets_s": t_targets, "train_s": t_train,
-                     "rows": int(sum(np.isfinite(t).sum() for t in targs)), "loss_first": hist[0],
-                     "loss_last": hist[-1]},
-           "propose_ms": propose_ms, "fixed_rule_ms": fixed_ms}
-    for name, P in rules.items():
-        r = {"nnz_W": P.nnz}
-        for prec in ("mixed32", "fp64"):
-            F, ms = events(lambda: diaf.factor(Ad, P, w.vrule, bud, alg="S", prec=prec, tie_tol=w.tie_tol), 3)
-            r[f"factor_ms_{prec}"] = ms
-        sr = scaled_residuals(F)
-        r["fro2_AWVinv_minus_I"] = float(np.sum(sr ** 2))
-        r["colres_median"] = float(np.median(sr))
-        torch.cuda.synchronize()
+    rules = {"fixed_sparsified_powers": FR}
+    out = {"workload": w.name, "keep": keep, "fixed_rule_ms": fixed_ms, "train": {}}
+    for p in powers:
         t0 = time.perf_counter()
-        _, info = S.bicgstab(b, F, tol=1e-8, maxit=2000)
+        feats, targs = [], []
+        for seed in train_seeds:
+            wt = lognormal(train_N, seed)
+            ones = torch.ones(wt.n, dtype=torch.int32, device=dev)
+            CAND = pats.pattern_power(wt.A, p)
+            At = diaf.DeviceCSC.from_host(wt.A, dev)
+            T = toggle_targets(At, CAND, host_pattern(fixed_rule(At, keep)), ones, wt.vrule, wt.tie_tol)
+            feats.append(diaf.propose_features(At, diaf.DeviceCSC.from_host(CAND, dev)))
+            targs.append(T.value)
         torch.cuda.synchronize()
-        r.update(bicgstab_its=info.iterations, converged=bool(info.converged),
-                 solve_ms=1e3 * (time.perf_counter() - t0))
-        F.close()
-        out[name] = r
+        t_targets = time.perf_counter() - t0
+        net = Proposer(seed=0, device=dev)
+        t0 = time.perf_counter()
+        hist = net.fit(feats, targs, epochs=epochs, batch=4096, lr=3e-3)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        CANDe = diaf.DeviceCSC.from_host(pats.pattern_power(w.A, p), dev)
+        J, propose_ms = events(lambda: net.propose(Ad, CANDe, keep))
+        name = f"learned_A{p}"
+        rules[name] = J
+        out["train"][name] = {"candidates": f"pattern(A^{p}) (at most {int(torch.diff(CANDe.colptr).max())} "
+                                            f"per column)", "instances": f"{train_N}^3 seeds {list(train_seeds)}",
+                              "targets_s": t_targets, "train_s": t_train,
+                              "rows": int(sum(torch.isfinite(t).sum().item() for t in targs)),
+                              "loss_first": hist[0], "loss_last": hist[-1], "propose_ms": propose_ms}
+    for vname, budget in (("V_diagonal", np.ones(w.n, dtype=np.int32)), ("V_upper_config", w.budget)):
+        bud = torch.from_numpy(budget).to(dev)
+        res = {}
+        for name, P in rules.items():
+            r = {"nnz_W": P.nnz}
+            _, r["factor_ms_mixed32"] = events(lambda: diaf.factor(Ad, P, w.vrule, bud, alg="S", prec="mixed32",
+                                                                   tie_tol=w.tie_tol), 3)
+            F, r["factor_ms_fp64"] = events(lambda: diaf.factor(Ad, P, w.vrule, bud, alg="S", prec="fp64",
+                                                                tie_tol=w.tie_tol), 3)
+            sr = scaled_residuals(F)
+            if vname == "V_diagonal":
+                r["fro2_AWVinv_minus_I"] = float(np.sum(sr ** 2))
+            r["colres_median"] = float(np.median(sr))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            try:
+                _, info = S.bicgstab(b, F, tol=1e-8, maxit=2000)
+                torch.cuda.synchronize()
+                r.update(bicgstab_its=info.iterations, converged=bool(info.converged),
+                         breakdown=bool(info.breakdown), relres=float(info.relres),
+                         solve_ms=1e3 * (time.perf_counter() - t0))
+            except diaf.DiafError as e:  # e.g. a zero diagonal entry of V
+                r.update(bicgstab_its=None, converged=False, error=str(e)[:160])
+            F.close()
+            res[name] = r
+        f = res["fixed_sparsified_powers"]
+        for name in rules:
+            if name.startswith("learned") and f.get("converged") and res[name].get("converged"):
+                d = f["bicgstab_its"] - res[name]["bicgstab_its"]
+                res[name]["its_gain_vs_fixed"] = d
+                res[name]["gain_beyond_jitter"] = abs(d) > 2
+        out[vname] = res
     return out
 
 

@@ -407,8 +407,9 @@ diaf_status diaf_sparsified_fill(const diaf_csc* A, int32_t k, int32_t p_l, int3
 #define DIAF_PROP_NPARAM 1377
 
 /* (Not in the paper: the learned proposal.)  Features of every entry of CAND
- * (same n as A, sorted columns of at most 32 rows; DIAF_EUNSUPPORTED for a
- * longer column) into feat (device, [CAND->nnz][8]).  Synchronises `stream`.
+ * (same n as A, sorted columns of at most 128 rows -- pattern(A^3) of a
+ * 7-point stencil has 63; DIAF_EUNSUPPORTED for a longer column) into feat
+ * (device, [CAND->nnz][8]).  Synchronises `stream`.
  * Errors: EINVAL (NULL, sizes), EUNSUPPORTED, ECUDA. */
 diaf_status diaf_propose_features(const diaf_csc* A, const diaf_pattern* CAND, float* feat, void* stream);
 
@@ -435,9 +436,34 @@ diaf_status diaf_mlp_adam(float* params, const float* grad, float* m, float* v, 
  * of Sec. 4.)  Keeps, per column j, min(keep, |CAND(:,j)|) rows: j itself
  * when it is a candidate, then the best scores (ties to the lower row; NaN
  * ranks last).
- * colptr (n+1) and rowidx (at most n*keep) are written; rows come out sorted. */
+ * colptr (n+1) and rowidx (at most n*keep) are written; rows come out sorted.
+ * Columns of CAND hold at most 128 rows (DIAF_EUNSUPPORTED otherwise; the
+ * output is then incomplete).  Synchronises `stream`.  Errors: EINVAL (NULL,
+ * keep < 1), ENOMEM, EUNSUPPORTED, ECUDA. */
 diaf_status diaf_propose_select(const diaf_pattern* CAND, const float* score, int32_t keep, int32_t* colptr,
                                 int32_t* rowidx, void* stream);
+
+/* (Not in the paper: the training targets of the learned proposal.)
+ * out[j] = res_j / |V(j,j)| for the factors F (infinity where V(j,j) is zero
+ * or absent); with a diagonal V this is the norm of column j of
+ * A W V^-1 - I.  out: n device doubles.  Stream-ordered, allocates nothing.
+ * Errors: EINVAL (NULL), ECUDA. */
+diaf_status diaf_scaled_residuals(const diaf_factors* F, double* out, void* stream);
+
+/* (Not in the paper.)  Toggle targets of one candidate slot: for every
+ * column j whose CAND column has an entry e at position `slot` other than
+ * the diagonal, value[e] = L(rt_j) - L(r0_j) when in_base[e] != 0 (the
+ * candidate was dropped from the base pattern) and L(r0_j) - L(rt_j)
+ * otherwise (added), clipped to [-clip, clip], where r0 / rt are the scaled
+ * residuals (diaf_scaled_residuals) of the base and of the toggled pattern,
+ * L(r) = log(min(max(r^2, 1e-30 max(M, 1e-300)), 1e30 M)) with non-finite r
+ * counted as the upper end, and M the largest finite r0_j^2 (1 when none is
+ * positive).  Other entries of value are left as they are.  in_base:
+ * CAND->nnz device bytes; r0, rt: n device doubles; value: CAND->nnz device
+ * doubles.  Stream-ordered; allocates one scalar.  Errors: EINVAL (NULL,
+ * slot < 0, clip <= 0), ENOMEM, ECUDA. */
+diaf_status diaf_toggle_targets(const diaf_pattern* CAND, const uint8_t* in_base, const double* r0, const double* rt,
+                                int32_t slot, double clip, double* value, void* stream);
 
 /* Right-preconditioned restarted GMRES(restart) on A x = b (Sec. 5's solver
  * for the complex problems): x0 = 0, Arnoldi with classical Gram-Schmidt

@@ -6,11 +6,15 @@ float64 numpy, for the tests: the eight candidate features, the network
 8 -> 32 -> 32 -> 1 with ReLU, the gradient of the mean squared error by
 backpropagation written out per layer, one Adam step (Kingma & Ba,
 "Adam: a method for stochastic optimization", 2015, Algorithm 1) and the
-per-column top-k selection.  Shares no code with the CUDA library.
+per-column top-k selection, and the training targets (the scaled
+per-column residual and the clipped log-ratio of one toggled candidate
+slot).  Shares no code with the CUDA library.
 
 Pins (tests/test_oracle_learned.py): features of a hand-worked 1D stencil;
 gradients against central finite differences; Adam's first step against
-its closed form lr * g / (|g| + eps); selection against brute force.
+its closed form lr * g / (|g| + eps); selection against brute force; toggle
+targets of a hand-worked three-column example and their invariance under a
+common scaling of the residuals.
 """
 from __future__ import annotations
 
@@ -145,3 +149,41 @@ def select(CAND, score: np.ndarray, keep: int):
         rows_out.extend(kept)
         colptr.append(len(rows_out))
     return np.array(colptr, dtype=np.int32), np.array(rows_out, dtype=np.int32)
+
+
+def scaled_residuals(res: np.ndarray, Vcp: np.ndarray, Vri: np.ndarray, Vv: np.ndarray) -> np.ndarray:
+    """res_j / |V(j,j)| per column (inf when V(j,j) is zero or absent)."""
+    n = res.size
+    out = np.full(n, np.inf)
+    for j in range(n):
+        for p in range(Vcp[j], Vcp[j + 1]):
+            if Vri[p] == j and abs(Vv[p]) > 0:
+                out[j] = res[j] / abs(Vv[p])
+    return out
+
+
+def toggle_targets_slot(CAND, in_base: np.ndarray, r0: np.ndarray, rt: np.ndarray, slot: int, clip: float,
+                        value: np.ndarray) -> np.ndarray:
+    """Targets of candidate slot `slot`: for every column j whose candidate
+    list has an entry e at position `slot` other than j itself,
+      value[e] = +(L(rt_j) - L(r0_j))   if the candidate is in the base pattern
+      value[e] = -(L(rt_j) - L(r0_j))   otherwise,
+    clipped to [-clip, clip], with L(r) = log(min(max(r^2, lo), hi)) (hi for a
+    non-finite r^2), lo = 1e-30 max(M, 1e-300), hi = 1e30 M, M the largest
+    finite r0_j^2 (1 when none is positive).  Other entries are unchanged."""
+    sq = r0.astype(np.float64) ** 2
+    ok = np.isfinite(sq) & (sq > 0)
+    M = float(sq[ok].max()) if ok.any() else 1.0
+    lo, hi = max(M, 1e-300) * 1e-30, 1e30 * M
+
+    def L(r):
+        v = float(r) ** 2
+        return np.log(min(max(v, lo), hi)) if np.isfinite(v) else np.log(hi)
+
+    for j in range(CAND.n):
+        e = CAND.colptr[j] + slot
+        if e >= CAND.colptr[j + 1] or CAND.rowidx[e] == j:
+            continue
+        d = L(rt[j]) - L(r0[j])
+        value[e] = min(max(d if in_base[e] else -d, -clip), clip)
+    return value

@@ -17,7 +17,8 @@ constexpr int H = DIAF_PROP_HIDDEN;
 constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + H * F, OFF_W2 = OFF_B1 + H, OFF_B2 = OFF_W2 + H * H,
               OFF_W3 = OFF_B2 + H, OFF_B3 = OFF_W3 + H, NPARAM = OFF_B3 + 1;
 static_assert(NPARAM == DIAF_PROP_NPARAM, "parameter count");
-constexpr int kCandMax = 32;
+constexpr int kCandMax = 128;  // candidates of one column (e.g. pattern(A^3) of a 7-point stencil: 63)
+constexpr int kCandPerLane = kCandMax / 32;
 constexpr int kFeatWarps = 8;
 
 __device__ __forceinline__ int find_sorted(const int32_t* a, int n, int key) {
@@ -39,7 +40,8 @@ __device__ __forceinline__ double entry_abs(const int32_t* Acp, const int32_t* A
   return pos >= 0 ? sqrt((double)sc_abs2(Av[a0 + pos])) : 0.0;
 }
 
-// Features of candidate c of column j (one warp per column, one lane per candidate):
+// Features of candidate c of column j (one warp per column; lane l takes the
+// candidates l, l + 32, l + 64, l + 96):
 //   f0 diagonal (c == j)            f1 c is a row of A(:,j)
 //   f2 |A_cj| / max_i |A_ij|        f3 |(A^2)_cj| / max over candidates |(A^2)_c'j|
 //   f4 log(|a_cc| / |a_jj|) in [-10, 10]
@@ -60,22 +62,37 @@ __global__ void __launch_bounds__(kFeatWarps * 32)
     if (lane == 0) atomicOr(status, DEV_ST_CAPACITY);
     return;
   }
-  const int c = lane < nc ? Cri[c0 + lane] : -1;
-  if (__any_sync(DIAF_FULL, lane < nc && (c < 0 || c >= n))) {
+  int cl[kCandPerLane];
+  bool bad = false;
+#pragma unroll
+  for (int u = 0; u < kCandPerLane; ++u) {
+    const int i = lane + 32 * u;
+    cl[u] = i < nc ? Cri[c0 + i] : -1;
+    bad |= i < nc && (cl[u] < 0 || cl[u] >= n);
+  }
+  if (__any_sync(DIAF_FULL, bad)) {
     if (lane == 0) atomicOr(status, DEV_ST_BAD_INPUT);
     return;
   }
-  cand[wib][lane] = lane < nc ? c : INT_MAX;
-  acc[wib][lane] = sc_zero<S>();
+#pragma unroll
+  for (int u = 0; u < kCandPerLane; ++u) {
+    cand[wib][lane + 32 * u] = lane + 32 * u < nc ? cl[u] : INT_MAX;
+    acc[wib][lane + 32 * u] = sc_zero<S>();
+  }
   __syncwarp();
   const int a0 = Acp[j], na = Acp[j + 1] - a0;
-  double aj_max = 0.0, ajj = 0.0, acj = 0.0;
+  double aj_max = 0.0, ajj = 0.0;
+  double acj[kCandPerLane];
+#pragma unroll
+  for (int u = 0; u < kCandPerLane; ++u) acj[u] = 0.0;
   for (int p = 0; p < na; ++p) {
     const int r = Ari[a0 + p];
     const double v = sqrt((double)sc_abs2(Av[a0 + p]));
     aj_max = v > aj_max ? v : aj_max;
     if (r == j) ajj = v;
-    if (r == c) acj = v;
+#pragma unroll
+    for (int u = 0; u < kCandPerLane; ++u)
+      if (r == cl[u]) acj[u] = v;
   }
   // (A^2)(c, j) = sum_k A(c, k) A(k, j): rows within one column k are distinct,
   // so the lanes of one k update distinct slots
@@ -93,16 +110,27 @@ __global__ void __launch_bounds__(kFeatWarps * 32)
     }
     __syncwarp();
   }
-  const double a2c = lane < nc ? sqrt((double)sc_abs2(acc[wib][lane])) : 0.0;
-  const double a2max = warp_max(a2c);
-  if (lane < nc) {
+  double a2c[kCandPerLane];
+  double a2m = 0.0;
+#pragma unroll
+  for (int u = 0; u < kCandPerLane; ++u) {
+    const int i = lane + 32 * u;
+    a2c[u] = i < nc ? sqrt((double)sc_abs2(acc[wib][i])) : 0.0;
+    a2m = a2c[u] > a2m ? a2c[u] : a2m;
+  }
+  const double a2max = warp_max(a2m);
+#pragma unroll
+  for (int u = 0; u < kCandPerLane; ++u) {
+    const int i = lane + 32 * u;
+    if (i >= nc) continue;
+    const int c = cl[u];
     const double acc_diag = entry_abs(Acp, Ari, Av, c, c);
     const double ajc = entry_abs(Acp, Ari, Av, j, c);
-    float* f = feat + (size_t)(c0 + lane) * F;
+    float* f = feat + (size_t)(c0 + i) * F;
     f[0] = c == j ? 1.0f : 0.0f;
-    f[1] = acj > 0.0 ? 1.0f : 0.0f;
-    f[2] = aj_max > 0.0 ? (float)(acj / aj_max) : 0.0f;
-    f[3] = a2max > 0.0 ? (float)(a2c / a2max) : 0.0f;
+    f[1] = acj[u] > 0.0 ? 1.0f : 0.0f;
+    f[2] = aj_max > 0.0 ? (float)(acj[u] / aj_max) : 0.0f;
+    f[3] = a2max > 0.0 ? (float)(a2c[u] / a2max) : 0.0f;
     double lr = (acc_diag > 0.0 && ajj > 0.0) ? log(acc_diag / ajj) : 0.0;
     f[4] = (float)(lr > 10.0 ? 10.0 : (lr < -10.0 ? -10.0 : lr));
     f[5] = ajj > 0.0 ? (float)(ajc / ajj) : 0.0f;
@@ -269,36 +297,119 @@ __global__ void adam_kernel(float* __restrict__ params, const float* __restrict_
 }
 
 // ---------------------------------------------------------------- selection
-__global__ void keep_count_kernel(int n, const int32_t* Ccp, int keep, int32_t* cnt) {
+__global__ void keep_count_kernel(int n, const int32_t* Ccp, int keep, int32_t* cnt, uint32_t* status) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const int nc = Ccp[j + 1] - Ccp[j];
   cnt[j] = nc < keep ? nc : keep;
+  if (nc > kCandMax) atomicOr(status, DEV_ST_CAPACITY);
 }
 
 // Warp per column: the diagonal always, then the candidates by decreasing
-// score (ties to the lower row); the kept rows are written in increasing order.
-__global__ void select_kernel(int n, const int32_t* __restrict__ Ccp, const int32_t* __restrict__ Cri,
-                              const float* __restrict__ score, int keep, const int32_t* __restrict__ outcp,
-                              int32_t* __restrict__ outri) {
-  const int lane = threadIdx.x & 31;
-  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (j >= n) return;
+// score (ties to the lower row); the kept rows are written in increasing
+// order.  Lane l ranks the candidates l, l + 32, l + 64, l + 96 against all
+// of the column's candidates (staged in shared memory).
+constexpr int kSelWarps = 8;
+__global__ void __launch_bounds__(kSelWarps * 32)
+    select_kernel(int n, const int32_t* __restrict__ Ccp, const int32_t* __restrict__ Cri,
+                  const float* __restrict__ score, int keep, const int32_t* __restrict__ outcp,
+                  int32_t* __restrict__ outri) {
+  __shared__ int32_t sc_c[kSelWarps][kCandMax];
+  __shared__ float sc_s[kSelWarps][kCandMax];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int j = blockIdx.x * kSelWarps + wib;
+  if (j >= n) return;  // warp-uniform
   const int c0 = Ccp[j], nc = Ccp[j + 1] - c0;
-  const int c = lane < nc ? Cri[c0 + lane] : INT_MAX;
-  float sc = lane < nc ? score[c0 + lane] : -INFINITY;
-  if (c == j) sc = INFINITY;
-  if (!(sc == sc)) sc = -INFINITY;  // NaN scores rank last
-  int rank = 0;
-  for (int o = 0; o < 32; ++o) {
-    const float so = __shfl_sync(DIAF_FULL, sc, o);
-    const int co = __shfl_sync(DIAF_FULL, c, o);
-    if (o < nc && (so > sc || (so == sc && co < c))) ++rank;
+  if (nc > kCandMax) return;  // reported by keep_count_kernel
+  int cl[kCandPerLane];
+  float sl[kCandPerLane];
+#pragma unroll
+  for (int u = 0; u < kCandPerLane; ++u) {
+    const int i = lane + 32 * u;
+    cl[u] = i < nc ? Cri[c0 + i] : INT_MAX;
+    float sc = i < nc ? score[c0 + i] : -INFINITY;
+    if (cl[u] == j) sc = INFINITY;
+    if (!(sc == sc)) sc = -INFINITY;  // NaN scores rank last
+    sl[u] = sc;
+    sc_c[wib][i] = cl[u];
+    sc_s[wib][i] = sc;
   }
+  __syncwarp();
   const int kj = nc < keep ? nc : keep;
-  const bool kept = lane < nc && rank < kj;
-  const unsigned b = __ballot_sync(DIAF_FULL, kept);
-  if (kept) outri[outcp[j] + __popc(b & ((1u << lane) - 1u))] = c;
+  int before = 0;  // kept candidates in the slots of earlier rounds
+#pragma unroll
+  for (int u = 0; u < kCandPerLane; ++u) {
+    const int i = lane + 32 * u;
+    int rank = 0;
+    if (i < nc)
+      for (int o = 0; o < nc; ++o) {
+        const float so = sc_s[wib][o];
+        const int co = sc_c[wib][o];
+        if (so > sl[u] || (so == sl[u] && co < cl[u])) ++rank;
+      }
+    const bool kept = i < nc && rank < kj;
+    const unsigned b = __ballot_sync(DIAF_FULL, kept);
+    if (kept) outri[outcp[j] + before + __popc(b & ((1u << lane) - 1u))] = cl[u];
+    before += __popc(b);
+  }
+}
+
+// Per column: res_j / |V(j, j)| (infinity when V(j, j) is zero or absent).
+template <class S>
+__global__ void scaled_residuals_kernel(int n, const double* __restrict__ res, const int32_t* __restrict__ Vcp,
+                                        const int32_t* __restrict__ Vri, const S* __restrict__ Vv,
+                                        double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double d = 0.0;
+  for (int p = Vcp[j]; p < Vcp[j + 1]; ++p)
+    if (Vri[p] == j) d = sqrt((double)sc_abs2(Vv[p]));
+  out[j] = d > 0.0 ? res[j] / d : INFINITY;
+}
+
+// The largest finite r_j^2 (one block; atomicMax on the bits of a
+// non-negative double orders like the value).
+__global__ void max_finite_sq_kernel(int n, const double* __restrict__ r, unsigned long long* out) {
+  __shared__ double red[32];
+  double m = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double v = r[j] * r[j];
+    if (isfinite(v) && v > m) m = v;
+  }
+  m = warp_max(m);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    m = warp_max(m);
+    if (threadIdx.x == 0) *out = (unsigned long long)__double_as_longlong(m);
+  }
+}
+
+// Toggle target of candidate slot `slot` of every column (not the diagonal):
+// with L(r) = log(min(max(r^2, floor), cap)) (non-finite r counts as cap),
+// floor = 1e-30 max(M, 1e-300) and cap = 1e30 M for M the largest finite
+// r0^2 (1 when no r0_j^2 is finite and positive), the value is
+// L(rt_j) - L(r0_j) for a candidate in the base pattern (dropped) and
+// L(r0_j) - L(rt_j) otherwise (added), clipped to [-clip, clip].
+__global__ void toggle_targets_kernel(int n, const int32_t* __restrict__ Ccp, const int32_t* __restrict__ Cri,
+                                      const uint8_t* __restrict__ in_base, const double* __restrict__ r0,
+                                      const double* __restrict__ rt, int slot, double clip,
+                                      const unsigned long long* __restrict__ mbits, double* __restrict__ value) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int e = Ccp[j] + slot;
+  if (e >= Ccp[j + 1] || Cri[e] == j) return;
+  double M = __longlong_as_double((long long)*mbits);
+  if (!(M > 0.0)) M = 1.0;
+  const double lo = fmax(M, 1e-300) * 1e-30, hi = 1e30 * M;
+  auto L = [&](double r) {
+    const double v = r * r;
+    return log(isfinite(v) ? fmin(fmax(v, lo), hi) : hi);
+  };
+  const double d = L(rt[j]) - L(r0[j]);
+  const double t = in_base[e] ? d : -d;
+  value[e] = fmin(fmax(t, -clip), clip);
 }
 
 }  // namespace
@@ -333,7 +444,7 @@ diaf_status diaf_propose_features(const diaf_csc* A, const diaf_pattern* CAND, f
     return DIAF_EINVAL;
   }
   if (h & DEV_ST_CAPACITY) {
-    diaf_set_last_error("a column has more than 32 candidates");
+    diaf_set_last_error("a column has more than 128 candidates");
     return DIAF_EUNSUPPORTED;
   }
   return DIAF_OK;
@@ -389,15 +500,80 @@ diaf_status diaf_propose_select(const diaf_pattern* CAND, const float* d_score, 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (n == 0) return cudaMemsetAsync(d_colptr, 0, sizeof(int32_t), s) == cudaSuccess ? DIAF_OK : DIAF_ECUDA;
   int32_t *cnt = nullptr, *bs = nullptr;
+  uint32_t* st = nullptr;
   if (cudaMallocAsync(&cnt, sizeof(int32_t) * n, s) != cudaSuccess) return DIAF_ENOMEM;
-  if (cudaMallocAsync(&bs, sizeof(int32_t) * scan_blocksums_size(n), s) != cudaSuccess) return DIAF_ENOMEM;
-  keep_count_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, CAND->colptr, keep, cnt);
-  DIAF_COUNT_LAUNCH();
-  exclusive_scan_i32(cnt, d_colptr, n, bs, s);
-  select_kernel<<<ceil_div(n, 8), 256, 0, s>>>(n, CAND->colptr, CAND->rowidx, d_score, keep, d_colptr, d_rowidx);
-  DIAF_COUNT_LAUNCH();
+  if (cudaMallocAsync(&bs, sizeof(int32_t) * scan_blocksums_size(n), s) != cudaSuccess) {
+    cudaFreeAsync(cnt, s);
+    return DIAF_ENOMEM;
+  }
+  if (cudaMallocAsync(&st, sizeof(uint32_t), s) != cudaSuccess) {
+    cudaFreeAsync(cnt, s);
+    cudaFreeAsync(bs, s);
+    return DIAF_ENOMEM;
+  }
+  cudaError_t e = cudaMemsetAsync(st, 0, sizeof(uint32_t), s);
+  if (e == cudaSuccess) {
+    keep_count_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, CAND->colptr, keep, cnt, st);
+    DIAF_COUNT_LAUNCH();
+    e = exclusive_scan_i32(cnt, d_colptr, n, bs, s);
+  }
+  if (e == cudaSuccess) {
+    select_kernel<<<ceil_div(n, kSelWarps), kSelWarps * 32, 0, s>>>(n, CAND->colptr, CAND->rowidx, d_score, keep,
+                                                                     d_colptr, d_rowidx);
+    DIAF_COUNT_LAUNCH();
+    e = cudaGetLastError();
+  }
+  uint32_t h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, st, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
   cudaFreeAsync(cnt, s);
   cudaFreeAsync(bs, s);
+  cudaFreeAsync(st, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    diaf_set_last_error(cudaGetErrorString(e));
+    return DIAF_ECUDA;
+  }
+  if (h & DEV_ST_CAPACITY) {
+    diaf_set_last_error("a column has more than 128 candidates");
+    return DIAF_EUNSUPPORTED;
+  }
+  return DIAF_OK;
+}
+
+diaf_status diaf_scaled_residuals(const diaf_factors* F, double* d_out, void* stream) {
+  if (!F || (F->n > 0 && !d_out)) {
+    diaf_set_last_error("NULL argument");
+    return DIAF_EINVAL;
+  }
+  if (F->n == 0) return DIAF_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (F->dtype == DIAF_C128)
+    scaled_residuals_kernel<Cx<double>><<<ceil_div(F->n, 256), 256, 0, s>>>(F->n, F->res, F->Vcp, F->Vri,
+                                                                           (const Cx<double>*)F->Vv, d_out);
+  else
+    scaled_residuals_kernel<double><<<ceil_div(F->n, 256), 256, 0, s>>>(F->n, F->res, F->Vcp, F->Vri,
+                                                                       (const double*)F->Vv, d_out);
+  DIAF_COUNT_LAUNCH();
+  return cudaGetLastError() == cudaSuccess ? DIAF_OK : DIAF_ECUDA;
+}
+
+diaf_status diaf_toggle_targets(const diaf_pattern* CAND, const uint8_t* d_in_base, const double* d_r0,
+                                const double* d_rt, int32_t slot, double clip, double* d_value, void* stream) {
+  if (!CAND || slot < 0 || !(clip > 0.0) || (CAND->n > 0 && (!d_in_base || !d_r0 || !d_rt || !d_value))) {
+    diaf_set_last_error("NULL argument, negative slot or clip <= 0");
+    return DIAF_EINVAL;
+  }
+  const int n = CAND->n;
+  if (n == 0) return DIAF_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long* mbits = nullptr;
+  if (cudaMallocAsync(&mbits, sizeof(unsigned long long), s) != cudaSuccess) return DIAF_ENOMEM;
+  max_finite_sq_kernel<<<1, 1024, 0, s>>>(n, d_r0, mbits);
+  DIAF_COUNT_LAUNCH();
+  toggle_targets_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, CAND->colptr, CAND->rowidx, d_in_base, d_r0, d_rt, slot,
+                                                         clip, mbits, d_value);
+  DIAF_COUNT_LAUNCH();
+  cudaFreeAsync(mbits, s);
   return cudaGetLastError() == cudaSuccess ? DIAF_OK : DIAF_ECUDA;
 }
 

@@ -147,6 +147,10 @@ def lib() -> ctypes.CDLL:
         L.diaf_mlp_grad.argtypes = [vp, vp, vp, ctypes.c_int64, vp, vp, vp]
         L.diaf_mlp_adam.argtypes = [vp, vp, vp, vp, ctypes.c_int32, ctypes.c_float, vp]
         L.diaf_propose_select.argtypes = [ctypes.POINTER(Pattern_t), vp, ctypes.c_int32, vp, vp, vp]
+        L.diaf_scaled_residuals.argtypes = [vp, vp, vp]
+        L.diaf_toggle_targets.argtypes = [ctypes.POINTER(Pattern_t), vp, vp, vp, ctypes.c_int32, ctypes.c_double,
+                                          vp, vp]
+        L.diaf_release_pool_memory.argtypes = []
         L.diaf_sparsified_count.argtypes = [ctypes.POINTER(CSC_t), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                             vp, ctypes.POINTER(ctypes.c_int64), vp]
         L.diaf_sparsified_fill.argtypes = [ctypes.POINTER(CSC_t), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -490,6 +494,23 @@ def propose_select(CAND: DeviceCSC, score: torch.Tensor, keep: int, stream=None)
                                      _stream(stream)))
     nnz = int(colptr[-1].item())
     return DeviceCSC(CAND.n, colptr, rowidx[:nnz].clone())
+
+
+def scaled_residuals(F: "Factors", stream=None) -> torch.Tensor:
+    """res_j / |V(j,j)| per column on the device (diaf_scaled_residuals)."""
+    out = torch.empty(F.n, dtype=torch.float64, device=F.res.device)
+    _check(lib().diaf_scaled_residuals(F._own.ptr, _ptr(out), _stream(stream)))
+    return out
+
+
+def toggle_targets(CAND: DeviceCSC, in_base: torch.Tensor, r0: torch.Tensor, rt: torch.Tensor, slot: int,
+                   clip: float, value: torch.Tensor, stream=None) -> torch.Tensor:
+    """Writes the toggle targets of candidate slot `slot` into value (diaf_toggle_targets)."""
+    assert in_base.dtype == torch.uint8 and r0.dtype == rt.dtype == value.dtype == torch.float64
+    c = CAND.pattern_t()
+    _check(lib().diaf_toggle_targets(ctypes.byref(c), _ptr(in_base), _ptr(r0), _ptr(rt), int(slot), float(clip),
+                                     _ptr(value), _stream(stream)))
+    return value
 
 
 def sparsified_powers(A: DeviceCSC, k: int = 2, p_l: int = 0, keep: int = 0, stream=None) -> DeviceCSC:

@@ -6,8 +6,9 @@ fallback.  Here a network scores every candidate row of a candidate pattern
 CAND(:,j) -- pattern(A^2) for the 7-point operators -- and the diagonal plus
 the best-scored candidates form J_j.  Every computation runs in libdiaf.so:
 features (diaf_propose_features), scores (diaf_mlp_forward), the kept
-pattern (diaf_propose_select), and the training step (diaf_mlp_grad,
-diaf_mlp_adam).  This module only arranges the calls.
+pattern (diaf_propose_select), the training targets (diaf_scaled_residuals,
+diaf_toggle_targets) and the training step (diaf_mlp_grad, diaf_mlp_adam).
+This module only arranges the calls and builds the toggled patterns.
 
 Training targets come from the exact columnwise solve itself.  Around a base
 pattern J0 (by default the fixed rule at the same size), candidate c of
@@ -73,22 +74,16 @@ def fixed_rule(A_dev: diaf.DeviceCSC, keep: int, k: int = 2) -> diaf.DeviceCSC:
 class Targets:
     """Per-candidate training targets of one instance (CAND's entry order)."""
 
-    value: np.ndarray    # float64 [CAND.nnz]; NaN on the diagonal (always kept, not trained)
-    in_base: np.ndarray  # bool [CAND.nnz]
-    res_base: np.ndarray  # per-column residual of J0
+    value: torch.Tensor   # float64 [CAND.nnz] on the device; NaN on the diagonal (always kept, not trained)
+    in_base: np.ndarray   # bool [CAND.nnz]
+    res_base: torch.Tensor  # per-column scaled residual of J0 (device)
 
 
 def scaled_residuals(F: diaf.Factors) -> np.ndarray:
-    """Per column ||A w_j - v_j|| / |v_jj| (host copy; inf where v_jj = 0).
-    With a diagonal V this is the norm of column j of A W V^-1 - I."""
-    res = F.res.cpu().numpy().astype(np.float64)
-    cp, ri, vv = (t.cpu().numpy() for t in (F.V.colptr, F.V.rowidx, F.V.vals))
-    col = np.repeat(np.arange(F.n), np.diff(cp))
-    d = np.zeros(F.n)
-    on = ri == col
-    d[col[on]] = np.abs(vv[on])
-    with np.errstate(divide="ignore", invalid="ignore"):
-        return np.where(d > 0, res / np.where(d > 0, d, 1.0), np.inf)
+    """Per column ||A w_j - v_j|| / |v_jj| (diaf_scaled_residuals; host copy,
+    inf where v_jj = 0).  With a diagonal V this is the norm of column j of
+    A W V^-1 - I."""
+    return diaf.scaled_residuals(F).cpu().numpy()
 
 
 def toggle_targets(A_dev: diaf.DeviceCSC, CAND, base, budget: torch.Tensor, vrule: int = diaf.RULE_UPPER,
@@ -97,7 +92,9 @@ def toggle_targets(A_dev: diaf.DeviceCSC, CAND, base, budget: torch.Tensor, vrul
     `base` (host Patterns CAND, base with base within CAND).  One FP64
     factorisation per slot, all columns at once; the per-column measure is
     ||A w_j - v_j|| / |v_jj| (scale-free: the column of A W V^-1 - I when V is
-    diagonal)."""
+    diagonal).  The measure, the log-ratio and the clip run on the device
+    (diaf_scaled_residuals, diaf_toggle_targets); the host only builds the
+    toggled patterns."""
     dev = A_dev.colptr.device
     n = CAND.n
     ck = _entry_keys(n, CAND.colptr, CAND.rowidx)
@@ -108,31 +105,22 @@ def toggle_targets(A_dev: diaf.DeviceCSC, CAND, base, budget: torch.Tensor, vrul
     col = np.repeat(np.arange(n), np.diff(CAND.colptr))
     slot = np.arange(CAND.nnz) - CAND.colptr[col]
     diag = CAND.rowidx == col
+    CAND_dev = diaf.DeviceCSC.from_host(CAND, dev)
+    in_base_dev = torch.from_numpy(in_base.astype(np.uint8)).to(dev)
 
     def residual(mask):
         F = diaf.factor(A_dev, _subpattern(CAND, mask, dev), vrule, budget, alg=alg, prec="fp64", tie_tol=tie_tol)
-        r = scaled_residuals(F)
+        r = diaf.scaled_residuals(F)
         F.close()
         return r
 
     r0 = residual(in_base)
-    fin = r0[np.isfinite(r0)]
-    floor = max(float(np.max(fin ** 2)) if fin.size else 1.0, 1e-300) * 1e-30
-    cap = 1e30 * (float(np.max(fin ** 2)) if fin.size else 1.0)
-
-    def logr2(r):
-        return np.log(np.clip(np.where(np.isfinite(r), r ** 2, cap), floor, cap))
-
-    l0 = logr2(r0)
-    value = np.full(CAND.nnz, np.nan)
+    value = torch.full((CAND.nnz,), float("nan"), dtype=torch.float64, device=dev)
     for t in range(int(slot.max()) + 1 if CAND.nnz else 0):
         tog = (slot == t) & ~diag
         if not tog.any():
             continue
-        lt = logr2(residual(in_base ^ tog))
-        d = (lt - l0)[col[tog]]
-        value[tog] = np.where(in_base[tog], d, -d)
-    value = np.clip(value, -clip, clip)
+        diaf.toggle_targets(CAND_dev, in_base_dev, r0, residual(in_base ^ tog), t, clip, value)
     return Targets(value, in_base, r0)
 
 
@@ -158,15 +146,17 @@ class Proposer:
         return diaf.propose_select(CAND_dev, self.scores(A_dev, CAND_dev), keep)
 
     # -- training
-    def fit(self, feats: list[torch.Tensor], targets: list[np.ndarray], epochs: int = 30, batch: int = 8192,
+    def fit(self, feats: list[torch.Tensor], targets: list, epochs: int = 30, batch: int = 8192,
             lr: float = 3e-3, seed: int = 0) -> list[float]:
         """Adam on the mean squared error over the rows with a finite target
-        (targets are rescaled to unit standard deviation; the ranking is
-        unchanged).  Returns the mean training loss of every epoch."""
-        X = torch.cat([f[torch.from_numpy(np.isfinite(t)).to(f.device)] for f, t in zip(feats, targets)])
-        y = np.concatenate([t[np.isfinite(t)] for t in targets])
-        self.target_scale = float(np.std(y)) or 1.0
-        Y = torch.from_numpy((y / self.target_scale).astype(np.float32)).to(X.device)
+        (targets -- device tensors or arrays -- are rescaled to unit standard
+        deviation; the ranking is unchanged).  Returns the mean training loss
+        of every epoch."""
+        ts = [torch.as_tensor(t, dtype=torch.float64).to(f.device) for f, t in zip(feats, targets)]
+        X = torch.cat([f[torch.isfinite(t)] for f, t in zip(feats, ts)])
+        y = torch.cat([t[torch.isfinite(t)] for t in ts])
+        self.target_scale = float(y.std(correction=0).item()) or 1.0
+        Y = (y / self.target_scale).to(torch.float32)
         N = X.shape[0]
         g = np.random.default_rng(seed)
         grad = torch.empty(NPARAM, dtype=torch.float32, device=X.device)

@@ -1,6 +1,8 @@
-"""Learned W-pattern proposal on the GPU: features, forward, gradient, Adam
-and selection against the numpy oracle, and what the trained network gains
-over the fixed sparsified-powers rule (Sec. 4.1) at the same nnz(W)."""
+"""Learned W-pattern proposal on the GPU: features (up to 128 candidates per
+column, pattern(A^3) included), forward, gradient, Adam, selection and the
+training targets (scaled residuals, toggle log-ratios) against the numpy
+oracle, and what the trained network gains over the fixed sparsified-powers
+rule (Sec. 4.1) at the same nnz(W)."""
 import numpy as np
 import pytest
 
@@ -33,27 +35,37 @@ def _feat(seed, n):
     return X.astype(np.float32)
 
 
-@pytest.mark.parametrize("case", ["lognormal8", "helmholtz12", "convdiff16_A2"])
+@pytest.mark.parametrize("case", ["lognormal8", "helmholtz12", "convdiff16_A2", "lognormal8_A3"])
 def test_features_match_oracle(D, case):
-    if case == "lognormal8":
+    if case.startswith("lognormal8"):
         A = ops.lognormal3d(8, seed=3)
     elif case == "helmholtz12":
         A = ops.helmholtz2d(12, ops.helmholtz_wavenumber(12))
     else:
         A = ops.convdiff2d(16)
-    CAND = pats.pattern_power(A, 2)
+    CAND = pats.pattern_power(A, 3 if case.endswith("A3") else 2)
+    if case.endswith("A3"):
+        assert np.diff(CAND.colptr).max() == 63  # beyond one candidate per lane
     f = D.propose_features(D.DeviceCSC.from_host(A), D.DeviceCSC.from_host(CAND)).cpu().numpy()
     o = OL.features(A, CAND)
     # computed in FP64 on the device, rounded once to FP32
     np.testing.assert_allclose(f, o.astype(np.float32), rtol=2e-7, atol=1e-7)
 
 
-def test_features_reject_long_columns_and_bad_rows(D):
+def test_features_and_select_reject_long_columns_and_bad_rows(D):
+    A = ops.lognormal3d(10, seed=0)
+    Ad = D.DeviceCSC.from_host(A)
+    C4 = pats.pattern_power(A, 4)
+    assert np.diff(C4.colptr).max() == 129  # one more than the kernels hold
+    C4d = D.DeviceCSC.from_host(C4)
+    with pytest.raises(D.DiafError) as e:
+        D.propose_features(Ad, C4d)
+    assert e.value.status == D.DIAF_EUNSUPPORTED
+    with pytest.raises(D.DiafError) as e:
+        D.propose_select(C4d, torch.zeros(C4.nnz, dtype=torch.float32, device="cuda"), 12)
+    assert e.value.status == D.DIAF_EUNSUPPORTED
     A = ops.lognormal3d(6, seed=0)
     Ad = D.DeviceCSC.from_host(A)
-    with pytest.raises(D.DiafError) as e:
-        D.propose_features(Ad, D.DeviceCSC.from_host(pats.pattern_power(A, 3)))  # up to 63 candidates
-    assert e.value.status == D.DIAF_EUNSUPPORTED
     P = pats.pattern_of(A)
     bad = P.rowidx.copy()
     bad[-1] = A.n  # out of range
@@ -130,10 +142,10 @@ def test_training_steps_match_oracle(D):
     assert d.max() <= 10 * 2 * 1e-3 + 1e-6
 
 
-@pytest.mark.parametrize("keep", [1, 5, 12, 40])
-def test_select_matches_oracle(D, keep):
+@pytest.mark.parametrize("keep,power", [(1, 2), (5, 2), (12, 2), (40, 2), (12, 3), (40, 3), (70, 3)])
+def test_select_matches_oracle(D, keep, power):
     A = ops.lognormal3d(8, seed=1)
-    CAND = pats.pattern_power(A, 2)
+    CAND = pats.pattern_power(A, power)
     rng = np.random.default_rng(9)
     score = rng.normal(0, 1, CAND.nnz).astype(np.float32)
     score[rng.random(CAND.nnz) < 0.1] = 0.5  # ties
@@ -143,6 +155,45 @@ def test_select_matches_oracle(D, keep):
     cp, ri = OL.select(CAND, score.astype(np.float64), keep)
     np.testing.assert_array_equal(J.colptr.cpu().numpy(), cp)
     np.testing.assert_array_equal(J.rowidx.cpu().numpy(), ri)
+
+
+@pytest.mark.parametrize("diagonal_v", [True, False])
+def test_scaled_residuals_match_oracle(D, diagonal_v):
+    w = lognormal(8, 3)
+    if diagonal_v:
+        w.budget = np.ones(w.n, dtype=np.int32)
+    F = D.factor(D.DeviceCSC.from_host(w.A), D.DeviceCSC.from_host(w.PW), w.vrule,
+                 torch.from_numpy(w.budget).cuda(), alg="S", prec="fp64", tie_tol=w.tie_tol)
+    got = D.scaled_residuals(F).cpu().numpy()
+    ref = OL.scaled_residuals(F.res.cpu().numpy(), F.V.colptr.cpu().numpy(), F.V.rowidx.cpu().numpy(),
+                              F.V.vals.cpu().numpy())
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_toggle_targets_match_oracle(D):
+    A = ops.lognormal3d(8, seed=5)
+    CAND = pats.pattern_power(A, 2)
+    g = np.random.default_rng(6)
+    in_base = g.random(CAND.nnz) < 0.5
+    r0 = g.lognormal(0, 2, A.n)
+    rt = r0 * g.lognormal(0, 1, A.n)
+    r0[g.random(A.n) < 0.02] = np.inf   # v_jj = 0 in the base
+    rt[g.random(A.n) < 0.02] = np.inf
+    rt[g.random(A.n) < 0.02] = 0.0      # an exact fit after the toggle
+    rt[g.random(A.n) < 0.01] = np.nan
+    Cd = D.DeviceCSC.from_host(CAND)
+    ib = torch.from_numpy(in_base.astype(np.uint8)).cuda()
+    r0d, rtd = torch.from_numpy(r0).cuda(), torch.from_numpy(rt).cuda()
+    val = torch.full((CAND.nnz,), float("nan"), dtype=torch.float64, device="cuda")
+    ref = np.full(CAND.nnz, np.nan)
+    for slot in range(int(np.diff(CAND.colptr).max())):
+        D.toggle_targets(Cd, ib, r0d, rtd, slot, 8.0, val)
+        OL.toggle_targets_slot(CAND, in_base, r0, rt, slot, 8.0, ref)
+    got = val.cpu().numpy()
+    assert np.array_equal(np.isnan(got), np.isnan(ref))
+    ok = ~np.isnan(ref)
+    np.testing.assert_allclose(got[ok], ref[ok], rtol=1e-13, atol=1e-13)
+    assert np.abs(got[ok]).max() == 8.0  # the clip is reached
 
 
 def _lognormal_diagV(N, seed):
@@ -181,7 +232,8 @@ def test_trained_network_beats_fixed_rule(D, alg):
         Ad = D.DeviceCSC.from_host(w.A)
         base = host_pattern(fixed_rule(Ad, keep))
         T = toggle_targets(Ad, CAND, base, torch.from_numpy(w.budget).cuda(), w.vrule, w.tie_tol, alg=alg)
-        assert np.mean(T.value[T.in_base & np.isfinite(T.value)] > 0) > 0.9  # dropping a kept row costs
+        tv = T.value.cpu().numpy()
+        assert np.mean(tv[T.in_base & np.isfinite(tv)] > 0) > 0.9  # dropping a kept row costs
         feats.append(D.propose_features(Ad, D.DeviceCSC.from_host(CAND)))
         targs.append(T.value)
     net = Proposer(seed=0)

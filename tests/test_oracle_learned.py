@@ -175,3 +175,54 @@ def test_sparsified_powers_matches_dense_series():
     for j in range(30):
         want = np.nonzero(np.abs(Wd[:, j]) > 1e-14)[0]
         assert list(P.col(j)) == list(want)
+
+
+def test_toggle_targets_hand_worked():
+    # three columns, candidates {0,1}, {0,1,2}, {1,2}; slot 1 toggles (0,1)->row 1,
+    # (1,1)->row 1 is the diagonal (skipped), (2,1)->row 2 is the diagonal (skipped);
+    # slot 0 toggles row 0 of column 1 and row 1 of column 2
+    CAND = Pattern(3, np.array([0, 2, 5, 7], dtype=np.int32), np.array([0, 1, 0, 1, 2, 1, 2], dtype=np.int32))
+    in_base = np.array([1, 1, 0, 1, 1, 1, 1], dtype=bool)
+    r0 = np.array([1.0, 2.0, np.inf])  # M = 4: lo = 4e-30, hi = 4e30
+    rt = np.array([2.0, 1.0, 3.0])
+    v = np.full(7, np.nan)
+    L.toggle_targets_slot(CAND, in_base, r0, rt, 1, 8.0, v)
+    # column 0, row 1 (in the base): dropping it doubled the residual: +log 4
+    assert v[1] == pytest.approx(np.log(4.0), rel=1e-15)
+    assert np.isnan(v[[0, 2, 3, 4, 5, 6]]).all()
+    L.toggle_targets_slot(CAND, in_base, r0, rt, 0, 8.0, v)
+    # column 1, row 0 (not in the base): adding it halved the residual: +log 4
+    assert v[2] == pytest.approx(np.log(4.0), rel=1e-15)
+    # column 2, row 1 (in the base): r0 = inf counts as hi = 4e30, rt = 3:
+    # log 9 - log 4e30 = -67.9..., clipped to -8
+    assert v[5] == -8.0
+    assert np.isnan(v[[0, 3, 4, 6]]).all()
+    # column 0 slot 0 is the diagonal: untouched
+    assert np.isnan(v[0])
+
+
+def test_toggle_targets_scale_invariant():
+    from workloads import operators as ops
+    A = ops.lognormal3d(5, seed=2)
+    CAND = pats.pattern_power(A, 2)
+    g = np.random.default_rng(4)
+    in_base = g.random(CAND.nnz) < 0.5
+    r0 = g.lognormal(0, 1, A.n)
+    rt = r0 * g.lognormal(0, 0.5, A.n)
+    for slot in range(6):
+        v1 = L.toggle_targets_slot(CAND, in_base, r0, rt, slot, 8.0, np.full(CAND.nnz, np.nan))
+        v2 = L.toggle_targets_slot(CAND, in_base, 1e3 * r0, 1e3 * rt, slot, 8.0, np.full(CAND.nnz, np.nan))
+        np.testing.assert_allclose(v1, v2, rtol=1e-12, atol=1e-12)
+        e = CAND.colptr[:-1] + slot
+        ok = (e < CAND.colptr[1:])
+        ok[ok] &= CAND.rowidx[e[ok]] != np.arange(A.n)[ok]
+        assert np.isfinite(v1[e[ok]]).all() and (np.abs(v1[e[ok]]) <= 8.0).all()
+
+
+def test_scaled_residuals_definition():
+    res = np.array([1.0, 2.0, 3.0])
+    Vcp = np.array([0, 1, 3, 4])
+    Vri = np.array([0, 0, 1, 0])
+    Vv = np.array([-2.0, 5.0, 4.0, 7.0])
+    out = L.scaled_residuals(res, Vcp, Vri, Vv)
+    assert out[0] == 0.5 and out[1] == 0.5 and out[2] == np.inf  # column 2 has no diagonal entry

@@ -329,9 +329,10 @@ def kv_sweep(w, A, PW, alg, prec, dev, budgets=(1, 2, 3, 4, 6, 8, 13)):
             _, info = S.bicgstab(b, F, tol=1e-8, maxit=1000)
             torch.cuda.synchronize()
             row.update(bicgstab_its=info.iterations, converged=bool(info.converged),
+                       breakdown=bool(info.breakdown), relres=float(info.relres),
                        solve_ms=1e3 * (time.perf_counter() - t0))
-        except diaf.DiafError as e:
-            row["solve"] = str(e)[:80]
+        except diaf.DiafError as e:  # no solve: V has a zero or missing diagonal entry
+            row.update(converged=False, solve=str(e)[:80])
         F.close()
         return row
 

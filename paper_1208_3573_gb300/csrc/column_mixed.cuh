@@ -61,9 +61,15 @@ struct MixedLayout {
   // Householder QR with the tile in registers (one row per lane): tiles of
   // up to 32 rows and 16 columns
   static constexpr bool kRegQR = KMAX <= 16 && MMAX <= 32;
+  // DIAF-S keeps the Jacobi's V in the working tile, which is dead once
+  // R-hat has been copied out of it (kTile >= KP KMAX since MMAX >= KMAX):
+  // one k x k factor less per warp (real 32-column tiles: 10 -> 12 warps
+  // per SM)
+  static constexpr int kFactors = ALG == DIAF_ALG_S ? 1 : 2;
+  static_assert(MMAX >= KMAX, "the working tile holds V");
   static constexpr size_t raw() {
     return sizeof(SD) * (3 * KMAX + 2 * MMAX + kRR * KP + 2 * kRR * kRR) +
-           sizeof(S) * (kTile + 2 * KP * KMAX + KMAX) +
+           sizeof(S) * (kTile + kFactors * KP * KMAX + KMAX) +
            sizeof(double) * (MMAX + 2 * KMAX) + idx_bytes<KMAX, MMAX>();
   }
   static constexpr size_t bytes() { return (raw() + 15) / 16 * 16; }
@@ -105,8 +111,8 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
   SD* Ms = Cs + kRR * kRR;               // DIAF-Q scratch: r = C v - mu v (as FP32)
   S* Tw = reinterpret_cast<S*>(Ms + kRR * kRR);  // FP32 working tile
   S* Rs = Tw + L::kTile;                 // FP32 R of T, then R-hat (Jacobi works on it)
-  S* Vj = Rs + KP * KMAX;                // FP32 Jacobi V
-  S* rinv = Vj + KP * KMAX;              // FP32 reciprocal diagonal
+  S* Vj = ALG == DIAF_ALG_S ? Tw : Rs + KP * KMAX;  // FP32 Jacobi V (DIAF-S: over the dead working tile)
+  S* rinv = Rs + L::kFactors * KP * KMAX;  // FP32 reciprocal diagonal
   float* hk = reinterpret_cast<float*>(rinv + KMAX);  // FP32 keys (MMAX; 2 MMAX floats reserved)
   double* sig = reinterpret_cast<double*>(hk + 2 * MMAX);
   R* sg = reinterpret_cast<R*>(sig);     // singular values / column norms in the FP32 type (KMAX)

@@ -58,6 +58,14 @@ struct MixedLayout {
   // slab holds the tile and two tiles of scratch for the FP64 keys of the
   // columns whose FP32 keys cannot decide.
   static constexpr size_t tile_bytes() { return 3 * sizeof(SD) * kTile; }
+  // The FP64 keys of the columns whose FP32 keys cannot decide: in shared
+  // memory (over the FP32 keys, which then take 2 MMAX floats), except for
+  // the real 32-column tiles, where shared memory sets the warps per SM and
+  // such columns are few: there they go to the slab after the FP64 R
+  // (12 -> 13 warps per SM).  On the symmetric Helmholtz tiles, where many
+  // columns take this path, the slab's latency cost 11 %.
+  static constexpr bool kKeysInSlab = KMAX > 16 && !ScalarInfo<S>::cplx;
+  static_assert(KP * KMAX * sizeof(SD) + MMAX * sizeof(double) <= kTile * sizeof(SD), "FP64 keys after R in the slab");
   // Householder QR with the tile in registers (one row per lane): tiles of
   // up to 32 rows and 16 columns
   static constexpr bool kRegQR = KMAX <= 16 && MMAX <= 32;
@@ -69,8 +77,8 @@ struct MixedLayout {
   static_assert(MMAX >= KMAX, "the working tile holds V");
   static constexpr size_t raw() {
     return sizeof(SD) * (3 * KMAX + 2 * MMAX + kRR * KP + 2 * kRR * kRR) +
-           sizeof(S) * (kTile + kFactors * KP * KMAX + KMAX) +
-           sizeof(double) * (MMAX + 2 * KMAX) + idx_bytes<KMAX, MMAX>();
+           sizeof(S) * (kTile + kFactors * KP * KMAX + KMAX) + sizeof(float) * MMAX * (kKeysInSlab ? 1 : 2) +
+           sizeof(double) * (2 * KMAX) + idx_bytes<KMAX, MMAX>();
   }
   static constexpr size_t bytes() { return (raw() + 15) / 16 * 16; }
 };
@@ -113,8 +121,8 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
   S* Rs = Tw + L::kTile;                 // FP32 R of T, then R-hat (Jacobi works on it)
   S* Vj = ALG == DIAF_ALG_S ? Tw : Rs + KP * KMAX;  // FP32 Jacobi V (DIAF-S: over the dead working tile)
   S* rinv = Rs + L::kFactors * KP * KMAX;  // FP32 reciprocal diagonal
-  float* hk = reinterpret_cast<float*>(rinv + KMAX);  // FP32 keys (MMAX; 2 MMAX floats reserved)
-  double* sig = reinterpret_cast<double*>(hk + 2 * MMAX);
+  float* hk = reinterpret_cast<float*>(rinv + KMAX);  // FP32 keys (MMAX; 2 MMAX floats unless kKeysInSlab)
+  double* sig = reinterpret_cast<double*>(hk + MMAX * (L::kKeysInSlab ? 1 : 2));
   R* sg = reinterpret_cast<R*>(sig);     // singular values / column norms in the FP32 type (KMAX)
   double* cn = sig + KMAX;               // column norms of the tile
   ColumnIdx ix = carve_idx<KMAX, MMAX>(reinterpret_cast<int32_t*>(cn + KMAX));
@@ -192,7 +200,8 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
       // the FP64 kernel's choice; the rest of the column stays mixed
       SD* Tq = Tx;             // QR workspace, then the FP64 rows of Q (LDT x KMAX)
       SD* Rq = Tx + L::kTile;  // the FP64 R (KP x KMAX)
-      double* hd = reinterpret_cast<double*>(hk);  // FP64 keys (the 2 MMAX floats reserved)
+      double* hd = L::kKeysInSlab ? reinterpret_cast<double*>(Rq + KP * KMAX)  // FP64 keys (MMAX)
+                                  : reinterpret_cast<double*>(hk);
       for (int i = lane; i < me * k; i += DIAF_WARP) Tq[(i % me) + (i / me) * LDT] = Ts[(i % me) + (i / me) * LDT];
       __syncwarp();
       warp_householder_qr_rs<SD, LDT, KMAX, MMAX / DIAF_WARP>(Tq, me, k, lane);

@@ -62,8 +62,8 @@ struct MixedLayout {
   // memory (over the FP32 keys, which then take 2 MMAX floats), except for
   // the real 32-column tiles, where shared memory sets the warps per SM and
   // such columns are few: there they go to the slab after the FP64 R
-  // (12 -> 13 warps per SM).  On the symmetric Helmholtz tiles, where many
-  // columns take this path, the slab's latency cost 11 %.
+  // (12 -> 13 warps per SM).  On the complex Helmholtz tiles the slab
+  // placement measured 11 % slower, so it is limited to the real wide ones.
   static constexpr bool kKeysInSlab = KMAX > 16 && !ScalarInfo<S>::cplx;
   static_assert(KP * KMAX * sizeof(SD) + MMAX * sizeof(double) <= kTile * sizeof(SD), "FP64 keys after R in the slab");
   // Householder QR with the tile in registers (one row per lane): tiles of

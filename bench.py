@@ -503,6 +503,7 @@ def main():
     h2d = sum(t.numel() * t.element_size() for t in hA + hP + [hB])
     e2e_ms = []
     d2h = 0
+    host = None  # pinned output buffers, allocated in the untimed first pass and reused
     for i in range(max(1, args.steps // 2) + 1):
         flush.zero_()
         torch.cuda.synchronize()
@@ -513,7 +514,8 @@ def main():
         budd = hB.to(dev, non_blocking=True)
         F = step(Ad, PWd, budd)
         outs = [F.W.vals, F.V.colptr, F.V.rowidx, F.V.vals, F.res]
-        host = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs]
+        if host is None or any(h.shape != o.shape or h.dtype != o.dtype for h, o in zip(host, outs)):
+            host = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs]
         for h, o in zip(host, outs):
             h.copy_(o, non_blocking=True)
         s1.record(stream)

@@ -976,6 +976,23 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   if (ce == cudaSuccess) ce = F->alloc((char**)&F->Wr.vals, esz * F->nnz_w);
   if (ce == cudaSuccess)
     ce = csc_to_csr(n, F->nnz_w, F->Wcp, F->Wri, F->Wv, cplx, F->Wr.rowptr, F->Wr.colidx, F->Wr.vals, work, s);
+  // the level-ordered copies' buffers (sizes known now; the level count is
+  // at most n), so that only copies and kernels follow the host's pass
+  LevelCsr& Vl = F->Vl;
+  int32_t *dorder = nullptr, *pos = nullptr;
+  Vl.n = n;
+  Vl.nnz = F->nnz_v - n;
+  if (ce == cudaSuccess) ce = F->alloc(&Vl.lvlptr, n + 1);
+  if (ce == cudaSuccess) ce = F->alloc(&dorder, n);
+  if (ce == cudaSuccess) ce = F->alloc(&pos, n);
+  if (ce == cudaSuccess) ce = F->alloc(&Vl.rowptr, n + 1);
+  if (ce == cudaSuccess) ce = F->alloc(&Vl.colidx, Vl.nnz > 0 ? Vl.nnz : 0);
+  if (ce == cudaSuccess) ce = F->alloc((char**)&Vl.vals, esz * (Vl.nnz > 0 ? Vl.nnz : 0));
+  if (ce == cudaSuccess) ce = F->alloc((char**)&Vl.dinv, esz * n);
+  if (ce == cudaSuccess) ce = F->alloc(&Vl.xrow, n);
+  if (ce == cudaSuccess) ce = F->alloc(&F->Wl.colidx, F->nnz_w);
+  if (ce == cudaSuccess) ce = F->alloc((char**)&F->tbuf, esz * n);
+  int32_t* const wl_colidx = F->Wl.colidx;
   PT_DEV(s);
   PT_HOST();
   // wait for the copies even after an error: they write into the staging buffer
@@ -1013,30 +1030,17 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   std::vector<int32_t> cur(ptr, ptr + nlev);
   for (int i = 0; i < n; ++i) order[cur[lev[i]]++] = i;
   PT_HOST();
-  LevelCsr& Vl = F->Vl;
-  Vl.n = n;
   Vl.nlev = nlev;
-  Vl.nnz = F->nnz_v - n;
   Vl.maxw = 0;
   for (int l = 0; l < nlev; ++l) Vl.maxw = std::max(Vl.maxw, ptr[l + 1] - ptr[l]);
-  int32_t *dorder, *pos;
-  DIAF_CU(F->alloc(&Vl.lvlptr, nlev + 1));
-  DIAF_CU(F->alloc(&dorder, n));
-  DIAF_CU(F->alloc(&pos, n));
-  DIAF_CU(F->alloc(&Vl.rowptr, n + 1));
-  DIAF_CU(F->alloc(&Vl.colidx, Vl.nnz));
-  DIAF_CU(F->alloc((char**)&Vl.vals, esz * Vl.nnz));
-  DIAF_CU(F->alloc((char**)&Vl.dinv, esz * n));
-  DIAF_CU(F->alloc(&Vl.xrow, n));
   DIAF_CU(cudaMemcpyAsync(Vl.lvlptr, ptr, sizeof(int32_t) * (nlev + 1), cudaMemcpyHostToDevice, s));
   if (n > 0) DIAF_CU(cudaMemcpyAsync(dorder, order, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
   PT_DEV(s);
   DIAF_CU(stage_release(s));  // the next user of the staging buffer waits for these copies
   DIAF_CU(csr_level_permute(F->Vr, cplx, dorder, pos, work, Vl, s));
   F->Wl = F->Wr;
-  DIAF_CU(F->alloc(&F->Wl.colidx, F->nnz_w));
+  F->Wl.colidx = wl_colidx;
   DIAF_CU(remap_columns(F->nnz_w, pos, F->Wr.colidx, F->Wl.colidx, s));
-  DIAF_CU(F->alloc((char**)&F->tbuf, esz * n));
   PT_DEV(s);
   PT_HOST();
   F->apply_ready = true;

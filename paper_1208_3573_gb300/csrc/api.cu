@@ -1044,6 +1044,7 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   PT_DEV(s);
   PT_HOST();
   F->apply_ready = true;
+  F->solve_cold = true;
   return DIAF_OK;
 }
 
@@ -1082,8 +1083,15 @@ diaf_status diaf_apply(diaf_factors* F, const void* x, void* y, void* stream) {
     DIAF_CU(csr_spmv(F->Wr, cplx, F->tbuf, y, s));
     return DIAF_OK;
   }
-  DIAF_CU(trsv_levels_perm(F->Vl, cplx, x, F->tbuf, s));
+#ifdef DIAF_PREP_TIMING
+  PrepTimer pt("apply");
+#endif
+  PT_DEV(s);
+  DIAF_CU(trsv_levels_perm(F->Vl, cplx, x, F->tbuf, s, F->solve_cold));
+  F->solve_cold = false;
+  PT_DEV(s);
   DIAF_CU(csr_spmv(F->Wl, cplx, F->tbuf, y, s));
+  PT_DEV(s);
   return DIAF_OK;
 }
 

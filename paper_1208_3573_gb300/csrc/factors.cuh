@@ -36,6 +36,7 @@ struct diaf_factors {
   int32_t* fb_counts = nullptr;  // mixed precision: columns per bucket finished by the FP64 kernel
   // apply
   bool apply_ready = false;
+  bool solve_cold = false;  // the level-ordered copies were just built: the next solve warms them
   bool v_upper = true;
   Csr Vr, Wr;
   void* tbuf = nullptr;

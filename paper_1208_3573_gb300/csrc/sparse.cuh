@@ -53,9 +53,12 @@ cudaError_t csr_level_permute(const Csr& V, bool cplx, const int32_t* order, int
 // cout[e] = pos[cin[e]] (column indices renumbered to level positions).
 cudaError_t remap_columns(int64_t nnz, const int32_t* pos, const int32_t* cin, int32_t* cout, cudaStream_t s);
 
-// t = V^-1 x by level scheduling on L: one 1024-thread block, a barrier
-// between levels; t in level order (t[p] belongs to row xrow[p]).
-cudaError_t trsv_levels_perm(const LevelCsr& L, bool cplx, const void* x, void* t, cudaStream_t s);
+// t = V^-1 x by level scheduling on L: one block, a barrier between levels;
+// t in level order (t[p] belongs to row xrow[p]).  warm: read all of the
+// solve's data once first (for the first solve after L was built, whose data
+// is cold on the solving SM).
+cudaError_t trsv_levels_perm(const LevelCsr& L, bool cplx, const void* x, void* t, cudaStream_t s,
+                             bool warm = false);
 
 // Block-diagonal V: dense LU with partial pivoting of every diagonal block
 // (blocks = runs of equal, non-decreasing block ids; at most 64 rows each).

@@ -1006,7 +1006,9 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
     DIAF_CU(se);
   }
   // level of every row (host, O(nnz)); the device checks the diagonal's values meanwhile
-  std::vector<int32_t> lev(n, 0);
+  // host scratch reused across calls of this thread (the pass sets every entry)
+  static thread_local std::vector<int32_t> lev, cur;
+  if (lev.size() < (size_t)n) lev.resize(n);
   int nlev = 0;
   bool vup = true;
   const int ls = level_schedule_host(n, cp, ri, lev.data(), &nlev, &vup);
@@ -1027,7 +1029,8 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   for (int l = 0; l <= nlev; ++l) ptr[l] = 0;
   for (int i = 0; i < n; ++i) ptr[lev[i] + 1] += 1;
   for (int l = 0; l < nlev; ++l) ptr[l + 1] += ptr[l];
-  std::vector<int32_t> cur(ptr, ptr + nlev);
+  if (cur.size() < (size_t)nlev) cur.resize(nlev);
+  std::copy(ptr, ptr + nlev, cur.begin());
   for (int i = 0; i < n; ++i) order[cur[lev[i]]++] = i;
   PT_HOST();
   Vl.nlev = nlev;

@@ -267,8 +267,45 @@ __device__ void gather_rows_warp(const PlanArgs& a, int j, int32_t* s, int N, in
   __syncwarp();
 }
 
+// Sorted unique rows of s[0..E) into s[0..m) (returns m) through a bitmap of
+// the span [lo, lo + 32 nw) in `bits` (one warp): each entry sets its bit,
+// then the words are read back in order.  The result equals sorting and
+// removing duplicates.
+__device__ int bitmap_unique_warp(int32_t* s, int E, int lo, int nw, uint32_t* bits, int lane) {
+  for (int w = lane; w < nw; w += 32) bits[w] = 0u;
+  __syncwarp();
+  for (int t = lane; t < E; t += 32) {
+    const int d = s[t] - lo;
+    atomicOr(&bits[d >> 5], 1u << (d & 31));
+  }
+  __syncwarp();
+  int base = 0;
+  for (int w0 = 0; w0 < nw; w0 += 32) {
+    const int w = w0 + lane;
+    uint32_t b = w < nw ? bits[w] : 0u;
+    const int c = __popc(b);
+    int inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(DIAF_FULL, inc, o);
+      if (lane >= o) inc += y;
+    }
+    int pos = base + inc - c;
+    while (b) {
+      s[pos++] = lo + 32 * w + (__ffs(b) - 1);
+      b &= b - 1u;
+    }
+    base += __shfl_sync(DIAF_FULL, inc, 31);
+  }
+  __syncwarp();
+  return base;
+}
+
+constexpr int kBitmapWords = 64;  // spans of up to 2,048 rows take the bitmap
+
 __global__ void __launch_bounds__(kPlanWarps * 32) plan_rows_warp_kernel(PlanArgs a) {
   __shared__ int32_t sbuf[kPlanWarps][kWarpGather];
+  __shared__ uint32_t sbits[kPlanWarps][kBitmapWords];
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int gw = blockIdx.x * kPlanWarps + warp, nw = gridDim.x * kPlanWarps;
   int mx[2] = {0, 0};
@@ -278,10 +315,23 @@ __global__ void __launch_bounds__(kPlanWarps * 32) plan_rows_warp_kernel(PlanArg
     int N = 2;
     while (N < E) N <<= 1;
     gather_rows_warp(a, j, sbuf[warp], N, lane);
-    if (N <= 32) bitonic_sort_regs<1>(sbuf[warp], N, lane);
-    else if (N <= 64) bitonic_sort_regs<2>(sbuf[warp], N, lane);
-    else if (N <= 128) bitonic_sort_regs<4>(sbuf[warp], N, lane);
-    else bitonic_sort_regs<8>(sbuf[warp], N, lane);
+    // rows within a short span (banded operators): a bitmap instead of the sort
+    int lo = INT_MAX, hi = -1;
+    for (int t = lane; t < E; t += 32) {
+      const int r = sbuf[warp][t];
+      lo = r < lo ? r : lo;
+      hi = r > hi ? r : hi;
+    }
+    lo = warp_min(lo);
+    hi = warp_max(hi);
+    if (E > 0 && hi - lo < 32 * kBitmapWords) {
+      E = bitmap_unique_warp(sbuf[warp], E, lo, ((hi - lo) >> 5) + 1, sbits[warp], lane);
+    } else {
+      if (N <= 32) bitonic_sort_regs<1>(sbuf[warp], N, lane);
+      else if (N <= 64) bitonic_sort_regs<2>(sbuf[warp], N, lane);
+      else if (N <= 128) bitonic_sort_regs<4>(sbuf[warp], N, lane);
+      else bitonic_sort_regs<8>(sbuf[warp], N, lane);
+    }
     finish_column<32>(a, j, sbuf[warp], E, lane, nullptr, mx);
     __syncwarp();
   }

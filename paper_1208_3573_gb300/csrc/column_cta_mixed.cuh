@@ -238,11 +238,197 @@ __device__ inline void cta_col_norms_f(const float* T, int ld, int m, int k, dou
   __syncthreads();
 }
 
+// g = H x = A-hat^T (A-hat x) in FP64 from the FP64 tile (rows of I_j
+// excluded), z = A-hat x (m) as scratch.
+__device__ inline void cta_hat_gram_apply(const double* Ts, int ld, int m, int k, const int32_t* inI, const double* x,
+                                          double* z, double* g) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int r = tid; r < m; r += kCtaThreads) {
+    double zr = 0.0;
+    if (inI[r] < 0)
+      for (int q = 0; q < k; ++q) zr += Ts[r + (size_t)q * ld] * x[q];
+    z[r] = zr;
+  }
+  __syncthreads();
+  for (int c = warp; c < k; c += kCtaWarps) {
+    double gc = 0.0;
+    for (int r = lane; r < m; r += 32) gc += Ts[r + (size_t)c * ld] * z[r];
+    gc = warp_sum(gc);
+    if (lane == 0) g[c] = gc;
+  }
+  __syncthreads();
+}
+
+// One second-order correction of x (FP64, k) with Rayleigh quotient d and
+// g = H x in the FP32 singular basis V (columns i, leading dimension ldv,
+// values sig): r = g - d x, x <- x - sum_i V_i (V_i^T r) / (sig_i^2 - d) over
+// i other than e0 and e1 (projection in FP32; rf, cc: k floats of scratch).
+// Returns this thread's largest |update|.
+__device__ inline float cta_basis_correction(const float* V, int ldv, const double* sig, int k, uint64_t excl,
+                                             double d, const double* g, double* x, float* rf, float* cc) {
+  const int tid = threadIdx.x;
+  for (int c = tid; c < k; c += kCtaThreads) rf[c] = (float)(g[c] - d * x[c]);
+  __syncthreads();
+  for (int i = tid; i < k; i += kCtaThreads) {
+    float vr = 0.0f;
+    for (int q = 0; q < k; ++q) vr += V[q + i * ldv] * rf[q];
+    const float si = (float)sig[i];
+    const float den = si * si - (float)d;
+    cc[i] = ((excl >> i) & 1) ? 0.0f : -vr / den;
+  }
+  __syncthreads();
+  float big = 0.0f;
+  for (int c = tid; c < k; c += kCtaThreads) {
+    float dx = 0.0f;
+    for (int i = 0; i < k; ++i) dx += V[c + i * ldv] * cc[i];
+    x[c] += (double)dx;
+    big = fmaxf(big, fabsf(dx));
+  }
+  __syncthreads();
+  return big;
+}
+
+constexpr int kClusterMax = 4;  // most singular values of a close cluster resolved in mixed precision
+
+// Eigen-decomposition of the symmetric p x p matrix K (leading dimension
+// kClusterMax, FP64) by cyclic Jacobi rotations, one thread: K becomes
+// diagonal, Q (same layout) its eigenvectors, th the eigenvalues in
+// ascending order (Q's columns sorted with them).
+__device__ inline void small_sym_eig(double* K, double* Q, double* th, int p) {
+  constexpr int P = kClusterMax;
+  for (int i = 0; i < p; ++i)
+    for (int j = 0; j < p; ++j) Q[i + j * P] = i == j ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int i = 0; i < p; ++i) {
+      dia += K[i + i * P] * K[i + i * P];
+      for (int j = i + 1; j < p; ++j) off += K[i + j * P] * K[i + j * P];
+    }
+    if (!(off > 1e-32 * dia)) break;
+    for (int i = 0; i < p; ++i)
+      for (int j = i + 1; j < p; ++j) {
+        const double kij = K[i + j * P];
+        if (kij == 0.0) continue;
+        const double tau = (K[j + j * P] - K[i + i * P]) / (2.0 * kij);
+        const double t = copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        const double cs = 1.0 / sqrt(1.0 + t * t), sn = t * cs;
+        for (int r = 0; r < p; ++r) {  // K <- K J (columns i, j)
+          const double a = K[r + i * P], b = K[r + j * P];
+          K[r + i * P] = cs * a - sn * b;
+          K[r + j * P] = sn * a + cs * b;
+        }
+        for (int c = 0; c < p; ++c) {  // K <- J^T K (rows i, j)
+          const double a = K[i + c * P], b = K[j + c * P];
+          K[i + c * P] = cs * a - sn * b;
+          K[j + c * P] = sn * a + cs * b;
+        }
+        for (int r = 0; r < p; ++r) {  // Q <- Q J
+          const double a = Q[r + i * P], b = Q[r + j * P];
+          Q[r + i * P] = cs * a - sn * b;
+          Q[r + j * P] = sn * a + cs * b;
+        }
+      }
+  }
+  for (int i = 0; i < p; ++i) th[i] = K[i + i * P];
+  for (int i = 0; i < p; ++i) {  // selection sort, ascending
+    int lo = i;
+    for (int j = i + 1; j < p; ++j)
+      if (th[j] < th[lo]) lo = j;
+    if (lo != i) {
+      const double t = th[i];
+      th[i] = th[lo];
+      th[lo] = t;
+      for (int r = 0; r < p; ++r) {
+        const double q = Q[r + i * P];
+        Q[r + i * P] = Q[r + lo * P];
+        Q[r + lo * P] = q;
+      }
+    }
+  }
+}
+
+// Rayleigh-Ritz step on the span of the p vectors X (k each, stride k) in
+// FP64, with G = H X: X is orthonormalised by modified Gram-Schmidt (G
+// follows linearly), the p x p matrix X^T H X diagonalised, and X, G become
+// its Ritz vectors for the Ritz values th (ascending; K, Q, th: shared
+// scratch of kClusterMax^2, kClusterMax^2 and kClusterMax doubles).
+__device__ inline void cta_cluster_rayleigh_ritz(double* X, double* G, int p, int k, double* red, double* K,
+                                                 double* Q, double* th) {
+  constexpr int P = kClusterMax;
+  const int tid = threadIdx.x;
+  for (int a = 0; a < p; ++a) {
+    double* xa = X + a * k;
+    double* ga = G + a * k;
+    for (int b = 0; b < a; ++b) {
+      const double* xb = X + b * k;
+      const double* gb = G + b * k;
+      double part = 0.0;
+      for (int c = tid; c < k; c += kCtaThreads) part += xb[c] * xa[c];
+      const double coef = block_sum(part, red);
+      for (int c = tid; c < k; c += kCtaThreads) {
+        xa[c] -= coef * xb[c];
+        ga[c] -= coef * gb[c];
+      }
+    }
+    double part = 0.0;
+    for (int c = tid; c < k; c += kCtaThreads) part += xa[c] * xa[c];
+    const double inv = 1.0 / sqrt(block_sum(part, red));
+    for (int c = tid; c < k; c += kCtaThreads) {
+      xa[c] *= inv;
+      ga[c] *= inv;
+    }
+  }
+  for (int a = 0; a < p; ++a)
+    for (int b = a; b < p; ++b) {
+      double part = 0.0;
+      for (int c = tid; c < k; c += kCtaThreads) part += 0.5 * (X[a * k + c] * G[b * k + c] + X[b * k + c] * G[a * k + c]);
+      const double h = block_sum(part, red);
+      if (tid == 0) K[a + b * P] = K[b + a * P] = h;
+    }
+  if (tid == 0) small_sym_eig(K, Q, th, p);
+  __syncthreads();
+  for (int c = tid; c < k; c += kCtaThreads) {
+    double xs[P], gs[P];
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+      xs[a] = a < p ? X[a * k + c] : 0.0;
+      gs[a] = a < p ? G[a * k + c] : 0.0;
+    }
+#pragma unroll
+    for (int a = 0; a < P; ++a)
+      if (a < p) {
+        double xn = 0.0, gn = 0.0;
+#pragma unroll
+        for (int b = 0; b < P; ++b)
+          if (b < p) {
+            xn += xs[b] * Q[b + a * P];
+            gn += gs[b] * Q[b + a * P];
+          }
+        X[a * k + c] = xn;
+        G[a * k + c] = gn;
+      }
+  }
+  __syncthreads();
+}
+
+constexpr int kClusterMaxCorrections = 4;       // close cluster: corrections before the column goes to FP64
+constexpr float kClusterCorrectionTol = 1e-10f;  // ... converged when no update exceeds this
+
+#ifdef DIAF_PHASE_TIMING
+#define CTA_FB(why)                                                         \
+  do {                                                                      \
+    if (threadIdx.x == 0 && a.phase) {                                      \
+      atomicAdd(&a.phase[16 + (why)], 1ull);                                \
+    }                                                                       \
+  } while (0)
+#else
+#define CTA_FB(why) do {} while (0)
+#endif
 // Returns true when the column was finished here, false when it is handed back.
 __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, int j, unsigned char* smem) {
   using L = CtaMixedSmem;
   constexpr int KP = L::KP;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const int mcap = sc.ldm;
   float* Rs = reinterpret_cast<float*>(smem);  // R of T, then R-hat (KP x KMAX)
   float* Vj = Rs + KP * kCtaKmax;               // Jacobi V (Gram path: first D R_s^-1)
@@ -371,7 +557,7 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
       rinv[c] = d > 0.0f ? 1.0f / Rs[c + c * KP] : 0.0f;
     }
     kap = block_max(kp, redF);
-    if (!(kap <= kMixedKappaMax)) return false;
+    if (!(kap <= kMixedKappaMax)) { CTA_FB(0); return false; }
     if (a.rule != DIAF_RULE_FIXED) {
       for (int r = tid; r < m; r += kCtaThreads) {  // Q = T R^-1 by rows (FP32), into Tw
         float h = 0.0f;
@@ -469,7 +655,7 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
   const int jpos = misc[0];
   int inrows = 0;
   for (int t = 0; t < l; ++t) inrows += (Iloc[t] >= 0);
-  if (m - inrows < k) return false;  // A-hat has fewer rows than columns
+  if (m - inrows < k) { CTA_FB(1); return false; }  // A-hat has fewer rows than columns
 
   DIAF_PHASE(4);
   // ---- R-hat: from G on the Gram path (G minus the I_j rows' outer
@@ -527,7 +713,7 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
       const float d = fabsf(Tw[c + (size_t)c * ld]);
       kh = fmaxf(kh, d > 0.0f ? (float)cn[c] / d : (cn[c] > 0.0 ? INFINITY : 0.0f));
     }
-    if (!(block_max(kh, redF) <= kMixedKappaMax)) return false;
+    if (!(block_max(kh, redF) <= kMixedKappaMax)) { CTA_FB(2); return false; }
     for (int i = tid; i < k * k; i += kCtaThreads) {
       const int r = i % k, c = i / k;
       Rs[r + c * KP] = (r <= c) ? Tw[r + (size_t)c * ld] : 0.0f;
@@ -556,50 +742,75 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
       gap = dmin(gap, sig[c] * sig[c] - smin * smin);
     }
   if (k > 1 && (snext - smin) <= 1e-6 * smax) flags |= DIAF_FLAG_DEGENERATE;
-  if (k > 1 && gap <= 1e-5 * smax * smax) return false;
-  const int iters = (k > 1 && gap < 1e-2 * smax * smax) ? 2 : 1;
+  // A close cluster: sigma_min^2 and the next singular values, each within
+  // 1e-5 smax^2 of the one before, up to kClusterMax of them (the rest at
+  // least that far beyond).  Their FP32 vectors can be mixed (and even
+  // ordered wrongly) at FP32 accuracy, so all of them are corrected against
+  // the other singular vectors and the cluster is resolved by a
+  // Rayleigh-Ritz step in FP64.  A longer chain goes to the FP64 kernel.
+  int32_t* cl = cst;  // the cluster's singular indices (the gather's offsets are dead)
+  uint64_t excl = 1ull << imin;
+  int p = 1;
+  if (k > 1 && gap <= 1e-5 * smax * smax) {
+    double last = smin;
+    for (;;) {
+      int nx = -1;
+      for (int c = 0; c < k; ++c)
+        if (!((excl >> c) & 1) && (nx < 0 || sig[c] < sig[nx])) nx = c;
+      if (nx < 0 || sig[nx] * sig[nx] - last * last > 1e-5 * smax * smax) break;
+      if (p == kClusterMax) { CTA_FB(3); return false; }
+      if (tid == 0) cl[p] = nx;
+      excl |= 1ull << nx;
+      last = sig[nx];
+      ++p;
+    }
+    if (tid == 0) cl[0] = imin;
+  }
 
   // ---- FP64 correction in the FP32 singular basis
-  for (int c = tid; c < k; c += kCtaThreads) wv[c] = (double)Vj[c + imin * KP];
-  __syncthreads();
-  for (int it = 0; it < iters; ++it) {
-    for (int r = tid; r < m; r += kCtaThreads) {  // z = A-hat x
-      double z = 0.0;
-      if (inI[r] < 0)
-        for (int q = 0; q < k; ++q) z += Ts[r + (size_t)q * ld] * wv[q];
-      zz[r] = z;
-    }
+  if (p == 1) {
+    const int iters = (k > 1 && gap < 1e-2 * smax * smax) ? 2 : 1;
+    for (int c = tid; c < k; c += kCtaThreads) wv[c] = (double)Vj[c + imin * KP];
     __syncthreads();
-    for (int c = warp; c < k; c += kCtaWarps) {  // H x = A-hat^T z
-      double g = 0.0;
-      for (int r = lane; r < m; r += 32) g += Ts[r + (size_t)c * ld] * zz[r];
-      g = warp_sum(g);
-      if (lane == 0) gg[c] = g;
+    for (int it = 0; it < iters; ++it) {
+      cta_hat_gram_apply(Ts, ld, m, k, inI, wv, zz, gg);
+      double xg = 0.0, xx = 0.0;
+      for (int c = tid; c < k; c += kCtaThreads) {
+        xg += wv[c] * gg[c];
+        xx += wv[c] * wv[c];
+      }
+      xg = block_sum(xg, red);
+      xx = block_sum(xx, red);
+      const double d = xg / xx;
+      cta_basis_correction(Vj, KP, sig, k, excl, d, gg, wv, rf, cc);
     }
+  } else {
+    // the cluster's vectors X and G = H X (p x k each) in the slab's
+    // working tile, dead here (2 kClusterMax k doubles <= ldm kcap floats);
+    // the p x p Rayleigh-Ritz matrices over the column norms, dead here
+    __syncthreads();  // cl
+    double* Xc = reinterpret_cast<double*>(Tw);
+    double* Gc = Xc + (size_t)kClusterMax * k;
+    double* Km = cn;
+    double* Qm = Km + kClusterMax * kClusterMax;
+    double* th = Qm + kClusterMax * kClusterMax;
+    for (int i = tid; i < p * k; i += kCtaThreads) Xc[i] = (double)Vj[(i % k) + cl[i / k] * KP];
     __syncthreads();
-    double xg = 0.0, xx = 0.0;
-    for (int c = tid; c < k; c += kCtaThreads) {
-      xg += wv[c] * gg[c];
-      xx += wv[c] * wv[c];
+    bool conv = false;
+    for (int it = 0;; ++it) {
+      for (int c = 0; c < p; ++c) cta_hat_gram_apply(Ts, ld, m, k, inI, Xc + c * k, zz, Gc + c * k);
+      cta_cluster_rayleigh_ritz(Xc, Gc, p, k, red, Km, Qm, th);
+      if (conv) break;
+      if (it == kClusterMaxCorrections) { CTA_FB(3); return false; }
+      float big = 0.0f;
+      for (int c = 0; c < p; ++c)
+        big = fmaxf(big, cta_basis_correction(Vj, KP, sig, k, excl, th[c], Gc + c * k, Xc + c * k, rf, cc));
+      conv = block_max(big, redF) <= kClusterCorrectionTol;
     }
-    xg = block_sum(xg, red);
-    xx = block_sum(xx, red);
-    const double d = xg / xx;
-    for (int c = tid; c < k; c += kCtaThreads) rf[c] = (float)(gg[c] - d * wv[c]);
-    __syncthreads();
-    for (int i = tid; i < k; i += kCtaThreads) {
-      float vr = 0.0f;
-      for (int q = 0; q < k; ++q) vr += Vj[q + i * KP] * rf[q];
-      const float si = (float)sig[i];
-      const float den = si * si - (float)d;
-      cc[i] = i == imin ? 0.0f : -vr / den;
-    }
-    __syncthreads();
-    for (int c = tid; c < k; c += kCtaThreads) {
-      float dx = 0.0f;
-      for (int i = 0; i < k; ++i) dx += Vj[c + i * KP] * cc[i];
-      wv[c] += (double)dx;
-    }
+    for (int c = tid; c < k; c += kCtaThreads) wv[c] = Xc[c];  // the smallest Ritz vector
+    // the DEGENERATE decision on the FP64 Ritz values
+    flags &= ~DIAF_FLAG_DEGENERATE;
+    if (sqrt(dmax(th[1], 0.0)) - sqrt(dmax(th[0], 0.0)) <= 1e-6 * smax) flags |= DIAF_FLAG_DEGENERATE;
     __syncthreads();
   }
   double xn = 0.0;
@@ -623,7 +834,7 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
   return true;
 }
 
-__global__ void __launch_bounds__(kCtaThreads) column_cta_mixed_kernel(ColArgs a, CtaScratch sc) {
+__global__ void __launch_bounds__(kCtaThreads, 3) column_cta_mixed_kernel(ColArgs a, CtaScratch sc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int idx_s;
   const int count = *a.list_count;

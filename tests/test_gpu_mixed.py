@@ -107,6 +107,33 @@ def test_mixed_parity_full_size_powerlaw_sampled(D):
     print("fallbacks per bucket", fb, "of", list(F.info.bucket_cols))
 
 
+def test_mixed_close_pairs_powerlaw(D):
+    """Columns whose two smallest singular values of A-hat are close (sigma^2
+    gap at most 1e-5 ||T||_F^2, a superset of the kernels' close-pair test
+    against sigma_max^2): the large-tile kernel resolves such a pair by FP64
+    corrections of both vectors and a 2 x 2 Rayleigh-Ritz step instead of
+    handing the column to the FP64 kernel.  Every such column of n = 200,000
+    must be at parity (unique vectors within 1e-6, DEGENERATE from the FP64
+    Ritz values), and few of the large bucket's columns may go to FP64."""
+    w = make_workload("powerlaw200k")
+    F = run_gpu(D, w.A, w.PW, w.vrule, w.budget, alg="S", prec="mixed32", tie_tol=w.tie_tol)
+    g = host_factors(F)
+    o_all = O.factor(w.A, w.PW, w.vrule, w.budget, alg="S", tie_tol=w.tie_tol)
+    colnorm2 = np.bincount(np.repeat(np.arange(w.n), np.diff(w.A.colptr)), weights=w.A.vals ** 2, minlength=w.n)
+    k = w.PW.counts()
+    tf2 = np.bincount(np.repeat(np.arange(w.n), k), weights=colnorm2[w.PW.rowidx], minlength=w.n)
+    s0, s1 = o_all.sig[:, 0], o_all.sig[:, 1]
+    close = np.nonzero((k > 1) & (s1 ** 2 - s0 ** 2 <= 1e-5 * tf2))[0].astype(np.int32)
+    assert close.size > 100
+    o = O.factor(w.A, w.PW, w.vrule, w.budget, alg="S", tie_tol=w.tie_tol, cols=close)
+    rep = compare(g, o, w.A, w.PW, "S", rtol_res=RTOL_RES, vec_tol=VEC_TOL, mixed=True, floor_rel=1e-10, cols=close)
+    assert_parity(rep)
+    fb = F.fallbacks()
+    kept = int(np.count_nonzero((g["flags"][close] & 64) == 0))
+    print("close columns", close.size, "kept in mixed precision", kept, "fallbacks per bucket", fb)
+    assert fb[2] < 100
+
+
 @pytest.mark.parametrize("alg", ["S", "Q"])
 def test_mixed_parity_full_size_lognormal64(D, alg):
     """262,144 columns with k = 25 tiles: every I_j of the mixed form must be the

@@ -105,6 +105,100 @@ __device__ double cta_select_rows_w0(const int32_t* rs, const K* hk, int32_t* pi
   return mg;
 }
 
+// The same greedy V rule (the same picks and the same decision margin as
+// cta_select_rows_w0) from one sort instead of a scan of every remaining key
+// per pick: warp 0 lists the admissible rows, the CTA sorts the list by key
+// (descending; the lower row first among equal keys), and thread 0 walks
+// it.  At a pick the largest remaining key heads the remaining list, the
+// rows within tau of it are the run that follows (the lowest of them is
+// picked), and the smallest distance of a non-leading key from the
+// threshold is in that run or at the first remaining key below it (|h -
+// thr| grows with the distance in the sorted order), so a pick reads only
+// that run.  Needs finite keys and tau >= 0.  ord: shared scratch of at
+// least the power of two >= m ints; red: one double of shared scratch.
+template <class K>
+__device__ double cta_select_rows_sorted(const int32_t* rs, const K* hk, int32_t* pick, int m, int rule, int j, int s,
+                                         double tau, const int32_t* blk, double* red, int32_t* ord) {
+  const int tid = threadIdx.x;
+  __shared__ int na_s;
+  if ((tid >> 5) == 0) {  // compaction of the admissible rows, in row order
+    const int lane = tid & 31;
+    int cnt = 0;
+    for (int base = 0; base < m; base += 32) {
+      const int r = base + lane;
+      const bool ad = r < m && admissible_row(rule, rs[r], j, blk);
+      const uint32_t bal = __ballot_sync(DIAF_FULL, ad);
+      if (ad) ord[cnt + __popc(bal & ((1u << lane) - 1u))] = r;
+      cnt += __popc(bal);
+    }
+    if (lane == 0) na_s = cnt;
+  }
+  __syncthreads();
+  const int na = na_s;
+  int N = 1;
+  while (N < na) N <<= 1;
+  for (int i = na + tid; i < N; i += kCtaThreads) ord[i] = -1;  // padding, sorted last
+  __syncthreads();
+  // bitonic sort of ord[0, N) into the order "a before b"
+  for (int size = 2; size <= N; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = tid; i < (N >> 1); i += kCtaThreads) {
+        const int lo = (i / stride) * 2 * stride + (i % stride), hi = lo + stride;
+        const int a = ord[lo], b = ord[hi];
+        bool b_first;  // b belongs before a
+        if (a < 0 || b < 0) {
+          b_first = a < 0 && b >= 0;
+        } else {
+          const K ka = hk[a], kb = hk[b];
+          b_first = kb > ka || (kb == ka && b < a);
+        }
+        if (b_first == ((lo & size) == 0)) {
+          ord[lo] = b;
+          ord[hi] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) {
+    K margin = std::numeric_limits<K>::max();
+    int head = 0;
+    for (int t = 0; t < s; ++t) {
+      while (head < na && pick[ord[head]]) ++head;
+      if (head == na) break;  // no admissible row left
+      const int rmax = ord[head];
+      const K thr = hk[rmax] - K(tau);
+      int best = rmax;
+      int q = head + 1;
+      for (; q < na; ++q) {
+        const int r = ord[q];
+        if (pick[r]) continue;
+        const K h = hk[r];
+        margin = dmin(margin, (K)fabs(h - thr));
+        if (!(h >= thr)) break;  // the first remaining key below the threshold
+        best = r < best ? r : best;
+      }
+      pick[best] = 1;
+    }
+    red[0] = (double)margin;
+  }
+  __syncthreads();
+  const double mg = red[0];
+  __syncthreads();  // red is free again
+  return mg;
+}
+
+// The greedy V rule for the CTA kernels: the sorted form where it applies
+// (finite keys, tau >= 0), the scan otherwise.  ord as above.
+template <class K>
+__device__ double cta_select_rows_greedy(const int32_t* rs, const K* hk, int32_t* pick, int m, int rule, int j, int s,
+                                         double tau, const int32_t* blk, double* red, int32_t* ord) {
+  int bad = !(tau >= 0.0);
+  for (int r = threadIdx.x; r < m && !bad; r += kCtaThreads) bad = !isfinite((double)hk[r]);
+  if (__syncthreads_or(bad)) return cta_select_rows_w0(rs, hk, pick, m, rule, j, s, tau, blk, red);
+  return cta_select_rows_sorted(rs, hk, pick, m, rule, j, s, tau, blk, red, ord);
+}
+
 // Householder QR of the m x k tile T (leading dimension ld, global memory):
 // the norm of column c by a block reduction, then warp w updates the
 // trailing columns q = c+1+w, c+1+w+kCtaWarps, ... (dot product by a warp
@@ -404,7 +498,7 @@ __device__ void solve_column_cta(const ColArgs& a, const CtaScratch& sc, int j, 
   }
   if (a.rule != DIAF_RULE_FIXED) {
     double* redD = reinterpret_cast<double*>(red);
-    cta_select_rows_w0(rs, hk, pick, m, a.rule, j, l - 1, a.tie_tol, a.blk, redD);
+    cta_select_rows_greedy(rs, hk, pick, m, a.rule, j, l - 1, a.tie_tol, a.blk, redD, Is);  // Is, Iloc: scratch until I_j
   }
   // I_j
   if (tid == 0) {

@@ -575,7 +575,8 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
   }
   DIAF_PHASE(2);
   if (a.rule != DIAF_RULE_FIXED) {
-    const double margin = cta_select_rows_w0(rs, hk, pick, m, a.rule, j, l - 1, a.tie_tol, a.blk, red);
+    // (Is and Iloc, 2 mcap ints, are the sort's scratch until I_j is formed)
+    const double margin = cta_select_rows_greedy(rs, hk, pick, m, a.rule, j, l - 1, a.tie_tol, a.blk, red, Is);
     // key error bound: the FP32 QR's backward error amplified by kappa, or
     // kappa^2 for keys from the Gram matrix
     const double delta = kMixedDeltaScale * (m + k) * (double)FLT_EPSILON * (double)kap * (gram ? (double)kap : 1.0);
@@ -617,7 +618,7 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
         hk[r] = h;
       }
       __syncthreads();
-      cta_select_rows_w0(rs, hk, pick, m, a.rule, j, l - 1, a.tie_tol, a.blk, red);
+      cta_select_rows_greedy(rs, hk, pick, m, a.rule, j, l - 1, a.tie_tol, a.blk, red, Is);
     }
   }
   DIAF_PHASE(3);

@@ -199,6 +199,73 @@ __device__ double cta_select_rows_greedy(const int32_t* rs, const K* hk, int32_t
   return cta_select_rows_sorted(rs, hk, pick, m, rule, j, s, tau, blk, red, ord);
 }
 
+// Gather offsets of the tile's k columns J (warp 0; k <= 64): cst[q] =
+// the start of column J[q] of A, coff[q] = the entries of the columns before
+// it, *total = all the entries (an exclusive scan by shuffles).
+__device__ inline void cta_gather_offsets(const int32_t* Acp, const int32_t* J, int k, int32_t* cst, int32_t* coff,
+                                          int32_t* total) {
+  if ((threadIdx.x >> 5) != 0) return;
+  const int lane = threadIdx.x & 31;
+  int e = 0;
+  for (int base = 0; base < k; base += 32) {
+    const int q = base + lane;
+    int st = 0, len = 0;
+    if (q < k) {
+      const int c = J[q];
+      st = Acp[c];
+      len = Acp[c + 1] - st;
+    }
+    int incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(DIAF_FULL, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (q < k) {
+      cst[q] = st;
+      coff[q] = e + incl - len;
+    }
+    e += __shfl_sync(DIAF_FULL, incl, 31);
+  }
+  if (lane == 0) *total = e;
+}
+
+// I_j of a greedy rule (warp 0): the picked rows and j's own row of the
+// tile, in row order, with j inserted before the first larger row when it
+// is not a row of the tile (jin false).  Writes Is, Iloc (tile row, -1 for
+// an inserted j), inI of the listed rows and *jpos (the place of j), as the
+// one-thread construction in row order would.
+__device__ inline void cta_form_I_greedy(const int32_t* rs, const int32_t* pick, int m, int j, bool jin, int32_t* Is,
+                                         int32_t* Iloc, int32_t* inI, int32_t* jpos) {
+  if ((threadIdx.x >> 5) != 0) return;
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  if (lane == 0) *jpos = -1;
+  __syncwarp();
+  int cnt = 0, below = 0;  // rows listed so far; of them, rows < j
+  for (int base = 0; base < m; base += 32) {
+    const int r = base + lane;
+    const int row = r < m ? rs[r] : INT_MAX;
+    const bool f = r < m && (pick[r] || row == j);
+    const uint32_t bal = __ballot_sync(DIAF_FULL, f);
+    const uint32_t bl = __ballot_sync(DIAF_FULL, f && row < j);
+    if (f) {
+      const int idx = cnt + __popc(bal & lt) + ((!jin && row > j) ? 1 : 0);
+      Is[idx] = row;
+      Iloc[idx] = r;
+      inI[r] = idx;
+      if (row == j) *jpos = idx;
+    }
+    cnt += __popc(bal);
+    below += __popc(bl);
+  }
+  if (!jin && lane == 0) {
+    Is[below] = j;
+    Iloc[below] = -1;
+    *jpos = below;
+  }
+}
+
 // Householder QR of the m x k tile T (leading dimension ld, global memory):
 // the norm of column c by a block reduction, then warp w updates the
 // trailing columns q = c+1+w, c+1+w+kCtaWarps, ... (dot product by a warp
@@ -445,16 +512,7 @@ __device__ void solve_column_cta(const ColArgs& a, const CtaScratch& sc, int j, 
     pick[r] = 0;
   }
   for (size_t i = tid; i < (size_t)me * k; i += kCtaThreads) Ts[(i % me) + (i / me) * ld] = sc_zero<S>();
-  if (tid == 0) {
-    int e = 0;
-    for (int q = 0; q < k; ++q) {
-      int c = J[q];
-      cst[q] = a.Acp[c];
-      coff[q] = e;
-      e += a.Acp[c + 1] - a.Acp[c];
-    }
-    misc[1] = e;
-  }
+  cta_gather_offsets(a.Acp, J, k, cst, coff, misc + 1);
   __syncthreads();
   const int E = misc[1];
   for (int e = tid; e < E; e += kCtaThreads) {
@@ -501,10 +559,9 @@ __device__ void solve_column_cta(const ColArgs& a, const CtaScratch& sc, int j, 
     cta_select_rows_greedy(rs, hk, pick, m, a.rule, j, l - 1, a.tie_tol, a.blk, redD, Is);  // Is, Iloc: scratch until I_j
   }
   // I_j
-  if (tid == 0) {
-    misc[0] = -1;
-    int cnt = 0;
-    if (a.rule == DIAF_RULE_FIXED) {
+  if (a.rule == DIAF_RULE_FIXED) {
+    if (tid == 0) {
+      misc[0] = -1;
       const int32_t* Vf = a.Vfri + a.Vfcp[j];
       for (int t = 0; t < l; ++t) {
         int row = Vf[t];
@@ -515,20 +572,9 @@ __device__ void solve_column_cta(const ColArgs& a, const CtaScratch& sc, int j, 
         if (loc >= 0) inI[loc] = t;
         if (row == j) misc[0] = t;
       }
-    } else {
-      bool placed = false;
-      for (int r = 0; r < m; ++r) {
-        if (!placed && !a.jin[j] && rs[r] > j) { Is[cnt] = j; Iloc[cnt] = -1; misc[0] = cnt; ++cnt; placed = true; }
-        if (pick[r] || rs[r] == j) {
-          Is[cnt] = rs[r];
-          Iloc[cnt] = r;
-          inI[r] = cnt;
-          if (rs[r] == j) misc[0] = cnt;
-          ++cnt;
-        }
-      }
-      if (!placed && !a.jin[j]) { Is[cnt] = j; Iloc[cnt] = -1; misc[0] = cnt; ++cnt; }
     }
+  } else {
+    cta_form_I_greedy(rs, pick, m, j, a.jin[j] != 0, Is, Iloc, inI, misc);
   }
   __syncthreads();
   const int jpos = misc[0];

@@ -480,16 +480,7 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
     pick[r] = 0;
   }
   for (size_t i = tid; i < (size_t)me * k; i += kCtaThreads) Ts[(i % me) + (i / me) * ld] = 0.0;
-  if (tid == 0) {
-    int e = 0;
-    for (int q = 0; q < k; ++q) {
-      const int c = J[q];
-      cst[q] = a.Acp[c];
-      coff[q] = e;
-      e += a.Acp[c + 1] - a.Acp[c];
-    }
-    misc[1] = e;
-  }
+  cta_gather_offsets(a.Acp, J, k, cst, coff, misc + 1);
   __syncthreads();
   const int E = misc[1];
   for (int e = tid; e < E; e += kCtaThreads) {
@@ -623,10 +614,9 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
   }
   DIAF_PHASE(3);
   // I_j
-  if (tid == 0) {
-    misc[0] = -1;
-    int cnt = 0;
-    if (a.rule == DIAF_RULE_FIXED) {
+  if (a.rule == DIAF_RULE_FIXED) {
+    if (tid == 0) {
+      misc[0] = -1;
       const int32_t* Vf = a.Vfri + a.Vfcp[j];
       for (int t = 0; t < l; ++t) {
         const int row = Vf[t];
@@ -637,20 +627,9 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
         if (loc >= 0) inI[loc] = t;
         if (row == j) misc[0] = t;
       }
-    } else {
-      bool placed = false;
-      for (int r = 0; r < m; ++r) {
-        if (!placed && !a.jin[j] && rs[r] > j) { Is[cnt] = j; Iloc[cnt] = -1; misc[0] = cnt; ++cnt; placed = true; }
-        if (pick[r] || rs[r] == j) {
-          Is[cnt] = rs[r];
-          Iloc[cnt] = r;
-          inI[r] = cnt;
-          if (rs[r] == j) misc[0] = cnt;
-          ++cnt;
-        }
-      }
-      if (!placed && !a.jin[j]) { Is[cnt] = j; Iloc[cnt] = -1; misc[0] = cnt; ++cnt; }
     }
+  } else {
+    cta_form_I_greedy(rs, pick, m, j, a.jin[j] != 0, Is, Iloc, inI, misc);
   }
   __syncthreads();
   const int jpos = misc[0];

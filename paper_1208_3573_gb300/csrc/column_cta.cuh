@@ -304,8 +304,11 @@ __device__ void cta_householder_qr(S* T, int ld, int m, int k, RealOf<S>* redR, 
 // One-sided Jacobi on the p x q matrix G (shared memory, leading dimension
 // LDG) with V (q x q, leading dimension LDV): the same rotation as
 // warp_jacobi, the q/2 pairs of a round spread over the CTA (LPP threads per
-// pair), a barrier between rounds.
-template <class S, int LDG, int LDV>
+// pair), a barrier between rounds.  PREDICT as for warp_jacobi (callers
+// whose result is refined afterwards): no sweep that would only confirm
+// convergence after a sweep whose rotations all had |gamma| < sqrt(tol)
+// sqrt(alpha beta).
+template <class S, int LDG, int LDV, bool PREDICT = false>
 __device__ int cta_jacobi(S* G, int p, int q, S* V, RealOf<S>* redR) {
   using R = RealOf<S>;
   constexpr int LPP = kCtaThreads / (kCtaKmax / 2);  // 8 threads per pair
@@ -327,6 +330,7 @@ __device__ int cta_jacobi(S* G, int p, int q, S* V, RealOf<S>* redR) {
   const int grp = tid / LPP, sub = tid % LPP;
   for (int sweep = 1; sweep <= kMaxSweeps; ++sweep) {
     int rotated = 0;
+    int large = 0;  // PREDICT: a rotation with |gamma|^2 >= tol alpha beta
     for (int rnd = 0; rnd < qq - 1; ++rnd) {
       int a = -1, b = -1;
       if (grp < npairs) {
@@ -356,6 +360,7 @@ __device__ int cta_jacobi(S* G, int p, int q, S* V, RealOf<S>* redR) {
       const bool rot = act && al > tiny && be > tiny && ag2 > R(0) && ag2 > tol2 * (al * be);
       if (rot) {
         rotated = 1;
+        if (PREDICT && ag2 >= tol * (al * be)) large = 1;
         R ag;
         S eph;
         if constexpr (ScalarInfo<S>::cplx) {
@@ -387,6 +392,7 @@ __device__ int cta_jacobi(S* G, int p, int q, S* V, RealOf<S>* redR) {
       __syncthreads();
     }
     if (!__syncthreads_or(rotated)) return sweep;
+    if (PREDICT && !__syncthreads_or(large)) return sweep;
   }
   return -1;
 }

@@ -701,7 +701,7 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
     __syncthreads();
   }
   DIAF_PHASE(6);
-  if (cta_jacobi<float, KP, KP>(Rs, k, k, Vj, redF) < 0) flags |= DIAF_FLAG_JACOBI_NOCONV;
+  if (cta_jacobi<float, KP, KP, true>(Rs, k, k, Vj, redF) < 0) flags |= DIAF_FLAG_JACOBI_NOCONV;
   DIAF_PHASE(7);
   for (int c = tid; c < k; c += kCtaThreads) {
     float s2 = 0.0f;

@@ -79,6 +79,18 @@ FP64_NOMINAL_TFLOPS = 1.25
 JACOBI_SWEEPS = 5  # mean sweeps of the FP32 Jacobi on the headline workload (phase-timer build)
 
 
+def dominant_kernel(bucket: int, prec: str, alg: str, cplx: bool) -> str:
+    """Name of the numeric kernel that runs size bucket `bucket` (0: tiles up
+    to 32 x 16, 1: up to 64 x 32, 2: larger) for this precision and form."""
+    if prec == "fp64":
+        return "column_cta_kernel" if bucket == 2 else "column_warp_kernel"
+    if bucket == 2:
+        return "column_cta_mixed_kernel" if (alg == "S" and not cplx) else "column_cta_kernel (FP64)"
+    if bucket == 0 and alg == "S" and not cplx:
+        return "column_thread_kernel (four lanes per column)"
+    return "column_mixed_kernel"
+
+
 def algorithmic_flops(m: np.ndarray, k: np.ndarray, l: np.ndarray, alg: str, cplx: bool,
                       sweeps: float = JACOBI_SWEEPS) -> tuple[float, float]:
     """(all flops, FP64 flops) the method does per factorisation, summed over
@@ -532,18 +544,21 @@ def main():
     flops, flops64 = algorithmic_flops(m, k, lcount, args.alg, cplx)
     kern = float(np.mean([sum(x) for x in kern_ms]))
     achieved = flops / (kern / 1e3)
-    small_quad = args.prec == "mixed32" and not cplx and args.alg == "S"
+    # the kernel of the bucket that took the most time
+    bucket_mean = np.mean(np.array(kern_ms, dtype=np.float64), axis=0)
+    dom = int(np.argmax(bucket_mean))
+    kname = dominant_kernel(dom, args.prec, args.alg, cplx)
     if args.prec == "fp64":
-        peak, src, kname = FP64_NOMINAL_TFLOPS * 1e12, "FP64 nominal 1.25 TFLOP/s", "column_warp_kernel"
+        peak, src = FP64_NOMINAL_TFLOPS * 1e12, "FP64 nominal 1.25 TFLOP/s"
     else:
         peak, src = FP32_TFLOPS * 1e12, "FP32 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
-        kname = "column_thread_kernel (four lanes per column)" if small_quad else "column_mixed_kernel"
     # DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu
     # capture of the current kernel on this workload; None where none was taken
     traffic = TRAFFIC.get((w.name, args.alg, args.prec))
     gbytes = gathered_bytes(w)
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": traffic, "kernel": f"{kname} (numeric pass, all buckets)",
+            "frac": achieved / peak, "traffic": traffic, "kernel": f"{kname} (size bucket {dom}, {bucket_mean[dom] / kern:.0%} of the numeric pass; "
+                                                        "the figures cover the whole pass)",
             "kernel_ms": kern, "algorithmic_flops": flops, "jacobi_sweeps_assumed": JACOBI_SWEEPS,
             "peak_source": src,
             "fp64": {"flops": flops64, "achieved": flops64 / (kern / 1e3) / 1e12, "peak": FP64_NOMINAL_TFLOPS,

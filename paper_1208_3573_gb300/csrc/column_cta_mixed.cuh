@@ -571,6 +571,7 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
     // key error bound: the FP32 QR's backward error amplified by kappa, or
     // kappa^2 for keys from the Gram matrix
     const double delta = kMixedDeltaScale * (m + k) * (double)FLT_EPSILON * (double)kap * (gram ? (double)kap : 1.0);
+    DIAF_PHASE(3);
     if (l > 1 && margin <= 2.0 * delta) {
       // the FP32 keys cannot decide this column: the FP64 CTA kernel's QR and
       // key computation on an FP64 copy of the tile (in the FP32 tile's slab
@@ -610,6 +611,7 @@ __device__ bool solve_column_cta_mixed(const ColArgs& a, const CtaScratch& sc, i
       }
       __syncthreads();
       cta_select_rows_greedy(rs, hk, pick, m, a.rule, j, l - 1, a.tie_tol, a.blk, red, Is);
+      DIAF_PHASE(10);
     }
   }
   DIAF_PHASE(3);

@@ -68,3 +68,13 @@ def test_gathered_bytes():
         pass
     w = Wl(); w.A, w.PW = A, P
     assert bench.gathered_bytes(w) == (2 + 2 + 3) * 12.0
+
+
+def test_dominant_kernel_names_the_bucket_kernel():
+    assert bench.dominant_kernel(0, "mixed32", "S", False).startswith("column_thread_kernel")
+    assert bench.dominant_kernel(1, "mixed32", "S", False) == "column_mixed_kernel"
+    assert bench.dominant_kernel(2, "mixed32", "S", False) == "column_cta_mixed_kernel"
+    assert bench.dominant_kernel(2, "mixed32", "Q", False).startswith("column_cta_kernel")
+    assert bench.dominant_kernel(0, "mixed32", "S", True) == "column_mixed_kernel"
+    assert bench.dominant_kernel(1, "fp64", "S", False) == "column_warp_kernel"
+    assert bench.dominant_kernel(2, "fp64", "Q", True) == "column_cta_kernel"

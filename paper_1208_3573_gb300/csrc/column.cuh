@@ -28,6 +28,10 @@ constexpr float kMixedKappaMax = 300.0f;
 #define DIAF_MIXED_DELTA_SCALE 1.0
 #endif
 constexpr double kMixedDeltaScale = DIAF_MIXED_DELTA_SCALE;
+// A factor taken from a Gram matrix in FP32 carries kappa^2 instead of kappa:
+// the Gram paths of the mixed kernels are used only up to this column-scaled
+// kappa (the Householder QR otherwise).
+constexpr float kGramKappaMax = 30.0f;
 
 struct ColArgs {
   int n;

@@ -38,8 +38,8 @@ struct CtaMixedSmem {
 // product; the R of A-hat from G minus the I_j rows' outer products.  The
 // error of a Gram-based factor grows with kappa^2 instead of kappa, so the
 // path is taken only for column-scaled kappa <= kGramKappaMax (and the key
-// decisions use the kappa^2 bound); other tiles keep the Householder QRs.
-constexpr float kGramKappaMax = 30.0f;
+// decisions use the kappa^2 bound); other tiles keep the Householder QRs
+// (kGramKappaMax).
 
 __device__ __forceinline__ uint32_t tf32_head(float x) {
   uint32_t r;

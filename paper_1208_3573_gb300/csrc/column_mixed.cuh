@@ -43,6 +43,69 @@ template <> struct DoubleOf<Cx<float>> { using T = Cx<double>; };
 constexpr int kQRefineMax = 4;  // DIAF-Q: most corrections before the column goes to FP64
 constexpr int kRRMax = 8;  // DIAF-Q: sizes of the refinement's scratch (KP x 8 and 2 x 64 scalars)
 
+// R of the real m x k FP32 tile W (leading dimension LDT, one warp) from
+// its Gram matrix: lane q accumulates column q of G = W^T W (the other
+// columns read as broadcasts), cn receives the column norms, R_s =
+// chol(D G D) with D = diag(1 / cn) is formed in place in Rs (leading
+// dimension KP, upper triangle; strict lower triangle zeroed), and R = R_s
+// D^-1 is kept when the column-scaled kappa max_c 1 / R_s,cc is at most
+// kGramKappaMax.  Returns false (uniformly; Rs then undefined, cn the
+// column norms) for a zero column, a non-positive pivot or a larger kappa.
+template <int KMAX, int LDT, int KP>
+__device__ bool warp_gram_cholesky(const float* W, int m, int k, float* Rs, double* cn, int lane) {
+  float acc[KMAX];
+#pragma unroll
+  for (int p = 0; p < KMAX; ++p) acc[p] = 0.0f;
+  if (lane < k) {
+    const float* wq = W + lane * LDT;
+    for (int r = 0; r < m; ++r) {
+      const float x = wq[r];
+#pragma unroll
+      for (int p = 0; p < KMAX; ++p)
+        if (p < k) acc[p] = fmaf(x, W[r + p * LDT], acc[p]);
+    }
+  }
+  // the diagonal: lane q holds acc[q]
+  float gqq = 0.0f;
+#pragma unroll
+  for (int p = 0; p < KMAX; ++p)
+    if (p == lane) gqq = acc[p];
+  const float nq = sqrtf(gqq);
+  if (lane < k) cn[lane] = (double)nq;
+  const int zero = __any_sync(DIAF_FULL, lane < k && !(nq > 0.0f));
+  if (zero) return false;
+  const float dq = lane < k ? 1.0f / nq : 0.0f;
+  // D G D (upper triangle) into Rs: element (p, q) = acc[p] d_p d_q
+#pragma unroll
+  for (int p = 0; p < KMAX; ++p) {
+    const float dp = __shfl_sync(DIAF_FULL, dq, p);
+    if (lane < k && p < k) Rs[p + lane * KP] = p <= lane ? acc[p] * dp * dq : 0.0f;
+  }
+  __syncwarp();
+  // right-looking Cholesky, lane q owns column q
+  float kap = 0.0f;
+  for (int c = 0; c < k; ++c) {
+    const float d = Rs[c + c * KP];
+    if (!(d > 0.0f)) return false;  // uniform: every lane read the same pivot
+    const float rcc = sqrtf(d), rinv = 1.0f / rcc;
+    kap = fmaxf(kap, rinv);
+    __syncwarp();
+    const float rcq = lane > c && lane < k ? Rs[c + lane * KP] * rinv : 0.0f;
+    if (lane == c) Rs[c + c * KP] = rcc;
+    if (lane > c && lane < k) Rs[c + lane * KP] = rcq;
+    __syncwarp();
+    if (lane > c && lane < k)
+      for (int p = c + 1; p <= lane; ++p) Rs[p + lane * KP] -= Rs[c + p * KP] * rcq;
+    __syncwarp();
+  }
+  if (!(kap <= kGramKappaMax)) return false;
+  // R = R_s D^-1: column q times cn_q
+  if (lane < k)
+    for (int p = 0; p <= lane; ++p) Rs[p + lane * KP] *= nq;
+  __syncwarp();
+  return true;
+}
+
 template <class S, int KMAX, int MMAX, int ALG>
 struct MixedLayout {
   using SD = typename DoubleOf<S>::T;
@@ -237,19 +300,32 @@ __device__ void solve_column_mixed(const ColArgs& a, int j, unsigned char* smem,
         Tw[r + c * LDT] = (r < m && ix.inI[r] >= 0) ? sc_zero<S>() : sc_cast<S>(Ts[r + c * LDT]);
       }
       __syncwarp();
-      for (int c = lane; c < k; c += DIAF_WARP) {
-        R s2 = R(0);
-        for (int r = 0; r < m; ++r) s2 += sc_abs2(Tw[r + c * LDT]);
-        cn[c] = (double)sqrt(s2);
+      bool gram_hat = false;
+      if constexpr (!ScalarInfo<S>::cplx) {
+        // R-hat from the Gram matrix of A-hat's own rows (no downdating, so no
+        // cancellation): lane q forms column q of G-hat = A-hat^T A-hat in
+        // FP32, then a scaled Cholesky factor; kept when the column-scaled
+        // kappa is at most kGramKappaMax (the Householder QR otherwise, and for
+        // an exactly zero column of A-hat)
+        gram_hat = warp_gram_cholesky<KMAX, LDT, KP>(Tw, m, k, Rs, cn, lane);
       }
-      __syncwarp();
       DIAF_PHASE(5);
-      warp_householder_qr_rs<S, LDT, KMAX, MMAX / DIAF_WARP>(Tw, me, k, lane);
-      for (int i = lane; i < k * k; i += DIAF_WARP) {
-        int r = i % k, c = i / k;
-        Rs[r + c * KP] = (r <= c) ? Tw[r + c * LDT] : sc_zero<S>();
+      if (!gram_hat) {
+        if constexpr (ScalarInfo<S>::cplx) {  // (the Gram path gave the real tiles' norms)
+          for (int c = lane; c < k; c += DIAF_WARP) {
+            R s2 = R(0);
+            for (int r = 0; r < m; ++r) s2 += sc_abs2(Tw[r + c * LDT]);
+            cn[c] = (double)sqrt(s2);
+          }
+          __syncwarp();
+        }
+        warp_householder_qr_rs<S, LDT, KMAX, MMAX / DIAF_WARP>(Tw, me, k, lane);
+        for (int i = lane; i < k * k; i += DIAF_WARP) {
+          int r = i % k, c = i / k;
+          Rs[r + c * KP] = (r <= c) ? Tw[r + c * LDT] : sc_zero<S>();
+        }
+        __syncwarp();
       }
-      __syncwarp();
     }
     DIAF_PHASE(6);
     // an exactly zero column of A-hat (all its tile entries in I_j) is no

@@ -252,6 +252,16 @@ diaf_status diaf_factor_fallbacks(const diaf_factors* F, int32_t* counts, int32_
  * (instrumentation; never fails). */
 long long diaf_launch_count(void);
 
+/* Numbers of apply preparations (first diaf_apply calls on triangular V) in
+ * this process that built the level schedule from V's structure as it
+ * reached the host during the numeric pass (`streamed`: factors of rules
+ * UPPER / LOWER made by diaf_factor or diaf_factor_tuned while no other such
+ * factorisation held the library's one host-mapped copy of V's structure),
+ * and that copied V's structure to the host after the numeric pass
+ * (`copied`: every other case).  Either pointer may be NULL.
+ * (Instrumentation, no passage of the paper; never fails.) */
+void diaf_apply_prep_counts(int64_t* streamed, int64_t* copied);
+
 /* Caps the device memory that the setup and apply paths (diaf_factor,
  * diaf_factor_tuned, diaf_plan_*, diaf_apply and the factor handles they
  * keep) may hold at one time, over all handles of the process: bytes > 0 is
@@ -293,6 +303,14 @@ diaf_status diaf_get_factors(const diaf_factors* F, diaf_csc* W, diaf_csc* V, co
  * copies of W and V and the level schedule of the V solve (the depth of each
  * row in V's dependency graph, computed on the host; this first call
  * allocates and synchronises `stream` -- make it before any stream capture).
+ * For factors of rules UPPER / LOWER made by diaf_factor(_tuned), the column
+ * kernels also write V's row indices into a host-mapped buffer of the
+ * library as each column is finished (the columns of an upper V in
+ * descending order), and this first call builds the schedule from the
+ * columns as they arrive, while the numeric pass still runs.  One
+ * factorisation at a time holds that buffer, from diaf_factor until its
+ * first diaf_apply or diaf_free; the others copy V's structure after the
+ * numeric pass (same schedule, later).
  * Later calls only enqueue two kernels: the level-scheduled triangular solve
  * (one block, a barrier between levels) and the W SpMV.  Errors: EINVAL (V not
  * triangular or zero diagonal -- found by the first call), ENOMEM, ECUDA. */
@@ -341,7 +359,9 @@ diaf_status diaf_apply_static(diaf_factors* F, const void* x, void* y, void* str
 diaf_status diaf_sync(diaf_factors* F, void* stream);
 
 /* Frees F and every device buffer it owns (stream-ordered on the stream F was
- * created on; that stream must still exist).  NULL is ignored.  Never fails. */
+ * created on; that stream must still exist).  When F still holds the host
+ * copy of V's structure (no diaf_apply was made on it), it first waits for
+ * that stream.  NULL is ignored.  Never fails. */
 void diaf_free(diaf_factors* F);
 
 typedef struct diaf_solver diaf_solver; /* opaque: A in row-oriented form for Krylov solves */

@@ -193,6 +193,73 @@ diaf_status check_device() {
   return DIAF_OK;
 }
 
+// ---- V's structure streamed to the host during the numeric pass
+// One pinned buffer per process, mapped into the devices' address space: one
+// word per column first, then V's column pointers (copied after the symbolic
+// pass), then V's row indices, which the column kernels write as each column
+// becomes final before they set the column's word to the owner's generation
+// (system-scope release).  One factorisation at a time owns it, so the first
+// apply can build the level schedule from the columns as they arrive, while
+// the numeric pass still runs; a factorisation that finds it taken goes
+// without (its apply copies V's structure after the numeric pass).
+struct Mirror {
+  std::mutex mu;
+  unsigned char* buf = nullptr;
+  size_t cap = 0;    // bytes
+  size_t words = 0;  // columns the word area holds (zeroed when allocated)
+  uint32_t gen = 0;
+  bool busy = false;
+};
+Mirror g_mirror;
+std::atomic<long long> g_prep_streamed{0}, g_prep_copied{0};
+
+// Takes the mirror for F (F->n, F->nnz_v known) when it is free; grows it
+// when it is too small.  Returns false (F without a mirror) when it is taken
+// or cannot be had.
+bool mirror_acquire(diaf_factors* F) {
+  const size_t n = (size_t)F->n, nnz = (size_t)F->nnz_v;
+  std::lock_guard<std::mutex> lock(g_mirror.mu);
+  if (g_mirror.busy) return false;
+  auto bytes_for = [&](size_t words) { return sizeof(uint32_t) * words + sizeof(int32_t) * (words + 1 + nnz); };
+  if (n > g_mirror.words || bytes_for(g_mirror.words) > g_mirror.cap) {
+    // no kernel writes into the old buffer: every owner released it only
+    // after reading all of its columns or synchronising its stream
+    if (g_mirror.buf) cudaFreeHost(g_mirror.buf);
+    g_mirror.buf = nullptr;
+    g_mirror.cap = g_mirror.words = 0;
+    const size_t words = n + n / 4;
+    const size_t want = bytes_for(words) + sizeof(int32_t) * (nnz / 4);
+    if (cudaHostAlloc((void**)&g_mirror.buf, want, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+      (void)cudaGetLastError();
+      g_mirror.buf = nullptr;
+      return false;
+    }
+    std::memset(g_mirror.buf, 0, sizeof(uint32_t) * words);
+    g_mirror.cap = want;
+    g_mirror.words = words;
+  }
+  if (++g_mirror.gen == 0) {  // wrapped: no word may hold a stale generation equal to a new one
+    std::memset(g_mirror.buf, 0, sizeof(uint32_t) * g_mirror.words);
+    g_mirror.gen = 1;
+  }
+  F->mir_word = reinterpret_cast<uint32_t*>(g_mirror.buf);
+  F->mir_cp = reinterpret_cast<int32_t*>(F->mir_word + g_mirror.words);
+  F->mir_ri = F->mir_cp + (n + 1);
+  F->mir_gen = g_mirror.gen;
+  F->mirror = true;
+  g_mirror.busy = true;
+  return true;
+}
+
+// Gives the mirror back.  The caller has read every column of it, or has
+// synchronised F's stream: none of F's kernels writes into it any more.
+void mirror_release(diaf_factors* F) {
+  if (!F->mirror) return;
+  std::lock_guard<std::mutex> lock(g_mirror.mu);
+  g_mirror.busy = false;
+  F->mirror = false;
+}
+
 }  // namespace
 
 extern "C" {
@@ -214,6 +281,10 @@ const char* diaf_last_error(void) { return g_last_error.c_str(); }
 
 void diaf_free(diaf_factors* F) {
   if (!F) return;
+  if (F->mirror) {  // an apply never read it: the numeric pass may still write into it
+    (void)cudaStreamSynchronize(F->stream);
+    mirror_release(F);
+  }
   for (void* p : F->owned) diaf_dev_free(p, F->stream);
   for (cudaEvent_t e : F->ev)
     if (e) cudaEventDestroy(e);
@@ -221,6 +292,11 @@ void diaf_free(diaf_factors* F) {
 }
 
 long long diaf_launch_count(void) { return g_launches.load(); }
+
+void diaf_apply_prep_counts(int64_t* streamed, int64_t* copied) {
+  if (streamed) *streamed = g_prep_streamed.load();
+  if (copied) *copied = g_prep_copied.load();
+}
 
 diaf_status diaf_set_device_memory_limit(int64_t bytes) {
   if (bytes < 0) return fail(DIAF_EINVAL, "the limit must be >= 0 (0: no limit)");
@@ -650,7 +726,21 @@ diaf_status diaf_factor_tuned(const diaf_csc* A, const diaf_pattern* PW, const d
   NumericPlan np;
   st = symbolic_pass(A, PW, V, alg, prec, tuning, s, F, pool, np);
   if (st != DIAF_OK) return st;
-  DIAF_CU(cudaEventRecord(F->ev[1], s));
+  // a triangular V by rule: its structure goes to the host column by column
+  // during the numeric pass (the columns of an upper V in descending order,
+  // the order in which the level schedule visits them)
+  if ((V->rule == DIAF_RULE_UPPER || V->rule == DIAF_RULE_LOWER) && F->n > 0 && mirror_acquire(F)) {
+    int32_t *dri = nullptr;
+    uint32_t* dword = nullptr;
+    DIAF_CU(cudaHostGetDevicePointer((void**)&dri, F->mir_ri, 0));
+    DIAF_CU(cudaHostGetDevicePointer((void**)&dword, F->mir_word, 0));
+    DIAF_CU(cudaMemcpyAsync(F->mir_cp, F->Vcp, sizeof(int32_t) * (F->n + 1), cudaMemcpyDeviceToHost, s));
+    np.ca.Hri = dri;
+    np.ca.Hgen = dword;
+    np.ca.gen = F->mir_gen;
+    np.ca.list_desc = V->rule == DIAF_RULE_UPPER;
+  }
+  DIAF_CU(cudaEventRecord(F->ev[1], s));  // after the copy of V's column pointers
   st = enqueue_numeric(F, np, s, true);
   if (st != DIAF_OK) return st;
   DIAF_CU(cudaEventRecord(F->ev[2], s));
@@ -906,6 +996,56 @@ int level_schedule_host(int n, const int32_t* cp, const int32_t* ri, int32_t* le
   return r;
 }
 
+// True once event e has completed (or failed: a waiter then stops waiting).
+bool event_passed(cudaEvent_t e) {
+  if (cudaEventQuery(e) != cudaErrorNotReady) return true;
+  if (cudaPeekAtLastError() == cudaErrorNotReady) (void)cudaGetLastError();  // not an error
+  return false;
+}
+
+// The level schedule of a triangular V whose columns reach the host during
+// the numeric pass (the mirror): the columns are visited in the solve's order
+// (descending for an upper V, ascending for a lower one), each once its word
+// holds the owner's generation `gen` (acquire load, after which its rows are
+// visible).  lev[j] is final when the walk reaches column j, so the rows of
+// every level are counted on the way (cnt[0..nlev)) and row j's place among
+// them is rank[j] (the rows of a level in the walk's order).  Returns 0, 1 (an entry
+// on the wrong side of the diagonal), 2 (a diagonal entry missing), 3 (a row
+// index out of range) or 4 (`done`, the end of the numeric pass, passed while
+// a column had not arrived).  After 1, 3 or 4 the kernels may still write.
+int level_walk_streamed(int n, const int32_t* cp, const int32_t* ri, const uint32_t* word, uint32_t gen, bool up,
+                        cudaEvent_t done, int32_t* lev, int32_t* rank, int32_t* cnt, int* nlev) {
+  auto arrived = [&](int j) { return __atomic_load_n(word + j, __ATOMIC_ACQUIRE) == gen; };
+  for (int i = 0; i < n; ++i) lev[i] = 0;
+  int nl = 0;
+  bool nodiag = false;
+  for (int step = 0; step < n; ++step) {
+    const int j = up ? n - 1 - step : step;
+    if (!arrived(j)) {
+      for (unsigned spin = 1; !arrived(j); ++spin) {
+        if ((spin & 1023u) == 0 && event_passed(done)) {
+          if (arrived(j)) break;  // the pass's writes are all visible once it has ended
+          return 4;
+        }
+      }
+    }
+    const int lj = lev[j];
+    while (nl <= lj) cnt[nl++] = 0;
+    rank[j] = cnt[lj]++;
+    bool d = false;
+    for (int p = cp[j]; p < cp[j + 1]; ++p) {
+      const int i = ri[p];
+      if (i < 0 || i >= n) return 3;
+      if (i == j) { d = true; continue; }
+      if (up ? i > j : i < j) return 1;
+      if (lev[i] <= lj) lev[i] = lj + 1;
+    }
+    nodiag |= !d;
+  }
+  *nlev = nl;
+  return nodiag ? 2 : 0;
+}
+
 // Marks the end of the copies out of the staging buffer on stream s.
 cudaError_t stage_release(cudaStream_t s) {
   int dev = 0;
@@ -936,17 +1076,29 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   // then ptr and order on the way back): the level schedule is computed from
   // it on the host while the device builds the row-oriented copies of V and
   // W and checks V's diagonal
+  // (or, when F owns the mirror, V's structure is already on its way there)
+  const bool mir = F->mirror;
   std::lock_guard<std::mutex> stage_lock(g_stage.mu);
   const size_t n1 = (size_t)n + 1;
-  unsigned char* stage = stage_get(sizeof(int32_t) * (3 * n1 + (size_t)F->nnz_v) + sizeof(uint32_t));
-  if (!stage) return fail(DIAF_ENOMEM, "pinned host staging for the level schedule");
-  int32_t* cp = reinterpret_cast<int32_t*>(stage);
-  int32_t* ri = cp + n1;
-  int32_t* ptr = ri + F->nnz_v;     // level pointers (at most n + 1)
-  int32_t* order = ptr + n1;        // rows level by level (n)
-  uint32_t* hp = reinterpret_cast<uint32_t*>(order + n1);
-  DIAF_CU(cudaMemcpyAsync(cp, F->Vcp, sizeof(int32_t) * n1, cudaMemcpyDeviceToHost, s));
-  if (F->nnz_v > 0) DIAF_CU(cudaMemcpyAsync(ri, F->Vri, sizeof(int32_t) * F->nnz_v, cudaMemcpyDeviceToHost, s));
+  const size_t nri = mir ? 0 : (size_t)F->nnz_v;
+  unsigned char* stage = stage_get(sizeof(int32_t) * (5 * n1 + nri) + sizeof(uint32_t));
+  if (!stage) {
+    if (mir) {
+      (void)cudaStreamSynchronize(s);
+      mirror_release(F);
+    }
+    return fail(DIAF_ENOMEM, "pinned host staging for the level schedule");
+  }
+  int32_t* cp = mir ? F->mir_cp : reinterpret_cast<int32_t*>(stage);
+  int32_t* ri = mir ? F->mir_ri : reinterpret_cast<int32_t*>(stage) + n1;
+  int32_t* ptr = reinterpret_cast<int32_t*>(stage) + (mir ? 0 : n1 + nri);  // level pointers (at most n + 1)
+  int32_t* lev = ptr + n1;          // level of every row (n)
+  int32_t* rank = lev + n1;         // place of every row within its level (n)
+  uint32_t* hp = reinterpret_cast<uint32_t*>(rank + n1);
+  if (!mir) {
+    DIAF_CU(cudaMemcpyAsync(cp, F->Vcp, sizeof(int32_t) * n1, cudaMemcpyDeviceToHost, s));
+    if (F->nnz_v > 0) DIAF_CU(cudaMemcpyAsync(ri, F->Vri, sizeof(int32_t) * F->nnz_v, cudaMemcpyDeviceToHost, s));
+  }
   PT_DEV(s);
   cudaEvent_t ev[2];
   DIAF_CU(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
@@ -979,11 +1131,12 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   // the level-ordered copies' buffers (sizes known now; the level count is
   // at most n), so that only copies and kernels follow the host's pass
   LevelCsr& Vl = F->Vl;
-  int32_t *dorder = nullptr, *pos = nullptr;
+  int32_t *dorder = nullptr, *pos = nullptr, *dlev = nullptr;
   Vl.n = n;
   Vl.nnz = F->nnz_v - n;
   if (ce == cudaSuccess) ce = F->alloc(&Vl.lvlptr, n + 1);
   if (ce == cudaSuccess) ce = F->alloc(&dorder, n);
+  if (ce == cudaSuccess) ce = F->alloc(&dlev, 2 * (size_t)n);  // levels, then ranks
   if (ce == cudaSuccess) ce = F->alloc(&pos, n);
   if (ce == cudaSuccess) ce = F->alloc(&Vl.rowptr, n + 1);
   if (ce == cudaSuccess) ce = F->alloc(&Vl.colidx, Vl.nnz > 0 ? Vl.nnz : 0);
@@ -995,23 +1148,57 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   int32_t* const wl_colidx = F->Wl.colidx;
   PT_DEV(s);
   PT_HOST();
-  // wait for the copies even after an error: they write into the staging buffer
-  cudaError_t se = cudaEventSynchronize(ev[0]);
+  // wait for the copies even after an error: they write into the staging
+  // buffer (the mirror's columns are read as they arrive instead)
+  cudaError_t se = mir ? cudaSuccess : cudaEventSynchronize(ev[0]);
   PT_HOST();
   if (ce != cudaSuccess || se != cudaSuccess) {
     (void)cudaStreamSynchronize(s);
+    mirror_release(F);
     cudaEventDestroy(ev[0]);
     cudaEventDestroy(ev[1]);
     DIAF_CU(ce);
     DIAF_CU(se);
   }
   // level of every row (host, O(nnz)); the device checks the diagonal's values meanwhile
-  // host scratch reused across calls of this thread (the pass sets every entry)
-  static thread_local std::vector<int32_t> lev, cur;
-  if (lev.size() < (size_t)n) lev.resize(n);
+  // host scratch reused across calls of this thread: rows per level
+  static thread_local std::vector<int32_t> cur;
+  if (cur.size() < (size_t)n) cur.resize(n);
   int nlev = 0;
   bool vup = true;
-  const int ls = level_schedule_host(n, cp, ri, lev.data(), &nlev, &vup);
+  int ls = -1;
+  bool counted = false;  // cur[0..nlev) holds the rows per level, rank[] the places
+  if (mir) {
+    // V's column pointers reached the host before the numeric pass began
+    se = cudaEventSynchronize(F->ev[1]);
+    if (se == cudaSuccess) {
+      vup = F->rule == DIAF_RULE_UPPER;
+      ls = level_walk_streamed(n, cp, ri, F->mir_word, F->mir_gen, vup, F->ev[2], lev, rank, cur.data(), &nlev);
+    }
+    if (ls == 0 || ls == 2) {
+      counted = true;
+      g_prep_streamed.fetch_add(1, std::memory_order_relaxed);
+    } else {
+      // not every column arrived, or an entry is out of place: V's whole
+      // structure once the numeric pass has ended
+      se = cudaStreamSynchronize(s);
+      if (se == cudaSuccess && F->nnz_v > 0)
+        se = cudaMemcpy(ri, F->Vri, sizeof(int32_t) * F->nnz_v, cudaMemcpyDeviceToHost);
+      if (se != cudaSuccess) {
+        mirror_release(F);
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+        DIAF_CU(se);
+      }
+      ls = -1;
+    }
+  }
+  if (ls < 0) {
+    ls = level_schedule_host(n, cp, ri, lev, &nlev, &vup);
+    g_prep_copied.fetch_add(1, std::memory_order_relaxed);
+  }
+  // every column of the mirror has been read (or the stream synchronised)
+  mirror_release(F);
   F->v_upper = vup;
   if (ls == 1 || ls == 3) {
     (void)cudaStreamSynchronize(s);
@@ -1019,32 +1206,50 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
     cudaEventDestroy(ev[1]);
     return fail(DIAF_EINVAL, ls == 1 ? "V is not triangular" : "V has a row index out of range");
   }
-  const bool nodiag = ls == 2;
+  if (ls == 2) {
+    (void)cudaStreamSynchronize(s);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    return fail(DIAF_EINVAL, "V has a zero or missing diagonal entry");
+  }
+  PT_HOST();
+  if (!counted) {  // rows per level, and the places within a level in increasing row order
+    for (int l = 0; l < nlev; ++l) cur[l] = 0;
+    for (int i = 0; i < n; ++i) rank[i] = cur[lev[i]]++;
+  }
+  ptr[0] = 0;
+  Vl.maxw = 0;
+  for (int l = 0; l < nlev; ++l) {
+    ptr[l + 1] = ptr[l] + cur[l];
+    Vl.maxw = std::max(Vl.maxw, cur[l]);
+  }
+  Vl.nlev = nlev;
+  // the device orders the rows (order[ptr[lev[i]] + rank[i]] = i) and builds
+  // the level-ordered copies; the zero-diagonal check is read after that
+  ce = cudaMemcpyAsync(Vl.lvlptr, ptr, sizeof(int32_t) * (nlev + 1), cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(dlev, lev, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(dlev + n, rank, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s);
+  PT_DEV(s);
+  if (ce == cudaSuccess) ce = stage_release(s);  // the next user of the staging buffer waits for these copies
+  if (ce != cudaSuccess) {
+    (void)cudaStreamSynchronize(s);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    DIAF_CU(ce);
+  }
+  ce = level_order(n, dlev, dlev + n, Vl.lvlptr, dorder, s);
+  if (ce == cudaSuccess) ce = csr_level_permute(F->Vr, cplx, dorder, pos, work, Vl, s);
+  F->Wl = F->Wr;
+  F->Wl.colidx = wl_colidx;
+  if (ce == cudaSuccess) ce = remap_columns(F->nnz_w, pos, F->Wr.colidx, F->Wl.colidx, s);
+  PT_DEV(s);
   PT_HOST();
   se = cudaEventSynchronize(ev[1]);
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
+  DIAF_CU(ce);
   DIAF_CU(se);
-  if (nodiag || (*hp & 4u)) return fail(DIAF_EINVAL, "V has a zero or missing diagonal entry");
-  for (int l = 0; l <= nlev; ++l) ptr[l] = 0;
-  for (int i = 0; i < n; ++i) ptr[lev[i] + 1] += 1;
-  for (int l = 0; l < nlev; ++l) ptr[l + 1] += ptr[l];
-  if (cur.size() < (size_t)nlev) cur.resize(nlev);
-  std::copy(ptr, ptr + nlev, cur.begin());
-  for (int i = 0; i < n; ++i) order[cur[lev[i]]++] = i;
-  PT_HOST();
-  Vl.nlev = nlev;
-  Vl.maxw = 0;
-  for (int l = 0; l < nlev; ++l) Vl.maxw = std::max(Vl.maxw, ptr[l + 1] - ptr[l]);
-  DIAF_CU(cudaMemcpyAsync(Vl.lvlptr, ptr, sizeof(int32_t) * (nlev + 1), cudaMemcpyHostToDevice, s));
-  if (n > 0) DIAF_CU(cudaMemcpyAsync(dorder, order, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
-  PT_DEV(s);
-  DIAF_CU(stage_release(s));  // the next user of the staging buffer waits for these copies
-  DIAF_CU(csr_level_permute(F->Vr, cplx, dorder, pos, work, Vl, s));
-  F->Wl = F->Wr;
-  F->Wl.colidx = wl_colidx;
-  DIAF_CU(remap_columns(F->nnz_w, pos, F->Wr.colidx, F->Wl.colidx, s));
-  PT_DEV(s);
+  if (*hp & 4u) return fail(DIAF_EINVAL, "V has a zero or missing diagonal entry");
   PT_HOST();
   F->apply_ready = true;
   F->solve_cold = true;

@@ -67,7 +67,18 @@ struct ColArgs {
   uint32_t* status;
   unsigned long long* phase;  // profiling builds only: per-phase cycle counters (or null)
   void* tile_scratch;         // mixed warp kernels: one FP64 tile per resident warp (global memory)
+  // V's structure streamed to the host during the numeric pass (or all null / 0):
+  int list_desc;              // 1: the lists are taken from their end (descending columns, upper V)
+  int32_t* Hri;               // host-mapped copy of Vri, written as each column becomes final
+  uint32_t* Hgen;             // host-mapped word per column: set to gen after the column's rows
+  uint32_t gen;
 };
+
+// Column of the idx-th list entry taken by a persistent kernel: from the
+// list's end when the host walks V's columns in descending order.
+__device__ __forceinline__ int list_at(const ColArgs& a, int count, int idx) {
+  return a.list[a.list_desc ? count - 1 - idx : idx];
+}
 
 // ------------------------------------------------------------------ shared steps
 // Per-warp index scratch for the parts common to both kernels.
@@ -286,6 +297,12 @@ __device__ void finish_column(const ColArgs& a, int j, int k, int m, int l, int 
   if (lane == 0) {
     a.res[j] = resj;
     a.flags[j] = flags | a.extra_flags;
+  }
+  if (a.Hri) {  // the final I_j to the host: rows, then the column's word
+    for (int t = lane; t < l; t += DIAF_WARP) a.Hri[v0 + t] = ix.Is[t];
+    __threadfence_system();
+    __syncwarp();
+    if (lane == 0) store_release_sys(a.Hgen + j, a.gen);
   }
   __syncwarp();
 }
@@ -535,6 +552,6 @@ __global__ void column_warp_kernel(ColArgs a) {
     if (lane == 0) idx = atomicAdd(a.work_counter, 1);
     idx = __shfl_sync(DIAF_FULL, idx, 0);
     if (idx >= count) break;
-    solve_column_warp<S, KMAX, MMAX, ALG>(a, a.list[idx], smem, lane);
+    solve_column_warp<S, KMAX, MMAX, ALG>(a, list_at(a, count, idx), smem, lane);
   }
 }

@@ -468,6 +468,12 @@ __device__ void cta_finish(const ColArgs& a, int j, int k, int m, int l, int jpo
     a.res[j] = resj;
     a.flags[j] = flags | a.extra_flags;
   }
+  if (a.Hri) {  // the final I_j to the host: rows, then the column's word
+    for (int t = tid; t < l; t += kCtaThreads) a.Hri[v0 + t] = Is[t];
+    __threadfence_system();
+    __syncthreads();
+    if (tid == 0) store_release_sys(a.Hgen + j, a.gen);
+  }
   __syncthreads();
 }
 
@@ -755,6 +761,6 @@ __global__ void __launch_bounds__(kCtaThreads) column_cta_kernel(ColArgs a, CtaS
     const int idx = idx_s;
     __syncthreads();
     if (idx >= count) break;
-    solve_column_cta<S, ALG>(a, sc, a.list[idx], smem_raw);
+    solve_column_cta<S, ALG>(a, sc, list_at(a, count, idx), smem_raw);
   }
 }

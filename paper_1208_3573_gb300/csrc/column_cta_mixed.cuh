@@ -826,7 +826,7 @@ __global__ void __launch_bounds__(kCtaThreads, 3) column_cta_mixed_kernel(ColArg
     const int idx = idx_s;
     __syncthreads();
     if (idx >= count) break;
-    const int j = a.list[idx];
+    const int j = list_at(a, count, idx);
     if (!solve_column_cta_mixed(a, sc, j, smem_raw)) {
       if (threadIdx.x == 0) a.fb_list[atomicAdd(a.fb_count, 1)] = j;
     }

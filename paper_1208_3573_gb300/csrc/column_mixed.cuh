@@ -608,7 +608,7 @@ __device__ __forceinline__ void column_mixed_loop(const ColArgs& a) {
     if (lane == 0) idx = atomicAdd(a.work_counter, 1);
     idx = __shfl_sync(DIAF_FULL, idx, 0);
     if (idx >= count) break;
-    solve_column_mixed<S, KMAX, MMAX, ALG>(a, a.list[idx], smem, Ts, Ts + L::kTile, lane);
+    solve_column_mixed<S, KMAX, MMAX, ALG>(a, list_at(a, count, idx), smem, Ts, Ts + L::kTile, lane);
   }
 }
 

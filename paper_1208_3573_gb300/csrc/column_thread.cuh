@@ -745,6 +745,14 @@ __device__ void solve_column_quad(const ColArgs& a, const ThreadArgs& ta, int j,
     a.res[j] = resj;
     a.flags[j] = flags | a.extra_flags;
   }
+  if (a.Hri) {  // the final I_j to the host (the rows as written above), then the column's word
+    if (sub == 0 && !jin) a.Hri[v0 + jpos] = j;
+    for (int r = sub; r < m; r += 4)
+      if ((inI >> r) & 1u) a.Hri[v0 + pos_of(r)] = Rj[r];
+    __threadfence_system();
+    __syncwarp(qm);
+    if (sub == 0) store_release_sys(a.Hgen + j, a.gen);
+  }
   DIAF_PHASE(9);
 }
 
@@ -770,7 +778,7 @@ __global__ void __launch_bounds__(32 * kQuadWarps, 16) column_thread_kernel(ColA
     base = __shfl_sync(DIAF_FULL, base, 0);
     if (base >= count) break;
     const int idx = base + slot;
-    if (idx < count) solve_column_quad<KMAX>(a, ta, a.list[idx], S, D, G, sub, qm);
+    if (idx < count) solve_column_quad<KMAX>(a, ta, list_at(a, count, idx), S, D, G, sub, qm);
     __syncwarp();
   }
 }

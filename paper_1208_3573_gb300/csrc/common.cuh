@@ -17,6 +17,14 @@ enum : uint32_t {
   DEV_ST_SINGULAR = 8u,     // a zero pivot (block LU of V)
 };
 
+// System-scope release store: a host thread that reads *p == v with acquire
+// semantics also sees every write the storing thread (and any thread ordered
+// before it by a barrier and a system fence) made before it, host memory
+// included.
+__device__ __forceinline__ void store_release_sys(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.sys.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // ----------------------------------------------------------------- scalars
 template <class R>
 struct Cx {

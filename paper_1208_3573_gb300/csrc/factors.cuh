@@ -34,6 +34,13 @@ struct diaf_factors {
   cudaEvent_t ev[kEvents] = {};
   bool bucket_ran[kNumBuckets] = {};
   int32_t* fb_counts = nullptr;  // mixed precision: columns per bucket finished by the FP64 kernel
+  // V's structure streamed to the host during the numeric pass (api.cu): set
+  // while this factorisation owns the process's mapped mirror buffer
+  bool mirror = false;
+  int32_t* mir_cp = nullptr;    // host: V's column pointers (n + 1)
+  int32_t* mir_ri = nullptr;    // host: V's row indices (nnz_v), filled by the column kernels
+  uint32_t* mir_word = nullptr; // host: per column, set to mir_gen once column j's rows are there
+  uint32_t mir_gen = 0;
   // apply
   bool apply_ready = false;
   bool solve_cold = false;  // the level-ordered copies were just built: the next solve warms them

@@ -1,45 +1,89 @@
 // Row-oriented sparse operations for the solve phase.
+#include <climits>
+
 #include "plan.cuh"
 #include "sparse.cuh"
 
 namespace {
 
-__global__ void count_rows_kernel(int n, const int32_t* cp, const int32_t* ri, int32_t* cnt) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
+// CSC -> CSR.  kConvLanes lanes per column count the entries of every row
+// and, after the scan, place them (independent loads and atomics across the
+// lanes: the columns are short, so one thread per column would serialise
+// them); the atomics leave each row's entries in no particular order, so one
+// warp per row then sorts them by column.
+constexpr int kConvLanes = 8;
+
+__global__ void count_rows_kernel(int n, const int32_t* __restrict__ cp, const int32_t* __restrict__ ri,
+                                  int32_t* __restrict__ cnt) {
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int j = (int)(gid / kConvLanes), sub = (int)(gid % kConvLanes);
   if (j >= n) return;
-  for (int p = cp[j]; p < cp[j + 1]; ++p) atomicAdd(&cnt[ri[p]], 1);
+  const int e = cp[j + 1];
+  for (int p = cp[j] + sub; p < e; p += kConvLanes) atomicAdd(&cnt[ri[p]], 1);
 }
 
 template <class S>
-__global__ void fill_rows_kernel(int n, const int32_t* cp, const int32_t* ri, const S* v, const int32_t* rowptr,
-                                 int32_t* cursor, int32_t* colidx, S* vals) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void fill_rows_kernel(int n, const int32_t* __restrict__ cp, const int32_t* __restrict__ ri,
+                                 const S* __restrict__ v, const int32_t* __restrict__ rowptr,
+                                 int32_t* __restrict__ cursor, int32_t* __restrict__ colidx, S* __restrict__ vals) {
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int j = (int)(gid / kConvLanes), sub = (int)(gid % kConvLanes);
   if (j >= n) return;
-  for (int p = cp[j]; p < cp[j + 1]; ++p) {
-    int i = ri[p];
-    int pos = rowptr[i] + atomicAdd(&cursor[i], 1);
+  const int e = cp[j + 1];
+  for (int p = cp[j] + sub; p < e; p += kConvLanes) {
+    const int i = ri[p];
+    const int pos = rowptr[i] + atomicAdd(&cursor[i], 1);
     colidx[pos] = j;
     vals[pos] = v[p];
   }
 }
 
-// Rows are short: insertion sort by column makes the order deterministic.
+// One warp per row: a row of up to 32 entries is sorted by column with a
+// bitonic network of shuffles (each value follows its column through its
+// source position); a longer row by insertion sort in lane 0.  The result is
+// the same whatever order the atomics left.
 template <class S>
-__global__ void sort_rows_kernel(int n, const int32_t* rowptr, int32_t* colidx, S* vals) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int a = rowptr[i], b = rowptr[i + 1];
-  for (int p = a + 1; p < b; ++p) {
-    int c = colidx[p];
-    S v = vals[p];
-    int q = p - 1;
-    while (q >= a && colidx[q] > c) {
-      colidx[q + 1] = colidx[q];
-      vals[q + 1] = vals[q];
-      --q;
+__global__ void sort_rows_kernel(int n, const int32_t* __restrict__ rowptr, int32_t* __restrict__ colidx,
+                                 S* __restrict__ vals) {
+  const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (row >= n) return;  // whole warps: blockDim.x is a multiple of 32
+  const int a = rowptr[row], len = rowptr[row + 1] - a;
+  if (len <= 1) return;
+  if (len <= 32) {
+    int key = lane < len ? colidx[a + lane] : INT_MAX;
+    int src = lane;
+    for (int size = 2; size <= 32; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        const int ok = __shfl_xor_sync(DIAF_FULL, key, stride);
+        const int os = __shfl_xor_sync(DIAF_FULL, src, stride);
+        const bool keep_min = ((lane & stride) == 0) == ((lane & size) == 0);
+        const bool less = ok < key || (ok == key && os < src);  // (ok, os) before (key, src)
+        if (keep_min ? less : !less) {
+          key = ok;
+          src = os;
+        }
+      }
     }
-    colidx[q + 1] = c;
-    vals[q + 1] = v;
+    S v = sc_zero<S>();
+    if (lane < len) v = vals[a + src];
+    __syncwarp();
+    if (lane < len) {
+      colidx[a + lane] = key;
+      vals[a + lane] = v;
+    }
+  } else if (lane == 0) {
+    for (int p = a + 1; p < a + len; ++p) {
+      const int c = colidx[p];
+      const S v = vals[p];
+      int q = p - 1;
+      while (q >= a && colidx[q] > c) {
+        colidx[q + 1] = colidx[q];
+        vals[q + 1] = vals[q];
+        --q;
+      }
+      colidx[q + 1] = c;
+      vals[q + 1] = v;
+    }
   }
 }
 
@@ -49,14 +93,15 @@ cudaError_t csc_to_csr_t(int n, int64_t nnz, const int32_t* cp, const int32_t* r
   if (n <= 0) return cudaSuccess;
   int32_t* cnt = work;
   int32_t* bs = work + n;
+  const int lane_blocks = (int)(((int64_t)n * kConvLanes + 255) / 256);
   cudaMemsetAsync(cnt, 0, sizeof(int32_t) * n, s);
-  count_rows_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, cp, ri, cnt);
+  count_rows_kernel<<<lane_blocks, 256, 0, s>>>(n, cp, ri, cnt);
   DIAF_COUNT_LAUNCH();
   exclusive_scan_i32(cnt, rowptr, n, bs, s);
   cudaMemsetAsync(cnt, 0, sizeof(int32_t) * n, s);
-  fill_rows_kernel<S><<<ceil_div(n, 256), 256, 0, s>>>(n, cp, ri, v, rowptr, cnt, colidx, vals);
+  fill_rows_kernel<S><<<lane_blocks, 256, 0, s>>>(n, cp, ri, v, rowptr, cnt, colidx, vals);
   DIAF_COUNT_LAUNCH();
-  sort_rows_kernel<S><<<ceil_div(n, 256), 256, 0, s>>>(n, rowptr, colidx, vals);
+  sort_rows_kernel<S><<<ceil_div(n, 8), 256, 0, s>>>(n, rowptr, colidx, vals);
   DIAF_COUNT_LAUNCH();
   return cudaGetLastError();
 }
@@ -127,6 +172,12 @@ __global__ void fill_levels_kernel(int n, const int32_t* __restrict__ order, con
   }
   pdinv[p] = (1.0 / sc_abs2(d)) * sc_conj(d);
   xrow[p] = i;
+}
+
+__global__ void level_order_kernel(int n, const int32_t* __restrict__ lev, const int32_t* __restrict__ rank,
+                                   const int32_t* __restrict__ lvlptr, int32_t* __restrict__ order) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) order[lvlptr[lev[i]] + rank[i]] = i;
 }
 
 __global__ void remap_cols_kernel(int64_t nnz, const int32_t* __restrict__ pos, const int32_t* __restrict__ cin,
@@ -363,6 +414,14 @@ cudaError_t csr_level_permute(const Csr& V, bool cplx, const int32_t* order, int
     fill_levels_kernel<double><<<ceil_div(n, 256), 256, 0, s>>>(n, order, pos, V.rowptr, V.colidx,
                                                               (const double*)V.vals, L.rowptr, L.colidx,
                                                               (double*)L.vals, (double*)L.dinv, L.xrow);
+  DIAF_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+cudaError_t level_order(int n, const int32_t* lev, const int32_t* rank, const int32_t* lvlptr, int32_t* order,
+                        cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  level_order_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, lev, rank, lvlptr, order);
   DIAF_COUNT_LAUNCH();
   return cudaGetLastError();
 }

@@ -52,6 +52,10 @@ cudaError_t csr_level_permute(const Csr& V, bool cplx, const int32_t* order, int
 
 // cout[e] = pos[cin[e]] (column indices renumbered to level positions).
 cudaError_t remap_columns(int64_t nnz, const int32_t* pos, const int32_t* cin, int32_t* cout, cudaStream_t s);
+// The rows of V level by level: order[lvlptr[lev[i]] + rank[i]] = i (rank[i]:
+// row i's place among the rows of its level).
+cudaError_t level_order(int n, const int32_t* lev, const int32_t* rank, const int32_t* lvlptr, int32_t* order,
+                        cudaStream_t s);
 
 // t = V^-1 x by level scheduling on L: one block, a barrier between levels;
 // t in level order (t[p] belongs to row xrow[p]).  warm: read all of the

@@ -139,6 +139,8 @@ def lib() -> ctypes.CDLL:
                                  ctypes.POINTER(SolveInfo_t)]
         L.diaf_factor_timings.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]
         L.diaf_launch_count.restype = ctypes.c_longlong
+        L.diaf_apply_prep_counts.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+        L.diaf_apply_prep_counts.restype = None
         L.diaf_set_device_memory_limit.argtypes = [ctypes.c_int64]
         L.diaf_device_memory_in_use.restype = ctypes.c_int64
         L.diaf_factor_fallbacks.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]
@@ -323,6 +325,15 @@ class Factors:
 def launch_count() -> int:
     """Kernels launched by libdiaf.so in this process so far."""
     return int(lib().diaf_launch_count())
+
+
+def apply_prep_counts() -> tuple:
+    """(streamed, copied): apply preparations that built V's level schedule
+    from V's structure streamed to the host during the numeric pass, and
+    those that copied it after the pass."""
+    a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+    lib().diaf_apply_prep_counts(ctypes.byref(a), ctypes.byref(b))
+    return int(a.value), int(b.value)
 
 
 def set_device_memory_limit(nbytes: int) -> None:

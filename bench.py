@@ -50,12 +50,10 @@ def metric_name(workload: str, alg: str) -> str:
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# the dominant numeric kernel, from one ncu capture of the current kernel on
-# the workload (workload name, alg, prec); other configurations report None.
-# DRAM bytes (read + write) per launch of the numeric kernel, from one ncu capture of the current
-# kernel per (workload, algorithm, precision) (profiles/); None elsewhere.
+# the dominant numeric kernel, from one ncu capture of the current kernel per
+# (workload, algorithm, precision) (profiles/); None elsewhere.
 TRAFFIC = {
-    ("convdiff2d_256x256_Wp2", "S", "mixed32"): 27_296_000 + 24_675_328,   # column_thread_kernel<16>
+    ("convdiff2d_256x256_Wp2", "S", "mixed32"): 27_404_544 + 25_064_704,   # column_thread_kernel<16>
     ("convdiff2d_256x256_Wp2", "S", "fp64"): 24_370_944 + 768,             # column_warp_kernel<double,16,32,S>
     ("helmholtz2d_512x512", "S", "mixed32"): 133_556_736 + 47_571_456,     # column_mixed_kernel<Cx<float>,16,32,S>
 }
@@ -419,7 +417,7 @@ def whole_job_rate(units_per_rank: int, ms_local: float, world: int) -> tuple[fl
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="diaf", choices=["diaf", "reference"])
     ap.add_argument("--workload", default="convdiff256_A2")

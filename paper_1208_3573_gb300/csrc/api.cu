@@ -211,6 +211,7 @@ struct Mirror {
   bool busy = false;
 };
 Mirror g_mirror;
+constexpr int kMirrorDevices = 64;
 std::atomic<long long> g_prep_streamed{0}, g_prep_copied{0};
 
 // Takes the mirror for F (F->n, F->nnz_v known) when it is free; grows it
@@ -251,6 +252,24 @@ bool mirror_acquire(diaf_factors* F) {
   return true;
 }
 
+// The library's side stream on the current device (created on first use;
+// nullptr when it cannot be had, and the caller stays on its own stream).
+cudaStream_t side_stream() {
+  static std::mutex mu;
+  static cudaStream_t st[kMirrorDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMirrorDevices) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!st[dev] && cudaStreamCreateWithFlags(&st[dev], cudaStreamNonBlocking) != cudaSuccess) {
+    (void)cudaGetLastError();
+    st[dev] = nullptr;
+  }
+  return st[dev];
+}
+
 // Gives the mirror back.  The caller has read every column of it, or has
 // synchronised F's stream: none of F's kernels writes into it any more.
 void mirror_release(diaf_factors* F) {
@@ -285,6 +304,9 @@ void diaf_free(diaf_factors* F) {
     (void)cudaStreamSynchronize(F->stream);
     mirror_release(F);
   }
+  if (F->wev[1]) (void)cudaStreamWaitEvent(F->stream, F->wev[1], 0);  // F's side-stream work first
+  for (cudaEvent_t e : F->wev)
+    if (e) cudaEventDestroy(e);
   for (void* p : F->owned) diaf_dev_free(p, F->stream);
   for (cudaEvent_t e : F->ev)
     if (e) cudaEventDestroy(e);
@@ -1126,8 +1148,21 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   if (ce == cudaSuccess) ce = F->alloc(&F->Wr.rowptr, n + 1);
   if (ce == cudaSuccess) ce = F->alloc(&F->Wr.colidx, F->nnz_w);
   if (ce == cudaSuccess) ce = F->alloc((char**)&F->Wr.vals, esz * F->nnz_w);
+  // W's row-oriented copy on the side stream: the V solve occupies one SM,
+  // the others build W meanwhile (its own scratch; the first SpMV waits)
+  cudaStream_t ws = side_stream();
+  int32_t* wwork = work;
+  if (ws && ce == cudaSuccess) {
+    ce = F->alloc(&wwork, n + scan_blocksums_size(n));
+    for (int i = 0; i < 2 && ce == cudaSuccess; ++i)
+      if (!F->wev[i]) ce = cudaEventCreateWithFlags(&F->wev[i], cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventRecord(F->wev[0], s);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(ws, F->wev[0], 0);
+  }
+  cudaStream_t wsx = ws ? ws : s;
   if (ce == cudaSuccess)
-    ce = csc_to_csr(n, F->nnz_w, F->Wcp, F->Wri, F->Wv, cplx, F->Wr.rowptr, F->Wr.colidx, F->Wr.vals, work, s);
+    ce = csc_to_csr(n, F->nnz_w, F->Wcp, F->Wri, F->Wv, cplx, F->Wr.rowptr, F->Wr.colidx, F->Wr.vals, wwork, wsx);
+  if (ws && ce == cudaSuccess) ce = cudaEventRecord(F->wev[1], ws);  // diaf_free waits for it
   // the level-ordered copies' buffers (sizes known now; the level count is
   // at most n), so that only copies and kernels follow the host's pass
   LevelCsr& Vl = F->Vl;
@@ -1241,7 +1276,15 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   if (ce == cudaSuccess) ce = csr_level_permute(F->Vr, cplx, dorder, pos, work, Vl, s);
   F->Wl = F->Wr;
   F->Wl.colidx = wl_colidx;
-  if (ce == cudaSuccess) ce = remap_columns(F->nnz_w, pos, F->Wr.colidx, F->Wl.colidx, s);
+  if (ws) {  // W's columns renumbered to V's level order on the side stream, after V's permutation
+    if (ce == cudaSuccess) ce = cudaEventRecord(F->wev[0], s);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(ws, F->wev[0], 0);
+  }
+  if (ce == cudaSuccess) ce = remap_columns(F->nnz_w, pos, F->Wr.colidx, F->Wl.colidx, wsx);
+  if (ws && ce == cudaSuccess) {
+    ce = cudaEventRecord(F->wev[1], ws);
+    F->w_pending = ce == cudaSuccess;
+  }
   PT_DEV(s);
   PT_HOST();
   se = cudaEventSynchronize(ev[1]);
@@ -1298,6 +1341,10 @@ diaf_status diaf_apply(diaf_factors* F, const void* x, void* y, void* stream) {
   DIAF_CU(trsv_levels_perm(F->Vl, cplx, x, F->tbuf, s, F->solve_cold));
   F->solve_cold = false;
   PT_DEV(s);
+  if (F->w_pending) {  // W's row-oriented copy, built on the side stream during the solve
+    DIAF_CU(cudaStreamWaitEvent(s, F->wev[1], 0));
+    F->w_pending = false;
+  }
   DIAF_CU(csr_spmv(F->Wl, cplx, F->tbuf, y, s));
   PT_DEV(s);
   return DIAF_OK;

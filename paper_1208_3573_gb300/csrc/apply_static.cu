@@ -75,6 +75,11 @@ extern "C" diaf_status diaf_apply_static(diaf_factors* F, const void* x, void* y
   }
   void* t = base;
   const bool cplx = F->dtype == DIAF_C128;
+  if (F->w_pending) {  // the first diaf_apply stopped before its SpMV: W's copy may still be in the making
+    e = cudaStreamWaitEvent(s, F->wev[1], 0);
+    if (e != cudaSuccess) return fail(DIAF_ECUDA, cudaGetErrorString(e));
+    F->w_pending = false;
+  }
   e = trsv_levels_perm(F->Vl, cplx, x, t, s);
   if (e != cudaSuccess) return fail(DIAF_ECUDA, cudaGetErrorString(e));
   e = csr_spmv(F->Wl, cplx, t, y, s);

@@ -44,6 +44,11 @@ struct diaf_factors {
   // apply
   bool apply_ready = false;
   bool solve_cold = false;  // the level-ordered copies were just built: the next solve warms them
+  // W's row-oriented copy is built on the library's side stream while V is
+  // solved: wev[0] orders the side stream after F's stream, wev[1] marks the
+  // end of F's side-stream work (the first SpMV waits for it: w_pending)
+  cudaEvent_t wev[2] = {};
+  bool w_pending = false;
   bool v_upper = true;
   Csr Vr, Wr;
   void* tbuf = nullptr;

@@ -70,6 +70,15 @@ template <class R> __device__ __forceinline__ Cx<R> operator*(Cx<R> a, Cx<R> b) 
   return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
 }
 template <class R> __device__ __forceinline__ Cx<R> operator*(R s, Cx<R> a) { return {s * a.re, s * a.im}; }
+// acc - a b as fused multiply-adds: one for real scalars, four for complex
+// ones (two independent chains of two, against two products and two
+// subtractions of the plain form).
+__device__ __forceinline__ double sc_msub(double acc, double a, double b) { return fma(-a, b, acc); }
+template <class R> __device__ __forceinline__ Cx<R> sc_msub(Cx<R> acc, Cx<R> a, Cx<R> b) {
+  const R re = fma(a.im, b.im, fma(-a.re, b.re, acc.re));
+  const R im = fma(-a.im, b.re, fma(-a.re, b.im, acc.im));
+  return {re, im};
+}
 template <class R> __device__ __forceinline__ Cx<R> operator*(Cx<R> a, R s) { return {s * a.re, s * a.im}; }
 template <class R> __device__ __forceinline__ Cx<R>& operator+=(Cx<R>& a, Cx<R> b) { a.re += b.re; a.im += b.im; return a; }
 template <class R> __device__ __forceinline__ Cx<R>& operator-=(Cx<R>& a, Cx<R> b) { a.re -= b.re; a.im -= b.im; return a; }

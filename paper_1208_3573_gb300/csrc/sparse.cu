@@ -160,18 +160,29 @@ __global__ void fill_levels_kernel(int n, const int32_t* __restrict__ order, con
   const int i = order[p];
   int k = prow[p];
   S d = sc_zero<S>();
+  for (int e = rowptr[i]; e < rowptr[i + 1]; ++e)
+    if (colidx[e] == i) d = vals[e];
+  const S di = (1.0 / sc_abs2(d)) * sc_conj(d);
+  // the row scaled by 1/diag: the solve then computes t_i = x_i/d - sum (v_ij/d) t_j
   for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
     const int c = colidx[e];
-    if (c == i) {
-      d = vals[e];
-    } else {
+    if (c != i) {
       pcol[k] = pos[c];
-      pval[k] = vals[e];
+      pval[k] = di * vals[e];
       ++k;
     }
   }
-  pdinv[p] = (1.0 / sc_abs2(d)) * sc_conj(d);
+  pdinv[p] = di;
   xrow[p] = i;
+}
+
+// t[p] = x[xrow[p]] / diag of row p (level order): the scaled right-hand
+// side the level solves start from, for all rows at once.
+template <class S>
+__global__ void scale_rhs_kernel(int n, const S* __restrict__ dinv, const int32_t* __restrict__ xrow,
+                                 const S* __restrict__ x, S* __restrict__ t) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) t[p] = dinv[p] * x[xrow[p]];
 }
 
 __global__ void level_order_kernel(int n, const int32_t* __restrict__ lev, const int32_t* __restrict__ rank,
@@ -189,35 +200,34 @@ __global__ void remap_cols_kernel(int64_t nnz, const int32_t* __restrict__ pos, 
 // Level-scheduled solve on the level-ordered matrix: the rows of level l are
 // the contiguous positions lvlptr[l]..lvlptr[l+1], their off-diagonal
 // entries point at positions of earlier levels, t is kept in level order.
-// Nothing a row needs except t depends on the solve, so every thread loads
-// its next row (bounds, x, 1/diag and the first kPrefetch entries) before the
-// barrier that ends the current level; after the barrier only the loads of t
-// remain on the critical path.  Those come from a ring of the last kWin
+// The rows are stored scaled by 1/diag and t starts as the scaled right-hand
+// side (scale_rhs_kernel), so a row is t[p] -= sum v_pj t[j] in place, with
+// no multiplication after the sum.  Nothing a row needs except t of earlier
+// levels depends on the solve, so every thread loads its next row (bounds,
+// its start value t[p] and the first kPrefetch entries) before the barrier
+// that ends the current level; after the barrier only the loads of t remain
+// on the critical path.  Those come from a ring of the last kWin
 // positions of t in shared memory: while level [b, e) is written, slots of
 // positions >= e - kWin are not overwritten, so reads of such positions use
 // the ring and older ones use t in global memory (written too).
 // One pass of the block over everything the solve will read (level-ordered
-// rows, 1/diag, the row map, x), with 16-byte loads (the library's own
-// arrays are 256-byte aligned; x only when it is 16-byte aligned).  The first solve after
-// the level-ordered copies were built ran 0.42 ms instead of 0.29 ms on the
-// 256^2 convection-diffusion V, and a second solve right after it at full
-// speed: the data was cold for the one SM that runs the solve.  With this
-// pass (~30 us) in front, the first solve takes 0.35 ms; later solves skip it.
+// rows and the start values in t), with 16-byte loads (the library's own
+// arrays are 256-byte aligned).  The first solve after the level-ordered
+// copies were built ran 0.42 ms instead of 0.29 ms on the 256^2
+// convection-diffusion V, and a second solve right after it at full speed:
+// the data was cold for the one SM that runs the solve.  With this pass
+// (~30 us) in front, the first solve takes 0.35 ms; later solves skip it.
 template <class S>
 __device__ __forceinline__ void warm_level_data(int n, int nnz, const int32_t* rowptr, const int32_t* colidx,
-                                                const S* vals, const S* dinv, const int32_t* xrow, const S* x,
-                                                S* t) {
+                                                const S* vals, S* t) {
   unsigned acc = 0;
   const int4* r4 = reinterpret_cast<const int4*>(rowptr);
-  const int4* m4 = reinterpret_cast<const int4*>(xrow);
   const int4* c4 = reinterpret_cast<const int4*>(colidx);
-  const int4* d4 = reinterpret_cast<const int4*>(dinv);
   const int4* v4 = reinterpret_cast<const int4*>(vals);
-  const int4* x4 = reinterpret_cast<const int4*>(x);
-  const bool xa = (reinterpret_cast<uintptr_t>(x) & 15) == 0;  // x is the caller's: may be offset
-  for (int i = threadIdx.x; i < n / 4; i += blockDim.x) acc += r4[i].x ^ m4[i].y;
+  const int4* t4 = reinterpret_cast<const int4*>(t);
+  for (int i = threadIdx.x; i < n / 4; i += blockDim.x) acc += r4[i].x;
   for (int i = threadIdx.x; i < nnz / 4; i += blockDim.x) acc += c4[i].z;
-  for (int i = threadIdx.x; i < (int)(n * sizeof(S) / 16); i += blockDim.x) acc += d4[i].w ^ (xa ? x4[i].x : 0);
+  for (int i = threadIdx.x; i < (int)(n * sizeof(S) / 16); i += blockDim.x) acc += t4[i].w;
   for (int i = threadIdx.x; i < (int)(nnz * sizeof(S) / 16); i += blockDim.x) acc += v4[i].y;
   if (acc == 0x9e3779b9u && n < 0) t[0] = sc_zero<S>();  // keeps the loads; never taken
 }
@@ -229,7 +239,6 @@ template <class S>
 __global__ void __launch_bounds__(kLevelThreads, 1)
     trsv_levels_perm_kernel(int nlev, const int32_t* __restrict__ lvlptr, const int32_t* __restrict__ rowptr,
                             const int32_t* __restrict__ colidx, const S* __restrict__ vals,
-                            const S* __restrict__ dinv, const int32_t* __restrict__ xrow, const S* __restrict__ x,
                             S* t, int warm) {
   constexpr int kWin = level_window<S>();
   static_assert((kWin & (kWin - 1)) == 0, "ring size must be a power of two");
@@ -241,13 +250,13 @@ __global__ void __launch_bounds__(kLevelThreads, 1)
     for (int i = threadIdx.x; i <= nlev; i += blockDim.x) sptr[i] = lvlptr[i];
   if (warm) {
     const int n_ = lvlptr[nlev];
-    warm_level_data<S>(n_, rowptr[n_], rowptr, colidx, vals, dinv, xrow, x, t);
+    warm_level_data<S>(n_, rowptr[n_], rowptr, colidx, vals, t);
   }
   __syncthreads();
 #define DIAF_LP(l) (in_smem ? sptr[(l)] : lvlptr[(l)])
   // registers for the first row this thread takes in the coming level
   int rb = 0, re = 0;
-  S xb = sc_zero<S>(), db = sc_zero<S>();
+  S xb = sc_zero<S>();
   int pc[kPrefetch];
   S pv[kPrefetch];
 #define DIAF_FETCH(pp)                                 \
@@ -255,8 +264,7 @@ __global__ void __launch_bounds__(kLevelThreads, 1)
     const int p_ = (pp);                               \
     rb = rowptr[p_];                                   \
     re = rowptr[p_ + 1];                               \
-    xb = x[xrow[p_]];                                  \
-    db = dinv[p_];                                     \
+    xb = t[p_];                                        \
     _Pragma("unroll") for (int q = 0; q < kPrefetch; ++q) { \
       const bool in = rb + q < re;                     \
       pc[q] = in ? colidx[rb + q] : 0;                 \
@@ -273,18 +281,16 @@ __global__ void __launch_bounds__(kLevelThreads, 1)
       S acc = xb;
 #pragma unroll
       for (int q = 0; q < kPrefetch; ++q)
-        if (rb + q < re) acc -= pv[q] * DIAF_TGET(pc[q]);
-      for (int k = rb + kPrefetch; k < re; ++k) acc -= vals[k] * DIAF_TGET(colidx[k]);
-      const S tv = acc * db;
-      t[p] = tv;
-      tw[p & (kWin - 1)] = tv;
+        if (rb + q < re) acc = sc_msub(acc, pv[q], DIAF_TGET(pc[q]));
+      for (int k = rb + kPrefetch; k < re; ++k) acc = sc_msub(acc, vals[k], DIAF_TGET(colidx[k]));
+      t[p] = acc;
+      tw[p & (kWin - 1)] = acc;
     }
     for (p += blockDim.x; p < e; p += blockDim.x) {  // levels wider than the block
-      S acc = x[xrow[p]];
-      for (int k = rowptr[p]; k < rowptr[p + 1]; ++k) acc -= vals[k] * DIAF_TGET(colidx[k]);
-      const S tv = acc * dinv[p];
-      t[p] = tv;
-      tw[p & (kWin - 1)] = tv;
+      S acc = t[p];
+      for (int k = rowptr[p]; k < rowptr[p + 1]; ++k) acc = sc_msub(acc, vals[k], DIAF_TGET(colidx[k]));
+      t[p] = acc;
+      tw[p & (kWin - 1)] = acc;
     }
     if (lv + 1 < nlev) {
       const int nb = e, ne = DIAF_LP(lv + 2);
@@ -301,8 +307,8 @@ __global__ void __launch_bounds__(kLevelThreads, 1)
 // wide, with the row data fetched kDeep levels ahead instead of one.  A
 // thread keeps its rows of the next kDeep levels in kDeep register sets (set
 // k: the levels lv with lv mod kDeep = k).  A row's loads form two dependent
-// round trips (rowptr, xrow and 1/diag; then the entries and x), issued one
-// level apart -- the first right after the set's previous level is done, the
+// round trips (the bounds in rowptr; then the entries and the start value
+// t[p]), issued one level apart -- the first right after the set's previous level is done, the
 // second one level later -- so no thread waits on a load before a barrier.
 constexpr int kDeepThreads = 256;
 constexpr int kDeep = 4;
@@ -311,7 +317,6 @@ template <class S>
 __global__ void __launch_bounds__(kDeepThreads, 1)
     trsv_levels_deep_kernel(int nlev, const int32_t* __restrict__ lvlptr, const int32_t* __restrict__ rowptr,
                             const int32_t* __restrict__ colidx, const S* __restrict__ vals,
-                            const S* __restrict__ dinv, const int32_t* __restrict__ xrow, const S* __restrict__ x,
                             S* t, int warm) {
   constexpr int kWin = level_window<S>();
   extern __shared__ __align__(16) unsigned char level_ring[];
@@ -322,15 +327,15 @@ __global__ void __launch_bounds__(kDeepThreads, 1)
     for (int i = threadIdx.x; i <= nlev; i += blockDim.x) sptr[i] = lvlptr[i];
   if (warm) {
     const int n_ = lvlptr[nlev];
-    warm_level_data<S>(n_, rowptr[n_], rowptr, colidx, vals, dinv, xrow, x, t);
+    warm_level_data<S>(n_, rowptr[n_], rowptr, colidx, vals, t);
   }
   __syncthreads();
 #define DIAF_LP(l) (in_smem ? sptr[(l)] : lvlptr[(l)])
   int rb[kDeep], re[kDeep], xr[kDeep];
-  S xb[kDeep], db[kDeep];
+  S xb[kDeep];
   int pc[kDeep][kPrefetch];
   S pv[kDeep][kPrefetch];
-  // first round trip: the row's bounds, its x index and 1/diag (xr = -1: no row)
+  // first round trip: the row's bounds (xr = its position, -1: no row)
 #define DIAF_STAGE_A(k, lvl)                                      \
   do {                                                            \
     rb[k] = 0;                                                    \
@@ -340,15 +345,14 @@ __global__ void __launch_bounds__(kDeepThreads, 1)
     if (p_ < DIAF_LP((lvl) + 1)) {                                \
       rb[k] = rowptr[p_];                                         \
       re[k] = rowptr[p_ + 1];                                     \
-      xr[k] = xrow[p_];                                           \
-      db[k] = dinv[p_];                                           \
+      xr[k] = p_;                                                 \
     }                                                             \
   } while (0)
-  // second round trip: x and the first kPrefetch entries
+  // second round trip: the start value t[p] and the first kPrefetch entries
 #define DIAF_STAGE_B(k)                                           \
   do {                                                            \
     if (xr[k] >= 0) {                                             \
-      xb[k] = x[xr[k]];                                           \
+      xb[k] = t[xr[k]];                                           \
       _Pragma("unroll") for (int q = 0; q < kPrefetch; ++q) {     \
         const bool in = rb[k] + q < re[k];                        \
         pc[k][q] = in ? colidx[rb[k] + q] : 0;                    \
@@ -375,11 +379,10 @@ __global__ void __launch_bounds__(kDeepThreads, 1)
           S acc = xb[k];
 #pragma unroll
           for (int q = 0; q < kPrefetch; ++q)
-            if (rb[k] + q < re[k]) acc -= pv[k][q] * DIAF_TGET(pc[k][q]);
-          for (int j = rb[k] + kPrefetch; j < re[k]; ++j) acc -= vals[j] * DIAF_TGET(colidx[j]);
-          const S tv = acc * db[k];
-          t[p] = tv;
-          tw[p & (kWin - 1)] = tv;
+            if (rb[k] + q < re[k]) acc = sc_msub(acc, pv[k][q], DIAF_TGET(pc[k][q]));
+          for (int j = rb[k] + kPrefetch; j < re[k]; ++j) acc = sc_msub(acc, vals[j], DIAF_TGET(colidx[j]));
+          t[p] = acc;
+          tw[p & (kWin - 1)] = acc;
         }
 #undef DIAF_TGET
         if (lv + kDeep < nlev) DIAF_STAGE_A(k, lv + kDeep);
@@ -449,14 +452,14 @@ static cudaError_t trsv_levels_perm_t(const LevelCsr& L, const void* x, void* t,
     if (e != cudaSuccess) return e;
     configured_device = dev;
   }
+  scale_rhs_kernel<S><<<ceil_div(L.n, 256), 256, 0, s>>>(L.n, (const S*)L.dinv, L.xrow, (const S*)x, (S*)t);
+  DIAF_COUNT_LAUNCH();
   if (L.maxw <= kDeepThreads)
     trsv_levels_deep_kernel<S><<<1, kDeepThreads, ring, s>>>(L.nlev, L.lvlptr, L.rowptr, L.colidx,
-                                                             (const S*)L.vals, (const S*)L.dinv, L.xrow,
-                                                             (const S*)x, (S*)t, warm ? 1 : 0);
+                                                             (const S*)L.vals, (S*)t, warm ? 1 : 0);
   else
     trsv_levels_perm_kernel<S><<<1, kLevelThreads, ring, s>>>(L.nlev, L.lvlptr, L.rowptr, L.colidx,
-                                                              (const S*)L.vals, (const S*)L.dinv, L.xrow,
-                                                              (const S*)x, (S*)t, warm ? 1 : 0);
+                                                              (const S*)L.vals, (S*)t, warm ? 1 : 0);
   DIAF_COUNT_LAUNCH();
   return cudaGetLastError();
 }

@@ -174,12 +174,52 @@ struct Pool {
     *p = static_cast<T*>(q);
     return cudaSuccess;
   }
+  cudaError_t carve(const Carve& c) {
+    unsigned char* base = nullptr;
+    cudaError_t e = get(&base, c.total());
+    if (e == cudaSuccess) c.assign(base);
+    return e;
+  }
   void release() {
     for (void* p : ptrs) diaf_dev_free(p, s);
     ptrs.clear();
   }
   ~Pool() { release(); }
 };
+
+// CUDA events of the factor handles, recycled per device: a setup takes
+// kEvents of them, and creating them anew each time cost host time in front
+// of the setup's first device operation.
+struct EventCache {
+  std::mutex mu;
+  std::vector<cudaEvent_t> free[64];
+};
+EventCache g_events;
+
+cudaError_t event_get(cudaEvent_t* e, int dev) {
+  if (dev >= 0 && dev < 64) {
+    std::lock_guard<std::mutex> lock(g_events.mu);
+    std::vector<cudaEvent_t>& v = g_events.free[dev];
+    if (!v.empty()) {
+      *e = v.back();
+      v.pop_back();
+      return cudaSuccess;
+    }
+  }
+  return cudaEventCreate(e);
+}
+
+void event_put(cudaEvent_t e, int dev) {
+  if (!e) return;
+  if (dev >= 0 && dev < 64) {
+    std::lock_guard<std::mutex> lock(g_events.mu);
+    if (g_events.free[dev].size() < 256) {
+      g_events.free[dev].push_back(e);
+      return;
+    }
+  }
+  cudaEventDestroy(e);
+}
 
 diaf_status check_device() {
   int dev = 0, n = 0;
@@ -205,6 +245,7 @@ diaf_status check_device() {
 struct Mirror {
   std::mutex mu;
   unsigned char* buf = nullptr;
+  unsigned char* dbuf = nullptr;  // buf's device address
   size_t cap = 0;    // bytes
   size_t words = 0;  // columns the word area holds (zeroed when allocated)
   uint32_t gen = 0;
@@ -235,6 +276,12 @@ bool mirror_acquire(diaf_factors* F) {
       g_mirror.buf = nullptr;
       return false;
     }
+    if (cudaHostGetDevicePointer((void**)&g_mirror.dbuf, g_mirror.buf, 0) != cudaSuccess) {
+      (void)cudaGetLastError();
+      cudaFreeHost(g_mirror.buf);
+      g_mirror.buf = g_mirror.dbuf = nullptr;
+      return false;
+    }
     std::memset(g_mirror.buf, 0, sizeof(uint32_t) * words);
     g_mirror.cap = want;
     g_mirror.words = words;
@@ -246,6 +293,8 @@ bool mirror_acquire(diaf_factors* F) {
   F->mir_word = reinterpret_cast<uint32_t*>(g_mirror.buf);
   F->mir_cp = reinterpret_cast<int32_t*>(F->mir_word + g_mirror.words);
   F->mir_ri = F->mir_cp + (n + 1);
+  F->mir_word_dev = reinterpret_cast<uint32_t*>(g_mirror.dbuf);
+  F->mir_ri_dev = reinterpret_cast<int32_t*>(F->mir_word_dev + g_mirror.words) + (n + 1);
   F->mir_gen = g_mirror.gen;
   F->mirror = true;
   g_mirror.busy = true;
@@ -308,8 +357,7 @@ void diaf_free(diaf_factors* F) {
   for (cudaEvent_t e : F->wev)
     if (e) cudaEventDestroy(e);
   for (void* p : F->owned) diaf_dev_free(p, F->stream);
-  for (cudaEvent_t e : F->ev)
-    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : F->ev) event_put(e, F->device);
   delete F;
 }
 
@@ -456,16 +504,33 @@ diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_
 
   uint32_t* status;
   int32_t *stats, *big_count;
+  int64_t* bs64;
+  int32_t* bs32;
+  PlanArgs pa{};
   DIAF_CU(F->alloc(&status, 1));
   F->status = status;
-  DIAF_CU(pool.get(&stats, 4));
-  DIAF_CU(pool.get(&np.bucket_count, kNumBuckets));
-  DIAF_CU(pool.get(&big_count, 1));
-  DIAF_CU(pool.get(&np.work, kWorkCounters));
+  // the symbolic scratch in one allocation; the small counters in one block
+  // (stats[4], then the bucket counts, then the large-tile count: one memset)
+  {
+    Carve c;
+    c.add(&stats, 4 + kNumBuckets + 1);
+    c.add(&np.work, kWorkCounters);
+    c.add(&pa.k, n);
+    c.add(&pa.E, n);
+    c.add(&pa.Eoff, n + 1);
+    c.add(&pa.m, n);
+    c.add(&pa.l, n);
+    c.add(&pa.jin, n);
+    c.add(&np.bucket_list, (size_t)kNumBuckets * n);
+    c.add(&pa.big_list, n);
+    c.add(&bs64, scan_blocksums_size(n));
+    c.add(&bs32, scan_blocksums_size(n));
+    DIAF_CU(pool.carve(c));
+  }
+  np.bucket_count = stats + 4;
+  big_count = stats + 4 + kNumBuckets;
   DIAF_CU(cudaMemsetAsync(status, 0, sizeof(uint32_t), s));
-  DIAF_CU(cudaMemsetAsync(stats, 0, sizeof(int32_t) * 4, s));
-  DIAF_CU(cudaMemsetAsync(np.bucket_count, 0, sizeof(int32_t) * kNumBuckets, s));
-  DIAF_CU(cudaMemsetAsync(big_count, 0, sizeof(int32_t), s));
+  DIAF_CU(cudaMemsetAsync(stats, 0, sizeof(int32_t) * (4 + kNumBuckets + 1), s));
 
   // ---- input checks on the device (sorted, in range)
   DIAF_CU(check_csc(n, A->colptr, A->rowidx, A->nnz, status, s));
@@ -473,7 +538,6 @@ diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_
   if (V->rule == DIAF_RULE_FIXED) DIAF_CU(check_csc(n, V->fixed->colptr, V->fixed->rowidx, V->fixed->nnz, status, s));
 
   // ---- symbolic pass 1: k_j, E_j
-  PlanArgs pa{};
   pa.n = n;
   pa.Acp = A->colptr; pa.Ari = A->rowidx;
   pa.Wcp = PW->colptr; pa.Wri = PW->rowidx;
@@ -484,18 +548,6 @@ diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_
   pa.blk = V->rule == DIAF_RULE_BLOCK ? V->blocks : nullptr;
   pa.edge_m0 = tuning && tuning->m_edge0 > 0 ? tuning->m_edge0 : 32;
   pa.edge_m1 = tuning && tuning->m_edge1 > 0 ? tuning->m_edge1 : 64;
-  int64_t* bs64;
-  int32_t* bs32;
-  DIAF_CU(pool.get(&pa.k, n));
-  DIAF_CU(pool.get(&pa.E, n));
-  DIAF_CU(pool.get(&pa.Eoff, n + 1));
-  DIAF_CU(pool.get(&pa.m, n));
-  DIAF_CU(pool.get(&pa.l, n));
-  DIAF_CU(pool.get(&pa.jin, n));
-  DIAF_CU(pool.get(&np.bucket_list, (size_t)kNumBuckets * n));
-  DIAF_CU(pool.get(&pa.big_list, n));
-  DIAF_CU(pool.get(&bs64, scan_blocksums_size(n)));
-  DIAF_CU(pool.get(&bs32, scan_blocksums_size(n)));
   pa.bucket_list = np.bucket_list;
   pa.bucket_count = np.bucket_count;
   pa.big_count = big_count;
@@ -525,17 +577,18 @@ diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_
   } else {
     DIAF_CU(cudaMemsetAsync(F->Vcp, 0, sizeof(int32_t), s));
   }
-  int32_t h_nnzv = 0, h_stats[4] = {0};
+  int32_t h_nnzv = 0, h_blk[4 + kNumBuckets] = {0};  // stats, then the bucket counts
+  int32_t* const h_stats = h_blk;
   if (n > 0) {
     DIAF_CU(cudaMemcpyAsync(&h_nnzv, F->Vcp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    DIAF_CU(cudaMemcpyAsync(np.h_bc, np.bucket_count, sizeof(np.h_bc), cudaMemcpyDeviceToHost, s));
-    DIAF_CU(cudaMemcpyAsync(h_stats, stats, sizeof(h_stats), cudaMemcpyDeviceToHost, s));
+    DIAF_CU(cudaMemcpyAsync(h_blk, stats, sizeof(h_blk), cudaMemcpyDeviceToHost, s));
     DIAF_CU(cudaMemcpyAsync(&h_status, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     PT_DEV(s);
     PT_HOST();
     DIAF_CU(cudaStreamSynchronize(s));
     PT_HOST();
   }
+  for (int b = 0; b < kNumBuckets; ++b) np.h_bc[b] = h_blk[4 + b];
   if (h_status & DEV_ST_CAPACITY)
     return fail(DIAF_EUNSUPPORTED, "a column needs more than 4096 gathered entries or a tile beyond 1024 x 64");
   F->nnz_v = h_nnzv;
@@ -552,18 +605,24 @@ diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_
   for (int b = 0; b < kNumBuckets; ++b) F->info.bucket_cols[b] = np.h_bc[b];
 
   // ---- outputs
-  DIAF_CU(F->alloc(&F->Wcp, n + 1));
-  DIAF_CU(F->alloc(&F->Wri, PW->nnz));
-  DIAF_CU(F->alloc((char**)&F->Wv, esz * PW->nnz));
-  DIAF_CU(F->alloc(&F->Vri, h_nnzv));
-  DIAF_CU(F->alloc((char**)&F->Vv, esz * h_nnzv));
-  DIAF_CU(F->alloc(&F->res, n));
-  DIAF_CU(F->alloc(&F->flags, n));
+  {
+    Carve c;
+    c.add(&F->Wcp, n + 1);
+    c.add(&F->Wri, PW->nnz);
+    c.add((char**)&F->Wv, esz * PW->nnz);
+    c.add(&F->Vri, h_nnzv);
+    c.add((char**)&F->Vv, esz * h_nnzv);
+    c.add(&F->res, n);
+    c.add(&F->flags, n);
+    if (prec == DIAF_PREC_MIXED32) c.add(&F->fb_counts, kNumBuckets);
+    DIAF_CU(F->carve(c));
+  }
   DIAF_CU(cudaMemcpyAsync(F->Wcp, PW->colptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
   if (PW->nnz > 0)
     DIAF_CU(cudaMemcpyAsync(F->Wri, PW->rowidx, sizeof(int32_t) * PW->nnz, cudaMemcpyDeviceToDevice, s));
 
   // ---- numeric-pass arguments and scratch
+  Carve nc;
   ColArgs& ca = np.ca;
   ca.n = n;
   ca.Acp = A->colptr; ca.Ari = A->rowidx; ca.Av = A->vals;
@@ -585,9 +644,8 @@ diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_
   ca.phase = g_phase;
 #endif
   if (np.mixed) {
-    DIAF_CU(pool.get(&np.fb_list, (size_t)kNumBuckets * n));
-    DIAF_CU(pool.get(&np.fb_count, kNumBuckets));
-    DIAF_CU(F->alloc(&F->fb_counts, kNumBuckets));
+    nc.add(&np.fb_list, (size_t)kNumBuckets * n);
+    nc.add(&np.fb_count, kNumBuckets);
     // the warp buckets' FP64 tiles: one per warp of the larger persistent grid
     // (the buckets run one after the other on the stream)
     size_t tiles = 0;
@@ -597,7 +655,7 @@ diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_
                                : mixed_tile_scratch_f32(b, alg, np.h_bc[b], np.wpb[b]);
       if (t > tiles) tiles = t;
     }
-    if (tiles > 0) DIAF_CU(pool.get((char**)&ca.tile_scratch, tiles));
+    if (tiles > 0) nc.add((char**)&ca.tile_scratch, tiles);
     // bucket 0 of real DIAF-S: four lanes per column (unless the tuning asks for the warp kernel)
     const int small = tuning ? tuning->small_tiles : 0;
     if (!np.cplx && alg == DIAF_ALG_S && np.h_bc[0] > 0 && small != 2 && V->rule != DIAF_RULE_FIXED) {
@@ -609,8 +667,8 @@ diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_
         np.ta.K = K;
         np.ta.arena = thread_arena_floats(M, K);
         np.ta.nquads = np.tsh.nquads;
-        DIAF_CU(pool.get(&np.ta.slab, (size_t)np.tsh.nquads * thread_slab_doubles(M, K)));
-        DIAF_CU(pool.get(&np.ta.defer_list, np.h_bc[0]));
+        nc.add(&np.ta.slab, (size_t)np.tsh.nquads * thread_slab_doubles(M, K));
+        nc.add(&np.ta.defer_list, np.h_bc[0]);
         np.ta.defer_count = np.work + 3 * kNumBuckets;
         np.thread_cols = np.tsh.grid > 0;
       }
@@ -628,8 +686,9 @@ diaf_status symbolic_pass(const diaf_csc* A, const diaf_pattern* PW, const diaf_
     // the mixed kernel needs less shared memory: its own occupancy-sized grid
     np.cta_grid_mixed = np.mixed ? cta_columns_grid_mixed(A->dtype, alg, np.cs.ldm, np.h_bc[bl]) : 0;
     const int slabs = np.cta_grid > np.cta_grid_mixed ? np.cta_grid : np.cta_grid_mixed;
-    DIAF_CU(pool.get((char**)&np.cs.slab, (size_t)slabs * 2 * np.cs.ldm * np.cs.kcap * esz));
+    nc.add((char**)&np.cs.slab, (size_t)slabs * 2 * np.cs.ldm * np.cs.kcap * esz);
   }
+  if (!nc.reqs.empty()) DIAF_CU(pool.carve(nc));  // the numeric pass's scratch, one allocation
   PT_DEV(s);
   PT_HOST();
   return DIAF_OK;
@@ -742,7 +801,8 @@ diaf_status diaf_factor_tuned(const diaf_csc* A, const diaf_pattern* PW, const d
     bool keep = false;
     ~Guard() { if (!keep) diaf_free(f); }
   } guard{F};
-  for (cudaEvent_t& e : F->ev) DIAF_CU(cudaEventCreate(&e));
+  cudaGetDevice(&F->device);
+  for (cudaEvent_t& e : F->ev) DIAF_CU(event_get(&e, F->device));
   DIAF_CU(cudaEventRecord(F->ev[0], s));
   Pool pool(s);
   NumericPlan np;
@@ -752,13 +812,9 @@ diaf_status diaf_factor_tuned(const diaf_csc* A, const diaf_pattern* PW, const d
   // during the numeric pass (the columns of an upper V in descending order,
   // the order in which the level schedule visits them)
   if ((V->rule == DIAF_RULE_UPPER || V->rule == DIAF_RULE_LOWER) && F->n > 0 && mirror_acquire(F)) {
-    int32_t *dri = nullptr;
-    uint32_t* dword = nullptr;
-    DIAF_CU(cudaHostGetDevicePointer((void**)&dri, F->mir_ri, 0));
-    DIAF_CU(cudaHostGetDevicePointer((void**)&dword, F->mir_word, 0));
     DIAF_CU(cudaMemcpyAsync(F->mir_cp, F->Vcp, sizeof(int32_t) * (F->n + 1), cudaMemcpyDeviceToHost, s));
-    np.ca.Hri = dri;
-    np.ca.Hgen = dword;
+    np.ca.Hri = F->mir_ri_dev;
+    np.ca.Hgen = F->mir_word_dev;
     np.ca.gen = F->mir_gen;
     np.ca.list_desc = V->rule == DIAF_RULE_UPPER;
   }

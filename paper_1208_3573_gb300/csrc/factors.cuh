@@ -16,6 +16,36 @@ void diaf_set_last_error(const char* msg);
 cudaError_t diaf_dev_alloc(void** p, size_t bytes, cudaStream_t s);
 void diaf_dev_free(void* p, cudaStream_t s);
 
+// Several arrays from one stream-ordered allocation (each start 256-byte
+// aligned): add() records where each pointer goes and its size, and the
+// owner's carve() makes one allocation and sets the pointers.  Fewer
+// allocation calls on the host path of a setup, which otherwise outruns the
+// small device operations between them.
+struct Carve {
+  struct Req {
+    void** p;
+    size_t bytes;
+  };
+  std::vector<Req> reqs;
+  template <class T>
+  void add(T** p, size_t count) {
+    reqs.push_back({reinterpret_cast<void**>(p), sizeof(T) * (count > 0 ? count : 1)});
+  }
+  static size_t round(size_t b) { return (b + 255) & ~size_t(255); }
+  size_t total() const {
+    size_t t = 0;
+    for (const Req& r : reqs) t += round(r.bytes);
+    return t;
+  }
+  void assign(unsigned char* base) const {
+    size_t off = 0;
+    for (const Req& r : reqs) {
+      *r.p = base + off;
+      off += round(r.bytes);
+    }
+  }
+};
+
 struct diaf_factors {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -41,6 +71,8 @@ struct diaf_factors {
   int32_t* mir_ri = nullptr;    // host: V's row indices (nnz_v), filled by the column kernels
   uint32_t* mir_word = nullptr; // host: per column, set to mir_gen once column j's rows are there
   uint32_t mir_gen = 0;
+  int32_t* mir_ri_dev = nullptr;    // the same row indices and words as the column kernels address them
+  uint32_t* mir_word_dev = nullptr;
   // apply
   bool apply_ready = false;
   bool solve_cold = false;  // the level-ordered copies were just built: the next solve warms them
@@ -68,5 +100,11 @@ struct diaf_factors {
     owned.push_back(q);
     *p = static_cast<T*>(q);
     return cudaSuccess;
+  }
+  cudaError_t carve(const Carve& c) {
+    unsigned char* base = nullptr;
+    cudaError_t e = alloc(&base, c.total());
+    if (e == cudaSuccess) c.assign(base);
+    return e;
   }
 };

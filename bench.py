@@ -54,8 +54,8 @@ def metric_name(workload: str, alg: str) -> str:
 # (workload, algorithm, precision) (profiles/); None elsewhere.
 TRAFFIC = {
     ("convdiff2d_256x256_Wp2", "S", "mixed32"): 27_404_544 + 25_064_704,   # column_thread_kernel<16>
-    ("convdiff2d_256x256_Wp2", "S", "fp64"): 24_370_944 + 768,             # column_warp_kernel<double,16,32,S>
-    ("helmholtz2d_512x512", "S", "mixed32"): 133_556_736 + 47_571_456,     # column_mixed_kernel<Cx<float>,16,32,S>
+    ("convdiff2d_256x256_Wp2", "S", "fp64"): 24_367_104 + 768,             # column_warp_kernel<double,16,32,S>
+    ("helmholtz2d_512x512", "S", "mixed32"): 133_269_248 + 48_194_304,     # column_mixed_kernel<Cx<float>,16,32,S>
 }
 
 

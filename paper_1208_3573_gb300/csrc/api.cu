@@ -1081,20 +1081,32 @@ bool event_passed(cudaEvent_t e) {
   return false;
 }
 
-// The level schedule of a triangular V whose columns reach the host during
-// the numeric pass (the mirror): the columns are visited in the solve's order
-// (descending for an upper V, ascending for a lower one), each once its word
+// The level schedule of a triangular V from its columns (host arrays cp,
+// ri), visited in the solve's order: descending for an upper V, ascending for
+// a lower one.  With `word` (the mirror), column j is visited once its word
 // holds the owner's generation `gen` (acquire load, after which its rows are
-// visible).  lev[j] is final when the walk reaches column j, so the rows of
-// every level are counted on the way (cnt[0..nlev)) and row j's place among
-// them is rank[j] (the rows of a level in the walk's order).  Returns 0, 1 (an entry
-// on the wrong side of the diagonal), 2 (a diagonal entry missing), 3 (a row
-// index out of range) or 4 (`done`, the end of the numeric pass, passed while
-// a column had not arrived).  After 1, 3 or 4 the kernels may still write.
-int level_walk_streamed(int n, const int32_t* cp, const int32_t* ri, const uint32_t* word, uint32_t gen, bool up,
-                        cudaEvent_t done, int32_t* lev, int32_t* rank, int32_t* cnt, int* nlev) {
-  auto arrived = [&](int j) { return __atomic_load_n(word + j, __ATOMIC_ACQUIRE) == gen; };
-  for (int i = 0; i < n; ++i) lev[i] = 0;
+// visible); without, every column is there.  lev[j] is final when the walk
+// reaches column j, so the walk also gives row j its place among the rows of
+// its level (rank[j]; cnt[0..nlev) counts the rows per level), numbers the
+// off-diagonal entries of every row in the order it meets them (slot[p] for
+// entry p of the columns, rcnt[i] entries in row i) and notes where each
+// column's diagonal entry is (dpos[j]): all the device needs to lay V's rows
+// out level by level.  Returns 0, 1 (an entry on the wrong side of the
+// diagonal), 2 (a diagonal entry missing), 3 (a row index out of range) or 4
+// (`done`, the end of the numeric pass, passed while a column had not
+// arrived).  After 1, 3 or 4 the kernels may still write into the mirror.
+struct LevelWalk {
+  int32_t *lev, *rank, *rcnt, *dpos, *slot, *cnt;
+  int nlev;
+};
+
+int level_walk(int n, const int32_t* cp, const int32_t* ri, const uint32_t* word, uint32_t gen, bool up,
+               cudaEvent_t done, LevelWalk& w) {
+  auto arrived = [&](int j) { return !word || __atomic_load_n(word + j, __ATOMIC_ACQUIRE) == gen; };
+  for (int i = 0; i < n; ++i) {
+    w.lev[i] = 0;
+    w.rcnt[i] = 0;
+  }
   int nl = 0;
   bool nodiag = false;
   for (int step = 0; step < n; ++step) {
@@ -1107,20 +1119,27 @@ int level_walk_streamed(int n, const int32_t* cp, const int32_t* ri, const uint3
         }
       }
     }
-    const int lj = lev[j];
-    while (nl <= lj) cnt[nl++] = 0;
-    rank[j] = cnt[lj]++;
+    const int lj = w.lev[j];
+    while (nl <= lj) w.cnt[nl++] = 0;
+    w.rank[j] = w.cnt[lj]++;
     bool d = false;
     for (int p = cp[j]; p < cp[j + 1]; ++p) {
       const int i = ri[p];
       if (i < 0 || i >= n) return 3;
-      if (i == j) { d = true; continue; }
+      if (i == j) {
+        d = true;
+        w.dpos[j] = p;
+        w.slot[p] = -1;
+        continue;
+      }
       if (up ? i > j : i < j) return 1;
-      if (lev[i] <= lj) lev[i] = lj + 1;
+      w.slot[p] = w.rcnt[i]++;
+      if (w.lev[i] <= lj) w.lev[i] = lj + 1;
     }
+    if (!d) w.dpos[j] = -1;
     nodiag |= !d;
   }
-  *nlev = nl;
+  w.nlev = nl;
   return nodiag ? 2 : 0;
 }
 
@@ -1148,18 +1167,21 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   const int n = F->n;
   const bool cplx = F->dtype == DIAF_C128;
   const size_t esz = cplx ? 16 : 8;
+  const size_t nnzv = (size_t)F->nnz_v;
   int32_t* work;
   DIAF_CU(F->alloc(&work, n + scan_blocksums_size(n)));
-  // V's column structure goes to the host first (pinned staging: cp, ri;
-  // then ptr and order on the way back): the level schedule is computed from
-  // it on the host while the device builds the row-oriented copies of V and
-  // W and checks V's diagonal
-  // (or, when F owns the mirror, V's structure is already on its way there)
+  // V's structure is walked on the host (level of every row, its place in
+  // its level, the numbering of every row's entries, the diagonals) -- when F
+  // holds the mirror, while the numeric pass still writes V's columns there;
+  // otherwise from a copy taken after the pass (pinned staging: cp, ri).
+  // Meanwhile the device converts W to rows.  The walk's arrays go to the
+  // device in one copy, and the device lays V's rows out level by level.
   const bool mir = F->mirror;
   std::lock_guard<std::mutex> stage_lock(g_stage.mu);
   const size_t n1 = (size_t)n + 1;
-  const size_t nri = mir ? 0 : (size_t)F->nnz_v;
-  unsigned char* stage = stage_get(sizeof(int32_t) * (5 * n1 + nri) + sizeof(uint32_t));
+  const size_t nri = mir ? 0 : nnzv;
+  const size_t blk = 4 * (size_t)n + nnzv;  // lev, rank, rcnt, dpos, slot
+  unsigned char* stage = stage_get(sizeof(int32_t) * (n1 + nri + n1 + blk) + sizeof(uint32_t));
   if (!stage) {
     if (mir) {
       (void)cudaStreamSynchronize(s);
@@ -1167,15 +1189,16 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
     }
     return fail(DIAF_ENOMEM, "pinned host staging for the level schedule");
   }
-  int32_t* cp = mir ? F->mir_cp : reinterpret_cast<int32_t*>(stage);
-  int32_t* ri = mir ? F->mir_ri : reinterpret_cast<int32_t*>(stage) + n1;
-  int32_t* ptr = reinterpret_cast<int32_t*>(stage) + (mir ? 0 : n1 + nri);  // level pointers (at most n + 1)
-  int32_t* lev = ptr + n1;          // level of every row (n)
-  int32_t* rank = lev + n1;         // place of every row within its level (n)
-  uint32_t* hp = reinterpret_cast<uint32_t*>(rank + n1);
+  int32_t* const st32 = reinterpret_cast<int32_t*>(stage);
+  int32_t* cp = mir ? F->mir_cp : st32;
+  int32_t* ri = mir ? F->mir_ri : st32 + n1;
+  int32_t* ptr = st32 + (mir ? 0 : n1 + nri);  // level pointers (at most n + 1)
+  int32_t* hblk = ptr + n1;
+  LevelWalk lw{hblk, hblk + n, hblk + 2 * (size_t)n, hblk + 3 * (size_t)n, hblk + 4 * (size_t)n, nullptr, 0};
+  uint32_t* hp = reinterpret_cast<uint32_t*>(hblk + blk);
   if (!mir) {
     DIAF_CU(cudaMemcpyAsync(cp, F->Vcp, sizeof(int32_t) * n1, cudaMemcpyDeviceToHost, s));
-    if (F->nnz_v > 0) DIAF_CU(cudaMemcpyAsync(ri, F->Vri, sizeof(int32_t) * F->nnz_v, cudaMemcpyDeviceToHost, s));
+    if (nnzv > 0) DIAF_CU(cudaMemcpyAsync(ri, F->Vri, sizeof(int32_t) * nnzv, cudaMemcpyDeviceToHost, s));
   }
   PT_DEV(s);
   cudaEvent_t ev[2];
@@ -1187,25 +1210,12 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
     DIAF_CU(ce);
   }
   ce = cudaEventRecord(ev[0], s);
-  uint32_t* tri = nullptr;
-  F->Vr.n = n; F->Vr.nnz = F->nnz_v;
-  F->Wr.n = n; F->Wr.nnz = F->nnz_w;
-  if (ce == cudaSuccess) ce = F->alloc(&F->Vr.rowptr, n + 1);
-  if (ce == cudaSuccess) ce = F->alloc(&F->Vr.colidx, F->nnz_v);
-  if (ce == cudaSuccess) ce = F->alloc((char**)&F->Vr.vals, esz * F->nnz_v);
-  if (ce == cudaSuccess)
-    ce = csc_to_csr(n, F->nnz_v, F->Vcp, F->Vri, F->Vv, cplx, F->Vr.rowptr, F->Vr.colidx, F->Vr.vals, work, s);
-  if (ce == cudaSuccess) ce = F->alloc(&tri, 1);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(tri, 0, sizeof(uint32_t), s);
-  if (ce == cudaSuccess) ce = csr_triangle_check(F->Vr, cplx, tri, s);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(hp, tri, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
-  if (ce == cudaSuccess) ce = cudaEventRecord(ev[1], s);
-  PT_DEV(s);
+  // W to rows, on the side stream when there is one (its own scratch)
+  F->Wr.n = n;
+  F->Wr.nnz = F->nnz_w;
   if (ce == cudaSuccess) ce = F->alloc(&F->Wr.rowptr, n + 1);
   if (ce == cudaSuccess) ce = F->alloc(&F->Wr.colidx, F->nnz_w);
   if (ce == cudaSuccess) ce = F->alloc((char**)&F->Wr.vals, esz * F->nnz_w);
-  // W's row-oriented copy on the side stream: the V solve occupies one SM,
-  // the others build W meanwhile (its own scratch; the first SpMV waits)
   cudaStream_t ws = side_stream();
   int32_t* wwork = work;
   if (ws && ce == cudaSuccess) {
@@ -1219,23 +1229,29 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   if (ce == cudaSuccess)
     ce = csc_to_csr(n, F->nnz_w, F->Wcp, F->Wri, F->Wv, cplx, F->Wr.rowptr, F->Wr.colidx, F->Wr.vals, wwork, wsx);
   if (ws && ce == cudaSuccess) ce = cudaEventRecord(F->wev[1], ws);  // diaf_free waits for it
-  // the level-ordered copies' buffers (sizes known now; the level count is
-  // at most n), so that only copies and kernels follow the host's pass
+  // the level-ordered copy of V and its inputs (sizes known now; the level
+  // count is at most n), so that only copies and kernels follow the walk
   LevelCsr& Vl = F->Vl;
-  int32_t *dorder = nullptr, *pos = nullptr, *dlev = nullptr;
+  int32_t *pos = nullptr, *dblk = nullptr;
+  uint32_t* zflag = nullptr;
   Vl.n = n;
   Vl.nnz = F->nnz_v - n;
-  if (ce == cudaSuccess) ce = F->alloc(&Vl.lvlptr, n + 1);
-  if (ce == cudaSuccess) ce = F->alloc(&dorder, n);
-  if (ce == cudaSuccess) ce = F->alloc(&dlev, 2 * (size_t)n);  // levels, then ranks
-  if (ce == cudaSuccess) ce = F->alloc(&pos, n);
-  if (ce == cudaSuccess) ce = F->alloc(&Vl.rowptr, n + 1);
-  if (ce == cudaSuccess) ce = F->alloc(&Vl.colidx, Vl.nnz > 0 ? Vl.nnz : 0);
-  if (ce == cudaSuccess) ce = F->alloc((char**)&Vl.vals, esz * (Vl.nnz > 0 ? Vl.nnz : 0));
-  if (ce == cudaSuccess) ce = F->alloc((char**)&Vl.dinv, esz * n);
-  if (ce == cudaSuccess) ce = F->alloc(&Vl.xrow, n);
-  if (ce == cudaSuccess) ce = F->alloc(&F->Wl.colidx, F->nnz_w);
-  if (ce == cudaSuccess) ce = F->alloc((char**)&F->tbuf, esz * n);
+  {
+    Carve c;
+    c.add(&Vl.lvlptr, n + 1);
+    c.add(&Vl.rowptr, n + 1);
+    c.add(&Vl.colidx, Vl.nnz > 0 ? Vl.nnz : 0);
+    c.add((char**)&Vl.vals, esz * (Vl.nnz > 0 ? Vl.nnz : 0));
+    c.add((char**)&Vl.dinv, esz * n);
+    c.add(&Vl.xrow, n);
+    c.add(&pos, n);
+    c.add(&dblk, blk);
+    c.add(&zflag, 1);
+    c.add(&F->Wl.colidx, F->nnz_w);
+    c.add((char**)&F->tbuf, esz * n);
+    if (ce == cudaSuccess) ce = F->carve(c);
+  }
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(zflag, 0, sizeof(uint32_t), s);
   int32_t* const wl_colidx = F->Wl.colidx;
   PT_DEV(s);
   PT_HOST();
@@ -1251,30 +1267,27 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
     DIAF_CU(ce);
     DIAF_CU(se);
   }
-  // level of every row (host, O(nnz)); the device checks the diagonal's values meanwhile
-  // host scratch reused across calls of this thread: rows per level
-  static thread_local std::vector<int32_t> cur;
-  if (cur.size() < (size_t)n) cur.resize(n);
-  int nlev = 0;
+  // the walk (host, O(nnz)); rows per level in host scratch reused across
+  // calls of this thread (the walk sets what it uses)
+  static thread_local std::vector<int32_t> cnt;
+  if (cnt.size() < n1) cnt.resize(n1);
+  lw.cnt = cnt.data();
   bool vup = true;
   int ls = -1;
-  bool counted = false;  // cur[0..nlev) holds the rows per level, rank[] the places
   if (mir) {
     // V's column pointers reached the host before the numeric pass began
     se = cudaEventSynchronize(F->ev[1]);
     if (se == cudaSuccess) {
       vup = F->rule == DIAF_RULE_UPPER;
-      ls = level_walk_streamed(n, cp, ri, F->mir_word, F->mir_gen, vup, F->ev[2], lev, rank, cur.data(), &nlev);
+      ls = level_walk(n, cp, ri, F->mir_word, F->mir_gen, vup, F->ev[2], lw);
     }
     if (ls == 0 || ls == 2) {
-      counted = true;
       g_prep_streamed.fetch_add(1, std::memory_order_relaxed);
     } else {
       // not every column arrived, or an entry is out of place: V's whole
       // structure once the numeric pass has ended
       se = cudaStreamSynchronize(s);
-      if (se == cudaSuccess && F->nnz_v > 0)
-        se = cudaMemcpy(ri, F->Vri, sizeof(int32_t) * F->nnz_v, cudaMemcpyDeviceToHost);
+      if (se == cudaSuccess && nnzv > 0) se = cudaMemcpy(ri, F->Vri, sizeof(int32_t) * nnzv, cudaMemcpyDeviceToHost);
       if (se != cudaSuccess) {
         mirror_release(F);
         cudaEventDestroy(ev[0]);
@@ -1284,42 +1297,41 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
       ls = -1;
     }
   }
-  if (ls < 0) {
-    ls = level_schedule_host(n, cp, ri, lev, &nlev, &vup);
+  if (ls < 0) {  // the whole structure at hand: an upper V, else a lower one
+    vup = true;
+    ls = level_walk(n, cp, ri, nullptr, 0, true, nullptr, lw);
+    if (ls == 1) {
+      vup = false;
+      ls = level_walk(n, cp, ri, nullptr, 0, false, nullptr, lw);
+    }
     g_prep_copied.fetch_add(1, std::memory_order_relaxed);
   }
   // every column of the mirror has been read (or the stream synchronised)
   mirror_release(F);
   F->v_upper = vup;
-  if (ls == 1 || ls == 3) {
+  if (ls != 0) {
     (void)cudaStreamSynchronize(s);
     cudaEventDestroy(ev[0]);
     cudaEventDestroy(ev[1]);
-    return fail(DIAF_EINVAL, ls == 1 ? "V is not triangular" : "V has a row index out of range");
-  }
-  if (ls == 2) {
-    (void)cudaStreamSynchronize(s);
-    cudaEventDestroy(ev[0]);
-    cudaEventDestroy(ev[1]);
-    return fail(DIAF_EINVAL, "V has a zero or missing diagonal entry");
+    return fail(DIAF_EINVAL, ls == 1   ? "V is not triangular"
+                             : ls == 3 ? "V has a row index out of range"
+                                       : "V has a zero or missing diagonal entry");
   }
   PT_HOST();
-  if (!counted) {  // rows per level, and the places within a level in increasing row order
-    for (int l = 0; l < nlev; ++l) cur[l] = 0;
-    for (int i = 0; i < n; ++i) rank[i] = cur[lev[i]]++;
-  }
+  const int nlev = lw.nlev;
   ptr[0] = 0;
   Vl.maxw = 0;
   for (int l = 0; l < nlev; ++l) {
-    ptr[l + 1] = ptr[l] + cur[l];
-    Vl.maxw = std::max(Vl.maxw, cur[l]);
+    ptr[l + 1] = ptr[l] + cnt[l];
+    Vl.maxw = std::max(Vl.maxw, cnt[l]);
   }
   Vl.nlev = nlev;
-  // the device orders the rows (order[ptr[lev[i]] + rank[i]] = i) and builds
-  // the level-ordered copies; the zero-diagonal check is read after that
+  // the device places the rows (position of row i: ptr[lev i] + rank i),
+  // lays V's rows out level by level from its columns, and checks the
+  // diagonal's values; the zero-diagonal flag is read after all of that is
+  // enqueued
   ce = cudaMemcpyAsync(Vl.lvlptr, ptr, sizeof(int32_t) * (nlev + 1), cudaMemcpyHostToDevice, s);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(dlev, lev, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(dlev + n, rank, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(dblk, hblk, sizeof(int32_t) * blk, cudaMemcpyHostToDevice, s);
   PT_DEV(s);
   if (ce == cudaSuccess) ce = stage_release(s);  // the next user of the staging buffer waits for these copies
   if (ce != cudaSuccess) {
@@ -1328,11 +1340,15 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
     cudaEventDestroy(ev[1]);
     DIAF_CU(ce);
   }
-  ce = level_order(n, dlev, dlev + n, Vl.lvlptr, dorder, s);
-  if (ce == cudaSuccess) ce = csr_level_permute(F->Vr, cplx, dorder, pos, work, Vl, s);
+  const int32_t* dlev = dblk;
+  const int32_t* drank = dblk + n;
+  const int32_t* drcnt = dblk + 2 * (size_t)n;
+  const int32_t* ddpos = dblk + 3 * (size_t)n;
+  const int32_t* dslot = dblk + 4 * (size_t)n;
+  ce = level_place(n, dlev, drank, drcnt, Vl.lvlptr, pos, Vl.xrow, work, Vl.rowptr, s);
   F->Wl = F->Wr;
   F->Wl.colidx = wl_colidx;
-  if (ws) {  // W's columns renumbered to V's level order on the side stream, after V's permutation
+  if (ws) {  // W's columns renumbered to V's level order on the side stream, once the positions are known
     if (ce == cudaSuccess) ce = cudaEventRecord(F->wev[0], s);
     if (ce == cudaSuccess) ce = cudaStreamWaitEvent(ws, F->wev[0], 0);
   }
@@ -1341,14 +1357,18 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
     ce = cudaEventRecord(F->wev[1], ws);
     F->w_pending = ce == cudaSuccess;
   }
+  if (ce == cudaSuccess)
+    ce = level_fill(n, cplx, F->Vcp, F->Vri, F->Vv, ddpos, dslot, pos, Vl, zflag, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(hp, zflag, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaEventRecord(ev[1], s);
   PT_DEV(s);
   PT_HOST();
-  se = cudaEventSynchronize(ev[1]);
+  se = ce == cudaSuccess ? cudaEventSynchronize(ev[1]) : cudaStreamSynchronize(s);
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
   DIAF_CU(ce);
   DIAF_CU(se);
-  if (*hp & 4u) return fail(DIAF_EINVAL, "V has a zero or missing diagonal entry");
+  if (*hp) return fail(DIAF_EINVAL, "V has a zero or missing diagonal entry");
   PT_HOST();
   F->apply_ready = true;
   F->solve_cold = true;

@@ -82,7 +82,7 @@ struct diaf_factors {
   cudaEvent_t wev[2] = {};
   bool w_pending = false;
   bool v_upper = true;
-  Csr Vr, Wr;
+  Csr Wr;  // W's rows (V goes straight to its level-ordered form Vl)
   void* tbuf = nullptr;
   // level-scheduled V solve: V in level order, W's columns renumbered to it
   LevelCsr Vl;

@@ -120,60 +120,52 @@ __global__ void spmv_kernel(int n, const int32_t* __restrict__ rowptr, const int
   if (row < n && sub == 0) y[row] = acc;
 }
 
-template <class S>
-__global__ void tri_check_kernel(int n, const int32_t* rowptr, const int32_t* colidx, const S* vals, uint32_t* out) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  uint32_t f = 0;
-  bool diag = false;
-  for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
-    int c = colidx[p];
-    if (c < i) f |= 1u;
-    if (c > i) f |= 2u;
-    if (c == i && sc_abs2(vals[p]) > 0.0) diag = true;
-  }
-  if (!diag) f |= 4u;
-  if (f) atomicOr(out, f);
-}
-
 constexpr int kLevelThreads = 1024;
 constexpr int kLevelPtrSmem = 8192;  // level pointers kept in shared memory up to this many levels
 constexpr int kPrefetch = 4;         // off-diagonal entries of a row held in registers ahead of its level
 
-__global__ void scatter_pos_kernel(int n, const int32_t* __restrict__ order, const int32_t* __restrict__ rowptr,
-                                   int32_t* __restrict__ pos, int32_t* __restrict__ len) {
-  int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n) return;
-  const int i = order[p];
+// Row i of V goes to level position p = lvlptr[lev i] + rank i (the walk's
+// place of row i in its level); len[p] = its number of off-diagonal entries.
+__global__ void level_place_kernel(int n, const int32_t* __restrict__ lev, const int32_t* __restrict__ rank,
+                                   const int32_t* __restrict__ rcnt, const int32_t* __restrict__ lvlptr,
+                                   int32_t* __restrict__ pos, int32_t* __restrict__ xrow, int32_t* __restrict__ len) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int p = lvlptr[lev[i]] + rank[i];
   pos[i] = p;
-  len[p] = rowptr[i + 1] - rowptr[i] - 1;  // off-diagonal entries (the diagonal is present: checked)
+  xrow[p] = i;
+  len[p] = rcnt[i];
 }
 
+// V's rows level by level, straight from its columns: kConvLanes lanes per
+// column j; entry (i, j), i != j, goes to slot slot[e] of row position
+// pos[i] with column position pos[j] and value v_ij / v_ii (the row scaled by
+// its diagonal, which sits at entry dpos[i] of column i); the diagonal entry
+// gives 1/v_jj at position pos[j] and raises *zflag when it is zero (or not
+// a number).
 template <class S>
-__global__ void fill_levels_kernel(int n, const int32_t* __restrict__ order, const int32_t* __restrict__ pos,
-                                   const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                                   const S* __restrict__ vals, const int32_t* __restrict__ prow,
-                                   int32_t* __restrict__ pcol, S* __restrict__ pval, S* __restrict__ pdinv,
-                                   int32_t* __restrict__ xrow) {
-  int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n) return;
-  const int i = order[p];
-  int k = prow[p];
-  S d = sc_zero<S>();
-  for (int e = rowptr[i]; e < rowptr[i + 1]; ++e)
-    if (colidx[e] == i) d = vals[e];
-  const S di = (1.0 / sc_abs2(d)) * sc_conj(d);
-  // the row scaled by 1/diag: the solve then computes t_i = x_i/d - sum (v_ij/d) t_j
-  for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
-    const int c = colidx[e];
-    if (c != i) {
-      pcol[k] = pos[c];
-      pval[k] = di * vals[e];
-      ++k;
+__global__ void level_fill_kernel(int n, const int32_t* __restrict__ cp, const int32_t* __restrict__ ri,
+                                  const S* __restrict__ v, const int32_t* __restrict__ dpos,
+                                  const int32_t* __restrict__ slot, const int32_t* __restrict__ pos,
+                                  const int32_t* __restrict__ rowptr, int32_t* __restrict__ pcol,
+                                  S* __restrict__ pval, S* __restrict__ pdinv, uint32_t* __restrict__ zflag) {
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int j = (int)(gid / kConvLanes), sub = (int)(gid % kConvLanes);
+  if (j >= n) return;
+  const int e1 = cp[j + 1];
+  for (int e = cp[j] + sub; e < e1; e += kConvLanes) {
+    const int i = ri[e];
+    if (i == j) {
+      const S d = v[e];
+      if (!(sc_abs2(d) > 0.0)) atomicOr(zflag, 1u);
+      pdinv[pos[j]] = (1.0 / sc_abs2(d)) * sc_conj(d);
+    } else {
+      const S d = v[dpos[i]];
+      const int q = rowptr[pos[i]] + slot[e];
+      pcol[q] = pos[j];
+      pval[q] = ((1.0 / sc_abs2(d)) * sc_conj(d)) * v[e];
     }
   }
-  pdinv[p] = di;
-  xrow[p] = i;
 }
 
 // t[p] = x[xrow[p]] / diag of row p (level order): the scaled right-hand
@@ -183,12 +175,6 @@ __global__ void scale_rhs_kernel(int n, const S* __restrict__ dinv, const int32_
                                  const S* __restrict__ x, S* __restrict__ t) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < n) t[p] = dinv[p] * x[xrow[p]];
-}
-
-__global__ void level_order_kernel(int n, const int32_t* __restrict__ lev, const int32_t* __restrict__ rank,
-                                   const int32_t* __restrict__ lvlptr, int32_t* __restrict__ order) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) order[lvlptr[lev[i]] + rank[i]] = i;
 }
 
 __global__ void remap_cols_kernel(int64_t nnz, const int32_t* __restrict__ pos, const int32_t* __restrict__ cin,
@@ -400,31 +386,26 @@ __global__ void __launch_bounds__(kDeepThreads, 1)
 
 }  // namespace
 
-cudaError_t csr_level_permute(const Csr& V, bool cplx, const int32_t* order, int32_t* pos, int32_t* work,
-                              LevelCsr& L, cudaStream_t s) {
-  const int n = V.n;
-  if (n <= 0) return cudaSuccess;
+cudaError_t level_place(int n, const int32_t* lev, const int32_t* rank, const int32_t* rcnt, const int32_t* lvlptr,
+                        int32_t* pos, int32_t* xrow, int32_t* work, int32_t* rowptr, cudaStream_t s) {
+  if (n <= 0) return cudaMemsetAsync(rowptr, 0, sizeof(int32_t), s);
   int32_t* len = work;
   int32_t* bs = work + n;
-  scatter_pos_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, order, V.rowptr, pos, len);
+  level_place_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, lev, rank, rcnt, lvlptr, pos, xrow, len);
   DIAF_COUNT_LAUNCH();
-  exclusive_scan_i32(len, L.rowptr, n, bs, s);
-  if (cplx)
-    fill_levels_kernel<Cx<double>><<<ceil_div(n, 256), 256, 0, s>>>(
-        n, order, pos, V.rowptr, V.colidx, (const Cx<double>*)V.vals, L.rowptr, L.colidx, (Cx<double>*)L.vals,
-        (Cx<double>*)L.dinv, L.xrow);
-  else
-    fill_levels_kernel<double><<<ceil_div(n, 256), 256, 0, s>>>(n, order, pos, V.rowptr, V.colidx,
-                                                              (const double*)V.vals, L.rowptr, L.colidx,
-                                                              (double*)L.vals, (double*)L.dinv, L.xrow);
-  DIAF_COUNT_LAUNCH();
-  return cudaGetLastError();
+  return exclusive_scan_i32(len, rowptr, n, bs, s);
 }
 
-cudaError_t level_order(int n, const int32_t* lev, const int32_t* rank, const int32_t* lvlptr, int32_t* order,
-                        cudaStream_t s) {
+cudaError_t level_fill(int n, bool cplx, const int32_t* cp, const int32_t* ri, const void* v, const int32_t* dpos,
+                       const int32_t* slot, const int32_t* pos, LevelCsr& L, uint32_t* zflag, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  level_order_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, lev, rank, lvlptr, order);
+  const int blocks = (int)(((int64_t)n * kConvLanes + 255) / 256);
+  if (cplx)
+    level_fill_kernel<Cx<double>><<<blocks, 256, 0, s>>>(n, cp, ri, (const Cx<double>*)v, dpos, slot, pos, L.rowptr,
+                                                          L.colidx, (Cx<double>*)L.vals, (Cx<double>*)L.dinv, zflag);
+  else
+    level_fill_kernel<double><<<blocks, 256, 0, s>>>(n, cp, ri, (const double*)v, dpos, slot, pos, L.rowptr, L.colidx,
+                                                      (double*)L.vals, (double*)L.dinv, zflag);
   DIAF_COUNT_LAUNCH();
   return cudaGetLastError();
 }
@@ -491,14 +472,4 @@ cudaError_t csr_spmv(const Csr& M, bool cplx, const void* x, void* y, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t csr_triangle_check(const Csr& V, bool cplx, uint32_t* out, cudaStream_t s) {
-  if (V.n <= 0) return cudaSuccess;
-  if (cplx)
-    tri_check_kernel<Cx<double>><<<ceil_div(V.n, 256), 256, 0, s>>>(V.n, V.rowptr, V.colidx,
-                                                                     (const Cx<double>*)V.vals, out);
-  else
-    tri_check_kernel<double><<<ceil_div(V.n, 256), 256, 0, s>>>(V.n, V.rowptr, V.colidx, (const double*)V.vals, out);
-  DIAF_COUNT_LAUNCH();
-  return cudaGetLastError();
-}
 

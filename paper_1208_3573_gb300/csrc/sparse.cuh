@@ -22,14 +22,11 @@ cudaError_t csc_to_csr(int n, int64_t nnz, const int32_t* cp, const int32_t* ri,
 // y = M x (CSR); beta_zero: y overwritten.  Complex when cplx.
 cudaError_t csr_spmv(const Csr& M, bool cplx, const void* x, void* y, cudaStream_t s);
 
-// Checks that CSR V is triangular: status bit 1 = has strictly lower entries,
-// 2 = has strictly upper entries, 4 = missing or zero diagonal.
-cudaError_t csr_triangle_check(const Csr& V, bool cplx, uint32_t* out, cudaStream_t s);
-
 // V in level order for the level-scheduled solve: position p holds row
 // xrow[p] of V; the rows of level l (their depth in V's dependency graph) are
 // positions lvlptr[l]..lvlptr[l+1]; rowptr/colidx/vals hold each row's
-// off-diagonal entries with columns renumbered to positions; dinv = 1 / diag.
+// off-diagonal entries with columns renumbered to positions, scaled by the
+// row's 1 / diag; dinv = 1 / diag.
 struct LevelCsr {
   int n = 0;
   int nlev = 0;
@@ -43,19 +40,23 @@ struct LevelCsr {
   int maxw = 0;                 // rows of the widest level (picks the solve kernel)
 };
 
-// Builds L (buffers allocated by the caller; L.n, L.nlev, L.lvlptr set) from
-// the triangular CSR V (every diagonal entry present) and the level order
-// `order` (rows level by level); pos[i] receives the position of row i;
-// work needs n + scan_blocksums_size(n) int32.
-cudaError_t csr_level_permute(const Csr& V, bool cplx, const int32_t* order, int32_t* pos, int32_t* work,
-                              LevelCsr& L, cudaStream_t s);
+// L's row layout from the host's level walk (device arrays): row i of V goes
+// to position pos[i] = lvlptr[lev[i]] + rank[i] (xrow[pos[i]] = i), and
+// rowptr (n + 1) counts rcnt[i] off-diagonal entries at that position.  work
+// needs n + scan_blocksums_size(n) int32.
+cudaError_t level_place(int n, const int32_t* lev, const int32_t* rank, const int32_t* rcnt, const int32_t* lvlptr,
+                        int32_t* pos, int32_t* xrow, int32_t* work, int32_t* rowptr, cudaStream_t s);
+
+// L's entries straight from V's columns (cp, ri, v: V in CSC): entry e =
+// (i, j) of column j, i != j, goes to L.rowptr[pos[i]] + slot[e] with column
+// pos[j] and value v_ij / v_ii (v_ii at entry dpos[i]); the diagonal gives
+// L.dinv[pos[j]] = 1 / v_jj.  *zflag (zeroed by the caller) becomes nonzero
+// when a diagonal value is zero or not a number.
+cudaError_t level_fill(int n, bool cplx, const int32_t* cp, const int32_t* ri, const void* v, const int32_t* dpos,
+                       const int32_t* slot, const int32_t* pos, LevelCsr& L, uint32_t* zflag, cudaStream_t s);
 
 // cout[e] = pos[cin[e]] (column indices renumbered to level positions).
 cudaError_t remap_columns(int64_t nnz, const int32_t* pos, const int32_t* cin, int32_t* cout, cudaStream_t s);
-// The rows of V level by level: order[lvlptr[lev[i]] + rank[i]] = i (rank[i]:
-// row i's place among the rows of its level).
-cudaError_t level_order(int n, const int32_t* lev, const int32_t* rank, const int32_t* lvlptr, int32_t* order,
-                        cudaStream_t s);
 
 // t = V^-1 x by level scheduling on L: one block, a barrier between levels;
 // t in level order (t[p] belongs to row xrow[p]).  warm: read all of the

@@ -1158,7 +1158,34 @@ cudaError_t stage_release(cudaStream_t s) {
 }  // namespace
 
 
-static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
+// y = W V^-1 x on the level-ordered V: the level solve, then (after W's
+// row-oriented copy, when that is still being built on the side stream) the
+// W SpMV.  Stream work only.
+static diaf_status enqueue_level_apply(diaf_factors* F, const void* x, void* y, cudaStream_t s) {
+  const bool cplx = F->dtype == DIAF_C128;
+#ifdef DIAF_PREP_TIMING
+  PrepTimer pt("apply");
+#endif
+  PT_DEV(s);
+  DIAF_CU(trsv_levels_perm(F->Vl, cplx, x, F->tbuf, s, F->solve_cold));
+  F->solve_cold = false;
+  PT_DEV(s);
+  if (F->w_pending) {  // W's row-oriented copy, built on the side stream during the solve
+    DIAF_CU(cudaStreamWaitEvent(s, F->wev[1], 0));
+    F->w_pending = false;
+  }
+  DIAF_CU(csr_spmv(F->Wl, cplx, F->tbuf, y, s));
+  PT_DEV(s);
+  return DIAF_OK;
+}
+
+// Prepares the apply on F (row-oriented W, V level by level) and, for a
+// triangular V with n > 0, enqueues the first y = W V^-1 x right behind the
+// preparation's kernels, before it waits for the zero-diagonal check (which
+// precedes the solve on the stream; *applied = true then); on that check's
+// failure y is not valid and the call fails.
+static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s, const void* x, void* y, bool* applied) {
+  *applied = false;
   if (F->rule == DIAF_RULE_BLOCK) return prepare_apply_blocks(F, s);
 #ifdef DIAF_PREP_TIMING
   PrepTimer pt("prep");
@@ -1362,16 +1389,29 @@ static diaf_status prepare_apply(diaf_factors* F, cudaStream_t s) {
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(hp, zflag, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
   if (ce == cudaSuccess) ce = cudaEventRecord(ev[1], s);
   PT_DEV(s);
+  // the first apply goes right behind, before the host waits for the
+  // zero-diagonal flag (which reaches it while the solve runs): no host round
+  // trip between the preparation and the solve, and the call returns while
+  // the solve is still running
+  F->solve_cold = true;
+  diaf_status ast = DIAF_OK;
+  if (ce == cudaSuccess && n > 0) {
+    ast = enqueue_level_apply(F, x, y, s);
+    *applied = ast == DIAF_OK;
+  }
   PT_HOST();
   se = ce == cudaSuccess ? cudaEventSynchronize(ev[1]) : cudaStreamSynchronize(s);
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
   DIAF_CU(ce);
   DIAF_CU(se);
-  if (*hp) return fail(DIAF_EINVAL, "V has a zero or missing diagonal entry");
+  if (*hp) {
+    *applied = false;
+    return fail(DIAF_EINVAL, "V has a zero or missing diagonal entry");
+  }
+  if (ast != DIAF_OK) return ast;
   PT_HOST();
   F->apply_ready = true;
-  F->solve_cold = true;
   return DIAF_OK;
 }
 
@@ -1400,8 +1440,9 @@ diaf_status diaf_apply(diaf_factors* F, const void* x, void* y, void* stream) {
   if (x == y) return fail(DIAF_EINVAL, "x and y must not overlap");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (!F->apply_ready) {
-    diaf_status st = prepare_apply(F, s);
-    if (st != DIAF_OK) return st;
+    bool applied = false;
+    diaf_status st = prepare_apply(F, s, x, y, &applied);
+    if (st != DIAF_OK || applied) return st;
   }
   if (F->n == 0) return DIAF_OK;
   const bool cplx = F->dtype == DIAF_C128;
@@ -1410,20 +1451,7 @@ diaf_status diaf_apply(diaf_factors* F, const void* x, void* y, void* stream) {
     DIAF_CU(csr_spmv(F->Wr, cplx, F->tbuf, y, s));
     return DIAF_OK;
   }
-#ifdef DIAF_PREP_TIMING
-  PrepTimer pt("apply");
-#endif
-  PT_DEV(s);
-  DIAF_CU(trsv_levels_perm(F->Vl, cplx, x, F->tbuf, s, F->solve_cold));
-  F->solve_cold = false;
-  PT_DEV(s);
-  if (F->w_pending) {  // W's row-oriented copy, built on the side stream during the solve
-    DIAF_CU(cudaStreamWaitEvent(s, F->wev[1], 0));
-    F->w_pending = false;
-  }
-  DIAF_CU(csr_spmv(F->Wl, cplx, F->tbuf, y, s));
-  PT_DEV(s);
-  return DIAF_OK;
+  return enqueue_level_apply(F, x, y, s);
 }
 
 }  // extern "C"

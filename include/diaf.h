@@ -302,7 +302,11 @@ diaf_status diaf_get_factors(const diaf_factors* F, diaf_csc* W, diaf_csc* V, co
  * nonzero diagonal.  The first call on F prepares the apply: row-oriented
  * copies of W and V and the level schedule of the V solve (the depth of each
  * row in V's dependency graph, computed on the host; this first call
- * allocates and synchronises `stream` -- make it before any stream capture).
+ * allocates, and waits on the host for the preparation's work on `stream`
+ * (the numeric pass included); it returns while its solve may still run --
+ * make it before any stream capture).  The level-ordered V holds each row
+ * scaled by 1/diag, and W's row-oriented copy is built on a side stream of
+ * the library while the solve runs (the SpMV waits for it).
  * For factors of rules UPPER / LOWER made by diaf_factor(_tuned), the column
  * kernels also write V's row indices into a host-mapped buffer of the
  * library as each column is finished (the columns of an upper V in
@@ -311,9 +315,11 @@ diaf_status diaf_get_factors(const diaf_factors* F, diaf_csc* W, diaf_csc* V, co
  * factorisation at a time holds that buffer, from diaf_factor until its
  * first diaf_apply or diaf_free; the others copy V's structure after the
  * numeric pass (same schedule, later).
- * Later calls only enqueue two kernels: the level-scheduled triangular solve
- * (one block, a barrier between levels) and the W SpMV.  Errors: EINVAL (V not
- * triangular or zero diagonal -- found by the first call), ENOMEM, ECUDA. */
+ * Later calls only enqueue three kernels: the scaling of x by 1/diag (all
+ * SMs), the level-scheduled triangular solve (one block, a barrier between
+ * levels) and the W SpMV.  Errors: EINVAL (V not triangular or zero
+ * diagonal -- found by the first call, whose y is then not valid), ENOMEM,
+ * ECUDA. */
 diaf_status diaf_apply(diaf_factors* F, const void* x, void* y, void* stream);
 
 /* The level schedule of the apply's triangular solve, on the host (no GPU

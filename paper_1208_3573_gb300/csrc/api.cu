@@ -1036,43 +1036,6 @@ unsigned char* stage_get(size_t bytes) {
   return g_stage.buf;
 }
 
-// The level schedule of a triangular V given by its columns (host arrays):
-// lev[i] = depth of row i in V's dependency graph (row i waits for t_j when
-// V(i,j) != 0, i != j), pushed column by column in the solve's order (lev[j]
-// is final when column j is reached).  The pass assumes an upper V (columns
-// descending) and checks the structure on the way: an entry below the
-// diagonal restarts it for a lower V (ascending), where an entry above the
-// diagonal means V is not triangular.  Returns 0, 1 (not triangular), 2 (a
-// diagonal entry missing) or 3 (a row index out of range).
-int level_schedule_host(int n, const int32_t* cp, const int32_t* ri, int32_t* lev, int* nlev, bool* upper) {
-  auto pass = [&](bool up) -> int {
-    for (int i = 0; i < n; ++i) lev[i] = 0;
-    *nlev = n > 0 ? 1 : 0;
-    bool nodiag = false;
-    for (int step = 0; step < n; ++step) {
-      const int j = up ? n - 1 - step : step;
-      const int lj = lev[j] + 1;
-      if (lj > *nlev) *nlev = lj;
-      bool d = false;
-      for (int p = cp[j]; p < cp[j + 1]; ++p) {
-        const int i = ri[p];
-        if (i < 0 || i >= n) return 3;
-        if (i == j) { d = true; continue; }
-        if (up ? i > j : i < j) return 1;
-        if (lev[i] < lj) lev[i] = lj;
-      }
-      nodiag |= !d;
-    }
-    return nodiag ? 2 : 0;
-  };
-  *upper = true;
-  int r = pass(true);
-  if (r == 1) {
-    *upper = false;
-    r = pass(false);
-  }
-  return r;
-}
 
 // True once event e has completed (or failed: a waiter then stops waiting).
 bool event_passed(cudaEvent_t e) {
@@ -1424,9 +1387,19 @@ diaf_status diaf_level_schedule(int32_t n, const int32_t* colptr, const int32_t*
   if (colptr[0] != 0) return fail(DIAF_EINVAL, "colptr[0] must be 0");
   for (int32_t j = 0; j < n; ++j)
     if (colptr[j + 1] < colptr[j]) return fail(DIAF_EINVAL, "colptr must be non-decreasing");
-  int nl = 0;
+  // the walk of the apply's preparation, on the whole structure: an upper V,
+  // else a lower one
+  const size_t nn = (size_t)n, nnz = (size_t)colptr[n];
+  std::vector<int32_t> scratch(4 * nn + 1 + nnz);
+  LevelWalk w{level, scratch.data(), scratch.data() + nn, scratch.data() + 2 * nn, scratch.data() + 4 * nn + 1,
+              scratch.data() + 3 * nn, 0};
   bool up = true;
-  const int r = level_schedule_host(n, colptr, rowidx, level, &nl, &up);
+  int r = level_walk(n, colptr, rowidx, nullptr, 0, true, nullptr, w);
+  if (r == 1) {
+    up = false;
+    r = level_walk(n, colptr, rowidx, nullptr, 0, false, nullptr, w);
+  }
+  const int nl = w.nlev;
   if (r == 1) return fail(DIAF_EINVAL, "V is not triangular");
   if (r == 2) return fail(DIAF_EINVAL, "V has a missing diagonal entry");
   if (r == 3) return fail(DIAF_EINVAL, "V has a row index out of range");

@@ -91,3 +91,33 @@ def test_structure_errors(D):
     assert "out of range" in str(e.value)
     lev, nlev, up = D.level_schedule(np.zeros(1, np.int32), np.zeros(0, np.int32))
     assert nlev == 0 and lev.size == 0
+
+
+def rowwise_levels(cp, ri, n, upper):
+    """Depth of every row from V's rows (the transpose of the columns the
+    library walks): rows in the solve's order, each one level below the
+    deepest row it reads."""
+    M = sp.csc_matrix((np.ones(len(ri)), ri, cp), shape=(n, n)).tocsr()
+    lev = np.zeros(n, dtype=np.int64)
+    order = range(n - 1, -1, -1) if upper else range(n)
+    for i in order:
+        deps = [j for j in M.indices[M.indptr[i]:M.indptr[i + 1]] if j != i]
+        lev[i] = max((lev[j] + 1 for j in deps), default=0)
+    return lev
+
+
+@pytest.mark.parametrize("name,lower", [("convdiff32", False), ("helmholtz40", False), ("convdiff32", True)])
+def test_levels_of_the_oracles_v(D, name, lower):
+    """The V the method builds on a workload (the oracle's, upper or lower
+    rule): the library's walk against the row-wise depths."""
+    import oracle as O
+    from workloads import lower_budget, make_workload
+    w = make_workload(name)
+    rule, budget = (O.RULE_LOWER, lower_budget(w.A)) if lower else (w.vrule, w.budget)
+    o = O.factor(w.A, w.PW, rule, budget, alg="S", tie_tol=w.tie_tol)
+    cp = np.ascontiguousarray(o.voff, np.int32)
+    ri = np.ascontiguousarray(o.Vrowidx, np.int32)
+    lev, nlev, up = D.level_schedule(cp, ri)
+    want = rowwise_levels(cp, ri, w.n, not lower)
+    assert bool(up) == (not lower)
+    assert np.array_equal(lev, want) and nlev == want.max() + 1

@@ -30,7 +30,7 @@ def _worker(rank, world, port, out):
 def test_two_rank_whole_job_rate():
     import torch.multiprocessing as mp
     port = _free_port()
-    with mp.Manager() as man:
+    with mp.get_context("spawn").Manager() as man:  # no fork of a process that may run threads
         out = man.dict()
         mp.start_processes(_worker, args=(2, port, out), nprocs=2, start_method="spawn", join=True)
         res = dict(out)

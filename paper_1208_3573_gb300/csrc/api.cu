@@ -187,17 +187,21 @@ struct Pool {
   ~Pool() { release(); }
 };
 
+// Per-device tables of the library (event cache, side streams) have this
+// many slots; devices beyond them go without (fresh events, no side stream).
+constexpr int kDeviceSlots = 64;
+
 // CUDA events of the factor handles, recycled per device: a setup takes
 // kEvents of them, and creating them anew each time cost host time in front
 // of the setup's first device operation.
 struct EventCache {
   std::mutex mu;
-  std::vector<cudaEvent_t> free[64];
+  std::vector<cudaEvent_t> free[kDeviceSlots];
 };
 EventCache g_events;
 
 cudaError_t event_get(cudaEvent_t* e, int dev) {
-  if (dev >= 0 && dev < 64) {
+  if (dev >= 0 && dev < kDeviceSlots) {
     std::lock_guard<std::mutex> lock(g_events.mu);
     std::vector<cudaEvent_t>& v = g_events.free[dev];
     if (!v.empty()) {
@@ -211,7 +215,7 @@ cudaError_t event_get(cudaEvent_t* e, int dev) {
 
 void event_put(cudaEvent_t e, int dev) {
   if (!e) return;
-  if (dev >= 0 && dev < 64) {
+  if (dev >= 0 && dev < kDeviceSlots) {
     std::lock_guard<std::mutex> lock(g_events.mu);
     if (g_events.free[dev].size() < 256) {
       g_events.free[dev].push_back(e);
@@ -252,7 +256,6 @@ struct Mirror {
   bool busy = false;
 };
 Mirror g_mirror;
-constexpr int kMirrorDevices = 64;
 std::atomic<long long> g_prep_streamed{0}, g_prep_copied{0};
 
 // Takes the mirror for F (F->n, F->nnz_v known) when it is free; grows it
@@ -305,9 +308,9 @@ bool mirror_acquire(diaf_factors* F) {
 // nullptr when it cannot be had, and the caller stays on its own stream).
 cudaStream_t side_stream() {
   static std::mutex mu;
-  static cudaStream_t st[kMirrorDevices] = {};
+  static cudaStream_t st[kDeviceSlots] = {};
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMirrorDevices) {
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDeviceSlots) {
     (void)cudaGetLastError();
     return nullptr;
   }
